@@ -1,0 +1,225 @@
+/*
+ * cmc.h - C ABI of the GB300 library for the per-timestep hot path of the
+ * Henon Monte Carlo method for collisional star clusters (Pattabiraman et
+ * al., "A Parallel Monte Carlo Code for Simulating Collisional N-body
+ * Systems", section 2.1 and section 3.3).
+ *
+ * One timestep (cmc_step) advances every bound star of every cluster:
+ *   1. relaxation timestep: Eq. 7 averaged on bins of bin_size consecutive
+ *      stars (section 3.3), dt = minimum over bins;
+ *   2. two-body relaxation of radial neighbours (2j, 2j+1) (section 2.1
+ *      step 3(i));
+ *   3. new orbits: turning points by bisection on Q of Eq. 12 and a new
+ *      radius by the rejection of Eqs. 13-15 (section 2.1 step 5);
+ *      stars with E >= 0 escape;
+ *   4. sort by radius (section 2.1 step 6), ties by id, escaped stars last;
+ *   5. shell potential of Eqs. 1-5 and the energy correction for the orbit
+ *      having been drawn in the old potential (section 2.1 step 6).
+ * Random numbers come from a counter-based generator (Philox4x32-10) keyed
+ * by the cluster seed and indexed by (star id, step, stream tag, trial), so
+ * results do not depend on thread layout, batching or resumption.
+ *
+ * Units: G = 1 (Henon N-body units).  State arrays are structure-of-arrays:
+ * r (radius), vr (radial velocity), vt (transverse speed, >= 0), m (mass)
+ * as double, id as uint32.  An ensemble of clusters is stored back to back;
+ * cluster c owns n_per_cluster[c] consecutive entries.  After every call
+ * the stars of each cluster are sorted by (r, id) with escaped stars
+ * (r = +inf) at the end ordered by id.
+ *
+ * Conventions for every function:
+ *   - Status codes only; nothing aborts or throws across the ABI.
+ *   - ptr_kind 0: the array arguments are host pointers; 1: device
+ *     pointers (for example from torch tensors) on the library's device.
+ *   - Work is ordered on the context's CUDA stream (the caller's stream,
+ *     or the legacy default stream when NULL).  Calls that return host
+ *     data or a status that depends on device results synchronise it.
+ *   - The library owns all memory it allocates; caller arrays are copied
+ *     and never retained.  A context is used by one host thread at a time.
+ *   - A device-side error (bounded wait expired, invalid state) poisons the
+ *     context: later calls return CMC_EPOISONED.  cmc_last_error() gives
+ *     text for the last failure.
+ */
+#ifndef CMC_H
+#define CMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cmc_ctx cmc_ctx;
+
+typedef enum {
+    CMC_OK = 0,
+    CMC_EINVAL = 1,     /* bad argument or invalid input state */
+    CMC_ENOMEM = 2,     /* device or host allocation failed */
+    CMC_ECUDA = 3,      /* a CUDA runtime call failed */
+    CMC_ENOCONV = 4,    /* reserved: a bounded iteration did not converge */
+    CMC_ETIMEOUT = 5,   /* a bounded device wait gave up (context poisoned) */
+    CMC_EPOISONED = 6   /* an earlier device error poisoned the context */
+} cmc_status;
+
+/* Per-cluster counters returned by cmc_get_stats (cumulative). */
+enum {
+    CMC_STAT_ESCAPED = 0,     /* stars that reached E >= 0 and left */
+    CMC_STAT_DEGENERATE = 1,  /* orbits with rmax <= rmin or F = 0, kept in place */
+    CMC_STAT_CAP_HITS = 2,    /* rejection ran out of trials, star kept in place */
+    CMC_STAT_TRIALS = 3,      /* rejection trials drawn */
+    CMC_STAT_VIOLATIONS = 4,  /* trials with g(s) > F (bound exceeded) */
+    CMC_STAT_CLAMPS = 5,      /* energy corrections with T' < 0 set to 0 */
+    CMC_STAT_ANGLE_FAILS = 6, /* 64 failed unit-disk draws (never expected) */
+    CMC_STAT_TIES = 7,        /* runs of equal radii ordered by id */
+    CMC_NSTATS = 8
+};
+
+typedef struct {
+    int32_t precision;          /* 0: FP64 throughout; 1: mixed (orbit search,
+                                   bound and accept tests in FP32, turning
+                                   points and accepted orbit in FP64) */
+    int32_t bin_size;           /* stars per timestep bin, even, >= 2 (20) */
+    double theta_max;           /* maximum deflection angle of Eq. 7 (pi/2) */
+    double gamma;               /* Coulomb logarithm ln(gamma N) (0.1, Eq. 20) */
+    int32_t max_trials;         /* rejection trials per star per step (1000) */
+    int32_t energy_correction;  /* 1: apply the section 2.1 step 6 correction */
+    int32_t orbit_block;        /* threads per block of the orbit kernel (0: auto) */
+    int32_t reserved;
+} cmc_config;
+
+/* Fill cfg with the defaults shown above. */
+void cmc_config_default(cmc_config *cfg);
+
+/*
+ * Create a context holding n_clusters clusters.
+ *   n_per_cluster (host, n_clusters): stars per cluster, each >= 1.
+ *   seeds (host, n_clusters): generator key of each cluster.
+ *   r, vr, vt, m (ptr_kind, sum n doubles), id (ptr_kind, sum n uint32):
+ *     the stars, concatenated cluster by cluster, in any order.  Requires
+ *     r > 0 finite, vt >= 0, m >= 0, all finite, ids unique per cluster.
+ *   stream: cudaStream_t to order work on (NULL: legacy default stream).
+ * The stars are sorted by (r, id) and their potential computed.  The
+ * Coulomb logarithm of cluster c is ln(gamma * n_per_cluster[c]).
+ * Errors: CMC_EINVAL (arguments or state), CMC_ENOMEM, CMC_ECUDA.
+ * On error *out is NULL.
+ */
+cmc_status cmc_init(cmc_ctx **out, const cmc_config *cfg, int32_t n_clusters,
+                    const int64_t *n_per_cluster, const uint64_t *seeds,
+                    const double *r, const double *vr, const double *vt,
+                    const double *m, const uint32_t *id, int32_t ptr_kind,
+                    void *stream);
+
+/* Advance every cluster by n_steps timesteps (n_steps >= 0).  The step
+ * sequence is captured once in a CUDA graph and replayed.  Synchronises
+ * the stream at the end to check device error flags. */
+cmc_status cmc_step(cmc_ctx *ctx, int32_t n_steps);
+
+/* Total energies per cluster of the bound stars (section 2.1 step 6):
+ * out (host, n_clusters x 3) = {K, W, E} with K = 1/2 sum m v^2,
+ * W = -G sum_{i<j} m_i m_j / max(r_i, r_j), E = K + W. */
+cmc_status cmc_energy(cmc_ctx *ctx, double *out);
+
+/* Lagrangian radii: for each cluster and each fraction f in fracs (host,
+ * nf values in [0, 1]) the radius r_k of the first bound star whose
+ * enclosed mass M_k = sum_{i<=k} m_i reaches f times the bound mass.
+ * out: host, n_clusters x nf. */
+cmc_status cmc_lagrange_radii(cmc_ctx *ctx, const double *fracs, int32_t nf, double *out);
+
+/* Copy the state out (sorted as described above).  Any array may be NULL.
+ * phi receives the potential at each star (0 for escaped stars); step the
+ * number of steps taken so far (host pointer, may be NULL). */
+cmc_status cmc_get_state(cmc_ctx *ctx, double *r, double *vr, double *vt, double *m,
+                         uint32_t *id, double *phi, int64_t *step, int32_t ptr_kind);
+
+/* Replace the state of every cluster (same sizes as at cmc_init) and set
+ * the step counter; the stars are re-sorted and the potential recomputed.
+ * Escaped stars may be passed with r = +inf.  A state obtained from
+ * cmc_get_state resumes bit for bit. */
+cmc_status cmc_set_state(cmc_ctx *ctx, const double *r, const double *vr, const double *vt,
+                         const double *m, const uint32_t *id, int64_t step,
+                         int32_t ptr_kind);
+
+/* Bound stars per cluster: out (host, n_clusters). */
+cmc_status cmc_get_nbound(cmc_ctx *ctx, int64_t *out);
+
+/* Last timestep per cluster: out (host, n_clusters). */
+cmc_status cmc_get_dt(cmc_ctx *ctx, double *out);
+
+/* Cumulative counters: out (host, n_clusters x CMC_NSTATS). */
+cmc_status cmc_get_stats(cmc_ctx *ctx, int64_t *out);
+
+/* Number of kernels one cmc_step timestep launches. */
+int32_t cmc_kernels_per_step(const cmc_ctx *ctx);
+
+/* Order later work on another stream (cudaStream_t, NULL: default). */
+cmc_status cmc_set_stream(cmc_ctx *ctx, void *stream);
+
+/* Text of the last failure of this context ("" if none); ctx may be NULL
+ * for failures of cmc_init or of the stage functions below. */
+const char *cmc_last_error(const cmc_ctx *ctx);
+
+/* Release the context and its device memory (NULL is allowed). */
+void cmc_destroy(cmc_ctx *ctx);
+
+/* ---------------------------------------------------------------------
+ * Stage functions: one step of the hot path on caller-owned DEVICE
+ * arrays of a single cluster of n stars, ordered on `stream`.  They
+ * allocate their scratch with cudaMallocAsync on that stream and return
+ * once the work is enqueued (except where stated).  Arrays are device
+ * pointers; sorted inputs are sorted by (r, id).
+ * ------------------------------------------------------------------- */
+
+/* Counter-based RNG (section 3.6's per-star streams): out[4i..4i+3] =
+ * Philox4x32-10 of counter ctr[4i..4i+3] under key seed. */
+cmc_status cmc_rng_philox(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *out,
+                          void *stream);
+
+/* Sort by radius (section 2.1 step 6): perm[j] = input index of the star
+ * that goes to slot j, order (r, id) with r = +inf last by id.  This is the
+ * timestep's sort: a stable radix sort by r followed by ordering equal
+ * radii by id. */
+cmc_status cmc_sort_radius(int64_t n, const double *r, const uint32_t *id, uint32_t *perm,
+                           void *stream);
+
+/* Shell potential, Eqs. 1-5 (scan form), of n sorted stars (all bound).
+ * phi: n doubles out.  M (may be NULL): enclosed mass M_k out. */
+cmc_status cmc_potential(int64_t n, const double *r, const double *m, double *phi, double *M,
+                         void *stream);
+
+/* Relaxation timestep, Eq. 7 on bins (section 3.3), of n sorted stars:
+ * nbin (ceil(n/bin_size) doubles out) bin densities, dt (1 double out,
+ * device) the minimum over bins.  pref = (theta_max/(pi/2)) (pi/32). */
+cmc_status cmc_timestep(int64_t n, const double *r, const double *vr, const double *vt,
+                        const double *m, int32_t bin_size, double theta_max, double lnL,
+                        double *nbin, double *dt, void *stream);
+
+/* Two-body relaxation (section 2.1 step 3) of pairs (2j, 2j+1) of n
+ * sorted stars, in place on vr, vt; nbin from cmc_timestep; dt, lnL on
+ * the host. */
+cmc_status cmc_relax(int64_t n, double *vr, double *vt, const double *m, const uint32_t *id,
+                     const double *nbin, int32_t bin_size, double dt, double lnL,
+                     uint64_t seed, uint32_t step, void *stream);
+
+/* New orbits (section 2.1 step 5) of n sorted stars with potential phi:
+ * per star r_new, vr_new, vt_new, phi_new (= Phi_old(r_new)), rmin, rmax,
+ * F and code (0 moved, 1 escaped, 2 degenerate, 3 trial cap); escaped
+ * stars get r_new = +inf.  Any output except r_new may be NULL.
+ * precision: 0 FP64, 1 mixed. */
+cmc_status cmc_orbit(int64_t n, const double *r, const double *phi, const double *vr,
+                     const double *vt, const uint32_t *id, uint64_t seed, uint32_t step,
+                     int32_t max_trials, int32_t precision, double *r_new, double *vr_new,
+                     double *vt_new, double *phi_new, double *rmin, double *rmax, double *F,
+                     int32_t *code, void *stream);
+
+/* Energy correction (section 2.1 step 6) of n sorted stars in the new
+ * potential phi, in place on vr, vt; r_old and c = Phi_old(r_old) -
+ * Phi_old(r_new) per star (sorted with the stars). */
+cmc_status cmc_energy_correction(int64_t n, const double *r, const double *phi, double *vr,
+                                 double *vt, const double *r_old, const double *c,
+                                 void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CMC_H */

@@ -1,0 +1,251 @@
+"""GB300 hot path of the Henon Monte Carlo method (Pattabiraman et al.).
+
+Python face of libcmc.so.  ``Cluster`` wraps a context (cmc_init /
+cmc_step / cmc_energy / cmc_lagrange_radii ...); the ``stage_*`` functions
+wrap the single-step entry points on torch CUDA tensors.  PyTorch only
+provides device memory and streams; every step runs in the library's
+kernels.  The binding raises if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _native
+from ._native import CMCError, STAT_NAMES, cmc_config, check, load
+
+__all__ = ["Cluster", "CMCError", "config", "load", "STAT_NAMES", "stage_philox",
+           "stage_sort_radius", "stage_potential", "stage_timestep", "stage_relax",
+           "stage_orbit", "stage_energy_correction"]
+
+
+def config(**kw) -> cmc_config:
+    """cmc_config with the library defaults, overridden by keyword."""
+    cfg = cmc_config()
+    load().cmc_config_default(ctypes.byref(cfg))
+    for k, v in kw.items():
+        setattr(cfg, k, v)
+    return cfg
+
+
+def _ptr(a):
+    """Address of a numpy array or torch tensor (contiguous)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    assert a.is_contiguous()
+    return a.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+class Cluster:
+    """One or more clusters advanced together by the CUDA library.
+
+    state: dict with r, vr, vt, m (float64) and id (uint32) arrays, either
+    numpy (host) or torch CUDA tensors (device), clusters concatenated.
+    sizes: stars per cluster (default: one cluster); seeds: one per cluster.
+    """
+
+    def __init__(self, state, seeds, sizes=None, stream=None, **cfg):
+        self.lib = load()
+        r = state["r"]
+        n = int(r.shape[0])
+        sizes = [n] if sizes is None else [int(s) for s in sizes]
+        seeds = [int(s) for s in np.atleast_1d(seeds)]
+        if sum(sizes) != n or len(seeds) != len(sizes):
+            raise ValueError("sizes must sum to the number of stars, one seed per cluster")
+        self.n = n
+        self.sizes = sizes
+        self.n_clusters = len(sizes)
+        self.cfg = config(**cfg)
+        self.stream = _stream_ptr(stream)
+        kind = 0 if isinstance(r, np.ndarray) else 1
+        arrs = [self._prep(state[k], k, kind) for k in ("r", "vr", "vt", "m", "id")]
+        self._sizes = np.asarray(sizes, dtype=np.int64)
+        self._seeds = np.asarray(seeds, dtype=np.uint64)
+        ctx = ctypes.c_void_p()
+        st = self.lib.cmc_init(ctypes.byref(ctx), ctypes.byref(self.cfg), self.n_clusters,
+                               self._sizes.ctypes.data, self._seeds.ctypes.data,
+                               *[_ptr(a) for a in arrs], kind, self.stream)
+        check(st, None)
+        self.ctx = ctx
+
+    @staticmethod
+    def _prep(a, name, kind):
+        if kind == 0:
+            return np.ascontiguousarray(a, dtype=np.uint32 if name == "id" else np.float64)
+        import torch
+        want = torch.int32 if name == "id" else torch.float64
+        if name == "id" and a.dtype in (torch.int32, torch.uint32):
+            return a.contiguous()
+        return a.to(want).contiguous()
+
+    # -- lifecycle ---------------------------------------------------------
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.cmc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- API ---------------------------------------------------------------
+    def step(self, n_steps: int = 1):
+        check(self.lib.cmc_step(self.ctx, int(n_steps)), self.ctx)
+        return self
+
+    def energy(self) -> np.ndarray:
+        out = np.zeros((self.n_clusters, 3))
+        check(self.lib.cmc_energy(self.ctx, out.ctypes.data), self.ctx)
+        return out
+
+    def lagrange_radii(self, fracs) -> np.ndarray:
+        fr = np.ascontiguousarray(fracs, dtype=np.float64)
+        out = np.zeros((self.n_clusters, fr.shape[0]))
+        check(self.lib.cmc_lagrange_radii(self.ctx, fr.ctypes.data, fr.shape[0],
+                                          out.ctypes.data), self.ctx)
+        return out
+
+    def get_state(self, out=None):
+        """Sorted state as numpy arrays (or into the given torch tensors)."""
+        step = np.zeros(1, dtype=np.int64)
+        if out is None:
+            out = {k: np.empty(self.n) for k in ("r", "vr", "vt", "m", "phi")}
+            out["id"] = np.empty(self.n, dtype=np.uint32)
+            kind = 0
+        else:
+            kind = 0 if isinstance(out["r"], np.ndarray) else 1
+        check(self.lib.cmc_get_state(self.ctx, _ptr(out.get("r")), _ptr(out.get("vr")),
+                                     _ptr(out.get("vt")), _ptr(out.get("m")),
+                                     _ptr(out.get("id")), _ptr(out.get("phi")),
+                                     step.ctypes.data, kind), self.ctx)
+        out["step"] = int(step[0])
+        return out
+
+    def set_state(self, state, step: int):
+        kind = 0 if isinstance(state["r"], np.ndarray) else 1
+        arrs = [self._prep(state[k], k, kind) for k in ("r", "vr", "vt", "m", "id")]
+        check(self.lib.cmc_set_state(self.ctx, *[_ptr(a) for a in arrs], int(step), kind),
+              self.ctx)
+
+    def nbound(self) -> np.ndarray:
+        out = np.zeros(self.n_clusters, dtype=np.int64)
+        check(self.lib.cmc_get_nbound(self.ctx, out.ctypes.data), self.ctx)
+        return out
+
+    def dt(self) -> np.ndarray:
+        out = np.zeros(self.n_clusters)
+        check(self.lib.cmc_get_dt(self.ctx, out.ctypes.data), self.ctx)
+        return out
+
+    def stats(self) -> list:
+        out = np.zeros((self.n_clusters, _native.CMC_NSTATS), dtype=np.int64)
+        check(self.lib.cmc_get_stats(self.ctx, out.ctypes.data), self.ctx)
+        return [dict(zip(STAT_NAMES, (int(v) for v in row))) for row in out]
+
+    def kernels_per_step(self) -> int:
+        return int(self.lib.cmc_kernels_per_step(self.ctx))
+
+    def set_stream(self, stream):
+        self.stream = _stream_ptr(stream)
+        check(self.lib.cmc_set_stream(self.ctx, self.stream), self.ctx)
+
+
+# --------------------------------------------------------------- stages
+# Single-cluster entry points on torch CUDA tensors (sorted inputs).
+def _t(a):
+    return _ptr(a)
+
+
+def stage_philox(ctr, seed: int, stream=None):
+    import torch
+    out = torch.empty_like(ctr)
+    check(load().cmc_rng_philox(ctr.shape[0], _t(ctr), int(seed), _t(out),
+                                _stream_ptr(stream)))
+    return out
+
+
+def stage_sort_radius(r, ids, stream=None):
+    import torch
+    perm = torch.empty(r.shape[0], dtype=torch.int32, device=r.device)
+    check(load().cmc_sort_radius(r.shape[0], _t(r), _t(ids), _t(perm), _stream_ptr(stream)))
+    return perm
+
+
+def stage_potential(r, m, want_M: bool = False, stream=None):
+    import torch
+    phi = torch.empty_like(r)
+    M = torch.empty_like(r) if want_M else None
+    check(load().cmc_potential(r.shape[0], _t(r), _t(m), _t(phi), _t(M), _stream_ptr(stream)))
+    return (phi, M) if want_M else phi
+
+
+def stage_timestep(r, vr, vt, m, lnL: float, bin_size: int = 20, theta_max: float = None,
+                   stream=None):
+    import math
+
+    import torch
+    if theta_max is None:
+        theta_max = math.pi / 2
+    n = r.shape[0]
+    nbin = torch.zeros(max(1, (n + bin_size - 1) // bin_size), dtype=torch.float64,
+                       device=r.device)
+    dt = torch.zeros(1, dtype=torch.float64, device=r.device)
+    check(load().cmc_timestep(n, _t(r), _t(vr), _t(vt), _t(m), bin_size, theta_max, lnL,
+                              _t(nbin), _t(dt), _stream_ptr(stream)))
+    return dt, nbin[: (n + bin_size - 1) // bin_size]
+
+
+def stage_relax(vr, vt, m, ids, nbin, dt: float, lnL: float, seed: int, step: int,
+                bin_size: int = 20, stream=None):
+    vr = vr.clone()
+    vt = vt.clone()
+    check(load().cmc_relax(vr.shape[0], _t(vr), _t(vt), _t(m), _t(ids), _t(nbin), bin_size,
+                           float(dt), float(lnL), int(seed), int(step), _stream_ptr(stream)))
+    return vr, vt
+
+
+def stage_orbit(r, phi, vr, vt, ids, seed: int, step: int, max_trials: int = 1000,
+                precision: int = 0, stream=None):
+    import torch
+    n = r.shape[0]
+    f = lambda: torch.empty(n, dtype=torch.float64, device=r.device)
+    out = {k: f() for k in ("r_new", "vr", "vt", "phi_new", "rmin", "rmax", "F")}
+    out["code"] = torch.empty(n, dtype=torch.int32, device=r.device)
+    check(load().cmc_orbit(n, _t(r), _t(phi), _t(vr), _t(vt), _t(ids), int(seed), int(step),
+                           int(max_trials), int(precision), _t(out["r_new"]), _t(out["vr"]),
+                           _t(out["vt"]), _t(out["phi_new"]), _t(out["rmin"]),
+                           _t(out["rmax"]), _t(out["F"]), _t(out["code"]),
+                           _stream_ptr(stream)))
+    return out
+
+
+def stage_energy_correction(r, phi, vr, vt, r_old, c, stream=None):
+    vr = vr.clone()
+    vt = vt.clone()
+    check(load().cmc_energy_correction(r.shape[0], _t(r), _t(phi), _t(vr), _t(vt), _t(r_old),
+                                       _t(c), _stream_ptr(stream)))
+    return vr, vt

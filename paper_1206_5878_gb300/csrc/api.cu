@@ -1,0 +1,642 @@
+// C ABI (include/cmc.h): the context that advances clusters timestep by
+// timestep, and the stage functions that run one step of the hot path on
+// caller arrays.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cmc_host.hpp"
+#include "../../include/cmc.h"
+
+using namespace cmc;
+
+struct cmc_ctx {
+  cmc_config cfg{};
+  cudaStream_t stream = nullptr;      // caller's stream (may be the default)
+  cudaStream_t cap = nullptr;         // private stream used to capture the graph
+  int device = 0;
+  SegLayout L;
+  SortWork W;
+  double pref = 0.0;
+  // state (sorted SoA)
+  double *r = nullptr, *x = nullptr, *vr = nullptr, *vt = nullptr, *m = nullptr,
+         *phi = nullptr;
+  uint32_t* id = nullptr;
+  float2* t32 = nullptr;
+  // scratch
+  uint64_t* keys = nullptr;
+  uint32_t* vals = nullptr;
+  Payload* pay = nullptr;
+  double *r_old = nullptr, *cc = nullptr, *nbin = nullptr;
+  double *tile_a = nullptr, *tile_b = nullptr, *tile_c = nullptr, *Mbuf = nullptr,
+         *out3 = nullptr, *fr = nullptr, *lag = nullptr;
+  uint32_t* err = nullptr;
+  uint32_t* step = nullptr;
+  int64_t steps_taken = 0;
+  cudaGraphExec_t exec = nullptr;
+  bool poisoned = false;
+  std::string last_error;
+  int kernels_per_step = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+cmc_status fail(cmc_ctx* ctx, cmc_status s, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  else g_err = msg;
+  return s;
+}
+
+cmc_status cuda_fail(cmc_ctx* ctx, cudaError_t e, const char* where) {
+  std::string msg = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return fail(ctx, CMC_ENOMEM, msg);
+  return fail(ctx, CMC_ECUDA, msg);
+}
+
+template <class T>
+cudaError_t dalloc(T*& p, size_t count, cudaStream_t st) {
+  return cudaMallocAsync((void**)&p, sizeof(T) * (count ? count : 1), st);
+}
+
+template <class T>
+void dfree(T*& p, cudaStream_t st) {
+  if (p) cudaFreeAsync(p, st);
+  p = nullptr;
+}
+
+double t_rel_prefactor(double theta_max) {
+  return (theta_max / (kPi / 2)) * (kPi / 32);
+}
+
+cmc_status check_err_flags(cmc_ctx* ctx) {
+  uint32_t e = 0;
+  cudaError_t ce = cudaMemcpyAsync(&e, ctx->err, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                                   ctx->stream);
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(ctx->stream);
+  if (ce != cudaSuccess) {
+    ctx->poisoned = true;
+    return cuda_fail(ctx, ce, "device work");
+  }
+  if (e == 0) return CMC_OK;
+  ctx->poisoned = true;
+  std::string msg = "device error flags:";
+  if (e & kErrTimeout) msg += " bounded wait expired in the sort look-back;";
+  if (e & kErrTies) msg += " run of equal radii too long to order by id;";
+  if (e & kErrInput) msg += " invalid input state;";
+  if (e & kErrNonFinite) msg += " non-finite value;";
+  if (e & kErrTimeout) return fail(ctx, CMC_ETIMEOUT, msg);
+  if (e & kErrInput) {
+    ctx->poisoned = false;  // nothing was changed on the device state yet
+    return fail(ctx, CMC_EINVAL, msg);
+  }
+  return fail(ctx, CMC_ECUDA, msg);
+}
+
+// Sort the staged stars in r, vr, vt, m, id by (r, id) per segment and
+// compute nb and the potential.  Ids must be unique per segment.
+void order_state(cmc_ctx* c, cudaStream_t st) {
+  const SegLayout& L = c->L;
+  launch_id_keys(L, c->id, c->keys, st);
+  sort_segments(L, c->W, c->keys, c->vals, 0, 4, true, c->err, st);
+  launch_check_ids(L, c->keys, c->err, st);
+  launch_rekey_radius(L, c->vals, c->r, c->id, c->keys, st);
+  sort_segments(L, c->W, c->keys, c->vals, 0, 8, false, c->err, st);
+  launch_make_keys(L, c->r, c->vr, c->vt, c->m, c->id, c->W.keys_alt, c->pay, st);
+  launch_gather(L, c->keys, c->vals, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, nullptr,
+                nullptr, st);
+  launch_nb_from_keys(L, c->keys, st);
+  cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
+  launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32, nullptr, false,
+                   st);
+}
+
+// The kernels of one timestep, in the order of section 3.3.
+void record_step(cmc_ctx* c, cudaStream_t st) {
+  const SegLayout& L = c->L;
+  const bool mixed = c->cfg.precision == 1;
+  launch_bins(L, c->r, c->vr, c->vt, c->m, c->nbin, c->pref, st);
+  launch_relax(L, c->vr, c->vt, c->m, c->id, c->nbin, c->step, st);
+  launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
+               mixed ? c->t32 : nullptr, c->vr, c->vt, c->m, c->id, c->step, c->keys, c->pay,
+               nullptr, c->cfg.orbit_block, st);
+  sort_segments(L, c->W, c->keys, c->vals, 0, 8, true, c->err, st);
+  launch_tiefix(L, c->keys, c->vals, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)),
+                c->err, st);
+  launch_gather(L, c->keys, c->vals, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old,
+                c->cc, st);
+  launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
+                   mixed ? c->t32 : nullptr, nullptr, true, st);
+  if (c->cfg.energy_correction)
+    launch_correction(L, c->r, c->x, c->phi, c->vr, c->vt, c->r_old, c->cc, true, c->err, st);
+  launch_step_end(L, c->step, st);
+}
+
+int count_step_kernels(const cmc_ctx* c) {
+  // bins, relax, orbit, upsweep, hist scan, 8 passes, tie fix, gather,
+  // tile sums, potential, [correction], step end
+  return 3 + 2 + 8 + 1 + 1 + 2 + (c->cfg.energy_correction ? 1 : 0) + 1;
+}
+
+void free_ctx(cmc_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  double** ds[] = {&c->r, &c->x, &c->vr, &c->vt, &c->m, &c->phi, &c->r_old, &c->cc, &c->nbin,
+                   &c->tile_a, &c->tile_b, &c->tile_c, &c->Mbuf, &c->out3, &c->fr, &c->lag};
+  for (double** p : ds) dfree(*p, st);
+  dfree(c->id, st);
+  dfree(c->t32, st);
+  dfree(c->keys, st);
+  dfree(c->vals, st);
+  dfree(c->pay, st);
+  dfree(c->err, st);
+  dfree(c->step, st);
+  free_sort(c->W, st);
+  free_layout(c->L, st);
+  cudaStreamSynchronize(st);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+cmc_status copy_in(cmc_ctx* c, const double* r, const double* vr, const double* vt,
+                   const double* m, const uint32_t* id, int32_t ptr_kind) {
+  const size_t n = (size_t)c->L.n;
+  cudaMemcpyKind k = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaSuccess;
+  if (!e) e = cudaMemcpyAsync(c->r, r, n * sizeof(double), k, st);
+  if (!e) e = cudaMemcpyAsync(c->vr, vr, n * sizeof(double), k, st);
+  if (!e) e = cudaMemcpyAsync(c->vt, vt, n * sizeof(double), k, st);
+  if (!e) e = cudaMemcpyAsync(c->m, m, n * sizeof(double), k, st);
+  if (!e) e = cudaMemcpyAsync(c->id, id, n * sizeof(uint32_t), k, st);
+  if (e) return cuda_fail(c, e, "copy in");
+  return CMC_OK;
+}
+
+cmc_status load_state(cmc_ctx* c, const double* r, const double* vr, const double* vt,
+                      const double* m, const uint32_t* id, int32_t ptr_kind, bool allow_inf,
+                      int64_t step) {
+  cmc_status s = copy_in(c, r, vr, vt, m, id, ptr_kind);
+  if (s != CMC_OK) return s;
+  cudaStream_t st = c->stream;
+  cudaMemsetAsync(c->err, 0, sizeof(uint32_t), st);
+  uint32_t st32 = (uint32_t)step;
+  cudaMemcpyAsync(c->step, &st32, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+  launch_validate(c->L, c->r, c->vr, c->vt, c->m, allow_inf, c->err, st);
+  // a state that fails validation is not ordered (the sort needs finite keys)
+  s = check_err_flags(c);
+  if (s != CMC_OK) return s;
+  order_state(c, st);
+  cudaError_t e = cudaGetLastError();
+  if (e) return cuda_fail(c, e, "ordering the state");
+  s = check_err_flags(c);
+  if (s != CMC_OK) return s;
+  c->steps_taken = step;
+  return CMC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void cmc_config_default(cmc_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->precision = 0;
+  cfg->bin_size = 20;
+  cfg->theta_max = kPi / 2;
+  cfg->gamma = 0.1;
+  cfg->max_trials = 1000;
+  cfg->energy_correction = 1;
+  cfg->orbit_block = 0;
+}
+
+cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
+                    const int64_t* n_per_cluster, const uint64_t* seeds, const double* r,
+                    const double* vr, const double* vt, const double* m, const uint32_t* id,
+                    int32_t ptr_kind, void* stream) {
+  if (out) *out = nullptr;
+  if (!out || n_clusters < 1 || !n_per_cluster || !seeds || !r || !vr || !vt || !m || !id ||
+      (ptr_kind != 0 && ptr_kind != 1))
+    return fail(nullptr, CMC_EINVAL, "cmc_init: bad arguments");
+  cmc_config cfg;
+  if (cfg_in) cfg = *cfg_in;
+  else cmc_config_default(&cfg);
+  if ((cfg.precision != 0 && cfg.precision != 1) || cfg.bin_size < 2 || (cfg.bin_size & 1) ||
+      cfg.max_trials < 1 || cfg.max_trials > (1 << 24) || !(cfg.theta_max > 0.0) ||
+      !(cfg.gamma > 0.0) || cfg.orbit_block < 0 || cfg.orbit_block > 1024 ||
+      (cfg.orbit_block % 32))
+    return fail(nullptr, CMC_EINVAL, "cmc_init: bad configuration");
+  std::vector<int64_t> sizes(n_per_cluster, n_per_cluster + n_clusters);
+  std::vector<uint64_t> sd(seeds, seeds + n_clusters);
+  std::vector<double> lnL(n_clusters);
+  int64_t total = 0;
+  for (int c = 0; c < n_clusters; ++c) {
+    if (sizes[c] < 1) return fail(nullptr, CMC_EINVAL, "cmc_init: empty cluster");
+    total += sizes[c];
+    lnL[c] = std::log(cfg.gamma * (double)sizes[c]);
+  }
+  if (total >= (int64_t)1 << 31)
+    return fail(nullptr, CMC_EINVAL, "cmc_init: more than 2^31 - 1 stars");
+
+  cmc_ctx* c = new cmc_ctx();
+  c->cfg = cfg;
+  c->stream = (cudaStream_t)stream;
+  c->pref = t_rel_prefactor(cfg.theta_max);
+  cudaGetDevice(&c->device);
+  cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+  if (e) { cmc_status s = cuda_fail(nullptr, e, "cmc_init"); free_ctx(c); return s; }
+  cudaStream_t st = c->stream;
+  e = alloc_layout(c->L, sizes, sd, lnL, cfg.bin_size, st);
+  const size_t n = (size_t)total;
+  SegLayout& L = c->L;
+#define CMC_ALLOC(ptr, cnt) \
+  if (!e) e = dalloc(ptr, cnt, st);
+  CMC_ALLOC(c->r, n);
+  CMC_ALLOC(c->x, n);
+  CMC_ALLOC(c->vr, n);
+  CMC_ALLOC(c->vt, n);
+  CMC_ALLOC(c->m, n);
+  CMC_ALLOC(c->phi, n);
+  CMC_ALLOC(c->id, n);
+  if (cfg.precision == 1) CMC_ALLOC(c->t32, n);
+  CMC_ALLOC(c->keys, n);
+  CMC_ALLOC(c->vals, n);
+  CMC_ALLOC(c->pay, n);
+  CMC_ALLOC(c->r_old, n);
+  CMC_ALLOC(c->cc, n);
+  CMC_ALLOC(c->Mbuf, n);
+  CMC_ALLOC(c->nbin, (size_t)L.n_bins);
+  CMC_ALLOC(c->tile_a, (size_t)L.n_tiles);
+  CMC_ALLOC(c->tile_b, (size_t)L.n_tiles);
+  CMC_ALLOC(c->tile_c, (size_t)L.n_tiles);
+  CMC_ALLOC(c->out3, (size_t)3 * n_clusters);
+  CMC_ALLOC(c->err, 1);
+  CMC_ALLOC(c->step, 1);
+#undef CMC_ALLOC
+  if (!e) e = alloc_sort(c->W, L, 8, st);
+  if (e) { cmc_status s = cuda_fail(nullptr, e, "cmc_init: allocation"); free_ctx(c); return s; }
+  sort_prepare();
+  cmc_status s = load_state(c, r, vr, vt, m, id, ptr_kind, false, 0);
+  if (s != CMC_OK) {
+    g_err = c->last_error;
+    free_ctx(c);
+    return s;
+  }
+  c->kernels_per_step = count_step_kernels(c);
+  *out = c;
+  return CMC_OK;
+}
+
+cmc_status cmc_step(cmc_ctx* c, int32_t n_steps) {
+  if (!c || n_steps < 0) return fail(c, CMC_EINVAL, "cmc_step: bad arguments");
+  if (c->poisoned) return fail(c, CMC_EPOISONED, c->last_error);
+  if (n_steps == 0) return CMC_OK;
+  DeviceGuard g(c->device);
+  cudaError_t e;
+  if (!c->exec) {
+    cudaGraph_t graph;
+    e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+    if (e) return cuda_fail(c, e, "cmc_step: begin capture");
+    record_step(c, c->cap);
+    e = cudaStreamEndCapture(c->cap, &graph);
+    if (e) return cuda_fail(c, e, "cmc_step: capture");
+    e = cudaGraphInstantiate(&c->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e) { c->exec = nullptr; return cuda_fail(c, e, "cmc_step: instantiate"); }
+  }
+  for (int32_t i = 0; i < n_steps; ++i) {
+    e = cudaGraphLaunch(c->exec, c->stream);
+    if (e) return cuda_fail(c, e, "cmc_step: launch");
+  }
+  c->steps_taken += n_steps;
+  return check_err_flags(c);
+}
+
+cmc_status cmc_energy(cmc_ctx* c, double* out) {
+  if (!c || !out) return fail(c, CMC_EINVAL, "cmc_energy: bad arguments");
+  if (c->poisoned) return fail(c, CMC_EPOISONED, c->last_error);
+  DeviceGuard g(c->device);
+  launch_energy(c->L, c->r, c->vr, c->vt, c->m, c->tile_a, c->tile_b, c->tile_c, c->Mbuf,
+                c->out3, c->stream);
+  cudaError_t e = cudaMemcpyAsync(out, c->out3, sizeof(double) * 3 * c->L.n_seg,
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "cmc_energy");
+  return CMC_OK;
+}
+
+cmc_status cmc_lagrange_radii(cmc_ctx* c, const double* fracs, int32_t nf, double* out) {
+  if (!c || !fracs || !out || nf < 1 || nf > 4096)
+    return fail(c, CMC_EINVAL, "cmc_lagrange_radii: bad arguments");
+  for (int i = 0; i < nf; ++i)
+    if (!(fracs[i] >= 0.0 && fracs[i] <= 1.0))
+      return fail(c, CMC_EINVAL, "cmc_lagrange_radii: fraction outside [0, 1]");
+  if (c->poisoned) return fail(c, CMC_EPOISONED, c->last_error);
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  double *dfr = nullptr, *dout = nullptr;
+  cudaError_t e = dalloc(dfr, nf, st);
+  if (!e) e = dalloc(dout, (size_t)nf * c->L.n_seg, st);
+  if (!e) e = cudaMemcpyAsync(dfr, fracs, sizeof(double) * nf, cudaMemcpyHostToDevice, st);
+  if (!e) {
+    launch_energy(c->L, c->r, c->vr, c->vt, c->m, c->tile_a, c->tile_b, c->tile_c, c->Mbuf,
+                  c->out3, st);
+    launch_lagrange(c->L, c->r, c->Mbuf, dfr, nf, dout, st);
+    e = cudaMemcpyAsync(out, dout, sizeof(double) * nf * c->L.n_seg, cudaMemcpyDeviceToHost,
+                        st);
+  }
+  if (!e) e = cudaStreamSynchronize(st);
+  dfree(dfr, st);
+  dfree(dout, st);
+  if (e) return cuda_fail(c, e, "cmc_lagrange_radii");
+  return CMC_OK;
+}
+
+cmc_status cmc_get_state(cmc_ctx* c, double* r, double* vr, double* vt, double* m,
+                         uint32_t* id, double* phi, int64_t* step, int32_t ptr_kind) {
+  if (!c || (ptr_kind != 0 && ptr_kind != 1))
+    return fail(c, CMC_EINVAL, "cmc_get_state: bad arguments");
+  if (c->poisoned) return fail(c, CMC_EPOISONED, c->last_error);
+  DeviceGuard g(c->device);
+  const size_t n = (size_t)c->L.n;
+  cudaMemcpyKind k = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaSuccess;
+  if (!e && r) e = cudaMemcpyAsync(r, c->r, n * sizeof(double), k, st);
+  if (!e && vr) e = cudaMemcpyAsync(vr, c->vr, n * sizeof(double), k, st);
+  if (!e && vt) e = cudaMemcpyAsync(vt, c->vt, n * sizeof(double), k, st);
+  if (!e && m) e = cudaMemcpyAsync(m, c->m, n * sizeof(double), k, st);
+  if (!e && id) e = cudaMemcpyAsync(id, c->id, n * sizeof(uint32_t), k, st);
+  if (!e && phi) e = cudaMemcpyAsync(phi, c->phi, n * sizeof(double), k, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (e) return cuda_fail(c, e, "cmc_get_state");
+  if (step) *step = c->steps_taken;
+  return CMC_OK;
+}
+
+cmc_status cmc_set_state(cmc_ctx* c, const double* r, const double* vr, const double* vt,
+                         const double* m, const uint32_t* id, int64_t step, int32_t ptr_kind) {
+  if (!c || !r || !vr || !vt || !m || !id || step < 0 || (ptr_kind != 0 && ptr_kind != 1))
+    return fail(c, CMC_EINVAL, "cmc_set_state: bad arguments");
+  DeviceGuard g(c->device);
+  c->poisoned = false;
+  return load_state(c, r, vr, vt, m, id, ptr_kind, true, step);
+}
+
+cmc_status cmc_get_nbound(cmc_ctx* c, int64_t* out) {
+  if (!c || !out) return fail(c, CMC_EINVAL, "cmc_get_nbound: bad arguments");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaMemcpyAsync(out, c->L.nb, sizeof(int64_t) * c->L.n_seg,
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "cmc_get_nbound");
+  return CMC_OK;
+}
+
+cmc_status cmc_get_dt(cmc_ctx* c, double* out) {
+  if (!c || !out) return fail(c, CMC_EINVAL, "cmc_get_dt: bad arguments");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaMemcpyAsync(out, c->L.dt_last, sizeof(double) * c->L.n_seg,
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "cmc_get_dt");
+  return CMC_OK;
+}
+
+cmc_status cmc_get_stats(cmc_ctx* c, int64_t* out) {
+  if (!c || !out) return fail(c, CMC_EINVAL, "cmc_get_stats: bad arguments");
+  DeviceGuard g(c->device);
+  std::vector<unsigned long long> h((size_t)kStStride * c->L.n_seg);
+  cudaError_t e = cudaMemcpyAsync(h.data(), c->L.stats, sizeof(unsigned long long) * h.size(),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "cmc_get_stats");
+  for (int s = 0; s < c->L.n_seg; ++s)
+    for (int j = 0; j < CMC_NSTATS; ++j)
+      out[(size_t)s * CMC_NSTATS + j] = (int64_t)h[(size_t)s * kStStride + j];
+  return CMC_OK;
+}
+
+int32_t cmc_kernels_per_step(const cmc_ctx* c) { return c ? c->kernels_per_step : 0; }
+
+cmc_status cmc_set_stream(cmc_ctx* c, void* stream) {
+  if (!c) return fail(c, CMC_EINVAL, "cmc_set_stream: bad arguments");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "cmc_set_stream");
+  c->stream = (cudaStream_t)stream;
+  return CMC_OK;
+}
+
+const char* cmc_last_error(const cmc_ctx* c) {
+  return c ? c->last_error.c_str() : g_err.c_str();
+}
+
+void cmc_destroy(cmc_ctx* c) { free_ctx(c); }
+
+// ----------------------------------------------------------- stage API
+namespace {
+
+struct Stage {
+  SegLayout L;
+  cudaStream_t st;
+  cudaError_t e = cudaSuccess;
+  Stage(int64_t n, uint64_t seed, double lnL, int bin_size, cudaStream_t s) : st(s) {
+    std::vector<int64_t> sizes{n};
+    std::vector<uint64_t> sd{seed};
+    std::vector<double> ll{lnL};
+    e = alloc_layout(L, sizes, sd, ll, bin_size, st);
+  }
+  ~Stage() { free_layout(L, st); }
+};
+
+}  // namespace
+
+cmc_status cmc_rng_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out,
+                          void* stream) {
+  if (n < 0 || (n > 0 && (!ctr || !out))) return fail(nullptr, CMC_EINVAL, "cmc_rng_philox");
+  launch_philox(n, ctr, seed, out, (cudaStream_t)stream);
+  cudaError_t e = cudaGetLastError();
+  return e ? cuda_fail(nullptr, e, "cmc_rng_philox") : CMC_OK;
+}
+
+cmc_status cmc_sort_radius(int64_t n, const double* r, const uint32_t* id, uint32_t* perm,
+                           void* stream) {
+  if (n < 0 || n >= ((int64_t)1 << 31) || (n > 0 && (!r || !id || !perm)))
+    return fail(nullptr, CMC_EINVAL, "cmc_sort_radius: bad arguments");
+  if (n == 0) return CMC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Stage S(n, 0, 0.0, 20, st);
+  if (S.e) return cuda_fail(nullptr, S.e, "cmc_sort_radius");
+  SortWork W;
+  uint64_t* keys = nullptr;
+  uint32_t* err = nullptr;
+  cudaError_t e = alloc_sort(W, S.L, 8, st);
+  if (!e) e = dalloc(keys, n, st);
+  if (!e) e = dalloc(err, 1, st);
+  if (!e) {
+    sort_prepare();
+    cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
+    launch_make_keys(S.L, r, nullptr, nullptr, nullptr, id, keys, nullptr, st);
+    sort_segments(S.L, W, keys, perm, 0, 8, true, err, st);
+    launch_tiefix(S.L, keys, perm, id, 1, err, st);
+    e = cudaGetLastError();
+  }
+  dfree(keys, st);
+  dfree(err, st);
+  free_sort(W, st);
+  return e ? cuda_fail(nullptr, e, "cmc_sort_radius") : CMC_OK;
+}
+
+cmc_status cmc_potential(int64_t n, const double* r, const double* m, double* phi, double* M,
+                         void* stream) {
+  if (n < 0 || (n > 0 && (!r || !m || !phi)))
+    return fail(nullptr, CMC_EINVAL, "cmc_potential: bad arguments");
+  if (n == 0) return CMC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Stage S(n, 0, 0.0, 20, st);
+  if (S.e) return cuda_fail(nullptr, S.e, "cmc_potential");
+  double *x = nullptr, *ta = nullptr, *tb = nullptr;
+  cudaError_t e = dalloc(x, n, st);
+  if (!e) e = dalloc(ta, (size_t)S.L.n_tiles, st);
+  if (!e) e = dalloc(tb, (size_t)S.L.n_tiles, st);
+  if (!e) {
+    launch_recip(n, r, x, st);
+    launch_potential(S.L, r, x, m, ta, tb, phi, nullptr, M, false, st);
+    e = cudaGetLastError();
+  }
+  dfree(x, st);
+  dfree(ta, st);
+  dfree(tb, st);
+  return e ? cuda_fail(nullptr, e, "cmc_potential") : CMC_OK;
+}
+
+cmc_status cmc_timestep(int64_t n, const double* r, const double* vr, const double* vt,
+                        const double* m, int32_t bin_size, double theta_max, double lnL,
+                        double* nbin, double* dt, void* stream) {
+  if (n < 0 || bin_size < 2 || (bin_size & 1) || (n > 0 && (!r || !vr || !vt || !m || !nbin)) ||
+      !dt)
+    return fail(nullptr, CMC_EINVAL, "cmc_timestep: bad arguments");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (n == 0) {
+    const double inf = INFINITY;
+    cudaError_t e = cudaMemcpyAsync(dt, &inf, sizeof(double), cudaMemcpyHostToDevice, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    return e ? cuda_fail(nullptr, e, "cmc_timestep") : CMC_OK;
+  }
+  Stage S(n, 0, lnL, bin_size, st);
+  if (S.e) return cuda_fail(nullptr, S.e, "cmc_timestep");
+  launch_bins(S.L, r, vr, vt, m, nbin, t_rel_prefactor(theta_max), st);
+  cudaError_t e = cudaMemcpyAsync(dt, S.L.dt_bits, sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (!e) e = cudaGetLastError();
+  return e ? cuda_fail(nullptr, e, "cmc_timestep") : CMC_OK;
+}
+
+cmc_status cmc_relax(int64_t n, double* vr, double* vt, const double* m, const uint32_t* id,
+                     const double* nbin, int32_t bin_size, double dt, double lnL, uint64_t seed,
+                     uint32_t step, void* stream) {
+  if (n < 0 || bin_size < 2 || (bin_size & 1) || (n > 0 && (!vr || !vt || !m || !id || !nbin)))
+    return fail(nullptr, CMC_EINVAL, "cmc_relax: bad arguments");
+  if (n < 2) return CMC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Stage S(n, seed, lnL, bin_size, st);
+  if (S.e) return cuda_fail(nullptr, S.e, "cmc_relax");
+  uint32_t* dstep = nullptr;
+  cudaError_t e = dalloc(dstep, 1, st);
+  if (!e) e = cudaMemcpyAsync(S.L.dt_bits, &dt, sizeof(double), cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(dstep, &step, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+  if (!e) {
+    launch_relax(S.L, vr, vt, m, id, nbin, dstep, st);
+    e = cudaGetLastError();
+  }
+  if (!e) e = cudaStreamSynchronize(st);  // dt and step live on this stack
+  dfree(dstep, st);
+  return e ? cuda_fail(nullptr, e, "cmc_relax") : CMC_OK;
+}
+
+cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double* vr,
+                     const double* vt, const uint32_t* id, uint64_t seed, uint32_t step,
+                     int32_t max_trials, int32_t precision, double* r_new, double* vr_new,
+                     double* vt_new, double* phi_new, double* rmin, double* rmax, double* F,
+                     int32_t* code, void* stream) {
+  if (n < 0 || max_trials < 1 || (precision != 0 && precision != 1) ||
+      (n > 0 && (!r || !phi || !vr || !vt || !id || !r_new)))
+    return fail(nullptr, CMC_EINVAL, "cmc_orbit: bad arguments");
+  if (n == 0) return CMC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Stage S(n, seed, 0.0, 20, st);
+  if (S.e) return cuda_fail(nullptr, S.e, "cmc_orbit");
+  double *x = nullptr, *mm = nullptr;
+  float2* t32 = nullptr;
+  uint64_t* keys = nullptr;
+  Payload* pay = nullptr;
+  uint32_t* dstep = nullptr;
+  cudaError_t e = dalloc(x, n, st);
+  if (!e) e = dalloc(mm, n, st);
+  if (!e) e = dalloc(t32, n, st);
+  if (!e) e = dalloc(keys, n, st);
+  if (!e) e = dalloc(pay, n, st);
+  if (!e) e = dalloc(dstep, 1, st);
+  if (!e) e = cudaMemsetAsync(mm, 0, sizeof(double) * n, st);
+  if (!e) e = cudaMemcpyAsync(dstep, &step, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+  if (!e) {
+    launch_recip(n, r, x, st);
+    launch_make_t32(n, x, phi, t32, st);
+    OrbitStageOut d;
+    d.phi_new = phi_new; d.rmin = rmin; d.rmax = rmax; d.F = F; d.code = code;
+    launch_orbit(S.L, precision, max_trials, r, x, phi, t32, vr, vt, mm, id, dstep, keys, pay,
+                 &d, 0, st);
+    launch_unpack_orbit(n, keys, pay, r_new, vr_new, vt_new, st);
+    e = cudaGetLastError();
+  }
+  if (!e) e = cudaStreamSynchronize(st);
+  dfree(x, st);
+  dfree(mm, st);
+  dfree(t32, st);
+  dfree(keys, st);
+  dfree(pay, st);
+  dfree(dstep, st);
+  return e ? cuda_fail(nullptr, e, "cmc_orbit") : CMC_OK;
+}
+
+cmc_status cmc_energy_correction(int64_t n, const double* r, const double* phi, double* vr,
+                                 double* vt, const double* r_old, const double* c,
+                                 void* stream) {
+  if (n < 0 || (n > 0 && (!r || !phi || !vr || !vt || !r_old || !c)))
+    return fail(nullptr, CMC_EINVAL, "cmc_energy_correction: bad arguments");
+  if (n == 0) return CMC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  Stage S(n, 0, 0.0, 20, st);
+  if (S.e) return cuda_fail(nullptr, S.e, "cmc_energy_correction");
+  double* x = nullptr;
+  uint32_t* err = nullptr;
+  cudaError_t e = dalloc(x, n, st);
+  if (!e) e = dalloc(err, 1, st);
+  if (!e) {
+    launch_recip(n, r, x, st);
+    launch_correction(S.L, r, x, phi, vr, vt, r_old, c, false, err, st);
+    e = cudaGetLastError();
+  }
+  dfree(x, st);
+  dfree(err, st);
+  return e ? cuda_fail(nullptr, e, "cmc_energy_correction") : CMC_OK;
+}
+
+}  // extern "C"

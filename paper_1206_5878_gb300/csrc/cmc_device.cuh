@@ -1,0 +1,172 @@
+// Device-side building blocks shared by the kernels of the Henon Monte Carlo
+// timestep (Pattabiraman et al., section 2.1): counter-based random numbers,
+// the segment (cluster) layout, error flags, and the shell potential of
+// Eqs. 1 and 6 evaluated from the sorted table.
+//
+// Every kernel is compiled with --fmad=false: each floating-point operation
+// is one IEEE-754 round-to-nearest operation in the order written, so the
+// FP64 path reproduces an independent FP64 statement of the same method bit
+// for bit.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cmc {
+
+// ---------------------------------------------------------------- sizes
+constexpr int kTile = 4096;          // elements per tile (sort, gather, scans)
+constexpr int kBins = 256;           // radix digits per pass (8 bits)
+constexpr double kPi = 3.14159265358979323846;
+
+// stream tags (third counter word of the per-star random stream)
+constexpr uint32_t kTagPsi = 0;      // relaxation: azimuth of star 2's v_t
+constexpr uint32_t kTagPhi = 1;      // relaxation: azimuth of the deflection
+constexpr uint32_t kTagRej = 2;      // orbit: rejection trials
+constexpr uint32_t kTagSgn = 3;      // orbit: sign of the new v_r
+
+// escaped stars sort after every finite radius, by id
+constexpr uint64_t kEscKeyBase = 0x7FF0000000000001ull;
+
+// error bits (fatal: they poison the context)
+enum : uint32_t {
+  kErrTimeout = 1u << 0,   // a bounded device wait gave up
+  kErrTies = 1u << 1,      // a run of equal radii too long to order by id
+  kErrInput = 1u << 2,     // invalid input state
+  kErrNonFinite = 1u << 3, // a non-finite velocity appeared
+};
+
+// per-segment statistics (64-bit counters)
+enum : int {
+  kStEscaped = 0, kStDegenerate, kStCapHits, kStTrials, kStViolations,
+  kStClamps, kStAngleFails, kStTies, kStFlips, kStCount
+};
+constexpr int kStStride = 16;        // counters reserved per segment
+
+// ------------------------------------------------------- segment layout
+// Clusters of an ensemble are stored back to back.  Segment c owns global
+// positions [off[c], off[c+1]); its bound stars are the first nb[c].
+struct Seg {
+  const int64_t* off;      // n_seg + 1 offsets (device)
+  const int64_t* tile_off; // n_seg + 1 tile offsets (device)
+  const int64_t* pair_off; // n_seg + 1 pair offsets (by capacity, device)
+  const int64_t* bin_off;  // n_seg + 1 bin offsets (by capacity, device)
+  const uint64_t* seed;    // per segment
+  const double* lnL;       // ln(gamma N_c), per segment
+  int64_t* nb;             // bound stars per segment (device, changes)
+  uint64_t* dt_bits;       // timestep per segment as double bits
+  unsigned long long* stats;  // kStStride counters per segment
+  int n_seg;
+};
+
+// largest c with a[c] <= v, for a sorted array of n+1 offsets (a[0] = 0)
+__device__ __forceinline__ int seg_find(const int64_t* a, int n, int64_t v) {
+  int lo = 0, hi = n;  // invariant a[lo] <= v < a[hi]
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(a + mid) <= v) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ------------------------------------------------- counter-based RNG
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
+// 32x32->64 bit products and xors, keys bumped by the Weyl constants.
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint64_t seed) {
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+    uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+    uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// (2k + 1) 2^-53 from the top 52 bits k of (hi:lo): exact, inside (0, 1)
+__device__ __forceinline__ double u01(uint32_t lo, uint32_t hi) {
+  uint64_t k = ((((uint64_t)hi) << 32) | lo) >> 12;
+  return (double)(2ull * k + 1ull) * 0x1p-53;
+}
+
+// uniform planar direction (cos a, sin a) by rejection of a point in the
+// unit disk; the doubled angle gives cos = (u^2 - v^2)/q, sin = 2uv/q.
+__device__ __forceinline__ bool disk_angle(uint64_t seed, uint32_t id, uint32_t step,
+                                           uint32_t tag, double& c, double& s) {
+  for (uint32_t t = 0; t < 64u; ++t) {
+    U4 w = philox(id, step, tag, t, seed);
+    double u = 2.0 * u01(w.x, w.y) - 1.0;
+    double v = 2.0 * u01(w.z, w.w) - 1.0;
+    double uu = u * u, vv = v * v, q = uu + vv;
+    if (q <= 1.0) {
+      c = (uu - vv) / q;
+      s = ((2.0 * u) * v) / q;
+      return true;
+    }
+  }
+  c = 1.0; s = 0.0;
+  return false;
+}
+
+// ------------------------------------------------------------ sort keys
+__device__ __forceinline__ uint64_t radius_key(double r, uint32_t id) {
+  uint64_t b = (uint64_t)__double_as_longlong(r);
+  return (b >= 0x7FF0000000000000ull) ? kEscKeyBase + (uint64_t)id : b;
+}
+__device__ __forceinline__ bool key_is_escaper(uint64_t k) {
+  return k >= 0x7FF0000000000000ull;
+}
+
+// --------------------------------------------- shell potential (Eq. 6)
+// Table of one segment: sorted radii r[0..nb), x = 1/r, Phi.  Node nb is
+// the virtual star at 1/r = 0 with Phi = 0 (Eq. 2); inside r[0] Phi is
+// the constant Phi_0 (Eq. 1 with nothing enclosed).
+struct Table64 {
+  const double* r;
+  const double* x;
+  const double* phi;
+  int64_t nb;
+};
+
+// largest i in [0, nb) with r[i] <= q, else -1 (unique for sorted r)
+__device__ __forceinline__ int64_t shell_of(const Table64& t, double q) {
+  int64_t lo = -1, hi = t.nb;
+  while (hi - lo > 1) {
+    int64_t mid = lo + ((hi - lo) >> 1);
+    if (__ldg(t.r + mid) <= q) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// Eq. 6 inside shell i (i = -1: central constant)
+__device__ __forceinline__ double phi_in_shell(const Table64& t, int64_t i, double q) {
+  if (i < 0) return __ldg(t.phi);
+  double x = 1.0 / q;
+  double xj = __ldg(t.x + i), pj = __ldg(t.phi + i), xj1, pj1;
+  if (i + 1 < t.nb) { xj1 = __ldg(t.x + i + 1); pj1 = __ldg(t.phi + i + 1); }
+  else { xj1 = 0.0; pj1 = 0.0; }
+  double den = xj - xj1;
+  if (!(den > 0.0)) return pj;
+  return pj + ((xj - x) / den) * (pj1 - pj);
+}
+
+__device__ __forceinline__ double phi_of_r(const Table64& t, double q) {
+  return phi_in_shell(t, shell_of(t, q), q);
+}
+
+// ----------------------------------------------------- small utilities
+__device__ __forceinline__ void set_err(uint32_t* err, uint32_t bit) {
+  atomicOr(err, bit);
+}
+
+__device__ __forceinline__ void stat_add(unsigned long long* st, int seg, int which,
+                                         unsigned long long v) {
+  if (v) atomicAdd(st + (size_t)seg * kStStride + which, v);
+}
+
+}  // namespace cmc

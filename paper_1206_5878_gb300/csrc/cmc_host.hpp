@@ -1,0 +1,167 @@
+// Host-side internals of the CUDA library: the segment (cluster) layout on
+// the device, scratch buffers, and the launchers of each kernel.  Nothing
+// here is part of the C ABI (see include/cmc.h).
+#pragma once
+
+#include <cstdint>
+#include <cstddef>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "cmc_device.cuh"
+
+namespace cmc {
+
+// Device-resident description of the segments of one state.  Offsets are
+// fixed at initialisation; nb, dt and the statistics change every step.
+struct SegLayout {
+  int n_seg = 0;
+  int64_t n = 0;          // total stars
+  int64_t n_tiles = 0;    // tiles of kTile elements, never straddling segments
+  int64_t n_pairs = 0;    // pair slots (floor(n_c / 2) summed)
+  int64_t n_bins = 0;     // bin slots (ceil(n_c / bin_size) summed)
+  int bin_size = 20;
+  std::vector<int64_t> h_off, h_tile_off, h_pair_off, h_bin_off;
+  int64_t max_tiles_per_seg = 0;
+  // device arrays
+  int64_t* off = nullptr;
+  int64_t* tile_off = nullptr;
+  int64_t* pair_off = nullptr;
+  int64_t* bin_off = nullptr;
+  uint64_t* seed = nullptr;
+  double* lnL = nullptr;
+  int64_t* nb = nullptr;
+  int64_t* esc_step = nullptr;      // stars escaped during the current step
+  uint64_t* dt_bits = nullptr;
+  uint64_t* dt_last = nullptr;      // timestep of the last completed step
+  unsigned long long* stats = nullptr;
+
+  Seg dev() const {
+    Seg s;
+    s.off = off; s.tile_off = tile_off; s.pair_off = pair_off; s.bin_off = bin_off;
+    s.seed = seed; s.lnL = lnL; s.nb = nb; s.dt_bits = dt_bits; s.stats = stats;
+    s.n_seg = n_seg;
+    return s;
+  }
+};
+
+// Scratch of the radix sort (sized for a given layout).
+struct SortWork {
+  uint64_t* keys_alt = nullptr;
+  uint32_t* vals_alt = nullptr;
+  unsigned long long* desc = nullptr;   // [passes][n_tiles][256] look-back words
+  uint32_t* hist = nullptr;             // [n_seg][passes][256]
+  uint32_t* tickets = nullptr;          // [passes]
+  size_t zero_bytes = 0;                // desc + hist + tickets, zeroed per sort
+  void* zero_base = nullptr;
+  int max_passes = 0;
+};
+
+// allocation helpers (stream-ordered); return cudaError_t
+cudaError_t alloc_layout(SegLayout& L, const std::vector<int64_t>& sizes,
+                         const std::vector<uint64_t>& seeds, const std::vector<double>& lnL,
+                         int bin_size, cudaStream_t st);
+void free_layout(SegLayout& L, cudaStream_t st);
+cudaError_t alloc_sort(SortWork& W, const SegLayout& L, int max_passes, cudaStream_t st);
+void free_sort(SortWork& W, cudaStream_t st);
+
+// ------------------------------------------------------------- launchers
+// Stable LSD radix sort of (keys, vals) within each segment over the 8-bit
+// digits [first_pass, first_pass + passes).  When vals_identity is set the
+// input values are taken to be the global positions.  The result lands in
+// (keys, vals) when passes is even (the alternates are scratch).
+cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint32_t* vals,
+                          int first_pass, int passes, bool vals_identity, uint32_t* err,
+                          cudaStream_t st);
+
+// Order every run of equal finite keys by the ids of the sorted elements
+// (ids_by_val[vals[p] * id_stride]) so that ties follow the (r, id) order.
+void launch_tiefix(const SegLayout& L, const uint64_t* keys, uint32_t* vals,
+                   const uint32_t* ids_by_val, int id_stride, uint32_t* err,
+                   cudaStream_t st);
+
+void launch_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out,
+                   cudaStream_t st);
+
+struct Payload {     // one star between the orbit step and the sort (48 B)
+  double vr, vt, m, r_old, c;
+  uint32_t id, pad;
+};
+
+// keys of the current state (radius_key of r, id) and the payload (if pay)
+void launch_make_keys(const SegLayout& L, const double* r, const double* vr,
+                      const double* vt, const double* m, const uint32_t* id,
+                      uint64_t* keys, Payload* pay, cudaStream_t st);
+
+// keys = id (for the (r, id) order at initialisation), and radius keys of
+// the stars in the order of a permutation
+void launch_id_keys(const SegLayout& L, const uint32_t* id, uint64_t* keys, cudaStream_t st);
+void launch_rekey_radius(const SegLayout& L, const uint32_t* perm, const double* r,
+                         const uint32_t* id, uint64_t* keys, cudaStream_t st);
+
+// sorted (keys, vals) + payload -> SoA state (r, x, vr, vt, m, id, r_old, c)
+void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* vals,
+                   const Payload* pay, double* r, double* x, double* vr, double* vt,
+                   double* m, uint32_t* id, double* r_old, double* c, cudaStream_t st);
+
+// potential: per-tile sums then the tile-local scans (Eqs. 1-5 in scan
+// form).  nb_sub: subtract esc_step from nb (after the orbit step).
+void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
+                      double* tile_m, double* tile_mx, double* phi, float2* t32,
+                      double* Mout, bool nb_sub, cudaStream_t st);
+
+void launch_correction(const SegLayout& L, const double* r, const double* x,
+                       const double* phi, double* vr, double* vt, const double* r_old,
+                       const double* c, bool nb_sub, uint32_t* err, cudaStream_t st);
+
+void launch_bins(const SegLayout& L, const double* r, const double* vr, const double* vt,
+                 const double* m, double* nbin, double pref, cudaStream_t st);
+
+void launch_relax(const SegLayout& L, double* vr, double* vt, const double* m,
+                  const uint32_t* id, const double* nbin, const uint32_t* step,
+                  cudaStream_t st);
+
+struct OrbitStageOut {   // optional per-star outputs of the orbit stage
+  double* phi_new = nullptr;
+  double* rmin = nullptr;
+  double* rmax = nullptr;
+  double* F = nullptr;
+  int32_t* code = nullptr;
+  int32_t* trials = nullptr;
+};
+
+void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
+                  const double* x, const double* phi, const float2* t32, const double* vr,
+                  const double* vt, const double* m, const uint32_t* id, const uint32_t* step,
+                  uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
+                  cudaStream_t st);
+
+void launch_step_end(const SegLayout& L, uint32_t* step, cudaStream_t st);
+
+// energy diagnostics: per-segment K, W_pair (Mbuf receives M_k)
+void launch_energy(const SegLayout& L, const double* r, const double* vr, const double* vt,
+                   const double* m, double* tile_m, double* tile_k, double* tile_w,
+                   double* Mbuf, double* out3, cudaStream_t st);
+
+void launch_lagrange(const SegLayout& L, const double* r, const double* M,
+                     const double* fracs, int nf, double* out, cudaStream_t st);
+
+void launch_validate(const SegLayout& L, const double* r, const double* vr,
+                     const double* vt, const double* m, bool allow_inf, uint32_t* err,
+                     cudaStream_t st);
+
+// nb of every segment = position of its first escaper key (sorted keys)
+void launch_nb_from_keys(const SegLayout& L, const uint64_t* keys, cudaStream_t st);
+void launch_recip(int64_t n, const double* r, double* x, cudaStream_t st);
+void launch_make_t32(int64_t n, const double* x, const double* phi, float2* t32,
+                     cudaStream_t st);
+void launch_unpack_orbit(int64_t n, const uint64_t* keys, const Payload* pay, double* r_new,
+                         double* vr_new, double* vt_new, cudaStream_t st);
+void sort_prepare();
+
+void launch_check_ids(const SegLayout& L, const uint64_t* sorted_ids, uint32_t* err,
+                      cudaStream_t st);
+
+}  // namespace cmc

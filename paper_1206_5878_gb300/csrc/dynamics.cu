@@ -1,0 +1,178 @@
+// Relaxation timestep (Eq. 7 on fixed bins of consecutive stars, section
+// 3.3) and two-body relaxation between radial neighbours (section 2.1 step
+// 3(i)).  Both are FP64 and evaluate, operation for operation, the same
+// expressions as the independent FP64 statement of the method.
+#include "cmc_host.hpp"
+
+namespace cmc {
+
+namespace {
+
+// One thread per bin slot.  Bin b of a segment covers sorted positions
+// [b*bs, min((b+1)*bs, nb)).  For P >= 2 stars:
+//   n = 3 (P-1) / (4 pi (r_last^3 - r_first^3))
+//   <v_rel> = mean over pairs (2j, 2j+1) of sqrt(v1^2 + v2^2)
+//   <(M1+M2)^2> = mean over the same pairs of (m1 + m2)^2
+//   T_b = pref <v_rel>^3 / (lnL n <(M1+M2)^2>),  pref = (theta_max/(pi/2)) (pi/32)
+// and the segment's timestep is the minimum of T_b.
+__global__ void __launch_bounds__(256) k_bins(Seg S, int bs, double pref, const double* r,
+                                              const double* vr, const double* vt,
+                                              const double* m, double* nbin) {
+  __shared__ unsigned long long s_min[8];
+  __shared__ int s_seg0;
+  const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t b0 = (int64_t)blockIdx.x * blockDim.x;
+  if (threadIdx.x == 0) s_seg0 = seg_find(S.bin_off, S.n_seg, b0);
+  __syncthreads();
+  unsigned long long tb = 0x7FF0000000000000ull;  // +inf
+  int c = s_seg0;
+  if (b < S.bin_off[S.n_seg]) {
+    c = seg_find(S.bin_off, S.n_seg, b);
+    const int64_t lb = b - S.bin_off[c];
+    const int64_t sb = S.off[c];
+    const int64_t nbc = S.nb[c];
+    const int64_t first = lb * bs;
+    double n = 0.0;
+    if (first < nbc) {
+      int64_t P = nbc - first < bs ? nbc - first : bs;
+      if (P >= 2) {
+        const int64_t g = sb + first;
+        double rf = r[g], rl = r[g + P - 1];
+        double vol = rl * rl * rl - rf * rf * rf;
+        if (vol > 0.0) {
+          n = (3.0 * (double)(P - 1)) / ((4.0 * kPi) * vol);
+          int64_t q = P / 2;
+          double sv = 0.0, sm = 0.0;
+          for (int64_t j = 0; j < q; ++j) {
+            int64_t a = g + 2 * j;
+            double va2 = vr[a] * vr[a] + vt[a] * vt[a];
+            double vb2 = vr[a + 1] * vr[a + 1] + vt[a + 1] * vt[a + 1];
+            double ms = m[a] + m[a + 1];
+            sv = sv + sqrt(va2 + vb2);
+            sm = sm + ms * ms;
+          }
+          double v = sv / (double)q;
+          double msq = sm / (double)q;
+          double num = pref * (v * v * v);
+          double den = (S.lnL[c] * n) * msq;
+          if (den > 0.0) {
+            double T = num / den;
+            if (T < __longlong_as_double(0x7FF0000000000000ll))
+              tb = (unsigned long long)__double_as_longlong(T);
+          }
+        }
+      }
+    }
+    nbin[b] = n;
+  }
+  // positive doubles order like their bit patterns: min over the block for
+  // the block's first segment, direct atomics for any other segment
+  unsigned long long mine = (c == s_seg0) ? tb : 0x7FF0000000000000ull;
+  if (c != s_seg0 && tb != 0x7FF0000000000000ull)
+    atomicMin((unsigned long long*)(S.dt_bits + c), tb);
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long y = __shfl_down_sync(0xffffffffu, mine, o);
+    mine = y < mine ? y : mine;
+  }
+  if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = mine;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned long long v = s_min[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = s_min[w] < v ? s_min[w] : v;
+    if (v != 0x7FF0000000000000ull) atomicMin((unsigned long long*)(S.dt_bits + s_seg0), v);
+  }
+}
+
+// One thread per pair slot: stars a = 2j and b = 2j + 1 of a segment.
+__global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double* vt,
+                                               const double* m, const uint32_t* id,
+                                               const double* nbin, const uint32_t* step_p) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= S.pair_off[S.n_seg]) return;
+  const int c = seg_find(S.pair_off, S.n_seg, p);
+  const int64_t j = p - S.pair_off[c];
+  const int64_t la = 2 * j;
+  if (la + 1 >= S.nb[c]) return;
+  const int64_t a = S.off[c] + la, b = a + 1;
+  const double n = nbin[S.bin_off[c] + la / bs];
+  const double m1 = m[a], m2 = m[b];
+  const double msum = m1 + m2;
+  if (!(n > 0.0) || !(msum > 0.0)) return;
+  const double dt = __longlong_as_double((long long)S.dt_bits[c]);
+  const double lnL = S.lnL[c];
+  const uint64_t seed = S.seed[c];
+  const uint32_t step = *step_p;
+  const uint32_t ida = id[a];
+  int fails = 0;
+  double cpsi, spsi, cphi, sphi;
+  if (!disk_angle(seed, ida, step, kTagPsi, cpsi, spsi)) ++fails;
+  const double v1x = vr[a], v1y = vt[a], v1z = 0.0;
+  const double v2x = vr[b], vtb = vt[b];
+  const double v2y = vtb * cpsi, v2z = vtb * spsi;
+  const double wx = v1x - v2x, wy = v1y - v2y, wz = v1z - v2z;
+  const double w2 = (wx * wx + wy * wy) + wz * wz;
+  if (!(w2 > 0.0)) {
+    if (fails) stat_add(S.stats, c, kStAngleFails, (unsigned long long)fails);
+    return;
+  }
+  const double w = sqrt(w2);
+  double num = kPi * msum;
+  num = num * msum;
+  num = num * n;
+  num = num * lnL;
+  num = num * dt;
+  double s2 = num / (w2 * w);
+  if (!(s2 <= 1.0)) s2 = 1.0;
+  const double sb = sqrt(s2);
+  const double cosb = 1.0 - 2.0 * s2;
+  const double sinb = (2.0 * sb) * sqrt(1.0 - s2);
+  if (!disk_angle(seed, ida, step, kTagPhi, cphi, sphi)) ++fails;
+  // e1 = (w x xhat)/|w x xhat| = (0, wz, -wy)/|.| (yhat for radial w);
+  // u = w x e1 has length |w| and completes the frame perpendicular to w
+  const double wp2 = wy * wy + wz * wz;
+  double e1y, e1z;
+  if (wp2 > 0.0) {
+    const double wp = sqrt(wp2);
+    e1y = wz / wp;
+    e1z = -wy / wp;
+  } else {
+    e1y = 1.0;
+    e1z = 0.0;
+  }
+  const double ux = wy * e1z - wz * e1y;
+  const double uy = -(wx * e1z);
+  const double uz = wx * e1y;
+  const double a1 = w * cphi;
+  // w' = w cos(beta) + sin(beta) (|w| cos(phi) e1 + sin(phi) u)
+  const double wpx = wx * cosb + sinb * (sphi * ux);
+  const double wpy = wy * cosb + sinb * (a1 * e1y + sphi * uy);
+  const double wpz = wz * cosb + sinb * (a1 * e1z + sphi * uz);
+  const double dwx = wpx - wx, dwy = wpy - wy, dwz = wpz - wz;
+  const double f1 = m2 / msum, f2 = m1 / msum;
+  const double p1x = v1x + f1 * dwx, p1y = v1y + f1 * dwy, p1z = v1z + f1 * dwz;
+  const double p2x = v2x - f2 * dwx, p2y = v2y - f2 * dwy, p2z = v2z - f2 * dwz;
+  vr[a] = p1x;
+  vt[a] = sqrt(p1y * p1y + p1z * p1z);
+  vr[b] = p2x;
+  vt[b] = sqrt(p2y * p2y + p2z * p2z);
+  if (fails) stat_add(S.stats, c, kStAngleFails, (unsigned long long)fails);
+}
+
+}  // namespace
+
+void launch_bins(const SegLayout& L, const double* r, const double* vr, const double* vt,
+                 const double* m, double* nbin, double pref, cudaStream_t st) {
+  if (!L.n_bins) return;
+  k_bins<<<(unsigned)((L.n_bins + 255) / 256), 256, 0, st>>>(L.dev(), L.bin_size, pref, r, vr,
+                                                             vt, m, nbin);
+}
+
+void launch_relax(const SegLayout& L, double* vr, double* vt, const double* m,
+                  const uint32_t* id, const double* nbin, const uint32_t* step,
+                  cudaStream_t st) {
+  if (!L.n_pairs) return;
+  k_relax<<<(unsigned)((L.n_pairs + 127) / 128), 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m,
+                                                               id, nbin, step);
+}
+
+}  // namespace cmc

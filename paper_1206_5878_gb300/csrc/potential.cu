@@ -1,0 +1,553 @@
+// Shell potential (section 2.1 step 1, Eqs. 1-5), the energy correction of
+// section 2.1 step 6, the diagnostics, and the data movement around the
+// sort (payload gather).
+//
+// The potential is Eq. 1 in scan form, Phi_k = -G (M_k / r_k + S_k) with
+// M_k = sum_{i<=k} m_i and S_k = sum_{i>k} m_i / r_i, over the bound stars
+// of each segment.  The scan is reduce-then-scan on fixed tiles: one kernel
+// writes per-tile sums, the next combines, per tile, the sums of the tiles
+// before it (for M) and after it (for S) in a fixed order and scans inside
+// the tile.  Every sum is therefore evaluated in the same order on every
+// run, so a cluster gives the same bits whether it is advanced alone or in
+// an ensemble, and a resumed run repeats an uninterrupted one exactly.
+#include <cmath>
+
+#include "cmc_host.hpp"
+
+namespace cmc {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPer = kTile / kThreads;  // 16 consecutive elements per thread
+
+__device__ __forceinline__ int64_t nb_eff(const int64_t* nb, const int64_t* esc, int c,
+                                          bool sub) {
+  int64_t v = nb[c];
+  if (sub) v -= esc[c];
+  return v;
+}
+
+// fixed-shape block reduction of one double per thread (256 threads)
+__device__ __forceinline__ double block_sum(double v, double* s) {
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = kThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] = s[threadIdx.x] + s[threadIdx.x + w];
+    __syncthreads();
+  }
+  double r = s[0];
+  __syncthreads();
+  return r;
+}
+
+// fixed-shape inclusive scans of one double per thread (Hillis-Steele on
+// shared memory): forward for vm, backward for vs; returns the exclusive
+// values (sum over lower threads, sum over higher threads)
+__device__ __forceinline__ void block_scans(double vm, double vs, double* s1, double* s2,
+                                            double& pre_m, double& suf_s) {
+  // inclusive forward scan of vm, inclusive backward scan of vs
+  const int t = threadIdx.x;
+  s1[t] = vm;
+  s2[t] = vs;
+  __syncthreads();
+  for (int o = 1; o < kThreads; o <<= 1) {
+    double a = t >= o ? s1[t - o] : 0.0;
+    double b = t + o < kThreads ? s2[t + o] : 0.0;
+    __syncthreads();
+    if (t >= o) s1[t] = a + s1[t];
+    if (t + o < kThreads) s2[t] = s2[t] + b;
+    __syncthreads();
+  }
+  pre_m = t > 0 ? s1[t - 1] : 0.0;
+  suf_s = t + 1 < kThreads ? s2[t + 1] : 0.0;
+  __syncthreads();
+}
+
+struct TR {
+  int seg;
+  int64_t lt, nt, seg_begin, begin, end, bound_end;
+};
+
+__device__ __forceinline__ TR tile_of(const Seg& S, const int64_t* esc, int64_t t, bool sub) {
+  TR R;
+  R.seg = seg_find(S.tile_off, S.n_seg, t);
+  int64_t t0 = __ldg(S.tile_off + R.seg);
+  R.lt = t - t0;
+  R.nt = __ldg(S.tile_off + R.seg + 1) - t0;
+  R.seg_begin = __ldg(S.off + R.seg);
+  int64_t se = __ldg(S.off + R.seg + 1);
+  R.begin = R.seg_begin + R.lt * kTile;
+  R.end = R.begin + kTile < se ? R.begin + kTile : se;
+  R.bound_end = R.seg_begin + nb_eff(S.nb, esc, R.seg, sub);
+  return R;
+}
+
+// --------------------------------------------------------------- gather
+__global__ void k_make_keys(int64_t n, const double* r, const double* vr, const double* vt,
+                            const double* m, const uint32_t* id, uint64_t* keys,
+                            Payload* pay) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double rr = r[p];
+  uint32_t ii = id[p];
+  keys[p] = radius_key(rr, ii);
+  if (!pay) return;
+  Payload P;
+  P.vr = vr[p]; P.vt = vt[p]; P.m = m[p]; P.r_old = rr; P.c = 0.0; P.id = ii; P.pad = 0;
+  pay[p] = P;
+}
+
+__global__ void k_id_keys(int64_t n, const uint32_t* id, uint64_t* keys) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) keys[p] = (uint64_t)id[p];
+}
+
+__global__ void k_rekey_radius(int64_t n, const uint32_t* perm, const double* r,
+                               const uint32_t* id, uint64_t* keys) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  uint32_t q = perm[p];
+  keys[p] = radius_key(r[q], id[q]);
+}
+
+__global__ void k_gather(int64_t n, const uint64_t* __restrict__ keys,
+                         const uint32_t* __restrict__ vals, const Payload* __restrict__ pay,
+                         double* r, double* x, double* vr, double* vt, double* m,
+                         uint32_t* id, double* r_old, double* c) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  uint64_t k = keys[p];
+  const uint32_t v = vals[p];
+  if ((int64_t)v >= n) return;  // only after a reported sort failure
+  const Payload P = pay[v];
+  double rr, xx;
+  if (key_is_escaper(k)) { rr = __longlong_as_double(0x7FF0000000000000ll); xx = 0.0; }
+  else { rr = __longlong_as_double((long long)k); xx = 1.0 / rr; }
+  r[p] = rr; x[p] = xx; vr[p] = P.vr; vt[p] = P.vt; m[p] = P.m; id[p] = P.id;
+  if (r_old) r_old[p] = P.r_old;
+  if (c) c[p] = P.c;
+}
+
+// ------------------------------------------------------------ potential
+__global__ void __launch_bounds__(kThreads) k_tile_sums(Seg S, const int64_t* esc, bool sub,
+                                                        const double* x, const double* m,
+                                                        double* tile_m, double* tile_mx) {
+  __shared__ double s[kThreads];
+  TR R = tile_of(S, esc, blockIdx.x, sub);
+  double am = 0.0, ax = 0.0;
+  int64_t b = R.begin + (int64_t)threadIdx.x * kPer;
+  for (int i = 0; i < kPer; ++i) {
+    int64_t p = b + i;
+    if (p < R.end && p < R.bound_end) {
+      double mm = m[p];
+      am = am + mm;
+      ax = ax + mm * x[p];
+    }
+  }
+  double tm = block_sum(am, s);
+  double tx = block_sum(ax, s);
+  if (threadIdx.x == 0) { tile_m[blockIdx.x] = tm; tile_mx[blockIdx.x] = tx; }
+}
+
+__global__ void __launch_bounds__(kThreads) k_potential(Seg S, const int64_t* esc, bool sub,
+                                                        const double* x, const double* m,
+                                                        const double* tile_m,
+                                                        const double* tile_mx, double* phi,
+                                                        float2* t32, double* Mout) {
+  __shared__ double s1[kThreads], s2[kThreads];
+  TR R = tile_of(S, esc, blockIdx.x, sub);
+  const int64_t t0 = blockIdx.x - R.lt;
+  // tiles before (M) and after (S) this one, in a fixed order
+  double pm = 0.0, ps = 0.0;
+  for (int64_t j = threadIdx.x; j < R.nt; j += kThreads) {
+    if (j < R.lt) pm = pm + tile_m[t0 + j];
+    if (j > R.lt) ps = ps + tile_mx[t0 + j];
+  }
+  double Mbefore = block_sum(pm, s1);
+  double Safter = block_sum(ps, s1);
+  // the thread's 16 consecutive elements
+  const int64_t b = R.begin + (int64_t)threadIdx.x * kPer;
+  double mm[kPer], xx[kPer];
+  double am = 0.0, ax = 0.0;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    int64_t p = b + i;
+    bool ok = p < R.end && p < R.bound_end;
+    mm[i] = ok ? m[p] : 0.0;
+    xx[i] = ok ? x[p] : 0.0;
+    am = am + mm[i];
+    ax = ax + mm[i] * xx[i];
+  }
+  double pre_m, suf_s;
+  block_scans(am, ax, s1, s2, pre_m, suf_s);
+  // inclusive M along the thread's run; exclusive suffix S from its end
+  double Mk[kPer], Sk[kPer];
+  double run = 0.0;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    run = run + mm[i];
+    Mk[i] = (Mbefore + pre_m) + run;
+  }
+  double suf = 0.0;
+#pragma unroll
+  for (int i = kPer - 1; i >= 0; --i) {
+    Sk[i] = (Safter + suf_s) + suf;
+    suf = suf + mm[i] * xx[i];
+  }
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    int64_t p = b + i;
+    if (p >= R.end) break;
+    double ph = 0.0;
+    if (p < R.bound_end) ph = -(Mk[i] * xx[i] + Sk[i]);
+    phi[p] = ph;
+    if (t32) t32[p] = make_float2((float)xx[i], (float)ph);
+    if (Mout) Mout[p] = p < R.bound_end ? Mk[i] : 0.0;
+  }
+}
+
+// ---------------------------------------------------- energy correction
+// T' = T + 1/2 [(Phi_new(r_old) - Phi_new(r_new)) - (Phi_old(r_old) -
+// Phi_old(r_new))], clamped at 0; both components scaled by sqrt(T'/T).
+__global__ void k_correction(Seg S, const int64_t* esc, bool sub, const double* r,
+                             const double* x, const double* phi, double* vr, double* vt,
+                             const double* r_old, const double* cc, int64_t n) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool active = p < n;
+  int c = 0;
+  int64_t k = 0, nbc = 0, sb = 0;
+  if (active) {
+    c = seg_find(S.off, S.n_seg, p);
+    sb = __ldg(S.off + c);
+    k = p - sb;
+    nbc = nb_eff(S.nb, esc, c, sub);
+    active = k < nbc;
+  }
+  unsigned long long clamp = 0;
+  if (active) {
+    Table64 T{r + sb, x + sb, phi + sb, nbc};
+    double a = vr[p], b = vt[p];
+    double Tk = 0.5 * (a * a + b * b);
+    double dnew = phi_of_r(T, r_old[p]) - phi[p];
+    double Tp = Tk + 0.5 * (dnew - cc[p]);
+    if (Tp < 0.0) { Tp = 0.0; clamp = 1; }
+    if (Tk > 0.0) {
+      double f = sqrt(Tp / Tk);
+      vr[p] = a * f;
+      vt[p] = b * f;
+    }
+  }
+  if (clamp) stat_add(S.stats, c, kStClamps, 1ull);
+}
+
+// ---------------------------------------------------------- diagnostics
+__global__ void __launch_bounds__(kThreads) k_energy_tiles(Seg S, const double* r,
+                                                           const double* vr, const double* vt,
+                                                           const double* m,
+                                                           const double* tile_m,
+                                                           double* tile_k, double* tile_w,
+                                                           double* Mout) {
+  __shared__ double s1[kThreads], s2[kThreads];
+  TR R = tile_of(S, nullptr, blockIdx.x, false);
+  const int64_t t0 = blockIdx.x - R.lt;
+  double pm = 0.0;
+  for (int64_t j = threadIdx.x; j < R.lt; j += kThreads) pm = pm + tile_m[t0 + j];
+  double Mbefore = block_sum(pm, s1);
+  const int64_t b = R.begin + (int64_t)threadIdx.x * kPer;
+  double mm[kPer];
+  double am = 0.0;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    int64_t p = b + i;
+    mm[i] = (p < R.end && p < R.bound_end) ? m[p] : 0.0;
+    am = am + mm[i];
+  }
+  double pre_m, dummy;
+  block_scans(am, 0.0, s1, s2, pre_m, dummy);
+  double run = 0.0, ak = 0.0, aw = 0.0;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    int64_t p = b + i;
+    if (p < R.end && p < R.bound_end) {
+      double Mex = (Mbefore + pre_m) + run;  // mass strictly inside star p
+      double a = vr[p], bb = vt[p];
+      ak = ak + mm[i] * (a * a + bb * bb);
+      aw = aw + mm[i] * Mex / r[p];
+      run = run + mm[i];
+      if (Mout) Mout[p] = (Mbefore + pre_m) + run;
+    } else if (p < R.end && Mout) {
+      Mout[p] = 0.0;
+    }
+  }
+  double tk = block_sum(ak, s1);
+  double tw = block_sum(aw, s1);
+  if (threadIdx.x == 0) { tile_k[blockIdx.x] = tk; tile_w[blockIdx.x] = tw; }
+}
+
+__global__ void __launch_bounds__(kThreads) k_energy_final(Seg S, const double* tile_k,
+                                                           const double* tile_w,
+                                                           double* out3) {
+  __shared__ double s[kThreads];
+  const int c = blockIdx.x;
+  int64_t t0 = S.tile_off[c], t1 = S.tile_off[c + 1];
+  double ak = 0.0, aw = 0.0;
+  for (int64_t j = t0 + threadIdx.x; j < t1; j += kThreads) {
+    ak = ak + tile_k[j];
+    aw = aw + tile_w[j];
+  }
+  double K = block_sum(ak, s);
+  double W = block_sum(aw, s);
+  if (threadIdx.x == 0) {
+    out3[3 * c + 0] = 0.5 * K;
+    out3[3 * c + 1] = -W;
+    out3[3 * c + 2] = 0.5 * K - W;
+  }
+}
+
+__global__ void k_lagrange(Seg S, const double* r, const double* M, const double* fracs,
+                           int nf, double* out) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= S.n_seg * nf) return;
+  int c = i / nf, q = i % nf;
+  int64_t sb = S.off[c], nbc = S.nb[c];
+  if (nbc <= 0) { out[i] = 0.0; return; }
+  double target = fracs[q] * M[sb + nbc - 1];
+  int64_t lo = -1, hi = nbc - 1;  // first k with M_k >= target (M[nb-1] qualifies)
+  while (hi - lo > 1) {
+    int64_t mid = lo + ((hi - lo) >> 1);
+    if (M[sb + mid] >= target) hi = mid; else lo = mid;
+  }
+  out[i] = r[sb + hi];
+}
+
+__global__ void k_validate(int64_t n, const double* r, const double* vr, const double* vt,
+                           const double* m, bool allow_inf, uint32_t* err) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  double rr = r[p], a = vr[p], b = vt[p], mm = m[p];
+  bool rok = (rr > 0.0) && (isfinite(rr) || (allow_inf && isinf(rr)));
+  bool ok = rok && isfinite(a) && isfinite(b) && (b >= 0.0) && isfinite(mm) && (mm >= 0.0);
+  if (!ok) set_err(err, kErrInput);
+}
+
+__global__ void k_check_ids(int64_t n, const int64_t* off, int n_seg, const uint64_t* ids,
+                            uint32_t* err) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p + 1 >= n) return;
+  int c = seg_find(off, n_seg, p);
+  if (p + 1 < off[c + 1] && ids[p] == ids[p + 1]) set_err(err, kErrInput);
+}
+
+__global__ void k_step_end(Seg S, int64_t* esc, uint64_t* dt_last, uint32_t* step) {
+  for (int c = threadIdx.x; c < S.n_seg; c += blockDim.x) {
+    int64_t e = esc[c];
+    dt_last[c] = S.dt_bits[c];
+    S.nb[c] -= e;
+    S.stats[(size_t)c * kStStride + kStEscaped] += (unsigned long long)e;
+    esc[c] = 0;
+    S.dt_bits[c] = 0x7FF0000000000000ull;
+  }
+  if (threadIdx.x == 0) *step += 1u;
+}
+
+__global__ void k_nb_from_keys(Seg S, const uint64_t* keys) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= S.n_seg) return;
+  int64_t sb = S.off[c], se = S.off[c + 1];
+  int64_t lo = sb - 1, hi = se;  // first escaper key in [sb, se)
+  while (hi - lo > 1) {
+    int64_t mid = lo + ((hi - lo) >> 1);
+    if (key_is_escaper(keys[mid])) hi = mid; else lo = mid;
+  }
+  S.nb[c] = hi - sb;
+}
+
+__global__ void k_recip(int64_t n, const double* r, double* x) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) x[p] = 1.0 / r[p];
+}
+
+__global__ void k_make_t32(int64_t n, const double* x, const double* phi, float2* t32) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) t32[p] = make_float2((float)x[p], (float)phi[p]);
+}
+
+__global__ void k_unpack_orbit(int64_t n, const uint64_t* keys, const Payload* pay,
+                               double* r_new, double* vr_new, double* vt_new) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  uint64_t k = keys[p];
+  r_new[p] = key_is_escaper(k) ? __longlong_as_double(0x7FF0000000000000ll)
+                               : __longlong_as_double((long long)k);
+  if (vr_new) vr_new[p] = pay[p].vr;
+  if (vt_new) vt_new[p] = pay[p].vt;
+}
+
+inline unsigned blocks_for(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+}  // namespace
+
+void launch_nb_from_keys(const SegLayout& L, const uint64_t* keys, cudaStream_t st) {
+  k_nb_from_keys<<<blocks_for(L.n_seg, 128), 128, 0, st>>>(L.dev(), keys);
+}
+
+void launch_recip(int64_t n, const double* r, double* x, cudaStream_t st) {
+  if (n > 0) k_recip<<<blocks_for(n, 256), 256, 0, st>>>(n, r, x);
+}
+
+void launch_make_t32(int64_t n, const double* x, const double* phi, float2* t32,
+                     cudaStream_t st) {
+  if (n > 0) k_make_t32<<<blocks_for(n, 256), 256, 0, st>>>(n, x, phi, t32);
+}
+
+void launch_unpack_orbit(int64_t n, const uint64_t* keys, const Payload* pay, double* r_new,
+                         double* vr_new, double* vt_new, cudaStream_t st) {
+  if (n > 0)
+    k_unpack_orbit<<<blocks_for(n, 256), 256, 0, st>>>(n, keys, pay, r_new, vr_new, vt_new);
+}
+
+// ------------------------------------------------------------------ host
+cudaError_t alloc_layout(SegLayout& L, const std::vector<int64_t>& sizes,
+                         const std::vector<uint64_t>& seeds, const std::vector<double>& lnL,
+                         int bin_size, cudaStream_t st) {
+  L.n_seg = (int)sizes.size();
+  L.bin_size = bin_size;
+  L.h_off.assign(L.n_seg + 1, 0);
+  L.h_tile_off.assign(L.n_seg + 1, 0);
+  L.h_pair_off.assign(L.n_seg + 1, 0);
+  L.h_bin_off.assign(L.n_seg + 1, 0);
+  L.max_tiles_per_seg = 0;
+  for (int c = 0; c < L.n_seg; ++c) {
+    int64_t nc = sizes[c];
+    int64_t nt = (nc + kTile - 1) / kTile;
+    L.h_off[c + 1] = L.h_off[c] + nc;
+    L.h_tile_off[c + 1] = L.h_tile_off[c] + nt;
+    L.h_pair_off[c + 1] = L.h_pair_off[c] + nc / 2;
+    L.h_bin_off[c + 1] = L.h_bin_off[c] + (nc + bin_size - 1) / bin_size;
+    if (nt > L.max_tiles_per_seg) L.max_tiles_per_seg = nt;
+  }
+  L.n = L.h_off[L.n_seg];
+  L.n_tiles = L.h_tile_off[L.n_seg];
+  L.n_pairs = L.h_pair_off[L.n_seg];
+  L.n_bins = L.h_bin_off[L.n_seg];
+  size_t s1 = sizeof(int64_t) * (L.n_seg + 1);
+  cudaError_t e;
+#define CMC_A(ptr, bytes) \
+  if ((e = cudaMallocAsync((void**)&(ptr), (bytes), st))) return e;
+  CMC_A(L.off, s1);
+  CMC_A(L.tile_off, s1);
+  CMC_A(L.pair_off, s1);
+  CMC_A(L.bin_off, s1);
+  CMC_A(L.seed, sizeof(uint64_t) * L.n_seg);
+  CMC_A(L.lnL, sizeof(double) * L.n_seg);
+  CMC_A(L.nb, sizeof(int64_t) * L.n_seg);
+  CMC_A(L.esc_step, sizeof(int64_t) * L.n_seg);
+  CMC_A(L.dt_bits, sizeof(uint64_t) * L.n_seg);
+  CMC_A(L.dt_last, sizeof(uint64_t) * L.n_seg);
+  CMC_A(L.stats, sizeof(unsigned long long) * kStStride * L.n_seg);
+#undef CMC_A
+  cudaMemcpyAsync(L.off, L.h_off.data(), s1, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(L.tile_off, L.h_tile_off.data(), s1, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(L.pair_off, L.h_pair_off.data(), s1, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(L.bin_off, L.h_bin_off.data(), s1, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(L.seed, seeds.data(), sizeof(uint64_t) * L.n_seg, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(L.lnL, lnL.data(), sizeof(double) * L.n_seg, cudaMemcpyHostToDevice, st);
+  std::vector<int64_t> nb(sizes.begin(), sizes.end());
+  cudaMemcpyAsync(L.nb, nb.data(), sizeof(int64_t) * L.n_seg, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
+  std::vector<uint64_t> inf(L.n_seg, 0x7FF0000000000000ull);
+  cudaMemcpyAsync(L.dt_bits, inf.data(), sizeof(uint64_t) * L.n_seg, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(L.dt_last, inf.data(), sizeof(uint64_t) * L.n_seg, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(L.stats, 0, sizeof(unsigned long long) * kStStride * L.n_seg, st);
+  // the host vectors above must outlive the copies
+  return cudaStreamSynchronize(st);
+}
+
+void free_layout(SegLayout& L, cudaStream_t st) {
+  void* ps[] = {L.off, L.tile_off, L.pair_off, L.bin_off, L.seed, L.lnL,
+                L.nb, L.esc_step, L.dt_bits, L.dt_last, L.stats};
+  for (void* p : ps)
+    if (p) cudaFreeAsync(p, st);
+  L = SegLayout();
+}
+
+void launch_make_keys(const SegLayout& L, const double* r, const double* vr,
+                      const double* vt, const double* m, const uint32_t* id,
+                      uint64_t* keys, Payload* pay, cudaStream_t st) {
+  if (L.n) k_make_keys<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, r, vr, vt, m, id, keys, pay);
+}
+
+void launch_id_keys(const SegLayout& L, const uint32_t* id, uint64_t* keys, cudaStream_t st) {
+  if (L.n) k_id_keys<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, id, keys);
+}
+
+void launch_rekey_radius(const SegLayout& L, const uint32_t* perm, const double* r,
+                         const uint32_t* id, uint64_t* keys, cudaStream_t st) {
+  if (L.n) k_rekey_radius<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, perm, r, id, keys);
+}
+
+void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* vals,
+                   const Payload* pay, double* r, double* x, double* vr, double* vt,
+                   double* m, uint32_t* id, double* r_old, double* c, cudaStream_t st) {
+  if (L.n)
+    k_gather<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, keys, vals, pay, r, x, vr, vt, m, id,
+                                                  r_old, c);
+}
+
+void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
+                      double* tile_m, double* tile_mx, double* phi, float2* t32,
+                      double* Mout, bool nb_sub, cudaStream_t st) {
+  (void)r;
+  if (!L.n_tiles) return;
+  Seg S = L.dev();
+  k_tile_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, L.esc_step, nb_sub, x, m, tile_m,
+                                                       tile_mx);
+  k_potential<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, L.esc_step, nb_sub, x, m, tile_m,
+                                                       tile_mx, phi, t32, Mout);
+}
+
+void launch_correction(const SegLayout& L, const double* r, const double* x,
+                       const double* phi, double* vr, double* vt, const double* r_old,
+                       const double* c, bool nb_sub, uint32_t* err, cudaStream_t st) {
+  (void)err;
+  if (!L.n) return;
+  k_correction<<<blocks_for(L.n, 128), 128, 0, st>>>(L.dev(), L.esc_step, nb_sub, r, x, phi,
+                                                    vr, vt, r_old, c, L.n);
+}
+
+void launch_energy(const SegLayout& L, const double* r, const double* vr, const double* vt,
+                   const double* m, double* tile_m, double* tile_k, double* tile_w,
+                   double* Mbuf, double* out3, cudaStream_t st) {
+  if (!L.n_tiles) return;
+  Seg S = L.dev();
+  k_tile_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, L.esc_step, false, r, m, tile_m,
+                                                       tile_k);
+  k_energy_tiles<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, r, vr, vt, m, tile_m, tile_k,
+                                                          tile_w, Mbuf);
+  k_energy_final<<<(unsigned)L.n_seg, kThreads, 0, st>>>(S, tile_k, tile_w, out3);
+}
+
+void launch_lagrange(const SegLayout& L, const double* r, const double* M,
+                     const double* fracs, int nf, double* out, cudaStream_t st) {
+  int n = L.n_seg * nf;
+  if (n) k_lagrange<<<blocks_for(n, 128), 128, 0, st>>>(L.dev(), r, M, fracs, nf, out);
+}
+
+void launch_validate(const SegLayout& L, const double* r, const double* vr,
+                     const double* vt, const double* m, bool allow_inf, uint32_t* err,
+                     cudaStream_t st) {
+  if (L.n) k_validate<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, r, vr, vt, m, allow_inf, err);
+}
+
+void launch_check_ids(const SegLayout& L, const uint64_t* sorted_ids, uint32_t* err,
+                      cudaStream_t st) {
+  if (L.n > 1)
+    k_check_ids<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.off, L.n_seg, sorted_ids, err);
+}
+
+void launch_step_end(const SegLayout& L, uint32_t* step, cudaStream_t st) {
+  k_step_end<<<1, 256, 0, st>>>(L.dev(), L.esc_step, L.dt_last, step);
+}
+
+}  // namespace cmc

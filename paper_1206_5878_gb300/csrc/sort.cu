@@ -1,0 +1,383 @@
+// Key-value sort of the stars by radius (section 2.1 step 6).
+//
+// A stable least-significant-digit radix sort over 8-bit digits of the
+// 64-bit key, run independently inside every segment (cluster) of the
+// state.  Each digit pass is a single "onesweep" kernel: a CTA takes the
+// next tile by atomic ticket, ranks its 4096 keys with warp-level
+// __match_any_sync multisplits, publishes its digit counts, and obtains the
+// counts of all earlier tiles of its segment by decoupled look-back on
+// those published words (integer sums, so the result does not depend on
+// timing).  Tiles are taken in ticket order, so every tile a CTA waits on
+// is already running; each wait is still bounded and reports a timeout
+// instead of spinning forever.  The tile is reordered in shared memory so
+// that the scatter writes contiguous runs.
+#include <utility>
+
+#include "cmc_host.hpp"
+
+namespace cmc {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+constexpr int kIPT = kTile / kThreads;  // 16 keys per thread
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagInc = 2ull << 62;
+constexpr unsigned long long kCountMask = (1ull << 62) - 1;
+constexpr int kSpinCap = 1 << 22;
+static_assert(kThreads == kBins, "one thread per digit");
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+  unsigned m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+  return *(volatile const unsigned long long*)p;
+}
+
+struct TileRange {
+  int seg;
+  int64_t lt;        // tile index inside the segment
+  int64_t seg_begin, begin, end;
+};
+
+__device__ __forceinline__ TileRange tile_range(const int64_t* off, const int64_t* tile_off,
+                                                int n_seg, int64_t t) {
+  TileRange R;
+  R.seg = seg_find(tile_off, n_seg, t);
+  R.lt = t - __ldg(tile_off + R.seg);
+  R.seg_begin = __ldg(off + R.seg);
+  R.begin = R.seg_begin + R.lt * kTile;
+  int64_t se = __ldg(off + R.seg + 1);
+  R.end = R.begin + kTile < se ? R.begin + kTile : se;
+  return R;
+}
+
+// block-wide exclusive scan of one value per thread (256 threads)
+__device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* s_warp) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kWarps ? s_warp[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < kWarps) s_warp[lane] = w;
+  }
+  __syncthreads();
+  uint32_t before = warp ? s_warp[warp - 1] : 0;
+  return before + x - v;
+}
+
+// ---------------------------------------------------------------- upsweep
+// Per-segment histogram of every pass digit.  Counts are gathered per warp
+// with __match_any_sync so that a digit shared by many keys costs one
+// shared-memory atomic per warp instead of one per key.
+__global__ void __launch_bounds__(kThreads) k_upsweep(const int64_t* off, const int64_t* tile_off,
+                                                      int n_seg, const uint64_t* keys,
+                                                      int first_pass, int passes,
+                                                      uint32_t* hist) {
+  __shared__ uint32_t h[8 * kBins];
+  for (int i = threadIdx.x; i < passes * kBins; i += kThreads) h[i] = 0;
+  __syncthreads();
+  TileRange R = tile_range(off, tile_off, n_seg, blockIdx.x);
+  const int lane = threadIdx.x & 31;
+  for (int64_t p0 = R.begin; p0 < R.end; p0 += kThreads) {
+    int64_t p = p0 + threadIdx.x;
+    bool valid = p < R.end;
+    uint64_t k = valid ? __ldg(keys + p) : 0;
+    for (int q = 0; q < passes; ++q) {
+      int d = valid ? (int)((k >> (8 * (first_pass + q))) & 0xFF) : kBins;
+      unsigned peers = __match_any_sync(0xffffffffu, d);
+      if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[q * kBins + d], __popc(peers));
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kBins; i += kThreads)
+    if (h[i]) atomicAdd(&hist[((size_t)R.seg * passes) * kBins + i], h[i]);
+}
+
+// exclusive scan of each (segment, pass) histogram in place
+__global__ void __launch_bounds__(kThreads) k_hist_scan(uint32_t* hist) {
+  __shared__ uint32_t s_warp[kWarps];
+  uint32_t* h = hist + (size_t)blockIdx.x * kBins;
+  uint32_t v = h[threadIdx.x];
+  uint32_t e = block_excl_scan_u32(v, s_warp);
+  h[threadIdx.x] = e;
+}
+
+struct PassSmem {
+  uint64_t key[kTile];
+  uint32_t val[kTile];
+  uint32_t whist[kWarps][kBins];
+  int64_t gbase[kBins];
+  uint32_t dstart[kBins];
+  uint32_t s_warp[kWarps];
+  int64_t tile;
+};
+
+// ------------------------------------------------------------- onesweep
+template <bool kValIdentity>
+__global__ void __launch_bounds__(kThreads) k_pass(const int64_t* off, const int64_t* tile_off,
+                                                   int n_seg, int64_t n_tiles,
+                                                   const uint64_t* __restrict__ keys_in,
+                                                   const uint32_t* __restrict__ vals_in,
+                                                   uint64_t* __restrict__ keys_out,
+                                                   uint32_t* __restrict__ vals_out,
+                                                   int pass, int q, int passes,
+                                                   const uint32_t* base,
+                                                   unsigned long long* desc,
+                                                   uint32_t* tickets, uint32_t* err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  PassSmem& S = *reinterpret_cast<PassSmem*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int shift = 8 * pass;
+
+  if (tid == 0) S.tile = (int64_t)atomicAdd(tickets + q, 1u);
+  for (int i = tid; i < kWarps * kBins; i += kThreads) (&S.whist[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t t = S.tile;
+  TileRange R = tile_range(off, tile_off, n_seg, t);
+  const int64_t n_items = R.end - R.begin;
+
+  // warp-striped load: warp w owns elements [w*512, w*512+512) of the tile
+  uint64_t k[kIPT];
+  uint32_t v[kIPT];
+  int dg[kIPT];
+#pragma unroll
+  for (int i = 0; i < kIPT; ++i) {
+    int64_t e = (int64_t)warp * (32 * kIPT) + i * 32 + lane;
+    int64_t p = R.begin + e;
+    bool valid = e < n_items;
+    k[i] = valid ? keys_in[p] : 0ull;
+    v[i] = valid ? (kValIdentity ? (uint32_t)p : vals_in[p]) : 0u;
+    dg[i] = valid ? (int)((k[i] >> shift) & 0xFF) : kBins;
+  }
+
+  // warp-level multisplit ranks (stable: slot order, then lane order)
+  uint32_t rank[kIPT];
+  const unsigned lt_mask = lanemask_lt();
+#pragma unroll
+  for (int i = 0; i < kIPT; ++i) {
+    unsigned peers = __match_any_sync(0xffffffffu, dg[i]);
+    int leader = __ffs(peers) - 1;
+    uint32_t old = 0;
+    if (lane == leader && dg[i] < kBins) {
+      old = S.whist[warp][dg[i]];
+      S.whist[warp][dg[i]] = old + __popc(peers);
+    }
+    old = __shfl_sync(0xffffffffu, old, leader);
+    rank[i] = old + __popc(peers & lt_mask);
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // per digit: exclusive prefix over warps, tile count
+  const int d = tid;
+  uint32_t cnt = 0;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    uint32_t c = S.whist[w][d];
+    S.whist[w][d] = cnt;
+    cnt += c;
+  }
+
+  // decoupled look-back over the earlier tiles of this segment
+  unsigned long long* my = desc + ((size_t)q * n_tiles + t) * kBins + d;
+  uint64_t excl = 0;
+  if (R.lt == 0) {
+    atomicExch(my, kFlagInc | (unsigned long long)cnt);
+  } else {
+    atomicExch(my, kFlagAgg | (unsigned long long)cnt);
+    int64_t j = t - 1;
+    const int64_t first = t - R.lt;
+    int spins = 0;
+    while (j >= first) {
+      unsigned long long w = ld_volatile(desc + ((size_t)q * n_tiles + j) * kBins + d);
+      if ((w & ~kCountMask) == 0) {
+        if (++spins > kSpinCap) {
+          set_err(err, kErrTimeout);
+          --j;
+          spins = 0;
+          continue;
+        }
+        if (spins > 32) __nanosleep(64);
+        continue;
+      }
+      excl += (w & kCountMask);
+      if ((w & ~kCountMask) == kFlagInc) break;
+      --j;
+    }
+    atomicExch(my, kFlagInc | (unsigned long long)(excl + cnt));
+  }
+
+  uint32_t ds = block_excl_scan_u32(cnt, S.s_warp);
+  S.dstart[d] = ds;
+  S.gbase[d] = R.seg_begin + (int64_t)base[((size_t)R.seg * passes + q) * kBins + d] +
+               (int64_t)excl - (int64_t)ds;
+  __syncthreads();
+
+  // reorder the tile in shared memory by digit
+#pragma unroll
+  for (int i = 0; i < kIPT; ++i) {
+    if (dg[i] < kBins) {
+      uint32_t lp = S.dstart[dg[i]] + S.whist[warp][dg[i]] + rank[i];
+      S.key[lp] = k[i];
+      S.val[lp] = v[i];
+    }
+  }
+  __syncthreads();
+
+  // contiguous runs per digit go out coalesced; a destination outside the
+  // segment (possible only after a timed-out look-back) is dropped
+  const int64_t seg_end = __ldg(off + R.seg + 1);
+  for (int lp = tid; lp < n_items; lp += kThreads) {
+    uint64_t kk = S.key[lp];
+    int dd = (int)((kk >> shift) & 0xFF);
+    int64_t dest = S.gbase[dd] + lp;
+    if (dest < R.seg_begin || dest >= seg_end) {
+      set_err(err, kErrTimeout);
+      continue;
+    }
+    keys_out[dest] = kk;
+    vals_out[dest] = S.val[lp];
+  }
+}
+
+// ------------------------------------------------------------- tie fix
+// Runs of equal finite keys are put in increasing id order (insertion sort
+// by one thread per run; a run that is already ordered costs one pass).
+constexpr long long kTieMoveCap = 1ll << 22;
+
+__global__ void k_tiefix(const int64_t* off, int n_seg, int64_t n, const uint64_t* keys,
+                         uint32_t* vals, const uint32_t* ids_by_val, int id_stride,
+                         uint32_t* err, unsigned long long* stats) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int c = seg_find(off, n_seg, p);
+  int64_t sb = __ldg(off + c), se = __ldg(off + c + 1);
+  uint64_t kp = keys[p];
+  if (key_is_escaper(kp) || p + 1 >= se || keys[p + 1] != kp) return;
+  if (p > sb && keys[p - 1] == kp) return;  // not the start of the run
+  int64_t e = p + 2;
+  while (e < se && keys[e] == kp) ++e;
+  long long moves = 0;
+  for (int64_t i = p; i < e; ++i)
+    if ((int64_t)vals[i] >= n) {
+      set_err(err, kErrTimeout);
+      return;
+    }
+  for (int64_t i = p + 1; i < e; ++i) {
+    uint32_t v = vals[i];
+    uint32_t idv = ids_by_val[(size_t)v * id_stride];
+    int64_t j = i - 1;
+    while (j >= p && ids_by_val[(size_t)vals[j] * id_stride] > idv) {
+      vals[j + 1] = vals[j];
+      --j;
+      if (++moves > kTieMoveCap) {
+        set_err(err, kErrTies);
+        vals[j + 1] = v;
+        return;
+      }
+    }
+    vals[j + 1] = v;
+  }
+  if (stats) atomicAdd(stats + (size_t)c * kStStride + kStTies, 1ull);
+}
+
+__global__ void k_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint4 c = reinterpret_cast<const uint4*>(ctr)[i];
+  U4 w = philox(c.x, c.y, c.z, c.w, seed);
+  reinterpret_cast<uint4*>(out)[i] = make_uint4(w.x, w.y, w.z, w.w);
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host
+cudaError_t alloc_sort(SortWork& W, const SegLayout& L, int max_passes, cudaStream_t st) {
+  W.max_passes = max_passes;
+  size_t n = (size_t)L.n;
+  cudaError_t e;
+  if ((e = cudaMallocAsync((void**)&W.keys_alt, sizeof(uint64_t) * (n ? n : 1), st))) return e;
+  if ((e = cudaMallocAsync((void**)&W.vals_alt, sizeof(uint32_t) * (n ? n : 1), st))) return e;
+  size_t desc_b = sizeof(unsigned long long) * (size_t)max_passes * L.n_tiles * kBins;
+  size_t hist_b = sizeof(uint32_t) * (size_t)L.n_seg * max_passes * kBins;
+  size_t tick_b = sizeof(uint32_t) * 16;
+  W.zero_bytes = desc_b + hist_b + tick_b;
+  if ((e = cudaMallocAsync(&W.zero_base, W.zero_bytes, st))) return e;
+  W.desc = (unsigned long long*)W.zero_base;
+  W.hist = (uint32_t*)((char*)W.zero_base + desc_b);
+  W.tickets = (uint32_t*)((char*)W.zero_base + desc_b + hist_b);
+  return cudaSuccess;
+}
+
+void free_sort(SortWork& W, cudaStream_t st) {
+  if (W.keys_alt) cudaFreeAsync(W.keys_alt, st);
+  if (W.vals_alt) cudaFreeAsync(W.vals_alt, st);
+  if (W.zero_base) cudaFreeAsync(W.zero_base, st);
+  W = SortWork();
+}
+
+void sort_prepare() {
+  cudaFuncSetAttribute(k_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(PassSmem));
+  cudaFuncSetAttribute(k_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(PassSmem));
+}
+
+cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint32_t* vals,
+                          int first_pass, int passes, bool vals_identity, uint32_t* err,
+                          cudaStream_t st) {
+  if (passes <= 0 || passes > W.max_passes || L.n_tiles == 0) return cudaSuccess;
+  cudaMemsetAsync(W.zero_base, 0, W.zero_bytes, st);
+  k_upsweep<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(L.off, L.tile_off, L.n_seg, keys,
+                                                     first_pass, passes, W.hist);
+  k_hist_scan<<<(unsigned)(L.n_seg * passes), kThreads, 0, st>>>(W.hist);
+  uint64_t* kin = keys;
+  uint32_t* vin = vals;
+  uint64_t* kout = W.keys_alt;
+  uint32_t* vout = W.vals_alt;
+  for (int q = 0; q < passes; ++q) {
+    if (q == 0 && vals_identity)
+      k_pass<true><<<(unsigned)L.n_tiles, kThreads, sizeof(PassSmem), st>>>(
+          L.off, L.tile_off, L.n_seg, L.n_tiles, kin, vin, kout, vout, first_pass + q, q,
+          passes, W.hist, W.desc, W.tickets, err);
+    else
+      k_pass<false><<<(unsigned)L.n_tiles, kThreads, sizeof(PassSmem), st>>>(
+          L.off, L.tile_off, L.n_seg, L.n_tiles, kin, vin, kout, vout, first_pass + q, q,
+          passes, W.hist, W.desc, W.tickets, err);
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  return cudaGetLastError();
+}
+
+void launch_tiefix(const SegLayout& L, const uint64_t* keys, uint32_t* vals,
+                           const uint32_t* ids_by_val, int id_stride, uint32_t* err,
+                           cudaStream_t st) {
+  if (L.n == 0) return;
+  k_tiefix<<<(unsigned)((L.n + 255) / 256), 256, 0, st>>>(L.off, L.n_seg, L.n, keys, vals,
+                                                         ids_by_val, id_stride, err, L.stats);
+}
+
+void launch_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out,
+                   cudaStream_t st) {
+  if (n <= 0) return;
+  k_philox<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ctr, seed, out);
+}
+
+}  // namespace cmc

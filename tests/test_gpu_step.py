@@ -1,0 +1,223 @@
+"""Whole timesteps through the C ABI (cmc_init / cmc_step / cmc_energy /
+cmc_lagrange_radii / cmc_get_state / cmc_set_state) against the oracle, and
+the reproducibility properties of the design: batched = unbatched,
+resumed = uninterrupted, result independent of launch shape."""
+import math
+
+import numpy as np
+import pytest
+
+import initial_conditions as ic
+from gpu_util import dev, host
+from test_golden import paper_values
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def g():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1206_5878_gb300 as lib
+    lib.load()
+    return lib
+
+
+def _cluster(g, d, seed, **cfg):
+    return g.Cluster({k: d[k] for k in ("r", "vr", "vt", "m", "id")}, [seed], **cfg)
+
+
+def _phi_scale(st):
+    nb = np.isfinite(st["r"]).sum()
+    return abs(st["phi"][0]) if nb else 1.0
+
+
+def _compare_states(st, orc_cluster, rtol=1e-12):
+    """Same ids at the same sorted slots; r, v_t and Phi within rtol; v_r^2
+    within rtol of the energy scale |Phi_0| (v_r = sqrt(Q) magnifies the
+    rounding of Q near a turning point)."""
+    o = orc_cluster
+    np.testing.assert_array_equal(st["id"], o.id)
+    fin = np.isfinite(o.r)
+    np.testing.assert_array_equal(np.isfinite(st["r"]), fin)
+    assert np.max(np.abs(st["r"][fin] / o.r[fin] - 1)) < rtol
+    scale = _phi_scale(st)
+    assert np.max(np.abs(st["vr"] ** 2 - o.vr ** 2)) < rtol * scale
+    assert np.all(np.sign(st["vr"]) == np.sign(o.vr))
+    assert np.max(np.abs(st["vt"] - o.vt) / (np.abs(o.vt) + 1e-300)) < rtol or \
+        np.max(np.abs(st["vt"] ** 2 - o.vt ** 2)) < rtol * scale
+    assert np.max(np.abs(st["phi"][fin] / o.phi[fin] - 1)) < rtol
+
+
+@pytest.mark.parametrize("n,masses", [(1, "equal"), (2, "equal"), (21, "equal"),
+                                      (10_000, "equal"), (30_011, "salpeter")])
+def test_init_energy_and_lagrange(g, orc, n, masses):
+    d = ic.plummer(n, seed=1, masses=masses)
+    c = _cluster(g, d, 1)
+    o = orc.Cluster(d["r"], d["vr"], d["vt"], d["m"], d["id"], seed=1, pot_mode="dd")
+    st = c.get_state()
+    np.testing.assert_array_equal(st["id"], o.id)
+    np.testing.assert_array_equal(st["r"], o.r)
+    assert np.max(np.abs(st["phi"] / o.phi - 1)) < 1e-12
+    E = c.energy()[0]
+    Eo = o.energy()
+    assert np.max(np.abs(E - Eo) / np.abs(Eo).max()) < 1e-12
+    fr = [0.0, 0.1, 0.5, 0.9, 1.0]
+    lr = c.lagrange_radii(fr)[0]
+    lro = o.lagrange_radii(fr)
+    # the enclosed-mass threshold is a floating-point decision: the GPU's
+    # star is the oracle's or its neighbour where M_k sits at f M_b +- 1e-12
+    for a, b in zip(lr, lro):
+        if a != b:
+            ka, kb = np.searchsorted(o.r, a), np.searchsorted(o.r, b)
+            assert abs(ka - kb) == 1
+    assert c.nbound()[0] == n and c.kernels_per_step() > 10
+
+
+@pytest.mark.parametrize("n", [2, 3, 41, 4097, 10_000])
+def test_one_step_matches_oracle(g, orc, n):
+    d = ic.plummer(n, seed=n)
+    c = _cluster(g, d, 7)
+    o = orc.Cluster(d["r"], d["vr"], d["vt"], d["m"], d["id"], seed=7, pot_mode="dd")
+    c.step(1)
+    o.step(1)
+    _compare_states(c.get_state(), o)
+    assert c.nbound()[0] == o.nb
+    assert c.dt()[0] == o.last_dt  # same bins, same stars, same order
+    s = c.stats()[0]
+    for k in ("escaped", "degenerate", "cap_hits", "trials", "violations", "clamps"):
+        assert s[k] == o.last_stats[k], k
+
+
+def test_ten_steps_plummer_1e4_fp64(g, orc):
+    """Plummer N = 10^4, FP64, 10 steps: same trajectory as the oracle and
+    energy conserved to the paper's bound."""
+    d = ic.plummer(10_000, seed=1)
+    c = _cluster(g, d, 1)
+    o = orc.Cluster(d["r"], d["vr"], d["vt"], d["m"], d["id"], seed=1, pot_mode="dd")
+    E0 = c.energy()[0][2]
+    bound = paper_values()["energy_drift_bound"]
+    for step in range(10):
+        c.step(1)
+        o.step(1)
+        _compare_states(c.get_state(), o, rtol=1e-10)
+        assert abs(c.energy()[0][2] / E0 - 1) < bound
+        np.testing.assert_allclose(c.lagrange_radii([0.1, 0.5, 0.9])[0],
+                                   o.lagrange_radii([0.1, 0.5, 0.9]), rtol=1e-10)
+
+
+def test_ensemble_equals_separate_runs(g):
+    sizes = [1, 3, 4096, 4097, 9000, 20]
+    seeds = [1000 + c for c in range(len(sizes))]
+    parts = [ic.plummer(n, s) for n, s in zip(sizes, seeds)]
+    cat = {k: np.concatenate([p[k] for p in parts]) for k in ("r", "vr", "vt", "m", "id")}
+    ens = g.Cluster(cat, seeds, sizes=sizes)
+    ens.step(4)
+    est = ens.get_state()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for i, (p, s) in enumerate(zip(parts, seeds)):
+        one = _cluster(g, p, s)
+        one.step(4)
+        st = one.get_state()
+        sl = slice(off[i], off[i + 1])
+        for k in ("r", "vr", "vt", "m", "id", "phi"):
+            np.testing.assert_array_equal(est[k][sl], st[k], err_msg="%d %s" % (i, k))
+        assert ens.dt()[i] == one.dt()[0]
+        assert ens.stats()[i] == one.stats()[0]
+        np.testing.assert_array_equal(ens.energy()[i], one.energy()[0])
+
+
+def test_resume_is_bit_identical(g):
+    d = ic.plummer(12_345, seed=3, masses="salpeter")
+    a = _cluster(g, d, 3)
+    a.step(6)
+    b = _cluster(g, d, 3)
+    b.step(3)
+    mid = b.get_state()
+    c = _cluster(g, d, 3)
+    c.set_state(mid, mid["step"])
+    c.step(3)
+    sa, sc = a.get_state(), c.get_state()
+    for k in ("r", "vr", "vt", "m", "id", "phi"):
+        np.testing.assert_array_equal(sa[k], sc[k], err_msg=k)
+    assert sc["step"] == 6
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_launch_shape_does_not_change_bits(g, precision):
+    d = ic.plummer(20_000, seed=4)
+    outs = []
+    for blk in (32, 128, 256):
+        c = _cluster(g, d, 4, orbit_block=blk, precision=precision)
+        c.step(2)
+        outs.append(c.get_state())
+    for o in outs[1:]:
+        for k in ("r", "vr", "vt", "phi"):
+            np.testing.assert_array_equal(o[k], outs[0][k])
+
+
+def test_host_and_device_inputs_agree(g):
+    import torch
+    d = ic.plummer(5000, seed=8)
+    a = _cluster(g, d, 8)
+    b = g.Cluster({k: dev(d[k]) for k in ("r", "vr", "vt", "m", "id")}, [8])
+    a.step(2)
+    b.step(2)
+    sa, sb = a.get_state(), b.get_state()
+    out = {k: torch.empty(5000, dtype=torch.float64, device="cuda") for k in ("r", "vr", "vt",
+                                                                              "m", "phi")}
+    out["id"] = torch.empty(5000, dtype=torch.int32, device="cuda")
+    b.get_state(out)
+    for k in ("r", "vr", "vt", "m", "id", "phi"):
+        np.testing.assert_array_equal(sa[k], sb[k])
+        np.testing.assert_array_equal(sa[k], host(out[k]))
+
+
+def test_mixed_precision_plummer_1e4(g, orc):
+    """Mixed mode: energy within the paper's bound; per step, the state
+    advanced from the same FP64 state differs from the FP64 path only in
+    the stars whose FP32 accept decision flipped."""
+    d = ic.plummer(10_000, seed=2)
+    c = _cluster(g, d, 2, precision=1)
+    E0 = c.energy()[0][2]
+    for _ in range(10):
+        c.step(1)
+        assert abs(c.energy()[0][2] / E0 - 1) < paper_values()["energy_drift_bound"]
+    st = c.get_state()
+    f64 = _cluster(g, {k: st[k] for k in ("r", "vr", "vt", "m", "id")}, 2)
+    f32 = _cluster(g, {k: st[k] for k in ("r", "vr", "vt", "m", "id")}, 2, precision=1)
+    f64.set_state(st, st["step"])
+    f32.set_state(st, st["step"])
+    f64.step(1)
+    f32.step(1)
+    a, b = f64.get_state(), f32.get_state()
+    same = np.isin(a["id"], b["id"])
+    assert same.all()
+    ia, ib = np.argsort(a["id"]), np.argsort(b["id"])
+    eq = a["r"][ia] == b["r"][ib]
+    assert eq.mean() > 0.99
+
+
+def test_invalid_inputs_are_rejected(g):
+    d = ic.plummer(100, seed=1)
+    for bad in ("neg_r", "nan_v", "dup_id", "neg_vt", "neg_m"):
+        e = {k: d[k].copy() for k in ("r", "vr", "vt", "m", "id")}
+        if bad == "neg_r":
+            e["r"][5] = -1.0
+        elif bad == "nan_v":
+            e["vr"][7] = np.nan
+        elif bad == "dup_id":
+            e["id"][3] = e["id"][4]
+        elif bad == "neg_vt":
+            e["vt"][2] = -0.1
+        else:
+            e["m"][9] = -1e-3
+        with pytest.raises(g.CMCError) as ei:
+            _cluster(g, e, 1)
+        assert ei.value.status == 1  # CMC_EINVAL
+    c = _cluster(g, d, 1)
+    with pytest.raises(g.CMCError):
+        c.step(-1)
+    with pytest.raises(g.CMCError):
+        c.lagrange_radii([1.5])
+    c.step(1)  # the context is still usable
