@@ -83,7 +83,7 @@ typedef struct {
     double gamma;               /* Coulomb logarithm ln(gamma N) (0.1, Eq. 20) */
     int32_t max_trials;         /* rejection trials per star per step (1000) */
     int32_t energy_correction;  /* 1: apply the section 2.1 step 6 correction */
-    int32_t orbit_block;        /* threads per block of the orbit kernel (0: auto) */
+    int32_t orbit_block;        /* threads per block of the orbit kernel: 0 (auto) or a multiple of 32 up to 256 */
     int32_t reserved;
 } cmc_config;
 
@@ -147,6 +147,25 @@ cmc_status cmc_get_dt(cmc_ctx *ctx, double *out);
 
 /* Cumulative counters: out (host, n_clusters x CMC_NSTATS). */
 cmc_status cmc_get_stats(cmc_ctx *ctx, int64_t *out);
+
+/* Stages of one timestep, as timed by cmc_step_profiled. */
+enum {
+    CMC_STAGE_TIMESTEP = 0,    /* Eq. 7 bins and the minimum over bins */
+    CMC_STAGE_RELAX = 1,       /* two-body relaxation of neighbour pairs */
+    CMC_STAGE_ORBIT = 2,       /* turning points and rejection sampling */
+    CMC_STAGE_SORT = 3,        /* radix passes and the id order of ties */
+    CMC_STAGE_GATHER = 4,      /* payload into the sorted arrays */
+    CMC_STAGE_POTENTIAL = 5,   /* shell potential (Eqs. 1-5) */
+    CMC_STAGE_CORRECTION = 6,  /* energy correction */
+    CMC_STAGE_END = 7,         /* bookkeeping of the step */
+    CMC_NSTAGES = 8
+};
+
+/* Advance by n_steps timesteps like cmc_step, but launch the kernels one
+ * by one (no graph) with a CUDA event after each stage; stage_ms (host,
+ * CMC_NSTAGES) receives the summed device time of each stage.  Results are
+ * identical to cmc_step. */
+cmc_status cmc_step_profiled(cmc_ctx *ctx, int32_t n_steps, double *stage_ms);
 
 /* Number of kernels one cmc_step timestep launches. */
 int32_t cmc_kernels_per_step(const cmc_ctx *ctx);

@@ -376,7 +376,9 @@ int or_encounter(double m1, double m2, double vr1, double vt1, double vr2, doubl
     for (i = 0; i < 16; ++i) out[i] = 0.0;
     out[15] = 1.0;
     msum = m1 + m2;
-    if (!(n > 0.0) || !(msum > 0.0)) {
+    /* no density, no mass, or no positive Coulomb logarithm (ln(gamma N) <= 0
+     * for N <= 1/gamma): no deflection */
+    if (!(n > 0.0) || !(msum > 0.0) || !(lnL > 0.0) || !(dt < INFINITY)) {
         out[0] = vr1; out[1] = vt1; out[3] = vr2; out[4] = vt2;
         for (i = 0; i < 6; ++i) out[6 + i] = out[i];
         return 0;

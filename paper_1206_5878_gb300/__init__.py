@@ -117,6 +117,12 @@ class Cluster:
         check(self.lib.cmc_step(self.ctx, int(n_steps)), self.ctx)
         return self
 
+    def step_profiled(self, n_steps: int = 1) -> dict:
+        """Like step(); returns the summed device milliseconds per stage."""
+        ms = np.zeros(len(_native.STAGE_NAMES))
+        check(self.lib.cmc_step_profiled(self.ctx, int(n_steps), ms.ctypes.data), self.ctx)
+        return dict(zip(_native.STAGE_NAMES, (float(v) for v in ms)))
+
     def energy(self) -> np.ndarray:
         out = np.zeros((self.n_clusters, 3))
         check(self.lib.cmc_energy(self.ctx, out.ctypes.data), self.ctx)

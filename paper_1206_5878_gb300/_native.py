@@ -25,6 +25,8 @@ STATUS_NAMES = {0: "CMC_OK", 1: "CMC_EINVAL", 2: "CMC_ENOMEM", 3: "CMC_ECUDA",
 STAT_NAMES = ("escaped", "degenerate", "cap_hits", "trials", "violations", "clamps",
               "angle_fails", "ties")
 CMC_NSTATS = len(STAT_NAMES)
+STAGE_NAMES = ("timestep", "relax", "orbit", "sort", "gather", "potential", "correction",
+               "end")
 
 
 class cmc_config(ctypes.Structure):
@@ -39,6 +41,7 @@ SIGNATURES = {
     "cmc_init": (_i32, [_pp, ctypes.POINTER(cmc_config), _i32, _p, _p, _p, _p, _p, _p, _p,
                         _i32, _p]),
     "cmc_step": (_i32, [_p, _i32]),
+    "cmc_step_profiled": (_i32, [_p, _i32, _p]),
     "cmc_energy": (_i32, [_p, _p]),
     "cmc_lagrange_radii": (_i32, [_p, _p, _i32, _p]),
     "cmc_get_state": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p, _i32]),

@@ -146,6 +146,36 @@ void record_step(cmc_ctx* c, cudaStream_t st) {
   launch_step_end(L, c->step, st);
 }
 
+// The same kernels as record_step, with an event after each stage.
+void record_step_profiled(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev) {
+  const SegLayout& L = c->L;
+  const bool mixed = c->cfg.precision == 1;
+  cudaEventRecord(ev[0], st);
+  launch_bins(L, c->r, c->vr, c->vt, c->m, c->nbin, c->pref, st);
+  cudaEventRecord(ev[1], st);
+  launch_relax(L, c->vr, c->vt, c->m, c->id, c->nbin, c->step, st);
+  cudaEventRecord(ev[2], st);
+  launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
+               mixed ? c->t32 : nullptr, c->vr, c->vt, c->m, c->id, c->step, c->keys, c->pay,
+               nullptr, c->cfg.orbit_block, st);
+  cudaEventRecord(ev[3], st);
+  sort_segments(L, c->W, c->keys, c->vals, 0, 8, true, c->err, st);
+  launch_tiefix(L, c->keys, c->vals, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)),
+                c->err, st);
+  cudaEventRecord(ev[4], st);
+  launch_gather(L, c->keys, c->vals, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old,
+                c->cc, st);
+  cudaEventRecord(ev[5], st);
+  launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
+                   mixed ? c->t32 : nullptr, nullptr, true, st);
+  cudaEventRecord(ev[6], st);
+  if (c->cfg.energy_correction)
+    launch_correction(L, c->r, c->x, c->phi, c->vr, c->vt, c->r_old, c->cc, true, c->err, st);
+  cudaEventRecord(ev[7], st);
+  launch_step_end(L, c->step, st);
+  cudaEventRecord(ev[8], st);
+}
+
 int count_step_kernels(const cmc_ctx* c) {
   // bins, relax, orbit, upsweep, hist scan, 8 passes, tie fix, gather,
   // tile sums, potential, [correction], step end
@@ -240,7 +270,7 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   else cmc_config_default(&cfg);
   if ((cfg.precision != 0 && cfg.precision != 1) || cfg.bin_size < 2 || (cfg.bin_size & 1) ||
       cfg.max_trials < 1 || cfg.max_trials > (1 << 24) || !(cfg.theta_max > 0.0) ||
-      !(cfg.gamma > 0.0) || cfg.orbit_block < 0 || cfg.orbit_block > 1024 ||
+      !(cfg.gamma > 0.0) || cfg.orbit_block < 0 || cfg.orbit_block > 256 ||
       (cfg.orbit_block % 32))
     return fail(nullptr, CMC_EINVAL, "cmc_init: bad configuration");
   std::vector<int64_t> sizes(n_per_cluster, n_per_cluster + n_clusters);
@@ -325,6 +355,30 @@ cmc_status cmc_step(cmc_ctx* c, int32_t n_steps) {
     e = cudaGraphLaunch(c->exec, c->stream);
     if (e) return cuda_fail(c, e, "cmc_step: launch");
   }
+  c->steps_taken += n_steps;
+  return check_err_flags(c);
+}
+
+cmc_status cmc_step_profiled(cmc_ctx* c, int32_t n_steps, double* stage_ms) {
+  if (!c || n_steps < 0 || !stage_ms) return fail(c, CMC_EINVAL, "cmc_step_profiled: bad arguments");
+  if (c->poisoned) return fail(c, CMC_EPOISONED, c->last_error);
+  DeviceGuard g(c->device);
+  for (int i = 0; i < CMC_NSTAGES; ++i) stage_ms[i] = 0.0;
+  std::vector<cudaEvent_t> ev((size_t)(CMC_NSTAGES + 1) * (n_steps > 0 ? n_steps : 1));
+  for (auto& e : ev) cudaEventCreate(&e);
+  for (int32_t i = 0; i < n_steps; ++i) record_step_profiled(c, c->stream, &ev[(size_t)i * (CMC_NSTAGES + 1)]);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (!e) {
+    for (int32_t i = 0; i < n_steps; ++i)
+      for (int sidx = 0; sidx < CMC_NSTAGES; ++sidx) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[(size_t)i * (CMC_NSTAGES + 1) + sidx],
+                             ev[(size_t)i * (CMC_NSTAGES + 1) + sidx + 1]);
+        stage_ms[sidx] += ms;
+      }
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  if (e) return cuda_fail(c, e, "cmc_step_profiled");
   c->steps_taken += n_steps;
   return check_err_flags(c);
 }
@@ -497,7 +551,18 @@ cmc_status cmc_sort_radius(int64_t n, const double* r, const uint32_t* id, uint3
     launch_make_keys(S.L, r, nullptr, nullptr, nullptr, id, keys, nullptr, st);
     sort_segments(S.L, W, keys, perm, 0, 8, true, err, st);
     launch_tiefix(S.L, keys, perm, id, 1, err, st);
-    e = cudaGetLastError();
+    uint32_t he = 0;
+    e = cudaMemcpyAsync(&he, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+    if (!e) e = cudaStreamSynchronize(st);
+    if (!e && (he & kErrTies)) {
+      // runs of equal radii too long for the tie fix: order by id first,
+      // then stably by radius
+      launch_id_keys(S.L, id, keys, st);
+      sort_segments(S.L, W, keys, perm, 0, 4, true, err, st);
+      launch_rekey_radius(S.L, perm, r, id, keys, st);
+      sort_segments(S.L, W, keys, perm, 0, 8, false, err, st);
+    }
+    if (!e) e = cudaGetLastError();
   }
   dfree(keys, st);
   dfree(err, st);

