@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark: star-updates/s of the Henon Monte Carlo timestep on GB300.
+
+Default workload: Plummer sphere, N = 10^7 equal-mass stars (Henon units),
+mixed-precision orbits, one cluster per GPU.  A "step" is one full timestep
+(Eq. 7 bins, relaxation, new orbits, sort, potential, energy correction)
+through the library's graph-captured cmc_step.  Inputs (0.6 GB of state)
+are larger than the L2 cache; no flush is needed between steps.
+
+Prints one JSON line on rank 0.  --impl reference times the FP64 oracle on
+the host cores instead (a bounded sample of the same workload per step).
+Multi-GPU (torchrun): independent replicas, one cluster per rank (weak
+scaling); the time is the maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "star-updates/s per timestep at N=1e7 (1 GB300) + HBM roofline %, mixed vs FP64"
+UNIT = "star-updates/s"
+PROFILE = os.path.join(ROOT, "profiles", "orbit_kernel_counters.md")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+# ----------------------------------------------------------------- clocks
+class Clocks:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def __enter__(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.f:
+            return None
+        self.f.seek(0)
+        rows = [l.strip().split(", ") for l in self.f if l.strip()]
+        sm, smax, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------ peaks, roofline
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d.get("hbm_gbs"), "measured"
+    return 6800.0, "fallback"
+
+
+def orbit_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("orbit.cu", "cmc_device.cuh"):
+        with open(os.path.join(ROOT, "paper_1206_5878_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic_per_star(precision: str):
+    """DRAM bytes per star of the orbit kernel from the committed ncu summary,
+    or None when the kernel source changed since the counters were taken."""
+    if not os.path.exists(PROFILE):
+        return None
+    src, val = None, None
+    with open(PROFILE) as f:
+        for line in f:
+            if line.startswith("source_hash:"):
+                src = line.split(":", 1)[1].strip()
+            if line.startswith("dram_bytes_per_star_%s:" % precision):
+                val = float(line.split(":", 1)[1])
+    if src != orbit_source_hash():
+        return None
+    return val
+
+
+# Compulsory HBM bytes of one orbit-kernel launch per bound star: it reads
+# r, v_r, v_t, Phi, m (8 B each) and id (4 B), and writes the sort key (8 B)
+# and the 48-B payload record.  Table probes are not counted.
+ORBIT_BYTES_PER_STAR = 5 * 8 + 4 + 8 + 48
+
+
+# ------------------------------------------------------------ oracle sample
+def oracle_sample_step(state, n_orbit: int, seed: int, step: int):
+    """One oracle timestep measured on a bounded sample of the workload:
+    Eq. 7 bins, relaxation, sort, potential and energy correction on all N
+    stars, the orbit step on n_orbit random stars scaled to N.  Returns the
+    seconds of one timestep of N stars."""
+    import numpy as np
+
+    import oracle
+    r, vr, vt, m, ids, phi = state
+    n = r.shape[0]
+    lnL = oracle.coulomb_log(n)
+    t0 = time.perf_counter()
+    dt, nbin = oracle.timestep(r, vr, vt, m, lnL)
+    vr2, vt2, _ = oracle.relax(vr, vt, m, ids, nbin, dt, lnL, seed, step)
+    t1 = time.perf_counter()
+    rng = np.random.default_rng(step)
+    ks = rng.choice(n, size=min(n_orbit, n), replace=False)
+    rn = r.copy()
+    tt = time.perf_counter()
+    for k in ks:
+        o = oracle.orbit_star(int(k), r, phi, vr2[k], vt2[k], int(ids[k]), seed, step)
+        rn[k] = o["r_new"]
+    t2 = time.perf_counter()
+    perm = oracle.sort_perm(rn, ids)
+    t3 = time.perf_counter()
+    phin = oracle.potential(r, m, "recursion")
+    oracle.energy_correction(r, phin, vr2, vt2, r, np.zeros(n))
+    t4 = time.perf_counter()
+    per_star_sample = (t2 - tt) / len(ks)
+    whole = (t1 - t0) + (t4 - t2)
+    del perm
+    return whole + per_star_sample * n
+
+
+def build_oracle_state(n: int, seed: int):
+    import numpy as np
+
+    import initial_conditions as ic
+    import oracle
+    d = ic.plummer(n, seed=seed)
+    perm = oracle.sort_perm(d["r"], d["id"])
+    r, vr, vt, m, ids = (np.ascontiguousarray(d[k][perm]) for k in ("r", "vr", "vt", "m", "id"))
+    phi = oracle.potential(r, m, "recursion")
+    return r, vr, vt, m, ids, phi
+
+
+def cpu_baseline(n: int, seed: int, n_orbit: int = 50_000):
+    import oracle
+    oracle.build()
+    st = build_oracle_state(n, seed)
+    sec = oracle_sample_step(st, n_orbit, seed, 0)
+    return {"value": n / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": ("one oracle timestep of the N=%d Plummer cluster: Eq. 7 bins, "
+                       "relaxation, sort, potential and energy correction on all stars, the "
+                       "orbit step on %d random stars scaled to N (FP64, one core)"
+                       % (n, n_orbit))}
+
+
+# ------------------------------------------------------------------- arms
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    log("reference arm: oracle on the host, N=%d" % args.n)
+    st = build_oracle_state(args.n, args.seed)
+    n_orbit = args.ref_orbit_sample
+    for w in range(args.warmup):
+        oracle_sample_step(st, n_orbit, args.seed, w)
+    tot = 0.0
+    for k in range(args.steps):
+        tot += oracle_sample_step(st, n_orbit, args.seed, args.warmup + k)
+    value = args.n * args.steps / tot
+    sample = ("per step: Eq. 7 bins, relaxation, sort, potential and energy correction on "
+              "all %d stars, the orbit step on %d random stars scaled to N (FP64, one core)"
+              % (args.n, n_orbit))
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": "Plummer N=%d equal-mass (oracle, host)" % args.n,
+                       "n_stars": args.n, "seed": args.seed},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_cmc(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    import initial_conditions as ic
+    import paper_1206_5878_gb300 as g
+
+    torch.cuda.set_device(local_rank)
+    dist = world > 1
+    seed = args.seed + rank
+    n = args.n
+    prec = 1 if args.precision == "mixed" else 0
+    log("rank %d: building Plummer N=%d seed=%d" % (rank, n, seed))
+    d = ic.plummer(n, seed=seed)
+    dev = {k: torch.from_numpy(d[k].view(np.int32) if k == "id" else d[k]).cuda()
+           for k in ("r", "vr", "vt", "m", "id")}
+    c = g.Cluster(dev, [seed], precision=prec)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    c.step(args.warmup)
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with Clocks(local_rank) as clk:
+        ev0.record(stream)
+        c.step(args.steps)
+        ev1.record(stream)
+        barrier()
+    ms = max_over_ranks(ev0.elapsed_time(ev1))
+    clocks = clk.summary()
+    value = n * args.steps * world / (ms / 1e3)
+    kernels = c.kernels_per_step() * args.steps
+
+    # per-stage device times over the same number of steps (kernels launched
+    # one by one with events between the stages)
+    stages = c.step_profiled(args.steps)
+    stages_avg = {k: v / args.steps for k, v in stages.items()}
+    dom = max(stages_avg, key=stages_avg.get)
+    hbm, peak_kind = measured_peaks()
+    orbit_ms = stages_avg["orbit"]
+    achieved = ORBIT_BYTES_PER_STAR * n / (orbit_ms / 1e3) / 1e9
+    traffic_ps = profiled_traffic_per_star(args.precision)
+    roof = {"kernel": "k_orbit<%d>" % prec, "bound": "hbm", "achieved": achieved, "peak": hbm,
+            "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind,
+            "algorithmic_bytes_per_launch": ORBIT_BYTES_PER_STAR * n,
+            "traffic": None if traffic_ps is None else traffic_ps * n,
+            "launch_ms": orbit_ms, "dominant_stage": dom}
+    # step-level compulsory traffic (248 B per star-update) against HBM
+    step_frac = 248.0 * value / world / 1e9 / hbm
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64+f32" if prec else "f64", "data": "synthetic",
+           "config": {"workload": "Plummer N=%d equal-mass, %s orbits" % (n, args.precision),
+                      "n_stars": n, "precision": args.precision, "seed": args.seed,
+                      "parallelism": "replicas" if dist else "single",
+                      "l2": "inputs larger than L2 (state %.2f GB)" % (n * 60 / 1e9)},
+           "gpu_launches": kernels, "stages_ms": stages_avg, "roofline": roof,
+           "step_hbm_frac": step_frac, "clocks": clocks}
+
+    if args.fp64 and prec == 1:
+        c64 = g.Cluster(dev, [seed], precision=0)
+        c64.step(1)
+        barrier()
+        k64 = max(1, min(args.steps, 3))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        c64.step(k64)
+        e1.record(stream)
+        barrier()
+        ms64 = max_over_ranks(e0.elapsed_time(e1))
+        out["fp64"] = {"value": n * k64 * world / (ms64 / 1e3), "unit": UNIT,
+                       "ms_per_step": ms64 / k64, "steps": k64}
+        c64.close()
+
+    if args.e2e:
+        # the public API with host buffers: per step, the state goes in from
+        # pinned host memory, one timestep runs, the state comes back
+        pin = {k: torch.empty(n, dtype=torch.float64, pin_memory=True)
+               for k in ("r", "vr", "vt", "m")}
+        pin["id"] = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        hst = {k: v.numpy() for k, v in pin.items()}
+        hst["id"] = hst["id"].view(np.uint32)
+        st0 = c.get_state({k: hst[k] for k in ("r", "vr", "vt", "m", "id")})
+        step0 = st0["step"]
+        k_e2e = max(1, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(k_e2e):
+            c.set_state(hst, step0 + i)
+            c.step(1)
+            c.get_state(hst)
+        barrier()
+        sec = max_over_ranks(time.perf_counter() - t0)
+        out["e2e"] = {"value": n * k_e2e * world / sec, "unit": UNIT,
+                      "h2d_bytes_per_step": n * (4 * 8 + 4),
+                      "d2h_bytes_per_step": n * (4 * 8 + 4), "steps": k_e2e,
+                      "api": "cmc_set_state(host) + cmc_step(1) + cmc_get_state(host)"}
+    c.close()
+
+    if rank == 0 and args.cpu and world == 1:
+        log("cpu baseline: oracle on a sample of the workload")
+        out["cpu_baseline"] = cpu_baseline(n, args.seed, args.cpu_orbit_sample)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cmc", choices=["cmc", "reference"])
+    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-fp64", dest="fp64", action="store_false")
+    ap.add_argument("--no-e2e", dest="e2e", action="store_false")
+    ap.add_argument("--no-cpu", dest="cpu", action="store_false")
+    ap.add_argument("--cpu-orbit-sample", type=int, default=50_000)
+    ap.add_argument("--ref-orbit-sample", type=int, default=20_000)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    try:
+        run_cmc(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

