@@ -237,6 +237,30 @@ cmc_status cmc_energy_correction(int64_t n, const double *r, const double *phi, 
                                  double *vt, const double *r_old, const double *c,
                                  void *stream);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free shell potential.  The paper has no counterpart: this is
+ * cmc_potential (same arithmetic, same results) for callers that may not
+ * allocate device memory -- code that runs while a stream is captured into
+ * a CUDA graph, loops that forbid allocation after start-up, programs that
+ * give all device memory to their own pool.  cmc_potential takes scratch
+ * from cudaMallocAsync; this function allocates nothing.  Its only scratch,
+ * the per-tile sums of the scan, is one fixed array of the library's own
+ * device memory (2 * CMC_STATIC_MAX_STARS / 4096 doubles, 64 KiB) that
+ * every GPU that loads the library holds until the process exits.
+ *   n <= CMC_STATIC_MAX_STARS sorted stars; r, m (device, n doubles) in;
+ *   phi (device, n doubles) out; M (device, may be NULL) enclosed mass out.
+ * The first call on each device looks up the array's device address with
+ * that device current; make that first call before any stream capture.
+ * Every call shares the one array and overwrites it (nothing in it needs
+ * to start at zero), so calls whose work overlaps on the GPU (different
+ * streams) race: order them on one stream.  Returns CMC_EINVAL for
+ * n > CMC_STATIC_MAX_STARS or bad pointers, CMC_ECUDA if the launch fails;
+ * returns once the work is enqueued on `stream`.
+ * ------------------------------------------------------------------- */
+#define CMC_STATIC_MAX_STARS 16777216
+cmc_status cmc_potential_static(int64_t n, const double *r, const double *m, double *phi,
+                                double *M, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

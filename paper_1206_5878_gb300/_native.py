@@ -61,6 +61,7 @@ SIGNATURES = {
     "cmc_orbit": (_i32, [_i64, _p, _p, _p, _p, _p, _u64, _u32, _i32, _i32, _p, _p, _p, _p, _p,
                          _p, _p, _p, _p]),
     "cmc_energy_correction": (_i32, [_i64, _p, _p, _p, _p, _p, _p, _p]),
+    "cmc_potential_static": (_i32, [_i64, _p, _p, _p, _p, _p]),
 }
 
 _lib = None
