@@ -19,6 +19,7 @@ struct cmc_ctx {
   int device = 0;
   SegLayout L;
   SortWork W;
+  BucketWork bk;  // radius-bucket index of the float table (mixed mode)
   double pref = 0.0;
   // state (sorted SoA)
   double *r = nullptr, *x = nullptr, *vr = nullptr, *vt = nullptr, *m = nullptr,
@@ -123,63 +124,49 @@ void order_state(cmc_ctx* c, cudaStream_t st) {
   cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32, nullptr, false,
                    st);
+  if (c->cfg.precision == 1) launch_buckets(L, c->t32, false, c->bk, st);
 }
 
-// The kernels of one timestep, in the order of section 3.3.
-void record_step(cmc_ctx* c, cudaStream_t st) {
+// The kernels of one timestep, in the order of section 3.3.  With ev, an
+// event is recorded before the first stage and after every stage.
+void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   const SegLayout& L = c->L;
   const bool mixed = c->cfg.precision == 1;
+  auto mark = [&](int i) {
+    if (ev) cudaEventRecord(ev[i], st);
+  };
+  mark(0);
   launch_bins(L, c->r, c->vr, c->vt, c->m, c->nbin, c->pref, st);
+  mark(1);
   launch_relax(L, c->vr, c->vt, c->m, c->id, c->nbin, c->step, st);
+  mark(2);
   launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                mixed ? c->t32 : nullptr, c->vr, c->vt, c->m, c->id, c->step, c->keys, c->pay,
-               nullptr, c->cfg.orbit_block, st);
+               nullptr, c->cfg.orbit_block, c->bk.args(), st);
+  mark(3);
   sort_segments(L, c->W, c->keys, c->vals, 0, 8, true, c->err, st);
   launch_tiefix(L, c->keys, c->vals, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)),
                 c->err, st);
+  mark(4);
   launch_gather(L, c->keys, c->vals, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old,
                 c->cc, st);
+  mark(5);
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
                    mixed ? c->t32 : nullptr, nullptr, true, st);
+  if (mixed) launch_buckets(L, c->t32, true, c->bk, st);
+  mark(6);
   if (c->cfg.energy_correction)
     launch_correction(L, c->r, c->x, c->phi, c->vr, c->vt, c->r_old, c->cc, true, c->err, st);
+  mark(7);
   launch_step_end(L, c->step, st);
-}
-
-// The same kernels as record_step, with an event after each stage.
-void record_step_profiled(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev) {
-  const SegLayout& L = c->L;
-  const bool mixed = c->cfg.precision == 1;
-  cudaEventRecord(ev[0], st);
-  launch_bins(L, c->r, c->vr, c->vt, c->m, c->nbin, c->pref, st);
-  cudaEventRecord(ev[1], st);
-  launch_relax(L, c->vr, c->vt, c->m, c->id, c->nbin, c->step, st);
-  cudaEventRecord(ev[2], st);
-  launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
-               mixed ? c->t32 : nullptr, c->vr, c->vt, c->m, c->id, c->step, c->keys, c->pay,
-               nullptr, c->cfg.orbit_block, st);
-  cudaEventRecord(ev[3], st);
-  sort_segments(L, c->W, c->keys, c->vals, 0, 8, true, c->err, st);
-  launch_tiefix(L, c->keys, c->vals, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)),
-                c->err, st);
-  cudaEventRecord(ev[4], st);
-  launch_gather(L, c->keys, c->vals, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old,
-                c->cc, st);
-  cudaEventRecord(ev[5], st);
-  launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
-                   mixed ? c->t32 : nullptr, nullptr, true, st);
-  cudaEventRecord(ev[6], st);
-  if (c->cfg.energy_correction)
-    launch_correction(L, c->r, c->x, c->phi, c->vr, c->vt, c->r_old, c->cc, true, c->err, st);
-  cudaEventRecord(ev[7], st);
-  launch_step_end(L, c->step, st);
-  cudaEventRecord(ev[8], st);
+  mark(8);
 }
 
 int count_step_kernels(const cmc_ctx* c) {
   // bins, relax, orbit, upsweep, hist scan, 8 passes, tie fix, gather,
-  // tile sums, potential, [correction], step end
-  return 3 + 2 + 8 + 1 + 1 + 2 + (c->cfg.energy_correction ? 1 : 0) + 1;
+  // tile sums, potential, [2 bucket-index kernels], [correction], step end
+  return 3 + 2 + 8 + 1 + 1 + 2 + (c->cfg.precision == 1 ? 2 : 0) +
+         (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 
 void free_ctx(cmc_ctx* c) {
@@ -198,6 +185,7 @@ void free_ctx(cmc_ctx* c) {
   dfree(c->err, st);
   dfree(c->step, st);
   free_sort(c->W, st);
+  free_buckets(c->bk, st);
   free_layout(c->L, st);
   cudaStreamSynchronize(st);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -321,6 +309,7 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   CMC_ALLOC(c->step, 1);
 #undef CMC_ALLOC
   if (!e) e = alloc_sort(c->W, L, 8, st);
+  if (!e && cfg.precision == 1) e = alloc_buckets(c->bk, L, st);
   if (e) { cmc_status s = cuda_fail(nullptr, e, "cmc_init: allocation"); free_ctx(c); return s; }
   sort_prepare();
   cmc_status s = load_state(c, r, vr, vt, m, id, ptr_kind, false, 0);
@@ -366,7 +355,7 @@ cmc_status cmc_step_profiled(cmc_ctx* c, int32_t n_steps, double* stage_ms) {
   for (int i = 0; i < CMC_NSTAGES; ++i) stage_ms[i] = 0.0;
   std::vector<cudaEvent_t> ev((size_t)(CMC_NSTAGES + 1) * (n_steps > 0 ? n_steps : 1));
   for (auto& e : ev) cudaEventCreate(&e);
-  for (int32_t i = 0; i < n_steps; ++i) record_step_profiled(c, c->stream, &ev[(size_t)i * (CMC_NSTAGES + 1)]);
+  for (int32_t i = 0; i < n_steps; ++i) record_step(c, c->stream, &ev[(size_t)i * (CMC_NSTAGES + 1)]);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (!e) {
     for (int32_t i = 0; i < n_steps; ++i)
@@ -664,10 +653,17 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
   if (!e) {
     launch_recip(n, r, x, st);
     launch_make_t32(n, x, phi, t32, st);
+    BucketWork bk;
+    if (precision == 1) {
+      e = alloc_buckets(bk, S.L, st);
+      if (!e) launch_buckets(S.L, t32, false, bk, st);
+    }
     OrbitStageOut d;
     d.phi_new = phi_new; d.rmin = rmin; d.rmax = rmax; d.F = F; d.code = code;
-    launch_orbit(S.L, precision, max_trials, r, x, phi, t32, vr, vt, mm, id, dstep, keys, pay,
-                 &d, 0, st);
+    if (!e)
+      launch_orbit(S.L, precision, max_trials, r, x, phi, t32, vr, vt, mm, id, dstep, keys,
+                   pay, &d, 0, bk.args(), st);
+    free_buckets(bk, st);
     launch_unpack_orbit(n, keys, pay, r_new, vr_new, vt_new, st);
     e = cudaGetLastError();
   }

@@ -132,11 +132,38 @@ struct OrbitStageOut {   // optional per-star outputs of the orbit stage
   int32_t* trials = nullptr;
 };
 
+// Radius-bucket index of the float table of every segment (mixed mode):
+// start[off[c] + b] = first node of segment c whose bucket is >= b.
+struct BucketArgs {
+  const int* start = nullptr;
+  const int64_t* off = nullptr;
+  const uint32_t* base = nullptr;
+  const int4* prm = nullptr;  // shift, bucket count, first and last indexed node
+};
+
+struct BucketWork {
+  int* start = nullptr;
+  int64_t* off = nullptr;
+  uint32_t* base = nullptr;
+  int4* prm = nullptr;
+  BucketArgs args() const {
+    BucketArgs a;
+    a.start = start; a.off = off; a.base = base; a.prm = prm;
+    return a;
+  }
+};
+
+cudaError_t alloc_buckets(BucketWork& B, const SegLayout& L, cudaStream_t st);
+void free_buckets(BucketWork& B, cudaStream_t st);
+// build the index from t32 over the bound stars (nb - esc_step when nb_sub)
+void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWork& B,
+                    cudaStream_t st);
+
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
                   const double* x, const double* phi, const float2* t32, const double* vr,
                   const double* vt, const double* m, const uint32_t* id, const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
-                  cudaStream_t st);
+                  const BucketArgs& ba, cudaStream_t st);
 
 void launch_step_end(const SegLayout& L, uint32_t* step, cudaStream_t st);
 

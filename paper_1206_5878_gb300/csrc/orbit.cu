@@ -99,45 +99,6 @@ struct Table32 {
   int64_t nb;
 };
 
-__device__ __forceinline__ float Q_node32(const Table32& T, float E, float J, int64_t i) {
-  const float2 e = __ldg(T.t + i);
-  const float L = J * e.x;
-  return 2.0f * (E - e.y) - L * L;
-}
-
-// largest i with 1/r_i >= xq (FP32), else -1
-__device__ __forceinline__ int64_t shell_of32(const Table32& T, float xq) {
-  int64_t lo = -1, hi = T.nb;
-  while (hi - lo > 1) {
-    int64_t mid = lo + ((hi - lo) >> 1);
-    if (__ldg(&T.t[mid].x) >= xq) lo = mid; else hi = mid;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ float phi_in_shell32(const Table32& T, int64_t i, float xq) {
-  if (i < 0) return __ldg(&T.t[0].y);
-  const float2 a = __ldg(T.t + i);
-  float2 b = make_float2(0.0f, 0.0f);
-  if (i + 1 < T.nb) b = __ldg(T.t + i + 1);
-  const float den = a.x - b.x;
-  if (!(den > 0.0f)) return a.y;
-  return a.y + ((a.x - xq) / den) * (b.y - a.y);
-}
-
-__device__ __forceinline__ float g32(const Table32& T, float E, float J, float c0, float c1,
-                                     float s, int64_t& shell) {
-  const float rs = c0 + c1 * (s * (3.0f - s * s));
-  const float drds = (3.0f * c1) * (1.0f - s * s);
-  const float xq = 1.0f / rs;
-  shell = shell_of32(T, xq);
-  const float ph = phi_in_shell32(T, shell, xq);
-  const float L = J * xq;
-  const float Q = 2.0f * (E - ph) - L * L;
-  if (!(Q > 0.0f)) return 0.0f;
-  return drds / sqrtf(Q);
-}
-
 // move an approximate shell index to the exact FP64 one: largest i with
 // r_i <= q (bounded walk, then plain bisection)
 __device__ __forceinline__ int64_t fix_shell64(const Table64& T, int64_t i, double q) {
@@ -176,6 +137,138 @@ __device__ __forceinline__ int64_t verify_rmin(const Table64& T, const Star& s, 
   return bisect_rmin64(T, s);
 }
 
+// sample points of the bound F: s_j = -1 + (j + 1/2)/10.5 (IEEE double,
+// evaluated at compile time), and their float roundings
+#define CMC_SJ(j) (-1.0 + ((double)(j) + 0.5) / 10.5)
+#define CMC_SJ21(f) f(0), f(1), f(2), f(3), f(4), f(5), f(6), f(7), f(8), f(9), f(10), \
+    f(11), f(12), f(13), f(14), f(15), f(16), f(17), f(18), f(19), f(20)
+#define CMC_SJF(j) ((float)CMC_SJ(j))
+__constant__ double c_s64[21] = {CMC_SJ21(CMC_SJ)};
+__constant__ float c_s32[21] = {CMC_SJ21(CMC_SJF)};
+
+// ---- FP32 searches run in lockstep: K independent searches per thread,
+// each round issues K independent loads before any of them is needed.
+__device__ __forceinline__ int search_rounds(int nb) { return 32 - __clz(nb); }
+
+// largest i with 1/r_i >= xq[q] (i.e. r_i <= 1/xq), else -1, for K queries
+template <int K>
+__device__ __forceinline__ void shells32(const float2* __restrict__ t, int nb,
+                                         const float (&xq)[K], int (&out)[K]) {
+  int lo[K], hi[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) { lo[q] = -1; hi[q] = nb; }
+  const int rounds = search_rounds(nb);
+  for (int it = 0; it < rounds; ++it) {
+    float v[K];
+    int mid[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      mid[q] = hi[q] - lo[q] > 1 ? lo[q] + ((hi[q] - lo[q]) >> 1) : 0;
+      v[q] = __ldg(&t[mid[q]].x);
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+      if (hi[q] - lo[q] > 1) {
+        if (v[q] >= xq[q]) lo[q] = mid[q]; else hi[q] = mid[q];
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) out[q] = lo[q];
+}
+
+// Radius-bucket index of one segment's float table.  It covers the nodes
+// lo..hi, all but the sparse 1/1024 at each end (where a bucket resolution
+// fine enough for the core would leave long runs of empty buckets).
+// Bucket of a key x > 0: (base - bits(x)) >> shift, base = bits(x_lo).
+// Positive floats order like their bit patterns, so buckets are
+// non-decreasing along the (non-increasing) keys.  start[b] is the first
+// node whose bucket is >= b, start[nbk] = nb.  A node before start[b] has a
+// key above any query of bucket b, a node from start[b+1] on (within lo..hi)
+// a key below it, so the answer of a query of bucket b lies in
+// [start[b] - 1, start[b+1] - 1]; queries above x_lo search [-1, lo),
+// queries below x_hi search [hi, nb).
+struct Buckets {
+  const int* start;
+  uint32_t base;
+  int shift, nbk, lo, hi;
+};
+
+// largest i with x_i >= xq[q], else -1, for K queries (lockstep)
+template <int K>
+__device__ __forceinline__ void shells32_bk(const float2* __restrict__ t, int nb,
+                                            const Buckets& B, const float (&xq)[K],
+                                            int (&out)[K]) {
+  int lo[K], hi[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const long long d = (long long)B.base - (long long)__float_as_uint(xq[q]);
+    if (d < 0) { lo[q] = -1; hi[q] = B.lo; continue; }           // inner tail
+    const long long b = d >> B.shift;
+    if (b >= B.nbk) { lo[q] = B.hi; hi[q] = nb; continue; }      // outer tail
+    lo[q] = __ldg(B.start + b) - 1;
+    hi[q] = __ldg(B.start + b + 1);
+  }
+  bool more = true;
+  while (more) {
+    more = false;
+    float v[K];
+    int mid[K];
+#pragma unroll
+    for (int q = 0; q < K; ++q) {
+      mid[q] = hi[q] - lo[q] > 1 ? lo[q] + ((hi[q] - lo[q]) >> 1) : 0;
+      v[q] = __ldg(&t[mid[q]].x);
+    }
+#pragma unroll
+    for (int q = 0; q < K; ++q)
+      if (hi[q] - lo[q] > 1) {
+        if (v[q] >= xq[q]) lo[q] = mid[q]; else hi[q] = mid[q];
+        more |= hi[q] - lo[q] > 1;
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) out[q] = lo[q];
+}
+
+// g(s) of K points in FP32 (Eq. 6 on the float table)
+template <int K>
+__device__ __forceinline__ void g32_k(const float2* __restrict__ t, int nb, const Buckets& B,
+                                      float E, float J, float c0, float c1,
+                                      const float (&s)[K], float (&g)[K], int (&sh)[K]) {
+  float xq[K], drds[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const float rs = c0 + c1 * (s[q] * (3.0f - s[q] * s[q]));
+    drds[q] = (3.0f * c1) * (1.0f - s[q] * s[q]);
+    xq[q] = 1.0f / rs;
+  }
+  shells32_bk<K>(t, nb, B, xq, sh);
+  float2 a[K], b[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    const int i = sh[q] < 0 ? 0 : sh[q];
+    a[q] = __ldg(t + i);
+    b[q] = (i + 1 < nb) ? __ldg(t + i + 1) : make_float2(0.0f, 0.0f);
+  }
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    float ph;
+    if (sh[q] < 0) {
+      ph = a[q].y;
+    } else {
+      const float den = a[q].x - b[q].x;
+      ph = den > 0.0f ? a[q].y + ((a[q].x - xq[q]) / den) * (b[q].y - a[q].y) : a[q].y;
+    }
+    const float L = J * xq[q];
+    const float Q = 2.0f * (E - ph) - L * L;
+    g[q] = Q > 0.0f ? drds[q] / sqrtf(Q) : 0.0f;
+  }
+}
+
+// (2k + 1) 2^-24 from the top 23 bits of a word: exact in float, in (0, 1)
+__device__ __forceinline__ float u01f(uint32_t hi) {
+  return (float)(2u * (hi >> 9) + 1u) * 0x1p-24f;
+}
+
 template <int kPrec>
 __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const double* r,
                                                const double* x, const double* phi,
@@ -183,7 +276,7 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
                                                const double* vt, const double* m,
                                                const uint32_t* id, const uint32_t* step_p,
                                                uint64_t* keys, Payload* pay, int64_t* esc,
-                                               OrbitStageOut dbg, int64_t n) {
+                                               OrbitStageOut dbg, BucketArgs BA, int64_t n) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int c = seg_find(S.off, S.n_seg, p);
@@ -222,23 +315,38 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
   } else {
     int64_t jmax, jmin;
     Table32 T32{t32 + sb, nbc};
+    Buckets BK;
+    if (kPrec == 1) {
+      const int4 pr = BA.prm[c];
+      BK.start = BA.start + BA.off[c];
+      BK.base = BA.base[c];
+      BK.shift = pr.x;
+      BK.nbk = pr.y;
+      BK.lo = pr.z;
+      BK.hi = pr.w;
+    }
     const float E32 = (float)s.E, J32 = (float)s.J;
     if (kPrec == 0) {
       jmax = bisect_rmax64(T, s);
       jmin = bisect_rmin64(T, s);
     } else {
-      int64_t lo = k, hi = nbc;
-      while (hi - lo > 1) {
-        int64_t mid = lo + ((hi - lo) >> 1);
-        if (Q_node32(T32, E32, J32, mid) < 0.0f) hi = mid; else lo = mid;
+      // both bisections in lockstep (r_max over [k, nb], r_min over [-1, k])
+      const int nb32 = (int)nbc, k32 = (int)k;
+      int lo1 = k32, hi1 = nb32, lo2 = -1, hi2 = k32;
+      const int rounds = search_rounds(nb32);
+      for (int it = 0; it < rounds; ++it) {
+        const bool a1 = hi1 - lo1 > 1, a2 = hi2 - lo2 > 1;
+        const int m1 = a1 ? lo1 + ((hi1 - lo1) >> 1) : k32;
+        const int m2 = a2 ? lo2 + ((hi2 - lo2) >> 1) : k32;
+        const float2 e1 = __ldg(T32.t + m1), e2 = __ldg(T32.t + m2);
+        const float L1 = J32 * e1.x, L2 = J32 * e2.x;
+        const bool n1 = 2.0f * (E32 - e1.y) - L1 * L1 < 0.0f;
+        const bool n2 = 2.0f * (E32 - e2.y) - L2 * L2 < 0.0f;
+        if (a1) { if (n1) hi1 = m1; else lo1 = m1; }
+        if (a2) { if (n2) lo2 = m2; else hi2 = m2; }
       }
-      jmax = verify_rmax(T, s, lo);
-      lo = -1; hi = k;
-      while (hi - lo > 1) {
-        int64_t mid = lo + ((hi - lo) >> 1);
-        if (Q_node32(T32, E32, J32, mid) < 0.0f) lo = mid; else hi = mid;
-      }
-      jmin = verify_rmin(T, s, lo);
+      jmax = verify_rmax(T, s, lo1);
+      jmin = verify_rmin(T, s, lo2);
     }
     rmax = shell_root64(T, s, jmax, true);
     rmin = jmin < 0 ? central_root64(T, s) : shell_root64(T, s, jmin, false);
@@ -247,8 +355,8 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
     if (kPrec == 0) {
       double gmax = 0.0;
       for (int j = 0; j <= 20; ++j) {
-        double sj = -1.0 + ((double)j + 0.5) / 10.5, rs, ph, Q;
-        double g = g64(T, s, c0, c1, sj, rs, ph, Q);
+        double rs, ph, Q;
+        double g = g64(T, s, c0, c1, c_s64[j], rs, ph, Q);
         if (g > gmax) gmax = g;
       }
       F = 1.2 * gmax;
@@ -280,12 +388,18 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
       }
     } else {
       const float c0f = (float)c0, c1f = (float)c1;
+      const int nb32 = (int)nbc;
       float gmax = 0.0f;
-      for (int j = 0; j <= 20; ++j) {
-        const float sj = (float)(-1.0 + ((double)j + 0.5) / 10.5);
-        int64_t sh;
-        const float g = g32(T32, E32, J32, c0f, c1f, sj, sh);
-        if (g > gmax) gmax = g;
+      // the 21 samples of g in three groups of 7 independent searches
+#pragma unroll 1
+      for (int j0 = 0; j0 < 21; j0 += 7) {
+        float sj[7], g[7];
+        int sh[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) sj[q] = c_s32[j0 + q];
+        g32_k<7>(T32.t, nb32, BK, E32, J32, c0f, c1f, sj, g, sh);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) gmax = g[q] > gmax ? g[q] : gmax;
       }
       const float F32 = 1.2f * gmax;
       F = (double)F32;
@@ -293,17 +407,25 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
         code = 2;
       } else {
         code = 3;
-        for (int t = 0; t < max_trials; ++t) {
-          U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
-          const double X = u01(w.x, w.y), Xp = u01(w.z, w.w);
-          const double sv = 2.0 * X - 1.0;
-          int64_t sh;
-          const float g = g32(T32, E32, J32, c0f, c1f, (float)sv, sh);
-          if (g > F32) ++viol;
-          if (F32 * (float)Xp < g) {
-            // recompute the accepted point in FP64
+        // trials in pairs: both are drawn and tested, the first accepted wins
+        for (int t = 0; t < max_trials && code == 3; t += 2) {
+          U4 w[2];
+          float sv32[2], xp32[2], g[2];
+          int sh[2];
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            w[q] = philox(idk, step, kTagRej, (uint32_t)(t + q), seed);
+            sv32[q] = 2.0f * u01f(w[q].y) - 1.0f;
+            xp32[q] = u01f(w[q].w);
+          }
+          g32_k<2>(T32.t, nb32, BK, E32, J32, c0f, c1f, sv32, g, sh);
+          for (int q = 0; q < 2 && t + q < max_trials; ++q) {
+            if (g[q] > F32) ++viol;
+            if (!(F32 * xp32[q] < g[q])) continue;
+            // recompute the accepted point in FP64 from the full 53-bit X
+            const double sv = 2.0 * u01(w[q].x, w[q].y) - 1.0;
             const double rs = c0 + c1 * (sv * (3.0 - sv * sv));
-            const int64_t i64 = fix_shell64(T, sh, rs);
+            const int64_t i64 = fix_shell64(T, sh[q], rs);
             const double ph = phi_in_shell(T, i64, rs);
             const double L = s.J / rs;
             double Q = 2.0 * (s.E - ph) - L * L;
@@ -316,7 +438,7 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
             P.c = __ldg(T.phi + k) - ph;
             ph_new = ph;
             code = 0;
-            trials = t + 1;
+            trials = t + q + 1;
             break;
           }
         }
@@ -351,24 +473,103 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
   if (dbg.trials) dbg.trials[p] = trials;
 }
 
+// per segment: the indexed node range lo..hi, base = bits(x_lo), the
+// smallest shift that fits the key range into the segment's capacity, and
+// the bucket count
+__global__ void k_bucket_params(Seg S, const int64_t* esc, bool sub, const float2* t32,
+                                BucketArgs B, uint32_t* base, int4* prm) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= S.n_seg) return;
+  int64_t nb = S.nb[c];
+  if (sub) nb -= esc[c];
+  if (nb <= 0) { base[c] = 0; prm[c] = make_int4(0, 0, 0, -1); return; }
+  const int64_t sb = S.off[c];
+  const int tail = nb >= 4096 ? (int)(nb >> 10) : 0;
+  const int lo = tail, hi = (int)nb - 1 - tail;
+  const uint32_t b0 = __float_as_uint(t32[sb + lo].x);
+  const uint32_t b1 = __float_as_uint(t32[sb + hi].x);
+  const uint32_t span = b0 >= b1 ? b0 - b1 : 0u;
+  const int64_t cap = B.off[c + 1] - B.off[c] - 1;  // buckets that fit
+  int sh = 0;
+  while ((int64_t)(span >> sh) + 1 > cap) ++sh;
+  base[c] = b0;
+  prm[c] = make_int4(sh, (int)((span >> sh) + 1), lo, hi);
+}
+
+// one thread per indexed star: it writes start[b] for the buckets between
+// its predecessor's bucket and its own; the last one closes the table
+__global__ void k_bucket_build(Seg S, const int64_t* esc, bool sub, const float2* t32,
+                               BucketArgs B, int* start, int64_t n) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int c = seg_find(S.off, S.n_seg, p);
+  int64_t nb = S.nb[c];
+  if (sub) nb -= esc[c];
+  const int4 pr = B.prm[c];
+  const int64_t sb = S.off[c], k = p - sb;
+  if (k < pr.z || k > pr.w) return;
+  const uint32_t base = B.base[c];
+  const int sh = pr.x, nbk = pr.y;
+  int* st = start + B.off[c];
+  const long long bk = (long long)((base - __float_as_uint(t32[p].x)) >> sh);
+  const long long bp =
+      k == pr.z ? -1ll : (long long)((base - __float_as_uint(t32[p - 1].x)) >> sh);
+  for (long long b = bp + 1; b <= bk && b < nbk; ++b) st[b] = (int)k;
+  if (k == pr.w)
+    for (long long b = bk + 1; b <= nbk; ++b) st[b] = (int)nb;
+}
+
 }  // namespace
+
+cudaError_t alloc_buckets(BucketWork& B, const SegLayout& L, cudaStream_t st) {
+  std::vector<int64_t> off(L.n_seg + 1, 0);
+  for (int c = 0; c < L.n_seg; ++c) {
+    const int64_t nc = L.h_off[c + 1] - L.h_off[c];
+    off[c + 1] = off[c] + nc / 2 + 2;  // about two stars per bucket
+  }
+  cudaError_t e;
+  if ((e = cudaMallocAsync((void**)&B.start, sizeof(int) * off[L.n_seg], st))) return e;
+  if ((e = cudaMallocAsync((void**)&B.off, sizeof(int64_t) * (L.n_seg + 1), st))) return e;
+  if ((e = cudaMallocAsync((void**)&B.base, sizeof(uint32_t) * L.n_seg, st))) return e;
+  if ((e = cudaMallocAsync((void**)&B.prm, sizeof(int4) * L.n_seg, st))) return e;
+  e = cudaMemcpyAsync(B.off, off.data(), sizeof(int64_t) * (L.n_seg + 1),
+                      cudaMemcpyHostToDevice, st);
+  if (e) return e;
+  return cudaStreamSynchronize(st);  // off lives on this stack
+}
+
+void free_buckets(BucketWork& B, cudaStream_t st) {
+  void* ps[] = {B.start, B.off, B.base, B.prm};
+  for (void* p : ps)
+    if (p) cudaFreeAsync(p, st);
+  B = BucketWork();
+}
+
+void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWork& B,
+                    cudaStream_t st) {
+  if (!L.n) return;
+  k_bucket_params<<<(unsigned)((L.n_seg + 127) / 128), 128, 0, st>>>(
+      L.dev(), L.esc_step, nb_sub, t32, B.args(), B.base, B.prm);
+  k_bucket_build<<<(unsigned)((L.n + 255) / 256), 256, 0, st>>>(L.dev(), L.esc_step, nb_sub,
+                                                               t32, B.args(), B.start, L.n);
+}
 
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
                   const double* x, const double* phi, const float2* t32, const double* vr,
                   const double* vt, const double* m, const uint32_t* id, const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
-                  cudaStream_t st) {
+                  const BucketArgs& ba, cudaStream_t st) {
   if (!L.n) return;
   OrbitStageOut d;
   if (dbg) d = *dbg;
-  if (block <= 0) block = 128;
+  if (block <= 0) block = 64;
   const unsigned grid = (unsigned)((L.n + block - 1) / block);
   if (precision == 1)
     k_orbit<1><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, vr, vt, m, id, step,
-                                       keys, pay, L.esc_step, d, L.n);
+                                       keys, pay, L.esc_step, d, ba, L.n);
   else
     k_orbit<0><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, vr, vt, m, id, step,
-                                       keys, pay, L.esc_step, d, L.n);
+                                       keys, pay, L.esc_step, d, ba, L.n);
 }
 
 }  // namespace cmc
