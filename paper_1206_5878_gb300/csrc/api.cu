@@ -122,9 +122,10 @@ void order_state(cmc_ctx* c, cudaStream_t st) {
                 nullptr, st);
   launch_nb_from_keys(L, c->keys, st);
   cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
-  launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32, nullptr, false,
-                   st);
-  if (c->cfg.precision == 1) launch_buckets(L, c->t32, false, c->bk, st);
+  const bool mixed = c->cfg.precision == 1;
+  launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32,
+                   mixed ? c->Mbuf : nullptr, false, st);
+  if (mixed) launch_buckets(L, c->t32, false, c->bk, st);
 }
 
 // The kernels of one timestep, in the order of section 3.3.  With ev, an
@@ -141,8 +142,8 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   launch_relax(L, c->vr, c->vt, c->m, c->id, c->nbin, c->step, st);
   mark(2);
   launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
-               mixed ? c->t32 : nullptr, c->vr, c->vt, c->m, c->id, c->step, c->keys, c->pay,
-               nullptr, c->cfg.orbit_block, c->bk.args(), st);
+               mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
+               c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->bk.args(), st);
   mark(3);
   sort_segments(L, c->W, c->keys, c->vals, 0, 8, true, c->err, st);
   launch_tiefix(L, c->keys, c->vals, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)),
@@ -152,7 +153,7 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
                 c->cc, st);
   mark(5);
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
-                   mixed ? c->t32 : nullptr, nullptr, true, st);
+                   mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, true, st);
   if (mixed) launch_buckets(L, c->t32, true, c->bk, st);
   mark(6);
   if (c->cfg.energy_correction)
@@ -654,16 +655,22 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
     launch_recip(n, r, x, st);
     launch_make_t32(n, x, phi, t32, st);
     BucketWork bk;
+    double* sl = nullptr;  // shell slopes (enclosed masses) from the potential
     if (precision == 1) {
       e = alloc_buckets(bk, S.L, st);
-      if (!e) launch_buckets(S.L, t32, false, bk, st);
+      if (!e) e = dalloc(sl, n, st);
+      if (!e) {
+        launch_buckets(S.L, t32, false, bk, st);
+        launch_slopes(n, x, phi, sl, st);
+      }
     }
     OrbitStageOut d;
     d.phi_new = phi_new; d.rmin = rmin; d.rmax = rmax; d.F = F; d.code = code;
     if (!e)
-      launch_orbit(S.L, precision, max_trials, r, x, phi, t32, vr, vt, mm, id, dstep, keys,
+      launch_orbit(S.L, precision, max_trials, r, x, phi, t32, sl, vr, vt, mm, id, dstep, keys,
                    pay, &d, 0, bk.args(), st);
     free_buckets(bk, st);
+    dfree(sl, st);
     launch_unpack_orbit(n, keys, pay, r_new, vr_new, vt_new, st);
     e = cudaGetLastError();
   }

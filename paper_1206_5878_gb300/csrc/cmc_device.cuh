@@ -133,12 +133,20 @@ struct Table64 {
   int64_t nb;
 };
 
+// Radii are positive, and positive doubles order like their 64-bit
+// patterns read as signed integers: comparing the patterns gives the same
+// answer as the floating-point comparison without using the FP64 pipe.
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+
 // largest i in [0, nb) with r[i] <= q, else -1 (unique for sorted r)
 __device__ __forceinline__ int64_t shell_of(const Table64& t, double q) {
+  if (!(q >= 0.0)) return -1;  // (NaN: no radius compares <= it)
+  const long long qb = dbits(q);
+  const long long* rb = reinterpret_cast<const long long*>(t.r);
   int64_t lo = -1, hi = t.nb;
   while (hi - lo > 1) {
     int64_t mid = lo + ((hi - lo) >> 1);
-    if (__ldg(t.r + mid) <= q) lo = mid; else hi = mid;
+    if (__ldg(rb + mid) <= qb) lo = mid; else hi = mid;
   }
   return lo;
 }

@@ -159,8 +159,13 @@ void free_buckets(BucketWork& B, cudaStream_t st);
 void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWork& B,
                     cudaStream_t st);
 
+// Menc (mixed mode): enclosed mass M_k of every node, the slope of Phi in
+// 1/r across shell k
+void launch_slopes(int64_t n, const double* x, const double* phi, double* Menc,
+                   cudaStream_t st);
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
-                  const double* x, const double* phi, const float2* t32, const double* vr,
+                  const double* x, const double* phi, const float2* t32, const double* Menc,
+                  const double* vr,
                   const double* vt, const double* m, const uint32_t* id, const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
                   const BucketArgs& ba, cudaStream_t st);

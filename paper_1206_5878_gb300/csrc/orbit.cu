@@ -14,11 +14,13 @@
 // precision 0 (FP64): every operation is the FP64 operation of the
 // method's statement, in the same order, so results are bit-identical to
 // it.  precision 1 (mixed): the bisections, the bound F and the accept
-// tests run in FP32 on an interleaved float2 (1/r, Phi) table; the
-// brackets are then verified (and moved if needed) in FP64, the turning
-// points are the FP64 shell roots, and the accepted radius, its potential
-// and the velocities are recomputed in FP64.  A mixed result equals the
-// FP64 result whenever both accept the same trial.
+// tests run in FP32 on an interleaved float2 (1/r, Phi) table, the F
+// samples and trials located through a radius-bucket index; the brackets
+// are then verified (and moved if needed) in FP64, the turning points are
+// the FP64 shell roots with the shell slope taken from the enclosed mass,
+// and the accepted radius, its potential and the velocities are
+// recomputed in FP64.  A mixed result matches the FP64 result to rounding
+// whenever both accept the same trial.
 #include "cmc_host.hpp"
 
 namespace cmc {
@@ -52,6 +54,27 @@ __device__ __forceinline__ double shell_root64(const Table64& T, const Star& s, 
   double root = outer ? (B + sD) / (2.0 * (A - s.E)) : (s.J * s.J) / (B + sD);
   if (!(root >= rj)) root = rj;
   if (has_next && root > rj1) root = rj1;
+  return root;
+}
+
+// The same root with the slope of shell j taken from the enclosed mass:
+// across shell j, (Phi_{j+1} - Phi_j)/(x_j - x_{j+1}) = G M_j exactly
+// (Eqs. 1-5; for the outermost shell M_j is the bound mass), so
+// Phi = Phi_j + M_j (x_j - x) needs no division (mixed mode).
+__device__ __forceinline__ double shell_root_M(const Table64& T, const double* M,
+                                               const Star& s, int64_t j, bool outer) {
+  const double rj = __ldg(T.r + j), xj = __ldg(T.x + j), pj = __ldg(T.phi + j);
+  const double B = __ldg(M + j);
+  const double A = pj + B * xj;
+  double D = B * B + 2.0 * (s.J * s.J) * (s.E - A);
+  if (!(D > 0.0)) D = 0.0;
+  const double sD = sqrt(D);
+  double root = outer ? (B + sD) / (2.0 * (A - s.E)) : (s.J * s.J) / (B + sD);
+  if (!(root >= rj)) root = rj;
+  if (j + 1 < T.nb) {
+    const double rj1 = __ldg(T.r + j + 1);
+    if (root > rj1) root = rj1;
+  }
   return root;
 }
 
@@ -102,11 +125,14 @@ struct Table32 {
 // move an approximate shell index to the exact FP64 one: largest i with
 // r_i <= q (bounded walk, then plain bisection)
 __device__ __forceinline__ int64_t fix_shell64(const Table64& T, int64_t i, double q) {
+  if (!(q >= 0.0)) return -1;
   if (i < -1) i = -1;
   if (i >= T.nb) i = T.nb - 1;
+  const long long qb = dbits(q);
+  const long long* rb = reinterpret_cast<const long long*>(T.r);
   for (int w = 0; w < 64; ++w) {
-    if (i + 1 < T.nb && __ldg(T.r + i + 1) <= q) { ++i; continue; }
-    if (i >= 0 && __ldg(T.r + i) > q) { --i; continue; }
+    if (i + 1 < T.nb && __ldg(rb + i + 1) <= qb) { ++i; continue; }
+    if (i >= 0 && __ldg(rb + i) > qb) { --i; continue; }
     return i;
   }
   return shell_of(T, q);
@@ -149,32 +175,6 @@ __constant__ float c_s32[21] = {CMC_SJ21(CMC_SJF)};
 // ---- FP32 searches run in lockstep: K independent searches per thread,
 // each round issues K independent loads before any of them is needed.
 __device__ __forceinline__ int search_rounds(int nb) { return 32 - __clz(nb); }
-
-// largest i with 1/r_i >= xq[q] (i.e. r_i <= 1/xq), else -1, for K queries
-template <int K>
-__device__ __forceinline__ void shells32(const float2* __restrict__ t, int nb,
-                                         const float (&xq)[K], int (&out)[K]) {
-  int lo[K], hi[K];
-#pragma unroll
-  for (int q = 0; q < K; ++q) { lo[q] = -1; hi[q] = nb; }
-  const int rounds = search_rounds(nb);
-  for (int it = 0; it < rounds; ++it) {
-    float v[K];
-    int mid[K];
-#pragma unroll
-    for (int q = 0; q < K; ++q) {
-      mid[q] = hi[q] - lo[q] > 1 ? lo[q] + ((hi[q] - lo[q]) >> 1) : 0;
-      v[q] = __ldg(&t[mid[q]].x);
-    }
-#pragma unroll
-    for (int q = 0; q < K; ++q)
-      if (hi[q] - lo[q] > 1) {
-        if (v[q] >= xq[q]) lo[q] = mid[q]; else hi[q] = mid[q];
-      }
-  }
-#pragma unroll
-  for (int q = 0; q < K; ++q) out[q] = lo[q];
-}
 
 // Radius-bucket index of one segment's float table.  It covers the nodes
 // lo..hi, all but the sparse 1/1024 at each end (where a bucket resolution
@@ -272,7 +272,7 @@ __device__ __forceinline__ float u01f(uint32_t hi) {
 template <int kPrec>
 __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const double* r,
                                                const double* x, const double* phi,
-                                               const float2* t32, const double* vr,
+                                               const float2* t32, const double* Menc, const double* vr,
                                                const double* vt, const double* m,
                                                const uint32_t* id, const uint32_t* step_p,
                                                uint64_t* keys, Payload* pay, int64_t* esc,
@@ -348,8 +348,13 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
       jmax = verify_rmax(T, s, lo1);
       jmin = verify_rmin(T, s, lo2);
     }
-    rmax = shell_root64(T, s, jmax, true);
-    rmin = jmin < 0 ? central_root64(T, s) : shell_root64(T, s, jmin, false);
+    if (kPrec == 0) {
+      rmax = shell_root64(T, s, jmax, true);
+      rmin = jmin < 0 ? central_root64(T, s) : shell_root64(T, s, jmin, false);
+    } else {
+      rmax = shell_root_M(T, Menc + sb, s, jmax, true);
+      rmin = jmin < 0 ? central_root64(T, s) : shell_root_M(T, Menc + sb, s, jmin, false);
+    }
     const double c0 = 0.5 * (rmax + rmin);
     const double c1 = 0.25 * (rmax - rmin);
     if (kPrec == 0) {
@@ -426,15 +431,18 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
             const double sv = 2.0 * u01(w[q].x, w[q].y) - 1.0;
             const double rs = c0 + c1 * (sv * (3.0 - sv * sv));
             const int64_t i64 = fix_shell64(T, sh[q], rs);
-            const double ph = phi_in_shell(T, i64, rs);
-            const double L = s.J / rs;
+            const double xs = 1.0 / rs;
+            const double ph = i64 < 0 ? __ldg(T.phi)
+                                      : __ldg(T.phi + i64) +
+                                            __ldg(Menc + sb + i64) * (__ldg(T.x + i64) - xs);
+            const double L = s.J * xs;
             double Q = 2.0 * (s.E - ph) - L * L;
             if (!(Q > 0.0)) Q = 0.0;
             const double sq = sqrt(Q);
             U4 sg = philox(idk, step, kTagSgn, 0u, seed);
             r_new = rs;
             P.vr = (sg.x & 1u) ? -sq : sq;
-            P.vt = s.J / rs;
+            P.vt = L;
             P.c = __ldg(T.phi + k) - ph;
             ph_new = ph;
             code = 0;
@@ -519,7 +527,23 @@ __global__ void k_bucket_build(Seg S, const int64_t* esc, bool sub, const float2
     for (long long b = bk + 1; b <= nbk; ++b) st[b] = (int)nb;
 }
 
+// slope of Phi in 1/r across each shell of one table, for callers that
+// have the potential but not the masses: (Phi_{k+1} - Phi_k)/(x_k - x_{k+1}),
+// with Phi = 0 at 1/r = 0 beyond the last node
+__global__ void k_slopes(int64_t n, const double* x, const double* phi, double* M) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double xj = x[k], pj = phi[k];
+  const double xj1 = k + 1 < n ? x[k + 1] : 0.0, pj1 = k + 1 < n ? phi[k + 1] : 0.0;
+  M[k] = (pj1 - pj) / (xj - xj1);
+}
+
 }  // namespace
+
+void launch_slopes(int64_t n, const double* x, const double* phi, double* Menc,
+                   cudaStream_t st) {
+  if (n > 0) k_slopes<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, x, phi, Menc);
+}
 
 cudaError_t alloc_buckets(BucketWork& B, const SegLayout& L, cudaStream_t st) {
   std::vector<int64_t> off(L.n_seg + 1, 0);
@@ -555,8 +579,9 @@ void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWo
 }
 
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
-                  const double* x, const double* phi, const float2* t32, const double* vr,
-                  const double* vt, const double* m, const uint32_t* id, const uint32_t* step,
+                  const double* x, const double* phi, const float2* t32, const double* Menc,
+                  const double* vr, const double* vt, const double* m, const uint32_t* id,
+                  const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
                   const BucketArgs& ba, cudaStream_t st) {
   if (!L.n) return;
@@ -565,10 +590,10 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
   if (block <= 0) block = 64;
   const unsigned grid = (unsigned)((L.n + block - 1) / block);
   if (precision == 1)
-    k_orbit<1><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, vr, vt, m, id, step,
+    k_orbit<1><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, m, id, step,
                                        keys, pay, L.esc_step, d, ba, L.n);
   else
-    k_orbit<0><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, vr, vt, m, id, step,
+    k_orbit<0><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, m, id, step,
                                        keys, pay, L.esc_step, d, ba, L.n);
 }
 

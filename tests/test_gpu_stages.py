@@ -140,13 +140,21 @@ def test_orbit_mixed_against_fp64(g, orc, n):
     code = host(out["code"])
     np.testing.assert_array_equal(code, ref["code"])
     ok = code == 0
+    # turning points: FP64 shell roots (the slope of each shell here comes
+    # from the same division as in FP64 mode)
     np.testing.assert_array_equal(host(out["rmin"]), ref["rmin"])
     np.testing.assert_array_equal(host(out["rmax"]), ref["rmax"])
     same = ok & (host(out["r_new"]) == ref["r_new"])
     flips = ok.sum() - same.sum()
     assert flips <= max(3, 1e-3 * ok.sum())
-    for k in ("vr", "vt", "phi_new"):
-        np.testing.assert_array_equal(host(out[k])[same], ref[k][same], err_msg=k)
+    # the accepted orbit is recomputed in FP64 with Phi = Phi_j + M_j (x_j -
+    # 1/r) and v_t = J (1/r): a few roundings away from the FP64 path
+    scale = np.abs(s["phi"][0])
+    a, b = host(out["vr"])[same], ref["vr"][same]
+    assert np.max(np.abs(a * a - b * b)) < 1e-12 * scale
+    for k in ("vt", "phi_new"):
+        a, b = host(out[k])[same], ref[k][same]
+        assert np.max(np.abs(a - b) / np.maximum(np.abs(b), 1e-300)) < 1e-13, k
     # F is a sampled bound: g(s) = (dr/ds)/sqrt(Q) with Q = 2(E - Phi) - L^2
     # cancels in FP32 (E and Phi carry 2^-24 relative error each), so the
     # FP32 samples agree with FP64 to ~1e-5 typically, worse where Q is small
