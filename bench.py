@@ -294,7 +294,8 @@ def run_cmc(args, rank, world, local_rank):
                       "n_stars": n, "precision": args.precision, "seed": args.seed,
                       "parallelism": "replicas" if dist else "single",
                       "l2": "inputs larger than L2 (state %.2f GB)" % (n * 60 / 1e9)},
-           "gpu_launches": kernels, "stages_ms": stages_avg, "roofline": roof,
+           "gpu_launches": kernels, "stages_ms": stages_avg, "tuning": c.tuning(),
+           "roofline": roof,
            "step_hbm_frac": step_frac, "clocks": clocks}
 
     if args.fp64 and prec == 1:

@@ -84,7 +84,10 @@ typedef struct {
     int32_t max_trials;         /* rejection trials per star per step (1000) */
     int32_t energy_correction;  /* 1: apply the section 2.1 step 6 correction */
     int32_t orbit_block;        /* threads per block of the orbit kernel: 0 (auto) or a multiple of 32 up to 256 */
-    int32_t reserved;
+    int32_t autotune;           /* 1: at cmc_init, time the sort shapes (and the
+                                   orbit block size when orbit_block is 0) on
+                                   the real state and keep the fastest; results
+                                   do not depend on the choice (default 1) */
 } cmc_config;
 
 /* Fill cfg with the defaults shown above. */
@@ -166,6 +169,11 @@ enum {
  * CMC_NSTAGES) receives the summed device time of each stage.  Results are
  * identical to cmc_step. */
 cmc_status cmc_step_profiled(cmc_ctx *ctx, int32_t n_steps, double *stage_ms);
+
+/* Kernel shapes in use (chosen by autotune or the configuration): out
+ * (host, 3) = {orbit threads per block, sort keys per thread, sort
+ * multisplit (0: match, 1: ballot)}. */
+cmc_status cmc_get_tuning(const cmc_ctx *ctx, int32_t *out);
 
 /* Number of kernels one cmc_step timestep launches. */
 int32_t cmc_kernels_per_step(const cmc_ctx *ctx);

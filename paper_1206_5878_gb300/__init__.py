@@ -175,6 +175,14 @@ class Cluster:
     def kernels_per_step(self) -> int:
         return int(self.lib.cmc_kernels_per_step(self.ctx))
 
+    def tuning(self) -> dict:
+        """Kernel shapes in use: orbit block size, sort keys per thread and
+        multisplit (match or ballot)."""
+        out = np.zeros(3, dtype=np.int32)
+        check(self.lib.cmc_get_tuning(self.ctx, out.ctypes.data), self.ctx)
+        return {"orbit_block": int(out[0]), "sort_keys_per_thread": int(out[1]),
+                "sort_multisplit": "ballot" if out[2] else "match"}
+
     def set_stream(self, stream):
         self.stream = _stream_ptr(stream)
         check(self.lib.cmc_set_stream(self.ctx, self.stream), self.ctx)

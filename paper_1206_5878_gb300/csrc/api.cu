@@ -230,6 +230,73 @@ cmc_status load_state(cmc_ctx* c, const double* r, const double* vr, const doubl
   return CMC_OK;
 }
 
+// Time the shapes of the sort passes and of the orbit kernel on this state
+// and keep the fastest.  The orbit kernel runs once as a dry run (it writes
+// only keys and payload scratch) to give the sort realistic input; counters
+// it touched are reset.  Results never depend on the shapes.
+cmc_status autotune(cmc_ctx* c) {
+  const SegLayout& L = c->L;
+  cudaStream_t st = c->stream;
+  const bool mixed = c->cfg.precision == 1;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  auto run_orbit = [&](int blk) {
+    launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
+                 mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m,
+                 c->id, c->step, c->keys, c->pay, nullptr, blk, c->bk.args(), st);
+  };
+  auto time_it = [&](auto&& fn) {
+    float best = 3.4e38f;
+    for (int rep = 0; rep < 2; ++rep) {
+      cudaEventRecord(e0, st);
+      fn();
+      cudaEventRecord(e1, st);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) best = ms;
+    }
+    return best;
+  };
+  // orbit block size
+  int blk_best = c->cfg.orbit_block ? c->cfg.orbit_block : 64;
+  if (c->cfg.orbit_block == 0) {
+    float tb = 3.4e38f;
+    for (int blk : {64, 128, 256}) {
+      const float ms = time_it([&] { run_orbit(blk); });
+      if (ms < tb) { tb = ms; blk_best = blk; }
+    }
+    c->cfg.orbit_block = blk_best;
+  } else {
+    run_orbit(blk_best);
+  }
+  // sort shapes on copies of the keys the orbit step produced
+  uint64_t* saved = reinterpret_cast<uint64_t*>(c->cc);  // scratch of the same size
+  cudaMemcpyAsync(saved, c->keys, sizeof(uint64_t) * L.n, cudaMemcpyDeviceToDevice, st);
+  int best_ipt = 16, best_rank = 0;
+  float tbest = 3.4e38f;
+  for (int ipt : {8, 16})
+    for (int rank : {0, 1}) {
+      if (sort_set_shape(L, c->W, ipt, rank, st)) continue;
+      const float ms = time_it([&] {
+        cudaMemcpyAsync(c->keys, saved, sizeof(uint64_t) * L.n, cudaMemcpyDeviceToDevice, st);
+        sort_segments(L, c->W, c->keys, c->vals, 0, 8, true, c->err, st);
+      });
+      if (ms < tbest) { tbest = ms; best_ipt = ipt; best_rank = rank; }
+    }
+  cudaError_t e = sort_set_shape(L, c->W, best_ipt, best_rank, st);
+  // undo the dry run's bookkeeping
+  if (!e) e = cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
+  if (!e) e = cudaMemsetAsync(L.stats, 0, sizeof(unsigned long long) * kStStride * L.n_seg, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (!e) e = cudaGetLastError();
+  if (e) return cuda_fail(c, e, "autotune");
+  return check_err_flags(c);
+}
+
 }  // namespace
 
 extern "C" {
@@ -244,6 +311,7 @@ void cmc_config_default(cmc_config* cfg) {
   cfg->max_trials = 1000;
   cfg->energy_correction = 1;
   cfg->orbit_block = 0;
+  cfg->autotune = 1;
 }
 
 cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
@@ -319,6 +387,15 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
     free_ctx(c);
     return s;
   }
+  if (cfg.autotune) {
+    s = autotune(c);
+    if (s != CMC_OK) {
+      g_err = c->last_error;
+      free_ctx(c);
+      return s;
+    }
+  }
+  if (c->cfg.orbit_block == 0) c->cfg.orbit_block = 64;
   c->kernels_per_step = count_step_kernels(c);
   *out = c;
   return CMC_OK;
@@ -479,6 +556,14 @@ cmc_status cmc_get_stats(cmc_ctx* c, int64_t* out) {
 }
 
 int32_t cmc_kernels_per_step(const cmc_ctx* c) { return c ? c->kernels_per_step : 0; }
+
+cmc_status cmc_get_tuning(const cmc_ctx* c, int32_t* out) {
+  if (!c || !out) return CMC_EINVAL;
+  out[0] = c->cfg.orbit_block;
+  out[1] = c->W.ipt;
+  out[2] = c->W.rank;
+  return CMC_OK;
+}
 
 cmc_status cmc_set_stream(cmc_ctx* c, void* stream) {
   if (!c) return fail(c, CMC_EINVAL, "cmc_set_stream: bad arguments");

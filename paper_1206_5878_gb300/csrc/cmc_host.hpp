@@ -57,7 +57,17 @@ struct SortWork {
   size_t zero_bytes = 0;                // desc + hist + tickets, zeroed per sort
   void* zero_base = nullptr;
   int max_passes = 0;
+  // shape of the digit passes: keys per thread (8 or 16) and multisplit
+  // (0: __match_any_sync, 1: ballots); tiles of 256 * ipt keys
+  int ipt = 16;
+  int rank = 0;
+  int64_t n_stiles = 0;
+  int64_t* stile_off = nullptr;         // n_seg + 1 tile offsets of that shape
 };
+
+// choose the pass shape (host offsets are copied; not during stream capture)
+cudaError_t sort_set_shape(const SegLayout& L, SortWork& W, int ipt, int rank,
+                           cudaStream_t st);
 
 // allocation helpers (stream-ordered); return cudaError_t
 cudaError_t alloc_layout(SegLayout& L, const std::vector<int64_t>& sizes,

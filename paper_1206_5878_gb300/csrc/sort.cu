@@ -3,15 +3,21 @@
 // A stable least-significant-digit radix sort over 8-bit digits of the
 // 64-bit key, run independently inside every segment (cluster) of the
 // state.  Each digit pass is a single "onesweep" kernel: a CTA takes the
-// next tile by atomic ticket, ranks its 4096 keys with warp-level
-// __match_any_sync multisplits, publishes its digit counts, and obtains the
-// counts of all earlier tiles of its segment by decoupled look-back on
-// those published words (integer sums, so the result does not depend on
-// timing).  Tiles are taken in ticket order, so every tile a CTA waits on
-// is already running; each wait is still bounded and reports a timeout
-// instead of spinning forever.  The tile is reordered in shared memory so
-// that the scatter writes contiguous runs.
+// next tile by atomic ticket, ranks its keys with a stable warp-level
+// multisplit, publishes its digit counts, and obtains the counts of all
+// earlier tiles of its segment by decoupled look-back on those published
+// words (integer sums, so the result does not depend on timing).  Tiles are
+// taken in ticket order, so every tile a CTA waits on is already running;
+// each wait is still bounded and reports a timeout instead of spinning
+// forever.  The tile is reordered in shared memory so that the scatter
+// writes contiguous runs.
+//
+// Two shape parameters are chosen at initialisation by timing them on the
+// real keys: keys per thread (8 or 16, so tiles of 2048 or 4096) and the
+// multisplit (one __match_any_sync per key, or eight __ballot_sync
+// intersected bit by bit).
 #include <utility>
+#include <vector>
 
 #include "cmc_host.hpp"
 
@@ -21,11 +27,11 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kIPT = kTile / kThreads;  // 16 keys per thread
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr unsigned long long kCountMask = (1ull << 62) - 1;
 constexpr int kSpinCap = 1 << 22;
+constexpr int kMaxPasses = 8;
 static_assert(kThreads == kBins, "one thread per digit");
 
 __device__ __forceinline__ unsigned lanemask_lt() {
@@ -45,14 +51,14 @@ struct TileRange {
 };
 
 __device__ __forceinline__ TileRange tile_range(const int64_t* off, const int64_t* tile_off,
-                                                int n_seg, int64_t t) {
+                                                int n_seg, int64_t t, int tile) {
   TileRange R;
   R.seg = seg_find(tile_off, n_seg, t);
   R.lt = t - __ldg(tile_off + R.seg);
   R.seg_begin = __ldg(off + R.seg);
-  R.begin = R.seg_begin + R.lt * kTile;
+  R.begin = R.seg_begin + R.lt * tile;
   int64_t se = __ldg(off + R.seg + 1);
-  R.end = R.begin + kTile < se ? R.begin + kTile : se;
+  R.end = R.begin + tile < se ? R.begin + tile : se;
   return R;
 }
 
@@ -82,31 +88,31 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* s_
 }
 
 // ---------------------------------------------------------------- upsweep
-// Per-segment histogram of every pass digit.  Counts are gathered per warp
-// with __match_any_sync so that a digit shared by many keys costs one
-// shared-memory atomic per warp instead of one per key.
+// Per-segment histogram of every pass digit over tiles of kTile keys.  Each
+// warp counts into its own shared-memory histogram (collisions only among
+// its 32 lanes); the warps' histograms are summed before one global atomic
+// per bin.
 __global__ void __launch_bounds__(kThreads) k_upsweep(const int64_t* off, const int64_t* tile_off,
                                                       int n_seg, const uint64_t* keys,
                                                       int first_pass, int passes,
                                                       uint32_t* hist) {
-  __shared__ uint32_t h[8 * kBins];
-  for (int i = threadIdx.x; i < passes * kBins; i += kThreads) h[i] = 0;
+  extern __shared__ uint32_t h[];  // [kWarps][passes][kBins]
+  const int warp = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kWarps * passes * kBins; i += kThreads) h[i] = 0;
   __syncthreads();
-  TileRange R = tile_range(off, tile_off, n_seg, blockIdx.x);
-  const int lane = threadIdx.x & 31;
-  for (int64_t p0 = R.begin; p0 < R.end; p0 += kThreads) {
-    int64_t p = p0 + threadIdx.x;
-    bool valid = p < R.end;
-    uint64_t k = valid ? __ldg(keys + p) : 0;
-    for (int q = 0; q < passes; ++q) {
-      int d = valid ? (int)((k >> (8 * (first_pass + q))) & 0xFF) : kBins;
-      unsigned peers = __match_any_sync(0xffffffffu, d);
-      if (valid && lane == __ffs(peers) - 1) atomicAdd(&h[q * kBins + d], __popc(peers));
-    }
+  TileRange R = tile_range(off, tile_off, n_seg, blockIdx.x, kTile);
+  uint32_t* hw = h + (size_t)warp * passes * kBins;
+  for (int64_t p = R.begin + threadIdx.x; p < R.end; p += kThreads) {
+    const uint64_t k = __ldg(keys + p);
+    for (int q = 0; q < passes; ++q)
+      atomicAdd(&hw[q * kBins + (int)((k >> (8 * (first_pass + q))) & 0xFF)], 1u);
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * kBins; i += kThreads)
-    if (h[i]) atomicAdd(&hist[((size_t)R.seg * passes) * kBins + i], h[i]);
+  for (int i = threadIdx.x; i < passes * kBins; i += kThreads) {
+    uint32_t s = 0;
+    for (int w = 0; w < kWarps; ++w) s += h[(size_t)w * passes * kBins + i];
+    if (s) atomicAdd(&hist[((size_t)R.seg * passes) * kBins + i], s);
+  }
 }
 
 // exclusive scan of each (segment, pass) histogram in place
@@ -118,9 +124,10 @@ __global__ void __launch_bounds__(kThreads) k_hist_scan(uint32_t* hist) {
   h[threadIdx.x] = e;
 }
 
+template <int IPT>
 struct PassSmem {
-  uint64_t key[kTile];
-  uint32_t val[kTile];
+  uint64_t key[kThreads * IPT];
+  uint32_t val[kThreads * IPT];
   uint32_t whist[kWarps][kBins];
   int64_t gbase[kBins];
   uint32_t dstart[kBins];
@@ -128,20 +135,33 @@ struct PassSmem {
   int64_t tile;
 };
 
+// lanes of the warp that hold the same digit (digits 0..256, 256 = no key),
+// from one ballot per digit bit
+__device__ __forceinline__ unsigned peers_ballot(int d) {
+  unsigned m = 0xffffffffu;
+#pragma unroll
+  for (int b = 0; b < 9; ++b) {
+    const bool bit = (d >> b) & 1;
+    const unsigned x = __ballot_sync(0xffffffffu, bit);
+    m &= bit ? x : ~x;
+  }
+  return m;
+}
+
+constexpr int kRankMatch = 0;   // __match_any_sync
+constexpr int kRankBallot = 1;  // nine __ballot_sync
+
 // ------------------------------------------------------------- onesweep
-template <bool kValIdentity>
-__global__ void __launch_bounds__(kThreads) k_pass(const int64_t* off, const int64_t* tile_off,
-                                                   int n_seg, int64_t n_tiles,
-                                                   const uint64_t* __restrict__ keys_in,
-                                                   const uint32_t* __restrict__ vals_in,
-                                                   uint64_t* __restrict__ keys_out,
-                                                   uint32_t* __restrict__ vals_out,
-                                                   int pass, int q, int passes,
-                                                   const uint32_t* base,
-                                                   unsigned long long* desc,
-                                                   uint32_t* tickets, uint32_t* err) {
+template <bool kValIdentity, int IPT, int kRank>
+__global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 4 : 2))
+    k_pass(const int64_t* off, const int64_t* tile_off, int n_seg, int64_t n_tiles,
+           const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+           uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int pass, int q,
+           int passes, const uint32_t* base, unsigned long long* desc, uint32_t* tickets,
+           uint32_t* err) {
+  constexpr int kTileKeys = kThreads * IPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PassSmem& S = *reinterpret_cast<PassSmem*>(smem_raw);
+  PassSmem<IPT>& S = *reinterpret_cast<PassSmem<IPT>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int shift = 8 * pass;
 
@@ -149,16 +169,16 @@ __global__ void __launch_bounds__(kThreads) k_pass(const int64_t* off, const int
   for (int i = tid; i < kWarps * kBins; i += kThreads) (&S.whist[0][0])[i] = 0;
   __syncthreads();
   const int64_t t = S.tile;
-  TileRange R = tile_range(off, tile_off, n_seg, t);
+  TileRange R = tile_range(off, tile_off, n_seg, t, kTileKeys);
   const int64_t n_items = R.end - R.begin;
 
-  // warp-striped load: warp w owns elements [w*512, w*512+512) of the tile
-  uint64_t k[kIPT];
-  uint32_t v[kIPT];
-  int dg[kIPT];
+  // warp-striped load: warp w owns elements [w*32*IPT, (w+1)*32*IPT)
+  uint64_t k[IPT];
+  uint32_t v[IPT];
+  int dg[IPT];
 #pragma unroll
-  for (int i = 0; i < kIPT; ++i) {
-    int64_t e = (int64_t)warp * (32 * kIPT) + i * 32 + lane;
+  for (int i = 0; i < IPT; ++i) {
+    int64_t e = (int64_t)warp * (32 * IPT) + i * 32 + lane;
     int64_t p = R.begin + e;
     bool valid = e < n_items;
     k[i] = valid ? keys_in[p] : 0ull;
@@ -167,11 +187,12 @@ __global__ void __launch_bounds__(kThreads) k_pass(const int64_t* off, const int
   }
 
   // warp-level multisplit ranks (stable: slot order, then lane order)
-  uint32_t rank[kIPT];
+  uint32_t rank[IPT];
   const unsigned lt_mask = lanemask_lt();
 #pragma unroll
-  for (int i = 0; i < kIPT; ++i) {
-    unsigned peers = __match_any_sync(0xffffffffu, dg[i]);
+  for (int i = 0; i < IPT; ++i) {
+    const unsigned peers = kRank == kRankMatch ? __match_any_sync(0xffffffffu, dg[i])
+                                               : peers_ballot(dg[i]);
     int leader = __ffs(peers) - 1;
     uint32_t old = 0;
     if (lane == leader && dg[i] < kBins) {
@@ -231,7 +252,7 @@ __global__ void __launch_bounds__(kThreads) k_pass(const int64_t* off, const int
 
   // reorder the tile in shared memory by digit
 #pragma unroll
-  for (int i = 0; i < kIPT; ++i) {
+  for (int i = 0; i < IPT; ++i) {
     if (dg[i] < kBins) {
       uint32_t lp = S.dstart[dg[i]] + S.whist[warp][dg[i]] + rank[i];
       S.key[lp] = k[i];
@@ -273,12 +294,12 @@ __global__ void k_tiefix(const int64_t* off, int n_seg, int64_t n, const uint64_
   if (p > sb && keys[p - 1] == kp) return;  // not the start of the run
   int64_t e = p + 2;
   while (e < se && keys[e] == kp) ++e;
-  long long moves = 0;
   for (int64_t i = p; i < e; ++i)
     if ((int64_t)vals[i] >= n) {
       set_err(err, kErrTimeout);
       return;
     }
+  long long moves = 0;
   for (int64_t i = p + 1; i < e; ++i) {
     uint32_t v = vals[i];
     uint32_t idv = ids_by_val[(size_t)v * id_stride];
@@ -305,16 +326,80 @@ __global__ void k_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t
   reinterpret_cast<uint4*>(out)[i] = make_uint4(w.x, w.y, w.z, w.w);
 }
 
+template <bool kId, int IPT, int kRank>
+void set_pass_smem() {
+  cudaFuncSetAttribute(k_pass<kId, IPT, kRank>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(PassSmem<IPT>));
+}
+
+template <int IPT, int kRank>
+void launch_pass(const SegLayout& L, SortWork& W, bool id, const uint64_t* kin,
+                 const uint32_t* vin, uint64_t* kout, uint32_t* vout, int pass, int q,
+                 int passes, uint32_t* err, cudaStream_t st) {
+  const unsigned grid = (unsigned)W.n_stiles;
+  const size_t sm = sizeof(PassSmem<IPT>);
+  if (id)
+    k_pass<true, IPT, kRank><<<grid, kThreads, sm, st>>>(L.off, W.stile_off, L.n_seg,
+                                                         W.n_stiles, kin, vin, kout, vout, pass,
+                                                         q, passes, W.hist, W.desc, W.tickets,
+                                                         err);
+  else
+    k_pass<false, IPT, kRank><<<grid, kThreads, sm, st>>>(L.off, W.stile_off, L.n_seg,
+                                                          W.n_stiles, kin, vin, kout, vout,
+                                                          pass, q, passes, W.hist, W.desc,
+                                                          W.tickets, err);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host
+void sort_prepare() {
+  set_pass_smem<true, 8, kRankMatch>();
+  set_pass_smem<false, 8, kRankMatch>();
+  set_pass_smem<true, 8, kRankBallot>();
+  set_pass_smem<false, 8, kRankBallot>();
+  set_pass_smem<true, 16, kRankMatch>();
+  set_pass_smem<false, 16, kRankMatch>();
+  set_pass_smem<true, 16, kRankBallot>();
+  set_pass_smem<false, 16, kRankBallot>();
+  cudaFuncSetAttribute(k_upsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(sizeof(uint32_t) * kWarps * kMaxPasses * kBins));
+}
+
+static std::vector<int64_t> sort_tile_offsets(const SegLayout& L, int tile) {
+  std::vector<int64_t> o(L.n_seg + 1, 0);
+  for (int c = 0; c < L.n_seg; ++c) {
+    const int64_t nc = L.h_off[c + 1] - L.h_off[c];
+    o[c + 1] = o[c] + (nc + tile - 1) / tile;
+  }
+  return o;
+}
+
+cudaError_t sort_set_shape(const SegLayout& L, SortWork& W, int ipt, int rank,
+                           cudaStream_t st) {
+  if ((ipt != 8 && ipt != 16) || (rank != 0 && rank != 1)) return cudaErrorInvalidValue;
+  std::vector<int64_t> o = sort_tile_offsets(L, kThreads * ipt);
+  cudaError_t e = cudaMemcpyAsync(W.stile_off, o.data(), sizeof(int64_t) * o.size(),
+                                  cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaStreamSynchronize(st);  // o lives on this stack
+  if (e) return e;
+  W.ipt = ipt;
+  W.rank = rank;
+  W.n_stiles = o[L.n_seg];
+  return cudaSuccess;
+}
+
 cudaError_t alloc_sort(SortWork& W, const SegLayout& L, int max_passes, cudaStream_t st) {
   W.max_passes = max_passes;
   size_t n = (size_t)L.n;
   cudaError_t e;
   if ((e = cudaMallocAsync((void**)&W.keys_alt, sizeof(uint64_t) * (n ? n : 1), st))) return e;
   if ((e = cudaMallocAsync((void**)&W.vals_alt, sizeof(uint32_t) * (n ? n : 1), st))) return e;
-  size_t desc_b = sizeof(unsigned long long) * (size_t)max_passes * L.n_tiles * kBins;
+  if ((e = cudaMallocAsync((void**)&W.stile_off, sizeof(int64_t) * (L.n_seg + 1), st)))
+    return e;
+  // look-back words for the smallest tiles (the most tiles)
+  const int64_t max_tiles = sort_tile_offsets(L, kThreads * 8)[L.n_seg];
+  size_t desc_b = sizeof(unsigned long long) * (size_t)max_passes * max_tiles * kBins;
   size_t hist_b = sizeof(uint32_t) * (size_t)L.n_seg * max_passes * kBins;
   size_t tick_b = sizeof(uint32_t) * 16;
   W.zero_bytes = desc_b + hist_b + tick_b;
@@ -322,21 +407,15 @@ cudaError_t alloc_sort(SortWork& W, const SegLayout& L, int max_passes, cudaStre
   W.desc = (unsigned long long*)W.zero_base;
   W.hist = (uint32_t*)((char*)W.zero_base + desc_b);
   W.tickets = (uint32_t*)((char*)W.zero_base + desc_b + hist_b);
-  return cudaSuccess;
+  return sort_set_shape(L, W, 16, 0, st);
 }
 
 void free_sort(SortWork& W, cudaStream_t st) {
   if (W.keys_alt) cudaFreeAsync(W.keys_alt, st);
   if (W.vals_alt) cudaFreeAsync(W.vals_alt, st);
+  if (W.stile_off) cudaFreeAsync(W.stile_off, st);
   if (W.zero_base) cudaFreeAsync(W.zero_base, st);
   W = SortWork();
-}
-
-void sort_prepare() {
-  cudaFuncSetAttribute(k_pass<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(PassSmem));
-  cudaFuncSetAttribute(k_pass<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(PassSmem));
 }
 
 cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint32_t* vals,
@@ -344,22 +423,24 @@ cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint3
                           cudaStream_t st) {
   if (passes <= 0 || passes > W.max_passes || L.n_tiles == 0) return cudaSuccess;
   cudaMemsetAsync(W.zero_base, 0, W.zero_bytes, st);
-  k_upsweep<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(L.off, L.tile_off, L.n_seg, keys,
-                                                     first_pass, passes, W.hist);
+  k_upsweep<<<(unsigned)L.n_tiles, kThreads, sizeof(uint32_t) * kWarps * passes * kBins, st>>>(
+      L.off, L.tile_off, L.n_seg, keys, first_pass, passes, W.hist);
   k_hist_scan<<<(unsigned)(L.n_seg * passes), kThreads, 0, st>>>(W.hist);
   uint64_t* kin = keys;
   uint32_t* vin = vals;
   uint64_t* kout = W.keys_alt;
   uint32_t* vout = W.vals_alt;
   for (int q = 0; q < passes; ++q) {
-    if (q == 0 && vals_identity)
-      k_pass<true><<<(unsigned)L.n_tiles, kThreads, sizeof(PassSmem), st>>>(
-          L.off, L.tile_off, L.n_seg, L.n_tiles, kin, vin, kout, vout, first_pass + q, q,
-          passes, W.hist, W.desc, W.tickets, err);
+    const bool id = q == 0 && vals_identity;
+    const int pass = first_pass + q;
+    if (W.ipt == 8 && W.rank == kRankMatch)
+      launch_pass<8, kRankMatch>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st);
+    else if (W.ipt == 8)
+      launch_pass<8, kRankBallot>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st);
+    else if (W.rank == kRankMatch)
+      launch_pass<16, kRankMatch>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st);
     else
-      k_pass<false><<<(unsigned)L.n_tiles, kThreads, sizeof(PassSmem), st>>>(
-          L.off, L.tile_off, L.n_seg, L.n_tiles, kin, vin, kout, vout, first_pass + q, q,
-          passes, W.hist, W.desc, W.tickets, err);
+      launch_pass<16, kRankBallot>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st);
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
@@ -367,8 +448,8 @@ cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint3
 }
 
 void launch_tiefix(const SegLayout& L, const uint64_t* keys, uint32_t* vals,
-                           const uint32_t* ids_by_val, int id_stride, uint32_t* err,
-                           cudaStream_t st) {
+                   const uint32_t* ids_by_val, int id_stride, uint32_t* err,
+                   cudaStream_t st) {
   if (L.n == 0) return;
   k_tiefix<<<(unsigned)((L.n + 255) / 256), 256, 0, st>>>(L.off, L.n_seg, L.n, keys, vals,
                                                          ids_by_val, id_stride, err, L.stats);

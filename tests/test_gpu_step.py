@@ -172,6 +172,22 @@ def test_launch_shape_does_not_change_bits(g, precision):
             np.testing.assert_array_equal(o[k], outs[0][k])
 
 
+def test_autotuned_shapes_do_not_change_bits(g):
+    d = ic.plummer(30_001, seed=6, masses="salpeter")
+    a = _cluster(g, d, 6, autotune=0)
+    b = _cluster(g, d, 6, autotune=1, precision=0)
+    ta, tb = a.tuning(), b.tuning()
+    assert ta == {"orbit_block": 64, "sort_keys_per_thread": 16, "sort_multisplit": "match"}
+    assert tb["orbit_block"] in (64, 128, 256) and tb["sort_keys_per_thread"] in (8, 16)
+    assert b.stats()[0]["trials"] == 0  # the tuner's dry run left no trace
+    a.step(3)
+    b.step(3)
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("r", "vr", "vt", "m", "id", "phi"):
+        np.testing.assert_array_equal(sa[k], sb[k])
+    assert a.stats() == b.stats()
+
+
 def test_host_and_device_inputs_agree(g):
     import torch
     d = ic.plummer(5000, seed=8)
