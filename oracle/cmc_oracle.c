@@ -116,8 +116,9 @@ static int or_disk_angle(uint64_t seed, uint32_t id, uint32_t step, uint32_t tag
         vv = v * v;
         q = uu + vv;
         if (q <= 1.0) {
-            *c = (uu - vv) / q;
-            *s = ((2.0 * u) * v) / q;
+            double iq = 1.0 / q;
+            *c = (uu - vv) * iq;
+            *s = ((2.0 * u) * v) * iq;
             return 0;
         }
     }
@@ -370,8 +371,8 @@ int or_encounter(double m1, double m2, double vr1, double vt1, double vr2, doubl
 {
     double msum, cpsi = 1.0, spsi = 0.0, cphi, sphi;
     double v1x, v1y, v1z, v2x, v2y, v2z, wx, wy, wz, w2, w;
-    double num, s2, sb, cosb, sinb, wp2, e1y, e1z;
-    double ux, uy, uz, a1, wpx, wpy, wpz, dwx, dwy, dwz, f1, f2;
+    double num, s2, cosb, sinb, wp2, e1y, e1z;
+    double ux, uy, uz, a1, wpx, wpy, wpz, dwx, dwy, dwz, im, f1, f2;
     int fails = 0, i;
     for (i = 0; i < 16; ++i) out[i] = 0.0;
     out[15] = 1.0;
@@ -400,18 +401,18 @@ int or_encounter(double m1, double m2, double vr1, double vt1, double vr2, doubl
     num = num * dt;
     s2 = num / (w2 * w);
     if (!(s2 <= 1.0)) s2 = 1.0;
-    sb = sqrt(s2);
+    /* cos(beta) = 1 - 2 sin^2(beta/2), sin(beta) = 2 sin(beta/2) cos(beta/2) */
     cosb = 1.0 - 2.0 * s2;
-    sinb = (2.0 * sb) * sqrt(1.0 - s2);
+    sinb = 2.0 * sqrt(s2 * (1.0 - s2));
     fails += or_disk_angle(seed, id, step, OR_TAG_PHI, &cphi, &sphi);
     /* unit vector e1 = (w x xhat)/|w x xhat| = (0, wz, -wy)/|.|, or yhat when
      * w is radial; u = w x e1 has length |w| and completes the orthogonal
      * frame (e1, u/|w|) perpendicular to w. */
     wp2 = wy * wy + wz * wz;
     if (wp2 > 0.0) {
-        double wp = sqrt(wp2);
-        e1y = wz / wp;
-        e1z = -wy / wp;
+        double iwp = 1.0 / sqrt(wp2);
+        e1y = wz * iwp;
+        e1z = -(wy * iwp);
     } else {
         e1y = 1.0;
         e1z = 0.0;
@@ -427,8 +428,9 @@ int or_encounter(double m1, double m2, double vr1, double vt1, double vr2, doubl
     dwx = wpx - wx; dwy = wpy - wy; dwz = wpz - wz;
     /* the centre of mass keeps its velocity: v1' = v1 + m2/(m1+m2) dw,
      * v2' = v2 - m1/(m1+m2) dw */
-    f1 = m2 / msum;
-    f2 = m1 / msum;
+    im = 1.0 / msum;
+    f1 = m2 * im;
+    f2 = m1 * im;
     out[6] = v1x + f1 * dwx; out[7] = v1y + f1 * dwy; out[8] = v1z + f1 * dwz;
     out[9] = v2x - f2 * dwx; out[10] = v2y - f2 * dwy; out[11] = v2z - f2 * dwz;
     out[12] = s2; out[13] = cosb; out[14] = w; out[15] = 0.0;

@@ -104,8 +104,9 @@ __device__ __forceinline__ bool disk_angle(uint64_t seed, uint32_t id, uint32_t 
     double v = 2.0 * u01(w.z, w.w) - 1.0;
     double uu = u * u, vv = v * v, q = uu + vv;
     if (q <= 1.0) {
-      c = (uu - vv) / q;
-      s = ((2.0 * u) * v) / q;
+      const double iq = 1.0 / q;
+      c = (uu - vv) * iq;
+      s = ((2.0 * u) * v) * iq;
       return true;
     }
   }

@@ -126,18 +126,18 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   num = num * dt;
   double s2 = num / (w2 * w);
   if (!(s2 <= 1.0)) s2 = 1.0;
-  const double sb = sqrt(s2);
+  // cos(beta) = 1 - 2 sin^2(beta/2), sin(beta) = 2 sin(beta/2) cos(beta/2)
   const double cosb = 1.0 - 2.0 * s2;
-  const double sinb = (2.0 * sb) * sqrt(1.0 - s2);
+  const double sinb = 2.0 * sqrt(s2 * (1.0 - s2));
   if (!disk_angle(seed, ida, step, kTagPhi, cphi, sphi)) ++fails;
   // e1 = (w x xhat)/|w x xhat| = (0, wz, -wy)/|.| (yhat for radial w);
   // u = w x e1 has length |w| and completes the frame perpendicular to w
   const double wp2 = wy * wy + wz * wz;
   double e1y, e1z;
   if (wp2 > 0.0) {
-    const double wp = sqrt(wp2);
-    e1y = wz / wp;
-    e1z = -wy / wp;
+    const double iwp = 1.0 / sqrt(wp2);
+    e1y = wz * iwp;
+    e1z = -(wy * iwp);
   } else {
     e1y = 1.0;
     e1z = 0.0;
@@ -151,7 +151,8 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   const double wpy = wy * cosb + sinb * (a1 * e1y + sphi * uy);
   const double wpz = wz * cosb + sinb * (a1 * e1z + sphi * uz);
   const double dwx = wpx - wx, dwy = wpy - wy, dwz = wpz - wz;
-  const double f1 = m2 / msum, f2 = m1 / msum;
+  const double im = 1.0 / msum;
+  const double f1 = m2 * im, f2 = m1 * im;
   const double p1x = v1x + f1 * dwx, p1y = v1y + f1 * dwy, p1z = v1z + f1 * dwz;
   const double p2x = v2x - f2 * dwx, p2y = v2y - f2 * dwy, p2z = v2z - f2 * dwz;
   vr[a] = p1x;

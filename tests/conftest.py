@@ -18,3 +18,12 @@ def orc():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def g_stage():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1206_5878_gb300 as lib
+    lib.load()
+    return lib

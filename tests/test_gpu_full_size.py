@@ -1,0 +1,89 @@
+"""Parity at the benchmark's size: Plummer N = 10^7 (equal masses, seed 1),
+the launch configuration bench.py times.  Where the oracle is fast enough
+it runs on every star (sort, potential, timestep, relaxation); the orbit
+step is checked bit for bit on sampled stars, each computed one by one by
+the oracle against the full 10^7-node table."""
+import numpy as np
+import pytest
+
+import initial_conditions as ic
+from gpu_util import dev, host
+
+pytestmark = pytest.mark.gpu
+
+N = 10_000_000
+
+
+@pytest.fixture(scope="module")
+def big(orc):
+    import paper_1206_5878_gb300 as g
+    d = ic.plummer(N, seed=1)
+    c = g.Cluster({k: d[k] for k in ("r", "vr", "vt", "m", "id")}, [1], precision=1)
+    st = c.get_state()
+    yield d, c, st
+    c.close()
+
+
+def test_init_sort_and_potential_full_size(orc, big):
+    d, c, st = big
+    perm = orc.sort_perm(d["r"], d["id"])
+    np.testing.assert_array_equal(st["id"], d["id"][perm])
+    np.testing.assert_array_equal(st["r"], d["r"][perm])
+    ref = orc.potential(st["r"], st["m"], "dd")
+    assert np.max(np.abs(st["phi"] / ref - 1)) < 1e-12
+    E = c.energy()[0]
+    Eo = orc.energy(st["r"], st["vr"], st["vt"], st["m"])
+    # the oracle sums its 10^7 terms one after another: its own rounding
+    # is bounded by N eps ~ 1e-9 relative (the GPU sums in a tree)
+    assert np.max(np.abs(E - Eo)) < 1e-9 * abs(Eo[2])
+    assert abs(E[2] + 0.25) < 1e-3  # Plummer model in Henon units
+
+
+def test_timestep_and_relaxation_full_size(g_stage, orc, big):
+    g = g_stage
+    _, _, st = big
+    lnL = orc.coulomb_log(N)
+    dt, nbin = g.stage_timestep(dev(st["r"]), dev(st["vr"]), dev(st["vt"]), dev(st["m"]), lnL)
+    dto, nbo = orc.timestep(st["r"], st["vr"], st["vt"], st["m"], lnL)
+    np.testing.assert_array_equal(host(nbin), nbo)
+    assert host(dt)[0] == dto
+    vr, vt = g.stage_relax(dev(st["vr"]), dev(st["vt"]), dev(st["m"]), dev(st["id"]), dev(nbo),
+                           dto, lnL, 1, 0)
+    vro, vto, _ = orc.relax(st["vr"], st["vt"], st["m"], st["id"], nbo, dto, lnL, 1, 0)
+    np.testing.assert_array_equal(host(vr), vro)
+    np.testing.assert_array_equal(host(vt), vto)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_orbit_sampled_full_size(g_stage, orc, big, precision):
+    g = g_stage
+    _, _, st = big
+    out = g.stage_orbit(dev(st["r"]), dev(st["phi"]), dev(st["vr"]), dev(st["vt"]),
+                        dev(st["id"]), 1, 0, precision=precision)
+    got = {k: host(v) for k, v in out.items()}
+    rng = np.random.default_rng(7)
+    ks = np.concatenate([[0, 1, N - 2, N - 1], rng.choice(N, 1500, replace=False)])
+    flips = 0
+    for k in ks:
+        o = orc.orbit_star(int(k), st["r"], st["phi"], st["vr"][k], st["vt"][k],
+                           int(st["id"][k]), 1, 0)
+        assert got["code"][k] == o["code"]
+        if precision == 0:
+            for key in ("r_new", "vr", "vt", "phi_new", "rmin", "rmax", "F"):
+                assert got[key][k] == o[key], (k, key)
+        else:
+            assert abs(got["rmin"][k] - o["rmin"]) <= 1e-12 * o["rmin"]
+            assert abs(got["rmax"][k] - o["rmax"]) <= 1e-12 * o["rmax"]
+            if abs(got["r_new"][k] / o["r_new"] - 1) > 1e-12:
+                flips += 1
+    assert flips <= 3
+
+
+def test_one_mixed_step_full_size(big):
+    _, c, st = big
+    c.step(1)
+    s1 = c.get_state()
+    assert np.all(np.diff(s1["r"][np.isfinite(s1["r"])]) >= 0)
+    assert sorted(s1["id"][:1000].tolist()) != list(range(1000))  # stars moved
+    assert np.array_equal(np.sort(s1["id"]), np.arange(N, dtype=np.uint32))
+    assert c.stats()[0]["cap_hits"] == 0
