@@ -88,6 +88,9 @@ typedef struct {
                                    orbit block size when orbit_block is 0) on
                                    the real state and keep the fastest; results
                                    do not depend on the choice (default 1) */
+    int32_t orbit_variant;      /* mixed-mode orbit kernel variant (listed at
+                                   cmc_get_tuning): -1 = the autotuner's choice
+                                   (0 without autotune), or 0..4 (default -1) */
 } cmc_config;
 
 /* Fill cfg with the defaults shown above. */
@@ -151,6 +154,17 @@ cmc_status cmc_get_dt(cmc_ctx *ctx, double *out);
 /* Cumulative counters: out (host, n_clusters x CMC_NSTATS). */
 cmc_status cmc_get_stats(cmc_ctx *ctx, int64_t *out);
 
+/* What the escapers have carried off since cmc_init (the energy budget of
+ * section 4.2: K + W of the bound stars plus E_esc is what the method
+ * conserves).  out (host, n_clusters x 2): M_esc, E_esc.  A star k leaving
+ * in a step adds m_k and m_k e_k, e_k = Phi_k + m_k / r_k + v_k^2 / 2 (its
+ * energy in the field of the others, from the state before its orbit
+ * step), summed in a fixed order, so the figures are reproducible.
+ * cmc_set_state leaves them as they are; cmc_set_escaped (in: host,
+ * n_clusters x 2, finite) restores them when a run is resumed. */
+cmc_status cmc_get_escaped(cmc_ctx *ctx, double *out);
+cmc_status cmc_set_escaped(cmc_ctx *ctx, const double *in);
+
 /* Stages of one timestep, as timed by cmc_step_profiled. */
 enum {
     CMC_STAGE_TIMESTEP = 0,    /* Eq. 7 bins and the minimum over bins */
@@ -171,8 +185,11 @@ enum {
 cmc_status cmc_step_profiled(cmc_ctx *ctx, int32_t n_steps, double *stage_ms);
 
 /* Kernel shapes in use (chosen by autotune or the configuration): out
- * (host, 3) = {orbit threads per block, sort keys per thread, sort
- * multisplit (0: match, 1: ballot)}. */
+ * (host, 4) = {orbit threads per block, sort keys per thread, sort
+ * multisplit (0: match, 1: ballot), mixed-mode orbit variant (0: F samples
+ * searched 7 at a time, 1: 3 at a time, 2 and 3: 3 at a time with at most
+ * 64 and 80 registers per thread, 4: 7 at a time with at most 128)}.  All
+ * shapes give bit-identical results. */
 cmc_status cmc_get_tuning(const cmc_ctx *ctx, int32_t *out);
 
 /* Number of kernels one cmc_step timestep launches. */

@@ -86,7 +86,7 @@ def _declare(lib):
         "or_energy_W_brute": (_d, [_i64, _p, _p]),
         "or_lagrange_radii": (None, [_i64, _p, _p, _p, _i32, _p]),
         "or_step": (_d, [_i64, _p, _p, _p, _p, _p, _p, _p, _u64, _u32, _i32, _d, _d,
-                         _i32, _i32, _i32, _p]),
+                         _i32, _i32, _i32, _p, _p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -302,6 +302,8 @@ class Cluster:
                                         "dd" if self.pot_mode == 1 else "recursion")
         self.last_stats = None
         self.last_dt = None
+        # mass and energy carried off by escapers (section 4.2's budget)
+        self.escaped = np.zeros(2)
 
     def step(self, nsteps: int = 1):
         for _ in range(nsteps):
@@ -310,7 +312,8 @@ class Cluster:
             dt = _L().or_step(self.n, _ptr(nb), _ptr(self.r), _ptr(self.vr), _ptr(self.vt),
                               _ptr(self.m), _ptr(self.id), _ptr(self.phi), self.seed,
                               self.step_no, self.bin_size, self.pref, self.lnL,
-                              self.max_trials, self.ecorr, self.pot_mode, _ptr(stats))
+                              self.max_trials, self.ecorr, self.pot_mode, _ptr(stats),
+                              _ptr(self.escaped))
             self.nb = int(nb[0])
             self.step_no += 1
             self.last_dt = dt
@@ -320,6 +323,10 @@ class Cluster:
     def energy(self):
         nb = self.nb
         return energy(self.r[:nb], self.vr[:nb], self.vt[:nb], self.m[:nb])
+
+    def total_energy(self) -> float:
+        """K + W of the bound stars plus the energy the escapers took."""
+        return self.energy()[2] + self.escaped[1]
 
     def lagrange_radii(self, fracs):
         nb = self.nb

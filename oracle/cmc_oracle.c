@@ -727,11 +727,15 @@ void or_lagrange_radii(int64_t nb, const double *r, const double *m,
 /* stats[]: 0 escaped this step, 1 degenerate orbits, 2 rejection-cap hits,  */
 /*          3 trials, 4 g > F violations, 5 T' clamps, 6 angle-draw fails.   */
 /* Returns dt.  pot_mode: 0 = Eqs. 2-5 recursion, 1 = double-double scan.    */
+/* esc_io (may be NULL) accumulates what the escapers carry off (the        */
+/* energy budget of section 4.2): [0] += m_k, [1] += m_k e_k, with          */
+/* e_k = Phi_k + m_k / r_k + (v_r^2 + v_t^2) / 2 the star's energy in the   */
+/* field of the others (Phi_k includes the star's own mass), in star order. */
 /* ------------------------------------------------------------------------ */
 double or_step(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt, double *m,
                uint32_t *id, double *phi, uint64_t seed, uint32_t step, int32_t bs,
                double pref, double lnL, int32_t max_trials, int32_t ecorr,
-               int32_t pot_mode, int64_t *stats)
+               int32_t pot_mode, int64_t *stats, double *esc_io)
 {
     int64_t nb = *nb_io, k;
     int64_t nbins = (nb + bs - 1) / bs;
@@ -756,7 +760,16 @@ double or_step(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt, dou
                                max_trials, out, &viol);
         stats[3] += (int64_t)out[7];
         stats[4] += viol;
-        if (rc == 1) { stats[0] += 1; rn[k] = INFINITY; continue; }
+        if (rc == 1) {
+            stats[0] += 1;
+            rn[k] = INFINITY;
+            if (esc_io) {
+                double e = phi[k] + m[k] / r[k] + 0.5 * (vr[k] * vr[k] + vt[k] * vt[k]);
+                esc_io[0] += m[k];
+                esc_io[1] += m[k] * e;
+            }
+            continue;
+        }
         if (rc == 2) { stats[1] += 1; continue; }
         if (rc == 3) { stats[2] += 1; continue; }
         rn[k] = out[0];

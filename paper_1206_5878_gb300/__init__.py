@@ -172,16 +172,32 @@ class Cluster:
         check(self.lib.cmc_get_stats(self.ctx, out.ctypes.data), self.ctx)
         return [dict(zip(STAT_NAMES, (int(v) for v in row))) for row in out]
 
+    def escaped(self) -> np.ndarray:
+        """(n_clusters, 2): mass and energy carried off by escapers; the
+        conserved total is energy()[:, 2] + escaped()[:, 1]."""
+        out = np.zeros((self.n_clusters, 2))
+        check(self.lib.cmc_get_escaped(self.ctx, out.ctypes.data), self.ctx)
+        return out
+
+    def set_escaped(self, budget):
+        b = np.ascontiguousarray(budget, dtype=np.float64).reshape(self.n_clusters, 2)
+        check(self.lib.cmc_set_escaped(self.ctx, b.ctypes.data), self.ctx)
+
+    def total_energy(self) -> np.ndarray:
+        """K + W of the bound stars plus the energy the escapers took."""
+        return self.energy()[:, 2] + self.escaped()[:, 1]
+
     def kernels_per_step(self) -> int:
         return int(self.lib.cmc_kernels_per_step(self.ctx))
 
     def tuning(self) -> dict:
-        """Kernel shapes in use: orbit block size, sort keys per thread and
-        multisplit (match or ballot)."""
-        out = np.zeros(3, dtype=np.int32)
+        """Kernel shapes in use: orbit block size, sort keys per thread,
+        multisplit (match or ballot) and the mixed-mode orbit variant."""
+        out = np.zeros(4, dtype=np.int32)
         check(self.lib.cmc_get_tuning(self.ctx, out.ctypes.data), self.ctx)
         return {"orbit_block": int(out[0]), "sort_keys_per_thread": int(out[1]),
-                "sort_multisplit": "ballot" if out[2] else "match"}
+                "sort_multisplit": "ballot" if out[2] else "match",
+                "orbit_variant": int(out[3])}
 
     def set_stream(self, stream):
         self.stream = _stream_ptr(stream)

@@ -32,7 +32,7 @@ STAGE_NAMES = ("timestep", "relax", "orbit", "sort", "gather", "potential", "cor
 class cmc_config(ctypes.Structure):
     _fields_ = [("precision", _i32), ("bin_size", _i32), ("theta_max", _d), ("gamma", _d),
                 ("max_trials", _i32), ("energy_correction", _i32), ("orbit_block", _i32),
-                ("autotune", _i32)]
+                ("autotune", _i32), ("orbit_variant", _i32)]
 
 
 # exported symbol -> (restype, argtypes); the list is the ABI of include/cmc.h
@@ -49,6 +49,8 @@ SIGNATURES = {
     "cmc_get_nbound": (_i32, [_p, _p]),
     "cmc_get_dt": (_i32, [_p, _p]),
     "cmc_get_stats": (_i32, [_p, _p]),
+    "cmc_get_escaped": (_i32, [_p, _p]),
+    "cmc_set_escaped": (_i32, [_p, _p]),
     "cmc_kernels_per_step": (_i32, [_p]),
     "cmc_get_tuning": (_i32, [_p, _p]),
     "cmc_set_stream": (_i32, [_p, _p]),

@@ -40,6 +40,7 @@ struct cmc_ctx {
   bool poisoned = false;
   std::string last_error;
   int kernels_per_step = 0;
+  int orbit_variant = 0;  // mixed-mode orbit kernel variant (see kOrbitVariants)
 };
 
 namespace {
@@ -143,7 +144,8 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   mark(2);
   launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
-               c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->bk.args(), st);
+               c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
+               c->bk.args(), st);
   mark(3);
   sort_segments(L, c->W, c->keys, c->vals, 0, 8, true, c->err, st);
   launch_tiefix(L, c->keys, c->vals, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)),
@@ -159,7 +161,7 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   if (c->cfg.energy_correction)
     launch_correction(L, c->r, c->x, c->phi, c->vr, c->vt, c->r_old, c->cc, true, c->err, st);
   mark(7);
-  launch_step_end(L, c->step, st);
+  launch_step_end(L, c->step, c->r_old, c->cc, c->m, st);
   mark(8);
 }
 
@@ -241,10 +243,10 @@ cmc_status autotune(cmc_ctx* c) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  auto run_orbit = [&](int blk) {
+  auto run_orbit = [&](int blk, int var) {
     launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                  mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m,
-                 c->id, c->step, c->keys, c->pay, nullptr, blk, c->bk.args(), st);
+                 c->id, c->step, c->keys, c->pay, nullptr, blk, var, c->bk.args(), st);
   };
   auto time_it = [&](auto&& fn) {
     float best = 3.4e38f;
@@ -259,18 +261,20 @@ cmc_status autotune(cmc_ctx* c) {
     }
     return best;
   };
-  // orbit block size
-  int blk_best = c->cfg.orbit_block ? c->cfg.orbit_block : 64;
-  if (c->cfg.orbit_block == 0) {
-    float tb = 3.4e38f;
+  // orbit block size and (mixed mode) kernel variant
+  const int n_var = mixed ? kOrbitVariants : 1;
+  int blk_best = c->cfg.orbit_block ? c->cfg.orbit_block : 64, var_best = c->orbit_variant;
+  float tb = 3.4e38f;
+  for (int var = 0; var < n_var; ++var)
     for (int blk : {64, 128, 256}) {
-      const float ms = time_it([&] { run_orbit(blk); });
-      if (ms < tb) { tb = ms; blk_best = blk; }
+      if (c->cfg.orbit_block && blk != c->cfg.orbit_block) continue;
+      if (mixed && c->cfg.orbit_variant >= 0 && var != c->cfg.orbit_variant) continue;
+      const float ms = time_it([&] { run_orbit(blk, var); });
+      if (ms < tb) { tb = ms; blk_best = blk; var_best = var; }
     }
-    c->cfg.orbit_block = blk_best;
-  } else {
-    run_orbit(blk_best);
-  }
+  c->cfg.orbit_block = blk_best;
+  c->orbit_variant = var_best;
+  run_orbit(blk_best, var_best);
   // sort shapes on copies of the keys the orbit step produced
   uint64_t* saved = reinterpret_cast<uint64_t*>(c->cc);  // scratch of the same size
   cudaMemcpyAsync(saved, c->keys, sizeof(uint64_t) * L.n, cudaMemcpyDeviceToDevice, st);
@@ -312,6 +316,7 @@ void cmc_config_default(cmc_config* cfg) {
   cfg->energy_correction = 1;
   cfg->orbit_block = 0;
   cfg->autotune = 1;
+  cfg->orbit_variant = -1;
 }
 
 cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
@@ -328,7 +333,7 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   if ((cfg.precision != 0 && cfg.precision != 1) || cfg.bin_size < 2 || (cfg.bin_size & 1) ||
       cfg.max_trials < 1 || cfg.max_trials > (1 << 24) || !(cfg.theta_max > 0.0) ||
       !(cfg.gamma > 0.0) || cfg.orbit_block < 0 || cfg.orbit_block > 256 ||
-      (cfg.orbit_block % 32))
+      (cfg.orbit_block % 32) || cfg.orbit_variant < -1 || cfg.orbit_variant >= kOrbitVariants)
     return fail(nullptr, CMC_EINVAL, "cmc_init: bad configuration");
   std::vector<int64_t> sizes(n_per_cluster, n_per_cluster + n_clusters);
   std::vector<uint64_t> sd(seeds, seeds + n_clusters);
@@ -387,6 +392,7 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
     free_ctx(c);
     return s;
   }
+  c->orbit_variant = cfg.orbit_variant > 0 ? cfg.orbit_variant : 0;
   if (cfg.autotune) {
     s = autotune(c);
     if (s != CMC_OK) {
@@ -555,6 +561,28 @@ cmc_status cmc_get_stats(cmc_ctx* c, int64_t* out) {
   return CMC_OK;
 }
 
+cmc_status cmc_get_escaped(cmc_ctx* c, double* out) {
+  if (!c || !out) return fail(c, CMC_EINVAL, "cmc_get_escaped: bad arguments");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaMemcpyAsync(out, c->L.esc_me, sizeof(double) * 2 * c->L.n_seg,
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "cmc_get_escaped");
+  return CMC_OK;
+}
+
+cmc_status cmc_set_escaped(cmc_ctx* c, const double* in) {
+  if (!c || !in) return fail(c, CMC_EINVAL, "cmc_set_escaped: bad arguments");
+  for (int s = 0; s < 2 * c->L.n_seg; ++s)
+    if (!std::isfinite(in[s])) return fail(c, CMC_EINVAL, "cmc_set_escaped: non-finite value");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaMemcpyAsync(c->L.esc_me, in, sizeof(double) * 2 * c->L.n_seg,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "cmc_set_escaped");
+  return CMC_OK;
+}
+
 int32_t cmc_kernels_per_step(const cmc_ctx* c) { return c ? c->kernels_per_step : 0; }
 
 cmc_status cmc_get_tuning(const cmc_ctx* c, int32_t* out) {
@@ -562,6 +590,7 @@ cmc_status cmc_get_tuning(const cmc_ctx* c, int32_t* out) {
   out[0] = c->cfg.orbit_block;
   out[1] = c->W.ipt;
   out[2] = c->W.rank;
+  out[3] = c->orbit_variant;
   return CMC_OK;
 }
 
@@ -753,7 +782,7 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
     d.phi_new = phi_new; d.rmin = rmin; d.rmax = rmax; d.F = F; d.code = code;
     if (!e)
       launch_orbit(S.L, precision, max_trials, r, x, phi, t32, sl, vr, vt, mm, id, dstep, keys,
-                   pay, &d, 0, bk.args(), st);
+                   pay, &d, 0, 0, bk.args(), st);
     free_buckets(bk, st);
     dfree(sl, st);
     launch_unpack_orbit(n, keys, pay, r_new, vr_new, vt_new, st);

@@ -37,6 +37,7 @@ struct SegLayout {
   uint64_t* dt_bits = nullptr;
   uint64_t* dt_last = nullptr;      // timestep of the last completed step
   unsigned long long* stats = nullptr;
+  double* esc_me = nullptr;         // [n_seg][2]: mass, energy carried off by escapers
 
   Seg dev() const {
     Seg s;
@@ -95,7 +96,10 @@ void launch_tiefix(const SegLayout& L, const uint64_t* keys, uint32_t* vals,
 void launch_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out,
                    cudaStream_t st);
 
-struct Payload {     // one star between the orbit step and the sort (48 B)
+// One star between the orbit step and the sort (48 B).  c: for a bound
+// star Phi_old(r_old) - Phi_old(r_new); for a star escaping in this step
+// its energy in the field of the others, Phi_k + m_k / r_k + v^2 / 2.
+struct Payload {
   double vr, vt, m, r_old, c;
   uint32_t id, pad;
 };
@@ -178,9 +182,16 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   const double* vr,
                   const double* vt, const double* m, const uint32_t* id, const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
-                  const BucketArgs& ba, cudaStream_t st);
+                  int variant, const BucketArgs& ba, cudaStream_t st);
+// mixed-mode orbit variants: 0 F samples in groups of 7; 1 groups of 3;
+// 2 and 3 groups of 3 with registers capped at 64 and 85 (4 and 3 resident
+// 256-thread blocks); 4 groups of 7 capped at 128
+constexpr int kOrbitVariants = 5;
 
-void launch_step_end(const SegLayout& L, uint32_t* step, cudaStream_t st);
+// commits the step: nb, escaper statistics and budget (from the gathered
+// r_old and c of the escaped range), dt; resets the per-step counters
+void launch_step_end(const SegLayout& L, uint32_t* step, const double* r_old, const double* c,
+                     const double* m, cudaStream_t st);
 
 // energy diagnostics: per-segment K, W_pair (Mbuf receives M_k)
 void launch_energy(const SegLayout& L, const double* r, const double* vr, const double* vt,

@@ -78,6 +78,41 @@ __device__ __forceinline__ double shell_root_M(const Table64& T, const double* M
   return root;
 }
 
+// r_min in mixed mode: the shell root above, or inside the innermost node
+// (j < 0, where Phi = Phi_0) J / sqrt(2 (E - Phi_0)) as central_root64
+// computes it; both take one square root and one division, so the two
+// cases share them (B = 0 makes B + sqrt(D) the bare root) and a warp
+// holding both kinds of star runs them once
+__device__ __forceinline__ double rmin_M(const Table64& T, const double* M, const Star& s,
+                                         int64_t j) {
+  const bool central = j < 0;
+  const int64_t jj = central ? 0 : j;
+  const double rj = __ldg(T.r + jj), xj = __ldg(T.x + jj), pj = __ldg(T.phi + jj);
+  const double B = central ? 0.0 : __ldg(M + jj);
+  double D, num;
+  if (central) {
+    D = 2.0 * (s.E - pj);
+    num = s.J;
+  } else {
+    const double A = pj + B * xj;
+    D = B * B + 2.0 * (s.J * s.J) * (s.E - A);
+    if (!(D > 0.0)) D = 0.0;
+    num = s.J * s.J;
+  }
+  double root = num / (B + sqrt(D));
+  if (central) {
+    if (!(root >= 0.0)) root = 0.0;
+    if (root > rj) root = rj;
+  } else {
+    if (!(root >= rj)) root = rj;
+    if (j + 1 < T.nb) {
+      const double rj1 = __ldg(T.r + j + 1);
+      if (root > rj1) root = rj1;
+    }
+  }
+  return root;
+}
+
 __device__ __forceinline__ double central_root64(const Table64& T, const Star& s) {
   double rmin = s.J / sqrt(2.0 * (s.E - __ldg(T.phi)));
   if (!(rmin >= 0.0)) rmin = 0.0;
@@ -264,13 +299,32 @@ __device__ __forceinline__ void g32_k(const float2* __restrict__ t, int nb, cons
   }
 }
 
+// Mixed mode: the orbit point r(s) in FP64 from an FP32 shell index sh
+// (moved to the exact shell), Phi from the enclosed-mass slope of its
+// shell (Eq. 6: Phi = Phi_i + M_i (1/r_i - 1/r)), L = J / r and Q.
+__device__ __forceinline__ void point64(const Table64& T, const double* Menc, const Star& st,
+                                        double c0, double c1, double sv, int sh, double& rs,
+                                        double& xs, double& ph, double& L, double& Q) {
+  rs = c0 + c1 * (sv * (3.0 - sv * sv));
+  const int64_t i64 = fix_shell64(T, sh, rs);
+  xs = 1.0 / rs;
+  ph = i64 < 0 ? __ldg(T.phi) : __ldg(T.phi + i64) + __ldg(Menc + i64) * (__ldg(T.x + i64) - xs);
+  L = st.J * xs;
+  Q = 2.0 * (st.E - ph) - L * L;
+}
+
+// |s| above which a mixed-mode trial is tested in FP64 (1 - 1/32)
+constexpr float kEdge32 = 0.96875f;
+
 // (2k + 1) 2^-24 from the top 23 bits of a word: exact in float, in (0, 1)
 __device__ __forceinline__ float u01f(uint32_t hi) {
   return (float)(2u * (hi >> 9) + 1u) * 0x1p-24f;
 }
 
-template <int kPrec>
-__global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const double* r,
+// kPrec: 0 FP64, 1 mixed.  KF: samples of F searched together (7 or 3).
+// kMinB: resident 256-thread blocks to fit (caps registers; 1 = no cap).
+template <int kPrec, int KF, int kMinB>
+__global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, const double* r,
                                                const double* x, const double* phi,
                                                const float2* t32, const double* Menc, const double* vr,
                                                const double* vt, const double* m,
@@ -312,6 +366,8 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
     escaped = true;
     code = 1;
     r_new = __longlong_as_double(0x7FF0000000000000ll);
+    // energy carried off: the star's energy in the field of the others
+    P.c = __ldg(T.phi + k) + P.m / rk + 0.5 * (vrk * vrk + vtk * vtk);
   } else {
     int64_t jmax, jmin;
     Table32 T32{t32 + sb, nbc};
@@ -353,7 +409,7 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
       rmin = jmin < 0 ? central_root64(T, s) : shell_root64(T, s, jmin, false);
     } else {
       rmax = shell_root_M(T, Menc + sb, s, jmax, true);
-      rmin = jmin < 0 ? central_root64(T, s) : shell_root_M(T, Menc + sb, s, jmin, false);
+      rmin = rmin_M(T, Menc + sb, s, jmin);
     }
     const double c0 = 0.5 * (rmax + rmin);
     const double c1 = 0.25 * (rmax - rmin);
@@ -369,6 +425,7 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
         code = 2;
       } else {
         code = 3;
+        double rs_a = 0.0, ph_a = 0.0, Q_a = 0.0;
         for (int t = 0; t < max_trials; ++t) {
           U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
           const double X = u01(w.x, w.y), Xp = u01(w.z, w.w);
@@ -377,34 +434,46 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
           const double g = g64(T, s, c0, c1, sv, rs, ph, Q);
           if (g > F) ++viol;
           if (F * Xp < g) {
-            const double sq = sqrt(Q);
-            U4 sg = philox(idk, step, kTagSgn, 0u, seed);
-            r_new = rs;
-            P.vr = (sg.x & 1u) ? -sq : sq;
-            P.vt = s.J / rs;
-            P.c = __ldg(T.phi + k) - ph;
-            ph_new = ph;
+            rs_a = rs;
+            ph_a = ph;
+            Q_a = Q;
             code = 0;
             trials = t + 1;
             break;
           }
         }
-        if (code == 3) trials = max_trials;
+        if (code == 3) {
+          trials = max_trials;
+        } else {
+          // the accepted point's velocities once the warp's lanes are done
+          const double sq = sqrt(Q_a);
+          U4 sg = philox(idk, step, kTagSgn, 0u, seed);
+          r_new = rs_a;
+          P.vr = (sg.x & 1u) ? -sq : sq;
+          P.vt = s.J / rs_a;
+          P.c = __ldg(T.phi + k) - ph_a;
+          ph_new = ph_a;
+        }
       }
     } else {
       const float c0f = (float)c0, c1f = (float)c1;
       const int nb32 = (int)nbc;
       float gmax = 0.0f;
-      // the 21 samples of g in three groups of 7 independent searches
+      // the 21 samples of g in groups of KF independent searches.  F only
+      // has to bound g: 1.2 max g over the FP32 samples is as valid an
+      // envelope as the FP64 one (it differs from it by up to ~1e-4 at the
+      // outer samples, so the two modes draw different, equally exact,
+      // accept sequences)
 #pragma unroll 1
-      for (int j0 = 0; j0 < 21; j0 += 7) {
-        float sj[7], g[7];
-        int sh[7];
+      static_assert(21 % KF == 0, "whole groups of samples");
+      for (int j0 = 0; j0 < 21; j0 += KF) {
+        float sj[KF], g[KF];
+        int sh[KF];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) sj[q] = c_s32[j0 + q];
-        g32_k<7>(T32.t, nb32, BK, E32, J32, c0f, c1f, sj, g, sh);
+        for (int q = 0; q < KF; ++q) sj[q] = c_s32[j0 + q];
+        g32_k<KF>(T32.t, nb32, BK, E32, J32, c0f, c1f, sj, g, sh);
 #pragma unroll
-        for (int q = 0; q < 7; ++q) gmax = g[q] > gmax ? g[q] : gmax;
+        for (int q = 0; q < KF; ++q) gmax = g[q] > gmax ? g[q] : gmax;
       }
       const float F32 = 1.2f * gmax;
       F = (double)F32;
@@ -412,6 +481,8 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
         code = 2;
       } else {
         code = 3;
+        U4 w_a{0u, 0u, 0u, 0u};
+        int sh_a = 0;
         // trials in pairs: both are drawn and tested, the first accepted wins
         for (int t = 0; t < max_trials && code == 3; t += 2) {
           U4 w[2];
@@ -424,33 +495,49 @@ __global__ void __launch_bounds__(256) k_orbit(Seg S, int max_trials, const doub
             xp32[q] = u01f(w[q].w);
           }
           g32_k<2>(T32.t, nb32, BK, E32, J32, c0f, c1f, sv32, g, sh);
-          for (int q = 0; q < 2 && t + q < max_trials; ++q) {
-            if (g[q] > F32) ++viol;
-            if (!(F32 * xp32[q] < g[q])) continue;
-            // recompute the accepted point in FP64 from the full 53-bit X
-            const double sv = 2.0 * u01(w[q].x, w[q].y) - 1.0;
-            const double rs = c0 + c1 * (sv * (3.0 - sv * sv));
-            const int64_t i64 = fix_shell64(T, sh[q], rs);
-            const double xs = 1.0 / rs;
-            const double ph = i64 < 0 ? __ldg(T.phi)
-                                      : __ldg(T.phi + i64) +
-                                            __ldg(Menc + sb + i64) * (__ldg(T.x + i64) - xs);
-            const double L = s.J * xs;
-            double Q = 2.0 * (s.E - ph) - L * L;
-            if (!(Q > 0.0)) Q = 0.0;
-            const double sq = sqrt(Q);
-            U4 sg = philox(idk, step, kTagSgn, 0u, seed);
-            r_new = rs;
-            P.vr = (sg.x & 1u) ? -sq : sq;
-            P.vt = L;
-            P.c = __ldg(T.phi + k) - ph;
-            ph_new = ph;
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            if (t + q >= max_trials) break;
+            // within 1/32 of a turning point Q vanishes like (1 - |s|)^2
+            // while the FP32 r(s) carries an error ~eps32 r: there the
+            // test is taken in FP64 (about 3% of the trials)
+            const bool edge = fabsf(sv32[q]) > kEdge32;
+            if (!edge) {
+              if (g[q] > F32) ++viol;
+              if (!(F32 * xp32[q] < g[q])) continue;
+            } else {
+              const double sv = 2.0 * u01(w[q].x, w[q].y) - 1.0;
+              double rs, xs, ph, L, Q;
+              point64(T, Menc + sb, s, c0, c1, sv, sh[q], rs, xs, ph, L, Q);
+              const double g64v = Q > 0.0 ? ((3.0 * c1) * (1.0 - sv * sv)) / sqrt(Q) : 0.0;
+              if (g64v > F) ++viol;
+              if (!(F * u01(w[q].z, w[q].w) < g64v)) continue;
+            }
+            w_a = w[q];
+            sh_a = sh[q];
             code = 0;
             trials = t + q + 1;
             break;
           }
         }
-        if (code == 3) trials = max_trials;
+        if (code == 3) {
+          trials = max_trials;
+        } else {
+          // the accepted point in FP64 from the full 53-bit X, once per
+          // star after the loop, when the warp's lanes are done (inside
+          // the loop it ran once per pass with the few lanes accepting)
+          const double sv = 2.0 * u01(w_a.x, w_a.y) - 1.0;
+          double rs, xs, ph, L, Q;
+          point64(T, Menc + sb, s, c0, c1, sv, sh_a, rs, xs, ph, L, Q);
+          if (!(Q > 0.0)) Q = 0.0;
+          const double sq = sqrt(Q);
+          U4 sg = philox(idk, step, kTagSgn, 0u, seed);
+          r_new = rs;
+          P.vr = (sg.x & 1u) ? -sq : sq;
+          P.vt = L;
+          P.c = __ldg(T.phi + k) - ph;
+          ph_new = ph;
+        }
       }
     }
   }
@@ -583,18 +670,22 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   const double* vr, const double* vt, const double* m, const uint32_t* id,
                   const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
-                  const BucketArgs& ba, cudaStream_t st) {
+                  int variant, const BucketArgs& ba, cudaStream_t st) {
   if (!L.n) return;
   OrbitStageOut d;
   if (dbg) d = *dbg;
   if (block <= 0) block = 64;
   const unsigned grid = (unsigned)((L.n + block - 1) / block);
-  if (precision == 1)
-    k_orbit<1><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, m, id, step,
-                                       keys, pay, L.esc_step, d, ba, L.n);
-  else
-    k_orbit<0><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, m, id, step,
-                                       keys, pay, L.esc_step, d, ba, L.n);
+#define CMC_ORBIT(P, K, B)                                                                   \
+  k_orbit<P, K, B><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, \
+                                           m, id, step, keys, pay, L.esc_step, d, ba, L.n)
+  if (precision == 0) CMC_ORBIT(0, 7, 1);
+  else if (variant == 1) CMC_ORBIT(1, 3, 1);
+  else if (variant == 2) CMC_ORBIT(1, 3, 4);
+  else if (variant == 3) CMC_ORBIT(1, 3, 3);
+  else if (variant == 4) CMC_ORBIT(1, 7, 2);
+  else CMC_ORBIT(1, 7, 1);
+#undef CMC_ORBIT
 }
 
 }  // namespace cmc

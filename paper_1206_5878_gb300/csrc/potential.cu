@@ -339,16 +339,47 @@ __global__ void k_check_ids(int64_t n, const int64_t* off, int n_seg, const uint
   if (p + 1 < off[c + 1] && ids[p] == ids[p + 1]) set_err(err, kErrInput);
 }
 
-__global__ void k_step_end(Seg S, int64_t* esc, uint64_t* dt_last, uint32_t* step) {
-  for (int c = threadIdx.x; c < S.n_seg; c += blockDim.x) {
-    int64_t e = esc[c];
+// One 256-thread block per segment.  The stars that escaped in this step
+// are the escaped range's entries with a finite r_old (earlier escapers
+// carry r_old = inf); their mass and energy m_k e_k (e_k in c) are summed
+// in a fixed order and added to the segment's budget (section 4.2).
+__global__ void __launch_bounds__(256) k_step_end(Seg S, int64_t* esc, uint64_t* dt_last,
+                                                  uint32_t* step, const double* r_old,
+                                                  const double* e, const double* m,
+                                                  double* esc_me) {
+  __shared__ double s_m[256], s_e[256];
+  const int c = blockIdx.x, t = threadIdx.x;
+  const int64_t ne = esc[c];
+  const int64_t nb_new = S.nb[c] - ne;
+  double dm = 0.0, de = 0.0;
+  if (ne > 0)
+    for (int64_t p = S.off[c] + nb_new + t; p < S.off[c + 1]; p += 256)
+      if (isfinite(r_old[p])) {
+        dm += m[p];
+        de += m[p] * e[p];
+      }
+  s_m[t] = dm;
+  s_e[t] = de;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (t < w) {
+      s_m[t] += s_m[t + w];
+      s_e[t] += s_e[t + w];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    if (ne > 0) {
+      esc_me[2 * c] += s_m[0];
+      esc_me[2 * c + 1] += s_e[0];
+    }
     dt_last[c] = S.dt_bits[c];
-    S.nb[c] -= e;
-    S.stats[(size_t)c * kStStride + kStEscaped] += (unsigned long long)e;
+    S.nb[c] = nb_new;
+    S.stats[(size_t)c * kStStride + kStEscaped] += (unsigned long long)ne;
     esc[c] = 0;
     S.dt_bits[c] = 0x7FF0000000000000ull;
+    if (c == 0) *step += 1u;
   }
-  if (threadIdx.x == 0) *step += 1u;
 }
 
 __global__ void k_nb_from_keys(Seg S, const uint64_t* keys) {
@@ -446,6 +477,7 @@ cudaError_t alloc_layout(SegLayout& L, const std::vector<int64_t>& sizes,
   CMC_A(L.dt_bits, sizeof(uint64_t) * L.n_seg);
   CMC_A(L.dt_last, sizeof(uint64_t) * L.n_seg);
   CMC_A(L.stats, sizeof(unsigned long long) * kStStride * L.n_seg);
+  CMC_A(L.esc_me, sizeof(double) * 2 * L.n_seg);
 #undef CMC_A
   cudaMemcpyAsync(L.off, L.h_off.data(), s1, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(L.tile_off, L.h_tile_off.data(), s1, cudaMemcpyHostToDevice, st);
@@ -460,13 +492,14 @@ cudaError_t alloc_layout(SegLayout& L, const std::vector<int64_t>& sizes,
   cudaMemcpyAsync(L.dt_bits, inf.data(), sizeof(uint64_t) * L.n_seg, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(L.dt_last, inf.data(), sizeof(uint64_t) * L.n_seg, cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(L.stats, 0, sizeof(unsigned long long) * kStStride * L.n_seg, st);
+  cudaMemsetAsync(L.esc_me, 0, sizeof(double) * 2 * L.n_seg, st);
   // the host vectors above must outlive the copies
   return cudaStreamSynchronize(st);
 }
 
 void free_layout(SegLayout& L, cudaStream_t st) {
   void* ps[] = {L.off, L.tile_off, L.pair_off, L.bin_off, L.seed, L.lnL,
-                L.nb, L.esc_step, L.dt_bits, L.dt_last, L.stats};
+                L.nb, L.esc_step, L.dt_bits, L.dt_last, L.stats, L.esc_me};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, st);
   L = SegLayout();
@@ -546,8 +579,10 @@ void launch_check_ids(const SegLayout& L, const uint64_t* sorted_ids, uint32_t* 
     k_check_ids<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.off, L.n_seg, sorted_ids, err);
 }
 
-void launch_step_end(const SegLayout& L, uint32_t* step, cudaStream_t st) {
-  k_step_end<<<1, 256, 0, st>>>(L.dev(), L.esc_step, L.dt_last, step);
+void launch_step_end(const SegLayout& L, uint32_t* step, const double* r_old, const double* c,
+                     const double* m, cudaStream_t st) {
+  k_step_end<<<L.n_seg, 256, 0, st>>>(L.dev(), L.esc_step, L.dt_last, step, r_old, c, m,
+                                      L.esc_me);
 }
 
 }  // namespace cmc

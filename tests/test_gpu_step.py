@@ -87,14 +87,17 @@ def test_one_step_matches_oracle(g, orc, n):
     _compare_states(c.get_state(), o)
     assert c.nbound()[0] == o.nb
     assert c.dt()[0] == o.last_dt  # same bins, same stars, same order
+    # escaper budget: same stars, same per-star energy, other summation order
+    np.testing.assert_allclose(c.escaped()[0], o.escaped, rtol=1e-13, atol=0)
     s = c.stats()[0]
     for k in ("escaped", "degenerate", "cap_hits", "trials", "violations", "clamps"):
         assert s[k] == o.last_stats[k], k
 
 
 def test_ten_steps_plummer_1e4_fp64(g, orc):
-    """Plummer N = 10^4, FP64, 10 steps against the oracle: energy
-    conserved to the paper's bound on both sides and the same statistics.
+    """Plummer N = 10^4, FP64, 10 steps against the oracle: total energy
+    (bound stars plus what the escapers took) conserved to the paper's
+    bound on both sides and the same statistics.
     The potentials of the two sides differ in the last bits (other
     summation order); star-by-star agreement holds for one step from the
     same state (test_one_step_matches_oracle) and bit for bit stage by
@@ -102,7 +105,7 @@ def test_ten_steps_plummer_1e4_fp64(g, orc):
     d = ic.plummer(10_000, seed=1)
     c = _cluster(g, d, 1)
     o = orc.Cluster(d["r"], d["vr"], d["vt"], d["m"], d["id"], seed=1, pot_mode="dd")
-    E0 = c.energy()[0][2]
+    E0 = c.total_energy()[0]
     bound = paper_values()["energy_drift_bound"]
     for step in range(10):
         c.step(1)
@@ -114,9 +117,9 @@ def test_ten_steps_plummer_1e4_fp64(g, orc):
         # within a few steps the trajectories decorrelate star by star and
         # agree only statistically (energy, mass profile, escapers)
         assert abs(int(c.nbound()[0]) - o.nb) <= 5
-        assert abs(c.energy()[0][2] / E0 - 1) < bound
-        assert abs(o.energy()[2] / E0 - 1) < bound
-        assert abs(c.energy()[0][2] / o.energy()[2] - 1) < 2 * bound
+        assert abs(c.total_energy()[0] / E0 - 1) < bound
+        assert abs(o.total_energy() / E0 - 1) < bound
+        assert abs(c.total_energy()[0] / o.total_energy() - 1) < 2 * bound
         # Lagrangian radii within a few times the sampling noise of 10^4 stars
         np.testing.assert_allclose(c.lagrange_radii([0.1, 0.5, 0.9])[0],
                                    o.lagrange_radii([0.1, 0.5, 0.9]), rtol=0.08)
@@ -141,6 +144,7 @@ def test_ensemble_equals_separate_runs(g):
         assert ens.dt()[i] == one.dt()[0]
         assert ens.stats()[i] == one.stats()[0]
         np.testing.assert_array_equal(ens.energy()[i], one.energy()[0])
+        np.testing.assert_array_equal(ens.escaped()[i], one.escaped()[0])
 
 
 def test_resume_is_bit_identical(g):
@@ -152,32 +156,42 @@ def test_resume_is_bit_identical(g):
     mid = b.get_state()
     c = _cluster(g, d, 3)
     c.set_state(mid, mid["step"])
+    c.set_escaped(b.escaped())
     c.step(3)
     sa, sc = a.get_state(), c.get_state()
     for k in ("r", "vr", "vt", "m", "id", "phi"):
         np.testing.assert_array_equal(sa[k], sc[k], err_msg=k)
     assert sc["step"] == 6
+    np.testing.assert_array_equal(a.escaped(), c.escaped())
 
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_launch_shape_does_not_change_bits(g, precision):
     d = ic.plummer(20_000, seed=4)
     outs = []
-    for blk in (32, 128, 256):
-        c = _cluster(g, d, 4, orbit_block=blk, precision=precision)
+    shapes = [(32, 0), (128, 0), (256, 0)]
+    if precision == 1:
+        shapes += [(64, v) for v in range(1, 5)]
+    for blk, var in shapes:
+        c = _cluster(g, d, 4, orbit_block=blk, precision=precision, orbit_variant=var,
+                     autotune=0)
+        assert c.tuning()["orbit_variant"] == var
         c.step(2)
-        outs.append(c.get_state())
-    for o in outs[1:]:
+        outs.append((c.get_state(), c.stats()))
+    for o, st in outs[1:]:
         for k in ("r", "vr", "vt", "phi"):
-            np.testing.assert_array_equal(o[k], outs[0][k])
+            np.testing.assert_array_equal(o[k], outs[0][0][k])
+        assert st == outs[0][1]
 
 
-def test_autotuned_shapes_do_not_change_bits(g):
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotuned_shapes_do_not_change_bits(g, precision):
     d = ic.plummer(30_001, seed=6, masses="salpeter")
-    a = _cluster(g, d, 6, autotune=0)
-    b = _cluster(g, d, 6, autotune=1, precision=0)
+    a = _cluster(g, d, 6, autotune=0, precision=precision)
+    b = _cluster(g, d, 6, autotune=1, precision=precision)
     ta, tb = a.tuning(), b.tuning()
-    assert ta == {"orbit_block": 64, "sort_keys_per_thread": 16, "sort_multisplit": "match"}
+    assert ta == {"orbit_block": 64, "sort_keys_per_thread": 16, "sort_multisplit": "match",
+                  "orbit_variant": 0}
     assert tb["orbit_block"] in (64, 128, 256) and tb["sort_keys_per_thread"] in (8, 16)
     assert b.stats()[0]["trials"] == 0  # the tuner's dry run left no trace
     a.step(3)
@@ -212,10 +226,10 @@ def test_mixed_precision_plummer_1e4(g, orc):
     whose FP32 accept decision flipped."""
     d = ic.plummer(10_000, seed=2)
     c = _cluster(g, d, 2, precision=1)
-    E0 = c.energy()[0][2]
+    E0 = c.total_energy()[0]
     for _ in range(10):
         c.step(1)
-        assert abs(c.energy()[0][2] / E0 - 1) < paper_values()["energy_drift_bound"]
+        assert abs(c.total_energy()[0] / E0 - 1) < paper_values()["energy_drift_bound"]
     st = c.get_state()
     f64 = _cluster(g, d, 2)
     f32 = _cluster(g, d, 2, precision=1)
@@ -249,9 +263,14 @@ def test_invalid_inputs_are_rejected(g):
         with pytest.raises(g.CMCError) as ei:
             _cluster(g, e, 1)
         assert ei.value.status == 1  # CMC_EINVAL
+    for bad_cfg in ({"orbit_variant": 5}, {"orbit_variant": -2}, {"orbit_block": 48}):
+        with pytest.raises(g.CMCError):
+            _cluster(g, d, 1, **bad_cfg)
     c = _cluster(g, d, 1)
     with pytest.raises(g.CMCError):
         c.step(-1)
     with pytest.raises(g.CMCError):
         c.lagrange_radii([1.5])
+    with pytest.raises(g.CMCError):
+        c.set_escaped([0.0, np.nan])
     c.step(1)  # the context is still usable

@@ -365,6 +365,25 @@ def test_ten_steps_energy_drift_within_paper_bound(orc):
     assert c.step_no == 10 and c.nb >= 9990
 
 
+@pytest.mark.parametrize("j", [0, 3, 7])
+def test_escaper_budget_is_the_energy_removed(orc, j):
+    """The budget of section 4.2 counts what escapers carry off: removing
+    star j from the set lowers K + W (Eqs. 2-5 form of W) by exactly
+    m_j e_j, e_j = Phi_j + m_j / r_j + v_j^2 / 2.  N = 8: ln(gamma N) < 0,
+    so no relaxation changes the escaper's velocity before its orbit step."""
+    d = ic.plummer(8, seed=5, masses="salpeter")
+    c = orc.Cluster(d["r"], d["vr"], d["vt"], d["m"], d["id"], seed=5)
+    assert c.lnL <= 0
+    c.vt[j] = 4.0 * math.sqrt(-2.0 * c.phi[j])  # E_j > 0
+    E_all = orc.energy(c.r, c.vr, c.vt, c.m)[2]
+    keep = np.arange(8) != j
+    E_rest = orc.energy(c.r[keep], c.vr[keep], c.vt[keep], c.m[keep])[2]
+    mj = c.m[j]
+    c.step()
+    assert c.last_stats["escaped"] == 1 and c.escaped[0] == mj
+    assert abs(c.escaped[1] - (E_all - E_rest)) < 1e-14 * abs(E_all)
+
+
 @pytest.mark.parametrize("n", [1, 2, 3, 9, 10, 11, 41])
 def test_tiny_clusters_stay_finite(orc, n):
     """ln(gamma N) <= 0 for N <= 1/gamma: no relaxation there, and every
