@@ -158,8 +158,13 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
                    mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, true, st);
   if (mixed) launch_buckets(L, c->t32, true, c->bk, st);
   mark(6);
-  if (c->cfg.energy_correction)
-    launch_correction(L, c->r, c->x, c->phi, c->vr, c->vt, c->r_old, c->cc, true, c->err, st);
+  if (c->cfg.energy_correction) {
+    if (mixed)
+      launch_correction_mixed(L, c->r, c->x, c->phi, c->t32, c->Mbuf, c->bk.args(), c->vr, c->vt,
+                              c->r_old, c->cc, st);
+    else
+      launch_correction(L, c->r, c->x, c->phi, c->vr, c->vt, c->r_old, c->cc, true, c->err, st);
+  }
   mark(7);
   launch_step_end(L, c->step, c->r_old, c->cc, c->m, st);
   mark(8);
@@ -386,6 +391,7 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   if (!e && cfg.precision == 1) e = alloc_buckets(c->bk, L, st);
   if (e) { cmc_status s = cuda_fail(nullptr, e, "cmc_init: allocation"); free_ctx(c); return s; }
   sort_prepare();
+  potential_prepare();
   cmc_status s = load_state(c, r, vr, vt, m, id, ptr_kind, false, 0);
   if (s != CMC_OK) {
     g_err = c->last_error;
@@ -687,6 +693,7 @@ cmc_status cmc_potential(int64_t n, const double* r, const double* m, double* ph
   if (!e) e = dalloc(ta, (size_t)S.L.n_tiles, st);
   if (!e) e = dalloc(tb, (size_t)S.L.n_tiles, st);
   if (!e) {
+    potential_prepare();
     launch_recip(n, r, x, st);
     launch_potential(S.L, r, x, m, ta, tb, phi, nullptr, M, false, st);
     e = cudaGetLastError();

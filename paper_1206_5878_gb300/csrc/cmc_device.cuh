@@ -90,28 +90,80 @@ __device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint
 
 // (2k + 1) 2^-53 from the top 52 bits k of (hi:lo): exact, inside (0, 1)
 __device__ __forceinline__ double u01(uint32_t lo, uint32_t hi) {
-  uint64_t k = ((((uint64_t)hi) << 32) | lo) >> 12;
-  return (double)(2ull * k + 1ull) * 0x1p-53;
+  // (2k + 1) 2^-53 is exact: its bits are assembled with integer operations
+  // (leading-zero count, shift, exponent) instead of an int -> double
+  // conversion and a multiply on the FP64 pipe
+  const uint64_t k = ((((uint64_t)hi) << 32) | lo) >> 12;
+  const uint64_t mo = 2ull * k + 1ull;  // odd, < 2^53
+  const int lz = __clzll((long long)mo) - 11;
+  const uint64_t mm = mo << lz;  // top bit at 52
+  return __longlong_as_double(
+      (long long)(((uint64_t)(1022 - lz) << 52) | (mm & 0x000FFFFFFFFFFFFFull)));
+}
+
+// 2 X - 1 for X = u01(lo, hi) equals U 2^-52 exactly, U = 2k + 1 - 2^52 (odd,
+// |U| < 2^52); sym_int gives U, sym_double the double
+__device__ __forceinline__ int64_t sym_int(uint32_t lo, uint32_t hi) {
+  const uint64_t k = ((((uint64_t)hi) << 32) | lo) >> 12;
+  return (int64_t)(2ull * k + 1ull) - (int64_t)(1ull << 52);
+}
+__device__ __forceinline__ double sym_double(int64_t U) {
+  const uint64_t a = U < 0 ? (uint64_t)(-U) : (uint64_t)U;
+  const int lz = __clzll((long long)a) - 11;
+  const uint64_t aa = a << lz;
+  return __longlong_as_double((long long)((U < 0 ? 0x8000000000000000ull : 0ull) |
+                                          ((uint64_t)(1023 - lz) << 52) |
+                                          (aa & 0x000FFFFFFFFFFFFFull)));
 }
 
 // uniform planar direction (cos a, sin a) by rejection of a point in the
 // unit disk; the doubled angle gives cos = (u^2 - v^2)/q, sin = 2uv/q.
+//
+// The draw (u, v) = (U, V) 2^-52 is accepted when the FP64 value of
+// u u + v v is <= 1.  That value is within 2^-51 of the exact sum (both
+// below 2), so outside a band of 2^54 around 2^104 the exact integer test
+// U^2 + V^2 <= 2^104 (128-bit) gives the same answer; inside the band the
+// FP64 expression decides.  The loop is integer work only; the FP64
+// arithmetic of the accepted draw runs once, after it.
 __device__ __forceinline__ bool disk_angle(uint64_t seed, uint32_t id, uint32_t step,
                                            uint32_t tag, double& c, double& s) {
+  int64_t Ua = 0, Va = 0;
+  bool ok = false;
   for (uint32_t t = 0; t < 64u; ++t) {
     U4 w = philox(id, step, tag, t, seed);
-    double u = 2.0 * u01(w.x, w.y) - 1.0;
-    double v = 2.0 * u01(w.z, w.w) - 1.0;
-    double uu = u * u, vv = v * v, q = uu + vv;
-    if (q <= 1.0) {
-      const double iq = 1.0 / q;
-      c = (uu - vv) * iq;
-      s = ((2.0 * u) * v) * iq;
-      return true;
+    const int64_t U = sym_int(w.x, w.y), V = sym_int(w.z, w.w);
+    const uint64_t A = U < 0 ? (uint64_t)(-U) : (uint64_t)U;
+    const uint64_t B = V < 0 ? (uint64_t)(-V) : (uint64_t)V;
+    const uint64_t l1 = A * A, l2 = B * B;
+    const uint64_t lo = l1 + l2;
+    const uint64_t hi = __umul64hi(A, A) + __umul64hi(B, B) + (lo < l1 ? 1ull : 0ull);
+    // S = hi 2^64 + lo against 2^104 -+ 2^54
+    const uint64_t H = 1ull << 40, band = 1ull << 54;
+    bool in = hi < H - 1 || (hi == H - 1 && lo <= 0ull - band);
+    const bool out = hi > H || (hi == H && lo >= band);
+    if (!in && !out) {
+      const double u = sym_double(U), v = sym_double(V);
+      const double uu = u * u, vv = v * v;
+      in = uu + vv <= 1.0;
+    }
+    if (in) {
+      Ua = U;
+      Va = V;
+      ok = true;
+      break;
     }
   }
-  c = 1.0; s = 0.0;
-  return false;
+  if (!ok) {
+    c = 1.0;
+    s = 0.0;
+    return false;
+  }
+  const double u = sym_double(Ua), v = sym_double(Va);
+  const double uu = u * u, vv = v * v, q = uu + vv;
+  const double iq = 1.0 / q;
+  c = (uu - vv) * iq;
+  s = ((2.0 * u) * v) * iq;
+  return true;
 }
 
 // ------------------------------------------------------------ sort keys

@@ -190,6 +190,13 @@ constexpr int kOrbitVariants = 5;
 
 // commits the step: nb, escaper statistics and budget (from the gathered
 // r_old and c of the escaped range), dt; resets the per-step counters
+// energy correction in mixed mode: shell of r_old from the bucket index of
+// the new table (nb - esc_step bound stars), Phi from the enclosed mass
+void launch_correction_mixed(const SegLayout& L, const double* r, const double* x,
+                             const double* phi, const float2* t32, const double* Menc,
+                             const BucketArgs& ba, double* vr, double* vt, const double* r_old,
+                             const double* c, cudaStream_t st);
+
 void launch_step_end(const SegLayout& L, uint32_t* step, const double* r_old, const double* c,
                      const double* m, cudaStream_t st);
 
@@ -213,6 +220,7 @@ void launch_make_t32(int64_t n, const double* x, const double* phi, float2* t32,
 void launch_unpack_orbit(int64_t n, const uint64_t* keys, const Payload* pay, double* r_new,
                          double* vr_new, double* vt_new, cudaStream_t st);
 void sort_prepare();
+void potential_prepare();  // shared-memory limit of the potential kernel
 
 void launch_check_ids(const SegLayout& L, const uint64_t* sorted_ids, uint32_t* err,
                       cudaStream_t st);

@@ -428,8 +428,8 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
         double rs_a = 0.0, ph_a = 0.0, Q_a = 0.0;
         for (int t = 0; t < max_trials; ++t) {
           U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
-          const double X = u01(w.x, w.y), Xp = u01(w.z, w.w);
-          const double sv = 2.0 * X - 1.0;
+          const double Xp = u01(w.z, w.w);
+          const double sv = sym_double(sym_int(w.x, w.y));  // 2 X - 1, exact
           double rs, ph, Q;
           const double g = g64(T, s, c0, c1, sv, rs, ph, Q);
           if (g > F) ++viol;
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
               if (g[q] > F32) ++viol;
               if (!(F32 * xp32[q] < g[q])) continue;
             } else {
-              const double sv = 2.0 * u01(w[q].x, w[q].y) - 1.0;
+              const double sv = sym_double(sym_int(w[q].x, w[q].y));
               double rs, xs, ph, L, Q;
               point64(T, Menc + sb, s, c0, c1, sv, sh[q], rs, xs, ph, L, Q);
               const double g64v = Q > 0.0 ? ((3.0 * c1) * (1.0 - sv * sv)) / sqrt(Q) : 0.0;
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
           // the accepted point in FP64 from the full 53-bit X, once per
           // star after the loop, when the warp's lanes are done (inside
           // the loop it ran once per pass with the few lanes accepting)
-          const double sv = 2.0 * u01(w_a.x, w_a.y) - 1.0;
+          const double sv = sym_double(sym_int(w_a.x, w_a.y));
           double rs, xs, ph, L, Q;
           point64(T, Menc + sb, s, c0, c1, sv, sh_a, rs, xs, ph, L, Q);
           if (!(Q > 0.0)) Q = 0.0;
@@ -566,6 +566,57 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
   if (dbg.F) dbg.F[p] = F;
   if (dbg.code) dbg.code[p] = code;
   if (dbg.trials) dbg.trials[p] = trials;
+}
+
+// Energy correction (section 2.1 step 6) in mixed mode, after the new
+// potential and its bucket index: the shell of r_old in the new table from
+// the index (FP32 1/r, moved to the exact FP64 shell by integer compares of
+// the radii), Phi_new(r_old) = Phi_i + M_i (1/r_i - 1/r_old) from the
+// enclosed mass of that shell (Eq. 6 without its division), then
+// T' = T + 1/2 [(Phi_new(r_old) - Phi_new,k) - c] clamped at 0 and both
+// velocity components scaled by sqrt(T'/T), as in the FP64 kernel.
+__global__ void __launch_bounds__(128) k_correction_mixed(Seg S, const int64_t* esc,
+                                                          const double* r, const double* x,
+                                                          const double* phi, const float2* t32,
+                                                          const double* Menc, BucketArgs BA,
+                                                          double* vr, double* vt,
+                                                          const double* r_old, const double* cc,
+                                                          int64_t n) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int c = seg_find(S.off, S.n_seg, p);
+  const int64_t sb = __ldg(S.off + c);
+  const int64_t nbc = S.nb[c] - esc[c];
+  if (p - sb >= nbc) return;
+  const Table64 T{r + sb, x + sb, phi + sb, nbc};
+  const double ro = r_old[p];
+  const double xo = 1.0 / ro;
+  Buckets BK;
+  const int4 pr = BA.prm[c];
+  BK.start = BA.start + BA.off[c];
+  BK.base = BA.base[c];
+  BK.shift = pr.x;
+  BK.nbk = pr.y;
+  BK.lo = pr.z;
+  BK.hi = pr.w;
+  const float xq[1] = {(float)xo};
+  int sh[1];
+  shells32_bk<1>(t32 + sb, (int)nbc, BK, xq, sh);
+  const int64_t i = fix_shell64(T, sh[0], ro);
+  const double pn = i < 0 ? __ldg(T.phi)
+                          : __ldg(T.phi + i) + __ldg(Menc + sb + i) * (__ldg(T.x + i) - xo);
+  const double a = vr[p], b = vt[p];
+  const double Tk = 0.5 * (a * a + b * b);
+  const double dnew = pn - phi[p];
+  double Tp = Tk + 0.5 * (dnew - cc[p]);
+  bool clamp = false;
+  if (Tp < 0.0) { Tp = 0.0; clamp = true; }
+  if (Tk > 0.0) {
+    const double f = sqrt(Tp / Tk);
+    vr[p] = a * f;
+    vt[p] = b * f;
+  }
+  if (clamp) stat_add(S.stats, c, kStClamps, 1ull);
 }
 
 // per segment: the indexed node range lo..hi, base = bits(x_lo), the
@@ -663,6 +714,15 @@ void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWo
       L.dev(), L.esc_step, nb_sub, t32, B.args(), B.base, B.prm);
   k_bucket_build<<<(unsigned)((L.n + 255) / 256), 256, 0, st>>>(L.dev(), L.esc_step, nb_sub,
                                                                t32, B.args(), B.start, L.n);
+}
+
+void launch_correction_mixed(const SegLayout& L, const double* r, const double* x,
+                             const double* phi, const float2* t32, const double* Menc,
+                             const BucketArgs& ba, double* vr, double* vt, const double* r_old,
+                             const double* c, cudaStream_t st) {
+  if (!L.n) return;
+  k_correction_mixed<<<(unsigned)((L.n + 127) / 128), 128, 0, st>>>(
+      L.dev(), L.esc_step, r, x, phi, t32, Menc, ba, vr, vt, r_old, c, L.n);
 }
 
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,

@@ -130,19 +130,27 @@ __global__ void k_gather(int64_t n, const uint64_t* __restrict__ keys,
 }
 
 // ------------------------------------------------------------ potential
+// padded shared-memory slot of tile element e: one spare double per 16, so
+// that a thread walking its 16 consecutive elements (stride 17 words across
+// the warp) and a warp reading 32 consecutive elements both stay within
+// two shared-memory wavefronts
+__device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
+constexpr int kPadN = kTile + kTile / 16;
+
+// per-tile sums of m and m x (striped, coalesced loads; fixed tree)
 __global__ void __launch_bounds__(kThreads) k_tile_sums(Seg S, const int64_t* esc, bool sub,
                                                         const double* x, const double* m,
                                                         double* tile_m, double* tile_mx) {
   __shared__ double s[kThreads];
   TR R = tile_of(S, esc, blockIdx.x, sub);
   double am = 0.0, ax = 0.0;
-  int64_t b = R.begin + (int64_t)threadIdx.x * kPer;
+#pragma unroll 4
   for (int i = 0; i < kPer; ++i) {
-    int64_t p = b + i;
+    const int64_t p = R.begin + (int64_t)i * kThreads + threadIdx.x;
     if (p < R.end && p < R.bound_end) {
-      double mm = m[p];
+      const double mm = __ldg(m + p);
       am = am + mm;
-      ax = ax + mm * x[p];
+      ax = ax + mm * __ldg(x + p);
     }
   }
   double tm = block_sum(am, s);
@@ -150,60 +158,78 @@ __global__ void __launch_bounds__(kThreads) k_tile_sums(Seg S, const int64_t* es
   if (threadIdx.x == 0) { tile_m[blockIdx.x] = tm; tile_mx[blockIdx.x] = tx; }
 }
 
+// Phi_k = -(M_k x_k + S_k) over one tile.  The tile's m and x are staged in
+// shared memory with coalesced loads; each thread scans its 16 consecutive
+// elements (local suffix sums of m x kept in registers), the per-thread
+// totals are scanned across the block, and the results (Phi, M_k, the
+// float table) leave through shared memory with coalesced stores.
 __global__ void __launch_bounds__(kThreads) k_potential(Seg S, const int64_t* esc, bool sub,
                                                         const double* x, const double* m,
                                                         const double* tile_m,
                                                         const double* tile_mx, double* phi,
                                                         float2* t32, double* Mout) {
+  extern __shared__ double smem[];
+  double* s_m = smem;              // m, then M_k
+  double* s_x = smem + kPadN;      // x
+  double* s_p = smem + 2 * kPadN;  // Phi
   __shared__ double s1[kThreads], s2[kThreads];
   TR R = tile_of(S, esc, blockIdx.x, sub);
   const int64_t t0 = blockIdx.x - R.lt;
+  const int t = threadIdx.x;
   // tiles before (M) and after (S) this one, in a fixed order
   double pm = 0.0, ps = 0.0;
-  for (int64_t j = threadIdx.x; j < R.nt; j += kThreads) {
+  for (int64_t j = t; j < R.nt; j += kThreads) {
     if (j < R.lt) pm = pm + tile_m[t0 + j];
     if (j > R.lt) ps = ps + tile_mx[t0 + j];
   }
-  double Mbefore = block_sum(pm, s1);
-  double Safter = block_sum(ps, s1);
-  // the thread's 16 consecutive elements
-  const int64_t b = R.begin + (int64_t)threadIdx.x * kPer;
-  double mm[kPer], xx[kPer];
-  double am = 0.0, ax = 0.0;
-#pragma unroll
+  const double Mbefore = block_sum(pm, s1);
+  const double Safter = block_sum(ps, s1);
+#pragma unroll 4
   for (int i = 0; i < kPer; ++i) {
-    int64_t p = b + i;
-    bool ok = p < R.end && p < R.bound_end;
-    mm[i] = ok ? m[p] : 0.0;
-    xx[i] = ok ? x[p] : 0.0;
-    am = am + mm[i];
-    ax = ax + mm[i] * xx[i];
+    const int e = i * kThreads + t;
+    const int64_t p = R.begin + e;
+    const bool ok = p < R.end && p < R.bound_end;
+    s_m[pad16(e)] = ok ? __ldg(m + p) : 0.0;
+    s_x[pad16(e)] = ok ? __ldg(x + p) : 0.0;
   }
+  __syncthreads();
+  const int e0 = t * kPer;
+  // exclusive suffix of m x along the thread's run, and its total
+  double suf[kPer];
+  double ax = 0.0;
+#pragma unroll
+  for (int i = kPer - 1; i >= 0; --i) {
+    suf[i] = ax;
+    ax = ax + s_m[pad16(e0 + i)] * s_x[pad16(e0 + i)];
+  }
+  double am = 0.0;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) am = am + s_m[pad16(e0 + i)];
   double pre_m, suf_s;
   block_scans(am, ax, s1, s2, pre_m, suf_s);
-  // inclusive M along the thread's run; exclusive suffix S from its end
-  double Mk[kPer], Sk[kPer];
+  const double bm = Mbefore + pre_m, bs = Safter + suf_s;
   double run = 0.0;
 #pragma unroll
   for (int i = 0; i < kPer; ++i) {
-    run = run + mm[i];
-    Mk[i] = (Mbefore + pre_m) + run;
+    const int q = pad16(e0 + i);
+    run = run + s_m[q];
+    const double Mk = bm + run;
+    const double ph = -(Mk * s_x[q] + (bs + suf[i]));
+    s_m[q] = Mk;
+    s_p[q] = ph;
   }
-  double suf = 0.0;
-#pragma unroll
-  for (int i = kPer - 1; i >= 0; --i) {
-    Sk[i] = (Safter + suf_s) + suf;
-    suf = suf + mm[i] * xx[i];
-  }
-#pragma unroll
+  __syncthreads();
+#pragma unroll 4
   for (int i = 0; i < kPer; ++i) {
-    int64_t p = b + i;
+    const int e = i * kThreads + t;
+    const int64_t p = R.begin + e;
     if (p >= R.end) break;
-    double ph = 0.0;
-    if (p < R.bound_end) ph = -(Mk[i] * xx[i] + Sk[i]);
+    const bool bound = p < R.bound_end;
+    const int q = pad16(e);
+    const double ph = bound ? s_p[q] : 0.0;
     phi[p] = ph;
-    if (t32) t32[p] = make_float2((float)xx[i], (float)ph);
-    if (Mout) Mout[p] = p < R.bound_end ? Mk[i] : 0.0;
+    if (t32) t32[p] = make_float2((float)s_x[q], (float)ph);
+    if (Mout) Mout[p] = bound ? s_m[q] : 0.0;
   }
 }
 
@@ -528,6 +554,13 @@ void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* val
                                                   r_old, c);
 }
 
+constexpr size_t kPotentialSmem = sizeof(double) * 3 * kPadN;
+
+void potential_prepare() {
+  cudaFuncSetAttribute(k_potential, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)kPotentialSmem);
+}
+
 void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
                       double* tile_m, double* tile_mx, double* phi, float2* t32,
                       double* Mout, bool nb_sub, cudaStream_t st) {
@@ -536,8 +569,8 @@ void launch_potential(const SegLayout& L, const double* r, const double* x, cons
   Seg S = L.dev();
   k_tile_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, L.esc_step, nb_sub, x, m, tile_m,
                                                        tile_mx);
-  k_potential<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, L.esc_step, nb_sub, x, m, tile_m,
-                                                       tile_mx, phi, t32, Mout);
+  k_potential<<<(unsigned)L.n_tiles, kThreads, kPotentialSmem, st>>>(
+      S, L.esc_step, nb_sub, x, m, tile_m, tile_mx, phi, t32, Mout);
 }
 
 void launch_correction(const SegLayout& L, const double* r, const double* x,

@@ -90,3 +90,34 @@ def test_disk_angle_is_unit_and_uniform(orc):
     chi2 = ((counts - len(ang) / 32) ** 2 / (len(ang) / 32)).sum()
     assert chi2 < 70
     assert abs(np.cos(ang).mean()) < 0.03 and abs(np.sin(ang).mean()) < 0.03
+
+
+def test_disk_test_integer_band_argument():
+    """The unit-disk acceptance (u u + v v <= 1 in FP64, u = U 2^-52 with U
+    odd and |U| < 2^52) agrees with the exact integer test U^2 + V^2 <=
+    2^104 wherever |U^2 + V^2 - 2^104| > 2^54: the FP64 sum of two rounded
+    squares below 1 is within 2^-51 of the exact one.  Near-boundary pairs
+    (B the integer square root of 2^104 - A^2, and B + 2) exercise both
+    sides of the circle; inside the band the two tests do disagree, which is
+    why the FP64 expression decides there."""
+    import math
+    rng = np.random.default_rng(11)
+    T, band = 1 << 104, 1 << 54
+    outside = disagree_in_band = 0
+    for A in rng.integers(1 << 40, 1 << 52, 20000):
+        A = int(A) | 1
+        B0 = math.isqrt(T - A * A)
+        for B in (B0 - 2, B0 - 1, B0, B0 + 1, B0 + 2):
+            if B <= 0 or B >= 1 << 52:
+                continue
+            S = A * A + B * B
+            u, v = A * 2.0 ** -52, B * 2.0 ** -52  # exact
+            fp = (u * u) + (v * v) <= 1.0
+            exact = S <= T
+            if abs(S - T) > band:
+                outside += 1
+                assert fp == exact, (A, B)
+            elif fp != exact:
+                disagree_in_band += 1
+    assert outside > 10000
+    assert disagree_in_band > 0
