@@ -278,7 +278,10 @@ def run_cmc(args, rank, world, local_rank):
     orbit_ms = stages_avg["orbit"]
     achieved = ORBIT_BYTES_PER_STAR * n / (orbit_ms / 1e3) / 1e9
     traffic_ps = profiled_traffic_per_star(args.precision)
-    roof = {"kernel": "k_orbit<%d>" % prec, "bound": "hbm", "achieved": achieved, "peak": hbm,
+    tun = c.tuning()
+    kname = "k_orbit (%s, variant %d, %d threads/block)" % (
+        args.precision, tun["orbit_variant"] if prec else 0, tun["orbit_block"])
+    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind,
             "algorithmic_bytes_per_launch": ORBIT_BYTES_PER_STAR * n,
             "traffic": None if traffic_ps is None else traffic_ps * n,
@@ -294,7 +297,7 @@ def run_cmc(args, rank, world, local_rank):
                       "n_stars": n, "precision": args.precision, "seed": args.seed,
                       "parallelism": "replicas" if dist else "single",
                       "l2": "inputs larger than L2 (state %.2f GB)" % (n * 60 / 1e9)},
-           "gpu_launches": kernels, "stages_ms": stages_avg, "tuning": c.tuning(),
+           "gpu_launches": kernels, "stages_ms": stages_avg, "tuning": tun,
            "roofline": roof,
            "step_hbm_frac": step_frac, "clocks": clocks}
 
