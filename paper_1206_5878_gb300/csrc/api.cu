@@ -126,7 +126,10 @@ void order_state(cmc_ctx* c, cudaStream_t st) {
   const bool mixed = c->cfg.precision == 1;
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32,
                    mixed ? c->Mbuf : nullptr, false, st);
-  if (mixed) launch_buckets(L, c->t32, false, c->bk, st);
+  if (mixed) {
+    launch_buckets(L, c->t32, false, c->bk, st);
+    launch_grid(L, c->x, c->phi, c->Mbuf, false, c->bk, st);
+  }
 }
 
 // The kernels of one timestep, in the order of section 3.3.  With ev, an
@@ -156,7 +159,10 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   mark(5);
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
                    mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, true, st);
-  if (mixed) launch_buckets(L, c->t32, true, c->bk, st);
+  if (mixed) {
+    launch_buckets(L, c->t32, true, c->bk, st);
+    launch_grid(L, c->x, c->phi, c->Mbuf, true, c->bk, st);
+  }
   mark(6);
   if (c->cfg.energy_correction) {
     if (mixed)
@@ -172,8 +178,8 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
 
 int count_step_kernels(const cmc_ctx* c) {
   // bins, relax, orbit, upsweep, hist scan, 8 passes, tie fix, gather,
-  // tile sums, potential, [2 bucket-index kernels], [correction], step end
-  return 3 + 2 + 8 + 1 + 1 + 2 + (c->cfg.precision == 1 ? 2 : 0) +
+  // tile sums, potential, [2 bucket-index + 2 grid kernels], [correction], step end
+  return 3 + 2 + 8 + 1 + 1 + 2 + (c->cfg.precision == 1 ? 4 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 
@@ -783,6 +789,7 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
       if (!e) {
         launch_buckets(S.L, t32, false, bk, st);
         launch_slopes(n, x, phi, sl, st);
+        launch_grid(S.L, x, phi, sl, false, bk, st);
       }
     }
     OrbitStageOut d;

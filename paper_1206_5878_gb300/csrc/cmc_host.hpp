@@ -148,11 +148,20 @@ struct OrbitStageOut {   // optional per-star outputs of the orbit stage
 
 // Radius-bucket index of the float table of every segment (mixed mode):
 // start[off[c] + b] = first node of segment c whose bucket is >= b.
+//
+// With it, a potential grid per segment: Phi (float) at the float keys
+// key0 + g 2^sh of 1/r, sh = 23 - p for 2^p cells per binade, so that no
+// cell straddles a power of two and Phi, linear in 1/r between stars, is
+// close to linear in the key inside a cell.
 struct BucketArgs {
   const int* start = nullptr;
   const int64_t* off = nullptr;
   const uint32_t* base = nullptr;
   const int4* prm = nullptr;  // shift, bucket count, first and last indexed node
+  const float* gphi = nullptr;
+  const int64_t* goff = nullptr;
+  const int4* gprm = nullptr;    // key0, sh, cells, key of 1/r_0 (as int)
+  const float4* gaux = nullptr;  // Phi_0, bound mass, 1/r at key0, unused
 };
 
 struct BucketWork {
@@ -160,9 +169,15 @@ struct BucketWork {
   int64_t* off = nullptr;
   uint32_t* base = nullptr;
   int4* prm = nullptr;
+  float* gphi = nullptr;
+  int64_t* goff = nullptr;
+  int4* gprm = nullptr;
+  float4* gaux = nullptr;
+  int64_t gcells = 0;  // grid cells over all segments
   BucketArgs args() const {
     BucketArgs a;
     a.start = start; a.off = off; a.base = base; a.prm = prm;
+    a.gphi = gphi; a.goff = goff; a.gprm = gprm; a.gaux = gaux;
     return a;
   }
 };
@@ -172,6 +187,9 @@ void free_buckets(BucketWork& B, cudaStream_t st);
 // build the index from t32 over the bound stars (nb - esc_step when nb_sub)
 void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWork& B,
                     cudaStream_t st);
+// build the potential grid from the FP64 table (x, Phi, enclosed masses)
+void launch_grid(const SegLayout& L, const double* x, const double* phi, const double* Menc,
+                 bool nb_sub, BucketWork& B, cudaStream_t st);
 
 // Menc (mixed mode): enclosed mass M_k of every node, the slope of Phi in
 // 1/r across shell k
@@ -183,9 +201,8 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   const double* vt, const double* m, const uint32_t* id, const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
                   int variant, const BucketArgs& ba, cudaStream_t st);
-// mixed-mode orbit variants: 0 F samples in groups of 7; 1 groups of 3;
-// 2 and 3 groups of 3 with registers capped at 64 and 85 (4 and 3 resident
-// 256-thread blocks); 4 groups of 7 capped at 128
+// mixed-mode orbit variants: register caps for 1 (none), 2, 3, 4 and 5
+// resident 256-thread blocks per SM (128, 80, 64 and 48 registers)
 constexpr int kOrbitVariants = 5;
 
 // commits the step: nb, escaper statistics and budget (from the gathered

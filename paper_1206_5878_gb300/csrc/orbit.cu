@@ -228,75 +228,128 @@ struct Buckets {
   int shift, nbk, lo, hi;
 };
 
-// largest i with x_i >= xq[q], else -1, for K queries (lockstep)
+// largest i with x_i >= xq[q], else -1, for K queries (lockstep).
+// The bucket of a query gives the bracket (start[b] - 1, start[b+1]); the
+// keys inside one bucket are close to uniform, so the query's position in
+// its bucket predicts the shell.  Each round loads 4 nodes per unfinished
+// query at once: the first round around the prediction, later rounds
+// evenly over the bracket (a bucket of up to 16 nodes takes at most 2
+// rounds, a prediction that is right 1).  Queries in the tails outside the
+// index search their tail the same way.  Any probe keeps the bracket
+// valid (x falls with i), so the answer is the unique one of a bisection.
 template <int K>
 __device__ __forceinline__ void shells32_bk(const float2* __restrict__ t, int nb,
                                             const Buckets& B, const float (&xq)[K],
                                             int (&out)[K]) {
-  int lo[K], hi[K];
+  int lo[K], hi[K], pred[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) {
+    pred[q] = -2;  // no prediction
     const long long d = (long long)B.base - (long long)__float_as_uint(xq[q]);
     if (d < 0) { lo[q] = -1; hi[q] = B.lo; continue; }           // inner tail
     const long long b = d >> B.shift;
     if (b >= B.nbk) { lo[q] = B.hi; hi[q] = nb; continue; }      // outer tail
-    lo[q] = __ldg(B.start + b) - 1;
-    hi[q] = __ldg(B.start + b + 1);
+    const int s0 = __ldg(B.start + b), s1 = __ldg(B.start + b + 1);
+    lo[q] = s0 - 1;
+    hi[q] = s1;
+    const int frac = (int)(d & ((1ll << B.shift) - 1));
+    pred[q] = s0 - 1 + (int)(((long long)(s1 - s0) * frac + (1ll << (B.shift - 1 > 0 ? B.shift - 1 : 0))) >> B.shift);
   }
   bool more = true;
   while (more) {
     more = false;
-    float v[K];
-    int mid[K];
+    int m[K][4];
+    float v[K][4];
 #pragma unroll
     for (int q = 0; q < K; ++q) {
-      mid[q] = hi[q] - lo[q] > 1 ? lo[q] + ((hi[q] - lo[q]) >> 1) : 0;
-      v[q] = __ldg(&t[mid[q]].x);
+      const int c = hi[q] - lo[q] - 1;  // candidates lo+1 .. hi-1
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        int mj;
+        if (pred[q] >= -1) mj = pred[q] - 1 + j;
+        else mj = lo[q] + 1 + (int)(((long long)(c > 0 ? c - 1 : 0) * j) / 3);
+        mj = mj < lo[q] + 1 ? lo[q] + 1 : mj;
+        mj = mj > hi[q] - 1 ? hi[q] - 1 : mj;
+        m[q][j] = mj;
+        v[q][j] = c > 0 ? __ldg(&t[mj].x) : 0.0f;
+      }
     }
 #pragma unroll
-    for (int q = 0; q < K; ++q)
+    for (int q = 0; q < K; ++q) {
       if (hi[q] - lo[q] > 1) {
-        if (v[q] >= xq[q]) lo[q] = mid[q]; else hi[q] = mid[q];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (v[q][j] >= xq[q]) lo[q] = m[q][j] > lo[q] ? m[q][j] : lo[q];
+          else hi[q] = m[q][j] < hi[q] ? m[q][j] : hi[q];
+        }
+        pred[q] = -2;
         more |= hi[q] - lo[q] > 1;
       }
+    }
   }
 #pragma unroll
   for (int q = 0; q < K; ++q) out[q] = lo[q];
 }
 
-// g(s) of K points in FP32 (Eq. 6 on the float table)
-template <int K>
-__device__ __forceinline__ void g32_k(const float2* __restrict__ t, int nb, const Buckets& B,
-                                      float E, float J, float c0, float c1,
-                                      const float (&s)[K], float (&g)[K], int (&sh)[K]) {
-  float xq[K], drds[K];
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    const float rs = c0 + c1 * (s[q] * (3.0f - s[q] * s[q]));
-    drds[q] = (3.0f * c1) * (1.0f - s[q] * s[q]);
-    xq[q] = 1.0f / rs;
-  }
-  shells32_bk<K>(t, nb, B, xq, sh);
-  float2 a[K], b[K];
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    const int i = sh[q] < 0 ? 0 : sh[q];
-    a[q] = __ldg(t + i);
-    b[q] = (i + 1 < nb) ? __ldg(t + i + 1) : make_float2(0.0f, 0.0f);
-  }
-#pragma unroll
-  for (int q = 0; q < K; ++q) {
-    float ph;
-    if (sh[q] < 0) {
-      ph = a[q].y;
-    } else {
-      const float den = a[q].x - b[q].x;
-      ph = den > 0.0f ? a[q].y + ((a[q].x - xq[q]) / den) * (b[q].y - a[q].y) : a[q].y;
-    }
-    const float L = J * xq[q];
-    const float Q = 2.0f * (E - ph) - L * L;
-    g[q] = Q > 0.0f ? drds[q] / sqrtf(Q) : 0.0f;
-  }
+// The potential grid of one segment (see BucketArgs): Phi (float) at the
+// float keys key0 + g 2^sh of 1/r.  Inside a binade a float's key is linear
+// in its value, so on a binade-aligned grid Phi, linear in 1/r between
+// stars, is interpolated linearly in the key up to the kinks of the stars
+// inside one cell (relative error ~2e-7 at 1024 cells per binade).
+struct Grid {
+  const float* phi;
+  uint32_t key0, kmax;
+  int sh;
+  float scale, phi0, mb, x0;
+};
+
+__device__ __forceinline__ Grid grid_of(const BucketArgs& B, int c) {
+  Grid G;
+  const int4 pr = B.gprm[c];
+  const float4 au = B.gaux[c];
+  G.phi = B.gphi + B.goff[c];
+  G.key0 = (uint32_t)pr.x;
+  G.sh = pr.y;
+  G.kmax = (uint32_t)pr.w;
+  G.scale = __int_as_float((127 - pr.y) << 23);  // 2^-sh
+  G.phi0 = au.x;
+  G.mb = au.y;
+  G.x0 = au.z;
+  return G;
+}
+
+__device__ __forceinline__ float grid_phi(const Grid& G, float xq) {
+  const uint32_t key = __float_as_uint(xq);
+  if (key >= G.kmax) return G.phi0;                               // inside the first star
+  if (key < G.key0) return __ldg(G.phi) + G.mb * (G.x0 - xq);     // beyond the last
+  const uint32_t d = key - G.key0;
+  const int g = (int)(d >> G.sh);
+  const float f = (float)(d & ((1u << G.sh) - 1u)) * G.scale;
+  const float a = __ldg(G.phi + g), b = __ldg(G.phi + g + 1);
+  return a + f * (b - a);
+}
+
+// g(s) = (dr/ds) / sqrt(Q) in FP32 with Phi from the grid
+__device__ __forceinline__ float g32_grid(const Grid& G, float E, float J, float c0, float c1,
+                                          float sv) {
+  const float rs = c0 + c1 * (sv * (3.0f - sv * sv));
+  const float drds = (3.0f * c1) * (1.0f - sv * sv);
+  const float xq = 1.0f / rs;
+  const float ph = grid_phi(G, xq);
+  const float L = J * xq;
+  const float Q = 2.0f * (E - ph) - L * L;
+  return Q > 0.0f ? drds / sqrtf(Q) : 0.0f;
+}
+
+// the FP32 shell (bucket index) of the point r(s), the start of the FP64
+// shell walk of an accepted or edge point
+__device__ __forceinline__ int shell32_of(const float2* __restrict__ t, int nb, const Buckets& B,
+                                          float c0, float c1, float sv) {
+  const float rs = c0 + c1 * (sv * (3.0f - sv * sv));
+  const float xq[1] = {1.0f / rs};
+  int sh[1];
+  shells32_bk<1>(t, nb, B, xq, sh);
+  return sh[0];
 }
 
 // Mixed mode: the orbit point r(s) in FP64 from an FP32 shell index sh
@@ -321,9 +374,9 @@ __device__ __forceinline__ float u01f(uint32_t hi) {
   return (float)(2u * (hi >> 9) + 1u) * 0x1p-24f;
 }
 
-// kPrec: 0 FP64, 1 mixed.  KF: samples of F searched together (7 or 3).
-// kMinB: resident 256-thread blocks to fit (caps registers; 1 = no cap).
-template <int kPrec, int KF, int kMinB>
+// kPrec: 0 FP64, 1 mixed.  kMinB: resident 256-thread blocks to fit
+// (caps registers; 1 = no cap).
+template <int kPrec, int kMinB>
 __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, const double* r,
                                                const double* x, const double* phi,
                                                const float2* t32, const double* Menc, const double* vr,
@@ -458,22 +511,17 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
     } else {
       const float c0f = (float)c0, c1f = (float)c1;
       const int nb32 = (int)nbc;
-      float gmax = 0.0f;
-      // the 21 samples of g in groups of KF independent searches.  F only
-      // has to bound g: 1.2 max g over the FP32 samples is as valid an
-      // envelope as the FP64 one (it differs from it by up to ~1e-4 at the
-      // outer samples, so the two modes draw different, equally exact,
+      const Grid GD = grid_of(BA, c);
+      // F from the 21 samples of g with Phi from the potential grid.  F
+      // only has to bound g: 1.2 max g over these FP32 samples is as valid
+      // an envelope as the FP64 one (it differs from it by up to ~1e-4 at
+      // the outer samples, so the two modes draw different, equally exact,
       // accept sequences)
-#pragma unroll 1
-      static_assert(21 % KF == 0, "whole groups of samples");
-      for (int j0 = 0; j0 < 21; j0 += KF) {
-        float sj[KF], g[KF];
-        int sh[KF];
-#pragma unroll
-        for (int q = 0; q < KF; ++q) sj[q] = c_s32[j0 + q];
-        g32_k<KF>(T32.t, nb32, BK, E32, J32, c0f, c1f, sj, g, sh);
-#pragma unroll
-        for (int q = 0; q < KF; ++q) gmax = g[q] > gmax ? g[q] : gmax;
+      float gmax = 0.0f;
+#pragma unroll 3
+      for (int j = 0; j < 21; ++j) {
+        const float g = g32_grid(GD, E32, J32, c0f, c1f, c_s32[j]);
+        gmax = g > gmax ? g : gmax;
       }
       const float F32 = 1.2f * gmax;
       F = (double)F32;
@@ -482,19 +530,18 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
       } else {
         code = 3;
         U4 w_a{0u, 0u, 0u, 0u};
-        int sh_a = 0;
+        float sv_a = 0.0f;
         // trials in pairs: both are drawn and tested, the first accepted wins
         for (int t = 0; t < max_trials && code == 3; t += 2) {
           U4 w[2];
           float sv32[2], xp32[2], g[2];
-          int sh[2];
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             w[q] = philox(idk, step, kTagRej, (uint32_t)(t + q), seed);
             sv32[q] = 2.0f * u01f(w[q].y) - 1.0f;
             xp32[q] = u01f(w[q].w);
+            g[q] = g32_grid(GD, E32, J32, c0f, c1f, sv32[q]);
           }
-          g32_k<2>(T32.t, nb32, BK, E32, J32, c0f, c1f, sv32, g, sh);
 #pragma unroll
           for (int q = 0; q < 2; ++q) {
             if (t + q >= max_trials) break;
@@ -508,13 +555,14 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
             } else {
               const double sv = sym_double(sym_int(w[q].x, w[q].y));
               double rs, xs, ph, L, Q;
-              point64(T, Menc + sb, s, c0, c1, sv, sh[q], rs, xs, ph, L, Q);
+              point64(T, Menc + sb, s, c0, c1, sv,
+                      shell32_of(T32.t, nb32, BK, c0f, c1f, sv32[q]), rs, xs, ph, L, Q);
               const double g64v = Q > 0.0 ? ((3.0 * c1) * (1.0 - sv * sv)) / sqrt(Q) : 0.0;
               if (g64v > F) ++viol;
               if (!(F * u01(w[q].z, w[q].w) < g64v)) continue;
             }
             w_a = w[q];
-            sh_a = sh[q];
+            sv_a = sv32[q];
             code = 0;
             trials = t + q + 1;
             break;
@@ -528,7 +576,8 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
           // the loop it ran once per pass with the few lanes accepting)
           const double sv = sym_double(sym_int(w_a.x, w_a.y));
           double rs, xs, ph, L, Q;
-          point64(T, Menc + sb, s, c0, c1, sv, sh_a, rs, xs, ph, L, Q);
+          point64(T, Menc + sb, s, c0, c1, sv, shell32_of(T32.t, nb32, BK, c0f, c1f, sv_a), rs,
+                  xs, ph, L, Q);
           if (!(Q > 0.0)) Q = 0.0;
           const double sq = sqrt(Q);
           U4 sg = philox(idk, step, kTagSgn, 0u, seed);
@@ -619,6 +668,66 @@ __global__ void __launch_bounds__(128) k_correction_mixed(Seg S, const int64_t* 
   if (clamp) stat_add(S.stats, c, kStClamps, 1ull);
 }
 
+// ------------------------------------------------------ potential grid
+// Grid cells per segment: twice the stars, between 512 and 2^15.
+int64_t grid_capacity(int64_t nc) {
+  int64_t g = 2 * nc;
+  if (g < 512) g = 512;  // p = 0 (a cell per binade) always fits
+  if (g > (1 << 15)) g = 1 << 15;
+  return g;
+}
+
+// per segment: the key range of 1/r over the bound stars, the finest 2^p
+// cells per binade (p <= 10) that fit the capacity, Phi_0 and the bound
+// mass (Phi = Phi_0 inside the first star; outside the last one Phi falls
+// by M_bound per unit of 1/r)
+__global__ void k_grid_params(Seg S, const int64_t* esc, bool sub, const double* x,
+                              const double* phi, const double* Menc, const int64_t* goff,
+                              int4* gprm, float4* gaux) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= S.n_seg) return;
+  int64_t nb = S.nb[c];
+  if (sub) nb -= esc[c];
+  if (nb <= 0) { gprm[c] = make_int4(0, 0, 0, 0); gaux[c] = make_float4(0.f, 0.f, 0.f, 0.f); return; }
+  const int64_t sb = S.off[c];
+  const uint32_t klo = __float_as_uint((float)x[sb + nb - 1]);
+  const uint32_t khi = __float_as_uint((float)x[sb]);
+  const int64_t cap = goff[c + 1] - goff[c];
+  int p = 10;
+  while (p > 0 && (int64_t)((khi >> (23 - p)) - (klo >> (23 - p))) + 2 > cap) --p;
+  const int sh = 23 - p;
+  const uint32_t key0 = (klo >> sh) << sh;
+  const int cells = (int)((khi - key0) >> sh) + 2;
+  gprm[c] = make_int4((int)key0, sh, cells, (int)khi);
+  gaux[c] = make_float4((float)phi[sb], (float)Menc[sb + nb - 1], __uint_as_float(key0), 0.f);
+}
+
+// Phi at every grid key from the FP64 table: shell = the last star with
+// 1/r_i >= 1/r (bisection), Phi = Phi_i + M_i (1/r_i - 1/r) (Eq. 6 with
+// the enclosed-mass slope), rounded to float
+__global__ void k_grid_build(Seg S, const int64_t* esc, bool sub, const double* x,
+                             const double* phi, const double* Menc, BucketArgs B, float* gphi,
+                             int64_t total) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= total) return;
+  const int c = seg_find(B.goff, S.n_seg, p);
+  const int4 pr = B.gprm[c];
+  const int g = (int)(p - B.goff[c]);
+  if (g >= pr.z) return;
+  int64_t nb = S.nb[c];
+  if (sub) nb -= esc[c];
+  const int64_t sb = S.off[c];
+  const double xg = (double)__uint_as_float((uint32_t)pr.x + ((uint32_t)g << pr.y));
+  int64_t lo = -1, hi = nb;
+  while (hi - lo > 1) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (__ldg(x + sb + mid) >= xg) lo = mid; else hi = mid;
+  }
+  const double ph = lo < 0 ? __ldg(phi + sb)
+                           : __ldg(phi + sb + lo) + __ldg(Menc + sb + lo) * (__ldg(x + sb + lo) - xg);
+  gphi[p] = (float)ph;
+}
+
 // per segment: the indexed node range lo..hi, base = bits(x_lo), the
 // smallest shift that fits the key range into the segment's capacity, and
 // the bucket count
@@ -684,27 +793,45 @@ void launch_slopes(int64_t n, const double* x, const double* phi, double* Menc,
 }
 
 cudaError_t alloc_buckets(BucketWork& B, const SegLayout& L, cudaStream_t st) {
-  std::vector<int64_t> off(L.n_seg + 1, 0);
+  std::vector<int64_t> off(L.n_seg + 1, 0), goff(L.n_seg + 1, 0);
   for (int c = 0; c < L.n_seg; ++c) {
     const int64_t nc = L.h_off[c + 1] - L.h_off[c];
     off[c + 1] = off[c] + nc / 2 + 2;  // about two stars per bucket
+    goff[c + 1] = goff[c] + grid_capacity(nc);
   }
+  B.gcells = goff[L.n_seg];
   cudaError_t e;
   if ((e = cudaMallocAsync((void**)&B.start, sizeof(int) * off[L.n_seg], st))) return e;
   if ((e = cudaMallocAsync((void**)&B.off, sizeof(int64_t) * (L.n_seg + 1), st))) return e;
   if ((e = cudaMallocAsync((void**)&B.base, sizeof(uint32_t) * L.n_seg, st))) return e;
   if ((e = cudaMallocAsync((void**)&B.prm, sizeof(int4) * L.n_seg, st))) return e;
+  if ((e = cudaMallocAsync((void**)&B.gphi, sizeof(float) * B.gcells, st))) return e;
+  if ((e = cudaMallocAsync((void**)&B.goff, sizeof(int64_t) * (L.n_seg + 1), st))) return e;
+  if ((e = cudaMallocAsync((void**)&B.gprm, sizeof(int4) * L.n_seg, st))) return e;
+  if ((e = cudaMallocAsync((void**)&B.gaux, sizeof(float4) * L.n_seg, st))) return e;
   e = cudaMemcpyAsync(B.off, off.data(), sizeof(int64_t) * (L.n_seg + 1),
                       cudaMemcpyHostToDevice, st);
+  if (!e)
+    e = cudaMemcpyAsync(B.goff, goff.data(), sizeof(int64_t) * (L.n_seg + 1),
+                        cudaMemcpyHostToDevice, st);
   if (e) return e;
-  return cudaStreamSynchronize(st);  // off lives on this stack
+  return cudaStreamSynchronize(st);  // off, goff live on this stack
 }
 
 void free_buckets(BucketWork& B, cudaStream_t st) {
-  void* ps[] = {B.start, B.off, B.base, B.prm};
+  void* ps[] = {B.start, B.off, B.base, B.prm, B.gphi, B.goff, B.gprm, B.gaux};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, st);
   B = BucketWork();
+}
+
+void launch_grid(const SegLayout& L, const double* x, const double* phi, const double* Menc,
+                 bool nb_sub, BucketWork& B, cudaStream_t st) {
+  if (!L.n || !B.gcells) return;
+  k_grid_params<<<(unsigned)((L.n_seg + 127) / 128), 128, 0, st>>>(
+      L.dev(), L.esc_step, nb_sub, x, phi, Menc, B.goff, B.gprm, B.gaux);
+  k_grid_build<<<(unsigned)((B.gcells + 255) / 256), 256, 0, st>>>(
+      L.dev(), L.esc_step, nb_sub, x, phi, Menc, B.args(), B.gphi, B.gcells);
 }
 
 void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWork& B,
@@ -736,15 +863,15 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
   if (dbg) d = *dbg;
   if (block <= 0) block = 64;
   const unsigned grid = (unsigned)((L.n + block - 1) / block);
-#define CMC_ORBIT(P, K, B)                                                                   \
-  k_orbit<P, K, B><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, \
-                                           m, id, step, keys, pay, L.esc_step, d, ba, L.n)
-  if (precision == 0) CMC_ORBIT(0, 7, 1);
-  else if (variant == 1) CMC_ORBIT(1, 3, 1);
-  else if (variant == 2) CMC_ORBIT(1, 3, 4);
-  else if (variant == 3) CMC_ORBIT(1, 3, 3);
-  else if (variant == 4) CMC_ORBIT(1, 7, 2);
-  else CMC_ORBIT(1, 7, 1);
+#define CMC_ORBIT(P, B)                                                                     \
+  k_orbit<P, B><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, m, \
+                                        id, step, keys, pay, L.esc_step, d, ba, L.n)
+  if (precision == 0) CMC_ORBIT(0, 1);
+  else if (variant == 1) CMC_ORBIT(1, 2);
+  else if (variant == 2) CMC_ORBIT(1, 3);
+  else if (variant == 3) CMC_ORBIT(1, 4);
+  else if (variant == 4) CMC_ORBIT(1, 5);
+  else CMC_ORBIT(1, 1);
 #undef CMC_ORBIT
 }
 
