@@ -90,7 +90,7 @@ typedef struct {
                                    do not depend on the choice (default 1) */
     int32_t orbit_variant;      /* mixed-mode orbit kernel variant (listed at
                                    cmc_get_tuning): -1 = the autotuner's choice
-                                   (0 without autotune), or 0..4 (default -1) */
+                                   (0 without autotune), or 0..6 (default -1) */
 } cmc_config;
 
 /* Fill cfg with the defaults shown above. */
@@ -186,10 +186,9 @@ cmc_status cmc_step_profiled(cmc_ctx *ctx, int32_t n_steps, double *stage_ms);
 
 /* Kernel shapes in use (chosen by autotune or the configuration): out
  * (host, 4) = {orbit threads per block, sort keys per thread, sort
- * multisplit (0: match, 1: ballot), mixed-mode orbit variant (0: F samples
- * searched 7 at a time, 1: 3 at a time, 2 and 3: 3 at a time with at most
- * 64 and 80 registers per thread, 4: 7 at a time with at most 128)}.  All
- * shapes give bit-identical results. */
+ * multisplit (0: match, 1: ballot), mixed-mode orbit variant (registers per
+ * thread capped for 1 (no cap), 2, 3, 4, 5, 6 or 8 resident 256-thread
+ * blocks per SM: variants 0..6)}.  All shapes give bit-identical results. */
 cmc_status cmc_get_tuning(const cmc_ctx *ctx, int32_t *out);
 
 /* Number of kernels one cmc_step timestep launches. */

@@ -148,7 +148,7 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
                c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
-               c->bk.args(), st);
+               c->bk.args(), c->r_old, c->cc, st);  // r_old, c: free until the gather
   mark(3);
   sort_segments(L, c->W, c->keys, c->vals, 0, 8, true, c->err, st);
   launch_tiefix(L, c->keys, c->vals, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)),
@@ -178,8 +178,9 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
 
 int count_step_kernels(const cmc_ctx* c) {
   // bins, relax, orbit, upsweep, hist scan, 8 passes, tie fix, gather,
-  // tile sums, potential, [2 bucket-index + 2 grid kernels], [correction], step end
-  return 3 + 2 + 8 + 1 + 1 + 2 + (c->cfg.precision == 1 ? 4 : 0) +
+  // tile sums, potential, [turning points, 2 bucket-index + 2 grid kernels],
+  // [correction], step end
+  return 3 + 2 + 8 + 1 + 1 + 2 + (c->cfg.precision == 1 ? 5 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 
@@ -257,7 +258,8 @@ cmc_status autotune(cmc_ctx* c) {
   auto run_orbit = [&](int blk, int var) {
     launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                  mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m,
-                 c->id, c->step, c->keys, c->pay, nullptr, blk, var, c->bk.args(), st);
+                 c->id, c->step, c->keys, c->pay, nullptr, blk, var, c->bk.args(), c->r_old,
+                 c->cc, st);
   };
   auto time_it = [&](auto&& fn) {
     float best = 3.4e38f;
@@ -794,11 +796,16 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
     }
     OrbitStageOut d;
     d.phi_new = phi_new; d.rmin = rmin; d.rmax = rmax; d.F = F; d.code = code;
+    double *tmin = nullptr, *tmax = nullptr;
+    if (!e && precision == 1) e = dalloc(tmin, n, st);
+    if (!e && precision == 1) e = dalloc(tmax, n, st);
     if (!e)
       launch_orbit(S.L, precision, max_trials, r, x, phi, t32, sl, vr, vt, mm, id, dstep, keys,
-                   pay, &d, 0, 0, bk.args(), st);
+                   pay, &d, 0, 0, bk.args(), tmin, tmax, st);
     free_buckets(bk, st);
     dfree(sl, st);
+    dfree(tmin, st);
+    dfree(tmax, st);
     launch_unpack_orbit(n, keys, pay, r_new, vr_new, vt_new, st);
     e = cudaGetLastError();
   }

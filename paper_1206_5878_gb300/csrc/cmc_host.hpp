@@ -192,7 +192,9 @@ void launch_grid(const SegLayout& L, const double* x, const double* phi, const d
                  bool nb_sub, BucketWork& B, cudaStream_t st);
 
 // Menc (mixed mode): enclosed mass M_k of every node, the slope of Phi in
-// 1/r across shell k
+// 1/r across shell k.  launch_orbit in mixed mode runs two kernels (turning
+// points, then sampling) and needs two scratch arrays of n doubles
+// (tp_min, tp_max) for the turning points between them.
 void launch_slopes(int64_t n, const double* x, const double* phi, double* Menc,
                    cudaStream_t st);
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
@@ -200,10 +202,13 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   const double* vr,
                   const double* vt, const double* m, const uint32_t* id, const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
-                  int variant, const BucketArgs& ba, cudaStream_t st);
-// mixed-mode orbit variants: register caps for 1 (none), 2, 3, 4 and 5
-// resident 256-thread blocks per SM (128, 80, 64 and 48 registers)
-constexpr int kOrbitVariants = 5;
+                  int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
+                  cudaStream_t st);
+// mixed-mode orbit variants: register caps for 1 (none), 2, 3, 4, 5, 6 and
+// 8 resident 256-thread blocks per SM (128, 80, 64, 48, 40 and 32
+// registers; the kernel is latency-bound, and occupancy buys more than the
+// spills cost)
+constexpr int kOrbitVariants = 7;
 
 // commits the step: nb, escaper statistics and budget (from the gathered
 // r_old and c of the escaped range), dt; resets the per-step counters

@@ -32,6 +32,12 @@ struct Star {
   int64_t k;
 };
 
+// Q = 2 (E - Phi) - (J x)^2 from node values, as Q_node64 evaluates it
+__device__ __forceinline__ double Qv(const Star& s, double x, double p) {
+  const double L = s.J * x;
+  return 2.0 * (s.E - p) - L * L;
+}
+
 __device__ __forceinline__ double Q_node64(const Table64& T, const Star& s, int64_t i) {
   double L = s.J * __ldg(T.x + i);
   return 2.0 * (s.E - __ldg(T.phi + i)) - L * L;
@@ -60,35 +66,31 @@ __device__ __forceinline__ double shell_root64(const Table64& T, const Star& s, 
 // The same root with the slope of shell j taken from the enclosed mass:
 // across shell j, (Phi_{j+1} - Phi_j)/(x_j - x_{j+1}) = G M_j exactly
 // (Eqs. 1-5; for the outermost shell M_j is the bound mass), so
-// Phi = Phi_j + M_j (x_j - x) needs no division (mixed mode).
-__device__ __forceinline__ double shell_root_M(const Table64& T, const double* M,
-                                               const Star& s, int64_t j, bool outer) {
-  const double rj = __ldg(T.r + j), xj = __ldg(T.x + j), pj = __ldg(T.phi + j);
-  const double B = __ldg(M + j);
+// Phi = Phi_j + M_j (x_j - x) needs no division (mixed mode).  The cores
+// take the node values, so that values loaded ahead and the table give
+// the same arithmetic.
+__device__ __forceinline__ double rmax_core(const Star& s, double rj, double xj, double pj,
+                                            double Mj, bool has_next, double rj1) {
+  const double B = Mj;
   const double A = pj + B * xj;
   double D = B * B + 2.0 * (s.J * s.J) * (s.E - A);
   if (!(D > 0.0)) D = 0.0;
   const double sD = sqrt(D);
-  double root = outer ? (B + sD) / (2.0 * (A - s.E)) : (s.J * s.J) / (B + sD);
+  double root = (B + sD) / (2.0 * (A - s.E));
   if (!(root >= rj)) root = rj;
-  if (j + 1 < T.nb) {
-    const double rj1 = __ldg(T.r + j + 1);
-    if (root > rj1) root = rj1;
-  }
+  if (has_next && root > rj1) root = rj1;
   return root;
 }
 
-// r_min in mixed mode: the shell root above, or inside the innermost node
-// (j < 0, where Phi = Phi_0) J / sqrt(2 (E - Phi_0)) as central_root64
+// r_min in mixed mode: the shell root, or inside the innermost node
+// (central, where Phi = Phi_0) J / sqrt(2 (E - Phi_0)) as central_root64
 // computes it; both take one square root and one division, so the two
 // cases share them (B = 0 makes B + sqrt(D) the bare root) and a warp
-// holding both kinds of star runs them once
-__device__ __forceinline__ double rmin_M(const Table64& T, const double* M, const Star& s,
-                                         int64_t j) {
-  const bool central = j < 0;
-  const int64_t jj = central ? 0 : j;
-  const double rj = __ldg(T.r + jj), xj = __ldg(T.x + jj), pj = __ldg(T.phi + jj);
-  const double B = central ? 0.0 : __ldg(M + jj);
+// holding both kinds of star runs them once.  Central: node values of
+// node 0 and rj = r_0.
+__device__ __forceinline__ double rmin_core(const Star& s, bool central, double rj, double xj,
+                                            double pj, double Mj, bool has_next, double rj1) {
+  const double B = central ? 0.0 : Mj;
   double D, num;
   if (central) {
     D = 2.0 * (s.E - pj);
@@ -105,12 +107,25 @@ __device__ __forceinline__ double rmin_M(const Table64& T, const double* M, cons
     if (root > rj) root = rj;
   } else {
     if (!(root >= rj)) root = rj;
-    if (j + 1 < T.nb) {
-      const double rj1 = __ldg(T.r + j + 1);
-      if (root > rj1) root = rj1;
-    }
+    if (has_next && root > rj1) root = rj1;
   }
   return root;
+}
+
+__device__ __forceinline__ double shell_root_M(const Table64& T, const double* M,
+                                               const Star& s, int64_t j) {
+  const bool nx = j + 1 < T.nb;
+  return rmax_core(s, __ldg(T.r + j), __ldg(T.x + j), __ldg(T.phi + j), __ldg(M + j), nx,
+                   nx ? __ldg(T.r + j + 1) : 0.0);
+}
+
+__device__ __forceinline__ double rmin_M(const Table64& T, const double* M, const Star& s,
+                                         int64_t j) {
+  const bool central = j < 0;
+  const int64_t jj = central ? 0 : j;
+  const bool nx = !central && j + 1 < T.nb;
+  return rmin_core(s, central, __ldg(T.r + jj), __ldg(T.x + jj), __ldg(T.phi + jj),
+                   central ? 0.0 : __ldg(M + jj), nx, nx ? __ldg(T.r + j + 1) : 0.0);
 }
 
 __device__ __forceinline__ double central_root64(const Table64& T, const Star& s) {
@@ -369,13 +384,71 @@ __device__ __forceinline__ void point64(const Table64& T, const double* Menc, co
 // |s| above which a mixed-mode trial is tested in FP64 (1 - 1/32)
 constexpr float kEdge32 = 0.96875f;
 
+
 // (2k + 1) 2^-24 from the top 23 bits of a word: exact in float, in (0, 1)
 __device__ __forceinline__ float u01f(uint32_t hi) {
   return (float)(2u * (hi >> 9) + 1u) * 0x1p-24f;
 }
 
-// kPrec: 0 FP64, 1 mixed.  kMinB: resident 256-thread blocks to fit
-// (caps registers; 1 = no cap).
+// Mixed mode, turning points of one bound star with E < 0: both node
+// bisections in FP32 in lockstep on the float table (r_max over [k, nb],
+// r_min over [-1, k]), each bracket verified in FP64 by a bounded walk,
+// then the FP64 roots inside the bracketing shells (Eq. 12).
+__device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __restrict__ t,
+                                              const double* Menc, const Star& s, double& rmin,
+                                              double& rmax) {
+  const float E32 = (float)s.E, J32 = (float)s.J;
+  const int nb32 = (int)T.nb, k32 = (int)s.k;
+  int lo1 = k32, hi1 = nb32, lo2 = -1, hi2 = k32;
+  const int rounds = search_rounds(nb32);
+  for (int it = 0; it < rounds; ++it) {
+    const bool a1 = hi1 - lo1 > 1, a2 = hi2 - lo2 > 1;
+    const int m1 = a1 ? lo1 + ((hi1 - lo1) >> 1) : k32;
+    const int m2 = a2 ? lo2 + ((hi2 - lo2) >> 1) : k32;
+    const float2 e1 = __ldg(t + m1), e2 = __ldg(t + m2);
+    const float L1 = J32 * e1.x, L2 = J32 * e2.x;
+    const bool n1 = 2.0f * (E32 - e1.y) - L1 * L1 < 0.0f;
+    const bool n2 = 2.0f * (E32 - e2.y) - L2 * L2 < 0.0f;
+    if (a1) { if (n1) hi1 = m1; else lo1 = m1; }
+    if (a2) { if (n2) lo2 = m2; else hi2 = m2; }
+  }
+  const int64_t jmax = verify_rmax(T, s, lo1);
+  const int64_t jmin = verify_rmin(T, s, lo2);
+  rmax = shell_root_M(T, Menc, s, jmax);
+  rmin = rmin_M(T, Menc, s, jmin);
+}
+
+// First kernel of the mixed-mode orbit step: the turning points of every
+// bound star with E < 0, into tp_min / tp_max (split from the sampling
+// kernel so that each runs with fewer registers and more warps).
+template <int kMinB>
+__global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
+    Seg S, const double* r, const double* x, const double* phi, const float2* t32,
+    const double* Menc, const double* vr, const double* vt, double* tp_min, double* tp_max,
+    int64_t n) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int c = seg_find(S.off, S.n_seg, p);
+  const int64_t sb = S.off[c];
+  const int64_t nbc = S.nb[c];
+  const int64_t k = p - sb;
+  if (k >= nbc) return;
+  const Table64 T{r + sb, x + sb, phi + sb, nbc};
+  const double rk = r[p], vrk = vr[p], vtk = vt[p];
+  Star s;
+  s.k = k;
+  s.E = __ldg(T.phi + k) + 0.5 * (vrk * vrk + vtk * vtk);
+  s.J = rk * vtk;
+  if (!(s.E < 0.0)) return;  // escaper: the sampling kernel handles it
+  double rmin, rmax;
+  turning_mixed(T, t32 + sb, Menc + sb, s, rmin, rmax);
+  tp_min[p] = rmin;
+  tp_max[p] = rmax;
+}
+
+// kPrec: 0 FP64, 1 mixed (turning points from k_turning_mixed in tp_min,
+// tp_max).  kMinB: resident 256-thread blocks to fit (caps registers; 1 =
+// no cap).
 template <int kPrec, int kMinB>
 __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, const double* r,
                                                const double* x, const double* phi,
@@ -383,7 +456,9 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
                                                const double* vt, const double* m,
                                                const uint32_t* id, const uint32_t* step_p,
                                                uint64_t* keys, Payload* pay, int64_t* esc,
-                                               OrbitStageOut dbg, BucketArgs BA, int64_t n) {
+                                               OrbitStageOut dbg, BucketArgs BA,
+                                               const double* tp_min, const double* tp_max,
+                                               int64_t n) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int c = seg_find(S.off, S.n_seg, p);
@@ -439,30 +514,13 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
       jmax = bisect_rmax64(T, s);
       jmin = bisect_rmin64(T, s);
     } else {
-      // both bisections in lockstep (r_max over [k, nb], r_min over [-1, k])
-      const int nb32 = (int)nbc, k32 = (int)k;
-      int lo1 = k32, hi1 = nb32, lo2 = -1, hi2 = k32;
-      const int rounds = search_rounds(nb32);
-      for (int it = 0; it < rounds; ++it) {
-        const bool a1 = hi1 - lo1 > 1, a2 = hi2 - lo2 > 1;
-        const int m1 = a1 ? lo1 + ((hi1 - lo1) >> 1) : k32;
-        const int m2 = a2 ? lo2 + ((hi2 - lo2) >> 1) : k32;
-        const float2 e1 = __ldg(T32.t + m1), e2 = __ldg(T32.t + m2);
-        const float L1 = J32 * e1.x, L2 = J32 * e2.x;
-        const bool n1 = 2.0f * (E32 - e1.y) - L1 * L1 < 0.0f;
-        const bool n2 = 2.0f * (E32 - e2.y) - L2 * L2 < 0.0f;
-        if (a1) { if (n1) hi1 = m1; else lo1 = m1; }
-        if (a2) { if (n2) lo2 = m2; else hi2 = m2; }
-      }
-      jmax = verify_rmax(T, s, lo1);
-      jmin = verify_rmin(T, s, lo2);
+      // turning points from k_turning_mixed
+      rmin = __ldg(tp_min + p);
+      rmax = __ldg(tp_max + p);
     }
     if (kPrec == 0) {
       rmax = shell_root64(T, s, jmax, true);
       rmin = jmin < 0 ? central_root64(T, s) : shell_root64(T, s, jmin, false);
-    } else {
-      rmax = shell_root_M(T, Menc + sb, s, jmax, true);
-      rmin = rmin_M(T, Menc + sb, s, jmin);
     }
     const double c0 = 0.5 * (rmax + rmin);
     const double c1 = 0.25 * (rmax - rmin);
@@ -531,42 +589,42 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
         code = 3;
         U4 w_a{0u, 0u, 0u, 0u};
         float sv_a = 0.0f;
-        // trials in pairs: both are drawn and tested, the first accepted wins
-        for (int t = 0; t < max_trials && code == 3; t += 2) {
-          U4 w[2];
-          float sv32[2], xp32[2], g[2];
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            w[q] = philox(idk, step, kTagRej, (uint32_t)(t + q), seed);
-            sv32[q] = 2.0f * u01f(w[q].y) - 1.0f;
-            xp32[q] = u01f(w[q].w);
-            g[q] = g32_grid(GD, E32, J32, c0f, c1f, sv32[q]);
-          }
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            if (t + q >= max_trials) break;
-            // within 1/32 of a turning point Q vanishes like (1 - |s|)^2
-            // while the FP32 r(s) carries an error ~eps32 r: there the
-            // test is taken in FP64 (about 3% of the trials)
-            const bool edge = fabsf(sv32[q]) > kEdge32;
-            if (!edge) {
-              if (g[q] > F32) ++viol;
-              if (!(F32 * xp32[q] < g[q])) continue;
-            } else {
-              const double sv = sym_double(sym_int(w[q].x, w[q].y));
-              double rs, xs, ph, L, Q;
-              point64(T, Menc + sb, s, c0, c1, sv,
-                      shell32_of(T32.t, nb32, BK, c0f, c1f, sv32[q]), rs, xs, ph, L, Q);
-              const double g64v = Q > 0.0 ? ((3.0 * c1) * (1.0 - sv * sv)) / sqrt(Q) : 0.0;
-              if (g64v > F) ++viol;
-              if (!(F * u01(w[q].z, w[q].w) < g64v)) continue;
+        // Trials one at a time.  Within 1/32 of a turning point Q vanishes
+        // like (1 - |s|)^2 while the FP32 r(s) carries an error ~eps32 r:
+        // such a trial (about 3%) leaves the FP32 loop and is tested in
+        // FP64 outside it, where the loop's values are dead.
+        int t = 0;
+        while (code == 3 && t < max_trials) {
+          bool edge = false;
+          for (; t < max_trials; ++t) {
+            const U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
+            const float sv = 2.0f * u01f(w.y) - 1.0f;
+            if (fabsf(sv) > kEdge32) {
+              w_a = w;
+              sv_a = sv;
+              edge = true;
+              break;
             }
-            w_a = w[q];
-            sv_a = sv32[q];
-            code = 0;
-            trials = t + q + 1;
-            break;
+            const float g = g32_grid(GD, E32, J32, c0f, c1f, sv);
+            if (g > F32) ++viol;
+            if (F32 * u01f(w.w) < g) {
+              w_a = w;
+              sv_a = sv;
+              code = 0;
+              break;
+            }
           }
+          if (edge) {
+            const double sv = sym_double(sym_int(w_a.x, w_a.y));
+            double rs, xs, ph, L, Q;
+            point64(T, Menc + sb, s, c0, c1, sv, shell32_of(T32.t, nb32, BK, c0f, c1f, sv_a),
+                    rs, xs, ph, L, Q);
+            const double g64v = Q > 0.0 ? ((3.0 * c1) * (1.0 - sv * sv)) / sqrt(Q) : 0.0;
+            if (g64v > F) ++viol;
+            if (F * u01(w_a.z, w_a.w) < g64v) code = 0;
+          }
+          if (code == 0) trials = t + 1;
+          else ++t;
         }
         if (code == 3) {
           trials = max_trials;
@@ -857,21 +915,35 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   const double* vr, const double* vt, const double* m, const uint32_t* id,
                   const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
-                  int variant, const BucketArgs& ba, cudaStream_t st) {
+                  int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
+                  cudaStream_t st) {
   if (!L.n) return;
   OrbitStageOut d;
   if (dbg) d = *dbg;
   if (block <= 0) block = 64;
   const unsigned grid = (unsigned)((L.n + block - 1) / block);
+#define CMC_TURN(B)                                                                          \
+  k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, t32, Menc, vr, vt, tp_min,  \
+                                             tp_max, L.n)
 #define CMC_ORBIT(P, B)                                                                     \
   k_orbit<P, B><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, m, \
-                                        id, step, keys, pay, L.esc_step, d, ba, L.n)
+                                        id, step, keys, pay, L.esc_step, d, ba, tp_min,      \
+                                        tp_max, L.n)
+#define CMC_MIXED(B) \
+  do {               \
+    CMC_TURN(B);     \
+    CMC_ORBIT(1, B); \
+  } while (0)
   if (precision == 0) CMC_ORBIT(0, 1);
-  else if (variant == 1) CMC_ORBIT(1, 2);
-  else if (variant == 2) CMC_ORBIT(1, 3);
-  else if (variant == 3) CMC_ORBIT(1, 4);
-  else if (variant == 4) CMC_ORBIT(1, 5);
-  else CMC_ORBIT(1, 1);
+  else if (variant == 1) CMC_MIXED(2);
+  else if (variant == 2) CMC_MIXED(3);
+  else if (variant == 3) CMC_MIXED(4);
+  else if (variant == 4) CMC_MIXED(5);
+  else if (variant == 5) CMC_MIXED(6);
+  else if (variant == 6) CMC_MIXED(8);
+  else CMC_MIXED(1);
+#undef CMC_MIXED
+#undef CMC_TURN
 #undef CMC_ORBIT
 }
 

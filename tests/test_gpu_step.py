@@ -171,7 +171,7 @@ def test_launch_shape_does_not_change_bits(g, precision):
     outs = []
     shapes = [(32, 0), (128, 0), (256, 0)]
     if precision == 1:
-        shapes += [(64, v) for v in range(1, 5)]
+        shapes += [(64, v) for v in range(1, 7)]
     for blk, var in shapes:
         c = _cluster(g, d, 4, orbit_block=blk, precision=precision, orbit_variant=var,
                      autotune=0)
@@ -263,7 +263,7 @@ def test_invalid_inputs_are_rejected(g):
         with pytest.raises(g.CMCError) as ei:
             _cluster(g, e, 1)
         assert ei.value.status == 1  # CMC_EINVAL
-    for bad_cfg in ({"orbit_variant": 5}, {"orbit_variant": -2}, {"orbit_block": 48}):
+    for bad_cfg in ({"orbit_variant": 7}, {"orbit_variant": -2}, {"orbit_block": 48}):
         with pytest.raises(g.CMCError):
             _cluster(g, d, 1, **bad_cfg)
     c = _cluster(g, d, 1)
