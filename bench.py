@@ -279,7 +279,7 @@ def run_cmc(args, rank, world, local_rank):
     achieved = ORBIT_BYTES_PER_STAR * n / (orbit_ms / 1e3) / 1e9
     traffic_ps = profiled_traffic_per_star(args.precision)
     tun = c.tuning()
-    kname = "k_orbit (%s, variant %d, %d threads/block)" % (
+    kname = "k_orbit (%s sampling, variant %d, %d threads/block)" % (
         args.precision, tun["orbit_variant"] if prec else 0, tun["orbit_block"])
     roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind,

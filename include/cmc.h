@@ -169,13 +169,14 @@ cmc_status cmc_set_escaped(cmc_ctx *ctx, const double *in);
 enum {
     CMC_STAGE_TIMESTEP = 0,    /* Eq. 7 bins and the minimum over bins */
     CMC_STAGE_RELAX = 1,       /* two-body relaxation of neighbour pairs */
-    CMC_STAGE_ORBIT = 2,       /* turning points and rejection sampling */
-    CMC_STAGE_SORT = 3,        /* radix passes and the id order of ties */
-    CMC_STAGE_GATHER = 4,      /* payload into the sorted arrays */
-    CMC_STAGE_POTENTIAL = 5,   /* shell potential (Eqs. 1-5) */
-    CMC_STAGE_CORRECTION = 6,  /* energy correction */
-    CMC_STAGE_END = 7,         /* bookkeeping of the step */
-    CMC_NSTAGES = 8
+    CMC_STAGE_TURNING = 2,     /* turning points (mixed mode; FP64 mode: in ORBIT) */
+    CMC_STAGE_ORBIT = 3,       /* rejection sampling (FP64 mode: and turning points) */
+    CMC_STAGE_SORT = 4,        /* radix passes and the id order of ties */
+    CMC_STAGE_GATHER = 5,      /* payload into the sorted arrays */
+    CMC_STAGE_POTENTIAL = 6,   /* shell potential (Eqs. 1-5) and mixed-mode tables */
+    CMC_STAGE_CORRECTION = 7,  /* energy correction */
+    CMC_STAGE_END = 8,         /* bookkeeping of the step */
+    CMC_NSTAGES = 9
 };
 
 /* Advance by n_steps timesteps like cmc_step, but launch the kernels one

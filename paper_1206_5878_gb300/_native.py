@@ -25,8 +25,8 @@ STATUS_NAMES = {0: "CMC_OK", 1: "CMC_EINVAL", 2: "CMC_ENOMEM", 3: "CMC_ECUDA",
 STAT_NAMES = ("escaped", "degenerate", "cap_hits", "trials", "violations", "clamps",
               "angle_fails", "ties")
 CMC_NSTATS = len(STAT_NAMES)
-STAGE_NAMES = ("timestep", "relax", "orbit", "sort", "gather", "potential", "correction",
-               "end")
+STAGE_NAMES = ("timestep", "relax", "turning", "orbit", "sort", "gather", "potential",
+               "correction", "end")
 
 
 class cmc_config(ctypes.Structure):

@@ -145,25 +145,30 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   mark(1);
   launch_relax(L, c->vr, c->vt, c->m, c->id, c->nbin, c->step, st);
   mark(2);
+  // turning points into r_old, c (free until the gather), then sampling
+  if (mixed)
+    launch_turning(L, c->r, c->x, c->phi, c->t32, c->Mbuf, c->vr, c->vt, c->r_old, c->cc,
+                   c->cfg.orbit_block, st);
+  mark(3);
   launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
                c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
-               c->bk.args(), c->r_old, c->cc, st);  // r_old, c: free until the gather
-  mark(3);
+               c->bk.args(), c->r_old, c->cc, st, false);
+  mark(4);
   sort_segments(L, c->W, c->keys, c->vals, 0, 8, true, c->err, st);
   launch_tiefix(L, c->keys, c->vals, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)),
                 c->err, st);
-  mark(4);
+  mark(5);
   launch_gather(L, c->keys, c->vals, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old,
                 c->cc, st);
-  mark(5);
+  mark(6);
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
                    mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, true, st);
   if (mixed) {
     launch_buckets(L, c->t32, true, c->bk, st);
     launch_grid(L, c->x, c->phi, c->Mbuf, true, c->bk, st);
   }
-  mark(6);
+  mark(7);
   if (c->cfg.energy_correction) {
     if (mixed)
       launch_correction_mixed(L, c->r, c->x, c->phi, c->t32, c->Mbuf, c->bk.args(), c->vr, c->vt,
@@ -171,9 +176,9 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
     else
       launch_correction(L, c->r, c->x, c->phi, c->vr, c->vt, c->r_old, c->cc, true, c->err, st);
   }
-  mark(7);
-  launch_step_end(L, c->step, c->r_old, c->cc, c->m, st);
   mark(8);
+  launch_step_end(L, c->step, c->r_old, c->cc, c->m, st);
+  mark(9);
 }
 
 int count_step_kernels(const cmc_ctx* c) {

@@ -910,13 +910,23 @@ void launch_correction_mixed(const SegLayout& L, const double* r, const double* 
       L.dev(), L.esc_step, r, x, phi, t32, Menc, ba, vr, vt, r_old, c, L.n);
 }
 
+void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,
+                    const float2* t32, const double* Menc, const double* vr, const double* vt,
+                    double* tp_min, double* tp_max, int block, cudaStream_t st) {
+  if (!L.n) return;
+  if (block <= 0) block = 64;
+  const unsigned grid = (unsigned)((L.n + block - 1) / block);
+  k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, t32, Menc, vr, vt, tp_min,
+                                             tp_max, L.n);
+}
+
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
                   const double* x, const double* phi, const float2* t32, const double* Menc,
                   const double* vr, const double* vt, const double* m, const uint32_t* id,
                   const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
-                  cudaStream_t st) {
+                  cudaStream_t st, bool with_turning) {
   if (!L.n) return;
   OrbitStageOut d;
   if (dbg) d = *dbg;
@@ -929,10 +939,10 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
   k_orbit<P, B><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, m, \
                                         id, step, keys, pay, L.esc_step, d, ba, tp_min,      \
                                         tp_max, L.n)
-#define CMC_MIXED(B) \
-  do {               \
-    CMC_TURN(B);     \
-    CMC_ORBIT(1, B); \
+#define CMC_MIXED(B)            \
+  do {                          \
+    if (with_turning) CMC_TURN(B); \
+    CMC_ORBIT(1, B);            \
   } while (0)
   if (precision == 0) CMC_ORBIT(0, 1);
   else if (variant == 1) CMC_MIXED(2);
