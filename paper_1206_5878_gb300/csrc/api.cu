@@ -147,8 +147,8 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   mark(2);
   // turning points into r_old, c (free until the gather), then sampling
   if (mixed)
-    launch_turning(L, c->r, c->x, c->phi, c->t32, c->Mbuf, c->vr, c->vt, c->r_old, c->cc,
-                   c->cfg.orbit_block, st);
+    launch_turning(L, c->r, c->x, c->phi, c->t32, c->Mbuf, c->vr, c->vt, c->bk.args(), c->r_old,
+                   c->cc, c->cfg.orbit_block, st);
   mark(3);
   launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,

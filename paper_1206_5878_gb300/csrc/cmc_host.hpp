@@ -208,7 +208,8 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
 // then runs the sampling kernel only)
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,
                     const float2* t32, const double* Menc, const double* vr, const double* vt,
-                    double* tp_min, double* tp_max, int block, cudaStream_t st);
+                    const BucketArgs& ba, double* tp_min, double* tp_max, int block,
+                    cudaStream_t st);
 // mixed-mode orbit variants: register caps for 1 (none), 2, 3, 4, 5, 6 and
 // 8 resident 256-thread blocks per SM (128, 80, 64, 48, 40 and 32
 // registers; the kernel is latency-bound, and occupancy buys more than the

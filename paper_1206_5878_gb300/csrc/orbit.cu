@@ -314,8 +314,8 @@ __device__ __forceinline__ void shells32_bk(const float2* __restrict__ t, int nb
 struct Grid {
   const float* phi;
   uint32_t key0, kmax;
-  int sh;
-  float scale, phi0, mb, x0;
+  int sh, cells;
+  float phi0, mb, x0;
 };
 
 __device__ __forceinline__ Grid grid_of(const BucketArgs& B, int c) {
@@ -325,8 +325,8 @@ __device__ __forceinline__ Grid grid_of(const BucketArgs& B, int c) {
   G.phi = B.gphi + B.goff[c];
   G.key0 = (uint32_t)pr.x;
   G.sh = pr.y;
+  G.cells = pr.z;
   G.kmax = (uint32_t)pr.w;
-  G.scale = __int_as_float((127 - pr.y) << 23);  // 2^-sh
   G.phi0 = au.x;
   G.mb = au.y;
   G.x0 = au.z;
@@ -339,7 +339,9 @@ __device__ __forceinline__ float grid_phi(const Grid& G, float xq) {
   if (key < G.key0) return __ldg(G.phi) + G.mb * (G.x0 - xq);     // beyond the last
   const uint32_t d = key - G.key0;
   const int g = (int)(d >> G.sh);
-  const float f = (float)(d & ((1u << G.sh) - 1u)) * G.scale;
+  // f = (d mod 2^sh) 2^-sh, exact: 1 + f assembled from its bits, minus 1
+  const float f =
+      __uint_as_float(0x3F800000u | ((d & ((1u << G.sh) - 1u)) << (23 - G.sh))) - 1.0f;
   const float a = __ldg(G.phi + g), b = __ldg(G.phi + g + 1);
   return a + f * (b - a);
 }
@@ -387,7 +389,97 @@ constexpr float kEdge32 = 0.96875f;
 
 // (2k + 1) 2^-24 from the top 23 bits of a word: exact in float, in (0, 1)
 __device__ __forceinline__ float u01f(uint32_t hi) {
-  return (float)(2u * (hi >> 9) + 1u) * 0x1p-24f;
+  // 1 + k 2^-23 assembled from its bits, minus 1 (exact), plus 2^-24
+  // (exact): no int -> float conversion
+  return (__uint_as_float(0x3F800000u | (hi >> 9)) - 1.0f) + 0x1p-24f;
+}
+
+// Q in FP32 at grid point g (1/r from the grid key, Phi from the grid)
+__device__ __forceinline__ float grid_q(const Grid& G, float E, float J, int g, float& xg) {
+  xg = __uint_as_float(G.key0 + ((uint32_t)g << G.sh));
+  const float L = J * xg;
+  return 2.0f * (E - __ldg(G.phi + g)) - L * L;
+}
+
+__device__ __forceinline__ float node_q(const float2* __restrict__ t, float E, float J, int i) {
+  const float2 n = __ldg(t + i);
+  const float L = J * n.x;
+  return 2.0f * (E - n.y) - L * L;
+}
+
+// FP32 node brackets of both turning points from the potential grid: the
+// sign changes of Q on the grid points (bisections on the L1-resident grid,
+// in lockstep), the root inside the cell by linear interpolation in 1/r,
+// its node through the bucket index, then a short walk over neighbouring
+// nodes to where Q32 changes sign (r_max: node j with Q32 >= 0, j + 1 with
+// Q32 < 0 or the virtual node nb; r_min: j with Q32 < 0 or -1, j + 1 with
+// Q32 >= 0 or the star).  Returns false when a walk exceeds its bound.
+__device__ __forceinline__ bool grid_brackets(const Grid& G, const float2* __restrict__ t,
+                                              const Buckets& BK, float E, float J, int nb, int k,
+                                              int& jmax, int& jmin) {
+  const float xk = __ldg(&t[k].x);
+  const uint32_t kk = __float_as_uint(xk);
+  if (G.cells < 2 || kk < G.key0) return false;
+  int gk = (int)((kk - G.key0) >> G.sh);  // grid points 0..gk lie at or outside the star
+  if (gk > G.cells - 1) gk = G.cells - 1;
+  // r_max: last grid point in [0, gk] with Q < 0 (-1: none; Q -> 2E < 0 as 1/r -> 0)
+  // r_min: first grid point in [gk + 1, cells) with Q < 0 (cells: none)
+  int alo = -1, ahi = gk + 1, blo = gk, bhi = G.cells;
+  float xa_lo = 0.0f, qa_lo = 0.0f, xb_hi = 0.0f, qb_hi = 0.0f;
+  float xa_hi = xk, qa_hi = 0.0f, xb_lo = xk, qb_lo = 0.0f;
+  while (ahi - alo > 1 || bhi - blo > 1) {
+    const bool ra = ahi - alo > 1, rb = bhi - blo > 1;
+    const int ma = ra ? (alo + ahi) >> 1 : 0, mb = rb ? (blo + bhi) >> 1 : 0;
+    float xa, xb;
+    const float qa = grid_q(G, E, J, ma, xa), qb = grid_q(G, E, J, mb, xb);
+    if (ra) {
+      if (qa < 0.0f) { alo = ma; xa_lo = xa; qa_lo = qa; }
+      else { ahi = ma; xa_hi = xa; qa_hi = qa; }
+    }
+    if (rb) {
+      if (qb < 0.0f) { bhi = mb; xb_hi = xb; qb_hi = qb; }
+      else { blo = mb; xb_lo = xb; qb_lo = qb; }
+    }
+  }
+  // the star's own end of each bracket: Q32 at the star
+  const float qk = node_q(t, E, J, k);
+  if (ahi == gk + 1) qa_hi = qk;
+  if (blo == gk) qb_lo = qk;
+  float xq[2];
+  // root estimates (Q linear in 1/r across a cell up to ~(cell width)^2)
+  xq[0] = alo < 0 ? 0.0f : xa_lo + (xa_hi - xa_lo) * (qa_lo / (qa_lo - qa_hi));
+  xq[1] = bhi >= G.cells ? 0.0f : xb_lo + (xb_hi - xb_lo) * (qb_lo / (qb_lo - qb_hi));
+  int sh[2];
+  shells32_bk<2>(t, nb, BK, xq, sh);
+  int j1 = alo < 0 ? nb - 1 : sh[0];
+  int j2 = bhi >= G.cells ? -1 : sh[1];
+  j1 = j1 < k ? k : (j1 > nb - 1 ? nb - 1 : j1);
+  j2 = j2 < -1 ? -1 : (j2 > k - 1 ? k - 1 : j2);
+  bool d1 = false, d2 = false;
+  for (int w = 0; w < 64 && !(d1 && d2); ++w) {
+    if (!d1) {
+      if (j1 + 1 < nb && !(node_q(t, E, J, j1 + 1) < 0.0f)) ++j1;
+      else if (j1 > k && node_q(t, E, J, j1) < 0.0f) --j1;
+      else d1 = true;
+    }
+    if (!d2) {
+      if (j2 + 1 < k && node_q(t, E, J, j2 + 1) < 0.0f) ++j2;
+      else if (j2 >= 0 && !(node_q(t, E, J, j2) < 0.0f)) --j2;
+      else d2 = true;
+    }
+  }
+  jmax = j1;
+  jmin = j2;
+  return d1 && d2;
+}
+
+// Q in FP32 at a float-table node and the bound on its difference from
+// the FP64 Q at that node (see turning_mixed)
+__device__ __forceinline__ void q32_bound(float E, float J, float2 n, float& q, float& tol) {
+  const float L = J * n.x;
+  const float L2 = L * L;
+  q = 2.0f * (E - n.y) - L2;
+  tol = 0x1p-21f * (fabsf(E) + fabsf(n.y)) + (10.0f * 0x1p-24f) * L2;
 }
 
 // Mixed mode, turning points of one bound star with E < 0: both node
@@ -395,25 +487,52 @@ __device__ __forceinline__ float u01f(uint32_t hi) {
 // r_min over [-1, k]), each bracket verified in FP64 by a bounded walk,
 // then the FP64 roots inside the bracketing shells (Eq. 12).
 __device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __restrict__ t,
-                                              const double* Menc, const Star& s, double& rmin,
+                                              const double* Menc, const Grid& G,
+                                              const Buckets& BK, const Star& s, double& rmin,
                                               double& rmax) {
   const float E32 = (float)s.E, J32 = (float)s.J;
   const int nb32 = (int)T.nb, k32 = (int)s.k;
-  int lo1 = k32, hi1 = nb32, lo2 = -1, hi2 = k32;
-  const int rounds = search_rounds(nb32);
-  for (int it = 0; it < rounds; ++it) {
-    const bool a1 = hi1 - lo1 > 1, a2 = hi2 - lo2 > 1;
-    const int m1 = a1 ? lo1 + ((hi1 - lo1) >> 1) : k32;
-    const int m2 = a2 ? lo2 + ((hi2 - lo2) >> 1) : k32;
-    const float2 e1 = __ldg(t + m1), e2 = __ldg(t + m2);
-    const float L1 = J32 * e1.x, L2 = J32 * e2.x;
-    const bool n1 = 2.0f * (E32 - e1.y) - L1 * L1 < 0.0f;
-    const bool n2 = 2.0f * (E32 - e2.y) - L2 * L2 < 0.0f;
-    if (a1) { if (n1) hi1 = m1; else lo1 = m1; }
-    if (a2) { if (n2) lo2 = m2; else hi2 = m2; }
+  int lo1, lo2;
+  if (!grid_brackets(G, t, BK, E32, J32, nb32, k32, lo1, lo2)) {
+    // both node bisections in FP32, in lockstep
+    lo1 = k32, lo2 = -1;
+    int hi1 = nb32, hi2 = k32;
+    const int rounds = search_rounds(nb32);
+    for (int it = 0; it < rounds; ++it) {
+      const bool a1 = hi1 - lo1 > 1, a2 = hi2 - lo2 > 1;
+      const int m1 = a1 ? lo1 + ((hi1 - lo1) >> 1) : k32;
+      const int m2 = a2 ? lo2 + ((hi2 - lo2) >> 1) : k32;
+      const float2 e1 = __ldg(t + m1), e2 = __ldg(t + m2);
+      const float L1 = J32 * e1.x, L2 = J32 * e2.x;
+      const bool n1 = 2.0f * (E32 - e1.y) - L1 * L1 < 0.0f;
+      const bool n2 = 2.0f * (E32 - e2.y) - L2 * L2 < 0.0f;
+      if (a1) { if (n1) hi1 = m1; else lo1 = m1; }
+      if (a2) { if (n2) lo2 = m2; else hi2 = m2; }
+    }
   }
-  const int64_t jmax = verify_rmax(T, s, lo1);
-  const int64_t jmin = verify_rmin(T, s, lo2);
+  // The FP64 walks start at the FP32 brackets and stop at once when the
+  // FP64 Q has the bracket's signs at its two nodes.  The FP32 Q differs
+  // from the exact one by at most 6u(|E| + |Phi|) + 8u L^2 (u = 2^-24:
+  // inputs rounded to float, five float operations), so where |Q32| is
+  // above 8u(|E| + |Phi|) + 10u L^2 its sign is the FP64 sign and the
+  // walk is skipped; otherwise it runs.  Same brackets either way.
+  bool cmax = true, cmin = true;
+  {
+    const float2 n1 = __ldg(t + (lo1 + 1 < nb32 ? lo1 + 1 : lo1)), n0 = __ldg(t + lo1);
+    const int i2 = lo2 < 0 ? 0 : lo2;
+    const float2 m1 = __ldg(t + lo2 + 1), m0 = __ldg(t + i2);
+    float q, tol;
+    q32_bound(E32, J32, n1, q, tol);
+    if (lo1 + 1 < nb32) cmax = cmax && q < -tol;
+    q32_bound(E32, J32, n0, q, tol);
+    if (lo1 > k32) cmax = cmax && q > tol;
+    q32_bound(E32, J32, m1, q, tol);
+    if (lo2 + 1 < k32) cmin = cmin && q > tol;
+    q32_bound(E32, J32, m0, q, tol);
+    if (lo2 >= 0) cmin = cmin && q < -tol;
+  }
+  const int64_t jmax = cmax ? (int64_t)lo1 : verify_rmax(T, s, lo1);
+  const int64_t jmin = cmin ? (int64_t)lo2 : verify_rmin(T, s, lo2);
   rmax = shell_root_M(T, Menc, s, jmax);
   rmin = rmin_M(T, Menc, s, jmin);
 }
@@ -424,8 +543,8 @@ __device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __
 template <int kMinB>
 __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
     Seg S, const double* r, const double* x, const double* phi, const float2* t32,
-    const double* Menc, const double* vr, const double* vt, double* tp_min, double* tp_max,
-    int64_t n) {
+    const double* Menc, const double* vr, const double* vt, BucketArgs BA, double* tp_min,
+    double* tp_max, int64_t n) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int c = seg_find(S.off, S.n_seg, p);
@@ -441,7 +560,15 @@ __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
   s.J = rk * vtk;
   if (!(s.E < 0.0)) return;  // escaper: the sampling kernel handles it
   double rmin, rmax;
-  turning_mixed(T, t32 + sb, Menc + sb, s, rmin, rmax);
+  Buckets BK;
+  const int4 pr = BA.prm[c];
+  BK.start = BA.start + BA.off[c];
+  BK.base = BA.base[c];
+  BK.shift = pr.x;
+  BK.nbk = pr.y;
+  BK.lo = pr.z;
+  BK.hi = pr.w;
+  turning_mixed(T, t32 + sb, Menc + sb, grid_of(BA, c), BK, s, rmin, rmax);
   tp_min[p] = rmin;
   tp_max[p] = rmax;
 }
@@ -912,11 +1039,12 @@ void launch_correction_mixed(const SegLayout& L, const double* r, const double* 
 
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,
                     const float2* t32, const double* Menc, const double* vr, const double* vt,
-                    double* tp_min, double* tp_max, int block, cudaStream_t st) {
+                    const BucketArgs& ba, double* tp_min, double* tp_max, int block,
+                    cudaStream_t st) {
   if (!L.n) return;
   if (block <= 0) block = 64;
   const unsigned grid = (unsigned)((L.n + block - 1) / block);
-  k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, t32, Menc, vr, vt, tp_min,
+  k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, t32, Menc, vr, vt, ba, tp_min,
                                              tp_max, L.n);
 }
 
@@ -933,8 +1061,8 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
   if (block <= 0) block = 64;
   const unsigned grid = (unsigned)((L.n + block - 1) / block);
 #define CMC_TURN(B)                                                                          \
-  k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, t32, Menc, vr, vt, tp_min,  \
-                                             tp_max, L.n)
+  k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, t32, Menc, vr, vt, ba,      \
+                                             tp_min, tp_max, L.n)
 #define CMC_ORBIT(P, B)                                                                     \
   k_orbit<P, B><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, m, \
                                         id, step, keys, pay, L.esc_step, d, ba, tp_min,      \
