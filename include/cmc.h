@@ -71,7 +71,10 @@ enum {
     CMC_STAT_CLAMPS = 5,      /* energy corrections with T' < 0 set to 0 */
     CMC_STAT_ANGLE_FAILS = 6, /* 64 failed unit-disk draws (never expected) */
     CMC_STAT_TIES = 7,        /* runs of equal radii ordered by id */
-    CMC_NSTATS = 8
+    CMC_STAT_FP64_TRIALS = 8, /* mixed mode: trials whose FP32 accept test could
+                                 not be decided within its error bound, taken
+                                 in FP64 (0 in FP64 mode) */
+    CMC_NSTATS = 9
 };
 
 typedef struct {

@@ -23,7 +23,7 @@ CMC_OK, CMC_EINVAL, CMC_ENOMEM, CMC_ECUDA, CMC_ENOCONV, CMC_ETIMEOUT, CMC_EPOISO
 STATUS_NAMES = {0: "CMC_OK", 1: "CMC_EINVAL", 2: "CMC_ENOMEM", 3: "CMC_ECUDA",
                 4: "CMC_ENOCONV", 5: "CMC_ETIMEOUT", 6: "CMC_EPOISONED"}
 STAT_NAMES = ("escaped", "degenerate", "cap_hits", "trials", "violations", "clamps",
-              "angle_fails", "ties")
+              "angle_fails", "ties", "fp64_trials")
 CMC_NSTATS = len(STAT_NAMES)
 STAGE_NAMES = ("timestep", "relax", "turning", "orbit", "sort", "gather", "potential",
                "correction", "end")

@@ -35,6 +35,7 @@ struct cmc_ctx {
          *out3 = nullptr, *fr = nullptr, *lag = nullptr;
   uint32_t* err = nullptr;
   uint32_t* step = nullptr;
+  uint32_t* pcount = nullptr;  // pending stars of the mixed-mode orbit step
   int64_t steps_taken = 0;
   cudaGraphExec_t exec = nullptr;
   bool poisoned = false;
@@ -153,7 +154,7 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
                c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
-               c->bk.args(), c->r_old, c->cc, st, false);
+               c->bk.args(), c->r_old, c->cc, c->vals, c->pcount, st, false);
   mark(4);
   sort_segments(L, c->W, c->keys, c->vals, 0, 8, true, c->err, st);
   launch_tiefix(L, c->keys, c->vals, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)),
@@ -183,9 +184,9 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
 
 int count_step_kernels(const cmc_ctx* c) {
   // bins, relax, orbit, upsweep, hist scan, 8 passes, tie fix, gather,
-  // tile sums, potential, [turning points, 2 bucket-index + 2 grid kernels],
-  // [correction], step end
-  return 3 + 2 + 8 + 1 + 1 + 2 + (c->cfg.precision == 1 ? 5 : 0) +
+  // tile sums, potential, [turning points, FP32 sampler, FP64 continuation,
+  // 2 bucket-index + 2 grid kernels], [correction], step end
+  return 3 + 2 + 8 + 1 + 1 + 2 + (c->cfg.precision == 1 ? 7 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 
@@ -204,6 +205,7 @@ void free_ctx(cmc_ctx* c) {
   dfree(c->pay, st);
   dfree(c->err, st);
   dfree(c->step, st);
+  dfree(c->pcount, st);
   free_sort(c->W, st);
   free_buckets(c->bk, st);
   free_layout(c->L, st);
@@ -264,7 +266,7 @@ cmc_status autotune(cmc_ctx* c) {
     launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                  mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m,
                  c->id, c->step, c->keys, c->pay, nullptr, blk, var, c->bk.args(), c->r_old,
-                 c->cc, st);
+                 c->cc, c->vals, c->pcount, st);
   };
   auto time_it = [&](auto&& fn) {
     float best = 3.4e38f;
@@ -399,6 +401,7 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   CMC_ALLOC(c->out3, (size_t)3 * n_clusters);
   CMC_ALLOC(c->err, 1);
   CMC_ALLOC(c->step, 1);
+  CMC_ALLOC(c->pcount, 1);
 #undef CMC_ALLOC
   if (!e) e = alloc_sort(c->W, L, 8, st);
   if (!e && cfg.precision == 1) e = alloc_buckets(c->bk, L, st);
@@ -802,15 +805,20 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
     OrbitStageOut d;
     d.phi_new = phi_new; d.rmin = rmin; d.rmax = rmax; d.F = F; d.code = code;
     double *tmin = nullptr, *tmax = nullptr;
+    uint32_t *plist = nullptr, *pcnt = nullptr;
     if (!e && precision == 1) e = dalloc(tmin, n, st);
     if (!e && precision == 1) e = dalloc(tmax, n, st);
+    if (!e && precision == 1) e = dalloc(plist, n, st);
+    if (!e && precision == 1) e = dalloc(pcnt, 1, st);
     if (!e)
       launch_orbit(S.L, precision, max_trials, r, x, phi, t32, sl, vr, vt, mm, id, dstep, keys,
-                   pay, &d, 0, 0, bk.args(), tmin, tmax, st);
+                   pay, &d, 0, 0, bk.args(), tmin, tmax, plist, pcnt, st);
     free_buckets(bk, st);
     dfree(sl, st);
     dfree(tmin, st);
     dfree(tmax, st);
+    dfree(plist, st);
+    dfree(pcnt, st);
     launch_unpack_orbit(n, keys, pay, r_new, vr_new, vt_new, st);
     e = cudaGetLastError();
   }

@@ -39,7 +39,7 @@ enum : uint32_t {
 // per-segment statistics (64-bit counters)
 enum : int {
   kStEscaped = 0, kStDegenerate, kStCapHits, kStTrials, kStViolations,
-  kStClamps, kStAngleFails, kStTies, kStFlips, kStCount
+  kStClamps, kStAngleFails, kStTies, kStFp64Trials, kStCount
 };
 constexpr int kStStride = 16;        // counters reserved per segment
 

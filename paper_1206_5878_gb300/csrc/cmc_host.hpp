@@ -192,9 +192,11 @@ void launch_grid(const SegLayout& L, const double* x, const double* phi, const d
                  bool nb_sub, BucketWork& B, cudaStream_t st);
 
 // Menc (mixed mode): enclosed mass M_k of every node, the slope of Phi in
-// 1/r across shell k.  launch_orbit in mixed mode runs two kernels (turning
-// points, then sampling) and needs two scratch arrays of n doubles
-// (tp_min, tp_max) for the turning points between them.
+// 1/r across shell k.  launch_orbit in mixed mode runs four kernels
+// (turning points, FP32 sampler, FP64 continuation of the pending stars,
+// finishing) and needs two scratch arrays of n doubles (tp_min, tp_max:
+// the turning points), a list of n uint32 (the pending stars) and one
+// uint32 counter.
 void launch_slopes(int64_t n, const double* x, const double* phi, double* Menc,
                    cudaStream_t st);
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
@@ -203,7 +205,8 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   const double* vt, const double* m, const uint32_t* id, const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
-                  cudaStream_t st, bool with_turning = true);
+                  uint32_t* plist, uint32_t* pcount, cudaStream_t st,
+                  bool with_turning = true);
 // the turning-point kernel alone (mixed mode; launch_orbit(..., false)
 // then runs the sampling kernel only)
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,

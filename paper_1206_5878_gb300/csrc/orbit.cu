@@ -315,7 +315,7 @@ struct Grid {
   const float* phi;
   uint32_t key0, kmax;
   int sh, cells;
-  float phi0, mb, x0;
+  float phi0, mb, x0, err;  // err: relative bound on the interpolation error
 };
 
 __device__ __forceinline__ Grid grid_of(const BucketArgs& B, int c) {
@@ -330,6 +330,7 @@ __device__ __forceinline__ Grid grid_of(const BucketArgs& B, int c) {
   G.phi0 = au.x;
   G.mb = au.y;
   G.x0 = au.z;
+  G.err = au.w;
   return G;
 }
 
@@ -382,9 +383,6 @@ __device__ __forceinline__ void point64(const Table64& T, const double* Menc, co
   L = st.J * xs;
   Q = 2.0 * (st.E - ph) - L * L;
 }
-
-// |s| above which a mixed-mode trial is tested in FP64 (1 - 1/32)
-constexpr float kEdge32 = 0.96875f;
 
 
 // (2k + 1) 2^-24 from the top 23 bits of a word: exact in float, in (0, 1)
@@ -573,9 +571,225 @@ __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
   tp_max[p] = rmax;
 }
 
+// One trial's accept test in FP32 with a bound on its error: +1 accepted,
+// 0 rejected, -1 undecided (the trial is then taken in FP64).  The test is
+// F X' < g(s), g = (dr/ds) / sqrt(Q), at the FP64 point s (52 bits) and
+// X' (53 bits); the float values use 23 bits of each, so |s32 - s| and
+// |X'32 - X'| are at most 2^-23 and 2^-24.  Bounds (u = 2^-24):
+//   r(s):  |r32 - r| <= 3|c1| (1 - s^2 + 2^-21) 2^-23 + 8u (|c0| + 2|c1|)
+//   Q:     16u (|E| + |Phi| + L^2)             float operations and inputs
+//          + (2 err_grid + 4u) |Phi|           grid interpolation and values
+//          + 1.5 * 2 (M x + L^2) |dr| / r      Q's slope in r, M <= M_bound
+//   g:     1.5 * (1/2) dQ / Q + 6|c1| 2^-23 / (dr/ds) + 16u
+// Close to a turning point Q is within a few dQ of zero and the trial is
+// left undecided; elsewhere the FP32 answer is the FP64 one.
+__device__ __forceinline__ int accept32(const Grid& G, float E, float J, float c0, float c1,
+                                        float F, float sv, float xp,
+                                        unsigned long long& viol) {
+  const float ss = sv * sv;
+  const float rs = c0 + c1 * (sv * (3.0f - ss));
+  const float drds = (3.0f * c1) * (1.0f - ss);
+  const float xq = 1.0f / rs;
+  const float ph = grid_phi(G, xq);
+  const float L = J * xq, L2 = L * L;
+  const float Q = 2.0f * (E - ph) - L2;
+  const float ac1 = fabsf(c1), aph = fabsf(ph);
+  const float dr = 3.0f * ac1 * ((1.0f - ss) + 0x1p-21f) * 0x1p-23f +
+                   0x1p-21f * (fabsf(c0) + 2.0f * ac1);
+  const float qerr = 0x1p-20f * (fabsf(E) + aph + L2) + (2.0f * G.err + 0x1p-22f) * aph +
+                     3.0f * (G.mb * xq + L2) * (dr * xq);
+  if (!(Q > 4.0f * qerr)) return -1;
+  const float g = drds / sqrtf(Q);
+  const float eg = (0.75f * qerr) / Q + (6.0f * ac1 * 0x1p-23f) / drds + 0x1p-20f;
+  const float a = F * xp, da = F * 0x1p-22f;
+  if (a + da < g * (1.0f - eg)) {
+    if (g > F) ++viol;
+    return 1;
+  }
+  if (a - da > g * (1.0f + eg)) {
+    if (g > F) ++viol;
+    return 0;
+  }
+  return -1;
+}
+
+// Result of the FP32 sampler in a star's key slot: bits 0-29 the trial
+// index, 30-31 the status, 32-63 the bits of F (float)
+enum : uint32_t { kSmpAccepted = 0, kSmpPending = 1, kSmpDegenerate = 2, kSmpCap = 3 };
+
+// Second kernel of the mixed-mode orbit step (after k_turning_mixed): the
+// envelope F = 1.2 max g over the 21 samples with Phi from the potential
+// grid, then the FP32 trials (accept32) up to the first one that is
+// accepted (kSmpAccepted) or that FP32 cannot decide (kSmpPending:
+// k_pending64 takes it and the rest of the sequence in FP64).  Only
+// float state is live in the loop, so the kernel runs at full occupancy
+// without spilling.  F only has to bound g: 1.2 max g over these FP32
+// samples is as valid an envelope as the FP64 one (it differs from it by up
+// to ~1e-4 at the outer samples, so the two modes draw different, equally
+// exact, accept sequences).
+template <int kMinB>
+__global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, const double* r,
+                                                  const double* phi, const double* vr,
+                                                  const double* vt, const uint32_t* id,
+                                                  const uint32_t* step_p, BucketArgs BA,
+                                                  const double* tp_min, const double* tp_max,
+                                                  uint64_t* keys, uint32_t* plist,
+                                                  uint32_t* pcount, int64_t n) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long viol = 0;
+  bool pend = false;
+  int c = -1;  // lanes past the end form their own group below
+  if (p < n) {
+    c = seg_find(S.off, S.n_seg, p);
+    const int64_t k = p - S.off[c];
+    const double vrk = vr[p], vtk = vt[p];
+    const double E = __ldg(phi + p) + 0.5 * (vrk * vrk + vtk * vtk);
+    if (k < S.nb[c] && E < 0.0) {
+      const double J = r[p] * vtk;
+      const double rmin = __ldg(tp_min + p), rmax = __ldg(tp_max + p);
+      const double c0 = 0.5 * (rmax + rmin);
+      const double c1 = 0.25 * (rmax - rmin);
+      const float c0f = (float)c0, c1f = (float)c1, E32 = (float)E, J32 = (float)J;
+      const Grid GD = grid_of(BA, c);
+      float gmax = 0.0f;
+#pragma unroll 3
+      for (int j = 0; j < 21; ++j) {
+        const float g = g32_grid(GD, E32, J32, c0f, c1f, c_s32[j]);
+        gmax = g > gmax ? g : gmax;
+      }
+      const float F32 = 1.2f * gmax;
+      uint32_t st = kSmpCap;
+      int t = 0;
+      if (!(rmax > rmin) || !(F32 > 0.0f)) {
+        st = kSmpDegenerate;
+      } else {
+        const uint32_t idk = id[p], step = *step_p;
+        const uint64_t seed = S.seed[c];
+        for (; t < max_trials; ++t) {
+          const U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
+          const int d = accept32(GD, E32, J32, c0f, c1f, F32, 2.0f * u01f(w.y) - 1.0f,
+                                 u01f(w.w), viol);
+          if (d == 0) continue;
+          st = d > 0 ? kSmpAccepted : kSmpPending;
+          break;
+        }
+      }
+      keys[p] = ((uint64_t)__float_as_uint(F32) << 32) | ((uint64_t)st << 30) |
+                (uint64_t)(t & 0x3FFFFFFF);
+      pend = st == kSmpPending;
+    }
+  }
+  // pending stars onto the list of k_pending64 (one atomic per warp)
+  const unsigned pm = __ballot_sync(__activemask(), pend);
+  if (pm) {
+    const int lane = threadIdx.x & 31;
+    uint32_t base = 0;
+    if (lane == __ffs(pm) - 1) base = atomicAdd(pcount, (uint32_t)__popc(pm));
+    base = __shfl_sync(__activemask(), base, __ffs(pm) - 1);
+    if (pend) plist[base + __popc(pm & ((1u << lane) - 1u))] = (uint32_t)p;
+  }
+  // violations: one atomic per segment present in the warp
+  const unsigned full = __activemask();
+  const unsigned peers = __match_any_sync(full, c);
+  const unsigned vi = __reduce_add_sync(peers, (unsigned)viol);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1 && c >= 0) stat_add(S.stats, c, kStViolations, vi);
+}
+
+// Third kernel of the mixed-mode orbit step: every star the FP32 sampler
+// left pending (a trial whose accept test FP32 could not decide, mostly
+// close to a turning point, where Q vanishes like (1 - |s|)^2) takes that
+// trial and the rest of its sequence in FP64; its key slot then holds
+// kSmpAccepted and the accepted trial, or kSmpCap.  Most threads find no
+// pending star and leave at once.
+// one pending star (p = n: an idle lane); counts go to the statistics
+__device__ __forceinline__ void pending_star(Seg S, int max_trials, const double* r,
+                                             const double* x, const double* phi,
+                                             const float2* t32, const double* Menc,
+                                             const double* vr, const double* vt,
+                                             const uint32_t* id, const uint32_t* step_p,
+                                             BucketArgs BA, const double* tp_min,
+                                             const double* tp_max, uint64_t* keys, int64_t p,
+                                             int64_t n) {
+  unsigned long long viol = 0;
+  unsigned int n64 = 0;
+  int c = -1;
+  if (p < n) {
+    c = seg_find(S.off, S.n_seg, p);
+    const int64_t sb = S.off[c], nbc = S.nb[c], k = p - sb;
+    if (k < nbc) {
+      const uint64_t res = keys[p];
+      const double vrk = vr[p], vtk = vt[p];
+      Star s;
+      s.k = k;
+      s.E = __ldg(phi + p) + 0.5 * (vrk * vrk + vtk * vtk);
+      s.J = r[p] * vtk;
+      if (s.E < 0.0 && ((uint32_t)(res >> 30) & 3u) == kSmpPending) {
+        const Table64 T{r + sb, x + sb, phi + sb, nbc};
+        Buckets BK;
+        const int4 pr = BA.prm[c];
+        BK.start = BA.start + BA.off[c];
+        BK.base = BA.base[c];
+        BK.shift = pr.x;
+        BK.nbk = pr.y;
+        BK.lo = pr.z;
+        BK.hi = pr.w;
+        const double rmin = __ldg(tp_min + p), rmax = __ldg(tp_max + p);
+        const double c0 = 0.5 * (rmax + rmin);
+        const double c1 = 0.25 * (rmax - rmin);
+        const float c0f = (float)c0, c1f = (float)c1;
+        const double F = (double)__uint_as_float((uint32_t)(res >> 32));
+        const uint32_t idk = id[p], step = *step_p;
+        const uint64_t seed = S.seed[c];
+        uint32_t st = kSmpCap;
+        int t = (int)(res & 0x3FFFFFFFull);
+        for (; t < max_trials; ++t) {
+          const U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
+          const double sv = sym_double(sym_int(w.x, w.y));
+          double rs, xs, ph, L, Q;
+          point64(T, Menc + sb, s, c0, c1, sv,
+                  shell32_of(t32 + sb, (int)nbc, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs,
+                  xs, ph, L, Q);
+          const double g64v = Q > 0.0 ? ((3.0 * c1) * (1.0 - sv * sv)) / sqrt(Q) : 0.0;
+          ++n64;
+          if (g64v > F) ++viol;
+          if (F * u01(w.z, w.w) < g64v) { st = kSmpAccepted; break; }
+        }
+        if (t >= max_trials) t = max_trials;
+        keys[p] = (res & 0xFFFFFFFF00000000ull) | ((uint64_t)st << 30) |
+                  (uint64_t)(t & 0x3FFFFFFF);
+      }
+    }
+  }
+  const unsigned full = __activemask();
+  const unsigned peers = __match_any_sync(full, c);
+  const unsigned vi = __reduce_add_sync(peers, (unsigned)viol);
+  const unsigned nf = __reduce_add_sync(peers, n64);
+  if ((threadIdx.x & 31) == __ffs(peers) - 1 && c >= 0) {
+    stat_add(S.stats, c, kStViolations, vi);
+    stat_add(S.stats, c, kStFp64Trials, nf);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const double* r,
+                                                   const double* x, const double* phi,
+                                                   const float2* t32, const double* Menc,
+                                                   const double* vr, const double* vt,
+                                                   const uint32_t* id, const uint32_t* step_p,
+                                                   BucketArgs BA, const double* tp_min,
+                                                   const double* tp_max, uint64_t* keys,
+                                                   const uint32_t* plist,
+                                                   const uint32_t* pcount, int64_t n) {
+  const uint32_t np = *pcount;
+  for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < np; i0 += gridDim.x * blockDim.x) {
+    pending_star(S, max_trials, r, x, phi, t32, Menc, vr, vt, id, step_p, BA, tp_min, tp_max,
+                 keys, i0 + threadIdx.x < np ? (int64_t)plist[i0 + threadIdx.x] : n, n);
+  }
+}
+
 // kPrec: 0 FP64, 1 mixed (turning points from k_turning_mixed in tp_min,
-// tp_max).  kMinB: resident 256-thread blocks to fit (caps registers; 1 =
-// no cap).
+// tp_max, FP32 sampler result from k_sample32 / k_pending64 in the key
+// slot).  kMinB: resident 256-thread blocks to fit (caps registers; 1 = no
+// cap).
 template <int kPrec, int kMinB>
 __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, const double* r,
                                                const double* x, const double* phi,
@@ -694,75 +908,36 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
         }
       }
     } else {
-      const float c0f = (float)c0, c1f = (float)c1;
-      const int nb32 = (int)nbc;
-      const Grid GD = grid_of(BA, c);
-      // F from the 21 samples of g with Phi from the potential grid.  F
-      // only has to bound g: 1.2 max g over these FP32 samples is as valid
-      // an envelope as the FP64 one (it differs from it by up to ~1e-4 at
-      // the outer samples, so the two modes draw different, equally exact,
-      // accept sequences)
-      float gmax = 0.0f;
-#pragma unroll 3
-      for (int j = 0; j < 21; ++j) {
-        const float g = g32_grid(GD, E32, J32, c0f, c1f, c_s32[j]);
-        gmax = g > gmax ? g : gmax;
-      }
-      const float F32 = 1.2f * gmax;
-      F = (double)F32;
-      if (!(rmax > rmin) || !(F32 > 0.0f)) {
+      // the FP32 sampler's result (k_sample32); a pending star continues
+      // its trial sequence here in FP64 from the trial near a turning point
+      const uint64_t res = keys[p];
+      const uint32_t st = (uint32_t)(res >> 30) & 3u;
+      int t = (int)(res & 0x3FFFFFFFull);
+      F = (double)__uint_as_float((uint32_t)(res >> 32));
+      if (st == kSmpDegenerate) {
         code = 2;
-      } else {
+      } else if (st == kSmpCap) {
         code = 3;
-        U4 w_a{0u, 0u, 0u, 0u};
-        float sv_a = 0.0f;
-        // Trials one at a time.  Within 1/32 of a turning point Q vanishes
-        // like (1 - |s|)^2 while the FP32 r(s) carries an error ~eps32 r:
-        // such a trial (about 3%) leaves the FP32 loop and is tested in
-        // FP64 outside it, where the loop's values are dead.
-        int t = 0;
-        while (code == 3 && t < max_trials) {
-          bool edge = false;
-          for (; t < max_trials; ++t) {
-            const U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
-            const float sv = 2.0f * u01f(w.y) - 1.0f;
-            if (fabsf(sv) > kEdge32) {
-              w_a = w;
-              sv_a = sv;
-              edge = true;
-              break;
-            }
-            const float g = g32_grid(GD, E32, J32, c0f, c1f, sv);
-            if (g > F32) ++viol;
-            if (F32 * u01f(w.w) < g) {
-              w_a = w;
-              sv_a = sv;
-              code = 0;
-              break;
-            }
-          }
-          if (edge) {
-            const double sv = sym_double(sym_int(w_a.x, w_a.y));
-            double rs, xs, ph, L, Q;
-            point64(T, Menc + sb, s, c0, c1, sv, shell32_of(T32.t, nb32, BK, c0f, c1f, sv_a),
-                    rs, xs, ph, L, Q);
-            const double g64v = Q > 0.0 ? ((3.0 * c1) * (1.0 - sv * sv)) / sqrt(Q) : 0.0;
-            if (g64v > F) ++viol;
-            if (F * u01(w_a.z, w_a.w) < g64v) code = 0;
-          }
-          if (code == 0) trials = t + 1;
-          else ++t;
-        }
-        if (code == 3) {
+        trials = max_trials;
+      } else {
+        const float c0f = (float)c0, c1f = (float)c1;
+        const int nb32 = (int)nbc;
+        // (k_pending64 has resolved every pending star to accepted or cap)
+        const bool acc = st == kSmpAccepted;
+        if (!acc) {
+          code = 3;
           trials = max_trials;
         } else {
+          code = 0;
+          trials = t + 1;
           // the accepted point in FP64 from the full 53-bit X, once per
-          // star after the loop, when the warp's lanes are done (inside
-          // the loop it ran once per pass with the few lanes accepting)
-          const double sv = sym_double(sym_int(w_a.x, w_a.y));
+          // star, with the warp's lanes together
+          const U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
+          const double sv = sym_double(sym_int(w.x, w.y));
           double rs, xs, ph, L, Q;
-          point64(T, Menc + sb, s, c0, c1, sv, shell32_of(T32.t, nb32, BK, c0f, c1f, sv_a), rs,
-                  xs, ph, L, Q);
+          point64(T, Menc + sb, s, c0, c1, sv,
+                  shell32_of(T32.t, nb32, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs, xs, ph,
+                  L, Q);
           if (!(Q > 0.0)) Q = 0.0;
           const double sq = sqrt(Q);
           U4 sg = philox(idk, step, kTagSgn, 0u, seed);
@@ -892,7 +1067,7 @@ __global__ void k_grid_params(Seg S, const int64_t* esc, bool sub, const double*
 // the enclosed-mass slope), rounded to float
 __global__ void k_grid_build(Seg S, const int64_t* esc, bool sub, const double* x,
                              const double* phi, const double* Menc, BucketArgs B, float* gphi,
-                             int64_t total) {
+                             float4* gaux, int64_t total) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= total) return;
   const int c = seg_find(B.goff, S.n_seg, p);
@@ -903,14 +1078,33 @@ __global__ void k_grid_build(Seg S, const int64_t* esc, bool sub, const double* 
   if (sub) nb -= esc[c];
   const int64_t sb = S.off[c];
   const double xg = (double)__uint_as_float((uint32_t)pr.x + ((uint32_t)g << pr.y));
-  int64_t lo = -1, hi = nb;
-  while (hi - lo > 1) {
-    const int64_t mid = lo + ((hi - lo) >> 1);
-    if (__ldg(x + sb + mid) >= xg) lo = mid; else hi = mid;
+  const double xn = (double)__uint_as_float((uint32_t)pr.x + ((uint32_t)(g + 1) << pr.y));
+  int64_t lo = -1, hi = nb, lo2 = -1, hi2 = nb;
+  while (hi - lo > 1 || hi2 - lo2 > 1) {
+    if (hi - lo > 1) {
+      const int64_t mid = lo + ((hi - lo) >> 1);
+      if (__ldg(x + sb + mid) >= xg) lo = mid; else hi = mid;
+    }
+    if (hi2 - lo2 > 1) {
+      const int64_t mid = lo2 + ((hi2 - lo2) >> 1);
+      if (__ldg(x + sb + mid) >= xn) lo2 = mid; else hi2 = mid;
+    }
   }
   const double ph = lo < 0 ? __ldg(phi + sb)
                            : __ldg(phi + sb + lo) + __ldg(Menc + sb + lo) * (__ldg(x + sb + lo) - xg);
   gphi[p] = (float)ph;
+  // Phi is convex in 1/r (its slope -M(1/r) rises with 1/r), so inside the
+  // cell [xg, xn] it lies below the chord by at most (xn - xg) dM / 4, dM
+  // the mass of the stars in the cell; relative to |Phi(xg)|, the smallest
+  // |Phi| of the cell, the largest over the segment's cells bounds the
+  // grid's interpolation error (gaux.w; floats >= 0 order as their bits)
+  if (g + 1 < pr.z && ph < 0.0) {
+    const double Ma = lo < 0 ? 0.0 : __ldg(Menc + sb + lo);
+    const double Mb = lo2 < 0 ? 0.0 : __ldg(Menc + sb + lo2);
+    const double dM = Ma - Mb;
+    const float rel = (float)(((xn - xg) * (dM > 0.0 ? dM : 0.0) * 0.25) / -ph);
+    atomicMax(reinterpret_cast<unsigned int*>(&gaux[c].w), __float_as_uint(rel));
+  }
 }
 
 // per segment: the indexed node range lo..hi, base = bits(x_lo), the
@@ -1016,7 +1210,7 @@ void launch_grid(const SegLayout& L, const double* x, const double* phi, const d
   k_grid_params<<<(unsigned)((L.n_seg + 127) / 128), 128, 0, st>>>(
       L.dev(), L.esc_step, nb_sub, x, phi, Menc, B.goff, B.gprm, B.gaux);
   k_grid_build<<<(unsigned)((B.gcells + 255) / 256), 256, 0, st>>>(
-      L.dev(), L.esc_step, nb_sub, x, phi, Menc, B.args(), B.gphi, B.gcells);
+      L.dev(), L.esc_step, nb_sub, x, phi, Menc, B.args(), B.gphi, B.gaux, B.gcells);
 }
 
 void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWork& B,
@@ -1054,12 +1248,14 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
-                  cudaStream_t st, bool with_turning) {
+                  uint32_t* plist, uint32_t* pcount, cudaStream_t st, bool with_turning) {
   if (!L.n) return;
   OrbitStageOut d;
   if (dbg) d = *dbg;
   if (block <= 0) block = 64;
   const unsigned grid = (unsigned)((L.n + block - 1) / block);
+  // the pending list is short: a grid of a few blocks per SM walks it
+  const unsigned pgrid = (unsigned)((L.n + 127) / 128 < 1216 ? (L.n + 127) / 128 : 1216);
 #define CMC_TURN(B)                                                                          \
   k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, t32, Menc, vr, vt, ba,      \
                                              tp_min, tp_max, L.n)
@@ -1067,10 +1263,15 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
   k_orbit<P, B><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, m, \
                                         id, step, keys, pay, L.esc_step, d, ba, tp_min,      \
                                         tp_max, L.n)
-#define CMC_MIXED(B)            \
-  do {                          \
-    if (with_turning) CMC_TURN(B); \
-    CMC_ORBIT(1, B);            \
+#define CMC_MIXED(B)                                                                        \
+  do {                                                                                      \
+    if (with_turning) CMC_TURN(B);                                                          \
+    cudaMemsetAsync(pcount, 0, sizeof(uint32_t), st);                                      \
+    k_sample32<B><<<grid, block, 0, st>>>(L.dev(), max_trials, r, phi, vr, vt, id, step, ba, \
+                                          tp_min, tp_max, keys, plist, pcount, L.n);        \
+    k_pending64<<<pgrid, 128, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, id, \
+                                       step, ba, tp_min, tp_max, keys, plist, pcount, L.n);  \
+    CMC_ORBIT(1, 4);                                                                        \
   } while (0)
   if (precision == 0) CMC_ORBIT(0, 1);
   else if (variant == 1) CMC_MIXED(2);
