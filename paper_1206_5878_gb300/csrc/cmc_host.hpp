@@ -122,9 +122,15 @@ void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* val
 
 // potential: per-tile sums then the tile-local scans (Eqs. 1-5 in scan
 // form).  nb_sub: subtract esc_step from nb (after the orbit step).
+// Optional outputs: t32 (float 1/r, Phi), Mout (M_k) and node (the record
+// {r, 1/r, Phi, M_k} of every star: one 32-byte sector per node for the
+// kernels that read a few nodes at random).
 void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
                       double* tile_m, double* tile_mx, double* phi, float2* t32,
-                      double* Mout, bool nb_sub, cudaStream_t st);
+                      double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node = nullptr);
+// node records from the arrays (stage calls)
+void launch_make_nodes(int64_t n, const double* r, const double* x, const double* phi,
+                       const double* M, double4_32a* node, cudaStream_t st);
 
 void launch_correction(const SegLayout& L, const double* r, const double* x,
                        const double* phi, double* vr, double* vt, const double* r_old,
@@ -161,7 +167,8 @@ struct BucketArgs {
   const float* gphi = nullptr;
   const int64_t* goff = nullptr;
   const int4* gprm = nullptr;    // key0, sh, cells, key of 1/r_0 (as int)
-  const float4* gaux = nullptr;  // Phi_0, bound mass, 1/r at key0, unused
+  const float4* gaux = nullptr;  // Phi_0, bound mass, 1/r at key0, interpolation bound
+  const double4_32a* node = nullptr; // {r, 1/r, Phi, M} per star (potential kernel)
 };
 
 struct BucketWork {
@@ -174,10 +181,12 @@ struct BucketWork {
   int4* gprm = nullptr;
   float4* gaux = nullptr;
   int64_t gcells = 0;  // grid cells over all segments
+  double4_32a* node = nullptr;
   BucketArgs args() const {
     BucketArgs a;
     a.start = start; a.off = off; a.base = base; a.prm = prm;
     a.gphi = gphi; a.goff = goff; a.gprm = gprm; a.gaux = gaux;
+    a.node = node;
     return a;
   }
 };

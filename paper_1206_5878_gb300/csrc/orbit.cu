@@ -128,6 +128,61 @@ __device__ __forceinline__ double rmin_M(const Table64& T, const double* M, cons
                    central ? 0.0 : __ldg(M + jj), nx, nx ? __ldg(T.r + j + 1) : 0.0);
 }
 
+// The same roots from the node records {r, 1/r, Phi, M} (mixed mode): one
+// sector per node instead of one per array
+__device__ __forceinline__ double rmax_node(const double4_32a* __restrict__ nd, int64_t nb,
+                                            const Star& s, int64_t j) {
+  const double4_32a a = nd[j];
+  const bool nx = j + 1 < nb;
+  return rmax_core(s, a.x, a.y, a.z, a.w, nx, nx ? nd[j + 1].x : 0.0);
+}
+
+__device__ __forceinline__ double rmin_node(const double4_32a* __restrict__ nd, int64_t nb,
+                                            const Star& s, int64_t j) {
+  const bool central = j < 0;
+  const double4_32a a = nd[central ? 0 : j];
+  const bool nx = !central && j + 1 < nb;
+  return rmin_core(s, central, a.x, a.y, a.z, central ? 0.0 : a.w, nx, nx ? nd[j + 1].x : 0.0);
+}
+
+// fix_shell64 on the node records: the FP64 shell of q (largest i with
+// r_i <= q, -1 if none) from a guess i, and that shell's record (node 0's
+// for -1).  The records of the guess and its successor are loaded together.
+__device__ __forceinline__ int64_t fix_shell_nodes(const double4_32a* __restrict__ nd, int64_t nb,
+                                                   int64_t i, double q, double4_32a& a) {
+  if (!(q >= 0.0)) {
+    a = nd[0];
+    return -1;
+  }
+  if (i < -1) i = -1;
+  if (i >= nb) i = nb - 1;
+  const long long qb = dbits(q);
+  a = nd[i < 0 ? 0 : i];
+  double4_32a b = i + 1 < nb ? nd[i + 1] : a;
+  for (int w = 0; w < 64; ++w) {
+    if (i + 1 < nb && dbits(b.x) <= qb) {
+      ++i;
+      a = b;
+      if (i + 1 < nb) b = nd[i + 1];
+      continue;
+    }
+    if (i >= 0 && dbits(a.x) > qb) {
+      --i;
+      b = a;
+      a = nd[i < 0 ? 0 : i];
+      continue;
+    }
+    return i;
+  }
+  int64_t lo = -1, hi = nb;
+  while (hi - lo > 1) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if (dbits(nd[mid].x) <= qb) lo = mid; else hi = mid;
+  }
+  a = nd[lo < 0 ? 0 : lo];
+  return lo;
+}
+
 __device__ __forceinline__ double central_root64(const Table64& T, const Star& s) {
   double rmin = s.J / sqrt(2.0 * (s.E - __ldg(T.phi)));
   if (!(rmin >= 0.0)) rmin = 0.0;
@@ -373,13 +428,15 @@ __device__ __forceinline__ int shell32_of(const float2* __restrict__ t, int nb, 
 // Mixed mode: the orbit point r(s) in FP64 from an FP32 shell index sh
 // (moved to the exact shell), Phi from the enclosed-mass slope of its
 // shell (Eq. 6: Phi = Phi_i + M_i (1/r_i - 1/r)), L = J / r and Q.
-__device__ __forceinline__ void point64(const Table64& T, const double* Menc, const Star& st,
-                                        double c0, double c1, double sv, int sh, double& rs,
-                                        double& xs, double& ph, double& L, double& Q) {
+__device__ __forceinline__ void point64(const double4_32a* __restrict__ nd, int64_t nb,
+                                        const Star& st, double c0, double c1, double sv, int sh,
+                                        double& rs, double& xs, double& ph, double& L,
+                                        double& Q) {
   rs = c0 + c1 * (sv * (3.0 - sv * sv));
-  const int64_t i64 = fix_shell64(T, sh, rs);
+  double4_32a a;
+  const int64_t i64 = fix_shell_nodes(nd, nb, sh, rs, a);
   xs = 1.0 / rs;
-  ph = i64 < 0 ? __ldg(T.phi) : __ldg(T.phi + i64) + __ldg(Menc + i64) * (__ldg(T.x + i64) - xs);
+  ph = i64 < 0 ? a.z : a.z + a.w * (a.y - xs);
   L = st.J * xs;
   Q = 2.0 * (st.E - ph) - L * L;
 }
@@ -485,7 +542,7 @@ __device__ __forceinline__ void q32_bound(float E, float J, float2 n, float& q, 
 // r_min over [-1, k]), each bracket verified in FP64 by a bounded walk,
 // then the FP64 roots inside the bracketing shells (Eq. 12).
 __device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __restrict__ t,
-                                              const double* Menc, const Grid& G,
+                                              const double4_32a* __restrict__ nd, const Grid& G,
                                               const Buckets& BK, const Star& s, double& rmin,
                                               double& rmax) {
   const float E32 = (float)s.E, J32 = (float)s.J;
@@ -531,8 +588,8 @@ __device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __
   }
   const int64_t jmax = cmax ? (int64_t)lo1 : verify_rmax(T, s, lo1);
   const int64_t jmin = cmin ? (int64_t)lo2 : verify_rmin(T, s, lo2);
-  rmax = shell_root_M(T, Menc, s, jmax);
-  rmin = rmin_M(T, Menc, s, jmin);
+  rmax = rmax_node(nd, T.nb, s, jmax);
+  rmin = rmin_node(nd, T.nb, s, jmin);
 }
 
 // First kernel of the mixed-mode orbit step: the turning points of every
@@ -566,7 +623,7 @@ __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
   BK.nbk = pr.y;
   BK.lo = pr.z;
   BK.hi = pr.w;
-  turning_mixed(T, t32 + sb, Menc + sb, grid_of(BA, c), BK, s, rmin, rmax);
+  turning_mixed(T, t32 + sb, BA.node + sb, grid_of(BA, c), BK, s, rmin, rmax);
   tp_min[p] = rmin;
   tp_max[p] = rmax;
 }
@@ -724,7 +781,6 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
       s.E = __ldg(phi + p) + 0.5 * (vrk * vrk + vtk * vtk);
       s.J = r[p] * vtk;
       if (s.E < 0.0 && ((uint32_t)(res >> 30) & 3u) == kSmpPending) {
-        const Table64 T{r + sb, x + sb, phi + sb, nbc};
         Buckets BK;
         const int4 pr = BA.prm[c];
         BK.start = BA.start + BA.off[c];
@@ -746,7 +802,7 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
           const U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
           const double sv = sym_double(sym_int(w.x, w.y));
           double rs, xs, ph, L, Q;
-          point64(T, Menc + sb, s, c0, c1, sv,
+          point64(BA.node + sb, nbc, s, c0, c1, sv,
                   shell32_of(t32 + sb, (int)nbc, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs,
                   xs, ph, L, Q);
           const double g64v = Q > 0.0 ? ((3.0 * c1) * (1.0 - sv * sv)) / sqrt(Q) : 0.0;
@@ -935,7 +991,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
           const U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
           const double sv = sym_double(sym_int(w.x, w.y));
           double rs, xs, ph, L, Q;
-          point64(T, Menc + sb, s, c0, c1, sv,
+          point64(BA.node + sb, nbc, s, c0, c1, sv,
                   shell32_of(T32.t, nb32, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs, xs, ph,
                   L, Q);
           if (!(Q > 0.0)) Q = 0.0;
@@ -997,7 +1053,6 @@ __global__ void __launch_bounds__(128) k_correction_mixed(Seg S, const int64_t* 
   const int64_t sb = __ldg(S.off + c);
   const int64_t nbc = S.nb[c] - esc[c];
   if (p - sb >= nbc) return;
-  const Table64 T{r + sb, x + sb, phi + sb, nbc};
   const double ro = r_old[p];
   const double xo = 1.0 / ro;
   Buckets BK;
@@ -1011,9 +1066,9 @@ __global__ void __launch_bounds__(128) k_correction_mixed(Seg S, const int64_t* 
   const float xq[1] = {(float)xo};
   int sh[1];
   shells32_bk<1>(t32 + sb, (int)nbc, BK, xq, sh);
-  const int64_t i = fix_shell64(T, sh[0], ro);
-  const double pn = i < 0 ? __ldg(T.phi)
-                          : __ldg(T.phi + i) + __ldg(Menc + sb + i) * (__ldg(T.x + i) - xo);
+  double4_32a nd;
+  const int64_t i = fix_shell_nodes(BA.node + sb, nbc, sh[0], ro, nd);
+  const double pn = i < 0 ? nd.z : nd.z + nd.w * (nd.y - xo);
   const double a = vr[p], b = vt[p];
   const double Tk = 0.5 * (a * a + b * b);
   const double dnew = pn - phi[p];
@@ -1188,6 +1243,7 @@ cudaError_t alloc_buckets(BucketWork& B, const SegLayout& L, cudaStream_t st) {
   if ((e = cudaMallocAsync((void**)&B.goff, sizeof(int64_t) * (L.n_seg + 1), st))) return e;
   if ((e = cudaMallocAsync((void**)&B.gprm, sizeof(int4) * L.n_seg, st))) return e;
   if ((e = cudaMallocAsync((void**)&B.gaux, sizeof(float4) * L.n_seg, st))) return e;
+  if ((e = cudaMallocAsync((void**)&B.node, sizeof(double4_32a) * (L.n > 0 ? L.n : 1), st))) return e;
   e = cudaMemcpyAsync(B.off, off.data(), sizeof(int64_t) * (L.n_seg + 1),
                       cudaMemcpyHostToDevice, st);
   if (!e)
@@ -1198,7 +1254,7 @@ cudaError_t alloc_buckets(BucketWork& B, const SegLayout& L, cudaStream_t st) {
 }
 
 void free_buckets(BucketWork& B, cudaStream_t st) {
-  void* ps[] = {B.start, B.off, B.base, B.prm, B.gphi, B.goff, B.gprm, B.gaux};
+  void* ps[] = {B.start, B.off, B.base, B.prm, B.gphi, B.goff, B.gprm, B.gaux, B.node};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, st);
   B = BucketWork();

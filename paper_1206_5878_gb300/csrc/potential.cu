@@ -164,10 +164,11 @@ __global__ void __launch_bounds__(kThreads) k_tile_sums(Seg S, const int64_t* es
 // totals are scanned across the block, and the results (Phi, M_k, the
 // float table) leave through shared memory with coalesced stores.
 __global__ void __launch_bounds__(kThreads) k_potential(Seg S, const int64_t* esc, bool sub,
-                                                        const double* x, const double* m,
-                                                        const double* tile_m,
+                                                        const double* r, const double* x,
+                                                        const double* m, const double* tile_m,
                                                         const double* tile_mx, double* phi,
-                                                        float2* t32, double* Mout) {
+                                                        float2* t32, double* Mout,
+                                                        double4_32a* node) {
   extern __shared__ double smem[];
   double* s_m = smem;              // m, then M_k
   double* s_x = smem + kPadN;      // x
@@ -230,6 +231,7 @@ __global__ void __launch_bounds__(kThreads) k_potential(Seg S, const int64_t* es
     phi[p] = ph;
     if (t32) t32[p] = make_float2((float)s_x[q], (float)ph);
     if (Mout) Mout[p] = bound ? s_m[q] : 0.0;
+    if (node) node[p] = make_double4_32a(r[p], s_x[q], ph, bound ? s_m[q] : 0.0);
   }
 }
 
@@ -430,6 +432,12 @@ __global__ void k_make_t32(int64_t n, const double* x, const double* phi, float2
   if (p < n) t32[p] = make_float2((float)x[p], (float)phi[p]);
 }
 
+__global__ void k_make_nodes(int64_t n, const double* r, const double* x, const double* phi,
+                             const double* M, double4_32a* node) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < n) node[p] = make_double4_32a(r[p], x[p], phi[p], M[p]);
+}
+
 __global__ void k_unpack_orbit(int64_t n, const uint64_t* keys, const Payload* pay,
                                double* r_new, double* vr_new, double* vt_new) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -456,6 +464,11 @@ void launch_recip(int64_t n, const double* r, double* x, cudaStream_t st) {
 void launch_make_t32(int64_t n, const double* x, const double* phi, float2* t32,
                      cudaStream_t st) {
   if (n > 0) k_make_t32<<<blocks_for(n, 256), 256, 0, st>>>(n, x, phi, t32);
+}
+
+void launch_make_nodes(int64_t n, const double* r, const double* x, const double* phi,
+                       const double* M, double4_32a* node, cudaStream_t st) {
+  if (n > 0) k_make_nodes<<<blocks_for(n, 256), 256, 0, st>>>(n, r, x, phi, M, node);
 }
 
 void launch_unpack_orbit(int64_t n, const uint64_t* keys, const Payload* pay, double* r_new,
@@ -563,14 +576,13 @@ void potential_prepare() {
 
 void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
                       double* tile_m, double* tile_mx, double* phi, float2* t32,
-                      double* Mout, bool nb_sub, cudaStream_t st) {
-  (void)r;
+                      double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node) {
   if (!L.n_tiles) return;
   Seg S = L.dev();
   k_tile_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, L.esc_step, nb_sub, x, m, tile_m,
                                                        tile_mx);
   k_potential<<<(unsigned)L.n_tiles, kThreads, kPotentialSmem, st>>>(
-      S, L.esc_step, nb_sub, x, m, tile_m, tile_mx, phi, t32, Mout);
+      S, L.esc_step, nb_sub, r, x, m, tile_m, tile_mx, phi, t32, Mout, node);
 }
 
 void launch_correction(const SegLayout& L, const double* r, const double* x,
