@@ -112,41 +112,9 @@ __device__ __forceinline__ double rmin_core(const Star& s, bool central, double 
   return root;
 }
 
-__device__ __forceinline__ double shell_root_M(const Table64& T, const double* M,
-                                               const Star& s, int64_t j) {
-  const bool nx = j + 1 < T.nb;
-  return rmax_core(s, __ldg(T.r + j), __ldg(T.x + j), __ldg(T.phi + j), __ldg(M + j), nx,
-                   nx ? __ldg(T.r + j + 1) : 0.0);
-}
-
-__device__ __forceinline__ double rmin_M(const Table64& T, const double* M, const Star& s,
-                                         int64_t j) {
-  const bool central = j < 0;
-  const int64_t jj = central ? 0 : j;
-  const bool nx = !central && j + 1 < T.nb;
-  return rmin_core(s, central, __ldg(T.r + jj), __ldg(T.x + jj), __ldg(T.phi + jj),
-                   central ? 0.0 : __ldg(M + jj), nx, nx ? __ldg(T.r + j + 1) : 0.0);
-}
-
-// The same roots from the node records {r, 1/r, Phi, M} (mixed mode): one
-// sector per node instead of one per array
-__device__ __forceinline__ double rmax_node(const double4_32a* __restrict__ nd, int64_t nb,
-                                            const Star& s, int64_t j) {
-  const double4_32a a = nd[j];
-  const bool nx = j + 1 < nb;
-  return rmax_core(s, a.x, a.y, a.z, a.w, nx, nx ? nd[j + 1].x : 0.0);
-}
-
-__device__ __forceinline__ double rmin_node(const double4_32a* __restrict__ nd, int64_t nb,
-                                            const Star& s, int64_t j) {
-  const bool central = j < 0;
-  const double4_32a a = nd[central ? 0 : j];
-  const bool nx = !central && j + 1 < nb;
-  return rmin_core(s, central, a.x, a.y, a.z, central ? 0.0 : a.w, nx, nx ? nd[j + 1].x : 0.0);
-}
-
-// fix_shell64 on the node records: the FP64 shell of q (largest i with
-// r_i <= q, -1 if none) from a guess i, and that shell's record (node 0's
+// The FP64 shell of q (largest i with r_i <= q, -1 if none; integer
+// compares of the radii's bits) from a guess i by a bounded walk, then a
+// bisection, on the node records; a receives that shell's record (node 0's
 // for -1).  The records of the guess and its successor are loaded together.
 __device__ __forceinline__ int64_t fix_shell_nodes(const double4_32a* __restrict__ nd, int64_t nb,
                                                    int64_t i, double q, double4_32a& a) {
@@ -226,47 +194,6 @@ struct Table32 {
   const float2* t;  // (1/r, Phi) per node
   int64_t nb;
 };
-
-// move an approximate shell index to the exact FP64 one: largest i with
-// r_i <= q (bounded walk, then plain bisection)
-__device__ __forceinline__ int64_t fix_shell64(const Table64& T, int64_t i, double q) {
-  if (!(q >= 0.0)) return -1;
-  if (i < -1) i = -1;
-  if (i >= T.nb) i = T.nb - 1;
-  const long long qb = dbits(q);
-  const long long* rb = reinterpret_cast<const long long*>(T.r);
-  for (int w = 0; w < 64; ++w) {
-    if (i + 1 < T.nb && __ldg(rb + i + 1) <= qb) { ++i; continue; }
-    if (i >= 0 && __ldg(rb + i) > qb) { --i; continue; }
-    return i;
-  }
-  return shell_of(T, q);
-}
-
-// FP32 bracket -> FP64 bracket for r_max: node lo has Q >= 0 (or is the
-// star), node lo+1 has Q < 0 (or is the virtual node nb)
-__device__ __forceinline__ int64_t verify_rmax(const Table64& T, const Star& s, int64_t j) {
-  if (j < s.k) j = s.k;
-  if (j > T.nb - 1) j = T.nb - 1;
-  for (int w = 0; w < 64; ++w) {
-    if (j + 1 < T.nb && !(Q_node64(T, s, j + 1) < 0.0)) { ++j; continue; }
-    if (j > s.k && Q_node64(T, s, j) < 0.0) { --j; continue; }
-    return j;
-  }
-  return bisect_rmax64(T, s);
-}
-
-// r_min: node lo has Q < 0 (or is -1), node lo+1 has Q >= 0 (or is the star)
-__device__ __forceinline__ int64_t verify_rmin(const Table64& T, const Star& s, int64_t j) {
-  if (j < -1) j = -1;
-  if (j > s.k - 1) j = s.k - 1;
-  for (int w = 0; w < 64; ++w) {
-    if (j + 1 < s.k && Q_node64(T, s, j + 1) < 0.0) { ++j; continue; }
-    if (j >= 0 && !(Q_node64(T, s, j) < 0.0)) { --j; continue; }
-    return j;
-  }
-  return bisect_rmin64(T, s);
-}
 
 // sample points of the bound F: s_j = -1 + (j + 1/2)/10.5 (IEEE double,
 // evaluated at compile time), and their float roundings
@@ -528,13 +455,67 @@ __device__ __forceinline__ bool grid_brackets(const Grid& G, const float2* __res
   return d1 && d2;
 }
 
-// Q in FP32 at a float-table node and the bound on its difference from
-// the FP64 Q at that node (see turning_mixed)
-__device__ __forceinline__ void q32_bound(float E, float J, float2 n, float& q, float& tol) {
-  const float L = J * n.x;
-  const float L2 = L * L;
-  q = 2.0f * (E - n.y) - L2;
-  tol = 0x1p-21f * (fabsf(E) + fabsf(n.y)) + (10.0f * 0x1p-24f) * L2;
+// verify_rmax / verify_rmin on the node records: the same walks (a bounded
+// walk from the FP32 bracket, then the full bisection), returning the
+// records of the bracket's node (a; node 0 for r_min's -1) and of the node
+// after it (b)
+__device__ __forceinline__ int64_t verify_rmax_nodes(const Table64& T,
+                                                     const double4_32a* __restrict__ nd,
+                                                     const Star& s, int64_t j, double4_32a& a,
+                                                     double4_32a& b) {
+  const int64_t nb = T.nb;
+  if (j < s.k) j = s.k;
+  if (j > nb - 1) j = nb - 1;
+  a = nd[j];
+  b = j + 1 < nb ? nd[j + 1] : a;
+  for (int w = 0; w < 64; ++w) {
+    if (j + 1 < nb && !(Qv(s, b.y, b.z) < 0.0)) {
+      ++j;
+      a = b;
+      b = j + 1 < nb ? nd[j + 1] : a;
+      continue;
+    }
+    if (j > s.k && Qv(s, a.y, a.z) < 0.0) {
+      --j;
+      b = a;
+      a = nd[j];
+      continue;
+    }
+    return j;
+  }
+  j = bisect_rmax64(T, s);
+  a = nd[j];
+  b = j + 1 < nb ? nd[j + 1] : a;
+  return j;
+}
+
+__device__ __forceinline__ int64_t verify_rmin_nodes(const Table64& T,
+                                                     const double4_32a* __restrict__ nd,
+                                                     const Star& s, int64_t j, double4_32a& a,
+                                                     double4_32a& b) {
+  if (j < -1) j = -1;
+  if (j > s.k - 1) j = s.k - 1;
+  a = nd[j < 0 ? 0 : j];
+  b = nd[j + 1];
+  for (int w = 0; w < 64; ++w) {
+    if (j + 1 < s.k && Qv(s, b.y, b.z) < 0.0) {
+      ++j;
+      a = b;
+      b = nd[j + 1];
+      continue;
+    }
+    if (j >= 0 && !(Qv(s, a.y, a.z) < 0.0)) {
+      --j;
+      b = a;
+      a = nd[j < 0 ? 0 : j];
+      continue;
+    }
+    return j;
+  }
+  j = bisect_rmin64(T, s);
+  a = nd[j < 0 ? 0 : j];
+  b = nd[j + 1];
+  return j;
 }
 
 // Mixed mode, turning points of one bound star with E < 0: both node
@@ -565,31 +546,13 @@ __device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __
       if (a2) { if (n2) lo2 = m2; else hi2 = m2; }
     }
   }
-  // The FP64 walks start at the FP32 brackets and stop at once when the
-  // FP64 Q has the bracket's signs at its two nodes.  The FP32 Q differs
-  // from the exact one by at most 6u(|E| + |Phi|) + 8u L^2 (u = 2^-24:
-  // inputs rounded to float, five float operations), so where |Q32| is
-  // above 8u(|E| + |Phi|) + 10u L^2 its sign is the FP64 sign and the
-  // walk is skipped; otherwise it runs.  Same brackets either way.
-  bool cmax = true, cmin = true;
-  {
-    const float2 n1 = __ldg(t + (lo1 + 1 < nb32 ? lo1 + 1 : lo1)), n0 = __ldg(t + lo1);
-    const int i2 = lo2 < 0 ? 0 : lo2;
-    const float2 m1 = __ldg(t + lo2 + 1), m0 = __ldg(t + i2);
-    float q, tol;
-    q32_bound(E32, J32, n1, q, tol);
-    if (lo1 + 1 < nb32) cmax = cmax && q < -tol;
-    q32_bound(E32, J32, n0, q, tol);
-    if (lo1 > k32) cmax = cmax && q > tol;
-    q32_bound(E32, J32, m1, q, tol);
-    if (lo2 + 1 < k32) cmin = cmin && q > tol;
-    q32_bound(E32, J32, m0, q, tol);
-    if (lo2 >= 0) cmin = cmin && q < -tol;
-  }
-  const int64_t jmax = cmax ? (int64_t)lo1 : verify_rmax(T, s, lo1);
-  const int64_t jmin = cmin ? (int64_t)lo2 : verify_rmin(T, s, lo2);
-  rmax = rmax_node(nd, T.nb, s, jmax);
-  rmin = rmin_node(nd, T.nb, s, jmin);
+  // FP64 walks from the FP32 brackets on the node records, which hold the
+  // values the roots need next
+  double4_32a a1, b1, a2, b2;
+  const int64_t jmax = verify_rmax_nodes(T, nd, s, lo1, a1, b1);
+  const int64_t jmin = verify_rmin_nodes(T, nd, s, lo2, a2, b2);
+  rmax = rmax_core(s, a1.x, a1.y, a1.z, a1.w, jmax + 1 < T.nb, b1.x);
+  rmin = rmin_core(s, jmin < 0, a2.x, a2.y, a2.z, jmin < 0 ? 0.0 : a2.w, jmin >= 0, b2.x);
 }
 
 // First kernel of the mixed-mode orbit step: the turning points of every
@@ -906,7 +869,6 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
       BK.lo = pr.z;
       BK.hi = pr.w;
     }
-    const float E32 = (float)s.E, J32 = (float)s.J;
     if (kPrec == 0) {
       jmax = bisect_rmax64(T, s);
       jmin = bisect_rmin64(T, s);
