@@ -156,9 +156,11 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
                c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
                c->bk.args(), c->r_old, c->cc, c->vals, c->pcount, st, false);
   mark(4);
-  sort_segments(L, c->W, c->keys, c->vals, 0, 8, true, c->err, st);
+  // radix passes over bits 16-63 of the radius keys; runs equal in those
+  // bits (radii within 2^-36 of each other) are put in (r, id) order after
+  sort_segments(L, c->W, c->keys, c->vals, 2, 6, true, c->err, st);
   launch_tiefix(L, c->keys, c->vals, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)),
-                c->err, st);
+                c->err, st, 16);
   mark(5);
   launch_gather(L, c->keys, c->vals, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old,
                 c->cc, st);
@@ -306,7 +308,7 @@ cmc_status autotune(cmc_ctx* c) {
       if (sort_set_shape(L, c->W, ipt, rank, st)) continue;
       const float ms = time_it([&] {
         cudaMemcpyAsync(c->keys, saved, sizeof(uint64_t) * L.n, cudaMemcpyDeviceToDevice, st);
-        sort_segments(L, c->W, c->keys, c->vals, 0, 8, true, c->err, st);
+        sort_segments(L, c->W, c->keys, c->vals, 2, 6, true, c->err, st);
       });
       if (ms < tbest) { tbest = ms; best_ipt = ipt; best_rank = rank; }
     }
@@ -676,8 +678,10 @@ cmc_status cmc_sort_radius(int64_t n, const double* r, const uint32_t* id, uint3
     sort_prepare();
     cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
     launch_make_keys(S.L, r, nullptr, nullptr, nullptr, id, keys, nullptr, st);
-    sort_segments(S.L, W, keys, perm, 0, 8, true, err, st);
-    launch_tiefix(S.L, keys, perm, id, 1, err, st);
+    // as in the timestep: passes over bits 16-63, then runs equal in those
+    // bits in (r, id) order
+    sort_segments(S.L, W, keys, perm, 2, 6, true, err, st);
+    launch_tiefix(S.L, keys, perm, id, 1, err, st, 16);
     uint32_t he = 0;
     e = cudaMemcpyAsync(&he, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaStreamSynchronize(st);

@@ -25,8 +25,11 @@ constexpr uint32_t kTagPhi = 1;      // relaxation: azimuth of the deflection
 constexpr uint32_t kTagRej = 2;      // orbit: rejection trials
 constexpr uint32_t kTagSgn = 3;      // orbit: sign of the new v_r
 
-// escaped stars sort after every finite radius, by id
-constexpr uint64_t kEscKeyBase = 0x7FF0000000000001ull;
+// escaped stars sort after every finite radius, by id: key 0x7FF0...0 | id
+// << 16, above every finite radius and unique in its top 48 bits (the
+// timestep's sort orders by those and puts runs of equal top bits in
+// (key, id) order)
+constexpr uint64_t kEscKeyBase = 0x7FF0000000000000ull;
 
 // error bits (fatal: they poison the context)
 enum : uint32_t {
@@ -169,7 +172,7 @@ __device__ __forceinline__ bool disk_angle(uint64_t seed, uint32_t id, uint32_t 
 // ------------------------------------------------------------ sort keys
 __device__ __forceinline__ uint64_t radius_key(double r, uint32_t id) {
   uint64_t b = (uint64_t)__double_as_longlong(r);
-  return (b >= 0x7FF0000000000000ull) ? kEscKeyBase + (uint64_t)id : b;
+  return (b >= 0x7FF0000000000000ull) ? kEscKeyBase | ((uint64_t)id << 16) : b;
 }
 __device__ __forceinline__ bool key_is_escaper(uint64_t k) {
   return k >= 0x7FF0000000000000ull;

@@ -87,11 +87,13 @@ cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint3
                           int first_pass, int passes, bool vals_identity, uint32_t* err,
                           cudaStream_t st);
 
-// Order every run of equal finite keys by the ids of the sorted elements
-// (ids_by_val[vals[p] * id_stride]) so that ties follow the (r, id) order.
-void launch_tiefix(const SegLayout& L, const uint64_t* keys, uint32_t* vals,
+// Order every run of finite keys equal in their bits from `shift` up by
+// (key, id of the element: ids_by_val[vals[p] * id_stride]), so that after
+// a sort on those bits the (r, id) order holds (shift 0: runs of equal
+// radii, ordered by id).
+void launch_tiefix(const SegLayout& L, uint64_t* keys, uint32_t* vals,
                    const uint32_t* ids_by_val, int id_stride, uint32_t* err,
-                   cudaStream_t st);
+                   cudaStream_t st, int shift = 0);
 
 void launch_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out,
                    cudaStream_t st);

@@ -282,40 +282,49 @@ __global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 4 : 2))
 // by one thread per run; a run that is already ordered costs one pass).
 constexpr long long kTieMoveCap = 1ll << 22;
 
-__global__ void k_tiefix(const int64_t* off, int n_seg, int64_t n, const uint64_t* keys,
-                         uint32_t* vals, const uint32_t* ids_by_val, int id_stride,
+__global__ void k_tiefix(const int64_t* off, int n_seg, int64_t n, uint64_t* keys,
+                         uint32_t* vals, const uint32_t* ids_by_val, int id_stride, int shift,
                          uint32_t* err, unsigned long long* stats) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   int c = seg_find(off, n_seg, p);
   int64_t sb = __ldg(off + c), se = __ldg(off + c + 1);
-  uint64_t kp = keys[p];
-  if (key_is_escaper(kp) || p + 1 >= se || keys[p + 1] != kp) return;
-  if (p > sb && keys[p - 1] == kp) return;  // not the start of the run
+  const uint64_t kp = keys[p], hp = kp >> shift;
+  if (key_is_escaper(kp) || p + 1 >= se || (keys[p + 1] >> shift) != hp) return;
+  if (p > sb && (keys[p - 1] >> shift) == hp) return;  // not the start of the run
   int64_t e = p + 2;
-  while (e < se && keys[e] == kp) ++e;
+  while (e < se && (keys[e] >> shift) == hp) ++e;
   for (int64_t i = p; i < e; ++i)
     if ((int64_t)vals[i] >= n) {
       set_err(err, kErrTimeout);
       return;
     }
+  // insertion sort of the run by (key, id)
   long long moves = 0;
+  bool equal = false;
   for (int64_t i = p + 1; i < e; ++i) {
-    uint32_t v = vals[i];
-    uint32_t idv = ids_by_val[(size_t)v * id_stride];
+    const uint64_t kv = keys[i];
+    const uint32_t v = vals[i];
+    const uint32_t idv = ids_by_val[(size_t)v * id_stride];
     int64_t j = i - 1;
-    while (j >= p && ids_by_val[(size_t)vals[j] * id_stride] > idv) {
+    while (j >= p) {
+      const uint64_t kj = keys[j];
+      if (kj == kv) equal = true;
+      if (!(kj > kv || (kj == kv && ids_by_val[(size_t)vals[j] * id_stride] > idv))) break;
+      keys[j + 1] = kj;
       vals[j + 1] = vals[j];
       --j;
       if (++moves > kTieMoveCap) {
         set_err(err, kErrTies);
+        keys[j + 1] = kv;
         vals[j + 1] = v;
         return;
       }
     }
+    keys[j + 1] = kv;
     vals[j + 1] = v;
   }
-  if (stats) atomicAdd(stats + (size_t)c * kStStride + kStTies, 1ull);
+  if (equal && stats) atomicAdd(stats + (size_t)c * kStStride + kStTies, 1ull);
 }
 
 __global__ void k_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out) {
@@ -447,12 +456,12 @@ cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint3
   return cudaGetLastError();
 }
 
-void launch_tiefix(const SegLayout& L, const uint64_t* keys, uint32_t* vals,
+void launch_tiefix(const SegLayout& L, uint64_t* keys, uint32_t* vals,
                    const uint32_t* ids_by_val, int id_stride, uint32_t* err,
-                   cudaStream_t st) {
+                   cudaStream_t st, int shift) {
   if (L.n == 0) return;
-  k_tiefix<<<(unsigned)((L.n + 255) / 256), 256, 0, st>>>(L.off, L.n_seg, L.n, keys, vals,
-                                                         ids_by_val, id_stride, err, L.stats);
+  k_tiefix<<<(unsigned)((L.n + 255) / 256), 256, 0, st>>>(
+      L.off, L.n_seg, L.n, keys, vals, ids_by_val, id_stride, shift, err, L.stats);
 }
 
 void launch_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out,

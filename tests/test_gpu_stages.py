@@ -34,12 +34,18 @@ def test_philox_bit_exact(g, orc):
 
 
 @pytest.mark.parametrize("n", SIZES)
-@pytest.mark.parametrize("case", ["random", "ties", "short_ties", "escapers"])
+@pytest.mark.parametrize("case", ["random", "ties", "short_ties", "near_ties", "escapers"])
 def test_sort_permutation_bit_exact(g, orc, n, case):
     rng = np.random.default_rng(n)
     r = rng.lognormal(0.0, 1.5, n)
     ids = rng.permutation(n).astype(np.uint32)
-    if case == "ties":
+    if case == "near_ties":
+        # radii that differ only in the lowest mantissa bits (equal in the
+        # bits the radix passes sort on), some exactly equal, shuffled
+        base = np.repeat(rng.lognormal(0.0, 1.5, (n + 3) // 4), 4)[:n]
+        r = base * (1.0 + rng.integers(0, 8, n) * 2.0 ** -50)
+        r = r[rng.permutation(n)]
+    elif case == "ties":
         r = np.round(r, 1) + 0.05  # long runs of equal radii in scrambled id order
     elif case == "short_ties":
         r = np.round(r, 5) + 1e-6  # pairs and triples of equal radii
