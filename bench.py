@@ -30,7 +30,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "star-updates/s per timestep at N=1e7 (1 GB300) + HBM roofline %, mixed vs FP64"
 UNIT = "star-updates/s"
-PROFILE = os.path.join(ROOT, "profiles", "orbit_kernel_counters.md")
+PROFILE = os.path.join(ROOT, "profiles", "step_kernels_N1e7_mixed.md")
 
 
 def log(*a):
@@ -103,17 +103,21 @@ def measured_peaks():
     return 6800.0, "fallback"
 
 
-def orbit_source_hash() -> str:
+def kernel_source_hash() -> str:
+    """Hash of every CUDA source of the library (as the profile summaries
+    record it): a summary's DRAM figures count only for the same kernels."""
     h = hashlib.sha256()
-    for f in ("orbit.cu", "cmc_device.cuh"):
-        with open(os.path.join(ROOT, "paper_1206_5878_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+    csrc = os.path.join(ROOT, "paper_1206_5878_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".hpp")):
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic_per_star(precision: str):
-    """DRAM bytes per star of the orbit kernel from the committed ncu summary,
-    or None when the kernel source changed since the counters were taken."""
+def profiled_traffic_per_star(kernel: str, precision: str):
+    """DRAM bytes per star of one kernel launch from the committed ncu
+    summary, or None when a kernel source changed since it was taken."""
     if not os.path.exists(PROFILE):
         return None
     src, val = None, None
@@ -121,17 +125,30 @@ def profiled_traffic_per_star(precision: str):
         for line in f:
             if line.startswith("source_hash:"):
                 src = line.split(":", 1)[1].strip()
-            if line.startswith("dram_bytes_per_star_%s:" % precision):
+            if line.startswith("dram_bytes_per_star_%s_%s:" % (kernel, precision)):
                 val = float(line.split(":", 1)[1])
-    if src != orbit_source_hash():
+    if src != kernel_source_hash():
         return None
     return val
 
 
-# Compulsory HBM bytes of one orbit-kernel launch per bound star: it reads
-# r, v_r, v_t, Phi, m (8 B each) and id (4 B), and writes the sort key (8 B)
-# and the 48-B payload record.  Table probes are not counted.
-ORBIT_BYTES_PER_STAR = 5 * 8 + 4 + 8 + 48
+# Compulsory HBM bytes per star of each stage's kernels (table probes and
+# scratch between the kernels of one stage not counted), and the kernel
+# that carries the stage (mixed mode).
+#   timestep:   r, v_r, v_t, m read (32 B)
+#   relax:      v_r, v_t, m (8 B each), id (4 B) read; v_r, v_t written
+#   turning:    r, v_r, v_t, Phi read; r_min, r_max written
+#   orbit:      r, v_r, v_t, Phi, m, id read; sort key and 48-B payload written
+#   sort:       6 passes of key + value read and written
+#   gather:     key, value and payload read; r, 1/r, v_r, v_t, m, id, r_old, c written
+#   potential:  1/r, m read twice; Phi, M, the float table written
+#   correction: r, 1/r, Phi, v_r, v_t, r_old, c read; v_r, v_t written
+STAGE_BYTES = {"timestep": 32, "relax": 44, "turning": 48, "orbit": 5 * 8 + 4 + 8 + 48,
+               "sort": 6 * 24, "gather": 12 + 48 + 60, "potential": 32 + 24,
+               "correction": 56 + 16}
+STAGE_KERNEL = {"timestep": "k_bins", "relax": "k_relax", "turning": "k_turning_mixed",
+                "orbit": "k_orbit", "sort": "k_pass", "gather": "k_gather",
+                "potential": "k_potential", "correction": "k_correction_mixed"}
 
 
 # ------------------------------------------------------------ oracle sample
@@ -275,17 +292,23 @@ def run_cmc(args, rank, world, local_rank):
     stages_avg = {k: v / args.steps for k, v in stages.items()}
     dom = max(stages_avg, key=stages_avg.get)
     hbm, peak_kind = measured_peaks()
-    orbit_ms = stages_avg["orbit"]
-    achieved = ORBIT_BYTES_PER_STAR * n / (orbit_ms / 1e3) / 1e9
-    traffic_ps = profiled_traffic_per_star(args.precision)
+    # roofline of the dominant stage's kernel (the stage is one launch but
+    # for the orbit sampling, timed over its kernels)
+    dom_ms = stages_avg[dom]
+    nbytes = STAGE_BYTES.get(dom, 0) * n
+    achieved = nbytes / (dom_ms / 1e3) / 1e9
     tun = c.tuning()
-    kname = "k_orbit (%s sampling, variant %d, %d threads/block)" % (
-        args.precision, tun["orbit_variant"] if prec else 0, tun["orbit_block"])
-    roof = {"kernel": kname, "bound": "hbm", "achieved": achieved, "peak": hbm,
+    kname = STAGE_KERNEL.get(dom, dom)
+    if dom == "orbit":
+        kname = "k_sample32 + k_pending64 + k_orbit (mixed sampling, variant %d)" % (
+            tun["orbit_variant"]) if prec else "k_orbit (FP64)"
+    traffic_ps = profiled_traffic_per_star(STAGE_KERNEL.get(dom, dom), args.precision)
+    roof = {"kernel": kname, "stage": dom, "bound": "hbm", "achieved": achieved, "peak": hbm,
             "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind,
-            "algorithmic_bytes_per_launch": ORBIT_BYTES_PER_STAR * n,
+            "algorithmic_bytes_per_launch": nbytes,
             "traffic": None if traffic_ps is None else traffic_ps * n,
-            "launch_ms": orbit_ms, "dominant_stage": dom}
+            "launch_ms": dom_ms,
+            "note": "bound by FP64 issue and dependent table lookups, not HBM bandwidth"}
     # step-level compulsory traffic (248 B per star-update) against HBM
     step_frac = 248.0 * value / world / 1e9 / hbm
 

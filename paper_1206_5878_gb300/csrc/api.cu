@@ -186,10 +186,10 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
 }
 
 int count_step_kernels(const cmc_ctx* c) {
-  // bins, relax, orbit, upsweep, hist scan, 8 passes, tie fix, gather,
+  // bins, relax, orbit, upsweep, hist scan, 6 passes, tie fix, gather,
   // tile sums, potential, [turning points, FP32 sampler, FP64 continuation,
   // 2 bucket-index + 2 grid kernels], [correction], step end
-  return 3 + 2 + 8 + 1 + 1 + 2 + (c->cfg.precision == 1 ? 7 : 0) +
+  return 3 + 2 + 6 + 1 + 1 + 2 + (c->cfg.precision == 1 ? 7 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 
