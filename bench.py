@@ -210,6 +210,88 @@ def cpu_baseline(n: int, seed: int, n_orbit: int = 50_000):
                        % (n, n_orbit))}
 
 
+# ------------------------------------------------------------------ suite
+SUITE = [
+    # name, N, masses, precisions, steps (the measured-workload list)
+    ("plummer_1e4_fp64", 10_000, "equal", ("fp64",), 10),
+    ("plummer_1e5", 100_000, "equal", ("fp64", "mixed"), 200),
+    ("salpeter_1e6_mixed", 1_000_000, "salpeter", ("mixed",), 100),
+    ("ensemble_64", None, "equal", ("fp64", "mixed"), 50),
+    ("plummer_1e7", 10_000_000, "equal", ("mixed", "fp64"), 20),
+]
+
+
+def run_suite(args):
+    """Every measured workload: star-updates/s over the timed steps (CUDA
+    events around the graph launches), total-energy drift from the start,
+    the 10/50/90% Lagrangian radii at the end, the sort and potential stages
+    against HBM (their compulsory bytes), and the oracle's star-updates/s on
+    one core (whole steps up to N = 1e5, sampled orbit steps above).  One
+    JSON line per workload and precision."""
+    import numpy as np
+    import torch
+
+    import initial_conditions as ic
+    import paper_1206_5878_gb300 as g
+    g.load()
+    hbm, _ = measured_peaks()
+    for name, n, masses, precs, steps in SUITE:
+        if name == "ensemble_64":
+            cat, sizes, seeds = ic.ensemble(64, seed=1)
+            state, sizes, seeds = cat, [int(x) for x in sizes], [int(x) for x in seeds]
+            n = sum(sizes)
+        else:
+            d = ic.plummer(n, seed=1, masses=masses)
+            state = {k: d[k] for k in ("r", "vr", "vt", "m", "id")}
+            sizes, seeds = None, [1]
+        dev = {k: torch.from_numpy(np.ascontiguousarray(
+            v if k != "id" else v.view(np.int32))).cuda() for k, v in state.items()}
+        cpu = None
+        if args.cpu and name != "ensemble_64":
+            cpu = cpu_baseline_full(n, masses) if n <= 100_000 else \
+                cpu_baseline(n, 1, n_orbit=20_000)["value"]
+        for prec in precs:
+            c = g.Cluster(dev, seeds, sizes=sizes, precision=1 if prec == "mixed" else 0)
+            E0 = c.total_energy()
+            c.step(2)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            c.step(steps)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            drift = float(np.max(np.abs(c.total_energy() / E0 - 1)))
+            stg = c.step_profiled(2)
+            lag = c.lagrange_radii([0.1, 0.5, 0.9])[0].tolist() if sizes is None else None
+            st = c.stats()
+            esc = sum(x["escaped"] for x in st)
+            out = {"workload": name, "precision": prec, "n_stars": n, "clusters": len(seeds),
+                   "steps": steps + 2, "ms_per_step": ms,
+                   "star_updates_per_s": n / (ms / 1e3),
+                   "energy_drift": drift, "escaped": esc, "lagrange_10_50_90": lag,
+                   "sort_hbm_frac": STAGE_BYTES["sort"] * n / (stg["sort"] / 2 / 1e3) / 1e9 / hbm,
+                   "potential_hbm_frac": STAGE_BYTES["potential"] * n /
+                   (stg["potential"] / 2 / 1e3) / 1e9 / hbm,
+                   "stages_ms": {k: v / 2 for k, v in stg.items()},
+                   "oracle_star_updates_per_s": cpu}
+            print(json.dumps(out), flush=True)
+            c.close()
+
+
+def cpu_baseline_full(n: int, masses: str) -> float:
+    """The oracle's whole timestep (every stage on every star) on one core."""
+    import initial_conditions as ic
+    import oracle
+    oracle.build()
+    d = ic.plummer(n, seed=1, masses=masses)
+    o = oracle.Cluster(d["r"], d["vr"], d["vt"], d["m"], d["id"], seed=1)
+    t0 = time.perf_counter()
+    o.step(1)
+    return n / (time.perf_counter() - t0)
+
+
 # ------------------------------------------------------------------- arms
 def run_reference(args, rank, world):
     if rank != 0:
@@ -385,6 +467,9 @@ def main():
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
     ap.add_argument("--cpu-orbit-sample", type=int, default=50_000)
     ap.add_argument("--ref-orbit-sample", type=int, default=20_000)
+    ap.add_argument("--suite", action="store_true",
+                    help="run every measured workload (one JSON line each) instead of the "
+                         "N=1e7 benchmark line")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -394,6 +479,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.suite:
+        run_suite(args)
         return
     if world > 1:
         import torch
