@@ -126,7 +126,8 @@ void order_state(cmc_ctx* c, cudaStream_t st) {
   cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
   const bool mixed = c->cfg.precision == 1;
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32,
-                   mixed ? c->Mbuf : nullptr, false, st, mixed ? c->bk.node : nullptr);
+                   mixed ? c->Mbuf : nullptr, false, st, mixed ? c->bk.node : nullptr,
+                   mixed ? c->bk.tdf : nullptr);
   if (mixed) {
     launch_buckets(L, c->t32, false, c->bk, st);
     launch_grid(L, c->x, c->phi, c->Mbuf, false, c->bk, st);
@@ -167,7 +168,8 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   mark(6);
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
                    mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, true, st,
-                   mixed ? c->bk.node : nullptr);
+                   mixed ? c->bk.node : nullptr,
+                   mixed ? c->bk.tdf : nullptr);
   if (mixed) {
     launch_buckets(L, c->t32, true, c->bk, st);
     launch_grid(L, c->x, c->phi, c->Mbuf, true, c->bk, st);
@@ -804,7 +806,7 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
       if (!e) {
         launch_buckets(S.L, t32, false, bk, st);
         launch_slopes(n, x, phi, sl, st);
-        launch_make_nodes(n, r, x, phi, sl, bk.node, st);
+        launch_make_nodes(n, r, x, phi, sl, bk.node, bk.tdf, st);
         launch_grid(S.L, x, phi, sl, false, bk, st);
       }
     }

@@ -129,10 +129,11 @@ void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* val
 // kernels that read a few nodes at random).
 void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
                       double* tile_m, double* tile_mx, double* phi, float2* t32,
-                      double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node = nullptr);
-// node records from the arrays (stage calls)
+                      double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node = nullptr,
+                      float4* tdf = nullptr);
+// node records (and float-pair table) from the arrays (stage calls)
 void launch_make_nodes(int64_t n, const double* r, const double* x, const double* phi,
-                       const double* M, double4_32a* node, cudaStream_t st);
+                       const double* M, double4_32a* node, float4* tdf, cudaStream_t st);
 
 void launch_correction(const SegLayout& L, const double* r, const double* x,
                        const double* phi, double* vr, double* vt, const double* r_old,
@@ -171,6 +172,7 @@ struct BucketArgs {
   const int4* gprm = nullptr;    // key0, sh, cells, key of 1/r_0 (as int)
   const float4* gaux = nullptr;  // Phi_0, bound mass, 1/r at key0, interpolation bound
   const double4_32a* node = nullptr; // {r, 1/r, Phi, M} per star (potential kernel)
+  const float4* tdf = nullptr;       // {1/r, Phi} per star as float pairs (hi, lo, hi, lo)
 };
 
 struct BucketWork {
@@ -184,11 +186,13 @@ struct BucketWork {
   float4* gaux = nullptr;
   int64_t gcells = 0;  // grid cells over all segments
   double4_32a* node = nullptr;
+  float4* tdf = nullptr;
   BucketArgs args() const {
     BucketArgs a;
     a.start = start; a.off = off; a.base = base; a.prm = prm;
     a.gphi = gphi; a.goff = goff; a.gprm = gprm; a.gaux = gaux;
     a.node = node;
+    a.tdf = tdf;
     return a;
   }
 };

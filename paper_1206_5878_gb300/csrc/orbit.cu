@@ -69,14 +69,25 @@ __device__ __forceinline__ double shell_root64(const Table64& T, const Star& s, 
 // Phi = Phi_j + M_j (x_j - x) needs no division (mixed mode).  The cores
 // take the node values, so that values loaded ahead and the table give
 // the same arithmetic.
+// inside (optional): whether the root lies inside the shell by more than
+// its rounding error (relative margin 2^-30, with D and A - E free of
+// cancellation beyond 2^-20), so that the FP64 Q has the bracket's signs at
+// both nodes
 __device__ __forceinline__ double rmax_core(const Star& s, double rj, double xj, double pj,
-                                            double Mj, bool has_next, double rj1) {
+                                            double Mj, bool has_next, double rj1,
+                                            bool* inside = nullptr) {
   const double B = Mj;
   const double A = pj + B * xj;
-  double D = B * B + 2.0 * (s.J * s.J) * (s.E - A);
+  const double t = 2.0 * (s.J * s.J) * (s.E - A);
+  double D = B * B + t;
   if (!(D > 0.0)) D = 0.0;
   const double sD = sqrt(D);
   double root = (B + sD) / (2.0 * (A - s.E));
+  if (inside) {
+    const double m = 0x1p-30;
+    *inside = D > 0x1p-20 * (B * B + fabs(t)) && fabs(A - s.E) > 0x1p-20 * fabs(A) &&
+              root > rj * (1.0 + m) && (!has_next || root < rj1 * (1.0 - m));
+  }
   if (!(root >= rj)) root = rj;
   if (has_next && root > rj1) root = rj1;
   return root;
@@ -89,19 +100,30 @@ __device__ __forceinline__ double rmax_core(const Star& s, double rj, double xj,
 // holding both kinds of star runs them once.  Central: node values of
 // node 0 and rj = r_0.
 __device__ __forceinline__ double rmin_core(const Star& s, bool central, double rj, double xj,
-                                            double pj, double Mj, bool has_next, double rj1) {
+                                            double pj, double Mj, bool has_next, double rj1,
+                                            bool* inside = nullptr) {
   const double B = central ? 0.0 : Mj;
-  double D, num;
+  double D, num, scale;
   if (central) {
     D = 2.0 * (s.E - pj);
     num = s.J;
+    scale = 2.0 * (fabs(s.E) + fabs(pj));
   } else {
     const double A = pj + B * xj;
-    D = B * B + 2.0 * (s.J * s.J) * (s.E - A);
+    const double t = 2.0 * (s.J * s.J) * (s.E - A);
+    D = B * B + t;
     if (!(D > 0.0)) D = 0.0;
     num = s.J * s.J;
+    scale = B * B + fabs(t);
   }
   double root = num / (B + sqrt(D));
+  if (inside) {
+    // central: inside node 0 (the bracket -1); else inside shell j
+    const double m = 0x1p-30;
+    *inside = D > 0x1p-20 * scale &&
+              (central ? root < rj * (1.0 - m)
+                       : root > rj * (1.0 + m) && (!has_next || root < rj1 * (1.0 - m)));
+  }
   if (central) {
     if (!(root >= 0.0)) root = 0.0;
     if (root > rj) root = rj;
@@ -376,6 +398,63 @@ __device__ __forceinline__ float u01f(uint32_t hi) {
   return (__uint_as_float(0x3F800000u | (hi >> 9)) - 1.0f) + 0x1p-24f;
 }
 
+// ------------------------------------------- double-float (float pairs)
+// A value as hi + lo with two floats (~48 bits), from the error-free sum of
+// two floats (Knuth's two-sum; every operation rounds once, no contraction)
+// and product (the fused multiply-add gives the product's error exactly).
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF df_of(double v) {
+  DF d;
+  d.hi = (float)v;
+  d.lo = (float)(v - (double)d.hi);
+  return d;
+}
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = a + b;
+  const float bb = s - a;
+  DF d;
+  d.hi = s;
+  d.lo = (a - (s - bb)) + (b - bb);
+  return d;
+}
+
+__device__ __forceinline__ DF df_norm(float hi, float lo) {
+  const float s = hi + lo;
+  DF d;
+  d.hi = s;
+  d.lo = lo - (s - hi);
+  return d;
+}
+
+__device__ __forceinline__ DF df_sub(DF a, DF b) {
+  const DF s = two_sum(a.hi, -b.hi);
+  return df_norm(s.hi, s.lo + (a.lo - b.lo));
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = a.hi * b.hi;
+  const float e = __fmaf_rn(a.hi, b.hi, -p);
+  return df_norm(p, e + (a.hi * b.lo + a.lo * b.hi));
+}
+
+// sign of Q = 2 (E - Phi) - (J x)^2 at a node from the float pairs (a
+// positive or negative float with the sign of Q; the pairs resolve Q to
+// ~1e-13 of |E| + |Phi| + L^2, finer than the steps between neighbouring
+// nodes of a 10^7-star cluster)
+__device__ __forceinline__ float node_q_df(const float4* __restrict__ tdf, DF E, DF J, int i) {
+  const float4 t = __ldg(tdf + i);
+  const DF x{t.x, t.y}, ph{t.z, t.w};
+  const DF d = df_sub(E, ph);
+  const DF L = df_mul(J, x);
+  const DF L2 = df_mul(L, L);
+  const DF q = df_sub(DF{2.0f * d.hi, 2.0f * d.lo}, L2);
+  return q.hi != 0.0f ? q.hi : q.lo;
+}
+
 // Q in FP32 at grid point g (1/r from the grid key, Phi from the grid)
 __device__ __forceinline__ float grid_q(const Grid& G, float E, float J, int g, float& xg) {
   xg = __uint_as_float(G.key0 + ((uint32_t)g << G.sh));
@@ -397,8 +476,9 @@ __device__ __forceinline__ float node_q(const float2* __restrict__ t, float E, f
 // Q32 < 0 or the virtual node nb; r_min: j with Q32 < 0 or -1, j + 1 with
 // Q32 >= 0 or the star).  Returns false when a walk exceeds its bound.
 __device__ __forceinline__ bool grid_brackets(const Grid& G, const float2* __restrict__ t,
-                                              const Buckets& BK, float E, float J, int nb, int k,
-                                              int& jmax, int& jmin) {
+                                              const float4* __restrict__ tdf,
+                                              const Buckets& BK, float E, float J, DF Ed, DF Jd,
+                                              int nb, int k, int& jmax, int& jmin) {
   const float xk = __ldg(&t[k].x);
   const uint32_t kk = __float_as_uint(xk);
   if (G.cells < 2 || kk < G.key0) return false;
@@ -440,13 +520,13 @@ __device__ __forceinline__ bool grid_brackets(const Grid& G, const float2* __res
   bool d1 = false, d2 = false;
   for (int w = 0; w < 64 && !(d1 && d2); ++w) {
     if (!d1) {
-      if (j1 + 1 < nb && !(node_q(t, E, J, j1 + 1) < 0.0f)) ++j1;
-      else if (j1 > k && node_q(t, E, J, j1) < 0.0f) --j1;
+      if (j1 + 1 < nb && !(node_q_df(tdf, Ed, Jd, j1 + 1) < 0.0f)) ++j1;
+      else if (j1 > k && node_q_df(tdf, Ed, Jd, j1) < 0.0f) --j1;
       else d1 = true;
     }
     if (!d2) {
-      if (j2 + 1 < k && node_q(t, E, J, j2 + 1) < 0.0f) ++j2;
-      else if (j2 >= 0 && !(node_q(t, E, J, j2) < 0.0f)) --j2;
+      if (j2 + 1 < k && node_q_df(tdf, Ed, Jd, j2 + 1) < 0.0f) ++j2;
+      else if (j2 >= 0 && !(node_q_df(tdf, Ed, Jd, j2) < 0.0f)) --j2;
       else d2 = true;
     }
   }
@@ -523,13 +603,14 @@ __device__ __forceinline__ int64_t verify_rmin_nodes(const Table64& T,
 // r_min over [-1, k]), each bracket verified in FP64 by a bounded walk,
 // then the FP64 roots inside the bracketing shells (Eq. 12).
 __device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __restrict__ t,
+                                              const float4* __restrict__ tdf,
                                               const double4_32a* __restrict__ nd, const Grid& G,
                                               const Buckets& BK, const Star& s, double& rmin,
                                               double& rmax) {
   const float E32 = (float)s.E, J32 = (float)s.J;
   const int nb32 = (int)T.nb, k32 = (int)s.k;
   int lo1, lo2;
-  if (!grid_brackets(G, t, BK, E32, J32, nb32, k32, lo1, lo2)) {
+  if (!grid_brackets(G, t, tdf, BK, E32, J32, df_of(s.E), df_of(s.J), nb32, k32, lo1, lo2)) {
     // both node bisections in FP32, in lockstep
     lo1 = k32, lo2 = -1;
     int hi1 = nb32, hi2 = k32;
@@ -546,13 +627,27 @@ __device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __
       if (a2) { if (n2) lo2 = m2; else hi2 = m2; }
     }
   }
-  // FP64 walks from the FP32 brackets on the node records, which hold the
-  // values the roots need next
-  double4_32a a1, b1, a2, b2;
-  const int64_t jmax = verify_rmax_nodes(T, nd, s, lo1, a1, b1);
-  const int64_t jmin = verify_rmin_nodes(T, nd, s, lo2, a2, b2);
-  rmax = rmax_core(s, a1.x, a1.y, a1.z, a1.w, jmax + 1 < T.nb, b1.x);
-  rmin = rmin_core(s, jmin < 0, a2.x, a2.y, a2.z, jmin < 0 ? 0.0 : a2.w, jmin >= 0, b2.x);
+  // The FP64 roots in the shells of these brackets, from the node records.
+  // A root inside its shell by more than its rounding error means the FP64
+  // Q changes sign between the shell's nodes: the bracket is the one the
+  // FP64 walk would stop at, and the root is final.  Otherwise the FP64
+  // walk runs from the bracket and the root is taken again.
+  const int64_t nb = T.nb;
+  const int64_t ja = lo1 < s.k ? s.k : (lo1 > nb - 1 ? nb - 1 : lo1);
+  const int64_t jb = lo2 < -1 ? -1 : (lo2 > s.k - 1 ? s.k - 1 : lo2);
+  double4_32a a1 = nd[ja], b1 = ja + 1 < nb ? nd[ja + 1] : a1;
+  double4_32a a2 = nd[jb < 0 ? 0 : jb], b2 = nd[jb + 1];
+  bool in1, in2;
+  rmax = rmax_core(s, a1.x, a1.y, a1.z, a1.w, ja + 1 < nb, b1.x, &in1);
+  rmin = rmin_core(s, jb < 0, a2.x, a2.y, a2.z, jb < 0 ? 0.0 : a2.w, jb >= 0, b2.x, &in2);
+  if (!in1) {
+    const int64_t jmax = verify_rmax_nodes(T, nd, s, lo1, a1, b1);
+    rmax = rmax_core(s, a1.x, a1.y, a1.z, a1.w, jmax + 1 < nb, b1.x);
+  }
+  if (!in2) {
+    const int64_t jmin = verify_rmin_nodes(T, nd, s, lo2, a2, b2);
+    rmin = rmin_core(s, jmin < 0, a2.x, a2.y, a2.z, jmin < 0 ? 0.0 : a2.w, jmin >= 0, b2.x);
+  }
 }
 
 // First kernel of the mixed-mode orbit step: the turning points of every
@@ -586,7 +681,7 @@ __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
   BK.nbk = pr.y;
   BK.lo = pr.z;
   BK.hi = pr.w;
-  turning_mixed(T, t32 + sb, BA.node + sb, grid_of(BA, c), BK, s, rmin, rmax);
+  turning_mixed(T, t32 + sb, BA.tdf + sb, BA.node + sb, grid_of(BA, c), BK, s, rmin, rmax);
   tp_min[p] = rmin;
   tp_max[p] = rmax;
 }
@@ -1206,6 +1301,7 @@ cudaError_t alloc_buckets(BucketWork& B, const SegLayout& L, cudaStream_t st) {
   if ((e = cudaMallocAsync((void**)&B.gprm, sizeof(int4) * L.n_seg, st))) return e;
   if ((e = cudaMallocAsync((void**)&B.gaux, sizeof(float4) * L.n_seg, st))) return e;
   if ((e = cudaMallocAsync((void**)&B.node, sizeof(double4_32a) * (L.n > 0 ? L.n : 1), st))) return e;
+  if ((e = cudaMallocAsync((void**)&B.tdf, sizeof(float4) * (L.n > 0 ? L.n : 1), st))) return e;
   e = cudaMemcpyAsync(B.off, off.data(), sizeof(int64_t) * (L.n_seg + 1),
                       cudaMemcpyHostToDevice, st);
   if (!e)
@@ -1216,7 +1312,7 @@ cudaError_t alloc_buckets(BucketWork& B, const SegLayout& L, cudaStream_t st) {
 }
 
 void free_buckets(BucketWork& B, cudaStream_t st) {
-  void* ps[] = {B.start, B.off, B.base, B.prm, B.gphi, B.goff, B.gprm, B.gaux, B.node};
+  void* ps[] = {B.start, B.off, B.base, B.prm, B.gphi, B.goff, B.gprm, B.gaux, B.node, B.tdf};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, st);
   B = BucketWork();

@@ -129,6 +129,13 @@ __global__ void k_gather(int64_t n, const uint64_t* __restrict__ keys,
   if (c) c[p] = P.c;
 }
 
+// (hi, lo) float pairs of 1/r and Phi: hi the float nearest, lo the float
+// nearest the remainder (together ~48 bits)
+__device__ __forceinline__ float4 float_pairs(double x, double ph) {
+  const float xh = (float)x, ph_h = (float)ph;
+  return make_float4(xh, (float)(x - (double)xh), ph_h, (float)(ph - (double)ph_h));
+}
+
 // ------------------------------------------------------------ potential
 // padded shared-memory slot of tile element e: one spare double per 16, so
 // that a thread walking its 16 consecutive elements (stride 17 words across
@@ -168,7 +175,7 @@ __global__ void __launch_bounds__(kThreads) k_potential(Seg S, const int64_t* es
                                                         const double* m, const double* tile_m,
                                                         const double* tile_mx, double* phi,
                                                         float2* t32, double* Mout,
-                                                        double4_32a* node) {
+                                                        double4_32a* node, float4* tdf) {
   extern __shared__ double smem[];
   double* s_m = smem;              // m, then M_k
   double* s_x = smem + kPadN;      // x
@@ -232,6 +239,7 @@ __global__ void __launch_bounds__(kThreads) k_potential(Seg S, const int64_t* es
     if (t32) t32[p] = make_float2((float)s_x[q], (float)ph);
     if (Mout) Mout[p] = bound ? s_m[q] : 0.0;
     if (node) node[p] = make_double4_32a(r[p], s_x[q], ph, bound ? s_m[q] : 0.0);
+    if (tdf) tdf[p] = float_pairs(s_x[q], ph);
   }
 }
 
@@ -433,9 +441,11 @@ __global__ void k_make_t32(int64_t n, const double* x, const double* phi, float2
 }
 
 __global__ void k_make_nodes(int64_t n, const double* r, const double* x, const double* phi,
-                             const double* M, double4_32a* node) {
+                             const double* M, double4_32a* node, float4* tdf) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < n) node[p] = make_double4_32a(r[p], x[p], phi[p], M[p]);
+  if (p >= n) return;
+  node[p] = make_double4_32a(r[p], x[p], phi[p], M[p]);
+  tdf[p] = float_pairs(x[p], phi[p]);
 }
 
 __global__ void k_unpack_orbit(int64_t n, const uint64_t* keys, const Payload* pay,
@@ -467,8 +477,8 @@ void launch_make_t32(int64_t n, const double* x, const double* phi, float2* t32,
 }
 
 void launch_make_nodes(int64_t n, const double* r, const double* x, const double* phi,
-                       const double* M, double4_32a* node, cudaStream_t st) {
-  if (n > 0) k_make_nodes<<<blocks_for(n, 256), 256, 0, st>>>(n, r, x, phi, M, node);
+                       const double* M, double4_32a* node, float4* tdf, cudaStream_t st) {
+  if (n > 0) k_make_nodes<<<blocks_for(n, 256), 256, 0, st>>>(n, r, x, phi, M, node, tdf);
 }
 
 void launch_unpack_orbit(int64_t n, const uint64_t* keys, const Payload* pay, double* r_new,
@@ -576,13 +586,14 @@ void potential_prepare() {
 
 void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
                       double* tile_m, double* tile_mx, double* phi, float2* t32,
-                      double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node) {
+                      double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node,
+                      float4* tdf) {
   if (!L.n_tiles) return;
   Seg S = L.dev();
   k_tile_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, L.esc_step, nb_sub, x, m, tile_m,
                                                        tile_mx);
   k_potential<<<(unsigned)L.n_tiles, kThreads, kPotentialSmem, st>>>(
-      S, L.esc_step, nb_sub, r, x, m, tile_m, tile_mx, phi, t32, Mout, node);
+      S, L.esc_step, nb_sub, r, x, m, tile_m, tile_mx, phi, t32, Mout, node, tdf);
 }
 
 void launch_correction(const SegLayout& L, const double* r, const double* x,
