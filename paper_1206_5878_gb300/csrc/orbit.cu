@@ -63,6 +63,39 @@ __device__ __forceinline__ double shell_root64(const Table64& T, const Star& s, 
   return root;
 }
 
+// --------------------------------------- comparisons on the integer pipes
+// On this GPU the FP64 pipe issues two lanes per SM and clock, and the
+// turning-point kernels are bound by it; tests that need no FP64
+// arithmetic read the bit patterns instead (IEEE-754 doubles of one sign
+// order like their patterns).  kInfBits: +Inf; patterns above it with the
+// sign clear are NaNs.
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+__device__ __forceinline__ unsigned long long ubits(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+__device__ __forceinline__ unsigned long long absbits(double v) {
+  return ubits(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+// v > 0 and not NaN (+Inf included)
+__device__ __forceinline__ bool pos_num(double v) { return ubits(v) - 1ull < kInfBits; }
+// v >= rj for rj > 0, false for NaN (as the FP64 comparison)
+__device__ __forceinline__ bool ge_pos(double v, double rj) {
+  const unsigned long long u = ubits(v);
+  return u >= ubits(rj) && u <= kInfBits;
+}
+// w > 2^-k v for |w|, |v| given as absolute bit patterns, w not NaN: below
+// exponent k the scaled v is under the smallest normal, which w then bounds
+__device__ __forceinline__ bool above_scaled(unsigned long long w, unsigned long long v, int k) {
+  const unsigned long long d = (unsigned long long)k << 52;
+  return w <= kInfBits && ((v >> 52) > (unsigned long long)k ? w > v - d : w >= (1ull << 52));
+}
+// b - a is 2^24 or more units in the last place of a, for 0 <= a < b finite,
+// so b - a > 2^-29 a: the gap of the certificates below
+__device__ __forceinline__ bool gap_above(double a, double b) {
+  const unsigned long long ua = ubits(a), ub = ubits(b);
+  return ua < kInfBits && ub < kInfBits && ub > ua && ub - ua >= (1ull << 24);
+}
+
 // The same root with the slope of shell j taken from the enclosed mass:
 // across shell j, (Phi_{j+1} - Phi_j)/(x_j - x_{j+1}) = G M_j exactly
 // (Eqs. 1-5; for the outermost shell M_j is the bound mass), so
@@ -70,26 +103,31 @@ __device__ __forceinline__ double shell_root64(const Table64& T, const Star& s, 
 // take the node values, so that values loaded ahead and the table give
 // the same arithmetic.
 // inside (optional): whether the root lies inside the shell by more than
-// its rounding error (relative margin 2^-30, with D and A - E free of
-// cancellation beyond 2^-20), so that the FP64 Q has the bracket's signs at
-// both nodes
+// its rounding error, so that the FP64 Q has the bracket's signs at both
+// nodes: the root at least 2^24 ulps (a relative gap above 2^-29) from
+// each node, D above 2^-19 max(B^2, |t|) and |A - E| above 2^-20 |A|
+// (neither more than 20 bits cancelled).  The clamps are the FP64
+// comparisons restated on the bit patterns (radii are positive).
 __device__ __forceinline__ double rmax_core(const Star& s, double rj, double xj, double pj,
                                             double Mj, bool has_next, double rj1,
                                             bool* inside = nullptr) {
   const double B = Mj;
   const double A = pj + B * xj;
-  const double t = 2.0 * (s.J * s.J) * (s.E - A);
-  double D = B * B + t;
-  if (!(D > 0.0)) D = 0.0;
+  const double em = s.E - A;
+  const double BB = B * B;
+  const double t = 2.0 * (s.J * s.J) * em;
+  double D = BB + t;
+  if (!pos_num(D)) D = 0.0;
   const double sD = sqrt(D);
-  double root = (B + sD) / (2.0 * (A - s.E));
+  // 2 (A - E) = -(2 (E - A)) exactly
+  double root = (B + sD) / -(2.0 * em);
   if (inside) {
-    const double m = 0x1p-30;
-    *inside = D > 0x1p-20 * (B * B + fabs(t)) && fabs(A - s.E) > 0x1p-20 * fabs(A) &&
-              root > rj * (1.0 + m) && (!has_next || root < rj1 * (1.0 - m));
+    const unsigned long long bt = absbits(BB) > absbits(t) ? absbits(BB) : absbits(t);
+    *inside = above_scaled(ubits(D), bt, 19) && above_scaled(absbits(em), absbits(A), 20) &&
+              gap_above(rj, root) && (!has_next || gap_above(root, rj1));
   }
-  if (!(root >= rj)) root = rj;
-  if (has_next && root > rj1) root = rj1;
+  if (!ge_pos(root, rj)) root = rj;
+  if (has_next && ubits(root) > ubits(rj1)) root = rj1;
   return root;
 }
 
@@ -103,33 +141,40 @@ __device__ __forceinline__ double rmin_core(const Star& s, bool central, double 
                                             double pj, double Mj, bool has_next, double rj1,
                                             bool* inside = nullptr) {
   const double B = central ? 0.0 : Mj;
-  double D, num, scale;
+  double D, num;
+  unsigned long long scale;
+  int sk;
   if (central) {
     D = 2.0 * (s.E - pj);
     num = s.J;
-    scale = 2.0 * (fabs(s.E) + fabs(pj));
+    // 2 (|E| + |Phi_0|) <= 4 max(|E|, |Phi_0|)
+    scale = absbits(s.E) > absbits(pj) ? absbits(s.E) : absbits(pj);
+    sk = 18;
   } else {
     const double A = pj + B * xj;
+    const double BB = B * B;
     const double t = 2.0 * (s.J * s.J) * (s.E - A);
-    D = B * B + t;
-    if (!(D > 0.0)) D = 0.0;
+    D = BB + t;
+    if (!pos_num(D)) D = 0.0;
     num = s.J * s.J;
-    scale = B * B + fabs(t);
+    scale = absbits(BB) > absbits(t) ? absbits(BB) : absbits(t);
+    sk = 19;
   }
   double root = num / (B + sqrt(D));
   if (inside) {
     // central: inside node 0 (the bracket -1); else inside shell j
-    const double m = 0x1p-30;
-    *inside = D > 0x1p-20 * scale &&
-              (central ? root < rj * (1.0 - m)
-                       : root > rj * (1.0 + m) && (!has_next || root < rj1 * (1.0 - m)));
+    *inside = above_scaled(ubits(D), scale, sk) &&
+              (central ? gap_above(root, rj)
+                       : gap_above(rj, root) && (!has_next || gap_above(root, rj1)));
   }
   if (central) {
-    if (!(root >= 0.0)) root = 0.0;
-    if (root > rj) root = rj;
+    // root >= 0 (-0 included, NaN not), then root <= r_0
+    const unsigned long long u = ubits(root);
+    if (!(u <= kInfBits || u == 0x8000000000000000ull)) root = 0.0;
+    if (__double_as_longlong(root) > __double_as_longlong(rj)) root = rj;
   } else {
-    if (!(root >= rj)) root = rj;
-    if (has_next && root > rj1) root = rj1;
+    if (!ge_pos(root, rj)) root = rj;
+    if (has_next && ubits(root) > ubits(rj1)) root = rj1;
   }
   return root;
 }
@@ -413,6 +458,30 @@ __device__ __forceinline__ DF df_of(double v) {
   return d;
 }
 
+// The same split from the bit pattern with integer operations (hi: the top
+// 24 significand bits of v, lo: the next 24 of the remaining 29, both
+// truncated, together within 2^-46 |v|), for 2^-60 <= |v| < 2^100 where both
+// are normal floats; other values (zero included) by the conversions.
+__device__ __forceinline__ DF df_split(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned ex = (unsigned)(u >> 52) & 0x7FFu;
+  if (ex < 1023u - 60u || ex >= 1023u + 100u) return df_of(v);
+  const unsigned sg = (unsigned)(u >> 32) & 0x80000000u;
+  DF d;
+  d.hi = __uint_as_float(sg | ((ex - 896u) << 23) | ((unsigned)(u >> 29) & 0x7FFFFFu));
+  const unsigned ml = (unsigned)u & 0x1FFFFFFFu;
+  if (ml == 0u) {
+    d.lo = 0.0f;
+    return d;
+  }
+  const int lz = __clz((int)ml);  // 3 .. 31
+  // ml 2^(ex - 1075) = 1.f 2^(ex - 1075 + 31 - lz); exponent field in [15, 202]
+  const unsigned fe = ex - 1075u + 127u + (unsigned)(31 - lz);
+  const unsigned mant = ((ml << lz) << 1) >> 9;  // the 23 bits after the leading one
+  d.lo = __uint_as_float(sg | (fe << 23) | mant);
+  return d;
+}
+
 __device__ __forceinline__ DF two_sum(float a, float b) {
   const float s = a + b;
   const float bb = s - a;
@@ -607,10 +676,12 @@ __device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __
                                               const double4_32a* __restrict__ nd, const Grid& G,
                                               const Buckets& BK, const Star& s, double& rmin,
                                               double& rmax) {
-  const float E32 = (float)s.E, J32 = (float)s.J;
+  // E and J as float pairs; their high parts serve the FP32 searches
+  const DF Ed = df_split(s.E), Jd = df_split(s.J);
+  const float E32 = Ed.hi, J32 = Jd.hi;
   const int nb32 = (int)T.nb, k32 = (int)s.k;
   int lo1, lo2;
-  if (!grid_brackets(G, t, tdf, BK, E32, J32, df_of(s.E), df_of(s.J), nb32, k32, lo1, lo2)) {
+  if (!grid_brackets(G, t, tdf, BK, E32, J32, Ed, Jd, nb32, k32, lo1, lo2)) {
     // both node bisections in FP32, in lockstep
     lo1 = k32, lo2 = -1;
     int hi1 = nb32, hi2 = k32;
@@ -671,7 +742,10 @@ __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
   s.k = k;
   s.E = __ldg(T.phi + k) + 0.5 * (vrk * vrk + vtk * vtk);
   s.J = rk * vtk;
-  if (!(s.E < 0.0)) return;  // escaper: the sampling kernel handles it
+  // E < 0 on the bit pattern (negative, nonzero, not NaN); otherwise an
+  // escaper, which the sampling kernel handles
+  const unsigned long long eb = ubits(s.E);
+  if (!(eb > 0x8000000000000000ull && eb <= 0xFFF0000000000000ull)) return;
   double rmin, rmax;
   Buckets BK;
   const int4 pr = BA.prm[c];
