@@ -73,9 +73,6 @@ constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
 __device__ __forceinline__ unsigned long long ubits(double v) {
   return (unsigned long long)__double_as_longlong(v);
 }
-__device__ __forceinline__ unsigned long long absbits(double v) {
-  return ubits(v) & 0x7FFFFFFFFFFFFFFFull;
-}
 // v > 0 and not NaN (+Inf included)
 __device__ __forceinline__ bool pos_num(double v) { return ubits(v) - 1ull < kInfBits; }
 // v >= rj for rj > 0, false for NaN (as the FP64 comparison)
@@ -83,49 +80,23 @@ __device__ __forceinline__ bool ge_pos(double v, double rj) {
   const unsigned long long u = ubits(v);
   return u >= ubits(rj) && u <= kInfBits;
 }
-// w > 2^-k v for |w|, |v| given as absolute bit patterns, w not NaN: below
-// exponent k the scaled v is under the smallest normal, which w then bounds
-__device__ __forceinline__ bool above_scaled(unsigned long long w, unsigned long long v, int k) {
-  const unsigned long long d = (unsigned long long)k << 52;
-  return w <= kInfBits && ((v >> 52) > (unsigned long long)k ? w > v - d : w >= (1ull << 52));
-}
-// b - a is 2^24 or more units in the last place of a, for 0 <= a < b finite,
-// so b - a > 2^-29 a: the gap of the certificates below
-__device__ __forceinline__ bool gap_above(double a, double b) {
-  const unsigned long long ua = ubits(a), ub = ubits(b);
-  return ua < kInfBits && ub < kInfBits && ub > ua && ub - ua >= (1ull << 24);
-}
-
 // The same root with the slope of shell j taken from the enclosed mass:
 // across shell j, (Phi_{j+1} - Phi_j)/(x_j - x_{j+1}) = G M_j exactly
 // (Eqs. 1-5; for the outermost shell M_j is the bound mass), so
 // Phi = Phi_j + M_j (x_j - x) needs no division (mixed mode).  The cores
 // take the node values, so that values loaded ahead and the table give
-// the same arithmetic.
-// inside (optional): whether the root lies inside the shell by more than
-// its rounding error, so that the FP64 Q has the bracket's signs at both
-// nodes: the root at least 2^24 ulps (a relative gap above 2^-29) from
-// each node, D above 2^-19 max(B^2, |t|) and |A - E| above 2^-20 |A|
-// (neither more than 20 bits cancelled).  The clamps are the FP64
-// comparisons restated on the bit patterns (radii are positive).
+// the same arithmetic.  The clamps are the FP64 comparisons restated on
+// the bit patterns (radii are positive).
 __device__ __forceinline__ double rmax_core(const Star& s, double rj, double xj, double pj,
-                                            double Mj, bool has_next, double rj1,
-                                            bool* inside = nullptr) {
+                                            double Mj, bool has_next, double rj1) {
   const double B = Mj;
   const double A = pj + B * xj;
   const double em = s.E - A;
-  const double BB = B * B;
-  const double t = 2.0 * (s.J * s.J) * em;
-  double D = BB + t;
+  double D = B * B + 2.0 * (s.J * s.J) * em;
   if (!pos_num(D)) D = 0.0;
   const double sD = sqrt(D);
   // 2 (A - E) = -(2 (E - A)) exactly
   double root = (B + sD) / -(2.0 * em);
-  if (inside) {
-    const unsigned long long bt = absbits(BB) > absbits(t) ? absbits(BB) : absbits(t);
-    *inside = above_scaled(ubits(D), bt, 19) && above_scaled(absbits(em), absbits(A), 20) &&
-              gap_above(rj, root) && (!has_next || gap_above(root, rj1));
-  }
   if (!ge_pos(root, rj)) root = rj;
   if (has_next && ubits(root) > ubits(rj1)) root = rj1;
   return root;
@@ -138,35 +109,19 @@ __device__ __forceinline__ double rmax_core(const Star& s, double rj, double xj,
 // holding both kinds of star runs them once.  Central: node values of
 // node 0 and rj = r_0.
 __device__ __forceinline__ double rmin_core(const Star& s, bool central, double rj, double xj,
-                                            double pj, double Mj, bool has_next, double rj1,
-                                            bool* inside = nullptr) {
+                                            double pj, double Mj, bool has_next, double rj1) {
   const double B = central ? 0.0 : Mj;
   double D, num;
-  unsigned long long scale;
-  int sk;
   if (central) {
     D = 2.0 * (s.E - pj);
     num = s.J;
-    // 2 (|E| + |Phi_0|) <= 4 max(|E|, |Phi_0|)
-    scale = absbits(s.E) > absbits(pj) ? absbits(s.E) : absbits(pj);
-    sk = 18;
   } else {
     const double A = pj + B * xj;
-    const double BB = B * B;
-    const double t = 2.0 * (s.J * s.J) * (s.E - A);
-    D = BB + t;
+    D = B * B + 2.0 * (s.J * s.J) * (s.E - A);
     if (!pos_num(D)) D = 0.0;
     num = s.J * s.J;
-    scale = absbits(BB) > absbits(t) ? absbits(BB) : absbits(t);
-    sk = 19;
   }
   double root = num / (B + sqrt(D));
-  if (inside) {
-    // central: inside node 0 (the bracket -1); else inside shell j
-    *inside = above_scaled(ubits(D), scale, sk) &&
-              (central ? gap_above(root, rj)
-                       : gap_above(rj, root) && (!has_next || gap_above(root, rj1)));
-  }
   if (central) {
     // root >= 0 (-0 included, NaN not), then root <= r_0
     const unsigned long long u = ubits(root);
@@ -510,18 +465,24 @@ __device__ __forceinline__ DF df_mul(DF a, DF b) {
   return df_norm(p, e + (a.hi * b.lo + a.lo * b.hi));
 }
 
-// sign of Q = 2 (E - Phi) - (J x)^2 at a node from the float pairs (a
-// positive or negative float with the sign of Q; the pairs resolve Q to
-// ~1e-13 of |E| + |Phi| + L^2, finer than the steps between neighbouring
-// nodes of a 10^7-star cluster)
-__device__ __forceinline__ float node_q_df(const float4* __restrict__ tdf, DF E, DF J, int i) {
+// Q = 2 (E - Phi) - (J x)^2 at a node from the float pairs, and whether its
+// sign is certain.  The pairs hold E, J (truncated or rounded) within
+// 2^-46 and 1/r, Phi within 2^-48; each pair sum adds at most 2^-46 of its
+// operands' magnitudes and each pair product 2^-45 of its result, so L^2
+// is within 2^-42.9 and Q within 2^-42.7 of S = |E| + |Phi| + L^2.  The
+// FP64 evaluation 2 (E - Phi) - (J x) (J x) from the doubles is within
+// 2^-50 S.  Beyond 2^-40 S both therefore have the sign of the exact Q.
+__device__ __forceinline__ float node_q_df(const float4* __restrict__ tdf, DF E, DF J, int i,
+                                           bool& sure) {
   const float4 t = __ldg(tdf + i);
   const DF x{t.x, t.y}, ph{t.z, t.w};
   const DF d = df_sub(E, ph);
   const DF L = df_mul(J, x);
   const DF L2 = df_mul(L, L);
   const DF q = df_sub(DF{2.0f * d.hi, 2.0f * d.lo}, L2);
-  return q.hi != 0.0f ? q.hi : q.lo;
+  const float qv = q.hi != 0.0f ? q.hi : q.lo;
+  sure = fabsf(qv) > 0x1p-40f * ((fabsf(E.hi) + fabsf(ph.hi)) + L2.hi);
+  return qv;
 }
 
 // Q in FP32 at grid point g (1/r from the grid key, Phi from the grid)
@@ -547,9 +508,11 @@ __device__ __forceinline__ float node_q(const float2* __restrict__ t, float E, f
 __device__ __forceinline__ bool grid_brackets(const Grid& G, const float2* __restrict__ t,
                                               const float4* __restrict__ tdf,
                                               const Buckets& BK, float E, float J, DF Ed, DF Jd,
-                                              int nb, int k, int& jmax, int& jmin) {
+                                              int nb, int k, int& jmax, int& jmin, bool& cert1,
+                                              bool& cert2) {
   const float xk = __ldg(&t[k].x);
   const uint32_t kk = __float_as_uint(xk);
+  cert1 = cert2 = false;
   if (G.cells < 2 || kk < G.key0) return false;
   int gk = (int)((kk - G.key0) >> G.sh);  // grid points 0..gk lie at or outside the star
   if (gk > G.cells - 1) gk = G.cells - 1;
@@ -586,21 +549,38 @@ __device__ __forceinline__ bool grid_brackets(const Grid& G, const float2* __res
   int j2 = bhi >= G.cells ? -1 : sh[1];
   j1 = j1 < k ? k : (j1 > nb - 1 ? nb - 1 : j1);
   j2 = j2 < -1 ? -1 : (j2 > k - 1 ? k - 1 : j2);
-  bool d1 = false, d2 = false;
+  // walks; at the stop the sign tests that ended each walk are the FP64
+  // walk's own stopping tests, and when every one of them is certain the
+  // FP64 walk from this bracket would stop at once (cert)
+  bool d1 = false, d2 = false, s1a = true, s2a = true;
   for (int w = 0; w < 64 && !(d1 && d2); ++w) {
     if (!d1) {
-      if (j1 + 1 < nb && !(node_q_df(tdf, Ed, Jd, j1 + 1) < 0.0f)) ++j1;
-      else if (j1 > k && node_q_df(tdf, Ed, Jd, j1) < 0.0f) --j1;
-      else d1 = true;
+      bool su = true, sd = true;
+      if (j1 + 1 < nb && !(node_q_df(tdf, Ed, Jd, j1 + 1, su) < 0.0f)) {
+        ++j1;
+      } else if (j1 > k && node_q_df(tdf, Ed, Jd, j1, sd) < 0.0f) {
+        --j1;
+      } else {
+        d1 = true;
+        s1a = su && sd;
+      }
     }
     if (!d2) {
-      if (j2 + 1 < k && node_q_df(tdf, Ed, Jd, j2 + 1) < 0.0f) ++j2;
-      else if (j2 >= 0 && !(node_q_df(tdf, Ed, Jd, j2) < 0.0f)) --j2;
-      else d2 = true;
+      bool su = true, sd = true;
+      if (j2 + 1 < k && node_q_df(tdf, Ed, Jd, j2 + 1, su) < 0.0f) {
+        ++j2;
+      } else if (j2 >= 0 && !(node_q_df(tdf, Ed, Jd, j2, sd) < 0.0f)) {
+        --j2;
+      } else {
+        d2 = true;
+        s2a = su && sd;
+      }
     }
   }
   jmax = j1;
   jmin = j2;
+  cert1 = d1 && d2 && s1a;
+  cert2 = d1 && d2 && s2a;
   return d1 && d2;
 }
 
@@ -681,8 +661,11 @@ __device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __
   const float E32 = Ed.hi, J32 = Jd.hi;
   const int nb32 = (int)T.nb, k32 = (int)s.k;
   int lo1, lo2;
-  if (!grid_brackets(G, t, tdf, BK, E32, J32, Ed, Jd, nb32, k32, lo1, lo2)) {
-    // both node bisections in FP32, in lockstep
+  bool cert1, cert2;
+  if (!grid_brackets(G, t, tdf, BK, E32, J32, Ed, Jd, nb32, k32, lo1, lo2, cert1, cert2)) {
+    // both node bisections in FP32, in lockstep; their brackets are not
+    // certified (the FP64 walks run from them)
+    cert1 = cert2 = false;
     lo1 = k32, lo2 = -1;
     int hi1 = nb32, hi2 = k32;
     const int rounds = search_rounds(nb32);
@@ -698,27 +681,27 @@ __device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __
       if (a2) { if (n2) lo2 = m2; else hi2 = m2; }
     }
   }
-  // The FP64 roots in the shells of these brackets, from the node records.
-  // A root inside its shell by more than its rounding error means the FP64
-  // Q changes sign between the shell's nodes: the bracket is the one the
-  // FP64 walk would stop at, and the root is final.  Otherwise the FP64
-  // walk runs from the bracket and the root is taken again.
+  // A certified bracket is the one the FP64 walk stops at; otherwise that
+  // walk runs from it.  Then the FP64 roots in the bracketing shells.
   const int64_t nb = T.nb;
-  const int64_t ja = lo1 < s.k ? s.k : (lo1 > nb - 1 ? nb - 1 : lo1);
-  const int64_t jb = lo2 < -1 ? -1 : (lo2 > s.k - 1 ? s.k - 1 : lo2);
-  double4_32a a1 = nd[ja], b1 = ja + 1 < nb ? nd[ja + 1] : a1;
-  double4_32a a2 = nd[jb < 0 ? 0 : jb], b2 = nd[jb + 1];
-  bool in1, in2;
-  rmax = rmax_core(s, a1.x, a1.y, a1.z, a1.w, ja + 1 < nb, b1.x, &in1);
-  rmin = rmin_core(s, jb < 0, a2.x, a2.y, a2.z, jb < 0 ? 0.0 : a2.w, jb >= 0, b2.x, &in2);
-  if (!in1) {
-    const int64_t jmax = verify_rmax_nodes(T, nd, s, lo1, a1, b1);
-    rmax = rmax_core(s, a1.x, a1.y, a1.z, a1.w, jmax + 1 < nb, b1.x);
+  double4_32a a1, b1, a2, b2;
+  int64_t jmax, jmin;
+  if (cert1) {
+    jmax = lo1;
+    a1 = nd[jmax];
+    b1 = jmax + 1 < nb ? nd[jmax + 1] : a1;
+  } else {
+    jmax = verify_rmax_nodes(T, nd, s, lo1, a1, b1);
   }
-  if (!in2) {
-    const int64_t jmin = verify_rmin_nodes(T, nd, s, lo2, a2, b2);
-    rmin = rmin_core(s, jmin < 0, a2.x, a2.y, a2.z, jmin < 0 ? 0.0 : a2.w, jmin >= 0, b2.x);
+  if (cert2) {
+    jmin = lo2;
+    a2 = nd[jmin < 0 ? 0 : jmin];
+    b2 = nd[jmin + 1];
+  } else {
+    jmin = verify_rmin_nodes(T, nd, s, lo2, a2, b2);
   }
+  rmax = rmax_core(s, a1.x, a1.y, a1.z, a1.w, jmax + 1 < nb, b1.x);
+  rmin = rmin_core(s, jmin < 0, a2.x, a2.y, a2.z, jmin < 0 ? 0.0 : a2.w, jmin >= 0, b2.x);
 }
 
 // First kernel of the mixed-mode orbit step: the turning points of every

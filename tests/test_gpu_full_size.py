@@ -79,6 +79,31 @@ def test_orbit_sampled_full_size(g_stage, orc, big, precision):
     assert flips <= 3
 
 
+def test_mixed_turning_points_equal_fp64_on_every_star(g_stage, big):
+    """Mixed mode's r_min and r_max (float-pair bracket walks, certified or
+    walked again in FP64) equal FP64 mode's (FP64 bisection) bit for bit on
+    all 10^7 stars, at the start and after three mixed steps; about 250 stars
+    a step take the walks' fallback (an FP32 bisection), so that path is
+    covered too."""
+    g = g_stage
+    d, _, st0 = big
+    c = g.Cluster({k: d[k] for k in ("r", "vr", "vt", "m", "id")}, [1], precision=1,
+                  autotune=0)
+    try:
+        c.step(3)
+        states = [(st0, N), (c.get_state(), int(c.nbound()[0]))]
+    finally:
+        c.close()
+    for st, nb in states:
+        cut = {k: st[k][:nb] for k in ("r", "phi", "vr", "vt", "id")}
+        o = [g.stage_orbit(dev(cut["r"]), dev(cut["phi"]), dev(cut["vr"]), dev(cut["vt"]),
+                           dev(cut["id"]), 1, 5, precision=p) for p in (0, 1)]
+        for key in ("rmin", "rmax"):
+            a, b = host(o[0][key]), host(o[1][key])
+            bad = np.nonzero(a.view(np.int64) != b.view(np.int64))[0]
+            assert bad.size == 0, (key, bad[:5], a[bad[:5]], b[bad[:5]])
+
+
 def test_one_mixed_step_full_size(big):
     _, c, st = big
     c.step(1)
