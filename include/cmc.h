@@ -267,7 +267,9 @@ cmc_status cmc_energy_correction(int64_t n, const double *r, const double *phi, 
 
 /* ---------------------------------------------------------------------
  * Allocation-free shell potential.  The paper has no counterpart: this is
- * cmc_potential (same arithmetic, same results) for callers that may not
+ * cmc_potential (the same scan over the same tiles, with summation orders
+ * of its own inside a tile: results agree with cmc_potential's to rounding
+ * and repeat bit for bit from call to call) for callers that may not
  * allocate device memory -- code that runs while a stream is captured into
  * a CUDA graph, loops that forbid allocation after start-up, programs that
  * give all device memory to their own pool.  cmc_potential takes scratch

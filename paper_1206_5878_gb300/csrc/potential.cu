@@ -129,21 +129,59 @@ __global__ void k_gather(int64_t n, const uint64_t* __restrict__ keys,
   if (c) c[p] = P.c;
 }
 
+// Double -> float rounding to nearest even with integer operations: the
+// conversion instruction runs on the FP64 pipe, which the potential kernel
+// otherwise keeps busy with its scans.  For 2^-60 <= |v| < 2^126 (both
+// parts below normal floats) the top 24 significand bits are rounded by the
+// 29 bits below them; the remainder v - hi is then exact in those 29 bits
+// and rounded the same way.  Other values take the conversions.
+struct F32Pair {
+  float hi, lo;
+};
+
+__device__ __forceinline__ F32Pair f32_pair(double v) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+  const unsigned ex = (unsigned)(u >> 52) & 0x7FFu;
+  F32Pair r;
+  if (ex - 963u > 186u) {  // outside [963, 1149]
+    r.hi = (float)v;
+    r.lo = (float)(v - (double)r.hi);
+    return r;
+  }
+  const unsigned sg = (unsigned)(u >> 32) & 0x80000000u;
+  const unsigned top = ((ex - 896u) << 23) | ((unsigned)(u >> 29) & 0x7FFFFFu);
+  const unsigned rest = (unsigned)u & 0x1FFFFFFFu;  // the 29 bits below
+  const bool up = rest > 0x10000000u || (rest == 0x10000000u && (top & 1u));
+  r.hi = __uint_as_float(sg | (top + (up ? 1u : 0u)));  // a carry moves the exponent
+  // v - hi = (rest - (up ? 2^29 : 0)) 2^(ex - 1075), |.| <= 2^28
+  const int rem = (int)rest - (up ? (1 << 29) : 0);
+  if (rem == 0) {
+    r.lo = 0.0f;
+    return r;
+  }
+  const unsigned a = (unsigned)(rem < 0 ? -rem : rem);
+  const int lz = __clz((int)a);            // >= 3
+  const int pb = 31 - lz;                  // top bit of a
+  const unsigned n = a << lz;              // top bit at 31
+  unsigned m = n >> 8;                     // 24 bits with the leading one
+  const unsigned low = n & 0xFFu;
+  m += (low > 0x80u || (low == 0x80u && (m & 1u))) ? 1u : 0u;
+  // a 2^(ex - 1075) = (m / 2^23) 2^(ex - 1075 + pb); a carry to 2^24 bumps
+  // the exponent through the addition below
+  const unsigned fe = ex - 1075u + 127u + (unsigned)pb;  // in [15, 229]
+  const unsigned sl = (rem < 0 ? sg ^ 0x80000000u : sg);
+  r.lo = __uint_as_float(sl | ((fe << 23) + (m - 0x800000u)));
+  return r;
+}
+
 // (hi, lo) float pairs of 1/r and Phi: hi the float nearest, lo the float
 // nearest the remainder (together ~48 bits)
 __device__ __forceinline__ float4 float_pairs(double x, double ph) {
-  const float xh = (float)x, ph_h = (float)ph;
-  return make_float4(xh, (float)(x - (double)xh), ph_h, (float)(ph - (double)ph_h));
+  const F32Pair a = f32_pair(x), b = f32_pair(ph);
+  return make_float4(a.hi, a.lo, b.hi, b.lo);
 }
 
 // ------------------------------------------------------------ potential
-// padded shared-memory slot of tile element e: one spare double per 16, so
-// that a thread walking its 16 consecutive elements (stride 17 words across
-// the warp) and a warp reading 32 consecutive elements both stay within
-// two shared-memory wavefronts
-__device__ __forceinline__ int pad16(int e) { return e + (e >> 4); }
-constexpr int kPadN = kTile + kTile / 16;
-
 // per-tile sums of m and m x (striped, coalesced loads; fixed tree)
 __global__ void __launch_bounds__(kThreads) k_tile_sums(Seg S, const int64_t* esc, bool sub,
                                                         const double* x, const double* m,
@@ -165,61 +203,136 @@ __global__ void __launch_bounds__(kThreads) k_tile_sums(Seg S, const int64_t* es
   if (threadIdx.x == 0) { tile_m[blockIdx.x] = tm; tile_mx[blockIdx.x] = tx; }
 }
 
+// The potential kernel runs 512 threads on a tile, 8 consecutive elements
+// each, so that two tiles' worth of warps (32) share an SM; its shared
+// arrays pad one double per 8 (a thread's run of 8 sits 9 words from its
+// neighbour's, free of bank conflicts within each half-warp).
+constexpr int kPotThreads = 512;
+constexpr int kPotPer = kTile / kPotThreads;
+constexpr int kPotWarps = kPotThreads / 32;
+__device__ __forceinline__ int pad8(int e) { return e + (e >> 3); }
+constexpr int kPad8N = kTile + kTile / 8;
+
+// fixed-order block sum over kPotThreads threads: a tree in each warp, then
+// a tree over the warp totals in the first warp (w17: kPotWarps + 1 slots)
+__device__ __forceinline__ double block_sum_pot(double v, double* w17) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = v + __shfl_down_sync(0xFFFFFFFFu, v, o);
+  if (lane == 0) w17[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    double u = lane < kPotWarps ? w17[lane] : 0.0;
+#pragma unroll
+    for (int o = kPotWarps / 2; o > 0; o >>= 1) u = u + __shfl_down_sync(0xFFFFFFFFu, u, o);
+    if (lane == 0) w17[kPotWarps] = u;
+  }
+  __syncthreads();
+  const double r = w17[kPotWarps];
+  __syncthreads();
+  return r;
+}
+
+// exclusive forward scan of vm and backward scan of vs over kPotThreads
+// threads, in a fixed order: inclusive scans inside each warp by shuffles,
+// the 16 warp totals scanned by one warp, then (totals of the warps before
+// or after) + (lanes before or after in the warp)
+__device__ __forceinline__ void block_scans_pot(double vm, double vs, double* wm, double* ws,
+                                                double& pre_m, double& suf_s) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double a = vm, b = vs;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const double ua = __shfl_up_sync(0xFFFFFFFFu, a, o);
+    const double db = __shfl_down_sync(0xFFFFFFFFu, b, o);
+    if (lane >= o) a = ua + a;
+    if (lane + o < 32) b = b + db;
+  }
+  const double ea = __shfl_up_sync(0xFFFFFFFFu, a, 1);    // lanes before
+  const double eb = __shfl_down_sync(0xFFFFFFFFu, b, 1);  // lanes after
+  if (lane == 31) wm[w] = a;
+  if (lane == 0) ws[w] = b;
+  __syncthreads();
+  if (w == 0) {
+    double ta = lane < kPotWarps ? wm[lane] : 0.0;
+    double tb = lane < kPotWarps ? ws[lane] : 0.0;
+#pragma unroll
+    for (int o = 1; o < kPotWarps; o <<= 1) {
+      const double ua = __shfl_up_sync(0xFFFFFFFFu, ta, o);
+      const double db = __shfl_down_sync(0xFFFFFFFFu, tb, o);
+      if (lane >= o) ta = ua + ta;
+      if (lane + o < kPotWarps) tb = tb + db;
+    }
+    const double xa = __shfl_up_sync(0xFFFFFFFFu, ta, 1);
+    const double xb = __shfl_down_sync(0xFFFFFFFFu, tb, 1);
+    __syncwarp();
+    if (lane < kPotWarps) {
+      wm[lane] = lane > 0 ? xa : 0.0;
+      ws[lane] = lane + 1 < kPotWarps ? xb : 0.0;
+    }
+  }
+  __syncthreads();
+  pre_m = lane > 0 ? wm[w] + ea : wm[w];
+  suf_s = lane < 31 ? ws[w] + eb : ws[w];
+  __syncthreads();
+}
+
 // Phi_k = -(M_k x_k + S_k) over one tile.  The tile's m and x are staged in
-// shared memory with coalesced loads; each thread scans its 16 consecutive
+// shared memory with coalesced loads; each thread scans its 8 consecutive
 // elements (local suffix sums of m x kept in registers), the per-thread
 // totals are scanned across the block, and the results (Phi, M_k, the
-// float table) leave through shared memory with coalesced stores.
-__global__ void __launch_bounds__(kThreads) k_potential(Seg S, const int64_t* esc, bool sub,
-                                                        const double* r, const double* x,
-                                                        const double* m, const double* tile_m,
-                                                        const double* tile_mx, double* phi,
-                                                        float2* t32, double* Mout,
-                                                        double4_32a* node, float4* tdf) {
+// float tables, the node records) leave through shared memory with
+// coalesced stores.
+__global__ void __launch_bounds__(kPotThreads) k_potential(Seg S, const int64_t* esc, bool sub,
+                                                           const double* r, const double* x,
+                                                           const double* m, const double* tile_m,
+                                                           const double* tile_mx, double* phi,
+                                                           float2* t32, double* Mout,
+                                                           double4_32a* node, float4* tdf) {
   extern __shared__ double smem[];
-  double* s_m = smem;              // m, then M_k
-  double* s_x = smem + kPadN;      // x
-  double* s_p = smem + 2 * kPadN;  // Phi
-  __shared__ double s1[kThreads], s2[kThreads];
+  double* s_m = smem;               // m, then M_k
+  double* s_x = smem + kPad8N;      // x
+  double* s_p = smem + 2 * kPad8N;  // Phi
+  __shared__ double wm[kPotWarps + 1], ws[kPotWarps];
   TR R = tile_of(S, esc, blockIdx.x, sub);
   const int64_t t0 = blockIdx.x - R.lt;
   const int t = threadIdx.x;
   // tiles before (M) and after (S) this one, in a fixed order
   double pm = 0.0, ps = 0.0;
-  for (int64_t j = t; j < R.nt; j += kThreads) {
+  for (int64_t j = t; j < R.nt; j += kPotThreads) {
     if (j < R.lt) pm = pm + tile_m[t0 + j];
     if (j > R.lt) ps = ps + tile_mx[t0 + j];
   }
-  const double Mbefore = block_sum(pm, s1);
-  const double Safter = block_sum(ps, s1);
+  const double Mbefore = block_sum_pot(pm, wm);
+  const double Safter = block_sum_pot(ps, wm);
 #pragma unroll 4
-  for (int i = 0; i < kPer; ++i) {
-    const int e = i * kThreads + t;
+  for (int i = 0; i < kPotPer; ++i) {
+    const int e = i * kPotThreads + t;
     const int64_t p = R.begin + e;
     const bool ok = p < R.end && p < R.bound_end;
-    s_m[pad16(e)] = ok ? __ldg(m + p) : 0.0;
-    s_x[pad16(e)] = ok ? __ldg(x + p) : 0.0;
+    s_m[pad8(e)] = ok ? __ldg(m + p) : 0.0;
+    s_x[pad8(e)] = ok ? __ldg(x + p) : 0.0;
   }
   __syncthreads();
-  const int e0 = t * kPer;
+  const int e0 = t * kPotPer;
   // exclusive suffix of m x along the thread's run, and its total
-  double suf[kPer];
+  double suf[kPotPer];
   double ax = 0.0;
 #pragma unroll
-  for (int i = kPer - 1; i >= 0; --i) {
+  for (int i = kPotPer - 1; i >= 0; --i) {
     suf[i] = ax;
-    ax = ax + s_m[pad16(e0 + i)] * s_x[pad16(e0 + i)];
+    ax = ax + s_m[pad8(e0 + i)] * s_x[pad8(e0 + i)];
   }
   double am = 0.0;
 #pragma unroll
-  for (int i = 0; i < kPer; ++i) am = am + s_m[pad16(e0 + i)];
+  for (int i = 0; i < kPotPer; ++i) am = am + s_m[pad8(e0 + i)];
   double pre_m, suf_s;
-  block_scans(am, ax, s1, s2, pre_m, suf_s);
+  block_scans_pot(am, ax, wm, ws, pre_m, suf_s);
   const double bm = Mbefore + pre_m, bs = Safter + suf_s;
   double run = 0.0;
 #pragma unroll
-  for (int i = 0; i < kPer; ++i) {
-    const int q = pad16(e0 + i);
+  for (int i = 0; i < kPotPer; ++i) {
+    const int q = pad8(e0 + i);
     run = run + s_m[q];
     const double Mk = bm + run;
     const double ph = -(Mk * s_x[q] + (bs + suf[i]));
@@ -228,15 +341,15 @@ __global__ void __launch_bounds__(kThreads) k_potential(Seg S, const int64_t* es
   }
   __syncthreads();
 #pragma unroll 4
-  for (int i = 0; i < kPer; ++i) {
-    const int e = i * kThreads + t;
+  for (int i = 0; i < kPotPer; ++i) {
+    const int e = i * kPotThreads + t;
     const int64_t p = R.begin + e;
     if (p >= R.end) break;
     const bool bound = p < R.bound_end;
-    const int q = pad16(e);
+    const int q = pad8(e);
     const double ph = bound ? s_p[q] : 0.0;
     phi[p] = ph;
-    if (t32) t32[p] = make_float2((float)s_x[q], (float)ph);
+    if (t32) t32[p] = make_float2(f32_pair(s_x[q]).hi, f32_pair(ph).hi);
     if (Mout) Mout[p] = bound ? s_m[q] : 0.0;
     if (node) node[p] = make_double4_32a(r[p], s_x[q], ph, bound ? s_m[q] : 0.0);
     if (tdf) tdf[p] = float_pairs(s_x[q], ph);
@@ -577,7 +690,7 @@ void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* val
                                                   r_old, c);
 }
 
-constexpr size_t kPotentialSmem = sizeof(double) * 3 * kPadN;
+constexpr size_t kPotentialSmem = sizeof(double) * 3 * kPad8N;
 
 void potential_prepare() {
   cudaFuncSetAttribute(k_potential, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -592,7 +705,7 @@ void launch_potential(const SegLayout& L, const double* r, const double* x, cons
   Seg S = L.dev();
   k_tile_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, L.esc_step, nb_sub, x, m, tile_m,
                                                        tile_mx);
-  k_potential<<<(unsigned)L.n_tiles, kThreads, kPotentialSmem, st>>>(
+  k_potential<<<(unsigned)L.n_tiles, kPotThreads, kPotentialSmem, st>>>(
       S, L.esc_step, nb_sub, r, x, m, tile_m, tile_mx, phi, t32, Mout, node, tdf);
 }
 

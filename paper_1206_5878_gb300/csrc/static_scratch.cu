@@ -10,8 +10,10 @@
 // the library's own device memory, reserved when the library is loaded and
 // kept by every GPU that loads it until the process exits.
 //
-// The arithmetic is the same as cmc_potential's (same tiles, same fixed
-// summation order), so the two entry points give the same results.
+// The scan is cmc_potential's (same tiles, M_k and S_k from the tiles before
+// and after in a fixed order) with summation orders of its own inside a
+// tile: the two entry points agree to rounding, and each repeats its own
+// results bit for bit.
 #include <mutex>
 
 #include "cmc_host.hpp"
