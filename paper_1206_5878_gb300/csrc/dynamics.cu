@@ -100,9 +100,7 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   const double dt = __longlong_as_double((long long)S.dt_bits[c]);
   const double lnL = S.lnL[c];
   // no density, no mass, or no positive Coulomb logarithm: no deflection
-  if (!(n > 0.0) || !(msum > 0.0) || !(lnL > 0.0) ||
-      !(dt < __longlong_as_double(0x7FF0000000000000ll)))
-    return;
+  if (!pos_num(n) || !pos_num(msum) || !pos_num(lnL) || !lt_inf(dt)) return;
   const uint64_t seed = S.seed[c];
   const uint32_t step = *step_p;
   const uint32_t ida = id[a];
@@ -114,7 +112,7 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   const double v2y = vtb * cpsi, v2z = vtb * spsi;
   const double wx = v1x - v2x, wy = v1y - v2y, wz = v1z - v2z;
   const double w2 = (wx * wx + wy * wy) + wz * wz;
-  if (!(w2 > 0.0)) {
+  if (!pos_num(w2)) {
     if (fails) stat_add(S.stats, c, kStAngleFails, (unsigned long long)fails);
     return;
   }
@@ -125,7 +123,7 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   num = num * lnL;
   num = num * dt;
   double s2 = num / (w2 * w);
-  if (!(s2 <= 1.0)) s2 = 1.0;
+  if (!le1(s2)) s2 = 1.0;
   // cos(beta) = 1 - 2 sin^2(beta/2), sin(beta) = 2 sin(beta/2) cos(beta/2)
   const double cosb = 1.0 - 2.0 * s2;
   const double sinb = 2.0 * sqrt(s2 * (1.0 - s2));
@@ -134,7 +132,7 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   // u = w x e1 has length |w| and completes the frame perpendicular to w
   const double wp2 = wy * wy + wz * wz;
   double e1y, e1z;
-  if (wp2 > 0.0) {
+  if (pos_num(wp2)) {
     const double iwp = 1.0 / sqrt(wp2);
     e1y = wz * iwp;
     e1z = -(wy * iwp);

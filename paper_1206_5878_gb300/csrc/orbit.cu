@@ -63,23 +63,6 @@ __device__ __forceinline__ double shell_root64(const Table64& T, const Star& s, 
   return root;
 }
 
-// --------------------------------------- comparisons on the integer pipes
-// On this GPU the FP64 pipe issues two lanes per SM and clock, and the
-// turning-point kernels are bound by it; tests that need no FP64
-// arithmetic read the bit patterns instead (IEEE-754 doubles of one sign
-// order like their patterns).  kInfBits: +Inf; patterns above it with the
-// sign clear are NaNs.
-constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
-__device__ __forceinline__ unsigned long long ubits(double v) {
-  return (unsigned long long)__double_as_longlong(v);
-}
-// v > 0 and not NaN (+Inf included)
-__device__ __forceinline__ bool pos_num(double v) { return ubits(v) - 1ull < kInfBits; }
-// v >= rj for rj > 0, false for NaN (as the FP64 comparison)
-__device__ __forceinline__ bool ge_pos(double v, double rj) {
-  const unsigned long long u = ubits(v);
-  return u >= ubits(rj) && u <= kInfBits;
-}
 // The same root with the slope of shell j taken from the enclosed mass:
 // across shell j, (Phi_{j+1} - Phi_j)/(x_j - x_{j+1}) = G M_j exactly
 // (Eqs. 1-5; for the outermost shell M_j is the bound mass), so
@@ -140,7 +123,7 @@ __device__ __forceinline__ double rmin_core(const Star& s, bool central, double 
 // for -1).  The records of the guess and its successor are loaded together.
 __device__ __forceinline__ int64_t fix_shell_nodes(const double4_32a* __restrict__ nd, int64_t nb,
                                                    int64_t i, double q, double4_32a& a) {
-  if (!(q >= 0.0)) {
+  if (!ge0(q)) {
     a = nd[0];
     return -1;
   }
@@ -816,12 +799,12 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
     const int64_t k = p - S.off[c];
     const double vrk = vr[p], vtk = vt[p];
     const double E = __ldg(phi + p) + 0.5 * (vrk * vrk + vtk * vtk);
-    if (k < S.nb[c] && E < 0.0) {
+    if (k < S.nb[c] && lt0(E)) {
       const double J = r[p] * vtk;
       const double rmin = __ldg(tp_min + p), rmax = __ldg(tp_max + p);
-      const double c0 = 0.5 * (rmax + rmin);
-      const double c1 = 0.25 * (rmax - rmin);
-      const float c0f = (float)c0, c1f = (float)c1, E32 = (float)E, J32 = (float)J;
+      const double c0 = scale_down<1>(rmax + rmin);
+      const double c1 = scale_down<2>(rmax - rmin);
+      const float c0f = f32_rn(c0), c1f = f32_rn(c1), E32 = f32_rn(E), J32 = f32_rn(J);
       const Grid GD = grid_of(BA, c);
       float gmax = 0.0f;
 #pragma unroll 3
@@ -832,7 +815,7 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
       const float F32 = 1.2f * gmax;
       uint32_t st = kSmpCap;
       int t = 0;
-      if (!(rmax > rmin) || !(F32 > 0.0f)) {
+      if (!gt_pos(rmax, rmin) || !(F32 > 0.0f)) {
         st = kSmpDegenerate;
       } else {
         const uint32_t idk = id[p], step = *step_p;
@@ -895,7 +878,7 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
       s.k = k;
       s.E = __ldg(phi + p) + 0.5 * (vrk * vrk + vtk * vtk);
       s.J = r[p] * vtk;
-      if (s.E < 0.0 && ((uint32_t)(res >> 30) & 3u) == kSmpPending) {
+      if (lt0(s.E) && ((uint32_t)(res >> 30) & 3u) == kSmpPending) {
         Buckets BK;
         const int4 pr = BA.prm[c];
         BK.start = BA.start + BA.off[c];
@@ -905,9 +888,9 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
         BK.lo = pr.z;
         BK.hi = pr.w;
         const double rmin = __ldg(tp_min + p), rmax = __ldg(tp_max + p);
-        const double c0 = 0.5 * (rmax + rmin);
-        const double c1 = 0.25 * (rmax - rmin);
-        const float c0f = (float)c0, c1f = (float)c1;
+        const double c0 = scale_down<1>(rmax + rmin);
+        const double c1 = scale_down<2>(rmax - rmin);
+        const float c0f = f32_rn(c0), c1f = f32_rn(c1);
         const double F = (double)__uint_as_float((uint32_t)(res >> 32));
         const uint32_t idk = id[p], step = *step_p;
         const uint64_t seed = S.seed[c];
@@ -920,7 +903,7 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
           point64(BA.node + sb, nbc, s, c0, c1, sv,
                   shell32_of(t32 + sb, (int)nbc, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs,
                   xs, ph, L, Q);
-          const double g64v = Q > 0.0 ? ((3.0 * c1) * (1.0 - sv * sv)) / sqrt(Q) : 0.0;
+          const double g64v = pos_num(Q) ? ((3.0 * c1) * (1.0 - sv * sv)) / sqrt(Q) : 0.0;
           ++n64;
           if (g64v > F) ++viol;
           if (F * u01(w.z, w.w) < g64v) { st = kSmpAccepted; break; }
@@ -1002,7 +985,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
   const uint32_t step = *step_p;
   double ph_new = __ldg(T.phi + k);
 
-  if (!(s.E < 0.0)) {
+  if (!lt0(s.E)) {
     escaped = true;
     code = 1;
     r_new = __longlong_as_double(0x7FF0000000000000ll);
@@ -1033,8 +1016,8 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
       rmax = shell_root64(T, s, jmax, true);
       rmin = jmin < 0 ? central_root64(T, s) : shell_root64(T, s, jmin, false);
     }
-    const double c0 = 0.5 * (rmax + rmin);
-    const double c1 = 0.25 * (rmax - rmin);
+    const double c0 = scale_down<1>(rmax + rmin);
+    const double c1 = scale_down<2>(rmax - rmin);
     if (kPrec == 0) {
       double gmax = 0.0;
       for (int j = 0; j <= 20; ++j) {
@@ -1090,7 +1073,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
         code = 3;
         trials = max_trials;
       } else {
-        const float c0f = (float)c0, c1f = (float)c1;
+        const float c0f = f32_rn(c0), c1f = f32_rn(c1);
         const int nb32 = (int)nbc;
         // (k_pending64 has resolved every pending star to accepted or cap)
         const bool acc = st == kSmpAccepted;
@@ -1108,7 +1091,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
           point64(BA.node + sb, nbc, s, c0, c1, sv,
                   shell32_of(T32.t, nb32, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs, xs, ph,
                   L, Q);
-          if (!(Q > 0.0)) Q = 0.0;
+          if (!pos_num(Q)) Q = 0.0;
           const double sq = sqrt(Q);
           U4 sg = philox(idk, step, kTagSgn, 0u, seed);
           r_new = rs;
@@ -1177,7 +1160,7 @@ __global__ void __launch_bounds__(128) k_correction_mixed(Seg S, const int64_t* 
   BK.nbk = pr.y;
   BK.lo = pr.z;
   BK.hi = pr.w;
-  const float xq[1] = {(float)xo};
+  const float xq[1] = {f32_rn(xo)};
   int sh[1];
   shells32_bk<1>(t32 + sb, (int)nbc, BK, xq, sh);
   double4_32a nd;
@@ -1188,8 +1171,8 @@ __global__ void __launch_bounds__(128) k_correction_mixed(Seg S, const int64_t* 
   const double dnew = pn - phi[p];
   double Tp = Tk + 0.5 * (dnew - cc[p]);
   bool clamp = false;
-  if (Tp < 0.0) { Tp = 0.0; clamp = true; }
-  if (Tk > 0.0) {
+  if (lt0(Tp)) { Tp = 0.0; clamp = true; }
+  if (pos_num(Tk)) {
     const double f = sqrt(Tp / Tk);
     vr[p] = a * f;
     vt[p] = b * f;
