@@ -205,9 +205,12 @@ struct Table32 {
 #define CMC_SJ(j) (-1.0 + ((double)(j) + 0.5) / 10.5)
 #define CMC_SJ21(f) f(0), f(1), f(2), f(3), f(4), f(5), f(6), f(7), f(8), f(9), f(10), \
     f(11), f(12), f(13), f(14), f(15), f(16), f(17), f(18), f(19), f(20)
-#define CMC_SJF(j) ((float)CMC_SJ(j))
 __constant__ double c_s64[21] = {CMC_SJ21(CMC_SJ)};
-__constant__ float c_s32[21] = {CMC_SJ21(CMC_SJF)};
+// for the FP32 envelope: s_j (3 - s_j^2) and 3 (1 - s_j^2), rounded to float
+#define CMC_SJA(j) ((float)(CMC_SJ(j) * (3.0 - CMC_SJ(j) * CMC_SJ(j))))
+#define CMC_SJB(j) ((float)(3.0 * (1.0 - CMC_SJ(j) * CMC_SJ(j))))
+__constant__ float c_sa32[21] = {CMC_SJ21(CMC_SJA)};
+__constant__ float c_sb32[21] = {CMC_SJ21(CMC_SJB)};
 
 // ---- FP32 searches run in lockstep: K independent searches per thread,
 // each round issues K independent loads before any of them is needed.
@@ -334,16 +337,22 @@ __device__ __forceinline__ float grid_phi(const Grid& G, float xq) {
   return a + f * (b - a);
 }
 
-// g(s) = (dr/ds) / sqrt(Q) in FP32 with Phi from the grid
+// g(s_j) = (dr/ds) / sqrt(Q) at envelope sample j in FP32 with Phi from the
+// grid (sa = s(3 - s^2), sb = 3 (1 - s^2) from the tables).  The envelope
+// F = 1.2 max_j g(s_j) only has to bound g: the reciprocal and the inverse
+// square root are the one-instruction approximations (relative errors
+// below 2^-22), far inside the factor 1.2.
 __device__ __forceinline__ float g32_grid(const Grid& G, float E, float J, float c0, float c1,
-                                          float sv) {
-  const float rs = c0 + c1 * (sv * (3.0f - sv * sv));
-  const float drds = (3.0f * c1) * (1.0f - sv * sv);
-  const float xq = 1.0f / rs;
+                                          float sa, float sb) {
+  const float rs = c0 + c1 * sa;
+  const float drds = c1 * sb;
+  float xq, rq;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xq) : "f"(rs));
   const float ph = grid_phi(G, xq);
   const float L = J * xq;
   const float Q = 2.0f * (E - ph) - L * L;
-  return Q > 0.0f ? drds / sqrtf(Q) : 0.0f;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rq) : "f"(Q));
+  return Q > 0.0f ? drds * rq : 0.0f;
 }
 
 // the FP32 shell (bucket index) of the point r(s), the start of the FP64
@@ -809,7 +818,7 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
       float gmax = 0.0f;
 #pragma unroll 3
       for (int j = 0; j < 21; ++j) {
-        const float g = g32_grid(GD, E32, J32, c0f, c1f, c_s32[j]);
+        const float g = g32_grid(GD, E32, J32, c0f, c1f, c_sa32[j], c_sb32[j]);
         gmax = g > gmax ? g : gmax;
       }
       const float F32 = 1.2f * gmax;
