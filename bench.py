@@ -151,6 +151,20 @@ STAGE_KERNEL = {"timestep": "k_bins", "relax": "k_relax", "turning": "k_turning_
                 "potential": "k_potential", "correction": "k_correction_mixed"}
 
 
+
+# FP64 peak derived from the unit counts and clock (nominal 1.25 TFLOP/s)
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# FP64 operations per star of the formulas of the kernels that can dominate
+# a step (each +, -, x, /, sqrt counted once):
+#   k_relax (98 per pair of stars): two random azimuths (9 each: u^2, v^2,
+#     their sum, its reciprocal, two products for cos, three for sin), the
+#     second star's velocity (2), w and |w|^2 (8), |w| (1), the deflection
+#     numerator pi m^2 n lnL dt (5) and sin^2(beta/2) (2), cos beta, sin beta
+#     (6), the frame e1, u (12), w' (17), the mass ratios (3), the new
+#     velocities (12) and the two new tangential speeds (8)
+#   k_turning_mixed (28 per bound star): E (5), J (1), the r_max root in its
+#     shell (13), the r_min root (9, sharing J^2)
+KERNEL_FLOPS = {"relax": ("k_relax", 98 / 2), "turning": ("k_turning_mixed", 28)}
 # ------------------------------------------------------------ oracle sample
 def oracle_sample_step(state, n_orbit: int, seed: int, step: int):
     """One oracle timestep measured on a bounded sample of the workload:
@@ -372,25 +386,25 @@ def run_cmc(args, rank, world, local_rank):
     # one by one with events between the stages)
     stages = c.step_profiled(args.steps)
     stages_avg = {k: v / args.steps for k, v in stages.items()}
-    dom = max(stages_avg, key=stages_avg.get)
     hbm, peak_kind = measured_peaks()
-    # roofline of the dominant stage's kernel (the stage is one launch but
-    # for the orbit sampling, timed over its kernels)
+    # roofline of the dominant single kernel: the FP64-bound relaxation or
+    # turning-point kernel (every other stage is shorter or several kernels)
+    dom = max(KERNEL_FLOPS, key=lambda k: stages_avg.get(k, 0.0))
     dom_ms = stages_avg[dom]
-    nbytes = STAGE_BYTES.get(dom, 0) * n
-    achieved = nbytes / (dom_ms / 1e3) / 1e9
+    kname, flops_per_star = KERNEL_FLOPS[dom]
+    nflops = flops_per_star * n
+    achieved = nflops / (dom_ms / 1e3) / 1e9
     tun = c.tuning()
-    kname = STAGE_KERNEL.get(dom, dom)
-    if dom == "orbit":
-        kname = "k_sample32 + k_pending64 + k_orbit (mixed sampling, variant %d)" % (
-            tun["orbit_variant"]) if prec else "k_orbit (FP64)"
-    traffic_ps = profiled_traffic_per_star(STAGE_KERNEL.get(dom, dom), args.precision)
-    roof = {"kernel": kname, "stage": dom, "bound": "hbm", "achieved": achieved, "peak": hbm,
-            "unit": "GB/s", "frac": achieved / hbm, "peak_source": peak_kind,
-            "algorithmic_bytes_per_launch": nbytes,
+    traffic_ps = profiled_traffic_per_star(kname, args.precision)
+    roof = {"kernel": kname, "stage": dom, "bound": "alu", "achieved": achieved,
+            "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
+            "peak_source": "derived (FP64): 152 SMs x 2 FMA lanes/clock x 2 flop x 2.07 GHz",
+            "algorithmic_flops_per_launch": nflops,
             "traffic": None if traffic_ps is None else traffic_ps * n,
             "launch_ms": dom_ms,
-            "note": "bound by FP64 issue and dependent table lookups, not HBM bandwidth"}
+            "note": "FP64 operations of the kernel's formulas (+, -, x, /, sqrt once each); "
+                    "compiled without FMA contraction for bit-exact parity, so half the FMA "
+                    "peak is the issue ceiling, and / and sqrt take several FP64 issues each"}
     # step-level compulsory traffic (248 B per star-update) against HBM
     step_frac = 248.0 * value / world / 1e9 / hbm
 
