@@ -157,14 +157,16 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
                c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
                c->bk.args(), c->r_old, c->cc, c->vals, c->pcount, st, false);
   mark(4);
-  // radix passes over bits 16-63 of the radius keys; runs equal in those
-  // bits (radii within 2^-36 of each other) are put in (r, id) order after
-  sort_segments(L, c->W, c->keys, c->vals, 2, 6, true, c->err, st);
-  launch_tiefix(L, c->keys, c->vals, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)),
-                c->err, st, 16);
+  // radix passes over bits 24-63 of the radius keys; runs equal in those
+  // bits (radii within 2^-28 of each other, escapers whose ids differ in
+  // their low 4 bits) are put in (key, id) order after
+  uint64_t* sk = nullptr;
+  uint32_t* sv = nullptr;
+  sort_segments(L, c->W, c->keys, c->vals, 3, 5, true, c->err, st, &sk, &sv);
+  launch_tiefix(L, sk, sv, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)), c->err, st,
+                24);
   mark(5);
-  launch_gather(L, c->keys, c->vals, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old,
-                c->cc, st);
+  launch_gather(L, sk, sv, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old, c->cc, st);
   mark(6);
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
                    mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, true, st,
@@ -188,10 +190,10 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
 }
 
 int count_step_kernels(const cmc_ctx* c) {
-  // bins, relax, orbit, upsweep, hist scan, 6 passes, tie fix, gather,
+  // bins, relax, orbit, upsweep, hist scan, 5 passes, tie fix, gather,
   // tile sums, potential, [turning points, FP32 sampler, FP64 continuation,
   // 2 bucket-index + 2 grid kernels], [correction], step end
-  return 3 + 2 + 6 + 1 + 1 + 2 + (c->cfg.precision == 1 ? 7 : 0) +
+  return 3 + 2 + 5 + 1 + 1 + 2 + (c->cfg.precision == 1 ? 7 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 
@@ -310,7 +312,7 @@ cmc_status autotune(cmc_ctx* c) {
       if (sort_set_shape(L, c->W, ipt, rank, st)) continue;
       const float ms = time_it([&] {
         cudaMemcpyAsync(c->keys, saved, sizeof(uint64_t) * L.n, cudaMemcpyDeviceToDevice, st);
-        sort_segments(L, c->W, c->keys, c->vals, 2, 6, true, c->err, st);
+        sort_segments(L, c->W, c->keys, c->vals, 3, 5, true, c->err, st);
       });
       if (ms < tbest) { tbest = ms; best_ipt = ipt; best_rank = rank; }
     }
@@ -680,10 +682,10 @@ cmc_status cmc_sort_radius(int64_t n, const double* r, const uint32_t* id, uint3
     sort_prepare();
     cudaMemsetAsync(err, 0, sizeof(uint32_t), st);
     launch_make_keys(S.L, r, nullptr, nullptr, nullptr, id, keys, nullptr, st);
-    // as in the timestep: passes over bits 16-63, then runs equal in those
+    // as in the timestep: passes over bits 24-63, then runs equal in those
     // bits in (r, id) order
-    sort_segments(S.L, W, keys, perm, 2, 6, true, err, st);
-    launch_tiefix(S.L, keys, perm, id, 1, err, st, 16);
+    sort_segments(S.L, W, keys, perm, 3, 5, true, err, st);
+    launch_tiefix(S.L, keys, perm, id, 1, err, st, 24);
     uint32_t he = 0;
     e = cudaMemcpyAsync(&he, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaStreamSynchronize(st);

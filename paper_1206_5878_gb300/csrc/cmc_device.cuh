@@ -26,9 +26,9 @@ constexpr uint32_t kTagRej = 2;      // orbit: rejection trials
 constexpr uint32_t kTagSgn = 3;      // orbit: sign of the new v_r
 
 // escaped stars sort after every finite radius, by id: key 0x7FF0...0 | id
-// << 16, above every finite radius and unique in its top 48 bits (the
-// timestep's sort orders by those and puts runs of equal top bits in
-// (key, id) order)
+// << 20, above every finite radius (the timestep's sort orders by the top
+// 40 bits and puts runs equal in them -- escapers whose ids differ only in
+// their low 4 bits -- in (key, id) order, which for these keys is id order)
 constexpr uint64_t kEscKeyBase = 0x7FF0000000000000ull;
 
 // error bits (fatal: they poison the context)
@@ -172,7 +172,7 @@ __device__ __forceinline__ bool disk_angle(uint64_t seed, uint32_t id, uint32_t 
 // ------------------------------------------------------------ sort keys
 __device__ __forceinline__ uint64_t radius_key(double r, uint32_t id) {
   uint64_t b = (uint64_t)__double_as_longlong(r);
-  return (b >= 0x7FF0000000000000ull) ? kEscKeyBase | ((uint64_t)id << 16) : b;
+  return (b >= 0x7FF0000000000000ull) ? kEscKeyBase | ((uint64_t)id << 20) : b;
 }
 __device__ __forceinline__ bool key_is_escaper(uint64_t k) {
   return k >= 0x7FF0000000000000ull;

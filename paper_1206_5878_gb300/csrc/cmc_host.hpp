@@ -81,11 +81,14 @@ void free_sort(SortWork& W, cudaStream_t st);
 // ------------------------------------------------------------- launchers
 // Stable LSD radix sort of (keys, vals) within each segment over the 8-bit
 // digits [first_pass, first_pass + passes).  When vals_identity is set the
-// input values are taken to be the global positions.  The result lands in
-// (keys, vals) when passes is even (the alternates are scratch).
+// input values are taken to be the global positions.  After an even number
+// of passes the result is in (keys, vals); after an odd number it is in the
+// alternate buffers, which *keys_res / *vals_res then name when both are
+// given (else it is copied back into keys, vals).
 cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint32_t* vals,
                           int first_pass, int passes, bool vals_identity, uint32_t* err,
-                          cudaStream_t st);
+                          cudaStream_t st, uint64_t** keys_res = nullptr,
+                          uint32_t** vals_res = nullptr);
 
 // Order every run of finite keys equal in their bits from `shift` up by
 // (key, id of the element: ids_by_val[vals[p] * id_stride]), so that after

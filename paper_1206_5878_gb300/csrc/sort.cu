@@ -153,7 +153,7 @@ constexpr int kRankBallot = 1;  // nine __ballot_sync
 
 // ------------------------------------------------------------- onesweep
 template <bool kValIdentity, int IPT, int kRank>
-__global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 4 : 2))
+__global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : 2))
     k_pass(const int64_t* off, const int64_t* tile_off, int n_seg, int64_t n_tiles,
            const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
            uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int pass, int q,
@@ -278,8 +278,9 @@ __global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 4 : 2))
 }
 
 // ------------------------------------------------------------- tie fix
-// Runs of equal finite keys are put in increasing id order (insertion sort
-// by one thread per run; a run that is already ordered costs one pass).
+// Runs of keys equal in their bits above `shift` are put in (key, id) order
+// (insertion sort by one thread per run; a run that is already ordered
+// costs one pass): finite radii in (r, id) order, escapers in id order.
 constexpr long long kTieMoveCap = 1ll << 22;
 
 __global__ void k_tiefix(const int64_t* off, int n_seg, int64_t n, uint64_t* keys,
@@ -290,7 +291,7 @@ __global__ void k_tiefix(const int64_t* off, int n_seg, int64_t n, uint64_t* key
   int c = seg_find(off, n_seg, p);
   int64_t sb = __ldg(off + c), se = __ldg(off + c + 1);
   const uint64_t kp = keys[p], hp = kp >> shift;
-  if (key_is_escaper(kp) || p + 1 >= se || (keys[p + 1] >> shift) != hp) return;
+  if (p + 1 >= se || (keys[p + 1] >> shift) != hp) return;
   if (p > sb && (keys[p - 1] >> shift) == hp) return;  // not the start of the run
   int64_t e = p + 2;
   while (e < se && (keys[e] >> shift) == hp) ++e;
@@ -429,7 +430,9 @@ void free_sort(SortWork& W, cudaStream_t st) {
 
 cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint32_t* vals,
                           int first_pass, int passes, bool vals_identity, uint32_t* err,
-                          cudaStream_t st) {
+                          cudaStream_t st, uint64_t** keys_res, uint32_t** vals_res) {
+  if (keys_res) *keys_res = keys;
+  if (vals_res) *vals_res = vals;
   if (passes <= 0 || passes > W.max_passes || L.n_tiles == 0) return cudaSuccess;
   cudaMemsetAsync(W.zero_base, 0, W.zero_bytes, st);
   k_upsweep<<<(unsigned)L.n_tiles, kThreads, sizeof(uint32_t) * kWarps * passes * kBins, st>>>(
@@ -452,6 +455,17 @@ cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint3
       launch_pass<16, kRankBallot>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st);
     std::swap(kin, kout);
     std::swap(vin, vout);
+  }
+  // after an odd number of passes the result is in the alternate buffers:
+  // the caller takes them, or they are copied back
+  if (kin != keys) {
+    if (keys_res && vals_res) {
+      *keys_res = kin;
+      *vals_res = vin;
+    } else {
+      cudaMemcpyAsync(keys, kin, sizeof(uint64_t) * (size_t)L.n, cudaMemcpyDeviceToDevice, st);
+      cudaMemcpyAsync(vals, vin, sizeof(uint32_t) * (size_t)L.n, cudaMemcpyDeviceToDevice, st);
+    }
   }
   return cudaGetLastError();
 }
