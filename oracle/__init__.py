@@ -85,6 +85,8 @@ def _declare(lib):
         "or_energy": (None, [_i64, _p, _p, _p, _p, _p]),
         "or_energy_W_brute": (_d, [_i64, _p, _p]),
         "or_lagrange_radii": (None, [_i64, _p, _p, _p, _i32, _p]),
+        "or_core": (None, [_i64, _p, _p, _p]),
+        "or_core_rho": (None, [_i64, _p, _p, _p]),
         "or_step": (_d, [_i64, _p, _p, _p, _p, _p, _p, _p, _u64, _u32, _i32, _d, _d,
                          _i32, _i32, _i32, _p, _p]),
     }
@@ -261,6 +263,28 @@ def lagrange_radii(r, m, fracs):
     return out
 
 
+def core(r, m):
+    """Core density and density-weighted core radius (Eq. 19) from the
+    6th-order radial density estimator: (rho_c, r_c, number of estimates)."""
+    r, m = _f64(r), _f64(m)
+    out = np.zeros(3)
+    _L().or_core(r.shape[0], _ptr(r), _ptr(m), _ptr(out))
+    return out[0], out[1], int(out[2])
+
+
+def core_rho(r, m):
+    """The per-star density estimates behind core() (0 where none)."""
+    r, m = _f64(r), _f64(m)
+    out = np.zeros(r.shape[0])
+    _L().or_core_rho(r.shape[0], _ptr(r), _ptr(m), _ptr(out))
+    return out
+
+
+def half_mass_relaxation_time(n, r_h, mass=1.0, gamma=0.1):
+    """Eq. 20: t_rh = 0.138 N / ln(gamma N) (r_h^3 / (G M))^(1/2), G = 1."""
+    return 0.138 * n / math.log(gamma * n) * math.sqrt(r_h ** 3 / mass)
+
+
 # --------------------------------------------------------------------------
 # a cluster advanced step by step
 # --------------------------------------------------------------------------
@@ -331,3 +355,7 @@ class Cluster:
     def lagrange_radii(self, fracs):
         nb = self.nb
         return lagrange_radii(self.r[:nb], self.m[:nb], fracs)
+
+    def core(self):
+        nb = self.nb
+        return core(self.r[:nb], self.m[:nb])

@@ -720,6 +720,54 @@ void or_lagrange_radii(int64_t nb, const double *r, const double *m,
 }
 
 /* ------------------------------------------------------------------------ */
+/* Core diagnostics (section 4.3, Eq. 19).  The paper's density around star */
+/* i is the 6th-order estimator of Casertano & Hut (1985): the mass of j - 1 */
+/* neighbours over the volume out to the j-th (j = 6).  The method keeps     */
+/* radii only, so the estimator is taken in the radial order (reading): the  */
+/* stars i - 3 and i + 3 bound a shell that holds the 5 stars i - 2 .. i + 2, */
+/*   rho_i = (m_{i-2} + ... + m_{i+2}) / (4 pi / 3 (r_{i+3}^3 - r_{i-3}^3)), */
+/* unbiased for a Poisson sample (the shell spans 6 exponential gaps in      */
+/* volume); stars with fewer than 3 neighbours on a side, or a shell of no   */
+/* volume, have no estimate.                                                 */
+/*   rho_c = sum rho_i^2 / sum rho_i        (Eq. 19)                         */
+/*   r_c   = sum rho_i r_i / sum rho_i      (the density-weighted radius)    */
+/* out[0] = rho_c, out[1] = r_c, out[2] = number of estimates.               */
+/* ------------------------------------------------------------------------ */
+void or_core(int64_t nb, const double *r, const double *m, double *out)
+{
+    double s1 = 0.0, s2 = 0.0, sr = 0.0;
+    int64_t i, cnt = 0;
+    for (i = 3; i + 3 < nb; ++i) {
+        double mass = m[i - 2] + m[i - 1] + m[i] + m[i + 1] + m[i + 2];
+        double ro = r[i + 3], ri = r[i - 3];
+        double vol = (4.0 * OR_PI / 3.0) * (ro * ro * ro - ri * ri * ri);
+        double rho;
+        if (!(vol > 0.0)) continue;
+        rho = mass / vol;
+        s1 = s1 + rho;
+        s2 = s2 + rho * rho;
+        sr = sr + rho * r[i];
+        ++cnt;
+    }
+    out[0] = s1 > 0.0 ? s2 / s1 : 0.0;
+    out[1] = s1 > 0.0 ? sr / s1 : 0.0;
+    out[2] = (double)cnt;
+}
+
+/* The estimates rho_i themselves (0 where there is none), for the tests. */
+void or_core_rho(int64_t nb, const double *r, const double *m, double *rho)
+{
+    int64_t i;
+    for (i = 0; i < nb; ++i) {
+        double vol;
+        rho[i] = 0.0;
+        if (i < 3 || i + 3 >= nb) continue;
+        vol = (4.0 * OR_PI / 3.0) * (r[i + 3] * r[i + 3] * r[i + 3] - r[i - 3] * r[i - 3] * r[i - 3]);
+        if (vol > 0.0) rho[i] = (m[i - 2] + m[i - 1] + m[i] + m[i + 1] + m[i + 2]) / vol;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
 /* One full timestep of one cluster, in the order of section 3.3:            */
 /* timestep -> relaxation -> new orbits -> sort -> potential -> energy       */
 /* correction.  On entry the first *nb stars are bound and sorted, phi holds */
