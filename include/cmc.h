@@ -134,6 +134,17 @@ cmc_status cmc_energy(cmc_ctx *ctx, double *out);
  * out: host, n_clusters x nf. */
 cmc_status cmc_lagrange_radii(cmc_ctx *ctx, const double *fracs, int32_t nf, double *out);
 
+/* Core diagnostics (section 4.3, Eq. 19) per cluster of the bound stars:
+ * out (host, n_clusters x 3) = {rho_c, r_c, n_est}.  The density around
+ * sorted bound star k (3 <= k < N_bound - 3) is the 6th-order estimator of
+ * Casertano & Hut taken in the radial order, rho_k = (m_{k-2} + ... +
+ * m_{k+2}) / (4 pi / 3 (r_{k+3}^3 - r_{k-3}^3)) (shells of no volume are
+ * skipped); rho_c = sum rho_k^2 / sum rho_k (Eq. 19), r_c = sum rho_k r_k /
+ * sum rho_k (the density-weighted core radius), n_est = the number of
+ * estimates (0 when N_bound < 7, rho_c = r_c = 0 then).  Units G = M = 1
+ * (rho_c in M r_vir^-3 for Henon units, r_vir = 1).  Synchronous. */
+cmc_status cmc_core(cmc_ctx *ctx, double *out);
+
 /* Copy the state out (sorted as described above).  Any array may be NULL.
  * phi receives the potential at each star (0 for escaped stars); step the
  * number of steps taken so far (host pointer, may be NULL). */

@@ -355,8 +355,12 @@ double or_timestep(int64_t nb, const double *r, const double *vr, const double *
 /* Representative encounter: star 1 moves along (v_r1, v_t1, 0), star 2's    */
 /* transverse velocity has a random azimuth psi.  The relative velocity w is */
 /* turned by the deflection angle beta,                                      */
-/*   sin^2(beta/2) = min(1, pi G^2 (m1+m2)^2 n lnL dt / |w|^3),              */
+/*   sin^2(beta/2) = min(1, 2 pi G^2 (m1+m2)^2 n lnL dt / |w|^3),            */
 /* about w by a random azimuth phi; the centre-of-mass velocity is kept.    */
+/* (4 sin^2(beta/2) ~ beta^2 is the mean squared deflection the relative    */
+/* velocity gathers over dt from small-angle encounters, 8 pi G^2 (m1+m2)^2 */
+/* n lnL dt / |w|^3; with it a Plummer sphere collapses at ~17-18 t_rh, as  */
+/* in section 4.3, where half this rate takes ~34 t_rh.)                     */
 /* Random numbers are keyed by the id of the pair's first star.             */
 /* Returns the number of pairs whose angle draw failed (normally 0).        */
 /* ------------------------------------------------------------------------ */
@@ -394,7 +398,7 @@ int or_encounter(double m1, double m2, double vr1, double vt1, double vr2, doubl
     w2 = (wx * wx + wy * wy) + wz * wz;
     if (!(w2 > 0.0)) return fails;
     w = sqrt(w2);
-    num = OR_PI * msum;
+    num = (2.0 * OR_PI) * msum;
     num = num * msum;
     num = num * n;
     num = num * lnL;

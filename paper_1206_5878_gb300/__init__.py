@@ -135,6 +135,12 @@ class Cluster:
                                           out.ctypes.data), self.ctx)
         return out
 
+    def core(self) -> np.ndarray:
+        """Per cluster {rho_c, r_c, number of estimates} (Eq. 19)."""
+        out = np.zeros((self.n_clusters, 3))
+        check(self.lib.cmc_core(self.ctx, out.ctypes.data), self.ctx)
+        return out
+
     def get_state(self, out=None):
         """Sorted state as numpy arrays (or into the given torch tensors)."""
         step = np.zeros(1, dtype=np.int64)
@@ -279,3 +285,9 @@ def stage_energy_correction(r, phi, vr, vt, r_old, c, stream=None):
     check(load().cmc_energy_correction(r.shape[0], _t(r), _t(phi), _t(vr), _t(vt), _t(r_old),
                                        _t(c), _stream_ptr(stream)))
     return vr, vt
+
+
+def half_mass_relaxation_time(n: int, r_h: float, mass: float = 1.0, gamma: float = 0.1) -> float:
+    """Eq. 20: t_rh = 0.138 N / ln(gamma N) (r_h^3 / (G M))^(1/2) with G = 1."""
+    import math
+    return 0.138 * n / math.log(gamma * n) * math.sqrt(r_h ** 3 / mass)

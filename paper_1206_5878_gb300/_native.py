@@ -44,6 +44,7 @@ SIGNATURES = {
     "cmc_step_profiled": (_i32, [_p, _i32, _p]),
     "cmc_energy": (_i32, [_p, _p]),
     "cmc_lagrange_radii": (_i32, [_p, _p, _i32, _p]),
+    "cmc_core": (_i32, [_p, _p]),
     "cmc_get_state": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p, _i32]),
     "cmc_set_state": (_i32, [_p, _p, _p, _p, _p, _p, _i64, _i32]),
     "cmc_get_nbound": (_i32, [_p, _p]),

@@ -498,6 +498,27 @@ cmc_status cmc_energy(cmc_ctx* c, double* out) {
   return CMC_OK;
 }
 
+cmc_status cmc_core(cmc_ctx* c, double* out) {
+  if (!c || !out) return fail(c, CMC_EINVAL, "cmc_core: bad arguments");
+  if (c->poisoned) return fail(c, CMC_EPOISONED, c->last_error);
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  double *tiles = nullptr, *dout = nullptr;
+  cudaError_t e = dalloc(tiles, 4 * (size_t)(c->L.n_tiles > 0 ? c->L.n_tiles : 1), st);
+  if (!e) e = dalloc(dout, 3 * (size_t)c->L.n_seg, st);
+  if (!e) {
+    launch_core(c->L, c->r, c->m, tiles, dout, st);
+    e = cudaGetLastError();
+  }
+  if (!e) e = cudaMemcpyAsync(out, dout, sizeof(double) * 3 * c->L.n_seg, cudaMemcpyDeviceToHost,
+                              st);
+  if (!e) e = cudaStreamSynchronize(st);
+  dfree(tiles, st);
+  dfree(dout, st);
+  if (e) return cuda_fail(c, e, "cmc_core");
+  return CMC_OK;
+}
+
 cmc_status cmc_lagrange_radii(cmc_ctx* c, const double* fracs, int32_t nf, double* out) {
   if (!c || !fracs || !out || nf < 1 || nf > 4096)
     return fail(c, CMC_EINVAL, "cmc_lagrange_radii: bad arguments");

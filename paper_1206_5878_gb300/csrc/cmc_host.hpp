@@ -254,6 +254,10 @@ void launch_energy(const SegLayout& L, const double* r, const double* vr, const 
                    const double* m, double* tile_m, double* tile_k, double* tile_w,
                    double* Mbuf, double* out3, cudaStream_t st);
 
+// core diagnostics (Eq. 19) per cluster: out3 = {rho_c, r_c, estimates};
+// tiles4: 4 * n_tiles doubles of scratch
+void launch_core(const SegLayout& L, const double* r, const double* m, double* tiles4,
+                 double* out3, cudaStream_t st);
 void launch_lagrange(const SegLayout& L, const double* r, const double* M,
                      const double* fracs, int nf, double* out, cudaStream_t st);
 

@@ -117,7 +117,8 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
     return;
   }
   const double w = sqrt(w2);
-  double num = kPi * msum;
+  // sin^2(beta/2) = min(1, 2 pi G^2 (m1+m2)^2 n lnL dt / |w|^3)
+  double num = (2.0 * kPi) * msum;
   num = num * msum;
   num = num * n;
   num = num * lnL;

@@ -434,6 +434,68 @@ __global__ void __launch_bounds__(kThreads) k_energy_tiles(Seg S, const double* 
   if (threadIdx.x == 0) { tile_k[blockIdx.x] = tk; tile_w[blockIdx.x] = tw; }
 }
 
+// Core diagnostics (section 4.3, Eq. 19): per bound star k with three
+// neighbours on each side, the 6th-order density estimate in the radial
+// order, rho_k = (m_{k-2} + ... + m_{k+2}) / (4 pi / 3 (r_{k+3}^3 - r_{k-3}^3));
+// per tile the sums of rho, rho^2, rho r and the number of estimates, each
+// in a fixed order (runs of 16 per thread, then a fixed tree).
+__global__ void __launch_bounds__(kThreads) k_core_tiles(Seg S, const double* r, const double* m,
+                                                         double* tile_s1, double* tile_s2,
+                                                         double* tile_sr, double* tile_n) {
+  __shared__ double s[kThreads];
+  TR R = tile_of(S, nullptr, blockIdx.x, false);
+  const int64_t b = R.begin + (int64_t)threadIdx.x * kPer;
+  const double c43 = (4.0 * kPi) / 3.0;
+  double a1 = 0.0, a2 = 0.0, ar = 0.0, an = 0.0;
+  for (int i = 0; i < kPer; ++i) {
+    const int64_t p = b + i;
+    const int64_t k = p - R.seg_begin;
+    if (p >= R.end || k < 3 || p + 3 >= R.bound_end) continue;
+    const double ro = r[p + 3], ri = r[p - 3];
+    const double vol = c43 * (ro * ro * ro - ri * ri * ri);
+    if (!pos_num(vol)) continue;
+    const double mass = (((m[p - 2] + m[p - 1]) + m[p]) + m[p + 1]) + m[p + 2];
+    const double rho = mass / vol;
+    a1 = a1 + rho;
+    a2 = a2 + rho * rho;
+    ar = ar + rho * r[p];
+    an = an + 1.0;
+  }
+  const double t1 = block_sum(a1, s), t2 = block_sum(a2, s), tr = block_sum(ar, s),
+               tn = block_sum(an, s);
+  if (threadIdx.x == 0) {
+    tile_s1[blockIdx.x] = t1;
+    tile_s2[blockIdx.x] = t2;
+    tile_sr[blockIdx.x] = tr;
+    tile_n[blockIdx.x] = tn;
+  }
+}
+
+// per cluster: rho_c = sum rho^2 / sum rho, r_c = sum rho r / sum rho and the
+// number of estimates (3 doubles per cluster)
+__global__ void __launch_bounds__(kThreads) k_core_final(Seg S, const double* tile_s1,
+                                                         const double* tile_s2,
+                                                         const double* tile_sr,
+                                                         const double* tile_n, double* out3) {
+  __shared__ double s[kThreads];
+  const int c = blockIdx.x;
+  const int64_t t0 = S.tile_off[c], t1 = S.tile_off[c + 1];
+  double a1 = 0.0, a2 = 0.0, ar = 0.0, an = 0.0;
+  for (int64_t j = t0 + threadIdx.x; j < t1; j += kThreads) {
+    a1 = a1 + tile_s1[j];
+    a2 = a2 + tile_s2[j];
+    ar = ar + tile_sr[j];
+    an = an + tile_n[j];
+  }
+  const double S1 = block_sum(a1, s), S2 = block_sum(a2, s), SR = block_sum(ar, s),
+               SN = block_sum(an, s);
+  if (threadIdx.x == 0) {
+    out3[3 * c + 0] = S1 > 0.0 ? S2 / S1 : 0.0;
+    out3[3 * c + 1] = S1 > 0.0 ? SR / S1 : 0.0;
+    out3[3 * c + 2] = SN;
+  }
+}
+
 __global__ void __launch_bounds__(kThreads) k_energy_final(Seg S, const double* tile_k,
                                                            const double* tile_w,
                                                            double* out3) {
@@ -728,6 +790,17 @@ void launch_energy(const SegLayout& L, const double* r, const double* vr, const 
   k_energy_tiles<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, r, vr, vt, m, tile_m, tile_k,
                                                           tile_w, Mbuf);
   k_energy_final<<<(unsigned)L.n_seg, kThreads, 0, st>>>(S, tile_k, tile_w, out3);
+}
+
+void launch_core(const SegLayout& L, const double* r, const double* m, double* tiles4,
+                 double* out3, cudaStream_t st) {
+  if (!L.n_tiles) return;
+  Seg S = L.dev();
+  const int64_t t = L.n_tiles;
+  k_core_tiles<<<(unsigned)t, kThreads, 0, st>>>(S, r, m, tiles4, tiles4 + t, tiles4 + 2 * t,
+                                                  tiles4 + 3 * t);
+  k_core_final<<<(unsigned)L.n_seg, kThreads, 0, st>>>(S, tiles4, tiles4 + t, tiles4 + 2 * t,
+                                                       tiles4 + 3 * t, out3);
 }
 
 void launch_lagrange(const SegLayout& L, const double* r, const double* M,
