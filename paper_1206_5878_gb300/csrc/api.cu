@@ -110,18 +110,61 @@ cmc_status check_err_flags(cmc_ctx* ctx) {
   return fail(ctx, CMC_ECUDA, msg);
 }
 
+// Whether the staged stars are already in (r, id) order in every segment
+// with ids that fit a bitmap of the key scratch (64 bits per star): then
+// bitoff receives each segment's first bit.  A state read back with
+// cmc_get_state always qualifies.
+bool staged_in_order(cmc_ctx* c, std::vector<unsigned long long>& bitoff, cudaStream_t st) {
+  const SegLayout& L = c->L;
+  unsigned int* d = nullptr;  // [0] order flag, [1 + s] largest id of segment s
+  if (dalloc(d, (size_t)L.n_seg + 1, st)) return false;
+  std::vector<unsigned int> h((size_t)L.n_seg + 1, 1u);
+  cudaError_t e = cudaMemsetAsync(d, 0, sizeof(unsigned int) * h.size(), st);
+  if (!e) {
+    launch_order_check(L, c->r, c->id, d, d + 1, st);
+    e = cudaMemcpyAsync(h.data(), d, sizeof(unsigned int) * h.size(), cudaMemcpyDeviceToHost, st);
+  }
+  if (!e) e = cudaStreamSynchronize(st);
+  dfree(d, st);
+  if (e || h[0] != 0u) return false;
+  bitoff.assign((size_t)L.n_seg, 0ull);
+  unsigned long long total = 0;
+  for (int s = 0; s < L.n_seg; ++s) {
+    bitoff[s] = total;
+    total += (unsigned long long)h[1 + s] + 1ull;
+  }
+  return total <= 64ull * (unsigned long long)L.n;
+}
+
 // Sort the staged stars in r, vr, vt, m, id by (r, id) per segment and
-// compute nb and the potential.  Ids must be unique per segment.
+// compute nb and the potential.  Ids must be unique per segment.  Stars
+// already in order (a state read back and set again) keep their places: the
+// order was checked, the ids are checked with a bitmap, and both sorts and
+// the gather are skipped.
 void order_state(cmc_ctx* c, cudaStream_t st) {
   const SegLayout& L = c->L;
-  launch_id_keys(L, c->id, c->keys, st);
-  sort_segments(L, c->W, c->keys, c->vals, 0, 4, true, c->err, st);
-  launch_check_ids(L, c->keys, c->err, st);
-  launch_rekey_radius(L, c->vals, c->r, c->id, c->keys, st);
-  sort_segments(L, c->W, c->keys, c->vals, 0, 8, false, c->err, st);
-  launch_make_keys(L, c->r, c->vr, c->vt, c->m, c->id, c->W.keys_alt, c->pay, st);
-  launch_gather(L, c->keys, c->vals, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, nullptr,
-                nullptr, st);
+  std::vector<unsigned long long> bitoff;
+  unsigned long long* dbo = nullptr;
+  if (L.n > 0 && staged_in_order(c, bitoff, st) && !dalloc(dbo, bitoff.size(), st)) {
+    cudaMemcpyAsync(dbo, bitoff.data(), sizeof(unsigned long long) * bitoff.size(),
+                    cudaMemcpyHostToDevice, st);
+    // the bitmap lives in the key scratch (64 bits per star)
+    cudaMemsetAsync(c->keys, 0, sizeof(uint64_t) * (size_t)L.n, st);
+    launch_ids_bitmap(L, c->id, dbo, reinterpret_cast<unsigned long long*>(c->keys), c->err, st);
+    launch_make_keys(L, c->r, c->vr, c->vt, c->m, c->id, c->keys, nullptr, st);
+    launch_recip(L.n, c->r, c->x, st);
+    cudaStreamSynchronize(st);  // bitoff lives on this stack frame
+    dfree(dbo, st);
+  } else {
+    launch_id_keys(L, c->id, c->keys, st);
+    sort_segments(L, c->W, c->keys, c->vals, 0, 4, true, c->err, st);
+    launch_check_ids(L, c->keys, c->err, st);
+    launch_rekey_radius(L, c->vals, c->r, c->id, c->keys, st);
+    sort_segments(L, c->W, c->keys, c->vals, 0, 8, false, c->err, st);
+    launch_make_keys(L, c->r, c->vr, c->vt, c->m, c->id, c->W.keys_alt, c->pay, st);
+    launch_gather(L, c->keys, c->vals, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, nullptr,
+                  nullptr, st);
+  }
   launch_nb_from_keys(L, c->keys, st);
   cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
   const bool mixed = c->cfg.precision == 1;

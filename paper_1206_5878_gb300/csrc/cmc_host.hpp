@@ -275,6 +275,13 @@ void launch_unpack_orbit(int64_t n, const uint64_t* keys, const Payload* pay, do
 void sort_prepare();
 void potential_prepare();  // shared-memory limit of the potential kernel
 
+// (r, id) order of staged stars (flag bit 0 set when not) and the largest id
+// per segment (maxid: n_seg values, zeroed by the caller)
+void launch_order_check(const SegLayout& L, const double* r, const uint32_t* id, uint32_t* flag,
+                        unsigned int* maxid, cudaStream_t st);
+// duplicate ids by a bitmap with bitoff[c] + id per star (kErrInput)
+void launch_ids_bitmap(const SegLayout& L, const uint32_t* id, const unsigned long long* bitoff,
+                       unsigned long long* bitmap, uint32_t* err, cudaStream_t st);
 void launch_check_ids(const SegLayout& L, const uint64_t* sorted_ids, uint32_t* err,
                       cudaStream_t st);
 

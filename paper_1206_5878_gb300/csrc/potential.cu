@@ -550,6 +550,43 @@ __global__ void k_check_ids(int64_t n, const int64_t* off, int n_seg, const uint
   if (p + 1 < off[c + 1] && ids[p] == ids[p + 1]) set_err(err, kErrInput);
 }
 
+// Whether the staged stars are already in (r, id) order within every
+// segment (bit patterns of positive or infinite r order like the values),
+// flag bit 0 set otherwise, and the largest id of each segment.
+__global__ void k_order_check(int64_t n, const int64_t* off, int n_seg, const double* r,
+                              const uint32_t* id, uint32_t* flag, unsigned int* maxid) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool live = p < n;
+  int c = 0;
+  uint32_t ip = 0;
+  if (live) {
+    c = seg_find(off, n_seg, p);
+    ip = id[p];
+    if (p + 1 < off[c + 1]) {
+      const unsigned long long a = ubits(r[p]), b = ubits(r[p + 1]);
+      if (!(a < b || (a == b && ip < id[p + 1]))) atomicOr(flag, 1u);
+    }
+  }
+  // one atomic per segment present in the warp
+  const unsigned full = __activemask();
+  const unsigned peers = __match_any_sync(full, live ? c : -1);
+  const unsigned mx = __reduce_max_sync(peers, ip);
+  if (live && (threadIdx.x & 31) == __ffs(peers) - 1) atomicMax(maxid + c, mx);
+}
+
+// Duplicate ids of sorted input: bit bitoff[c] + id of a bitmap per star;
+// a bit found set already is a duplicate (error)
+__global__ void k_ids_bitmap(int64_t n, const int64_t* off, int n_seg, const uint32_t* id,
+                             const unsigned long long* bitoff, unsigned long long* bitmap,
+                             uint32_t* err) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int c = seg_find(off, n_seg, p);
+  const unsigned long long b = bitoff[c] + id[p];
+  const unsigned long long bit = 1ull << (b & 63ull);
+  if (atomicOr(bitmap + (b >> 6), bit) & bit) set_err(err, kErrInput);
+}
+
 // One 256-thread block per segment.  The stars that escaped in this step
 // are the escaped range's entries with a finite r_old (earlier escapers
 // carry r_old = inf); their mass and energy m_k e_k (e_k in c) are summed
@@ -813,6 +850,18 @@ void launch_validate(const SegLayout& L, const double* r, const double* vr,
                      const double* vt, const double* m, bool allow_inf, uint32_t* err,
                      cudaStream_t st) {
   if (L.n) k_validate<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, r, vr, vt, m, allow_inf, err);
+}
+
+void launch_order_check(const SegLayout& L, const double* r, const uint32_t* id, uint32_t* flag,
+                        unsigned int* maxid, cudaStream_t st) {
+  if (L.n) k_order_check<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.off, L.n_seg, r, id, flag,
+                                                               maxid);
+}
+
+void launch_ids_bitmap(const SegLayout& L, const uint32_t* id, const unsigned long long* bitoff,
+                       unsigned long long* bitmap, uint32_t* err, cudaStream_t st) {
+  if (L.n) k_ids_bitmap<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, L.off, L.n_seg, id, bitoff,
+                                                              bitmap, err);
 }
 
 void launch_check_ids(const SegLayout& L, const uint64_t* sorted_ids, uint32_t* err,

@@ -274,3 +274,34 @@ def test_invalid_inputs_are_rejected(g):
     with pytest.raises(g.CMCError):
         c.set_escaped([0.0, np.nan])
     c.step(1)  # the context is still usable
+
+
+def test_set_state_in_order_and_shuffled(g):
+    """A state read back is set again in place (its order and ids checked
+    without sorting); the same stars shuffled go through the sorts and give
+    the same state; an ordered state with a duplicated id is rejected."""
+    d = ic.plummer(30_000, seed=6)
+    a = _cluster(g, d, 6)
+    a.step(2)
+    st = a.get_state()
+    b = _cluster(g, d, 6)
+    b.set_state(st, st["step"])
+    rng = np.random.default_rng(1)
+    perm = rng.permutation(30_000)
+    c = _cluster(g, d, 6)
+    c.set_state({k: st[k][perm] for k in ("r", "vr", "vt", "m", "id")}, st["step"])
+    sb, sc = b.get_state(), c.get_state()
+    for k in ("r", "vr", "vt", "m", "id", "phi"):
+        np.testing.assert_array_equal(sb[k], st[k], err_msg=k)
+        np.testing.assert_array_equal(sc[k], st[k], err_msg=k)
+    b.step(2)
+    c.step(2)
+    a.step(2)
+    for k in ("r", "vr", "vt", "id", "phi"):
+        np.testing.assert_array_equal(b.get_state()[k], a.get_state()[k], err_msg=k)
+        np.testing.assert_array_equal(c.get_state()[k], a.get_state()[k], err_msg=k)
+    dup = {k: st[k].copy() for k in ("r", "vr", "vt", "m", "id")}
+    dup["id"][10] = dup["id"][20000]  # still in (r, id) order
+    with pytest.raises(g.CMCError) as ei:
+        b.set_state(dup, 0)
+    assert ei.value.status == 1  # CMC_EINVAL
