@@ -86,6 +86,13 @@ def _declare(lib):
         "or_energy_W_brute": (_d, [_i64, _p, _p]),
         "or_lagrange_radii": (None, [_i64, _p, _p, _p, _i32, _p]),
         "or_core": (None, [_i64, _p, _p, _p]),
+        "or_taus_next": (_u32, [_p]),
+        "or_taus_pow2": (None, [ctypes.c_int, ctypes.c_int, _p]),
+        "or_taus_pow": (None, [ctypes.c_int, _u64, _p]),
+        "or_gf2_apply_pub": (_u32, [_p, _u32]),
+        "or_taus_seed": (None, [_u64, _p]),
+        "or_taus_streams": (None, [_u64, _i64, _p]),
+        "or_taus_bind": (None, [_p]),
         "or_core_rho": (None, [_i64, _p, _p, _p]),
         "or_step": (_d, [_i64, _p, _p, _p, _p, _p, _p, _p, _u64, _u32, _i32, _d, _d,
                          _i32, _i32, _i32, _p, _p]),
@@ -280,6 +287,60 @@ def core_rho(r, m):
     return out
 
 
+def taus_next(z, count=1):
+    """count outputs of the combined Tausworthe generator from the four
+    words z (a uint32 array of 4, advanced in place)."""
+    assert z.dtype == np.uint32 and z.shape == (4,)
+    return np.array([_L().or_taus_next(_ptr(z)) for _ in range(count)], dtype=np.uint32)
+
+
+def taus_pow(j, D):
+    """T_j^D as 32 columns (uint32), component j = 0..3."""
+    out = np.zeros(32, dtype=np.uint32)
+    _L().or_taus_pow(int(j), int(D), _ptr(out))
+    return out
+
+
+def taus_pow2(j, e):
+    out = np.zeros(32, dtype=np.uint32)
+    _L().or_taus_pow2(int(j), int(e), _ptr(out))
+    return out
+
+
+def gf2_apply(cols, v):
+    cols = np.ascontiguousarray(cols, dtype=np.uint32)
+    return int(_L().or_gf2_apply_pub(_ptr(cols), int(v)))
+
+
+def taus_seed(seed):
+    z = np.zeros(4, dtype=np.uint32)
+    _L().or_taus_seed(int(seed), _ptr(z))
+    return z
+
+
+def taus_streams(seed, n_ids):
+    """Starting words of the streams of ids 0..n_ids-1 (4 per id)."""
+    t = np.zeros(4 * int(n_ids), dtype=np.uint32)
+    _L().or_taus_streams(int(seed), int(n_ids), _ptr(t))
+    return t
+
+
+class taus_bound:
+    """Within the block, the method's draws come from the given stream table
+    (4 words per id, advanced in place) instead of Philox counters."""
+
+    def __init__(self, table):
+        assert table.dtype == np.uint32 and table.flags.c_contiguous
+        self.table = table
+
+    def __enter__(self):
+        _L().or_taus_bind(_ptr(self.table))
+        return self.table
+
+    def __exit__(self, *a):
+        _L().or_taus_bind(None)
+
+
 def half_mass_relaxation_time(n, r_h, mass=1.0, gamma=0.1):
     """Eq. 20: t_rh = 0.138 N / ln(gamma N) (r_h^3 / (G M))^(1/2), G = 1."""
     return 0.138 * n / math.log(gamma * n) * math.sqrt(r_h ** 3 / mass)
@@ -301,7 +362,8 @@ class Cluster:
 
     def __init__(self, r, vr, vt, m, ids, seed: int, *, theta_max: float = THETA_MAX,
                  gamma: float = GAMMA, bin_size: int = BIN_SIZE, max_trials: int = 1000,
-                 energy_correction: bool = True, pot_mode: str = "recursion"):
+                 energy_correction: bool = True, pot_mode: str = "recursion",
+                 rng: str = "philox"):
         r, vr, vt, m = _f64(r), _f64(vr), _f64(vt), _f64(m)
         ids = _u32a(ids)
         n = r.shape[0]
@@ -328,16 +390,27 @@ class Cluster:
         self.last_dt = None
         # mass and energy carried off by escapers (section 4.2's budget)
         self.escaped = np.zeros(2)
+        # "taus113": one combined-Tausworthe stream per id (section 3.6)
+        self.taus = None
+        if rng == "taus113":
+            self.taus = taus_streams(self.seed, int(self.id.max()) + 1 if n else 0)
+        elif rng != "philox":
+            raise ValueError("rng: philox or taus113")
 
     def step(self, nsteps: int = 1):
         for _ in range(nsteps):
             nb = np.array([self.nb], dtype=np.int64)
             stats = np.zeros(7, dtype=np.int64)
-            dt = _L().or_step(self.n, _ptr(nb), _ptr(self.r), _ptr(self.vr), _ptr(self.vt),
-                              _ptr(self.m), _ptr(self.id), _ptr(self.phi), self.seed,
-                              self.step_no, self.bin_size, self.pref, self.lnL,
-                              self.max_trials, self.ecorr, self.pot_mode, _ptr(stats),
-                              _ptr(self.escaped))
+            if self.taus is not None:
+                _L().or_taus_bind(_ptr(self.taus))
+            try:
+                dt = _L().or_step(self.n, _ptr(nb), _ptr(self.r), _ptr(self.vr),
+                                  _ptr(self.vt), _ptr(self.m), _ptr(self.id), _ptr(self.phi),
+                                  self.seed, self.step_no, self.bin_size, self.pref, self.lnL,
+                                  self.max_trials, self.ecorr, self.pot_mode, _ptr(stats),
+                                  _ptr(self.escaped))
+            finally:
+                _L().or_taus_bind(None)
             self.nb = int(nb[0])
             self.step_no += 1
             self.last_dt = dt

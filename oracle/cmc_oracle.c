@@ -80,10 +80,136 @@ double or_u01(uint32_t lo, uint32_t hi)
     return (double)(2u * k + 1u) * 0x1p-53;
 }
 
+/* ------------------------------------------------------------------------ */
+/* The paper's generator, as an alternative (section 3.6, App. A.2): the    */
+/* combined Tausworthe generator of L'Ecuyer (1999), period ~2^113, four    */
+/* LFSR components with parameters (k, q, s) = (31, 6, 18), (29, 2, 2),     */
+/* (28, 13, 7), (25, 3, 13).  A step of component (k, q, s) on its 32-bit   */
+/* word z is b = ((z << q) ^ z) >> (k - s), z = ((z & m_k) << s) ^ b, m_k   */
+/* clearing the low 32 - k bits; the output is the xor of the four words.   */
+/* Every step is linear over GF(2), so T^D is a 32 x 32 bit matrix per      */
+/* component: the jump functions.                                           */
+/* ------------------------------------------------------------------------ */
+static const int OR_TK[4] = {31, 29, 28, 25};
+static const int OR_TQ[4] = {6, 2, 13, 3};
+static const int OR_TS[4] = {18, 2, 7, 13};
+
+static uint32_t or_taus_comp(uint32_t z, int j)
+{
+    uint32_t mask = 0xFFFFFFFFu << (32 - OR_TK[j]);
+    uint32_t b = ((z << OR_TQ[j]) ^ z) >> (OR_TK[j] - OR_TS[j]);
+    return ((z & mask) << OR_TS[j]) ^ b;
+}
+
+/* One output; advances the four words in place. */
+uint32_t or_taus_next(uint32_t z[4])
+{
+    int j;
+    for (j = 0; j < 4; ++j) z[j] = or_taus_comp(z[j], j);
+    return z[0] ^ z[1] ^ z[2] ^ z[3];
+}
+
+/* 32 x 32 bit matrices as 32 columns: col[i] = image of bit i. */
+static uint32_t or_gf2_apply(const uint32_t col[32], uint32_t v)
+{
+    uint32_t r = 0u;
+    int i;
+    for (i = 0; i < 32; ++i)
+        if ((v >> i) & 1u) r ^= col[i];
+    return r;
+}
+
+static void or_gf2_mul(const uint32_t a[32], const uint32_t b[32], uint32_t out[32])
+{
+    uint32_t t[32];
+    int i;
+    for (i = 0; i < 32; ++i) t[i] = or_gf2_apply(a, b[i]);
+    for (i = 0; i < 32; ++i) out[i] = t[i];
+}
+
+/* T_j^(2^e): the one-step matrix of component j squared e times. */
+void or_taus_pow2(int j, int e, uint32_t out[32])
+{
+    int i;
+    for (i = 0; i < 32; ++i) out[i] = or_taus_comp(1u << i, j);
+    for (i = 0; i < e; ++i) or_gf2_mul(out, out, out);
+}
+
+/* T_j^D by binary powers (D up to 2^64 - 1). */
+void or_taus_pow(int j, uint64_t D, uint32_t out[32])
+{
+    uint32_t p[32];
+    int i;
+    for (i = 0; i < 32; ++i) out[i] = 1u << i;
+    or_taus_pow2(j, 0, p);
+    while (D) {
+        if (D & 1u) or_gf2_mul(p, out, out);
+        D >>= 1;
+        if (D) or_gf2_mul(p, p, p);
+    }
+}
+
+/* The words applied to a vector: out = M v, per component. */
+uint32_t or_gf2_apply_pub(const uint32_t col[32], uint32_t v) { return or_gf2_apply(col, v); }
+
+/* Splitmix64 (Steele, Lea & Flood 2014): the seed's mixer. */
+static uint64_t or_splitmix64(uint64_t *x)
+{
+    uint64_t z = (*x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Starting words of a cluster's sequence from its seed (reading): two
+ * splitmix64 outputs, top bit of each word set (every component's state,
+ * its top k bits, is then nonzero). */
+void or_taus_seed(uint64_t seed, uint32_t z[4])
+{
+    uint64_t x = seed, a = or_splitmix64(&x), b = or_splitmix64(&x);
+    z[0] = (uint32_t)a | 0x80000000u;
+    z[1] = (uint32_t)(a >> 32) | 0x80000000u;
+    z[2] = (uint32_t)b | 0x80000000u;
+    z[3] = (uint32_t)(b >> 32) | 0x80000000u;
+}
+
+/* Streams of ids 0 .. n_ids-1, D = 2^80 apart (section 3.6's jump
+ * displacement), as the paper builds them: the jump function T^D applied
+ * repeatedly to the seeded words, each intermediate state starting the
+ * next stream.  table: 4 words per id. */
+void or_taus_streams(uint64_t seed, int64_t n_ids, uint32_t *table)
+{
+    uint32_t J[4][32], z[4];
+    int j;
+    int64_t i;
+    or_taus_seed(seed, z);
+    for (j = 0; j < 4; ++j) or_taus_pow2(j, 80, J[j]);
+    for (i = 0; i < n_ids; ++i)
+        for (j = 0; j < 4; ++j) {
+            table[4 * i + j] = z[j];
+            z[j] = or_gf2_apply(J[j], z[j]);
+        }
+}
+
+/* The draws of the method: in the default mode a block of four words of
+ * Philox4x32-10 at the counter (id, step, tag, trial); with a stream table
+ * bound (or_taus_bind), the next four outputs of the stream of that id --
+ * the method draws each star's blocks in a fixed order (relaxation trials,
+ * then orbit trials, then the sign), so tag and trial are implied. */
+static uint32_t *or_taus_table = 0;
+
+void or_taus_bind(uint32_t *table) { or_taus_table = table; }
+
 static void or_draw(uint64_t seed, uint32_t id, uint32_t step, uint32_t tag,
                     uint32_t trial, uint32_t out[4])
 {
     uint32_t ctr[4], key[2];
+    if (or_taus_table) {
+        uint32_t *z = or_taus_table + 4 * (size_t)id;
+        int k;
+        for (k = 0; k < 4; ++k) out[k] = or_taus_next(z);
+        return;
+    }
     ctr[0] = id; ctr[1] = step; ctr[2] = tag; ctr[3] = trial;
     key[0] = (uint32_t)seed; key[1] = (uint32_t)(seed >> 32);
     or_philox4x32_10(ctr, key, out);
