@@ -353,7 +353,7 @@ def run_cmc(args, rank, world, local_rank):
     d = ic.plummer(n, seed=seed)
     dev = {k: torch.from_numpy(d[k].view(np.int32) if k == "id" else d[k]).cuda()
            for k in ("r", "vr", "vt", "m", "id")}
-    c = g.Cluster(dev, [seed], precision=prec)
+    c = g.Cluster(dev, [seed], precision=prec, rng=args.rng)
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -412,7 +412,9 @@ def run_cmc(args, rank, world, local_rank):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "f64+f32" if prec else "f64", "data": "synthetic",
-           "config": {"workload": "Plummer N=%d equal-mass, %s orbits" % (n, args.precision),
+           "config": {"workload": "Plummer N=%d equal-mass, %s orbits" % (n, args.precision)
+                      + ("" if args.rng == "philox" else ", Tausworthe streams"),
+                      "rng": args.rng,
                       "n_stars": n, "precision": args.precision, "seed": args.seed,
                       "parallelism": "replicas" if dist else "single",
                       "l2": "inputs larger than L2 (state %.2f GB)" % (n * 60 / 1e9)},
@@ -475,6 +477,9 @@ def main():
     ap.add_argument("--impl", default="cmc", choices=["cmc", "reference"])
     ap.add_argument("--n", type=int, default=10_000_000)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--rng", default="philox", choices=["philox", "taus113"],
+                    help="draws: counter-based Philox (default) or the paper's combined "
+                         "Tausworthe streams")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--no-fp64", dest="fp64", action="store_false")
     ap.add_argument("--no-e2e", dest="e2e", action="store_false")

@@ -94,6 +94,17 @@ typedef struct {
     int32_t orbit_variant;      /* mixed-mode orbit kernel variant (listed at
                                    cmc_get_tuning): -1 = the autotuner's choice
                                    (0 without autotune), or 0..6 (default -1) */
+    int32_t rng;                /* 0: counter-based Philox4x32-10 draws keyed by
+                                   (star id, step, purpose, trial) (default);
+                                   1: the paper's combined Tausworthe generator
+                                   (section 3.6; L'Ecuyer 1999), one stream per
+                                   star id, the streams 2^80 apart in one
+                                   sequence seeded from the cluster seed, each
+                                   star's draws taken in a fixed order
+                                   (relaxation, orbit trials, v_r sign); ids must
+                                   then be below 4 N_c + 64 in every cluster
+                                   (stream slots are indexed by id); the mixed
+                                   sampler runs one launch shape */
 } cmc_config;
 
 /* Fill cfg with the defaults shown above. */
@@ -133,6 +144,16 @@ cmc_status cmc_energy(cmc_ctx *ctx, double *out);
  * enclosed mass M_k = sum_{i<=k} m_i reaches f times the bound mass.
  * out: host, n_clusters x nf. */
 cmc_status cmc_lagrange_radii(cmc_ctx *ctx, const double *fracs, int32_t nf, double *out);
+
+/* The stream states of the Tausworthe mode (rng = 1): slots of four
+ * 32-bit words, cluster by cluster, slot = the cluster's first slot + id.
+ * cmc_get_rng_state writes them to out (host, may be NULL) and their
+ * number of words to *n_words; cmc_set_rng_state reads n_words words (the
+ * same count) from in (host).  With cmc_get_state / cmc_set_state they make
+ * a checkpoint from which the run continues bit for bit.  CMC_EINVAL in
+ * the counter mode or for a wrong count. */
+cmc_status cmc_get_rng_state(cmc_ctx *ctx, uint32_t *out, int64_t *n_words);
+cmc_status cmc_set_rng_state(cmc_ctx *ctx, const uint32_t *in, int64_t n_words);
 
 /* Core diagnostics (section 4.3, Eq. 19) per cluster of the bound stars:
  * out (host, n_clusters x 3) = {rho_c, r_c, n_est}.  The density around

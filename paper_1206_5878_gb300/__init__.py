@@ -61,7 +61,11 @@ class Cluster:
     """
 
     def __init__(self, state, seeds, sizes=None, stream=None, **cfg):
+        """cfg: cmc_config fields by name; rng may also be given as
+        "philox" (0) or "taus113" (1)."""
         self.lib = load()
+        if isinstance(cfg.get("rng"), str):
+            cfg["rng"] = {"philox": 0, "taus113": 1}[cfg["rng"]]
         r = state["r"]
         n = int(r.shape[0])
         sizes = [n] if sizes is None else [int(s) for s in sizes]
@@ -134,6 +138,18 @@ class Cluster:
         check(self.lib.cmc_lagrange_radii(self.ctx, fr.ctypes.data, fr.shape[0],
                                           out.ctypes.data), self.ctx)
         return out
+
+    def rng_state(self) -> np.ndarray:
+        """The Tausworthe stream states (4 words per slot), rng = taus113 only."""
+        nw = np.zeros(1, dtype=np.int64)
+        check(self.lib.cmc_get_rng_state(self.ctx, None, nw.ctypes.data), self.ctx)
+        out = np.zeros(int(nw[0]), dtype=np.uint32)
+        check(self.lib.cmc_get_rng_state(self.ctx, out.ctypes.data, nw.ctypes.data), self.ctx)
+        return out
+
+    def set_rng_state(self, words):
+        words = np.ascontiguousarray(words, dtype=np.uint32)
+        check(self.lib.cmc_set_rng_state(self.ctx, words.ctypes.data, words.shape[0]), self.ctx)
 
     def core(self) -> np.ndarray:
         """Per cluster {rho_c, r_c, number of estimates} (Eq. 19)."""

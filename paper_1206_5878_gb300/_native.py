@@ -32,7 +32,7 @@ STAGE_NAMES = ("timestep", "relax", "turning", "orbit", "sort", "gather", "poten
 class cmc_config(ctypes.Structure):
     _fields_ = [("precision", _i32), ("bin_size", _i32), ("theta_max", _d), ("gamma", _d),
                 ("max_trials", _i32), ("energy_correction", _i32), ("orbit_block", _i32),
-                ("autotune", _i32), ("orbit_variant", _i32)]
+                ("autotune", _i32), ("orbit_variant", _i32), ("rng", _i32)]
 
 
 # exported symbol -> (restype, argtypes); the list is the ABI of include/cmc.h
@@ -45,6 +45,8 @@ SIGNATURES = {
     "cmc_energy": (_i32, [_p, _p]),
     "cmc_lagrange_radii": (_i32, [_p, _p, _i32, _p]),
     "cmc_core": (_i32, [_p, _p]),
+    "cmc_get_rng_state": (_i32, [_p, _p, _p]),
+    "cmc_set_rng_state": (_i32, [_p, _p, _i64]),
     "cmc_get_state": (_i32, [_p, _p, _p, _p, _p, _p, _p, _p, _i32]),
     "cmc_set_state": (_i32, [_p, _p, _p, _p, _p, _p, _i64, _i32]),
     "cmc_get_nbound": (_i32, [_p, _p]),

@@ -258,6 +258,8 @@ void free_ctx(cmc_ctx* c) {
   dfree(c->pcount, st);
   free_sort(c->W, st);
   free_buckets(c->bk, st);
+  dfree(c->L.taus, st);
+  dfree(c->L.taus_base, st);
   free_layout(c->L, st);
   cudaStreamSynchronize(st);
   if (c->cap) cudaStreamDestroy(c->cap);
@@ -305,6 +307,115 @@ cmc_status load_state(cmc_ctx* c, const double* r, const double* vr, const doubl
 // and keep the fastest.  The orbit kernel runs once as a dry run (it writes
 // only keys and payload scratch) to give the sort realistic input; counters
 // it touched are reset.  Results never depend on the shapes.
+// ------------------------------------------------ Tausworthe streams (host)
+// Components (k, q, s) of the combined generator (section 3.6; L'Ecuyer
+// 1999) and one step of a component word; every step is linear over GF(2).
+constexpr int kTausK[4] = {31, 29, 28, 25}, kTausQ[4] = {6, 2, 13, 3},
+              kTausS[4] = {18, 2, 7, 13};
+
+uint32_t taus_word_host(uint32_t z, int j) {
+  const uint32_t b = ((z << kTausQ[j]) ^ z) >> (kTausK[j] - kTausS[j]);
+  return ((z & (0xFFFFFFFFu << (32 - kTausK[j]))) << kTausS[j]) ^ b;
+}
+
+// 32 x 32 matrices over GF(2) as columns (the image of each bit)
+uint32_t gf2_times(const uint32_t* col, uint32_t v) {
+  uint32_t r = 0u;
+  for (int i = 0; i < 32; ++i)
+    if ((v >> i) & 1u) r ^= col[i];
+  return r;
+}
+
+void gf2_square(uint32_t* m) {
+  uint32_t t[32];
+  for (int i = 0; i < 32; ++i) t[i] = gf2_times(m, m[i]);
+  for (int i = 0; i < 32; ++i) m[i] = t[i];
+}
+
+// P[j][b] = T_j^(2^(80 + b)) for b = 0..31: T_j squared 80 times, then once
+// more per b
+std::vector<uint32_t> taus_jump_matrices() {
+  std::vector<uint32_t> P(4 * 32 * 32);
+  for (int j = 0; j < 4; ++j) {
+    uint32_t m[32];
+    for (int i = 0; i < 32; ++i) m[i] = taus_word_host(1u << i, j);
+    for (int k = 0; k < 80; ++k) gf2_square(m);
+    for (int b = 0; b < 32; ++b) {
+      for (int i = 0; i < 32; ++i) P[((size_t)j * 32 + b) * 32 + i] = m[i];
+      gf2_square(m);
+    }
+  }
+  return P;
+}
+
+// seeded starting words of a cluster's sequence (reading): two splitmix64
+// outputs (Steele, Lea & Flood 2014) of the cluster seed, the top bit of
+// each word set so that every component state is nonzero
+void taus_seed_words(uint64_t seed, uint32_t w[4]) {
+  uint64_t x = seed, o[2];
+  for (int i = 0; i < 2; ++i) {
+    x += 0x9E3779B97F4A7C15ull;
+    uint64_t z = x;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    o[i] = z ^ (z >> 31);
+  }
+  w[0] = (uint32_t)o[0] | 0x80000000u;
+  w[1] = (uint32_t)(o[0] >> 32) | 0x80000000u;
+  w[2] = (uint32_t)o[1] | 0x80000000u;
+  w[3] = (uint32_t)(o[1] >> 32) | 0x80000000u;
+}
+
+// One stream slot per id of every cluster (slot = base + id), started at
+// T^(id 2^80) of the cluster's seeded words.  Ids must stay below
+// 4 N_c + 64 so that the slots stay within a few words per star.
+cmc_status init_streams(cmc_ctx* c, const uint64_t* seeds) {
+  SegLayout& L = c->L;
+  cudaStream_t st = c->stream;
+  unsigned int* d = nullptr;
+  std::vector<unsigned int> h((size_t)L.n_seg + 1, 0u);
+  cudaError_t e = dalloc(d, h.size(), st);
+  if (!e) e = cudaMemsetAsync(d, 0, sizeof(unsigned int) * h.size(), st);
+  if (!e) {
+    launch_order_check(L, c->r, c->id, d, d + 1, st);
+    e = cudaMemcpyAsync(h.data(), d, sizeof(unsigned int) * h.size(), cudaMemcpyDeviceToHost, st);
+  }
+  if (!e) e = cudaStreamSynchronize(st);
+  dfree(d, st);
+  if (e) return cuda_fail(c, e, "cmc_init: streams");
+  std::vector<int64_t> base((size_t)L.n_seg + 1, 0);
+  std::vector<uint32_t> words((size_t)4 * L.n_seg);
+  for (int s = 0; s < L.n_seg; ++s) {
+    const int64_t nc = L.h_off[s + 1] - L.h_off[s];
+    if ((int64_t)h[1 + s] >= 4 * nc + 64)
+      return fail(c, CMC_EINVAL, "cmc_init: the Tausworthe streams need ids below 4 N + 64");
+    base[s + 1] = base[s] + (int64_t)h[1 + s] + 1;
+    taus_seed_words(seeds[s], &words[4 * (size_t)s]);
+  }
+  const std::vector<uint32_t> P = taus_jump_matrices();
+  uint32_t* dP = nullptr;
+  uint4* dw = nullptr;
+  L.taus_slots = base[L.n_seg];
+  e = dalloc(L.taus, (size_t)L.taus_slots, st);
+  if (!e) e = dalloc(L.taus_base, base.size(), st);
+  if (!e) e = dalloc(dP, P.size(), st);
+  if (!e) e = dalloc(dw, (size_t)L.n_seg, st);
+  if (!e) e = cudaMemcpyAsync(L.taus_base, base.data(), sizeof(int64_t) * base.size(),
+                              cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(dP, P.data(), sizeof(uint32_t) * P.size(), cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(dw, words.data(), sizeof(uint32_t) * words.size(),
+                              cudaMemcpyHostToDevice, st);
+  if (!e) {
+    launch_taus_init(L.taus_slots, L.n_seg, L.taus_base, dw, dP, L.taus, st);
+    e = cudaGetLastError();
+  }
+  if (!e) e = cudaStreamSynchronize(st);  // the host vectors live on this frame
+  dfree(dP, st);
+  dfree(dw, st);
+  if (e) return cuda_fail(c, e, "cmc_init: streams");
+  return CMC_OK;
+}
+
 cmc_status autotune(cmc_ctx* c) {
   const SegLayout& L = c->L;
   cudaStream_t st = c->stream;
@@ -312,6 +423,14 @@ cmc_status autotune(cmc_ctx* c) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
+  // the dry runs draw from the streams: keep a copy to put back
+  uint4* taus_saved = nullptr;
+  if (L.taus) {
+    cudaError_t es = dalloc(taus_saved, (size_t)L.taus_slots, st);
+    if (!es) es = cudaMemcpyAsync(taus_saved, L.taus, sizeof(uint4) * L.taus_slots,
+                                  cudaMemcpyDeviceToDevice, st);
+    if (es) return cuda_fail(c, es, "autotune");
+  }
   auto run_orbit = [&](int blk, int var) {
     launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                  mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m,
@@ -361,9 +480,13 @@ cmc_status autotune(cmc_ctx* c) {
     }
   cudaError_t e = sort_set_shape(L, c->W, best_ipt, best_rank, st);
   // undo the dry run's bookkeeping
+  if (!e && taus_saved)
+    e = cudaMemcpyAsync(L.taus, taus_saved, sizeof(uint4) * L.taus_slots,
+                        cudaMemcpyDeviceToDevice, st);
   if (!e) e = cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
   if (!e) e = cudaMemsetAsync(L.stats, 0, sizeof(unsigned long long) * kStStride * L.n_seg, st);
   if (!e) e = cudaStreamSynchronize(st);
+  if (taus_saved) dfree(taus_saved, st);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (!e) e = cudaGetLastError();
@@ -387,6 +510,7 @@ void cmc_config_default(cmc_config* cfg) {
   cfg->orbit_block = 0;
   cfg->autotune = 1;
   cfg->orbit_variant = -1;
+  cfg->rng = 0;
 }
 
 cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
@@ -403,7 +527,8 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   if ((cfg.precision != 0 && cfg.precision != 1) || cfg.bin_size < 2 || (cfg.bin_size & 1) ||
       cfg.max_trials < 1 || cfg.max_trials > (1 << 24) || !(cfg.theta_max > 0.0) ||
       !(cfg.gamma > 0.0) || cfg.orbit_block < 0 || cfg.orbit_block > 256 ||
-      (cfg.orbit_block % 32) || cfg.orbit_variant < -1 || cfg.orbit_variant >= kOrbitVariants)
+      (cfg.orbit_block % 32) || cfg.orbit_variant < -1 || cfg.orbit_variant >= kOrbitVariants ||
+      (cfg.rng != 0 && cfg.rng != 1))
     return fail(nullptr, CMC_EINVAL, "cmc_init: bad configuration");
   std::vector<int64_t> sizes(n_per_cluster, n_per_cluster + n_clusters);
   std::vector<uint64_t> sd(seeds, seeds + n_clusters);
@@ -463,6 +588,14 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
     g_err = c->last_error;
     free_ctx(c);
     return s;
+  }
+  if (cfg.rng == 1) {
+    s = init_streams(c, seeds);
+    if (s != CMC_OK) {
+      g_err = c->last_error;
+      free_ctx(c);
+      return s;
+    }
   }
   c->orbit_variant = cfg.orbit_variant > 0 ? cfg.orbit_variant : 0;
   if (cfg.autotune) {
@@ -538,6 +671,32 @@ cmc_status cmc_energy(cmc_ctx* c, double* out) {
                                   cudaMemcpyDeviceToHost, c->stream);
   if (!e) e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_fail(c, e, "cmc_energy");
+  return CMC_OK;
+}
+
+cmc_status cmc_get_rng_state(cmc_ctx* c, uint32_t* out, int64_t* n_words) {
+  if (!c || !n_words) return fail(c, CMC_EINVAL, "cmc_get_rng_state: bad arguments");
+  if (!c->L.taus) return fail(c, CMC_EINVAL, "cmc_get_rng_state: counter mode has no streams");
+  *n_words = 4 * c->L.taus_slots;
+  if (!out) return CMC_OK;
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaMemcpyAsync(out, c->L.taus, sizeof(uint4) * c->L.taus_slots,
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "cmc_get_rng_state");
+  return CMC_OK;
+}
+
+cmc_status cmc_set_rng_state(cmc_ctx* c, const uint32_t* in, int64_t n_words) {
+  if (!c || !in) return fail(c, CMC_EINVAL, "cmc_set_rng_state: bad arguments");
+  if (!c->L.taus) return fail(c, CMC_EINVAL, "cmc_set_rng_state: counter mode has no streams");
+  if (n_words != 4 * c->L.taus_slots)
+    return fail(c, CMC_EINVAL, "cmc_set_rng_state: wrong number of words");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaMemcpyAsync(c->L.taus, in, sizeof(uint4) * c->L.taus_slots,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "cmc_set_rng_state");
   return CMC_OK;
 }
 

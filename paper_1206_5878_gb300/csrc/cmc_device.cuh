@@ -59,6 +59,8 @@ struct Seg {
   int64_t* nb;             // bound stars per segment (device, changes)
   uint64_t* dt_bits;       // timestep per segment as double bits
   unsigned long long* stats;  // kStStride counters per segment
+  uint4* taus;             // combined-Tausworthe streams, one per id slot (or null)
+  const int64_t* taus_base;  // per segment: first stream slot (slot = base + id)
   int n_seg;
 };
 
@@ -119,6 +121,67 @@ __device__ __forceinline__ double sym_double(int64_t U) {
                                           (aa & 0x000FFFFFFFFFFFFFull)));
 }
 
+// ------------------------------------------- combined Tausworthe streams
+// The paper's generator as an option (section 3.6; L'Ecuyer 1999): four
+// LFSR words with (k, q, s) = (31, 6, 18), (29, 2, 2), (28, 13, 7),
+// (25, 3, 13); a step of a word z is b = ((z << q) ^ z) >> (k - s),
+// z = ((z & m_k) << s) ^ b (m_k clears the low 32 - k bits); the output is
+// the xor of the four words.
+template <int k, int q, int s>
+__device__ __forceinline__ uint32_t taus_word(uint32_t z) {
+  const uint32_t b = ((z << q) ^ z) >> (k - s);
+  return ((z & (0xFFFFFFFFu << (32 - k))) << s) ^ b;
+}
+__device__ __forceinline__ uint32_t taus_next(uint4& z) {
+  z.x = taus_word<31, 6, 18>(z.x);
+  z.y = taus_word<29, 2, 2>(z.y);
+  z.z = taus_word<28, 13, 7>(z.z);
+  z.w = taus_word<25, 3, 13>(z.w);
+  return z.x ^ z.y ^ z.z ^ z.w;
+}
+
+// A star's random blocks of four words.  Counter mode (kTaus false):
+// Philox4x32-10 at (id, step, tag, trial).  Stream mode: the next four
+// outputs of the star's own stream; the method asks for each star's blocks
+// in a fixed order (relaxation trials, orbit trials, the v_r sign), so the
+// tag and the trial are implied by the order.
+template <bool kTaus>
+struct Draws {
+  uint64_t seed;
+  uint32_t id, step;
+  uint4 z;
+  __device__ __forceinline__ U4 block(uint32_t tag, uint32_t t) {
+    if (!kTaus) return philox(id, step, tag, t, seed);
+    U4 w;
+    w.x = taus_next(z);
+    w.y = taus_next(z);
+    w.z = taus_next(z);
+    w.w = taus_next(z);
+    return w;
+  }
+  // pass over n blocks (stream mode)
+  __device__ __forceinline__ void skip(uint32_t n) {
+    if (kTaus)
+      for (uint32_t i = 0; i < 4u * n; ++i) taus_next(z);
+  }
+};
+
+template <bool kTaus>
+__device__ __forceinline__ Draws<kTaus> draws_of(const Seg& S, int c, uint32_t id,
+                                                 uint32_t step) {
+  Draws<kTaus> d;
+  d.seed = S.seed[c];
+  d.id = id;
+  d.step = step;
+  if (kTaus) d.z = S.taus[__ldg(S.taus_base + c) + id];
+  return d;
+}
+
+template <bool kTaus>
+__device__ __forceinline__ void draws_keep(const Seg& S, int c, const Draws<kTaus>& d) {
+  if (kTaus) S.taus[__ldg(S.taus_base + c) + d.id] = d.z;
+}
+
 // uniform planar direction (cos a, sin a) by rejection of a point in the
 // unit disk; the doubled angle gives cos = (u^2 - v^2)/q, sin = 2uv/q.
 //
@@ -128,12 +191,12 @@ __device__ __forceinline__ double sym_double(int64_t U) {
 // U^2 + V^2 <= 2^104 (128-bit) gives the same answer; inside the band the
 // FP64 expression decides.  The loop is integer work only; the FP64
 // arithmetic of the accepted draw runs once, after it.
-__device__ __forceinline__ bool disk_angle(uint64_t seed, uint32_t id, uint32_t step,
-                                           uint32_t tag, double& c, double& s) {
+template <bool kTaus>
+__device__ __forceinline__ bool disk_angle(Draws<kTaus>& g, uint32_t tag, double& c, double& s) {
   int64_t Ua = 0, Va = 0;
   bool ok = false;
   for (uint32_t t = 0; t < 64u; ++t) {
-    U4 w = philox(id, step, tag, t, seed);
+    U4 w = g.block(tag, t);
     const int64_t U = sym_int(w.x, w.y), V = sym_int(w.z, w.w);
     const uint64_t A = U < 0 ? (uint64_t)(-U) : (uint64_t)U;
     const uint64_t B = V < 0 ? (uint64_t)(-V) : (uint64_t)V;

@@ -38,11 +38,15 @@ struct SegLayout {
   uint64_t* dt_last = nullptr;      // timestep of the last completed step
   unsigned long long* stats = nullptr;
   double* esc_me = nullptr;         // [n_seg][2]: mass, energy carried off by escapers
+  uint4* taus = nullptr;            // combined-Tausworthe streams (stream mode only)
+  int64_t* taus_base = nullptr;     // per segment: first stream slot
+  int64_t taus_slots = 0;
 
   Seg dev() const {
     Seg s;
     s.off = off; s.tile_off = tile_off; s.pair_off = pair_off; s.bin_off = bin_off;
     s.seed = seed; s.lnL = lnL; s.nb = nb; s.dt_bits = dt_bits; s.stats = stats;
+    s.taus = taus; s.taus_base = taus_base;
     s.n_seg = n_seg;
     return s;
   }
@@ -282,6 +286,11 @@ void launch_order_check(const SegLayout& L, const double* r, const uint32_t* id,
 // duplicate ids by a bitmap with bitoff[c] + id per star (kErrInput)
 void launch_ids_bitmap(const SegLayout& L, const uint32_t* id, const unsigned long long* bitoff,
                        unsigned long long* bitmap, uint32_t* err, cudaStream_t st);
+// starting states of the Tausworthe streams (dynamics.cu): slots of
+// segment c from base[c] (n_seg + 1 offsets), words: the segment's seeded
+// words, P: [4][32][32] jump matrices T^(2^(80 + b))
+void launch_taus_init(int64_t slots, int n_seg, const int64_t* base, const uint4* words,
+                      const uint32_t* P, uint4* table, cudaStream_t st);
 void launch_check_ids(const SegLayout& L, const uint64_t* sorted_ids, uint32_t* err,
                       cudaStream_t st);
 

@@ -83,7 +83,10 @@ __global__ void __launch_bounds__(256) k_bins(Seg S, int bs, double pref, const 
   }
 }
 
-// One thread per pair slot: stars a = 2j and b = 2j + 1 of a segment.
+// One thread per pair slot: stars a = 2j and b = 2j + 1 of a segment.  The
+// pair's random draws come from its first star (counters keyed by its id,
+// or its stream, kept after the draws).
+template <bool kTaus>
 __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double* vt,
                                                const double* m, const uint32_t* id,
                                                const double* nbin, const uint32_t* step_p) {
@@ -101,18 +104,17 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   const double lnL = S.lnL[c];
   // no density, no mass, or no positive Coulomb logarithm: no deflection
   if (!pos_num(n) || !pos_num(msum) || !pos_num(lnL) || !lt_inf(dt)) return;
-  const uint64_t seed = S.seed[c];
-  const uint32_t step = *step_p;
-  const uint32_t ida = id[a];
+  Draws<kTaus> g = draws_of<kTaus>(S, c, id[a], *step_p);
   int fails = 0;
   double cpsi, spsi, cphi, sphi;
-  if (!disk_angle(seed, ida, step, kTagPsi, cpsi, spsi)) ++fails;
+  if (!disk_angle(g, kTagPsi, cpsi, spsi)) ++fails;
   const double v1x = vr[a], v1y = vt[a], v1z = 0.0;
   const double v2x = vr[b], vtb = vt[b];
   const double v2y = vtb * cpsi, v2z = vtb * spsi;
   const double wx = v1x - v2x, wy = v1y - v2y, wz = v1z - v2z;
   const double w2 = (wx * wx + wy * wy) + wz * wz;
   if (!pos_num(w2)) {
+    draws_keep(S, c, g);
     if (fails) stat_add(S.stats, c, kStAngleFails, (unsigned long long)fails);
     return;
   }
@@ -128,7 +130,8 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   // cos(beta) = 1 - 2 sin^2(beta/2), sin(beta) = 2 sin(beta/2) cos(beta/2)
   const double cosb = 1.0 - 2.0 * s2;
   const double sinb = 2.0 * sqrt(s2 * (1.0 - s2));
-  if (!disk_angle(seed, ida, step, kTagPhi, cphi, sphi)) ++fails;
+  if (!disk_angle(g, kTagPhi, cphi, sphi)) ++fails;
+  draws_keep(S, c, g);
   // e1 = (w x xhat)/|w x xhat| = (0, wz, -wy)/|.| (yhat for radial w);
   // u = w x e1 has length |w| and completes the frame perpendicular to w
   const double wp2 = wy * wy + wz * wz;
@@ -161,7 +164,38 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   if (fails) stat_add(S.stats, c, kStAngleFails, (unsigned long long)fails);
 }
 
+// Starting states of the Tausworthe streams: slot e of segment c (id =
+// e - base[c]) gets T^(id 2^80) of the segment's seeded words, T^(id 2^80)
+// as the product of the matrices P_b = T^(2^(80 + b)) over the bits of id.
+// P: [4 components][32 bits b][32 columns], a column = the image of one bit.
+__global__ void k_taus_init(int64_t slots, int n_seg, const int64_t* base, const uint4* words,
+                            const uint32_t* P, uint4* table) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= slots) return;
+  const int c = seg_find(base, n_seg, e);
+  const uint64_t idv = (uint64_t)(e - base[c]);
+  const uint4 w = words[c];
+  uint32_t v[4] = {w.x, w.y, w.z, w.w};
+  for (int j = 0; j < 4; ++j)
+    for (int b = 0; b < 32; ++b) {
+      if (!((idv >> b) & 1ull)) continue;
+      const uint32_t* col = P + ((size_t)j * 32 + b) * 32;
+      uint32_t r = 0u;
+      for (int i = 0; i < 32; ++i)
+        if ((v[j] >> i) & 1u) r ^= __ldg(col + i);
+      v[j] = r;
+    }
+  table[e] = make_uint4(v[0], v[1], v[2], v[3]);
+}
+
 }  // namespace
+
+void launch_taus_init(int64_t slots, int n_seg, const int64_t* base, const uint4* words,
+                      const uint32_t* P, uint4* table, cudaStream_t st) {
+  if (slots > 0)
+    k_taus_init<<<(unsigned)((slots + 255) / 256), 256, 0, st>>>(slots, n_seg, base, words, P,
+                                                                 table);
+}
 
 void launch_bins(const SegLayout& L, const double* r, const double* vr, const double* vt,
                  const double* m, double* nbin, double pref, cudaStream_t st) {
@@ -174,8 +208,11 @@ void launch_relax(const SegLayout& L, double* vr, double* vt, const double* m,
                   const uint32_t* id, const double* nbin, const uint32_t* step,
                   cudaStream_t st) {
   if (!L.n_pairs) return;
-  k_relax<<<(unsigned)((L.n_pairs + 127) / 128), 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m,
-                                                               id, nbin, step);
+  const unsigned grid = (unsigned)((L.n_pairs + 127) / 128);
+  if (L.taus)
+    k_relax<true><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin, step);
+  else
+    k_relax<false><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin, step);
 }
 
 }  // namespace cmc

@@ -791,7 +791,7 @@ enum : uint32_t { kSmpAccepted = 0, kSmpPending = 1, kSmpDegenerate = 2, kSmpCap
 // samples is as valid an envelope as the FP64 one (it differs from it by up
 // to ~1e-4 at the outer samples, so the two modes draw different, equally
 // exact, accept sequences).
-template <int kMinB>
+template <int kMinB, bool kTaus>
 __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, const double* r,
                                                   const double* phi, const double* vr,
                                                   const double* vt, const uint32_t* id,
@@ -827,10 +827,9 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
       if (!gt_pos(rmax, rmin) || !(F32 > 0.0f)) {
         st = kSmpDegenerate;
       } else {
-        const uint32_t idk = id[p], step = *step_p;
-        const uint64_t seed = S.seed[c];
+        Draws<kTaus> g = draws_of<kTaus>(S, c, id[p], *step_p);
         for (; t < max_trials; ++t) {
-          const U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
+          const U4 w = g.block(kTagRej, (uint32_t)t);
           const int d = accept32(GD, E32, J32, c0f, c1f, F32, 2.0f * u01f(w.y) - 1.0f,
                                  u01f(w.w), viol);
           if (d == 0) continue;
@@ -866,6 +865,7 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
 // kSmpAccepted and the accepted trial, or kSmpCap.  Most threads find no
 // pending star and leave at once.
 // one pending star (p = n: an idle lane); counts go to the statistics
+template <bool kTaus>
 __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double* r,
                                              const double* x, const double* phi,
                                              const float2* t32, const double* Menc,
@@ -901,12 +901,13 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
         const double c1 = scale_down<2>(rmax - rmin);
         const float c0f = f32_rn(c0), c1f = f32_rn(c1);
         const double F = (double)__uint_as_float((uint32_t)(res >> 32));
-        const uint32_t idk = id[p], step = *step_p;
-        const uint64_t seed = S.seed[c];
         uint32_t st = kSmpCap;
         int t = (int)(res & 0x3FFFFFFFull);
+        // stream mode: the blocks of trials 0 .. t-1 were the FP32 sampler's
+        Draws<kTaus> g = draws_of<kTaus>(S, c, id[p], *step_p);
+        g.skip((uint32_t)t);
         for (; t < max_trials; ++t) {
-          const U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
+          const U4 w = g.block(kTagRej, (uint32_t)t);
           const double sv = sym_double(sym_int(w.x, w.y));
           double rs, xs, ph, L, Q;
           point64(BA.node + sb, nbc, s, c0, c1, sv,
@@ -933,6 +934,7 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
   }
 }
 
+template <bool kTaus>
 __global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const double* r,
                                                    const double* x, const double* phi,
                                                    const float2* t32, const double* Menc,
@@ -944,8 +946,9 @@ __global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const 
                                                    const uint32_t* pcount, int64_t n) {
   const uint32_t np = *pcount;
   for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < np; i0 += gridDim.x * blockDim.x) {
-    pending_star(S, max_trials, r, x, phi, t32, Menc, vr, vt, id, step_p, BA, tp_min, tp_max,
-                 keys, i0 + threadIdx.x < np ? (int64_t)plist[i0 + threadIdx.x] : n, n);
+    pending_star<kTaus>(S, max_trials, r, x, phi, t32, Menc, vr, vt, id, step_p, BA, tp_min,
+                        tp_max, keys, i0 + threadIdx.x < np ? (int64_t)plist[i0 + threadIdx.x] : n,
+                        n);
   }
 }
 
@@ -953,7 +956,7 @@ __global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const 
 // tp_max, FP32 sampler result from k_sample32 / k_pending64 in the key
 // slot).  kMinB: resident 256-thread blocks to fit (caps registers; 1 = no
 // cap).
-template <int kPrec, int kMinB>
+template <int kPrec, int kMinB, bool kTaus>
 __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, const double* r,
                                                const double* x, const double* phi,
                                                const float2* t32, const double* Menc, const double* vr,
@@ -990,8 +993,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
   s.k = k;
   s.E = __ldg(T.phi + k) + 0.5 * (vrk * vrk + vtk * vtk);
   s.J = rk * vtk;
-  const uint64_t seed = S.seed[c];
-  const uint32_t step = *step_p;
+  Draws<kTaus> g = draws_of<kTaus>(S, c, idk, *step_p);
   double ph_new = __ldg(T.phi + k);
 
   if (!lt0(s.E)) {
@@ -1041,7 +1043,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
         code = 3;
         double rs_a = 0.0, ph_a = 0.0, Q_a = 0.0;
         for (int t = 0; t < max_trials; ++t) {
-          U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
+          U4 w = g.block(kTagRej, (uint32_t)t);
           const double Xp = u01(w.z, w.w);
           const double sv = sym_double(sym_int(w.x, w.y));  // 2 X - 1, exact
           double rs, ph, Q;
@@ -1058,10 +1060,12 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
         }
         if (code == 3) {
           trials = max_trials;
+          draws_keep(S, c, g);
         } else {
           // the accepted point's velocities once the warp's lanes are done
           const double sq = sqrt(Q_a);
-          U4 sg = philox(idk, step, kTagSgn, 0u, seed);
+          U4 sg = g.block(kTagSgn, 0u);
+          draws_keep(S, c, g);
           r_new = rs_a;
           P.vr = (sg.x & 1u) ? -sq : sq;
           P.vt = s.J / rs_a;
@@ -1081,6 +1085,8 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
       } else if (st == kSmpCap) {
         code = 3;
         trials = max_trials;
+        g.skip((uint32_t)max_trials);
+        draws_keep(S, c, g);
       } else {
         const float c0f = f32_rn(c0), c1f = f32_rn(c1);
         const int nb32 = (int)nbc;
@@ -1089,12 +1095,15 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
         if (!acc) {
           code = 3;
           trials = max_trials;
+          g.skip((uint32_t)max_trials);
+          draws_keep(S, c, g);
         } else {
           code = 0;
           trials = t + 1;
           // the accepted point in FP64 from the full 53-bit X, once per
           // star, with the warp's lanes together
-          const U4 w = philox(idk, step, kTagRej, (uint32_t)t, seed);
+          g.skip((uint32_t)t);  // stream mode: the rejected trials' blocks
+          const U4 w = g.block(kTagRej, (uint32_t)t);
           const double sv = sym_double(sym_int(w.x, w.y));
           double rs, xs, ph, L, Q;
           point64(BA.node + sb, nbc, s, c0, c1, sv,
@@ -1102,7 +1111,8 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
                   L, Q);
           if (!pos_num(Q)) Q = 0.0;
           const double sq = sqrt(Q);
-          U4 sg = philox(idk, step, kTagSgn, 0u, seed);
+          U4 sg = g.block(kTagSgn, 0u);
+          draws_keep(S, c, g);
           r_new = rs;
           P.vr = (sg.x & 1u) ? -sq : sq;
           P.vt = L;
@@ -1422,28 +1432,33 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
 #define CMC_TURN(B)                                                                          \
   k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, t32, Menc, vr, vt, ba,      \
                                              tp_min, tp_max, L.n)
-#define CMC_ORBIT(P, B)                                                                     \
-  k_orbit<P, B><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, m, \
-                                        id, step, keys, pay, L.esc_step, d, ba, tp_min,      \
-                                        tp_max, L.n)
-#define CMC_MIXED(B)                                                                        \
+#define CMC_ORBIT(P, B, T)                                                                  \
+  k_orbit<P, B, T><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, \
+                                           m, id, step, keys, pay, L.esc_step, d, ba, tp_min, \
+                                           tp_max, L.n)
+#define CMC_MIXED(B, T)                                                                     \
   do {                                                                                      \
     if (with_turning) CMC_TURN(B);                                                          \
     cudaMemsetAsync(pcount, 0, sizeof(uint32_t), st);                                      \
-    k_sample32<B><<<grid, block, 0, st>>>(L.dev(), max_trials, r, phi, vr, vt, id, step, ba, \
-                                          tp_min, tp_max, keys, plist, pcount, L.n);        \
-    k_pending64<<<pgrid, 128, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, id, \
-                                       step, ba, tp_min, tp_max, keys, plist, pcount, L.n);  \
-    CMC_ORBIT(1, 4);                                                                        \
+    k_sample32<B, T><<<grid, block, 0, st>>>(L.dev(), max_trials, r, phi, vr, vt, id, step, \
+                                             ba, tp_min, tp_max, keys, plist, pcount, L.n); \
+    k_pending64<T><<<pgrid, 128, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, \
+                                          id, step, ba, tp_min, tp_max, keys, plist, pcount, \
+                                          L.n);                                             \
+    CMC_ORBIT(1, 4, T);                                                                     \
   } while (0)
-  if (precision == 0) CMC_ORBIT(0, 1);
-  else if (variant == 1) CMC_MIXED(2);
-  else if (variant == 2) CMC_MIXED(3);
-  else if (variant == 3) CMC_MIXED(4);
-  else if (variant == 4) CMC_MIXED(5);
-  else if (variant == 5) CMC_MIXED(6);
-  else if (variant == 6) CMC_MIXED(8);
-  else CMC_MIXED(1);
+  if (L.taus) {
+    // stream mode: one launch shape of the sampler
+    if (precision == 0) CMC_ORBIT(0, 1, true);
+    else CMC_MIXED(5, true);
+  } else if (precision == 0) CMC_ORBIT(0, 1, false);
+  else if (variant == 1) CMC_MIXED(2, false);
+  else if (variant == 2) CMC_MIXED(3, false);
+  else if (variant == 3) CMC_MIXED(4, false);
+  else if (variant == 4) CMC_MIXED(5, false);
+  else if (variant == 5) CMC_MIXED(6, false);
+  else if (variant == 6) CMC_MIXED(8, false);
+  else CMC_MIXED(1, false);
 #undef CMC_MIXED
 #undef CMC_TURN
 #undef CMC_ORBIT
