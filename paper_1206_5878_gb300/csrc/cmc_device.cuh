@@ -74,6 +74,82 @@ __device__ __forceinline__ int seg_find(const int64_t* a, int n, int64_t v) {
   return lo;
 }
 
+// ------------------------------------- exact operations on bit patterns
+// The FP64 pipe of this GPU issues two lanes per SM and clock, and most of
+// the timestep's kernels are bound by it.  Operations that need no FP64
+// arithmetic -- comparisons, rounding to float, scaling by 1/2 or 1/4 --
+// run on the integer pipes from the bit patterns; each gives the IEEE-754
+// result of the FP64 operation it replaces (NaN, infinities, zeros and
+// subnormals included, by the bit tests or by falling back to the FP64
+// operation where the shortcut does not hold).
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+constexpr unsigned long long kSignBit = 0x8000000000000000ull;
+
+__device__ __forceinline__ unsigned long long ubits(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+// v < 0.0
+__device__ __forceinline__ bool lt0(double v) {
+  const unsigned long long u = ubits(v);
+  return u > kSignBit && u <= (kSignBit | kInfBits);
+}
+// v > 0.0 (+Inf included)
+__device__ __forceinline__ bool pos_num(double v) { return ubits(v) - 1ull < kInfBits; }
+// v >= 0.0 (-0 included)
+__device__ __forceinline__ bool ge0(double v) {
+  const unsigned long long u = ubits(v);
+  return u <= kInfBits || u == kSignBit;
+}
+// v < +Inf
+__device__ __forceinline__ bool lt_inf(double v) {
+  const unsigned long long u = ubits(v);
+  return (u & ~kSignBit) <= kInfBits && u != kInfBits;
+}
+// v <= 1.0
+__device__ __forceinline__ bool le1(double v) {
+  const unsigned long long u = ubits(v);
+  return (u & ~kSignBit) <= kInfBits && (u >= kSignBit || u <= 0x3FF0000000000000ull);
+}
+// v >= rj for rj > 0
+__device__ __forceinline__ bool ge_pos(double v, double rj) {
+  const unsigned long long u = ubits(v);
+  return u >= ubits(rj) && u <= kInfBits;
+}
+// a > b for a > 0 (b any value but NaN)
+__device__ __forceinline__ bool gt_pos(double a, double b) {
+  return __double_as_longlong(a) > __double_as_longlong(b);
+}
+// v 2^-k for k = 1, 2: the exponent field lowered by k when the result stays
+// normal, else the FP64 product
+template <int k>
+__device__ __forceinline__ double scale_down(double v) {
+  const unsigned long long u = ubits(v);
+  const unsigned f = (unsigned)(u >> 52) & 0x7FFu;
+  if (f > (unsigned)k && f < 0x7FFu) return __longlong_as_double((long long)(u - ((unsigned long long)k << 52)));
+  return v * (k == 1 ? 0.5 : 0.25);
+}
+// v 2^k for k = 1, 2: the exponent field raised by k when v and the result
+// are normal, else the FP64 product
+template <int k>
+__device__ __forceinline__ double scale_up(double v) {
+  const unsigned long long u = ubits(v);
+  const unsigned f = (unsigned)(u >> 52) & 0x7FFu;
+  if (f - 1u < 2046u - (unsigned)k) return __longlong_as_double((long long)(u + ((unsigned long long)k << 52)));
+  return v * (k == 1 ? 2.0 : 4.0);
+}
+// (float)v: the top 24 significand bits rounded to nearest even by the 29
+// bits below them, for doubles whose float is normal (2^-126 <= |v| <
+// 2^126); others by the conversion
+__device__ __forceinline__ float f32_rn(double v) {
+  const unsigned long long u = ubits(v);
+  const unsigned ex = (unsigned)(u >> 52) & 0x7FFu;
+  if (ex - 897u > 252u) return (float)v;  // outside [897, 1149]
+  const unsigned top = ((ex - 896u) << 23) | ((unsigned)(u >> 29) & 0x7FFFFFu);
+  const unsigned rest = (unsigned)u & 0x1FFFFFFFu;
+  const bool up = rest > 0x10000000u || (rest == 0x10000000u && (top & 1u));
+  return __uint_as_float(((unsigned)(u >> 32) & 0x80000000u) | (top + (up ? 1u : 0u)));
+}
+
 // ------------------------------------------------- counter-based RNG
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
 // 32x32->64 bit products and xors, keys bumped by the Weyl constants.
@@ -228,7 +304,7 @@ __device__ __forceinline__ bool disk_angle(Draws<kTaus>& g, uint32_t tag, double
   const double uu = u * u, vv = v * v, q = uu + vv;
   const double iq = 1.0 / q;
   c = (uu - vv) * iq;
-  s = ((2.0 * u) * v) * iq;
+  s = (scale_up<1>(u) * v) * iq;
   return true;
 }
 
@@ -284,73 +360,6 @@ __device__ __forceinline__ double phi_in_shell(const Table64& t, int64_t i, doub
 
 __device__ __forceinline__ double phi_of_r(const Table64& t, double q) {
   return phi_in_shell(t, shell_of(t, q), q);
-}
-
-// ------------------------------------- exact operations on bit patterns
-// The FP64 pipe of this GPU issues two lanes per SM and clock, and most of
-// the timestep's kernels are bound by it.  Operations that need no FP64
-// arithmetic -- comparisons, rounding to float, scaling by 1/2 or 1/4 --
-// run on the integer pipes from the bit patterns; each gives the IEEE-754
-// result of the FP64 operation it replaces (NaN, infinities, zeros and
-// subnormals included, by the bit tests or by falling back to the FP64
-// operation where the shortcut does not hold).
-constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
-constexpr unsigned long long kSignBit = 0x8000000000000000ull;
-
-__device__ __forceinline__ unsigned long long ubits(double v) {
-  return (unsigned long long)__double_as_longlong(v);
-}
-// v < 0.0
-__device__ __forceinline__ bool lt0(double v) {
-  const unsigned long long u = ubits(v);
-  return u > kSignBit && u <= (kSignBit | kInfBits);
-}
-// v > 0.0 (+Inf included)
-__device__ __forceinline__ bool pos_num(double v) { return ubits(v) - 1ull < kInfBits; }
-// v >= 0.0 (-0 included)
-__device__ __forceinline__ bool ge0(double v) {
-  const unsigned long long u = ubits(v);
-  return u <= kInfBits || u == kSignBit;
-}
-// v < +Inf
-__device__ __forceinline__ bool lt_inf(double v) {
-  const unsigned long long u = ubits(v);
-  return (u & ~kSignBit) <= kInfBits && u != kInfBits;
-}
-// v <= 1.0
-__device__ __forceinline__ bool le1(double v) {
-  const unsigned long long u = ubits(v);
-  return (u & ~kSignBit) <= kInfBits && (u >= kSignBit || u <= 0x3FF0000000000000ull);
-}
-// v >= rj for rj > 0
-__device__ __forceinline__ bool ge_pos(double v, double rj) {
-  const unsigned long long u = ubits(v);
-  return u >= ubits(rj) && u <= kInfBits;
-}
-// a > b for a > 0 (b any value but NaN)
-__device__ __forceinline__ bool gt_pos(double a, double b) {
-  return __double_as_longlong(a) > __double_as_longlong(b);
-}
-// v 2^-k for k = 1, 2: the exponent field lowered by k when the result stays
-// normal, else the FP64 product
-template <int k>
-__device__ __forceinline__ double scale_down(double v) {
-  const unsigned long long u = ubits(v);
-  const unsigned f = (unsigned)(u >> 52) & 0x7FFu;
-  if (f > (unsigned)k && f < 0x7FFu) return __longlong_as_double((long long)(u - ((unsigned long long)k << 52)));
-  return v * (k == 1 ? 0.5 : 0.25);
-}
-// (float)v: the top 24 significand bits rounded to nearest even by the 29
-// bits below them, for doubles whose float is normal (2^-126 <= |v| <
-// 2^126); others by the conversion
-__device__ __forceinline__ float f32_rn(double v) {
-  const unsigned long long u = ubits(v);
-  const unsigned ex = (unsigned)(u >> 52) & 0x7FFu;
-  if (ex - 897u > 252u) return (float)v;  // outside [897, 1149]
-  const unsigned top = ((ex - 896u) << 23) | ((unsigned)(u >> 29) & 0x7FFFFFu);
-  const unsigned rest = (unsigned)u & 0x1FFFFFFFu;
-  const bool up = rest > 0x10000000u || (rest == 0x10000000u && (top & 1u));
-  return __uint_as_float(((unsigned)(u >> 32) & 0x80000000u) | (top + (up ? 1u : 0u)));
 }
 
 // ----------------------------------------------------- small utilities

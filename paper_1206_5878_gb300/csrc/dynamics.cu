@@ -128,8 +128,8 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   double s2 = num / (w2 * w);
   if (!le1(s2)) s2 = 1.0;
   // cos(beta) = 1 - 2 sin^2(beta/2), sin(beta) = 2 sin(beta/2) cos(beta/2)
-  const double cosb = 1.0 - 2.0 * s2;
-  const double sinb = 2.0 * sqrt(s2 * (1.0 - s2));
+  const double cosb = 1.0 - scale_up<1>(s2);
+  const double sinb = scale_up<1>(sqrt(s2 * (1.0 - s2)));
   if (!disk_angle(g, kTagPhi, cphi, sphi)) ++fails;
   draws_keep(S, c, g);
   // e1 = (w x xhat)/|w x xhat| = (0, wz, -wy)/|.| (yhat for radial w);

@@ -40,7 +40,7 @@ __device__ __forceinline__ double Qv(const Star& s, double x, double p) {
 
 __device__ __forceinline__ double Q_node64(const Table64& T, const Star& s, int64_t i) {
   double L = s.J * __ldg(T.x + i);
-  return 2.0 * (s.E - __ldg(T.phi + i)) - L * L;
+  return scale_up<1>(s.E - __ldg(T.phi + i)) - L * L;
 }
 
 // root of Q inside shell j (nodes j, j+1; node nb is 1/r = 0, Phi = 0)
@@ -54,10 +54,10 @@ __device__ __forceinline__ double shell_root64(const Table64& T, const Star& s, 
   if (!(xj - xj1 > 0.0)) return rj;
   const double B = (pj1 - pj) / (xj - xj1);
   const double A = pj + B * xj;
-  double D = B * B + 2.0 * (s.J * s.J) * (s.E - A);
+  double D = B * B + scale_up<1>(s.J * s.J) * (s.E - A);
   if (!(D > 0.0)) D = 0.0;
   const double sD = sqrt(D);
-  double root = outer ? (B + sD) / (2.0 * (A - s.E)) : (s.J * s.J) / (B + sD);
+  double root = outer ? (B + sD) / scale_up<1>(A - s.E) : (s.J * s.J) / (B + sD);
   if (!(root >= rj)) root = rj;
   if (has_next && root > rj1) root = rj1;
   return root;
@@ -157,7 +157,7 @@ __device__ __forceinline__ int64_t fix_shell_nodes(const double4_32a* __restrict
 }
 
 __device__ __forceinline__ double central_root64(const Table64& T, const Star& s) {
-  double rmin = s.J / sqrt(2.0 * (s.E - __ldg(T.phi)));
+  double rmin = s.J / sqrt(scale_up<1>(s.E - __ldg(T.phi)));
   if (!(rmin >= 0.0)) rmin = 0.0;
   const double r0 = __ldg(T.r);
   if (rmin > r0) rmin = r0;
@@ -189,7 +189,7 @@ __device__ __forceinline__ double g64(const Table64& T, const Star& st, double c
   const double drds = (3.0 * c1) * (1.0 - s * s);
   ph = phi_of_r(T, rs);
   const double L = st.J / rs;
-  Q = 2.0 * (st.E - ph) - L * L;
+  Q = scale_up<1>(st.E - ph) - L * L;
   if (!(Q > 0.0)) return 0.0;
   return drds / sqrt(Q);
 }
@@ -379,7 +379,7 @@ __device__ __forceinline__ void point64(const double4_32a* __restrict__ nd, int6
   xs = 1.0 / rs;
   ph = i64 < 0 ? a.z : a.z + a.w * (a.y - xs);
   L = st.J * xs;
-  Q = 2.0 * (st.E - ph) - L * L;
+  Q = scale_up<1>(st.E - ph) - L * L;
 }
 
 
@@ -807,7 +807,7 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
     c = seg_find(S.off, S.n_seg, p);
     const int64_t k = p - S.off[c];
     const double vrk = vr[p], vtk = vt[p];
-    const double E = __ldg(phi + p) + 0.5 * (vrk * vrk + vtk * vtk);
+    const double E = __ldg(phi + p) + scale_down<1>(vrk * vrk + vtk * vtk);
     if (k < S.nb[c] && lt0(E)) {
       const double J = r[p] * vtk;
       const double rmin = __ldg(tp_min + p), rmax = __ldg(tp_max + p);
@@ -885,7 +885,7 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
       const double vrk = vr[p], vtk = vt[p];
       Star s;
       s.k = k;
-      s.E = __ldg(phi + p) + 0.5 * (vrk * vrk + vtk * vtk);
+      s.E = __ldg(phi + p) + scale_down<1>(vrk * vrk + vtk * vtk);
       s.J = r[p] * vtk;
       if (lt0(s.E) && ((uint32_t)(res >> 30) & 3u) == kSmpPending) {
         Buckets BK;
@@ -991,7 +991,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
   const Table64 T{r + sb, x + sb, phi + sb, nbc};
   Star s;
   s.k = k;
-  s.E = __ldg(T.phi + k) + 0.5 * (vrk * vrk + vtk * vtk);
+  s.E = __ldg(T.phi + k) + scale_down<1>(vrk * vrk + vtk * vtk);
   s.J = rk * vtk;
   Draws<kTaus> g = draws_of<kTaus>(S, c, idk, *step_p);
   double ph_new = __ldg(T.phi + k);
@@ -1001,7 +1001,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
     code = 1;
     r_new = __longlong_as_double(0x7FF0000000000000ll);
     // energy carried off: the star's energy in the field of the others
-    P.c = __ldg(T.phi + k) + P.m / rk + 0.5 * (vrk * vrk + vtk * vtk);
+    P.c = __ldg(T.phi + k) + P.m / rk + scale_down<1>(vrk * vrk + vtk * vtk);
   } else {
     int64_t jmax, jmin;
     Table32 T32{t32 + sb, nbc};
@@ -1186,9 +1186,9 @@ __global__ void __launch_bounds__(128) k_correction_mixed(Seg S, const int64_t* 
   const int64_t i = fix_shell_nodes(BA.node + sb, nbc, sh[0], ro, nd);
   const double pn = i < 0 ? nd.z : nd.z + nd.w * (nd.y - xo);
   const double a = vr[p], b = vt[p];
-  const double Tk = 0.5 * (a * a + b * b);
+  const double Tk = scale_down<1>(a * a + b * b);
   const double dnew = pn - phi[p];
-  double Tp = Tk + 0.5 * (dnew - cc[p]);
+  double Tp = Tk + scale_down<1>(dnew - cc[p]);
   bool clamp = false;
   if (lt0(Tp)) { Tp = 0.0; clamp = true; }
   if (pos_num(Tk)) {

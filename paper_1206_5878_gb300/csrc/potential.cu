@@ -377,9 +377,9 @@ __global__ void k_correction(Seg S, const int64_t* esc, bool sub, const double* 
   if (active) {
     Table64 T{r + sb, x + sb, phi + sb, nbc};
     double a = vr[p], b = vt[p];
-    double Tk = 0.5 * (a * a + b * b);
+    double Tk = scale_down<1>(a * a + b * b);
     double dnew = phi_of_r(T, r_old[p]) - phi[p];
-    double Tp = Tk + 0.5 * (dnew - cc[p]);
+    double Tp = Tk + scale_down<1>(dnew - cc[p]);
     if (Tp < 0.0) { Tp = 0.0; clamp = 1; }
     if (Tk > 0.0) {
       double f = sqrt(Tp / Tk);
