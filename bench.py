@@ -337,6 +337,46 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ ranks
+class Ranks:
+    """The launch's ranks as the timing sees them: a barrier on both sides
+    of the timed region and the maximum time over ranks.  device: "cuda"
+    with NCCL on a GPU box, "cpu" with gloo (the multi-process tests)."""
+
+    def __init__(self, rank: int, world: int, device: str = "cuda"):
+        self.rank, self.world, self.device = rank, world, device
+
+    def _sync(self):
+        if self.device == "cuda":
+            import torch
+            torch.cuda.synchronize()
+
+    def barrier(self):
+        self._sync()
+        if self.world > 1:
+            import torch
+            torch.distributed.barrier()
+        self._sync()
+
+    def max(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=self.device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+
+def replica_seed(base: int, rank: int) -> int:
+    """One independent cluster per rank (weak scaling): seed base + rank."""
+    return base + rank
+
+
+def whole_job_rate(n_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Star-updates/s of all ranks together over the slowest rank's time."""
+    return n_per_rank * steps * world / (ms_max / 1e3)
+
+
 def run_cmc(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -345,8 +385,8 @@ def run_cmc(args, rank, world, local_rank):
     import paper_1206_5878_gb300 as g
 
     torch.cuda.set_device(local_rank)
-    dist = world > 1
-    seed = args.seed + rank
+    ranks = Ranks(rank, world, "cuda")
+    seed = replica_seed(args.seed, rank)
     n = args.n
     prec = 1 if args.precision == "mixed" else 0
     log("rank %d: building Plummer N=%d seed=%d" % (rank, n, seed))
@@ -356,18 +396,8 @@ def run_cmc(args, rank, world, local_rank):
     c = g.Cluster(dev, [seed], precision=prec, rng=args.rng)
     stream = torch.cuda.current_stream()
 
-    def barrier():
-        torch.cuda.synchronize()
-        if dist:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x: float) -> float:
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    barrier, max_over_ranks = ranks.barrier, ranks.max
+    dist = world > 1
 
     c.step(args.warmup)
     barrier()
@@ -379,7 +409,7 @@ def run_cmc(args, rank, world, local_rank):
         barrier()
     ms = max_over_ranks(ev0.elapsed_time(ev1))
     clocks = clk.summary()
-    value = n * args.steps * world / (ms / 1e3)
+    value = whole_job_rate(n, args.steps, world, ms)
     kernels = c.kernels_per_step() * args.steps
 
     # per-stage device times over the same number of steps (kernels launched
