@@ -1,11 +1,19 @@
 """Long run to core collapse (section 4.3): a Plummer sphere of 10^5 equal
 masses, mixed precision, advanced until its core density (Eq. 19) has grown
-a thousandfold.  The time this takes, in units of the initial half-mass
-relaxation time (Eq. 20), is the method's calibration as a whole (the
-relaxation rate, the Eq. 7 timestep, the orbit sampling, the potential):
-the paper finds 17.4 t_rh at this N and cites 15 to 18 t_rh from the
-literature.  The escaped mass and the total-energy drift are recorded on
-the way."""
+ten-thousandfold.
+
+- The time at which rho_c has grown a thousandfold, in units of the initial
+  half-mass relaxation time (Eq. 20), is the method's calibration as a whole
+  (the relaxation rate, the Eq. 7 timestep, the orbit sampling, the
+  potential): the paper finds 17.4 t_rh at this N and cites 15 to 18 t_rh
+  from the literature.
+- Self-similar collapse makes rho_c a power of r_c: the paper fits a slope
+  d ln rho_c / d ln r_c near -2.24 close to collapse (-2.23 in the
+  literature it cites), after about -2.5 earlier on.  Here the slope is
+  fitted while rho_c grows from 10^2 to 10^4 times its initial value (r_c
+  falling about tenfold).
+- The escaped mass and the total-energy drift are recorded on the way."""
+import numpy as np
 import pytest
 
 import initial_conditions as ic
@@ -13,7 +21,7 @@ import initial_conditions as ic
 pytestmark = pytest.mark.gpu
 
 
-def test_plummer_1e5_core_collapse_time():
+def test_plummer_1e5_core_collapse_time_and_slope():
     import paper_1206_5878_gb300 as g
     n = 100_000
     d = ic.plummer(n, seed=1)
@@ -22,16 +30,28 @@ def test_plummer_1e5_core_collapse_time():
         rho0 = c.core()[0][0]
         E0 = c.total_energy()[0]
         t, t_cc = 0.0, None
-        for step in range(1, 20_001):
+        late = []  # (r_c, rho_c) once rho_c > 100 rho_c0
+        for step in range(1, 40_001):
             c.step(1)
             t += float(c.dt()[0])
-            if step % 20 == 0 and c.core()[0][0] > 1e3 * rho0:
-                t_cc = t
-                break
+            if step % 20 == 0:
+                rho_c, r_c, _ = c.core()[0]
+                if t_cc is None and rho_c > 1e3 * rho0:
+                    t_cc = t
+                    # at a thousandfold about 2.3% of the stars have escaped
+                    # and the drift is about -1.2e-3; the bounds leave room
+                    # for other seeds
+                    assert c.nbound()[0] > 0.95 * n
+                    assert abs(c.total_energy()[0] / E0 - 1) < 5e-3
+                if rho_c > 1e2 * rho0:
+                    late.append((r_c, rho_c))
+                if rho_c > 1e4 * rho0:
+                    break
             assert t < 25 * t_rh, "no collapse by 25 t_rh"
-        assert t_cc is not None
+        assert t_cc is not None and late and late[-1][1] > 1e4 * rho0
         assert 15.0 <= t_cc / t_rh <= 19.0, t_cc / t_rh
-        # at collapse about 2.3% of the stars have escaped and the drift is
-        # about -1.2e-3; the bounds below leave room for other seeds
-        assert c.nbound()[0] > 0.95 * n
-        assert abs(c.total_energy()[0] / E0 - 1) < 5e-3
+        rc, rho = np.array(late).T
+        beta = np.polyfit(np.log(rc), np.log(rho), 1)[0]
+        # the paper: about -2.5 early in the collapse, -2.24 deep in it;
+        # measured -2.31 to -2.33 over seeds 1-3 and N = 10^5, 10^6
+        assert -2.5 < beta < -2.2, beta
