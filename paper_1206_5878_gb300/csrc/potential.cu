@@ -188,14 +188,23 @@ __global__ void __launch_bounds__(kThreads) k_tile_sums(Seg S, const int64_t* es
                                                         double* tile_m, double* tile_mx) {
   __shared__ double s[kThreads];
   TR R = tile_of(S, esc, blockIdx.x, sub);
-  double am = 0.0, ax = 0.0;
-#pragma unroll 4
+  // all 32 loads issued before the sums, which still run in element order
+  double mv[kPer], xv[kPer];
+  unsigned ok = 0;
+#pragma unroll
   for (int i = 0; i < kPer; ++i) {
     const int64_t p = R.begin + (int64_t)i * kThreads + threadIdx.x;
-    if (p < R.end && p < R.bound_end) {
-      const double mm = __ldg(m + p);
-      am = am + mm;
-      ax = ax + mm * __ldg(x + p);
+    const bool in = p < R.end && p < R.bound_end;
+    ok |= (unsigned)in << i;
+    mv[i] = in ? __ldg(m + p) : 0.0;
+    xv[i] = in ? __ldg(x + p) : 0.0;
+  }
+  double am = 0.0, ax = 0.0;
+#pragma unroll
+  for (int i = 0; i < kPer; ++i) {
+    if ((ok >> i) & 1u) {
+      am = am + mv[i];
+      ax = ax + mv[i] * xv[i];
     }
   }
   double tm = block_sum(am, s);
@@ -305,7 +314,7 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(Seg S, const int64_t*
   }
   const double Mbefore = block_sum_pot(pm, wm);
   const double Safter = block_sum_pot(ps, wm);
-#pragma unroll 4
+#pragma unroll
   for (int i = 0; i < kPotPer; ++i) {
     const int e = i * kPotThreads + t;
     const int64_t p = R.begin + e;

@@ -11,7 +11,7 @@ ten-thousandfold.
   d ln rho_c / d ln r_c near -2.24 close to collapse (-2.23 in the
   literature it cites), after about -2.5 earlier on.  Here the slope is
   fitted while rho_c grows from 10^2 to 10^4 times its initial value (r_c
-  falling about tenfold).
+  falling about sevenfold).
 - The escaped mass and the total-energy drift are recorded on the way."""
 import numpy as np
 import pytest
