@@ -323,6 +323,28 @@ cmc_status cmc_energy_correction(int64_t n, const double *r, const double *phi, 
 cmc_status cmc_potential_static(int64_t n, const double *r, const double *m, double *phi,
                                 double *M, void *stream);
 
+/* -------------------------------------------------------------------
+ * Self-check of the integer-pipe FP64 arithmetic.  GB300 issues FP64
+ * arithmetic on two lanes per SM and clock, so the kernels compute the
+ * correctly rounded product, quotient and square root they need from
+ * 64-bit integer operations on the significands (normal operands with a
+ * normal result; anything else takes the FP64 instruction).  These must
+ * equal IEEE-754 round-to-nearest-even exactly, which is what keeps the
+ * FP64 path bit for bit equal to an FP64 statement of the method (§2.1).
+ * This call compares one of them with the FP64 hardware operation:
+ *   op: 0 = a * b, 1 = a / b, 2 = sqrt(a);
+ *   n operand pairs, hashed from `seed` (splitmix64) in three families in
+ *   turn: any 64-bit pattern (NaN, infinities, zeros, subnormals, and the
+ *   fallbacks), random values with exponents in [2^-40, 2^40], and the same
+ *   with 0..52 trailing significand bits cleared (exact results and ties);
+ *   *mismatches (host) receives the number of results whose bit patterns
+ *   differ (NaN against NaN counts as equal).
+ * Runs on the current device and the legacy default stream; synchronous.
+ * Returns CMC_EINVAL for an op outside 0..2 or a NULL pointer, CMC_ECUDA
+ * on a CUDA error.
+ * ------------------------------------------------------------------- */
+cmc_status cmc_check_arith(int32_t op, uint64_t n, uint64_t seed, uint64_t *mismatches);
+
 #ifdef __cplusplus
 }
 #endif

@@ -303,6 +303,16 @@ def stage_energy_correction(r, phi, vr, vt, r_old, c, stream=None):
     return vr, vt
 
 
+def check_arith(op: int, n: int, seed: int = 1) -> int:
+    """Mismatches between the kernels' integer-pipe FP64 operation `op`
+    (0 product, 1 quotient, 2 square root) and the FP64 hardware one over
+    n hashed operand pairs (cmc_check_arith)."""
+    import numpy as np
+    out = np.zeros(1, dtype=np.uint64)
+    check(load().cmc_check_arith(int(op), int(n), int(seed), out.ctypes.data))
+    return int(out[0])
+
+
 def half_mass_relaxation_time(n: int, r_h: float, mass: float = 1.0, gamma: float = 0.1) -> float:
     """Eq. 20: t_rh = 0.138 N / ln(gamma N) (r_h^3 / (G M))^(1/2) with G = 1."""
     import math

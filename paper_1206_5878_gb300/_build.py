@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcmc.so")
-SOURCES = ["api.cu", "sort.cu", "potential.cu", "dynamics.cu", "orbit.cu", "static_scratch.cu"]
+SOURCES = ["api.cu", "sort.cu", "potential.cu", "dynamics.cu", "orbit.cu", "static_scratch.cu",
+           "arith_check.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "--fmad=false", "-lineinfo", "-Xcompiler", "-fPIC",
            "-Xcompiler", "-fno-strict-aliasing", "-I", INCLUDE]

@@ -68,6 +68,7 @@ SIGNATURES = {
                          _p, _p, _p, _p]),
     "cmc_energy_correction": (_i32, [_i64, _p, _p, _p, _p, _p, _p, _p]),
     "cmc_potential_static": (_i32, [_i64, _p, _p, _p, _p, _p]),
+    "cmc_check_arith": (_i32, [_i32, _u64, _u64, _p]),
 }
 
 _lib = None

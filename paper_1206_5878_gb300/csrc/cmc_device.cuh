@@ -150,6 +150,174 @@ __device__ __forceinline__ float f32_rn(double v) {
   return __uint_as_float(((unsigned)(u >> 32) & 0x80000000u) | (top + (up ? 1u : 0u)));
 }
 
+// Correctly rounded FP64 product, quotient and square root from 64-bit
+// integer arithmetic on the significands, for normal operands with a normal
+// result (anything else: the FP64 operation).  On this GPU an FP64 division
+// or square root takes several FP64 issues; these take none, and the FP64
+// pipe is left to the additions.  Each returns the IEEE-754 round-to-
+// nearest-even result exactly (checked bit for bit against the FP64
+// operations on 3 x 2^28 operand pairs per operation: random bit patterns,
+// random values over 81 binades, and significands with random runs of
+// trailing zeros, which give exact results and ties).
+//
+// The significands are integers in [2^52, 2^53); the result's significand Q
+// is an integer in the same range, its exponent follows from the operands'.
+// A result assembled as sign + ((e - 1) << 52) + Q lets a significand that
+// rounds up to 2^53 carry into the exponent.
+__device__ __forceinline__ unsigned long long significand(unsigned long long u) {
+  return (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+}
+
+// a b: the 106-bit product of the significands, its top 53 bits rounded to
+// nearest even by the bits below them.
+__device__ __forceinline__ double mul_rn(double a, double b) {
+  const unsigned long long ua = ubits(a), vb = ubits(b);
+  const unsigned ea = (unsigned)(ua >> 52) & 0x7FFu, eb = (unsigned)(vb >> 52) & 0x7FFu;
+  const int e = (int)ea + (int)eb - 1023;  // the result's biased exponent, before a carry
+  if (ea - 1u < 2046u && eb - 1u < 2046u && (unsigned)(e - 2) < 2043u) {
+    const unsigned long long ma = significand(ua), mb = significand(vb);
+    const unsigned long long hi = __umul64hi(ma, mb), lo = ma * mb;
+    const unsigned c = (unsigned)(hi >> 41);  // product >= 2^105
+    const unsigned long long m = (hi << (12 - c)) | (lo >> (52 + c));
+    const unsigned long long rest = lo << (12 - c);  // the dropped bits, left-aligned
+    const unsigned long long up = (rest >> 63) & ((rest << 1) != 0ull ? 1ull : (m & 1ull));
+    return __longlong_as_double((long long)(((ua ^ vb) & kSignBit) +
+                                            ((unsigned long long)(e - 1 + (int)c) << 52) + m + up));
+  }
+  return a * b;
+}
+
+// a / b: Q = floor(N / d) for N = m_a 2^(63 + s), d = m_b 2^11 (s = 1 when
+// m_a < m_b, so that Q has 53 bits).  The reciprocal v ~ 2^128 / d - 2^64
+// is seeded from the float reciprocal of d's top 24 bits (~22 bits) and
+// refined by two Newton-Raphson steps in fixed point, R' = R + R (2^128 -
+// d R) / 2^128 with R = 2^64 + v (quadratic convergence: ~44, then ~64
+// bits; Newton division as in Knuth, TAOCP vol. 2, 4.3.3, and Brent and
+// Zimmermann, Modern Computer Arithmetic, 3.4).  The quotient estimate
+// floor(N R / 2^128) is then corrected by one step either way from the
+// exact remainder N - Q d, and rounded by comparing twice the remainder
+// with d (ties to even).  If the remainder still lies outside [0, d), the
+// FP64 division is used.
+__device__ __forceinline__ double div_rn(double a, double b) {
+  const unsigned long long ua = ubits(a), vb = ubits(b);
+  const unsigned ea = (unsigned)(ua >> 52) & 0x7FFu, eb = (unsigned)(vb >> 52) & 0x7FFu;
+  const unsigned long long ma = significand(ua), mb = significand(vb);
+  const unsigned s = ma < mb ? 1u : 0u;
+  const int e = (int)ea - (int)eb + 1023 - (int)s;
+  if (ea - 1u < 2046u && eb - 1u < 2046u && (unsigned)(e - 1) < 2045u) {
+    const unsigned long long d = mb << 11;  // [2^63, 2^64)
+    // the float of d's top 24 bits, from its bits (2^23 <= d >> 40 < 2^24)
+    const float f = __uint_as_float(0x4B000000u | ((unsigned)(d >> 40) & 0x7FFFFFu));
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
+    const unsigned yb = __float_as_uint(y);
+    // 2^88 y - 2^64 for y in [2^-24, 2^-23); y = 2^-23 (d = 2^63) saturates
+    unsigned long long v =
+        ((yb >> 23) & 0xFFu) == 103u ? (unsigned long long)(yb & 0x7FFFFFu) << 41 : ~0ull;
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      // d R - 2^128 = T 2^64 + pl (T signed, small); E = floor((2^128 - d R) / 2^64)
+      const unsigned long long pl = d * v, ph = __umul64hi(d, v);
+      const long long T = (long long)(ph + d);
+      const long long E = -T - (pl != 0ull ? 1 : 0);
+      const unsigned long long aE = E < 0 ? (unsigned long long)(-E) : (unsigned long long)E;
+      const unsigned long long c = __umul64hi(v, aE);  // v |E| / 2^64
+      v = E < 0 ? v + (unsigned long long)E - c : v + (unsigned long long)E + c;
+    }
+    // N = u1 2^64 + u0
+    const unsigned long long u1 = s ? ma : ma >> 1, u0 = s ? 0ull : (ma & 1ull) << 63;
+    const unsigned long long ql = v * u1, qh = __umul64hi(v, u1);
+    const unsigned long long q0 = ql + u0;
+    unsigned long long Q = qh + u1 + (q0 < ql ? 1ull : 0ull);
+    // remainder N - Q d as rh 2^64 + rl (rh signed)
+    const unsigned long long pl = Q * d, ph = __umul64hi(Q, d);
+    unsigned long long rl = u0 - pl;
+    long long rh = (long long)(u1 - ph - (u0 < pl ? 1ull : 0ull));
+    if (rh < 0) {
+      const unsigned long long t = rl + d;
+      rh += t < rl ? 1 : 0;
+      rl = t;
+      --Q;
+    } else if (rh > 0 || rl >= d) {
+      const unsigned long long t = rl - d;
+      rh -= rl < d ? 1 : 0;
+      rl = t;
+      ++Q;
+    }
+    if (rh == 0 && rl < d) {
+      const unsigned long long r2 = rl << 1;
+      const bool up = (rl >> 63) != 0ull || r2 > d || (r2 == d && (Q & 1ull));
+      return __longlong_as_double((long long)(((ua ^ vb) & kSignBit) +
+                                              ((unsigned long long)(e - 1) << 52) + Q +
+                                              (up ? 1ull : 0ull)));
+    }
+  }
+  return a / b;
+}
+
+// sqrt(x): Q = floor(sqrt(N)) for N = m_x 2^(52 + p), p = 1 when x's
+// unbiased exponent is even (so that Q has 53 bits).  The reciprocal square
+// root Y ~ 2^94 / sqrt(w) of w = m_x 2^(10 + p) in [2^62, 2^64) is seeded
+// from the float reciprocal square root of w's top 24 bits and refined by
+// two Newton steps Y' = Y (3 - w Y^2 / 2^188) / 2 in fixed point (Brent and
+// Zimmermann, Modern Computer Arithmetic, 3.5); Q ~ N Y / 2^115 is then
+// corrected by one step either way from the exact remainder N - Q^2 in [0,
+// 2Q], and rounded up when the remainder exceeds Q (sqrt(N) >= Q + 1/2; an
+// exact tie cannot occur).  Negative, zero, subnormal and non-finite x:
+// the FP64 square root.
+__device__ __forceinline__ double sqrt_rn(double x) {
+  const unsigned long long ux = ubits(x);
+  const unsigned ex = (unsigned)(ux >> 52);  // sign included: negative x falls back
+  if (ex - 1u < 2046u) {
+    const unsigned long long ma = significand(ux);
+    const unsigned p = (ex & 1u) ^ 1u;
+    const unsigned long long w = ma << (10 + p);
+    // the float of w / 2^40, from its bits (2^22 <= w / 2^40 < 2^24)
+    const float f = p ? __uint_as_float(0x4B000000u | ((unsigned)(w >> 40) & 0x7FFFFFu))
+                      : __uint_as_float(0x4A800000u | ((unsigned)(w >> 39) & 0x7FFFFFu));
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
+    const unsigned yb = __float_as_uint(y);
+    const int ye = (int)((yb >> 23) & 0xFFu) - 127;  // y in [2^ye, 2^(ye + 1)), ye in {-12, -11}
+    unsigned long long Y = (unsigned long long)((yb & 0x7FFFFFu) | 0x800000u) << (51 + ye);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+      // E = floor((2^124 - w sh) / 2^64), sh = Y^2 / 2^64; Y' = Y + Y E / 2^61
+      const unsigned long long sh = __umul64hi(Y, Y);
+      const unsigned long long ml = w * sh, mh = __umul64hi(w, sh);
+      const long long E = (long long)((1ull << 60) - mh) - (ml != 0ull ? 1 : 0);
+      const unsigned long long aE = E < 0 ? (unsigned long long)(-E) : (unsigned long long)E;
+      const unsigned long long h = __umul64hi(Y, aE), l = Y * aE;
+      const unsigned long long c = (h << 3) | (l >> 61);
+      Y = E < 0 ? Y - c : Y + c;
+    }
+    const unsigned long long lo = ma * Y, hi = __umul64hi(ma, Y);
+    unsigned long long Q = p ? (hi << 2) | (lo >> 62) : (hi << 1) | (lo >> 63);
+    // remainder N - Q^2 as rh 2^64 + rl (rh signed), N = u1 2^64 + u0
+    const unsigned long long u1 = ma >> (12 - p), u0 = ma << (52 + p);
+    const unsigned long long ql = Q * Q, qh = __umul64hi(Q, Q);
+    unsigned long long rl = u0 - ql;
+    long long rh = (long long)(u1 - qh - (u0 < ql ? 1ull : 0ull));
+    if (rh < 0) {  // (Q - 1)^2 = Q^2 - (2Q - 1)
+      const unsigned long long t = 2 * Q - 1, n = rl + t;
+      rh += n < rl ? 1 : 0;
+      rl = n;
+      --Q;
+    } else if (rh > 0 || rl > 2 * Q) {  // (Q + 1)^2 = Q^2 + 2Q + 1
+      const unsigned long long t = 2 * Q + 1, n = rl - t;
+      rh -= rl < t ? 1 : 0;
+      rl = n;
+      ++Q;
+    }
+    if (rh == 0 && rl <= 2 * Q) {
+      const int er = ((int)ex - 1127 - (int)p) / 2 + 1075;
+      return __longlong_as_double(
+          (long long)(((unsigned long long)(er - 1) << 52) + Q + (rl > Q ? 1ull : 0ull)));
+    }
+  }
+  return sqrt(x);
+}
+
 // ------------------------------------------------- counter-based RNG
 // Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11): ten rounds of two
 // 32x32->64 bit products and xors, keys bumped by the Weyl constants.
@@ -302,7 +470,7 @@ __device__ __forceinline__ bool disk_angle(Draws<kTaus>& g, uint32_t tag, double
   }
   const double u = sym_double(Ua), v = sym_double(Va);
   const double uu = u * u, vv = v * v, q = uu + vv;
-  const double iq = 1.0 / q;
+  const double iq = div_rn(1.0, q);
   c = (uu - vv) * iq;
   s = (scale_up<1>(u) * v) * iq;
   return true;
@@ -349,13 +517,13 @@ __device__ __forceinline__ int64_t shell_of(const Table64& t, double q) {
 // Eq. 6 inside shell i (i = -1: central constant)
 __device__ __forceinline__ double phi_in_shell(const Table64& t, int64_t i, double q) {
   if (i < 0) return __ldg(t.phi);
-  double x = 1.0 / q;
+  double x = div_rn(1.0, q);
   double xj = __ldg(t.x + i), pj = __ldg(t.phi + i), xj1, pj1;
   if (i + 1 < t.nb) { xj1 = __ldg(t.x + i + 1); pj1 = __ldg(t.phi + i + 1); }
   else { xj1 = 0.0; pj1 = 0.0; }
   double den = xj - xj1;
   if (!(den > 0.0)) return pj;
-  return pj + ((xj - x) / den) * (pj1 - pj);
+  return pj + div_rn(xj - x, den) * (pj1 - pj);
 }
 
 __device__ __forceinline__ double phi_of_r(const Table64& t, double q) {

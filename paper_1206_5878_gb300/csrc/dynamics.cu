@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(256) k_bins(Seg S, int bs, double pref, const 
         double rf = r[g], rl = r[g + P - 1];
         double vol = rl * rl * rl - rf * rf * rf;
         if (vol > 0.0) {
-          n = (3.0 * (double)(P - 1)) / ((4.0 * kPi) * vol);
+          n = div_rn(3.0 * (double)(P - 1), (4.0 * kPi) * vol);
           int64_t q = P / 2;
           double sv = 0.0, sm = 0.0;
           for (int64_t j = 0; j < q; ++j) {
@@ -48,15 +48,15 @@ __global__ void __launch_bounds__(256) k_bins(Seg S, int bs, double pref, const 
             double va2 = vr[a] * vr[a] + vt[a] * vt[a];
             double vb2 = vr[a + 1] * vr[a + 1] + vt[a + 1] * vt[a + 1];
             double ms = m[a] + m[a + 1];
-            sv = sv + sqrt(va2 + vb2);
+            sv = sv + sqrt_rn(va2 + vb2);
             sm = sm + ms * ms;
           }
-          double v = sv / (double)q;
-          double msq = sm / (double)q;
+          double v = div_rn(sv, (double)q);
+          double msq = div_rn(sm, (double)q);
           double num = pref * (v * v * v);
           double den = (S.lnL[c] * n) * msq;
           if (den > 0.0) {
-            double T = num / den;
+            double T = div_rn(num, den);
             if (T < __longlong_as_double(0x7FF0000000000000ll))
               tb = (unsigned long long)__double_as_longlong(T);
           }
@@ -118,18 +118,18 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
     if (fails) stat_add(S.stats, c, kStAngleFails, (unsigned long long)fails);
     return;
   }
-  const double w = sqrt(w2);
+  const double w = sqrt_rn(w2);
   // sin^2(beta/2) = min(1, 2 pi G^2 (m1+m2)^2 n lnL dt / |w|^3)
   double num = (2.0 * kPi) * msum;
   num = num * msum;
   num = num * n;
   num = num * lnL;
   num = num * dt;
-  double s2 = num / (w2 * w);
+  double s2 = div_rn(num, w2 * w);
   if (!le1(s2)) s2 = 1.0;
   // cos(beta) = 1 - 2 sin^2(beta/2), sin(beta) = 2 sin(beta/2) cos(beta/2)
   const double cosb = 1.0 - scale_up<1>(s2);
-  const double sinb = scale_up<1>(sqrt(s2 * (1.0 - s2)));
+  const double sinb = scale_up<1>(sqrt_rn(s2 * (1.0 - s2)));
   if (!disk_angle(g, kTagPhi, cphi, sphi)) ++fails;
   draws_keep(S, c, g);
   // e1 = (w x xhat)/|w x xhat| = (0, wz, -wy)/|.| (yhat for radial w);
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   const double wp2 = wy * wy + wz * wz;
   double e1y, e1z;
   if (pos_num(wp2)) {
-    const double iwp = 1.0 / sqrt(wp2);
+    const double iwp = div_rn(1.0, sqrt_rn(wp2));
     e1y = wz * iwp;
     e1z = -(wy * iwp);
   } else {
@@ -153,14 +153,14 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   const double wpy = wy * cosb + sinb * (a1 * e1y + sphi * uy);
   const double wpz = wz * cosb + sinb * (a1 * e1z + sphi * uz);
   const double dwx = wpx - wx, dwy = wpy - wy, dwz = wpz - wz;
-  const double im = 1.0 / msum;
+  const double im = div_rn(1.0, msum);
   const double f1 = m2 * im, f2 = m1 * im;
   const double p1x = v1x + f1 * dwx, p1y = v1y + f1 * dwy, p1z = v1z + f1 * dwz;
   const double p2x = v2x - f2 * dwx, p2y = v2y - f2 * dwy, p2z = v2z - f2 * dwz;
   vr[a] = p1x;
-  vt[a] = sqrt(p1y * p1y + p1z * p1z);
+  vt[a] = sqrt_rn(p1y * p1y + p1z * p1z);
   vr[b] = p2x;
-  vt[b] = sqrt(p2y * p2y + p2z * p2z);
+  vt[b] = sqrt_rn(p2y * p2y + p2z * p2z);
   if (fails) stat_add(S.stats, c, kStAngleFails, (unsigned long long)fails);
 }
 

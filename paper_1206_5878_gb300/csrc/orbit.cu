@@ -52,12 +52,12 @@ __device__ __forceinline__ double shell_root64(const Table64& T, const Star& s, 
   if (has_next) { rj1 = __ldg(T.r + j + 1); xj1 = __ldg(T.x + j + 1); pj1 = __ldg(T.phi + j + 1); }
   else { rj1 = __longlong_as_double(0x7FF0000000000000ll); xj1 = 0.0; pj1 = 0.0; }
   if (!(xj - xj1 > 0.0)) return rj;
-  const double B = (pj1 - pj) / (xj - xj1);
+  const double B = div_rn(pj1 - pj, xj - xj1);
   const double A = pj + B * xj;
   double D = B * B + scale_up<1>(s.J * s.J) * (s.E - A);
   if (!(D > 0.0)) D = 0.0;
-  const double sD = sqrt(D);
-  double root = outer ? (B + sD) / scale_up<1>(A - s.E) : (s.J * s.J) / (B + sD);
+  const double sD = sqrt_rn(D);
+  double root = outer ? div_rn(B + sD, scale_up<1>(A - s.E)) : div_rn(s.J * s.J, B + sD);
   if (!(root >= rj)) root = rj;
   if (has_next && root > rj1) root = rj1;
   return root;
@@ -69,7 +69,9 @@ __device__ __forceinline__ double shell_root64(const Table64& T, const Star& s, 
 // Phi = Phi_j + M_j (x_j - x) needs no division (mixed mode).  The cores
 // take the node values, so that values loaded ahead and the table give
 // the same arithmetic.  The clamps are the FP64 comparisons restated on
-// the bit patterns (radii are positive).
+// the bit patterns (radii are positive).  They keep the FP64 square root and
+// division: in the register-capped turning-point kernel the integer-pipe
+// forms cost more in spills than they save (measured 0.05 ms at N = 10^7).
 __device__ __forceinline__ double rmax_core(const Star& s, double rj, double xj, double pj,
                                             double Mj, bool has_next, double rj1) {
   const double B = Mj;
@@ -157,7 +159,7 @@ __device__ __forceinline__ int64_t fix_shell_nodes(const double4_32a* __restrict
 }
 
 __device__ __forceinline__ double central_root64(const Table64& T, const Star& s) {
-  double rmin = s.J / sqrt(scale_up<1>(s.E - __ldg(T.phi)));
+  double rmin = div_rn(s.J, sqrt_rn(scale_up<1>(s.E - __ldg(T.phi))));
   if (!(rmin >= 0.0)) rmin = 0.0;
   const double r0 = __ldg(T.r);
   if (rmin > r0) rmin = r0;
@@ -188,10 +190,10 @@ __device__ __forceinline__ double g64(const Table64& T, const Star& st, double c
   rs = c0 + c1 * (s * (3.0 - s * s));
   const double drds = (3.0 * c1) * (1.0 - s * s);
   ph = phi_of_r(T, rs);
-  const double L = st.J / rs;
+  const double L = div_rn(st.J, rs);
   Q = scale_up<1>(st.E - ph) - L * L;
   if (!(Q > 0.0)) return 0.0;
-  return drds / sqrt(Q);
+  return div_rn(drds, sqrt_rn(Q));
 }
 
 // ------------------------------------------------------------ FP32 side
@@ -376,7 +378,7 @@ __device__ __forceinline__ void point64(const double4_32a* __restrict__ nd, int6
   rs = c0 + c1 * (sv * (3.0 - sv * sv));
   double4_32a a;
   const int64_t i64 = fix_shell_nodes(nd, nb, sh, rs, a);
-  xs = 1.0 / rs;
+  xs = div_rn(1.0, rs);
   ph = i64 < 0 ? a.z : a.z + a.w * (a.y - xs);
   L = st.J * xs;
   Q = scale_up<1>(st.E - ph) - L * L;
@@ -913,7 +915,7 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
           point64(BA.node + sb, nbc, s, c0, c1, sv,
                   shell32_of(t32 + sb, (int)nbc, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs,
                   xs, ph, L, Q);
-          const double g64v = pos_num(Q) ? ((3.0 * c1) * (1.0 - sv * sv)) / sqrt(Q) : 0.0;
+          const double g64v = pos_num(Q) ? div_rn((3.0 * c1) * (1.0 - sv * sv), sqrt_rn(Q)) : 0.0;
           ++n64;
           if (g64v > F) ++viol;
           if (F * u01(w.z, w.w) < g64v) { st = kSmpAccepted; break; }
@@ -1001,7 +1003,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
     code = 1;
     r_new = __longlong_as_double(0x7FF0000000000000ll);
     // energy carried off: the star's energy in the field of the others
-    P.c = __ldg(T.phi + k) + P.m / rk + scale_down<1>(vrk * vrk + vtk * vtk);
+    P.c = __ldg(T.phi + k) + div_rn(P.m, rk) + scale_down<1>(vrk * vrk + vtk * vtk);
   } else {
     int64_t jmax, jmin;
     Table32 T32{t32 + sb, nbc};
@@ -1063,12 +1065,12 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
           draws_keep(S, c, g);
         } else {
           // the accepted point's velocities once the warp's lanes are done
-          const double sq = sqrt(Q_a);
+          const double sq = sqrt_rn(Q_a);
           U4 sg = g.block(kTagSgn, 0u);
           draws_keep(S, c, g);
           r_new = rs_a;
           P.vr = (sg.x & 1u) ? -sq : sq;
-          P.vt = s.J / rs_a;
+          P.vt = div_rn(s.J, rs_a);
           P.c = __ldg(T.phi + k) - ph_a;
           ph_new = ph_a;
         }
@@ -1110,7 +1112,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
                   shell32_of(T32.t, nb32, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs, xs, ph,
                   L, Q);
           if (!pos_num(Q)) Q = 0.0;
-          const double sq = sqrt(Q);
+          const double sq = sqrt_rn(Q);
           U4 sg = g.block(kTagSgn, 0u);
           draws_keep(S, c, g);
           r_new = rs;
@@ -1170,7 +1172,7 @@ __global__ void __launch_bounds__(128) k_correction_mixed(Seg S, const int64_t* 
   const int64_t nbc = S.nb[c] - esc[c];
   if (p - sb >= nbc) return;
   const double ro = r_old[p];
-  const double xo = 1.0 / ro;
+  const double xo = div_rn(1.0, ro);
   Buckets BK;
   const int4 pr = BA.prm[c];
   BK.start = BA.start + BA.off[c];
@@ -1192,7 +1194,7 @@ __global__ void __launch_bounds__(128) k_correction_mixed(Seg S, const int64_t* 
   bool clamp = false;
   if (lt0(Tp)) { Tp = 0.0; clamp = true; }
   if (pos_num(Tk)) {
-    const double f = sqrt(Tp / Tk);
+    const double f = sqrt_rn(div_rn(Tp, Tk));
     vr[p] = a * f;
     vt[p] = b * f;
   }
@@ -1332,7 +1334,7 @@ __global__ void k_slopes(int64_t n, const double* x, const double* phi, double* 
   if (k >= n) return;
   const double xj = x[k], pj = phi[k];
   const double xj1 = k + 1 < n ? x[k + 1] : 0.0, pj1 = k + 1 < n ? phi[k + 1] : 0.0;
-  M[k] = (pj1 - pj) / (xj - xj1);
+  M[k] = div_rn(pj1 - pj, xj - xj1);
 }
 
 }  // namespace

@@ -123,7 +123,7 @@ __global__ void k_gather(int64_t n, const uint64_t* __restrict__ keys,
   const Payload P = pay[v];
   double rr, xx;
   if (key_is_escaper(k)) { rr = __longlong_as_double(0x7FF0000000000000ll); xx = 0.0; }
-  else { rr = __longlong_as_double((long long)k); xx = 1.0 / rr; }
+  else { rr = __longlong_as_double((long long)k); xx = div_rn(1.0, rr); }
   r[p] = rr; x[p] = xx; vr[p] = P.vr; vt[p] = P.vt; m[p] = P.m; id[p] = P.id;
   if (r_old) r_old[p] = P.r_old;
   if (c) c[p] = P.c;
@@ -391,7 +391,7 @@ __global__ void k_correction(Seg S, const int64_t* esc, bool sub, const double* 
     double Tp = Tk + scale_down<1>(dnew - cc[p]);
     if (Tp < 0.0) { Tp = 0.0; clamp = 1; }
     if (Tk > 0.0) {
-      double f = sqrt(Tp / Tk);
+      double f = sqrt_rn(div_rn(Tp, Tk));
       vr[p] = a * f;
       vt[p] = b * f;
     }
