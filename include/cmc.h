@@ -325,10 +325,10 @@ cmc_status cmc_potential_static(int64_t n, const double *r, const double *m, dou
 
 /* -------------------------------------------------------------------
  * Self-check of the integer-pipe FP64 arithmetic.  GB300 issues FP64
- * arithmetic on two lanes per SM and clock, so the kernels compute the
- * correctly rounded product, quotient and square root they need from
- * 64-bit integer operations on the significands (normal operands with a
- * normal result; anything else takes the FP64 instruction).  These must
+ * arithmetic on two lanes per SM and clock, so the kernels compute their
+ * correctly rounded quotients, square roots and some products from 64-bit
+ * integer operations on the significands (normal operands with a normal
+ * result; anything else takes the FP64 instruction).  These must
  * equal IEEE-754 round-to-nearest-even exactly, which is what keeps the
  * FP64 path bit for bit equal to an FP64 statement of the method (§2.1).
  * This call compares one of them with the FP64 hardware operation:

@@ -154,9 +154,12 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   const double wpz = wz * cosb + sinb * (a1 * e1z + sphi * uz);
   const double dwx = wpx - wx, dwy = wpy - wy, dwz = wpz - wz;
   const double im = div_rn(1.0, msum);
-  const double f1 = m2 * im, f2 = m1 * im;
-  const double p1x = v1x + f1 * dwx, p1y = v1y + f1 * dwy, p1z = v1z + f1 * dwz;
-  const double p2x = v2x - f2 * dwx, p2y = v2y - f2 * dwy, p2z = v2z - f2 * dwz;
+  // these eight products on the integer pipes balance the FP64 pipe's load
+  // against the integer pipes' (measured: all of the kernel's products there
+  // made it a third slower, none of them 2% slower)
+  const double f1 = mul_rn(m2, im), f2 = mul_rn(m1, im);
+  const double p1x = v1x + mul_rn(f1, dwx), p1y = v1y + mul_rn(f1, dwy), p1z = v1z + mul_rn(f1, dwz);
+  const double p2x = v2x - mul_rn(f2, dwx), p2y = v2y - mul_rn(f2, dwy), p2z = v2z - mul_rn(f2, dwz);
   vr[a] = p1x;
   vt[a] = sqrt_rn(p1y * p1y + p1z * p1z);
   vr[b] = p2x;
