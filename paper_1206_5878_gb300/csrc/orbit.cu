@@ -197,11 +197,6 @@ __device__ __forceinline__ double g64(const Table64& T, const Star& st, double c
 }
 
 // ------------------------------------------------------------ FP32 side
-struct Table32 {
-  const float2* t;  // (1/r, Phi) per node
-  int64_t nb;
-};
-
 // sample points of the bound F: s_j = -1 + (j + 1/2)/10.5 (IEEE double,
 // evaluated at compile time), and their float roundings
 #define CMC_SJ(j) (-1.0 + ((double)(j) + 0.5) / 10.5)
@@ -244,10 +239,34 @@ struct Buckets {
 // rounds, a prediction that is right 1).  Queries in the tails outside the
 // index search their tail the same way.  Any probe keeps the bracket
 // valid (x falls with i), so the answer is the unique one of a bisection.
-template <int K>
-__device__ __forceinline__ void shells32_bk(const float2* __restrict__ t, int nb,
-                                            const Buckets& B, const float (&xq)[K],
-                                            int (&out)[K]) {
+//
+// The keys probed are those of a table adaptor: the float keys (1/r as a
+// float, the high part of a float pair: FloatKeys) or the FP64 1/r of the
+// node records compared on their bit patterns (NodeKeys; positive doubles
+// order like their patterns).  Probing the table that the caller reads next
+// (the float pairs of the bracket walks, the node record of the shell)
+// brings its lines into the cache with the search.
+struct FloatKeys {
+  const float* p;  // key i at p[i * stride]
+  int stride;
+  using V = float;
+  __device__ __forceinline__ V load(int i) const { return __ldg(p + (size_t)i * stride); }
+  __device__ __forceinline__ V key(float q) const { return q; }
+};
+struct NodeKeys {
+  const double4_32a* nd;
+  using V = long long;
+  __device__ __forceinline__ V load(int i) const { return dbits(nd[i].y); }
+  // the query widened to FP64 exactly, as bits (queries are positive, finite)
+  __device__ __forceinline__ V key(float q) const { return dbits((double)q); }
+};
+
+template <int K, class Tab>
+__device__ __forceinline__ void shells32_bk(const Tab& tab, int nb, const Buckets& B,
+                                            const float (&xq)[K], int (&out)[K]) {
+  typename Tab::V kq[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) kq[q] = tab.key(xq[q]);
   int lo[K], hi[K], pred[K];
 #pragma unroll
   for (int q = 0; q < K; ++q) {
@@ -266,7 +285,7 @@ __device__ __forceinline__ void shells32_bk(const float2* __restrict__ t, int nb
   while (more) {
     more = false;
     int m[K][4];
-    float v[K][4];
+    typename Tab::V v[K][4];
 #pragma unroll
     for (int q = 0; q < K; ++q) {
       const int c = hi[q] - lo[q] - 1;  // candidates lo+1 .. hi-1
@@ -278,7 +297,7 @@ __device__ __forceinline__ void shells32_bk(const float2* __restrict__ t, int nb
         mj = mj < lo[q] + 1 ? lo[q] + 1 : mj;
         mj = mj > hi[q] - 1 ? hi[q] - 1 : mj;
         m[q][j] = mj;
-        v[q][j] = c > 0 ? __ldg(&t[mj].x) : 0.0f;
+        v[q][j] = c > 0 ? tab.load(mj) : typename Tab::V(0);
       }
     }
 #pragma unroll
@@ -286,7 +305,7 @@ __device__ __forceinline__ void shells32_bk(const float2* __restrict__ t, int nb
       if (hi[q] - lo[q] > 1) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          if (v[q][j] >= xq[q]) lo[q] = m[q][j] > lo[q] ? m[q][j] : lo[q];
+          if (v[q][j] >= kq[q]) lo[q] = m[q][j] > lo[q] ? m[q][j] : lo[q];
           else hi[q] = m[q][j] < hi[q] ? m[q][j] : hi[q];
         }
         pred[q] = -2;
@@ -359,12 +378,12 @@ __device__ __forceinline__ float g32_grid(const Grid& G, float E, float J, float
 
 // the FP32 shell (bucket index) of the point r(s), the start of the FP64
 // shell walk of an accepted or edge point
-__device__ __forceinline__ int shell32_of(const float2* __restrict__ t, int nb, const Buckets& B,
-                                          float c0, float c1, float sv) {
+__device__ __forceinline__ int shell32_of(const double4_32a* __restrict__ nd, int nb,
+                                          const Buckets& B, float c0, float c1, float sv) {
   const float rs = c0 + c1 * (sv * (3.0f - sv * sv));
   const float xq[1] = {1.0f / rs};
   int sh[1];
-  shells32_bk<1>(t, nb, B, xq, sh);
+  shells32_bk<1>(NodeKeys{nd}, nb, B, xq, sh);
   return sh[0];
 }
 
@@ -486,10 +505,10 @@ __device__ __forceinline__ float grid_q(const Grid& G, float E, float J, int g, 
   return 2.0f * (E - __ldg(G.phi + g)) - L * L;
 }
 
-__device__ __forceinline__ float node_q(const float2* __restrict__ t, float E, float J, int i) {
-  const float2 n = __ldg(t + i);
+__device__ __forceinline__ float node_q(const float4* __restrict__ tdf, float E, float J, int i) {
+  const float4 n = __ldg(tdf + i);  // (1/r, Phi) as the float pairs' high parts
   const float L = J * n.x;
-  return 2.0f * (E - n.y) - L * L;
+  return 2.0f * (E - n.z) - L * L;
 }
 
 // FP32 node brackets of both turning points from the potential grid: the
@@ -499,12 +518,11 @@ __device__ __forceinline__ float node_q(const float2* __restrict__ t, float E, f
 // nodes to where Q32 changes sign (r_max: node j with Q32 >= 0, j + 1 with
 // Q32 < 0 or the virtual node nb; r_min: j with Q32 < 0 or -1, j + 1 with
 // Q32 >= 0 or the star).  Returns false when a walk exceeds its bound.
-__device__ __forceinline__ bool grid_brackets(const Grid& G, const float2* __restrict__ t,
-                                              const float4* __restrict__ tdf,
+__device__ __forceinline__ bool grid_brackets(const Grid& G, const float4* __restrict__ tdf,
                                               const Buckets& BK, float E, float J, DF Ed, DF Jd,
                                               int nb, int k, int& jmax, int& jmin, bool& cert1,
                                               bool& cert2) {
-  const float xk = __ldg(&t[k].x);
+  const float xk = __ldg(&tdf[k].x);
   const uint32_t kk = __float_as_uint(xk);
   cert1 = cert2 = false;
   if (G.cells < 2 || kk < G.key0) return false;
@@ -530,7 +548,7 @@ __device__ __forceinline__ bool grid_brackets(const Grid& G, const float2* __res
     }
   }
   // the star's own end of each bracket: Q32 at the star
-  const float qk = node_q(t, E, J, k);
+  const float qk = node_q(tdf, E, J, k);
   if (ahi == gk + 1) qa_hi = qk;
   if (blo == gk) qb_lo = qk;
   float xq[2];
@@ -538,7 +556,7 @@ __device__ __forceinline__ bool grid_brackets(const Grid& G, const float2* __res
   xq[0] = alo < 0 ? 0.0f : xa_lo + (xa_hi - xa_lo) * (qa_lo / (qa_lo - qa_hi));
   xq[1] = bhi >= G.cells ? 0.0f : xb_lo + (xb_hi - xb_lo) * (qb_lo / (qb_lo - qb_hi));
   int sh[2];
-  shells32_bk<2>(t, nb, BK, xq, sh);
+  shells32_bk<2>(FloatKeys{&tdf[0].x, 4}, nb, BK, xq, sh);
   int j1 = alo < 0 ? nb - 1 : sh[0];
   int j2 = bhi >= G.cells ? -1 : sh[1];
   j1 = j1 < k ? k : (j1 > nb - 1 ? nb - 1 : j1);
@@ -645,7 +663,7 @@ __device__ __forceinline__ int64_t verify_rmin_nodes(const Table64& T,
 // bisections in FP32 in lockstep on the float table (r_max over [k, nb],
 // r_min over [-1, k]), each bracket verified in FP64 by a bounded walk,
 // then the FP64 roots inside the bracketing shells (Eq. 12).
-__device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __restrict__ t,
+__device__ __forceinline__ void turning_mixed(const Table64& T,
                                               const float4* __restrict__ tdf,
                                               const double4_32a* __restrict__ nd, const Grid& G,
                                               const Buckets& BK, const Star& s, double& rmin,
@@ -656,7 +674,7 @@ __device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __
   const int nb32 = (int)T.nb, k32 = (int)s.k;
   int lo1, lo2;
   bool cert1, cert2;
-  if (!grid_brackets(G, t, tdf, BK, E32, J32, Ed, Jd, nb32, k32, lo1, lo2, cert1, cert2)) {
+  if (!grid_brackets(G, tdf, BK, E32, J32, Ed, Jd, nb32, k32, lo1, lo2, cert1, cert2)) {
     // both node bisections in FP32, in lockstep; their brackets are not
     // certified (the FP64 walks run from them)
     cert1 = cert2 = false;
@@ -667,10 +685,10 @@ __device__ __forceinline__ void turning_mixed(const Table64& T, const float2* __
       const bool a1 = hi1 - lo1 > 1, a2 = hi2 - lo2 > 1;
       const int m1 = a1 ? lo1 + ((hi1 - lo1) >> 1) : k32;
       const int m2 = a2 ? lo2 + ((hi2 - lo2) >> 1) : k32;
-      const float2 e1 = __ldg(t + m1), e2 = __ldg(t + m2);
+      const float4 e1 = __ldg(tdf + m1), e2 = __ldg(tdf + m2);
       const float L1 = J32 * e1.x, L2 = J32 * e2.x;
-      const bool n1 = 2.0f * (E32 - e1.y) - L1 * L1 < 0.0f;
-      const bool n2 = 2.0f * (E32 - e2.y) - L2 * L2 < 0.0f;
+      const bool n1 = 2.0f * (E32 - e1.z) - L1 * L1 < 0.0f;
+      const bool n2 = 2.0f * (E32 - e2.z) - L2 * L2 < 0.0f;
       if (a1) { if (n1) hi1 = m1; else lo1 = m1; }
       if (a2) { if (n2) lo2 = m2; else hi2 = m2; }
     }
@@ -732,7 +750,7 @@ __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
   BK.nbk = pr.y;
   BK.lo = pr.z;
   BK.hi = pr.w;
-  turning_mixed(T, t32 + sb, BA.tdf + sb, BA.node + sb, grid_of(BA, c), BK, s, rmin, rmax);
+  turning_mixed(T, BA.tdf + sb, BA.node + sb, grid_of(BA, c), BK, s, rmin, rmax);
   tp_min[p] = rmin;
   tp_max[p] = rmax;
 }
@@ -913,7 +931,7 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
           const double sv = sym_double(sym_int(w.x, w.y));
           double rs, xs, ph, L, Q;
           point64(BA.node + sb, nbc, s, c0, c1, sv,
-                  shell32_of(t32 + sb, (int)nbc, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs,
+                  shell32_of(BA.node + sb, (int)nbc, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs,
                   xs, ph, L, Q);
           const double g64v = pos_num(Q) ? div_rn((3.0 * c1) * (1.0 - sv * sv), sqrt_rn(Q)) : 0.0;
           ++n64;
@@ -1006,7 +1024,6 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
     P.c = __ldg(T.phi + k) + div_rn(P.m, rk) + scale_down<1>(vrk * vrk + vtk * vtk);
   } else {
     int64_t jmax, jmin;
-    Table32 T32{t32 + sb, nbc};
     Buckets BK;
     if (kPrec == 1) {
       const int4 pr = BA.prm[c];
@@ -1109,7 +1126,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
           const double sv = sym_double(sym_int(w.x, w.y));
           double rs, xs, ph, L, Q;
           point64(BA.node + sb, nbc, s, c0, c1, sv,
-                  shell32_of(T32.t, nb32, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs, xs, ph,
+                  shell32_of(BA.node + sb, nb32, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs, xs, ph,
                   L, Q);
           if (!pos_num(Q)) Q = 0.0;
           const double sq = sqrt_rn(Q);
@@ -1183,7 +1200,7 @@ __global__ void __launch_bounds__(128) k_correction_mixed(Seg S, const int64_t* 
   BK.hi = pr.w;
   const float xq[1] = {f32_rn(xo)};
   int sh[1];
-  shells32_bk<1>(t32 + sb, (int)nbc, BK, xq, sh);
+  shells32_bk<1>(NodeKeys{BA.node + sb}, (int)nbc, BK, xq, sh);
   double4_32a nd;
   const int64_t i = fix_shell_nodes(BA.node + sb, nbc, sh[0], ro, nd);
   const double pn = i < 0 ? nd.z : nd.z + nd.w * (nd.y - xo);
