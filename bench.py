@@ -141,10 +141,11 @@ def profiled_traffic_per_star(kernel: str, precision: str):
 #   orbit:      r, v_r, v_t, Phi, m, id read; sort key and 48-B payload written
 #   sort:       5 passes of key + value read and written
 #   gather:     key, value and payload read; r, 1/r, v_r, v_t, m, id, r_old, c written
-#   potential:  1/r, m read twice; Phi, M, the float table written
+#               (with the potential's per-tile sums of m and m/r)
+#   potential:  1/r, m read; Phi, M, the float table written
 #   correction: r, 1/r, Phi, v_r, v_t, r_old, c read; v_r, v_t written
 STAGE_BYTES = {"timestep": 32, "relax": 44, "turning": 48, "orbit": 5 * 8 + 4 + 8 + 48,
-               "sort": 5 * 24, "gather": 12 + 48 + 60, "potential": 32 + 24,
+               "sort": 5 * 24, "gather": 12 + 48 + 60, "potential": 16 + 24,
                "correction": 56 + 16}
 STAGE_KERNEL = {"timestep": "k_bins", "relax": "k_relax", "turning": "k_turning_mixed",
                 "orbit": "k_orbit", "sort": "k_pass", "gather": "k_gather",

@@ -209,12 +209,13 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   launch_tiefix(L, sk, sv, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)), c->err, st,
                 24);
   mark(5);
-  launch_gather(L, sk, sv, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old, c->cc, st);
+  launch_gather(L, sk, sv, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old, c->cc, st,
+                c->tile_a, c->tile_b);
   mark(6);
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
                    mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, true, st,
                    mixed ? c->bk.node : nullptr,
-                   mixed ? c->bk.tdf : nullptr);
+                   mixed ? c->bk.tdf : nullptr, true);
   if (mixed) {
     launch_buckets(L, c->t32, true, c->bk, st);
     launch_grid(L, c->x, c->phi, c->Mbuf, true, c->bk, st);
@@ -233,10 +234,10 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
 }
 
 int count_step_kernels(const cmc_ctx* c) {
-  // bins, relax, orbit, upsweep, hist scan, 5 passes, tie fix, gather,
-  // tile sums, potential, [turning points, FP32 sampler, FP64 continuation,
-  // 2 bucket-index + 2 grid kernels], [correction], step end
-  return 3 + 2 + 5 + 1 + 1 + 2 + (c->cfg.precision == 1 ? 7 : 0) +
+  // bins, relax, orbit, upsweep, hist scan, 5 passes, tie fix, gather with
+  // the tile sums, potential, [turning points, FP32 sampler, FP64
+  // continuation, 2 bucket-index + 2 grid kernels], [correction], step end
+  return 3 + 2 + 5 + 1 + 1 + 1 + (c->cfg.precision == 1 ? 7 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 

@@ -124,10 +124,14 @@ void launch_id_keys(const SegLayout& L, const uint32_t* id, uint64_t* keys, cuda
 void launch_rekey_radius(const SegLayout& L, const uint32_t* perm, const double* r,
                          const uint32_t* id, uint64_t* keys, cudaStream_t st);
 
-// sorted (keys, vals) + payload -> SoA state (r, x, vr, vt, m, id, r_old, c)
+// sorted (keys, vals) + payload -> SoA state (r, x, vr, vt, m, id, r_old, c);
+// with tile_m and tile_mx (and r_old, c) also the potential's per-tile sums
+// over the bound stars after the orbit step (launch_potential with
+// nb_sub and sums_ready then skips them)
 void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* vals,
                    const Payload* pay, double* r, double* x, double* vr, double* vt,
-                   double* m, uint32_t* id, double* r_old, double* c, cudaStream_t st);
+                   double* m, uint32_t* id, double* r_old, double* c, cudaStream_t st,
+                   double* tile_m = nullptr, double* tile_mx = nullptr);
 
 // potential: per-tile sums then the tile-local scans (Eqs. 1-5 in scan
 // form).  nb_sub: subtract esc_step from nb (after the orbit step).
@@ -137,7 +141,7 @@ void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* val
 void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
                       double* tile_m, double* tile_mx, double* phi, float2* t32,
                       double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node = nullptr,
-                      float4* tdf = nullptr);
+                      float4* tdf = nullptr, bool sums_ready = false);
 // node records (and float-pair table) from the arrays (stage calls)
 void launch_make_nodes(int64_t n, const double* r, const double* x, const double* phi,
                        const double* M, double4_32a* node, float4* tdf, cudaStream_t st);

@@ -129,6 +129,42 @@ __global__ void k_gather(int64_t n, const uint64_t* __restrict__ keys,
   if (c) c[p] = P.c;
 }
 
+// The gather of one tile with the potential's per-tile sums of m and m x
+// (k_tile_sums over the bound stars after the orbit step) taken from the
+// values it has just written: the same striped element order and tree, so
+// the same sums, without reading m and x back.
+__global__ void __launch_bounds__(kThreads) k_gather_sums(
+    Seg S, const int64_t* esc, int64_t n, const uint64_t* __restrict__ keys,
+    const uint32_t* __restrict__ vals, const Payload* __restrict__ pay, double* r, double* x,
+    double* vr, double* vt, double* m, uint32_t* id, double* r_old, double* c, double* tile_m,
+    double* tile_mx) {
+  __shared__ double s[kThreads];
+  TR R = tile_of(S, esc, blockIdx.x, true);
+  double am = 0.0, ax = 0.0;
+#pragma unroll 4
+  for (int i = 0; i < kPer; ++i) {
+    const int64_t p = R.begin + (int64_t)i * kThreads + threadIdx.x;
+    if (p >= R.end) continue;
+    const uint64_t k = keys[p];
+    const uint32_t v = vals[p];
+    if ((int64_t)v >= n) continue;  // only after a reported sort failure
+    const Payload P = pay[v];
+    double rr, xx;
+    if (key_is_escaper(k)) { rr = __longlong_as_double(0x7FF0000000000000ll); xx = 0.0; }
+    else { rr = __longlong_as_double((long long)k); xx = div_rn(1.0, rr); }
+    r[p] = rr; x[p] = xx; vr[p] = P.vr; vt[p] = P.vt; m[p] = P.m; id[p] = P.id;
+    r_old[p] = P.r_old;
+    c[p] = P.c;
+    if (p < R.bound_end) {
+      am = am + P.m;
+      ax = ax + P.m * xx;
+    }
+  }
+  double tm = block_sum(am, s);
+  double tx = block_sum(ax, s);
+  if (threadIdx.x == 0) { tile_m[blockIdx.x] = tm; tile_mx[blockIdx.x] = tx; }
+}
+
 // Double -> float rounding to nearest even with integer operations: the
 // conversion instruction runs on the FP64 pipe, which the potential kernel
 // otherwise keeps busy with its scans.  For 2^-60 <= |v| < 2^126 (both
@@ -792,8 +828,14 @@ void launch_rekey_radius(const SegLayout& L, const uint32_t* perm, const double*
 
 void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* vals,
                    const Payload* pay, double* r, double* x, double* vr, double* vt,
-                   double* m, uint32_t* id, double* r_old, double* c, cudaStream_t st) {
-  if (L.n)
+                   double* m, uint32_t* id, double* r_old, double* c, cudaStream_t st,
+                   double* tile_m, double* tile_mx) {
+  if (!L.n) return;
+  if (tile_m && tile_mx && r_old && c && L.n_tiles)
+    k_gather_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(L.dev(), L.esc_step, L.n, keys, vals,
+                                                            pay, r, x, vr, vt, m, id, r_old, c,
+                                                            tile_m, tile_mx);
+  else
     k_gather<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, keys, vals, pay, r, x, vr, vt, m, id,
                                                   r_old, c);
 }
@@ -808,11 +850,12 @@ void potential_prepare() {
 void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
                       double* tile_m, double* tile_mx, double* phi, float2* t32,
                       double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node,
-                      float4* tdf) {
+                      float4* tdf, bool sums_ready) {
   if (!L.n_tiles) return;
   Seg S = L.dev();
-  k_tile_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, L.esc_step, nb_sub, x, m, tile_m,
-                                                       tile_mx);
+  if (!sums_ready)
+    k_tile_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, L.esc_step, nb_sub, x, m, tile_m,
+                                                         tile_mx);
   k_potential<<<(unsigned)L.n_tiles, kPotThreads, kPotentialSmem, st>>>(
       S, L.esc_step, nb_sub, r, x, m, tile_m, tile_mx, phi, t32, Mout, node, tdf);
 }
