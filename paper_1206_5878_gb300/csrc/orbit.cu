@@ -77,11 +77,11 @@ __device__ __forceinline__ double rmax_core(const Star& s, double rj, double xj,
   const double B = Mj;
   const double A = pj + B * xj;
   const double em = s.E - A;
-  double D = B * B + 2.0 * (s.J * s.J) * em;
+  double D = B * B + scale_up<1>(s.J * s.J) * em;
   if (!pos_num(D)) D = 0.0;
   const double sD = sqrt(D);
   // 2 (A - E) = -(2 (E - A)) exactly
-  double root = (B + sD) / -(2.0 * em);
+  double root = (B + sD) / -scale_up<1>(em);
   if (!ge_pos(root, rj)) root = rj;
   if (has_next && ubits(root) > ubits(rj1)) root = rj1;
   return root;
@@ -98,11 +98,11 @@ __device__ __forceinline__ double rmin_core(const Star& s, bool central, double 
   const double B = central ? 0.0 : Mj;
   double D, num;
   if (central) {
-    D = 2.0 * (s.E - pj);
+    D = scale_up<1>(s.E - pj);
     num = s.J;
   } else {
     const double A = pj + B * xj;
-    D = B * B + 2.0 * (s.J * s.J) * (s.E - A);
+    D = B * B + scale_up<1>(s.J * s.J) * (s.E - A);
     if (!pos_num(D)) D = 0.0;
     num = s.J * s.J;
   }
@@ -735,7 +735,7 @@ __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
   const double rk = r[p], vrk = vr[p], vtk = vt[p];
   Star s;
   s.k = k;
-  s.E = __ldg(T.phi + k) + 0.5 * (vrk * vrk + vtk * vtk);
+  s.E = __ldg(T.phi + k) + scale_down<1>(vrk * vrk + vtk * vtk);
   s.J = rk * vtk;
   // E < 0 on the bit pattern (negative, nonzero, not NaN); otherwise an
   // escaper, which the sampling kernel handles
