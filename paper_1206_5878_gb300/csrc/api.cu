@@ -192,11 +192,11 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   mark(2);
   // turning points into r_old, c (free until the gather), then sampling
   if (mixed)
-    launch_turning(L, c->r, c->x, c->phi, c->t32, c->Mbuf, c->vr, c->vt, c->bk.args(), c->r_old,
+    launch_turning(L, c->r, c->x, c->phi, c->Mbuf, c->vr, c->vt, c->bk.args(), c->r_old,
                    c->cc, c->cfg.orbit_block, st);
   mark(3);
   launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
-               mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
+               mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
                c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
                c->bk.args(), c->r_old, c->cc, c->vals, c->pcount, st, false);
   mark(4);
@@ -223,7 +223,7 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   mark(7);
   if (c->cfg.energy_correction) {
     if (mixed)
-      launch_correction_mixed(L, c->r, c->x, c->phi, c->t32, c->Mbuf, c->bk.args(), c->vr, c->vt,
+      launch_correction_mixed(L, c->r, c->x, c->phi, c->Mbuf, c->bk.args(), c->vr, c->vt,
                               c->r_old, c->cc, st);
     else
       launch_correction(L, c->r, c->x, c->phi, c->vr, c->vt, c->r_old, c->cc, true, c->err, st);
@@ -434,7 +434,7 @@ cmc_status autotune(cmc_ctx* c) {
   }
   auto run_orbit = [&](int blk, int var) {
     launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
-                 mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m,
+                 mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m,
                  c->id, c->step, c->keys, c->pay, nullptr, blk, var, c->bk.args(), c->r_old,
                  c->cc, c->vals, c->pcount, st);
   };
@@ -1045,7 +1045,7 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
     if (!e && precision == 1) e = dalloc(plist, n, st);
     if (!e && precision == 1) e = dalloc(pcnt, 1, st);
     if (!e)
-      launch_orbit(S.L, precision, max_trials, r, x, phi, t32, sl, vr, vt, mm, id, dstep, keys,
+      launch_orbit(S.L, precision, max_trials, r, x, phi, sl, vr, vt, mm, id, dstep, keys,
                    pay, &d, 0, 0, bk.args(), tmin, tmax, plist, pcnt, st);
     free_buckets(bk, st);
     dfree(sl, st);

@@ -226,7 +226,7 @@ void launch_grid(const SegLayout& L, const double* x, const double* phi, const d
 void launch_slopes(int64_t n, const double* x, const double* phi, double* Menc,
                    cudaStream_t st);
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
-                  const double* x, const double* phi, const float2* t32, const double* Menc,
+                  const double* x, const double* phi, const double* Menc,
                   const double* vr,
                   const double* vt, const double* m, const uint32_t* id, const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
@@ -236,7 +236,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
 // the turning-point kernel alone (mixed mode; launch_orbit(..., false)
 // then runs the sampling kernel only)
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,
-                    const float2* t32, const double* Menc, const double* vr, const double* vt,
+                    const double* Menc, const double* vr, const double* vt,
                     const BucketArgs& ba, double* tp_min, double* tp_max, int block,
                     cudaStream_t st);
 // mixed-mode orbit variants: register caps for 1 (none), 2, 3, 4, 5, 6 and
@@ -250,7 +250,7 @@ constexpr int kOrbitVariants = 7;
 // energy correction in mixed mode: shell of r_old from the bucket index of
 // the new table (nb - esc_step bound stars), Phi from the enclosed mass
 void launch_correction_mixed(const SegLayout& L, const double* r, const double* x,
-                             const double* phi, const float2* t32, const double* Menc,
+                             const double* phi, const double* Menc,
                              const BucketArgs& ba, double* vr, double* vt, const double* r_old,
                              const double* c, cudaStream_t st);
 

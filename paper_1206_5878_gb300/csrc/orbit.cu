@@ -721,7 +721,7 @@ __device__ __forceinline__ void turning_mixed(const Table64& T,
 // kernel so that each runs with fewer registers and more warps).
 template <int kMinB>
 __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
-    Seg S, const double* r, const double* x, const double* phi, const float2* t32,
+    Seg S, const double* r, const double* x, const double* phi,
     const double* Menc, const double* vr, const double* vt, BucketArgs BA, double* tp_min,
     double* tp_max, int64_t n) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -888,7 +888,7 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
 template <bool kTaus>
 __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double* r,
                                              const double* x, const double* phi,
-                                             const float2* t32, const double* Menc,
+                                             const double* Menc,
                                              const double* vr, const double* vt,
                                              const uint32_t* id, const uint32_t* step_p,
                                              BucketArgs BA, const double* tp_min,
@@ -957,7 +957,7 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
 template <bool kTaus>
 __global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const double* r,
                                                    const double* x, const double* phi,
-                                                   const float2* t32, const double* Menc,
+                                                   const double* Menc,
                                                    const double* vr, const double* vt,
                                                    const uint32_t* id, const uint32_t* step_p,
                                                    BucketArgs BA, const double* tp_min,
@@ -966,7 +966,7 @@ __global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const 
                                                    const uint32_t* pcount, int64_t n) {
   const uint32_t np = *pcount;
   for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < np; i0 += gridDim.x * blockDim.x) {
-    pending_star<kTaus>(S, max_trials, r, x, phi, t32, Menc, vr, vt, id, step_p, BA, tp_min,
+    pending_star<kTaus>(S, max_trials, r, x, phi, Menc, vr, vt, id, step_p, BA, tp_min,
                         tp_max, keys, i0 + threadIdx.x < np ? (int64_t)plist[i0 + threadIdx.x] : n,
                         n);
   }
@@ -979,7 +979,7 @@ __global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const 
 template <int kPrec, int kMinB, bool kTaus>
 __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, const double* r,
                                                const double* x, const double* phi,
-                                               const float2* t32, const double* Menc, const double* vr,
+                                               const double* Menc, const double* vr,
                                                const double* vt, const double* m,
                                                const uint32_t* id, const uint32_t* step_p,
                                                uint64_t* keys, Payload* pay, int64_t* esc,
@@ -1177,7 +1177,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
 // velocity components scaled by sqrt(T'/T), as in the FP64 kernel.
 __global__ void __launch_bounds__(128) k_correction_mixed(Seg S, const int64_t* esc,
                                                           const double* r, const double* x,
-                                                          const double* phi, const float2* t32,
+                                                          const double* phi,
                                                           const double* Menc, BucketArgs BA,
                                                           double* vr, double* vt,
                                                           const double* r_old, const double* cc,
@@ -1415,27 +1415,27 @@ void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWo
 }
 
 void launch_correction_mixed(const SegLayout& L, const double* r, const double* x,
-                             const double* phi, const float2* t32, const double* Menc,
+                             const double* phi, const double* Menc,
                              const BucketArgs& ba, double* vr, double* vt, const double* r_old,
                              const double* c, cudaStream_t st) {
   if (!L.n) return;
   k_correction_mixed<<<(unsigned)((L.n + 127) / 128), 128, 0, st>>>(
-      L.dev(), L.esc_step, r, x, phi, t32, Menc, ba, vr, vt, r_old, c, L.n);
+      L.dev(), L.esc_step, r, x, phi, Menc, ba, vr, vt, r_old, c, L.n);
 }
 
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,
-                    const float2* t32, const double* Menc, const double* vr, const double* vt,
+                    const double* Menc, const double* vr, const double* vt,
                     const BucketArgs& ba, double* tp_min, double* tp_max, int block,
                     cudaStream_t st) {
   if (!L.n) return;
   if (block <= 0) block = 64;
   const unsigned grid = (unsigned)((L.n + block - 1) / block);
-  k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, t32, Menc, vr, vt, ba, tp_min,
+  k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, Menc, vr, vt, ba, tp_min,
                                              tp_max, L.n);
 }
 
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
-                  const double* x, const double* phi, const float2* t32, const double* Menc,
+                  const double* x, const double* phi, const double* Menc,
                   const double* vr, const double* vt, const double* m, const uint32_t* id,
                   const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
@@ -1449,10 +1449,10 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
   // the pending list is short: a grid of a few blocks per SM walks it
   const unsigned pgrid = (unsigned)((L.n + 127) / 128 < 1216 ? (L.n + 127) / 128 : 1216);
 #define CMC_TURN(B)                                                                          \
-  k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, t32, Menc, vr, vt, ba,      \
+  k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, Menc, vr, vt, ba,      \
                                              tp_min, tp_max, L.n)
 #define CMC_ORBIT(P, B, T)                                                                  \
-  k_orbit<P, B, T><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, \
+  k_orbit<P, B, T><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, Menc, vr, vt, \
                                            m, id, step, keys, pay, L.esc_step, d, ba, tp_min, \
                                            tp_max, L.n)
 #define CMC_MIXED(B, T)                                                                     \
@@ -1461,7 +1461,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
     cudaMemsetAsync(pcount, 0, sizeof(uint32_t), st);                                      \
     k_sample32<B, T><<<grid, block, 0, st>>>(L.dev(), max_trials, r, phi, vr, vt, id, step, \
                                              ba, tp_min, tp_max, keys, plist, pcount, L.n); \
-    k_pending64<T><<<pgrid, 128, 0, st>>>(L.dev(), max_trials, r, x, phi, t32, Menc, vr, vt, \
+    k_pending64<T><<<pgrid, 128, 0, st>>>(L.dev(), max_trials, r, x, phi, Menc, vr, vt, \
                                           id, step, ba, tp_min, tp_max, keys, plist, pcount, \
                                           L.n);                                             \
     CMC_ORBIT(1, 4, T);                                                                     \

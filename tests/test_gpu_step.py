@@ -147,6 +147,28 @@ def test_ensemble_equals_separate_runs(g):
         np.testing.assert_array_equal(ens.escaped()[i], one.escaped()[0])
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_step_potential_equals_the_potential_entry_point(g, precision):
+    """After a timestep the potential of the bound stars (its per-tile sums
+    taken by the post-sort gather) equals, bit for bit, cmc_potential on
+    the same sorted radii and masses (the sums read back from memory), for
+    every cluster of an ensemble whose sizes leave ragged last tiles."""
+    sizes = [4097, 30_000, 12_289]
+    seeds = [7 + c for c in range(len(sizes))]
+    parts = [ic.plummer(n, s) for n, s in zip(sizes, seeds)]
+    cat = {k: np.concatenate([p[k] for p in parts]) for k in ("r", "vr", "vt", "m", "id")}
+    ens = g.Cluster(cat, seeds, sizes=sizes, precision=precision)
+    ens.step(3)
+    st = ens.get_state()
+    nb = ens.nbound()
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    for c in range(len(sizes)):
+        sl = slice(off[c], off[c] + int(nb[c]))
+        phi, M = g.stage_potential(dev(st["r"][sl]), dev(st["m"][sl]), want_M=True)
+        np.testing.assert_array_equal(host(phi), st["phi"][sl], err_msg=str(c))
+    assert int(nb.sum()) < sum(sizes)  # escapers were left out of the sums
+
+
 def test_resume_is_bit_identical(g):
     d = ic.plummer(12_345, seed=3, masses="salpeter")
     a = _cluster(g, d, 3)
