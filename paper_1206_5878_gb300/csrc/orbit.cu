@@ -1175,7 +1175,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
 // enclosed mass of that shell (Eq. 6 without its division), then
 // T' = T + 1/2 [(Phi_new(r_old) - Phi_new,k) - c] clamped at 0 and both
 // velocity components scaled by sqrt(T'/T), as in the FP64 kernel.
-__global__ void __launch_bounds__(128) k_correction_mixed(Seg S, const int64_t* esc,
+__global__ void __launch_bounds__(128, 12) k_correction_mixed(Seg S, const int64_t* esc,
                                                           const double* r, const double* x,
                                                           const double* phi,
                                                           const double* Menc, BucketArgs BA,
