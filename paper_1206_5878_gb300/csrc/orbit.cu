@@ -1464,7 +1464,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
     k_pending64<T><<<pgrid, 128, 0, st>>>(L.dev(), max_trials, r, x, phi, Menc, vr, vt, \
                                           id, step, ba, tp_min, tp_max, keys, plist, pcount, \
                                           L.n);                                             \
-    CMC_ORBIT(1, 4, T);                                                                     \
+    CMC_ORBIT(1, 5, T);                                                                     \
   } while (0)
   if (L.taus) {
     // stream mode: one launch shape of the sampler
