@@ -153,7 +153,7 @@ constexpr int kRankBallot = 1;  // nine __ballot_sync
 
 // ------------------------------------------------------------- onesweep
 template <bool kValIdentity, int IPT, int kRank>
-__global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : 2))
+__global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : 3))
     k_pass(const int64_t* off, const int64_t* tile_off, int n_seg, int64_t n_tiles,
            const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
            uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int pass, int q,
