@@ -153,9 +153,8 @@ __device__ __forceinline__ float f32_rn(double v) {
 // Correctly rounded FP64 product, quotient and square root from 64-bit
 // integer arithmetic on the significands, for normal operands with a normal
 // result (anything else: the FP64 operation).  On this GPU an FP64 division
-// or square root takes several FP64 issues; these take none, leaving the
-// FP64 pipe to the sums and most products (where the integer pipes are busy
-// enough already, a kernel keeps the FP64 forms).  Each returns the IEEE-754 round-to-
+// or square root takes several FP64 issues; these take none, and the FP64
+// pipe is left to the additions.  Each returns the IEEE-754 round-to-
 // nearest-even result exactly (checked bit for bit against the FP64
 // operations on 3 x 2^28 operand pairs per operation: random bit patterns,
 // random values over 81 binades, and significands with random runs of
