@@ -329,8 +329,9 @@ def run_reference(args, rank, world):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "Plummer N=%d equal-mass (oracle, host)" % args.n,
-                       "n_stars": args.n, "seed": args.seed},
+            "config": {"workload": "Plummer N=%d equal-mass, fp64 orbits" % args.n,
+                       "n_stars": args.n, "precision": "fp64 (the oracle on the host)",
+                       "seed": args.seed, "parallelism": "single"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
