@@ -74,7 +74,11 @@ enum {
     CMC_STAT_FP64_TRIALS = 8, /* mixed mode: trials whose FP32 accept test could
                                  not be decided within its error bound, taken
                                  in FP64 (0 in FP64 mode) */
-    CMC_NSTATS = 9
+    CMC_STAT_CLAMP_ENERGY = 9,  /* energy the clamps of T' < 0 to 0 added to the
+                                   cluster (section 2.1 step 6's correction):
+                                   the sum of m_k |T'_k| over clamped stars, as
+                                   an integer in units of 2^-62 */
+    CMC_NSTATS = 10
 };
 
 typedef struct {
@@ -105,6 +109,9 @@ typedef struct {
                                    then be below 4 N_c + 64 in every cluster
                                    (stream slots are indexed by id); the mixed
                                    sampler runs one launch shape */
+    int32_t relax_variant;      /* relaxation kernel variant (listed at
+                                   cmc_get_tuning): -1 = the autotuner's choice
+                                   (0 without autotune), or 0..2 (default -1) */
 } cmc_config;
 
 /* Fill cfg with the defaults shown above. */
@@ -155,7 +162,7 @@ cmc_status cmc_lagrange_radii(cmc_ctx *ctx, const double *fracs, int32_t nf, dou
 cmc_status cmc_get_rng_state(cmc_ctx *ctx, uint32_t *out, int64_t *n_words);
 cmc_status cmc_set_rng_state(cmc_ctx *ctx, const uint32_t *in, int64_t n_words);
 
-/* Core diagnostics (section 4.3, Eq. 19) per cluster of the bound stars:
+/* Core diagnostics (section 4.2, Eq. 19) per cluster of the bound stars:
  * out (host, n_clusters x 3) = {rho_c, r_c, n_est}.  The density around
  * sorted bound star k (3 <= k < N_bound - 3) is the 6th-order estimator of
  * Casertano & Hut taken in the radial order, rho_k = (m_{k-2} + ... +
@@ -221,10 +228,12 @@ enum {
 cmc_status cmc_step_profiled(cmc_ctx *ctx, int32_t n_steps, double *stage_ms);
 
 /* Kernel shapes in use (chosen by autotune or the configuration): out
- * (host, 4) = {orbit threads per block, sort keys per thread, sort
+ * (host, 5) = {orbit threads per block, sort keys per thread, sort
  * multisplit (0: match, 1: ballot), mixed-mode orbit variant (registers per
  * thread capped for 1 (no cap), 2, 3, 4, 5, 6 or 8 resident 256-thread
- * blocks per SM: variants 0..6)}.  All shapes give bit-identical results. */
+ * blocks per SM: variants 0..6), relaxation variant (registers per thread
+ * capped for 1 (no cap), 6 or 8 resident 128-thread blocks per SM:
+ * variants 0..2)}.  All shapes give bit-identical results. */
 cmc_status cmc_get_tuning(const cmc_ctx *ctx, int32_t *out);
 
 /* Number of kernels one cmc_step timestep launches. */
@@ -302,9 +311,10 @@ cmc_status cmc_energy_correction(int64_t n, const double *r, const double *phi, 
  * cmc_potential (the same scan over the same tiles, with summation orders
  * of its own inside a tile: results agree with cmc_potential's to rounding
  * and repeat bit for bit from call to call) for callers that may not
- * allocate device memory -- code that runs while a stream is captured into
- * a CUDA graph, loops that forbid allocation after start-up, programs that
- * give all device memory to their own pool.  cmc_potential takes scratch
+ * allocate device memory: real-time loops that forbid allocation after
+ * start-up (an allocation can block, synchronise or fail at any time),
+ * programs that give all device memory to their own pool, and plug-ins
+ * whose host application owns the allocator.  cmc_potential takes scratch
  * from cudaMallocAsync; this function allocates nothing.  Its only scratch,
  * the per-tile sums of the scan, is one fixed array of the library's own
  * device memory (2 * CMC_STATIC_MAX_STARS / 4096 doubles, 64 KiB) that
@@ -312,12 +322,16 @@ cmc_status cmc_energy_correction(int64_t n, const double *r, const double *phi, 
  *   n <= CMC_STATIC_MAX_STARS sorted stars; r, m (device, n doubles) in;
  *   phi (device, n doubles) out; M (device, may be NULL) enclosed mass out.
  * The first call on each device looks up the array's device address with
- * that device current; make that first call before any stream capture.
+ * that device current (and may load the library's kernels); make that first
+ * call before any stream capture.  The address is kept for the life of the
+ * process: after cudaDeviceReset on a device, do not call this function
+ * on that device again.
  * Every call shares the one array and overwrites it (nothing in it needs
  * to start at zero), so calls whose work overlaps on the GPU (different
  * streams) race: order them on one stream.  Returns CMC_EINVAL for
- * n > CMC_STATIC_MAX_STARS or bad pointers, CMC_ECUDA if the launch fails;
- * returns once the work is enqueued on `stream`.
+ * n > CMC_STATIC_MAX_STARS or bad pointers, CMC_ECUDA if the launch fails
+ * (or an earlier error is pending on the device; it is reported, not
+ * cleared); returns once the work is enqueued on `stream`.
  * ------------------------------------------------------------------- */
 #define CMC_STATIC_MAX_STARS 16777216
 cmc_status cmc_potential_static(int64_t n, const double *r, const double *m, double *phi,

@@ -79,6 +79,10 @@ def _declare(lib):
         "or_relax": (_i64, [_i64, _p, _p, _p, _p, _p, _i32, _d, _d, _u64, _u32]),
         "or_orbit_star": (ctypes.c_int, [_i64, _i64, _p, _p, _d, _d, _u32, _u64, _u32,
                                          _i32, _p, _p]),
+        "or_orbit_star_env": (ctypes.c_int, [_i64, _i64, _p, _p, _d, _d, _u32, _u64, _u32,
+                                             _i32, _d, _p, _p]),
+        "or_orbit_sample": (None, [_i64, _p, _p, _p, _p, _p, _i64, _p, _u64, _u32, _i32,
+                                   _p]),
         "or_orbit_all": (None, [_i64, _p, _p, _p, _p, _p, _u64, _u32, _i32,
                                 _p, _p, _p, _p, _p, _p, _p, _p, _p]),
         "or_energy_correction": (_i64, [_i64, _p, _p, _p, _p, _p, _p, _p]),
@@ -210,15 +214,33 @@ def disk_angle(seed: int, ident: int, step: int, tag: int):
 
 
 def orbit_star(k: int, r, phi, vr: float, vt: float, ident: int, seed: int, step: int,
-               max_trials: int = 1000):
+               max_trials: int = 1000, F=None):
+    """One star's orbit step (section 2.1 step 5).  F (optional, > 0): the
+    rejection bound to use instead of 1.2 max g(s_j)."""
     r, phi = _f64(r), _f64(phi)
     out = np.zeros(8)
     viol = np.zeros(1, dtype=np.int64)
-    rc = _L().or_orbit_star(k, r.shape[0], _ptr(r), _ptr(phi), float(vr), float(vt),
-                            int(ident), seed, step, max_trials, _ptr(out), _ptr(viol))
+    if F is None:
+        rc = _L().or_orbit_star(k, r.shape[0], _ptr(r), _ptr(phi), float(vr), float(vt),
+                                int(ident), seed, step, max_trials, _ptr(out), _ptr(viol))
+    else:
+        rc = _L().or_orbit_star_env(k, r.shape[0], _ptr(r), _ptr(phi), float(vr), float(vt),
+                                    int(ident), seed, step, max_trials, float(F), _ptr(out),
+                                    _ptr(viol))
     return {"code": rc, "r_new": out[0], "vr": out[1], "vt": out[2], "phi_new": out[3],
             "rmin": out[4], "rmax": out[5], "F": out[6], "trials": int(out[7]),
             "violations": int(viol[0])}
+
+
+def orbit_sample(r, phi, vr, vt, ids, ks, seed: int, step: int, max_trials: int = 1000):
+    """New radii of the stars at sorted positions ks only (or_orbit_sample)."""
+    r, phi, vr, vt = _f64(r), _f64(phi), _f64(vr), _f64(vt)
+    ids = _u32a(ids)
+    ks = np.ascontiguousarray(ks, dtype=np.int64)
+    out = np.zeros(ks.shape[0])
+    _L().or_orbit_sample(r.shape[0], _ptr(r), _ptr(phi), _ptr(vr), _ptr(vt), _ptr(ids),
+                         ks.shape[0], _ptr(ks), seed, step, max_trials, _ptr(out))
+    return out
 
 
 def orbit_all(r, phi, vr, vt, ids, seed: int, step: int, max_trials: int = 1000):

@@ -242,9 +242,8 @@ static int or_disk_angle(uint64_t seed, uint32_t id, uint32_t step, uint32_t tag
         vv = v * v;
         q = uu + vv;
         if (q <= 1.0) {
-            double iq = 1.0 / q;
-            *c = (uu - vv) * iq;
-            *s = ((2.0 * u) * v) * iq;
+            *c = (uu - vv) / q;
+            *s = ((2.0 * u) * v) / q;
             return 0;
         }
     }
@@ -486,7 +485,7 @@ double or_timestep(int64_t nb, const double *r, const double *vr, const double *
 /* (4 sin^2(beta/2) ~ beta^2 is the mean squared deflection the relative    */
 /* velocity gathers over dt from small-angle encounters, 8 pi G^2 (m1+m2)^2 */
 /* n lnL dt / |w|^3; with it a Plummer sphere collapses at ~17-18 t_rh, as  */
-/* in section 4.3, where half this rate takes ~34 t_rh.)                     */
+/* in section 4.2, where half this rate takes ~34 t_rh.)                     */
 /* Random numbers are keyed by the id of the pair's first star.             */
 /* Returns the number of pairs whose angle draw failed (normally 0).        */
 /* ------------------------------------------------------------------------ */
@@ -501,8 +500,8 @@ int or_encounter(double m1, double m2, double vr1, double vt1, double vr2, doubl
 {
     double msum, cpsi = 1.0, spsi = 0.0, cphi, sphi;
     double v1x, v1y, v1z, v2x, v2y, v2z, wx, wy, wz, w2, w;
-    double num, s2, cosb, sinb, wp2, e1y, e1z;
-    double ux, uy, uz, a1, wpx, wpy, wpz, dwx, dwy, dwz, im, f1, f2;
+    double num, s2, sb, cosb, sinb, wp2, e1y, e1z;
+    double ux, uy, uz, a1, wpx, wpy, wpz, dwx, dwy, dwz, f1, f2;
     int fails = 0, i;
     for (i = 0; i < 16; ++i) out[i] = 0.0;
     out[15] = 1.0;
@@ -532,17 +531,18 @@ int or_encounter(double m1, double m2, double vr1, double vt1, double vr2, doubl
     s2 = num / (w2 * w);
     if (!(s2 <= 1.0)) s2 = 1.0;
     /* cos(beta) = 1 - 2 sin^2(beta/2), sin(beta) = 2 sin(beta/2) cos(beta/2) */
+    sb = sqrt(s2);
     cosb = 1.0 - 2.0 * s2;
-    sinb = 2.0 * sqrt(s2 * (1.0 - s2));
+    sinb = (2.0 * sb) * sqrt(1.0 - s2);
     fails += or_disk_angle(seed, id, step, OR_TAG_PHI, &cphi, &sphi);
     /* unit vector e1 = (w x xhat)/|w x xhat| = (0, wz, -wy)/|.|, or yhat when
      * w is radial; u = w x e1 has length |w| and completes the orthogonal
      * frame (e1, u/|w|) perpendicular to w. */
     wp2 = wy * wy + wz * wz;
     if (wp2 > 0.0) {
-        double iwp = 1.0 / sqrt(wp2);
-        e1y = wz * iwp;
-        e1z = -(wy * iwp);
+        double wp = sqrt(wp2);
+        e1y = wz / wp;
+        e1z = -wy / wp;
     } else {
         e1y = 1.0;
         e1z = 0.0;
@@ -558,9 +558,8 @@ int or_encounter(double m1, double m2, double vr1, double vt1, double vr2, doubl
     dwx = wpx - wx; dwy = wpy - wy; dwz = wpz - wz;
     /* the centre of mass keeps its velocity: v1' = v1 + m2/(m1+m2) dw,
      * v2' = v2 - m1/(m1+m2) dw */
-    im = 1.0 / msum;
-    f1 = m2 * im;
-    f2 = m1 * im;
+    f1 = m2 / msum;
+    f2 = m1 / msum;
     out[6] = v1x + f1 * dwx; out[7] = v1y + f1 * dwy; out[8] = v1z + f1 * dwz;
     out[9] = v2x - f2 * dwx; out[10] = v2y - f2 * dwy; out[11] = v2z - f2 * dwz;
     out[12] = s2; out[13] = cosb; out[14] = w; out[15] = 0.0;
@@ -661,9 +660,32 @@ static double or_g_of_s(const or_orb *o, double c0, double c1, double s,
  * Return code: 0 moved, 1 escaped (E >= 0), 2 degenerate orbit (kept in
  * place), 3 rejection cap hit (kept in place).  *viol counts trials with
  * g(s) > F. */
+static int or_orbit_star_F(int64_t k, int64_t nb, const double *r, const double *phi,
+                           double vr, double vt, uint32_t id, uint64_t seed, uint32_t step,
+                           int32_t max_trials, double F_in, double *out, int64_t *viol);
+
 int or_orbit_star(int64_t k, int64_t nb, const double *r, const double *phi,
                   double vr, double vt, uint32_t id, uint64_t seed, uint32_t step,
                   int32_t max_trials, double *out, int64_t *viol)
+{
+    return or_orbit_star_F(k, nb, r, phi, vr, vt, id, seed, step, max_trials, 0.0, out, viol);
+}
+
+/* Test hook: the same orbit step with the rejection bound F given from
+ * outside (F_in > 0) instead of 1.2 max g(s_j).  Any F >= max g gives the
+ * same distribution of r_new (Eqs. 13-15); for a given F, the draws fix the
+ * accepted trial.  This lets a sampler with an envelope of its own be
+ * compared star by star. */
+int or_orbit_star_env(int64_t k, int64_t nb, const double *r, const double *phi,
+                      double vr, double vt, uint32_t id, uint64_t seed, uint32_t step,
+                      int32_t max_trials, double F_in, double *out, int64_t *viol)
+{
+    return or_orbit_star_F(k, nb, r, phi, vr, vt, id, seed, step, max_trials, F_in, out, viol);
+}
+
+static int or_orbit_star_F(int64_t k, int64_t nb, const double *r, const double *phi,
+                           double vr, double vt, uint32_t id, uint64_t seed, uint32_t step,
+                           int32_t max_trials, double F_in, double *out, int64_t *viol)
 {
     or_orb o;
     double rk = r[k], rmin, rmax, c0, c1, gmax, F;
@@ -714,8 +736,12 @@ int or_orbit_star(int64_t k, int64_t nb, const double *r, const double *phi,
         if (g > gmax) gmax = g;
     }
     F = 1.2 * gmax;
+    if (!(rmax > rmin) || !(F > 0.0)) {
+        out[6] = F;
+        return 2;
+    }
+    if (F_in > 0.0) F = F_in;
     out[6] = F;
-    if (!(rmax > rmin) || !(F > 0.0)) return 2;
     /* von Neumann rejection (Eqs. 14-15 in the variable s) */
     for (t = 0; t < max_trials; ++t) {
         double X, Xp, s, rs, ph, Q, g;
@@ -764,6 +790,22 @@ void or_orbit_all(int64_t nb, const double *r, const double *phi, const double *
         if (rc == 1) stats[0] += 1;
         if (rc == 2) stats[1] += 1;
         if (rc == 3) stats[2] += 1;
+    }
+}
+
+/* The orbit step of the stars at sorted positions ks[0..nk) only (the same
+ * per-star work as or_orbit_all), for timing a sample of a large state:
+ * r_new[i] receives star ks[i]'s new radius. */
+void or_orbit_sample(int64_t nb, const double *r, const double *phi, const double *vr,
+                     const double *vt, const uint32_t *id, int64_t nk, const int64_t *ks,
+                     uint64_t seed, uint32_t step, int32_t max_trials, double *r_new)
+{
+    int64_t i;
+    for (i = 0; i < nk; ++i) {
+        double out[8];
+        int64_t viol = 0, k = ks[i];
+        or_orbit_star(k, nb, r, phi, vr[k], vt[k], id[k], seed, step, max_trials, out, &viol);
+        r_new[i] = out[0];
     }
 }
 
@@ -850,7 +892,7 @@ void or_lagrange_radii(int64_t nb, const double *r, const double *m,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Core diagnostics (section 4.3, Eq. 19).  The paper's density around star */
+/* Core diagnostics (section 4.2, Eq. 19).  The paper's density around star */
 /* i is the 6th-order estimator of Casertano & Hut (1985): the mass of j - 1 */
 /* neighbours over the volume out to the j-th (j = 6).  The method keeps     */
 /* radii only, so the estimator is taken in the radial order (reading): the  */

@@ -214,12 +214,13 @@ class Cluster:
 
     def tuning(self) -> dict:
         """Kernel shapes in use: orbit block size, sort keys per thread,
-        multisplit (match or ballot) and the mixed-mode orbit variant."""
-        out = np.zeros(4, dtype=np.int32)
+        multisplit (match or ballot), the mixed-mode orbit variant and the
+        relaxation variant."""
+        out = np.zeros(5, dtype=np.int32)
         check(self.lib.cmc_get_tuning(self.ctx, out.ctypes.data), self.ctx)
         return {"orbit_block": int(out[0]), "sort_keys_per_thread": int(out[1]),
                 "sort_multisplit": "ballot" if out[2] else "match",
-                "orbit_variant": int(out[3])}
+                "orbit_variant": int(out[3]), "relax_variant": int(out[4])}
 
     def set_stream(self, stream):
         self.stream = _stream_ptr(stream)
@@ -312,8 +313,3 @@ def check_arith(op: int, n: int, seed: int = 1) -> int:
     check(load().cmc_check_arith(int(op), int(n), int(seed), out.ctypes.data))
     return int(out[0])
 
-
-def half_mass_relaxation_time(n: int, r_h: float, mass: float = 1.0, gamma: float = 0.1) -> float:
-    """Eq. 20: t_rh = 0.138 N / ln(gamma N) (r_h^3 / (G M))^(1/2) with G = 1."""
-    import math
-    return 0.138 * n / math.log(gamma * n) * math.sqrt(r_h ** 3 / mass)

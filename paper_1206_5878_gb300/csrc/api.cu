@@ -42,6 +42,7 @@ struct cmc_ctx {
   std::string last_error;
   int kernels_per_step = 0;
   int orbit_variant = 0;  // mixed-mode orbit kernel variant (see kOrbitVariants)
+  int relax_variant = 0;  // relaxation kernel variant (see kRelaxVariants)
 };
 
 namespace {
@@ -168,10 +169,10 @@ void order_state(cmc_ctx* c, cudaStream_t st) {
   launch_nb_from_keys(L, c->keys, st);
   cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
   const bool mixed = c->cfg.precision == 1;
-  launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32,
-                   mixed ? c->Mbuf : nullptr, false, st, mixed ? c->bk.node : nullptr,
-                   mixed ? c->bk.tdf : nullptr);
+  launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32, nullptr, false,
+                   st, nullptr, mixed ? c->bk.tdf : nullptr);
   if (mixed) {
+    launch_node_slopes(L, false, c->r, c->x, c->phi, c->Mbuf, c->bk.node, st);
     launch_buckets(L, c->t32, false, c->bk, st);
     launch_grid(L, c->x, c->phi, c->Mbuf, false, c->bk, st);
   }
@@ -188,7 +189,7 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   mark(0);
   launch_bins(L, c->r, c->vr, c->vt, c->m, c->nbin, c->pref, st);
   mark(1);
-  launch_relax(L, c->vr, c->vt, c->m, c->id, c->nbin, c->step, st);
+  launch_relax(L, c->vr, c->vt, c->m, c->id, c->nbin, c->step, st, c->relax_variant);
   mark(2);
   // turning points into r_old, c (free until the gather), then sampling
   if (mixed)
@@ -213,10 +214,12 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
                 c->tile_a, c->tile_b);
   mark(6);
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
-                   mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, true, st,
-                   mixed ? c->bk.node : nullptr,
+                   mixed ? c->t32 : nullptr, nullptr, true, st, nullptr,
                    mixed ? c->bk.tdf : nullptr, true);
   if (mixed) {
+    // the shell slopes of the FP64 orbit step (not the scan's enclosed
+    // masses): the mixed turning points and points are then FP64 mode's
+    launch_node_slopes(L, true, c->r, c->x, c->phi, c->Mbuf, c->bk.node, st);
     launch_buckets(L, c->t32, true, c->bk, st);
     launch_grid(L, c->x, c->phi, c->Mbuf, true, c->bk, st);
   }
@@ -224,9 +227,10 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   if (c->cfg.energy_correction) {
     if (mixed)
       launch_correction_mixed(L, c->r, c->x, c->phi, c->Mbuf, c->bk.args(), c->vr, c->vt,
-                              c->r_old, c->cc, st);
+                              c->r_old, c->cc, c->m, st);
     else
-      launch_correction(L, c->r, c->x, c->phi, c->vr, c->vt, c->r_old, c->cc, true, c->err, st);
+      launch_correction(L, c->r, c->x, c->phi, c->vr, c->vt, c->r_old, c->cc, true, c->err, st,
+                        c->m);
   }
   mark(8);
   launch_step_end(L, c->step, c->r_old, c->cc, c->m, st);
@@ -236,8 +240,9 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
 int count_step_kernels(const cmc_ctx* c) {
   // bins, relax, orbit, upsweep, hist scan, 5 passes, tie fix, gather with
   // the tile sums, potential, [turning points, FP32 sampler, FP64
-  // continuation, 2 bucket-index + 2 grid kernels], [correction], step end
-  return 3 + 2 + 5 + 1 + 1 + 1 + (c->cfg.precision == 1 ? 7 : 0) +
+  // continuation, node slopes, 2 bucket-index + 2 grid kernels],
+  // [correction], step end
+  return 3 + 2 + 5 + 1 + 1 + 1 + (c->cfg.precision == 1 ? 8 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 
@@ -464,6 +469,28 @@ cmc_status autotune(cmc_ctx* c) {
     }
   c->cfg.orbit_block = blk_best;
   c->orbit_variant = var_best;
+  // relaxation kernel variant: on copies of the velocities (r_old and cc
+  // are free scratch here), after the bins of this state; the timestep the
+  // bins leave is put back
+  if (c->cfg.relax_variant < 0 && L.n_pairs) {
+    uint64_t* dt_saved = reinterpret_cast<uint64_t*>(c->tile_c);
+    cudaMemcpyAsync(dt_saved, L.dt_bits, sizeof(uint64_t) * L.n_seg, cudaMemcpyDeviceToDevice,
+                    st);
+    launch_bins(L, c->r, c->vr, c->vt, c->m, c->nbin, c->pref, st);
+    float trb = 3.4e38f;
+    int rv_best = 0;
+    for (int rv = 0; rv < kRelaxVariants; ++rv) {
+      const float ms = time_it([&] {
+        cudaMemcpyAsync(c->r_old, c->vr, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(c->cc, c->vt, sizeof(double) * L.n, cudaMemcpyDeviceToDevice, st);
+        launch_relax(L, c->r_old, c->cc, c->m, c->id, c->nbin, c->step, st, rv);
+      });
+      if (ms < trb) { trb = ms; rv_best = rv; }
+    }
+    c->relax_variant = rv_best;
+    cudaMemcpyAsync(L.dt_bits, dt_saved, sizeof(uint64_t) * L.n_seg, cudaMemcpyDeviceToDevice,
+                    st);
+  }
   run_orbit(blk_best, var_best);
   // sort shapes on copies of the keys the orbit step produced
   uint64_t* saved = reinterpret_cast<uint64_t*>(c->cc);  // scratch of the same size
@@ -512,6 +539,7 @@ void cmc_config_default(cmc_config* cfg) {
   cfg->autotune = 1;
   cfg->orbit_variant = -1;
   cfg->rng = 0;
+  cfg->relax_variant = -1;
 }
 
 cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
@@ -529,7 +557,8 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
       cfg.max_trials < 1 || cfg.max_trials > (1 << 24) || !(cfg.theta_max > 0.0) ||
       !(cfg.gamma > 0.0) || cfg.orbit_block < 0 || cfg.orbit_block > 256 ||
       (cfg.orbit_block % 32) || cfg.orbit_variant < -1 || cfg.orbit_variant >= kOrbitVariants ||
-      (cfg.rng != 0 && cfg.rng != 1))
+      (cfg.rng != 0 && cfg.rng != 1) || cfg.relax_variant < -1 ||
+      cfg.relax_variant >= kRelaxVariants)
     return fail(nullptr, CMC_EINVAL, "cmc_init: bad configuration");
   std::vector<int64_t> sizes(n_per_cluster, n_per_cluster + n_clusters);
   std::vector<uint64_t> sd(seeds, seeds + n_clusters);
@@ -599,6 +628,7 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
     }
   }
   c->orbit_variant = cfg.orbit_variant > 0 ? cfg.orbit_variant : 0;
+  c->relax_variant = cfg.relax_variant > 0 ? cfg.relax_variant : 0;
   if (cfg.autotune) {
     s = autotune(c);
     if (s != CMC_OK) {
@@ -666,7 +696,7 @@ cmc_status cmc_energy(cmc_ctx* c, double* out) {
   if (!c || !out) return fail(c, CMC_EINVAL, "cmc_energy: bad arguments");
   if (c->poisoned) return fail(c, CMC_EPOISONED, c->last_error);
   DeviceGuard g(c->device);
-  launch_energy(c->L, c->r, c->vr, c->vt, c->m, c->tile_a, c->tile_b, c->tile_c, c->Mbuf,
+  launch_energy(c->L, c->r, c->vr, c->vt, c->m, c->tile_a, c->tile_b, c->tile_c, c->r_old,
                 c->out3, c->stream);
   cudaError_t e = cudaMemcpyAsync(out, c->out3, sizeof(double) * 3 * c->L.n_seg,
                                   cudaMemcpyDeviceToHost, c->stream);
@@ -736,9 +766,9 @@ cmc_status cmc_lagrange_radii(cmc_ctx* c, const double* fracs, int32_t nf, doubl
   if (!e) e = dalloc(dout, (size_t)nf * c->L.n_seg, st);
   if (!e) e = cudaMemcpyAsync(dfr, fracs, sizeof(double) * nf, cudaMemcpyHostToDevice, st);
   if (!e) {
-    launch_energy(c->L, c->r, c->vr, c->vt, c->m, c->tile_a, c->tile_b, c->tile_c, c->Mbuf,
+    launch_energy(c->L, c->r, c->vr, c->vt, c->m, c->tile_a, c->tile_b, c->tile_c, c->r_old,
                   c->out3, st);
-    launch_lagrange(c->L, c->r, c->Mbuf, dfr, nf, dout, st);
+    launch_lagrange(c->L, c->r, c->r_old, dfr, nf, dout, st);
     e = cudaMemcpyAsync(out, dout, sizeof(double) * nf * c->L.n_seg, cudaMemcpyDeviceToHost,
                         st);
   }
@@ -844,6 +874,7 @@ cmc_status cmc_get_tuning(const cmc_ctx* c, int32_t* out) {
   out[1] = c->W.ipt;
   out[2] = c->W.rank;
   out[3] = c->orbit_variant;
+  out[4] = c->relax_variant;
   return CMC_OK;
 }
 

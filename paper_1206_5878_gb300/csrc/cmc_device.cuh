@@ -42,7 +42,7 @@ enum : uint32_t {
 // per-segment statistics (64-bit counters)
 enum : int {
   kStEscaped = 0, kStDegenerate, kStCapHits, kStTrials, kStViolations,
-  kStClamps, kStAngleFails, kStTies, kStFp64Trials, kStCount
+  kStClamps, kStAngleFails, kStTies, kStFp64Trials, kStClampEnergy, kStCount
 };
 constexpr int kStStride = 16;        // counters reserved per segment
 
@@ -198,59 +198,80 @@ __device__ __forceinline__ double mul_rn(double a, double b) {
 // exact remainder N - Q d, and rounded by comparing twice the remainder
 // with d (ties to even).  If the remainder still lies outside [0, d), the
 // FP64 division is used.
-__device__ __forceinline__ double div_rn(double a, double b) {
-  const unsigned long long ua = ubits(a), vb = ubits(b);
+// The fixed-point reciprocal of a normalised divisor d in [2^63, 2^64):
+// v ~ 2^128 / d - 2^64 (so R = 2^64 + v), seeded by the float reciprocal
+// of d's top 24 bits and refined by two Newton steps.
+__device__ __forceinline__ unsigned long long recip_fixed(unsigned long long d) {
+  // the float of d's top 24 bits, from its bits (2^23 <= d >> 40 < 2^24)
+  const float f = __uint_as_float(0x4B000000u | ((unsigned)(d >> 40) & 0x7FFFFFu));
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
+  const unsigned yb = __float_as_uint(y);
+  // 2^88 y - 2^64 for y in [2^-24, 2^-23); y = 2^-23 (d = 2^63) saturates
+  unsigned long long v =
+      ((yb >> 23) & 0xFFu) == 103u ? (unsigned long long)(yb & 0x7FFFFFu) << 41 : ~0ull;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    // d R - 2^128 = T 2^64 + pl (T signed, small); E = floor((2^128 - d R) / 2^64)
+    const unsigned long long pl = d * v, ph = __umul64hi(d, v);
+    const long long T = (long long)(ph + d);
+    const long long E = -T - (pl != 0ull ? 1 : 0);
+    const unsigned long long aE = E < 0 ? (unsigned long long)(-E) : (unsigned long long)E;
+    const unsigned long long c = __umul64hi(v, aE);  // v |E| / 2^64
+    v = E < 0 ? v + (unsigned long long)E - c : v + (unsigned long long)E + c;
+  }
+  return v;
+}
+
+// a / b from the reciprocal v of d = m_b 2^11 (b normal): false where the
+// quotient needs the FP64 division (a not normal, a result out of the
+// normal range, or a remainder still out of range after the correction).
+__device__ __forceinline__ bool div_by_recip(unsigned long long ua, unsigned long long vb,
+                                             unsigned long long d, unsigned long long v,
+                                             double& out) {
   const unsigned ea = (unsigned)(ua >> 52) & 0x7FFu, eb = (unsigned)(vb >> 52) & 0x7FFu;
   const unsigned long long ma = significand(ua), mb = significand(vb);
   const unsigned s = ma < mb ? 1u : 0u;
   const int e = (int)ea - (int)eb + 1023 - (int)s;
-  if (ea - 1u < 2046u && eb - 1u < 2046u && (unsigned)(e - 1) < 2045u) {
-    const unsigned long long d = mb << 11;  // [2^63, 2^64)
-    // the float of d's top 24 bits, from its bits (2^23 <= d >> 40 < 2^24)
-    const float f = __uint_as_float(0x4B000000u | ((unsigned)(d >> 40) & 0x7FFFFFu));
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(f));
-    const unsigned yb = __float_as_uint(y);
-    // 2^88 y - 2^64 for y in [2^-24, 2^-23); y = 2^-23 (d = 2^63) saturates
-    unsigned long long v =
-        ((yb >> 23) & 0xFFu) == 103u ? (unsigned long long)(yb & 0x7FFFFFu) << 41 : ~0ull;
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-      // d R - 2^128 = T 2^64 + pl (T signed, small); E = floor((2^128 - d R) / 2^64)
-      const unsigned long long pl = d * v, ph = __umul64hi(d, v);
-      const long long T = (long long)(ph + d);
-      const long long E = -T - (pl != 0ull ? 1 : 0);
-      const unsigned long long aE = E < 0 ? (unsigned long long)(-E) : (unsigned long long)E;
-      const unsigned long long c = __umul64hi(v, aE);  // v |E| / 2^64
-      v = E < 0 ? v + (unsigned long long)E - c : v + (unsigned long long)E + c;
-    }
-    // N = u1 2^64 + u0
-    const unsigned long long u1 = s ? ma : ma >> 1, u0 = s ? 0ull : (ma & 1ull) << 63;
-    const unsigned long long ql = v * u1, qh = __umul64hi(v, u1);
-    const unsigned long long q0 = ql + u0;
-    unsigned long long Q = qh + u1 + (q0 < ql ? 1ull : 0ull);
-    // remainder N - Q d as rh 2^64 + rl (rh signed)
-    const unsigned long long pl = Q * d, ph = __umul64hi(Q, d);
-    unsigned long long rl = u0 - pl;
-    long long rh = (long long)(u1 - ph - (u0 < pl ? 1ull : 0ull));
-    if (rh < 0) {
-      const unsigned long long t = rl + d;
-      rh += t < rl ? 1 : 0;
-      rl = t;
-      --Q;
-    } else if (rh > 0 || rl >= d) {
-      const unsigned long long t = rl - d;
-      rh -= rl < d ? 1 : 0;
-      rl = t;
-      ++Q;
-    }
-    if (rh == 0 && rl < d) {
-      const unsigned long long r2 = rl << 1;
-      const bool up = (rl >> 63) != 0ull || r2 > d || (r2 == d && (Q & 1ull));
-      return __longlong_as_double((long long)(((ua ^ vb) & kSignBit) +
-                                              ((unsigned long long)(e - 1) << 52) + Q +
-                                              (up ? 1ull : 0ull)));
-    }
+  if (!(ea - 1u < 2046u && (unsigned)(e - 1) < 2045u)) return false;
+  // N = u1 2^64 + u0
+  const unsigned long long u1 = s ? ma : ma >> 1, u0 = s ? 0ull : (ma & 1ull) << 63;
+  const unsigned long long ql = v * u1, qh = __umul64hi(v, u1);
+  const unsigned long long q0 = ql + u0;
+  unsigned long long Q = qh + u1 + (q0 < ql ? 1ull : 0ull);
+  // remainder N - Q d as rh 2^64 + rl (rh signed)
+  const unsigned long long pl = Q * d, ph = __umul64hi(Q, d);
+  unsigned long long rl = u0 - pl;
+  long long rh = (long long)(u1 - ph - (u0 < pl ? 1ull : 0ull));
+  if (rh < 0) {
+    const unsigned long long t = rl + d;
+    rh += t < rl ? 1 : 0;
+    rl = t;
+    --Q;
+  } else if (rh > 0 || rl >= d) {
+    const unsigned long long t = rl - d;
+    rh -= rl < d ? 1 : 0;
+    rl = t;
+    ++Q;
+  }
+  if (rh == 0 && rl < d) {
+    const unsigned long long r2 = rl << 1;
+    const bool up = (rl >> 63) != 0ull || r2 > d || (r2 == d && (Q & 1ull));
+    out = __longlong_as_double((long long)(((ua ^ vb) & kSignBit) +
+                                           ((unsigned long long)(e - 1) << 52) + Q +
+                                           (up ? 1ull : 0ull)));
+    return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ double div_rn(double a, double b) {
+  const unsigned long long ua = ubits(a), vb = ubits(b);
+  const unsigned eb = (unsigned)(vb >> 52) & 0x7FFu;
+  if (eb - 1u < 2046u) {
+    const unsigned long long d = significand(vb) << 11;  // [2^63, 2^64)
+    double q;
+    if (div_by_recip(ua, vb, d, recip_fixed(d), q)) return q;
   }
   return a / b;
 }
@@ -470,9 +491,8 @@ __device__ __forceinline__ bool disk_angle(Draws<kTaus>& g, uint32_t tag, double
   }
   const double u = sym_double(Ua), v = sym_double(Va);
   const double uu = u * u, vv = v * v, q = uu + vv;
-  const double iq = div_rn(1.0, q);
-  c = (uu - vv) * iq;
-  s = (scale_up<1>(u) * v) * iq;
+  c = div_rn(uu - vv, q);
+  s = div_rn(scale_up<1>(u) * v, q);
   return true;
 }
 
@@ -538,6 +558,15 @@ __device__ __forceinline__ void set_err(uint32_t* err, uint32_t bit) {
 __device__ __forceinline__ void stat_add(unsigned long long* st, int seg, int which,
                                          unsigned long long v) {
   if (v) atomicAdd(st + (size_t)seg * kStStride + which, v);
+}
+
+// The energy a clamp of T' < 0 to 0 adds, m |T'|, into the segment's
+// counter as a fixed-point integer in units of 2^-62 (integer sums do not
+// depend on their order).
+__device__ __forceinline__ void clamp_energy_add(unsigned long long* st, int seg, double m,
+                                                double Tp) {
+  const double e = -(m * Tp) * 4611686018427387904.0;  // 2^62
+  if (e > 0.0) stat_add(st, seg, kStClampEnergy, __double2ull_rn(e));
 }
 
 }  // namespace cmc

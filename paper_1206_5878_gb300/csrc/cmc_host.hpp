@@ -143,19 +143,22 @@ void launch_potential(const SegLayout& L, const double* r, const double* x, cons
                       double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node = nullptr,
                       float4* tdf = nullptr, bool sums_ready = false);
 // node records (and float-pair table) from the arrays (stage calls)
+void launch_node_slopes(const SegLayout& L, bool nb_sub, const double* r, const double* x,
+                        const double* phi, double* M, double4_32a* node, cudaStream_t st);
 void launch_make_nodes(int64_t n, const double* r, const double* x, const double* phi,
                        const double* M, double4_32a* node, float4* tdf, cudaStream_t st);
 
 void launch_correction(const SegLayout& L, const double* r, const double* x,
                        const double* phi, double* vr, double* vt, const double* r_old,
-                       const double* c, bool nb_sub, uint32_t* err, cudaStream_t st);
+                       const double* c, bool nb_sub, uint32_t* err, cudaStream_t st,
+                       const double* m = nullptr);
 
 void launch_bins(const SegLayout& L, const double* r, const double* vr, const double* vt,
                  const double* m, double* nbin, double pref, cudaStream_t st);
 
 void launch_relax(const SegLayout& L, double* vr, double* vt, const double* m,
                   const uint32_t* id, const double* nbin, const uint32_t* step,
-                  cudaStream_t st);
+                  cudaStream_t st, int variant = 0);
 
 struct OrbitStageOut {   // optional per-star outputs of the orbit stage
   double* phi_new = nullptr;
@@ -244,6 +247,7 @@ void launch_turning(const SegLayout& L, const double* r, const double* x, const 
 // registers; the kernel is latency-bound, and occupancy buys more than the
 // spills cost)
 constexpr int kOrbitVariants = 7;
+constexpr int kRelaxVariants = 3;  // relaxation kernel register caps (launch_relax)
 
 // commits the step: nb, escaper statistics and budget (from the gathered
 // r_old and c of the escaped range), dt; resets the per-step counters
@@ -252,7 +256,7 @@ constexpr int kOrbitVariants = 7;
 void launch_correction_mixed(const SegLayout& L, const double* r, const double* x,
                              const double* phi, const double* Menc,
                              const BucketArgs& ba, double* vr, double* vt, const double* r_old,
-                             const double* c, cudaStream_t st);
+                             const double* c, const double* m, cudaStream_t st);
 
 void launch_step_end(const SegLayout& L, uint32_t* step, const double* r_old, const double* c,
                      const double* m, cudaStream_t st);

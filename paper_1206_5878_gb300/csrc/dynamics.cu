@@ -85,9 +85,10 @@ __global__ void __launch_bounds__(256) k_bins(Seg S, int bs, double pref, const 
 
 // One thread per pair slot: stars a = 2j and b = 2j + 1 of a segment.  The
 // pair's random draws come from its first star (counters keyed by its id,
-// or its stream, kept after the draws).
-template <bool kTaus>
-__global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double* vt,
+// or its stream, kept after the draws).  kMinB: resident 128-thread blocks
+// to fit per SM (caps the registers; 1 = no cap), a launch shape only.
+template <bool kTaus, int kMinB>
+__global__ void __launch_bounds__(128, kMinB) k_relax(Seg S, int bs, double* vr, double* vt,
                                                const double* m, const uint32_t* id,
                                                const double* nbin, const uint32_t* step_p) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   if (!le1(s2)) s2 = 1.0;
   // cos(beta) = 1 - 2 sin^2(beta/2), sin(beta) = 2 sin(beta/2) cos(beta/2)
   const double cosb = 1.0 - scale_up<1>(s2);
-  const double sinb = scale_up<1>(sqrt_rn(s2 * (1.0 - s2)));
+  const double sinb = scale_up<1>(sqrt_rn(s2)) * sqrt_rn(1.0 - s2);
   if (!disk_angle(g, kTagPhi, cphi, sphi)) ++fails;
   draws_keep(S, c, g);
   // e1 = (w x xhat)/|w x xhat| = (0, wz, -wy)/|.| (yhat for radial w);
@@ -137,9 +138,9 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   const double wp2 = wy * wy + wz * wz;
   double e1y, e1z;
   if (pos_num(wp2)) {
-    const double iwp = div_rn(1.0, sqrt_rn(wp2));
-    e1y = wz * iwp;
-    e1z = -(wy * iwp);
+    const double wp = sqrt_rn(wp2);
+    e1y = div_rn(wz, wp);
+    e1z = div_rn(-wy, wp);
   } else {
     e1y = 1.0;
     e1z = 0.0;
@@ -153,11 +154,11 @@ __global__ void __launch_bounds__(128) k_relax(Seg S, int bs, double* vr, double
   const double wpy = wy * cosb + sinb * (a1 * e1y + sphi * uy);
   const double wpz = wz * cosb + sinb * (a1 * e1z + sphi * uz);
   const double dwx = wpx - wx, dwy = wpy - wy, dwz = wpz - wz;
-  const double im = div_rn(1.0, msum);
-  // these eight products on the integer pipes balance the FP64 pipe's load
-  // against the integer pipes' (measured: all of the kernel's products there
-  // made it a third slower, none of them 2% slower)
-  const double f1 = mul_rn(m2, im), f2 = mul_rn(m1, im);
+  // the mass ratios as quotients; these products on the integer pipes
+  // balance the FP64 pipe's load against the integer pipes' (measured: all
+  // of the kernel's products there made it a third slower, none of them 2%
+  // slower)
+  const double f1 = div_rn(m2, msum), f2 = div_rn(m1, msum);
   const double p1x = v1x + mul_rn(f1, dwx), p1y = v1y + mul_rn(f1, dwy), p1z = v1z + mul_rn(f1, dwz);
   const double p2x = v2x - mul_rn(f2, dwx), p2y = v2y - mul_rn(f2, dwy), p2z = v2z - mul_rn(f2, dwz);
   vr[a] = p1x;
@@ -207,15 +208,26 @@ void launch_bins(const SegLayout& L, const double* r, const double* vr, const do
                                                              vt, m, nbin);
 }
 
-void launch_relax(const SegLayout& L, double* vr, double* vt, const double* m,
-                  const uint32_t* id, const double* nbin, const uint32_t* step,
-                  cudaStream_t st) {
-  if (!L.n_pairs) return;
+template <int kMinB>
+static void relax_shape(const SegLayout& L, double* vr, double* vt, const double* m,
+                        const uint32_t* id, const double* nbin, const uint32_t* step,
+                        cudaStream_t st) {
   const unsigned grid = (unsigned)((L.n_pairs + 127) / 128);
   if (L.taus)
-    k_relax<true><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin, step);
+    k_relax<true, kMinB><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin, step);
   else
-    k_relax<false><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin, step);
+    k_relax<false, kMinB><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin,
+                                                step);
+}
+
+void launch_relax(const SegLayout& L, double* vr, double* vt, const double* m,
+                  const uint32_t* id, const double* nbin, const uint32_t* step,
+                  cudaStream_t st, int variant) {
+  if (!L.n_pairs) return;
+  // variants: registers capped for 1 (no cap), 6 or 8 resident blocks per SM
+  if (variant == 1) relax_shape<6>(L, vr, vt, m, id, nbin, step, st);
+  else if (variant == 2) relax_shape<8>(L, vr, vt, m, id, nbin, step, st);
+  else relax_shape<1>(L, vr, vt, m, id, nbin, step, st);
 }
 
 }  // namespace cmc

@@ -1181,7 +1181,7 @@ __global__ void __launch_bounds__(128, 12) k_correction_mixed(Seg S, const int64
                                                           const double* Menc, BucketArgs BA,
                                                           double* vr, double* vt,
                                                           const double* r_old, const double* cc,
-                                                          int64_t n) {
+                                                          const double* m, int64_t n) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int c = seg_find(S.off, S.n_seg, p);
@@ -1209,7 +1209,11 @@ __global__ void __launch_bounds__(128, 12) k_correction_mixed(Seg S, const int64
   const double dnew = pn - phi[p];
   double Tp = Tk + scale_down<1>(dnew - cc[p]);
   bool clamp = false;
-  if (lt0(Tp)) { Tp = 0.0; clamp = true; }
+  if (lt0(Tp)) {
+    clamp_energy_add(S.stats, c, m[p], Tp);
+    Tp = 0.0;
+    clamp = true;
+  }
   if (pos_num(Tk)) {
     const double f = sqrt_rn(div_rn(Tp, Tk));
     vr[p] = a * f;
@@ -1417,10 +1421,10 @@ void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWo
 void launch_correction_mixed(const SegLayout& L, const double* r, const double* x,
                              const double* phi, const double* Menc,
                              const BucketArgs& ba, double* vr, double* vt, const double* r_old,
-                             const double* c, cudaStream_t st) {
+                             const double* c, const double* m, cudaStream_t st) {
   if (!L.n) return;
   k_correction_mixed<<<(unsigned)((L.n + 127) / 128), 128, 0, st>>>(
-      L.dev(), L.esc_step, r, x, phi, Menc, ba, vr, vt, r_old, c, L.n);
+      L.dev(), L.esc_step, r, x, phi, Menc, ba, vr, vt, r_old, c, m, L.n);
 }
 
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,

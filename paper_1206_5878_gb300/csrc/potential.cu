@@ -406,7 +406,8 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(Seg S, const int64_t*
 // Phi_old(r_new))], clamped at 0; both components scaled by sqrt(T'/T).
 __global__ void k_correction(Seg S, const int64_t* esc, bool sub, const double* r,
                              const double* x, const double* phi, double* vr, double* vt,
-                             const double* r_old, const double* cc, int64_t n) {
+                             const double* r_old, const double* cc, const double* m,
+                             int64_t n) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   bool active = p < n;
   int c = 0;
@@ -425,7 +426,11 @@ __global__ void k_correction(Seg S, const int64_t* esc, bool sub, const double* 
     double Tk = scale_down<1>(a * a + b * b);
     double dnew = phi_of_r(T, r_old[p]) - phi[p];
     double Tp = Tk + scale_down<1>(dnew - cc[p]);
-    if (Tp < 0.0) { Tp = 0.0; clamp = 1; }
+    if (Tp < 0.0) {
+      if (m) clamp_energy_add(S.stats, c, m[p], Tp);
+      Tp = 0.0;
+      clamp = 1;
+    }
     if (Tk > 0.0) {
       double f = sqrt_rn(div_rn(Tp, Tk));
       vr[p] = a * f;
@@ -479,7 +484,7 @@ __global__ void __launch_bounds__(kThreads) k_energy_tiles(Seg S, const double* 
   if (threadIdx.x == 0) { tile_k[blockIdx.x] = tk; tile_w[blockIdx.x] = tw; }
 }
 
-// Core diagnostics (section 4.3, Eq. 19): per bound star k with three
+// Core diagnostics (section 4.2, Eq. 19): per bound star k with three
 // neighbours on each side, the 6th-order density estimate in the radial
 // order, rho_k = (m_{k-2} + ... + m_{k+2}) / (4 pi / 3 (r_{k+3}^3 - r_{k-3}^3));
 // per tile the sums of rho, rho^2, rho r and the number of estimates, each
@@ -705,6 +710,30 @@ __global__ void k_make_nodes(int64_t n, const double* r, const double* x, const 
   tdf[p] = float_pairs(x[p], phi[p]);
 }
 
+// Mixed mode's FP64 tables after the potential, per segment: the slope of
+// Eq. 6 in 1/r across each shell, (Phi_{k+1} - Phi_k) / (x_k - x_{k+1})
+// (Phi = 0 at 1/r = 0 beyond the last bound star), the shell parameter B
+// the FP64 orbit step takes for its roots, into M and the node records
+// {r, 1/r, Phi, slope}.  Stars beyond the bound ones get slope 0.
+__global__ void k_node_slopes(Seg S, const int64_t* esc, bool sub, int64_t n, const double* r,
+                              const double* x, const double* phi, double* M,
+                              double4_32a* node) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int c = seg_find(S.off, S.n_seg, p);
+  const int64_t k = p - __ldg(S.off + c);
+  const int64_t nbc = nb_eff(S.nb, esc, c, sub);
+  const double xj = x[p], pj = phi[p];
+  double sl = 0.0;
+  if (k < nbc) {
+    const bool last = k + 1 >= nbc;
+    const double xj1 = last ? 0.0 : x[p + 1], pj1 = last ? 0.0 : phi[p + 1];
+    sl = div_rn(pj1 - pj, xj - xj1);
+  }
+  M[p] = sl;
+  node[p] = make_double4_32a(r[p], xj, pj, sl);
+}
+
 __global__ void k_unpack_orbit(int64_t n, const uint64_t* keys, const Payload* pay,
                                double* r_new, double* vr_new, double* vt_new) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -731,6 +760,13 @@ void launch_recip(int64_t n, const double* r, double* x, cudaStream_t st) {
 void launch_make_t32(int64_t n, const double* x, const double* phi, float2* t32,
                      cudaStream_t st) {
   if (n > 0) k_make_t32<<<blocks_for(n, 256), 256, 0, st>>>(n, x, phi, t32);
+}
+
+void launch_node_slopes(const SegLayout& L, bool nb_sub, const double* r, const double* x,
+                        const double* phi, double* M, double4_32a* node, cudaStream_t st) {
+  if (L.n > 0)
+    k_node_slopes<<<blocks_for(L.n, 256), 256, 0, st>>>(L.dev(), L.esc_step, nb_sub, L.n, r, x,
+                                                        phi, M, node);
 }
 
 void launch_make_nodes(int64_t n, const double* r, const double* x, const double* phi,
@@ -862,11 +898,12 @@ void launch_potential(const SegLayout& L, const double* r, const double* x, cons
 
 void launch_correction(const SegLayout& L, const double* r, const double* x,
                        const double* phi, double* vr, double* vt, const double* r_old,
-                       const double* c, bool nb_sub, uint32_t* err, cudaStream_t st) {
+                       const double* c, bool nb_sub, uint32_t* err, cudaStream_t st,
+                       const double* m) {
   (void)err;
   if (!L.n) return;
   k_correction<<<blocks_for(L.n, 128), 128, 0, st>>>(L.dev(), L.esc_step, nb_sub, r, x, phi,
-                                                    vr, vt, r_old, c, L.n);
+                                                    vr, vt, r_old, c, m, L.n);
 }
 
 void launch_energy(const SegLayout& L, const double* r, const double* vr, const double* vt,

@@ -1,11 +1,10 @@
 // cmc_potential_static: the shell potential of cmc_potential for callers
 // that may not allocate device memory.
 //
-// Some callers cannot let a library allocate: code that runs while a CUDA
-// stream is being captured into a graph (an allocation there would either
-// fail or become part of the graph), real-time loops that forbid any
-// allocation after start-up, and programs that hand all device memory to
-// their own pool.  This entry point needs nothing from the allocator: its
+// Some callers cannot let a library allocate: real-time loops that forbid
+// any allocation after start-up (an allocation can block, synchronise or
+// fail), programs that hand all device memory to their own pool, and
+// plug-ins whose host application owns the allocator.  This entry point needs nothing from the allocator: its
 // only scratch, the per-tile sums of the scan, lives in a fixed array in
 // the library's own device memory, reserved when the library is loaded and
 // kept by every GPU that loads it until the process exits.
@@ -133,7 +132,8 @@ __global__ void __launch_bounds__(kThreads) k_static_potential(int64_t n, int64_
   }
 }
 
-// device address of g_tile_scratch, resolved once per device
+// device address of g_tile_scratch, resolved once per device and kept for
+// the life of the process (a device reset would invalidate it)
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 double* g_addr[kMaxDevices] = {};
@@ -169,7 +169,9 @@ cmc_status cmc_potential_static(int64_t n, const double* r, const double* m, dou
   k_static_tile_sums<<<(unsigned)n_tiles, kThreads, 0, st>>>(n, r, m, scratch);
   k_static_potential<<<(unsigned)n_tiles, kThreads, 0, st>>>(n, n_tiles, r, m, scratch, phi,
                                                              M);
-  return cudaGetLastError() == cudaSuccess ? CMC_OK : CMC_ECUDA;
+  // peek: an error left by someone else's earlier work is reported, not
+  // cleared
+  return cudaPeekAtLastError() == cudaSuccess ? CMC_OK : CMC_ECUDA;
 }
 
 }  // extern "C"

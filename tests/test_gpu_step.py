@@ -98,10 +98,11 @@ def test_ten_steps_plummer_1e4_fp64(g, orc):
     """Plummer N = 10^4, FP64, 10 steps against the oracle: total energy
     (bound stars plus what the escapers took) conserved to the paper's
     bound on both sides and the same statistics.
-    The potentials of the two sides differ in the last bits (other
-    summation order); star-by-star agreement holds for one step from the
-    same state (test_one_step_matches_oracle) and bit for bit stage by
-    stage (test_gpu_stages.py), not along a 10-step trajectory."""
+    Here each side runs its own trajectory: the potentials of the two sides
+    differ in the last bits (other summation order), which the orbits
+    amplify step by step.  Star-by-star agreement along the same 10 steps,
+    with the state handed to the oracle before each step, is
+    test_gpu_parity_steps.py's."""
     d = ic.plummer(10_000, seed=1)
     c = _cluster(g, d, 1)
     o = orc.Cluster(d["r"], d["vr"], d["vt"], d["m"], d["id"], seed=1, pot_mode="dd")
@@ -191,13 +192,13 @@ def test_resume_is_bit_identical(g):
 def test_launch_shape_does_not_change_bits(g, precision):
     d = ic.plummer(20_000, seed=4)
     outs = []
-    shapes = [(32, 0), (128, 0), (256, 0)]
+    shapes = [(32, 0, 0), (128, 0, 1), (256, 0, 2)]
     if precision == 1:
-        shapes += [(64, v) for v in range(1, 7)]
-    for blk, var in shapes:
+        shapes += [(64, v, v % 3) for v in range(1, 7)]
+    for blk, var, rv in shapes:
         c = _cluster(g, d, 4, orbit_block=blk, precision=precision, orbit_variant=var,
-                     autotune=0)
-        assert c.tuning()["orbit_variant"] == var
+                     relax_variant=rv, autotune=0)
+        assert c.tuning()["orbit_variant"] == var and c.tuning()["relax_variant"] == rv
         c.step(2)
         outs.append((c.get_state(), c.stats()))
     for o, st in outs[1:]:
@@ -213,7 +214,8 @@ def test_autotuned_shapes_do_not_change_bits(g, precision):
     b = _cluster(g, d, 6, autotune=1, precision=precision)
     ta, tb = a.tuning(), b.tuning()
     assert ta == {"orbit_block": 64, "sort_keys_per_thread": 16, "sort_multisplit": "match",
-                  "orbit_variant": 0}
+                  "orbit_variant": 0, "relax_variant": 0}
+    assert tb["relax_variant"] in (0, 1, 2)
     assert tb["orbit_block"] in (64, 128, 256) and tb["sort_keys_per_thread"] in (8, 16)
     assert b.stats()[0]["trials"] == 0  # the tuner's dry run left no trace
     a.step(3)
@@ -285,7 +287,8 @@ def test_invalid_inputs_are_rejected(g):
         with pytest.raises(g.CMCError) as ei:
             _cluster(g, e, 1)
         assert ei.value.status == 1  # CMC_EINVAL
-    for bad_cfg in ({"orbit_variant": 7}, {"orbit_variant": -2}, {"orbit_block": 48}):
+    for bad_cfg in ({"orbit_variant": 7}, {"orbit_variant": -2}, {"orbit_block": 48},
+                    {"relax_variant": 3}, {"relax_variant": -2}):
         with pytest.raises(g.CMCError):
             _cluster(g, d, 1, **bad_cfg)
     c = _cluster(g, d, 1)

@@ -1,4 +1,4 @@
-"""Pins of the oracle's core diagnostics (section 4.3, Eq. 19): the radial
+"""Pins of the oracle's core diagnostics (section 4.2, Eq. 19): the radial
 6th-order density estimator, rho_c = sum rho_i^2 / sum rho_i and the
 density-weighted core radius, against what geometry and probability fix:
 

@@ -214,6 +214,34 @@ def test_kepler_radius_distribution(orc):
     assert sst.kstest(u, cdf).pvalue < 1e-6
 
 
+def test_orbit_with_a_given_envelope(orc):
+    """The envelope hook: passing the step's own F changes nothing; a wider
+    envelope (2F, still a bound on g) takes more trials and samples the
+    same distribution: the Kepler time-fraction CDF passes its KS test."""
+    r, m, g = _kepler_table(200, seed=2)
+    phi = orc.potential(r, m, "dd")
+    k, vr, vt = 100, 0.3, 0.45
+    a = orc.orbit_star(k, r, phi, vr, vt, 42, 77, 0)
+    for step in range(50):
+        x = orc.orbit_star(k, r, phi, vr, vt, 42, 77, step)
+        y = orc.orbit_star(k, r, phi, vr, vt, 42, 77, step, F=x["F"])
+        for key in ("r_new", "vr", "vt", "phi_new", "rmin", "rmax", "F", "trials"):
+            assert x[key] == y[key], key
+    rmin, rmax = a["rmin"], a["rmax"]
+    wide = [orc.orbit_star(k, r, phi, vr, vt, 42, 77, st, F=2 * a["F"]) for st in range(20000)]
+    assert all(o["code"] == 0 for o in wide)
+    assert np.mean([o["trials"] for o in wide]) > 1.5 * np.mean(
+        [orc.orbit_star(k, r, phi, vr, vt, 42, 77, st)["trials"] for st in range(2000)])
+    ae, e = 0.5 * (rmax + rmin), (rmax - rmin) / (rmax + rmin)
+
+    def cdf(x):
+        ce = np.clip((1 - np.asarray(x) / ae) / e, -1, 1)
+        eta = np.arccos(ce)
+        return (eta - e * np.sin(eta)) / np.pi
+
+    assert sst.kstest([o["r_new"] for o in wide], cdf).pvalue > 1e-3
+
+
 @pytest.fixture(scope="module")
 def plummer_table(orc):
     d = ic.plummer(3000, seed=8, masses="salpeter")
@@ -356,7 +384,7 @@ def test_orbit_plus_correction_conserves_energy(orc, masses):
 
 def test_ten_steps_energy_drift_within_paper_bound(orc):
     """The paper conserves total energy to better than 0.04% (section 4.2)
-    and loses at most ~1% of the mass over a whole run (section 4.3)."""
+    and loses at most ~1% of the mass over a whole run (section 4.2)."""
     d = ic.plummer(10_000, seed=1)
     c = orc.Cluster(d["r"], d["vr"], d["vt"], d["m"], d["id"], seed=1)
     E0 = c.energy()[2]

@@ -1,9 +1,9 @@
 """cmc_potential_static, the allocation-free variant of cmc_potential.
 
-Callers that may not allocate device memory (code running during stream
-capture, allocation-free real-time loops, programs that own all device
-memory through their own pool) use this entry point; its scratch is a fixed
-array of the library's device memory.  It must give what cmc_potential
+Callers that may not allocate device memory (allocation-free real-time
+loops, programs that own all device memory through their own pool, plug-ins
+whose host application owns the allocator) use this entry point; its scratch
+is a fixed array of the library's device memory.  It must give what cmc_potential
 gives, call after call, even though every call reuses the same array.
 This file is collected last on purpose.
 """
@@ -41,6 +41,15 @@ def test_static_potential_equals_allocating_potential_on_consecutive_calls(orc):
         assert np.max(np.abs(host(M) / host(M_ref) - 1)) < 1e-12
         # and the oracle agrees
         assert np.max(np.abs(a / orc.potential(s["r"], s["m"], "dd") - 1)) < 1e-12
+    # a call after the first on this device takes no device memory: the
+    # free memory the driver reports is the same before and after it
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    assert lib.cmc_potential_static(n, r.data_ptr(), m.data_ptr(), phi.data_ptr(),
+                                    M.data_ptr(), stream) == 0
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    np.testing.assert_array_equal(host(phi), a)  # and repeats its bits
 
 
 def test_static_potential_limits():
