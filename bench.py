@@ -186,9 +186,7 @@ def oracle_sample_step(state, n_orbit: int, seed: int, step: int):
     ks = rng.choice(n, size=min(n_orbit, n), replace=False)
     rn = r.copy()
     tt = time.perf_counter()
-    for k in ks:
-        o = oracle.orbit_star(int(k), r, phi, vr2[k], vt2[k], int(ids[k]), seed, step)
-        rn[k] = o["r_new"]
+    rn[ks] = oracle.orbit_sample(r, phi, vr2, vt2, ids, ks, seed, step)
     t2 = time.perf_counter()
     perm = oracle.sort_perm(rn, ids)
     t3 = time.perf_counter()
@@ -199,6 +197,82 @@ def oracle_sample_step(state, n_orbit: int, seed: int, step: int):
     whole = (t1 - t0) + (t4 - t2)
     del perm
     return whole + per_star_sample * n
+
+
+def host_cpu():
+    """CPU model and core count of this host (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.TimeoutExpired):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"model": model or "unknown", "nproc": os.cpu_count()}
+
+
+def oracle_full_steps(n: int, steps: int, seed: int = 1):
+    """The oracle's complete timestep (every stage, every star, one core) on
+    a Plummer cluster of n stars, measured over `steps` steps."""
+    import initial_conditions as ic
+    import oracle
+    oracle.build()
+    d = ic.plummer(n, seed=seed)
+    o = oracle.Cluster(d["r"], d["vr"], d["vt"], d["m"], d["id"], seed=seed)
+    t0 = time.perf_counter()
+    o.step(steps)
+    sec = time.perf_counter() - t0
+    return {"n_stars": n, "steps": steps, "value": n * steps / sec, "unit": UNIT,
+            "ms_per_step": 1e3 * sec / steps, "cores": 1, "kind": "oracle",
+            "sample": "complete oracle timesteps of a Plummer N=%d cluster, measured" % n}
+
+
+def _ensemble_worker(args):
+    """One process: one complete oracle timestep of each cluster assigned to
+    it (the clusters of the 64-cluster ensemble)."""
+    rank, nproc = args
+    import initial_conditions as ic
+    import oracle
+    oracle.build()
+    sizes = ic.ensemble_sizes(64, 1)
+    done = 0
+    sec = 0.0
+    for c in range(rank, len(sizes), nproc):
+        d = ic.plummer(int(sizes[c]), 1000 + c)
+        o = oracle.Cluster(d["r"], d["vr"], d["vt"], d["m"], d["id"], seed=1000 + c)
+        t0 = time.perf_counter()
+        o.step(1)
+        sec += time.perf_counter() - t0
+        done += int(sizes[c])
+    return done, sec
+
+
+def oracle_ensemble_per_core():
+    """The 64-cluster ensemble on the host: one oracle process per core
+    (spawned), each taking every nproc-th cluster through one complete
+    timestep.  Rate = all clusters' stars / the slowest process's stepping
+    time."""
+    import multiprocessing as mp
+    nproc = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(nproc) as pool:
+        res = pool.map(_ensemble_worker, [(r, nproc) for r in range(nproc)])
+    stars = sum(r[0] for r in res)
+    sec = max(r[1] for r in res)
+    return {"value": stars / sec, "unit": UNIT, "cores": nproc, "kind": "oracle",
+            "sample": "one complete oracle timestep of each of the 64 ensemble clusters "
+                      "(%d stars), one process per core, measured" % stars}
 
 
 def build_oracle_state(n: int, seed: int):
@@ -219,10 +293,12 @@ def cpu_baseline(n: int, seed: int, n_orbit: int = 50_000):
     st = build_oracle_state(n, seed)
     sec = oracle_sample_step(st, n_orbit, seed, 0)
     return {"value": n / sec, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "estimated_from_sample": True, "orbit_sample_stars": n_orbit,
             "sample": ("one oracle timestep of the N=%d Plummer cluster: Eq. 7 bins, "
-                       "relaxation, sort, potential and energy correction on all stars, the "
-                       "orbit step on %d random stars scaled to N (FP64, one core)"
-                       % (n, n_orbit))}
+                       "relaxation, sort, potential and energy correction measured on all "
+                       "stars, the orbit step measured on %d random stars and its time "
+                       "scaled to N (FP64, one core)" % (n, n_orbit)),
+            "host": host_cpu()}
 
 
 # ------------------------------------------------------------------ suite
@@ -309,6 +385,14 @@ def cpu_baseline_full(n: int, masses: str) -> float:
 
 # ------------------------------------------------------------------- arms
 def run_reference(args, rank, world):
+    """The oracle on the host cores, on the GPU arm's workload (Plummer N
+    stars, seed), each step a bounded sample of it: the O(N) stages (Eq. 7
+    bins, relaxation, sort, potential, energy correction) on all N stars and
+    the orbit step on a random sample of stars against the full table.
+    The rate is the oracle's per-star-update cost measured on that sample,
+    1 / (t_all_stages / N + t_orbit / n_sample): an estimate of a whole
+    N-star step, never a timed one (a whole step of 10^7 stars takes the
+    oracle minutes); ms_per_step is the sampled step's measured wall time."""
     if rank != 0:
         return
     import oracle
@@ -318,24 +402,33 @@ def run_reference(args, rank, world):
     n_orbit = args.ref_orbit_sample
     for w in range(args.warmup):
         oracle_sample_step(st, n_orbit, args.seed, w)
-    tot = 0.0
+    est, wall = 0.0, 0.0
     for k in range(args.steps):
-        tot += oracle_sample_step(st, n_orbit, args.seed, args.warmup + k)
-    value = args.n * args.steps / tot
-    sample = ("per step: Eq. 7 bins, relaxation, sort, potential and energy correction on "
-              "all %d stars, the orbit step on %d random stars scaled to N (FP64, one core)"
-              % (args.n, n_orbit))
+        t0 = time.perf_counter()
+        est += oracle_sample_step(st, n_orbit, args.seed, args.warmup + k)
+        wall += time.perf_counter() - t0
+    value = args.n * args.steps / est
+    sample = ("per step: Eq. 7 bins, relaxation, sort, potential and energy correction "
+              "measured on all %d stars, the orbit step measured on %d random stars; the "
+              "rate is N / (t_stages + t_orbit N / %d) (FP64, one core)"
+              % (args.n, n_orbit, n_orbit))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "Plummer N=%d equal-mass, fp64 orbits" % args.n,
+            "config": {"workload": "Plummer N=%d equal-mass, fp64 orbits (oracle; orbit "
+                                   "step sampled on %d stars per step)" % (args.n, n_orbit),
                        "n_stars": args.n, "precision": "fp64 (the oracle on the host)",
                        "seed": args.seed, "parallelism": "single"},
+            "estimated_from_sample": True,
+            "estimated_ms_per_full_step": 1e3 * est / args.steps,
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": sample},
+                             "estimated_from_sample": True, "orbit_sample_stars": n_orbit,
+                             "sample": sample, "host": host_cpu()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
+    if args.ref_full:
+        line["measured_full_step"] = oracle_full_steps(100_000, 2, args.seed)
     print(json.dumps(line), flush=True)
 
 
@@ -497,6 +590,9 @@ def run_cmc(args, rank, world, local_rank):
     if rank == 0 and args.cpu and world == 1:
         log("cpu baseline: oracle on a sample of the workload")
         out["cpu_baseline"] = cpu_baseline(n, args.seed, args.cpu_orbit_sample)
+        log("cpu baseline: complete oracle steps at N=1e5, and the ensemble on every core")
+        out["cpu_baseline"]["measured_full_step"] = oracle_full_steps(100_000, 2, args.seed)
+        out["cpu_baseline"]["ensemble_per_core"] = oracle_ensemble_per_core()
     if rank == 0:
         print(json.dumps(out), flush=True)
 
@@ -518,6 +614,8 @@ def main():
     ap.add_argument("--no-cpu", dest="cpu", action="store_false")
     ap.add_argument("--cpu-orbit-sample", type=int, default=50_000)
     ap.add_argument("--ref-orbit-sample", type=int, default=20_000)
+    ap.add_argument("--no-ref-full", dest="ref_full", action="store_false",
+                    help="reference arm: skip the measured complete oracle steps at N=1e5")
     ap.add_argument("--suite", action="store_true",
                     help="run every measured workload (one JSON line each) instead of the "
                          "N=1e7 benchmark line")
