@@ -306,6 +306,18 @@ cmc_status cmc_energy_correction(int64_t n, const double *r, const double *phi, 
                                  double *vt, const double *r_old, const double *c,
                                  void *stream);
 
+/* Limits of the sort's bounded device waits on the current device, for all
+ * contexts and stage calls there (read by the kernels at launch, so graphs
+ * captured earlier follow them): lookback_polls = polls of an earlier
+ * tile's look-back word before a tile gives up on it (the step then
+ * returns CMC_ETIMEOUT and the context is poisoned; cmc_sort_radius
+ * returns CMC_ETIMEOUT); tie_moves = moves of the insertion sort that puts a
+ * run of equal sort keys in id order before it gives up on the run (a step
+ * then fails, cmc_sort_radius falls back to sorting by id, then by radius).
+ * Values <= 0 restore the defaults (2^22 each).  Returns CMC_ECUDA if the
+ * device cannot be reached. */
+cmc_status cmc_set_wait_limits(int32_t lookback_polls, int64_t tie_moves);
+
 /* ---------------------------------------------------------------------
  * Allocation-free shell potential.  The paper has no counterpart: this is
  * cmc_potential (the same scan over the same tiles, with summation orders

@@ -304,6 +304,12 @@ def stage_energy_correction(r, phi, vr, vt, r_old, c, stream=None):
     return vr, vt
 
 
+def set_wait_limits(lookback_polls: int = 0, tie_moves: int = 0):
+    """Limits of the sort's bounded device waits on the current device
+    (cmc_set_wait_limits; 0 restores the defaults)."""
+    check(load().cmc_set_wait_limits(int(lookback_polls), int(tie_moves)))
+
+
 def check_arith(op: int, n: int, seed: int = 1) -> int:
     """Mismatches between the kernels' integer-pipe FP64 operation `op`
     (0 product, 1 quotient, 2 square root) and the FP64 hardware one over

@@ -70,6 +70,7 @@ SIGNATURES = {
     "cmc_energy_correction": (_i32, [_i64, _p, _p, _p, _p, _p, _p, _p]),
     "cmc_potential_static": (_i32, [_i64, _p, _p, _p, _p, _p]),
     "cmc_check_arith": (_i32, [_i32, _u64, _u64, _p]),
+    "cmc_set_wait_limits": (_i32, [_i32, _i64]),
 }
 
 _lib = None

@@ -169,10 +169,10 @@ void order_state(cmc_ctx* c, cudaStream_t st) {
   launch_nb_from_keys(L, c->keys, st);
   cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
   const bool mixed = c->cfg.precision == 1;
-  launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32, nullptr, false,
-                   st, nullptr, mixed ? c->bk.tdf : nullptr);
+  launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32,
+                   mixed ? c->Mbuf : nullptr, false, st, mixed ? c->bk.node : nullptr,
+                   mixed ? c->bk.tdf : nullptr, false, true);
   if (mixed) {
-    launch_node_slopes(L, false, c->r, c->x, c->phi, c->Mbuf, c->bk.node, st);
     launch_buckets(L, c->t32, false, c->bk, st);
     launch_grid(L, c->x, c->phi, c->Mbuf, false, c->bk, st);
   }
@@ -213,13 +213,13 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   launch_gather(L, sk, sv, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old, c->cc, st,
                 c->tile_a, c->tile_b);
   mark(6);
+  // mixed mode's tables carry the shell slopes of the FP64 orbit step (not
+  // the scan's enclosed masses): its turning points and points are then
+  // FP64 mode's
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
-                   mixed ? c->t32 : nullptr, nullptr, true, st, nullptr,
-                   mixed ? c->bk.tdf : nullptr, true);
+                   mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, true, st,
+                   mixed ? c->bk.node : nullptr, mixed ? c->bk.tdf : nullptr, true, true);
   if (mixed) {
-    // the shell slopes of the FP64 orbit step (not the scan's enclosed
-    // masses): the mixed turning points and points are then FP64 mode's
-    launch_node_slopes(L, true, c->r, c->x, c->phi, c->Mbuf, c->bk.node, st);
     launch_buckets(L, c->t32, true, c->bk, st);
     launch_grid(L, c->x, c->phi, c->Mbuf, true, c->bk, st);
   }
@@ -240,8 +240,8 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
 int count_step_kernels(const cmc_ctx* c) {
   // bins, relax, orbit, upsweep, hist scan, 5 passes, tie fix, gather with
   // the tile sums, potential, [turning points, FP32 sampler, FP64
-  // continuation, node slopes, 2 bucket-index + 2 grid kernels],
-  // [correction], step end
+  // continuation, slopes at the tile seams, 2 bucket-index + 2 grid
+  // kernels], [correction], step end
   return 3 + 2 + 5 + 1 + 1 + 1 + (c->cfg.precision == 1 ? 8 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
@@ -919,6 +919,12 @@ cmc_status cmc_rng_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_
   return e ? cuda_fail(nullptr, e, "cmc_rng_philox") : CMC_OK;
 }
 
+cmc_status cmc_set_wait_limits(int32_t lookback_polls, int64_t tie_moves) {
+  cudaError_t e = set_wait_limits(lookback_polls, (long long)tie_moves);
+  if (e) return cuda_fail(nullptr, e, "cmc_set_wait_limits");
+  return CMC_OK;
+}
+
 cmc_status cmc_sort_radius(int64_t n, const double* r, const uint32_t* id, uint32_t* perm,
                            void* stream) {
   if (n < 0 || n >= ((int64_t)1 << 31) || (n > 0 && (!r || !id || !perm)))
@@ -931,6 +937,7 @@ cmc_status cmc_sort_radius(int64_t n, const double* r, const uint32_t* id, uint3
   uint64_t* keys = nullptr;
   uint32_t* err = nullptr;
   cudaError_t e = alloc_sort(W, S.L, 8, st);
+  uint32_t he = 0;
   if (!e) e = dalloc(keys, n, st);
   if (!e) e = dalloc(err, 1, st);
   if (!e) {
@@ -941,7 +948,6 @@ cmc_status cmc_sort_radius(int64_t n, const double* r, const uint32_t* id, uint3
     // bits in (r, id) order
     sort_segments(S.L, W, keys, perm, 3, 5, true, err, st);
     launch_tiefix(S.L, keys, perm, id, 1, err, st, 24);
-    uint32_t he = 0;
     e = cudaMemcpyAsync(&he, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
     if (!e) e = cudaStreamSynchronize(st);
     if (!e && (he & kErrTies)) {
@@ -951,13 +957,18 @@ cmc_status cmc_sort_radius(int64_t n, const double* r, const uint32_t* id, uint3
       sort_segments(S.L, W, keys, perm, 0, 4, true, err, st);
       launch_rekey_radius(S.L, perm, r, id, keys, st);
       sort_segments(S.L, W, keys, perm, 0, 8, false, err, st);
+      if (!e) e = cudaMemcpyAsync(&he, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, st);
+      if (!e) e = cudaStreamSynchronize(st);
     }
     if (!e) e = cudaGetLastError();
   }
   dfree(keys, st);
   dfree(err, st);
   free_sort(W, st);
-  return e ? cuda_fail(nullptr, e, "cmc_sort_radius") : CMC_OK;
+  if (e) return cuda_fail(nullptr, e, "cmc_sort_radius");
+  if (he & kErrTimeout)
+    return fail(nullptr, CMC_ETIMEOUT, "cmc_sort_radius: bounded wait expired in the look-back");
+  return CMC_OK;
 }
 
 cmc_status cmc_potential(int64_t n, const double* r, const double* m, double* phi, double* M,

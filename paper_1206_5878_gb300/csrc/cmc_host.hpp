@@ -137,14 +137,14 @@ void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* val
 // form).  nb_sub: subtract esc_step from nb (after the orbit step).
 // Optional outputs: t32 (float 1/r, Phi), Mout (M_k) and node (the record
 // {r, 1/r, Phi, M_k} of every star: one 32-byte sector per node for the
-// kernels that read a few nodes at random).
+// kernels that read a few nodes at random).  slopes: Mout and the records
+// carry the slope of Eq. 6 across each shell instead of M_k (the shell
+// parameter the FP64 orbit step takes).
 void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
                       double* tile_m, double* tile_mx, double* phi, float2* t32,
                       double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node = nullptr,
-                      float4* tdf = nullptr, bool sums_ready = false);
+                      float4* tdf = nullptr, bool sums_ready = false, bool slopes = false);
 // node records (and float-pair table) from the arrays (stage calls)
-void launch_node_slopes(const SegLayout& L, bool nb_sub, const double* r, const double* x,
-                        const double* phi, double* M, double4_32a* node, cudaStream_t st);
 void launch_make_nodes(int64_t n, const double* r, const double* x, const double* phi,
                        const double* M, double4_32a* node, float4* tdf, cudaStream_t st);
 
@@ -285,6 +285,9 @@ void launch_make_t32(int64_t n, const double* x, const double* phi, float2* t32,
 void launch_unpack_orbit(int64_t n, const uint64_t* keys, const Payload* pay, double* r_new,
                          double* vr_new, double* vt_new, cudaStream_t st);
 void sort_prepare();
+// look-back polls and tie-fix moves before the sort's waits give up (<= 0:
+// the defaults), on the current device
+cudaError_t set_wait_limits(int spin_polls, long long tie_moves);
 void potential_prepare();  // shared-memory limit of the potential kernel
 
 // (r, id) order of staged stars (flag bit 0 set when not) and the largest id

@@ -333,7 +333,8 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(Seg S, const int64_t*
                                                            const double* m, const double* tile_m,
                                                            const double* tile_mx, double* phi,
                                                            float2* t32, double* Mout,
-                                                           double4_32a* node, float4* tdf) {
+                                                           double4_32a* node, float4* tdf,
+                                                           bool slopes) {
   extern __shared__ double smem[];
   double* s_m = smem;               // m, then M_k
   double* s_x = smem + kPad8N;      // x
@@ -395,10 +396,42 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(Seg S, const int64_t*
     const double ph = bound ? s_p[q] : 0.0;
     phi[p] = ph;
     if (t32) t32[p] = make_float2(f32_pair(s_x[q]).hi, f32_pair(ph).hi);
-    if (Mout) Mout[p] = bound ? s_m[q] : 0.0;
-    if (node) node[p] = make_double4_32a(r[p], s_x[q], ph, bound ? s_m[q] : 0.0);
+    // the enclosed mass M_k, or with `slopes` the slope of Eq. 6 in 1/r
+    // across shell k, (Phi_{k+1} - Phi_k) / (x_k - x_{k+1}) with Phi = 0 at
+    // 1/r = 0 beyond the last bound star (the FP64 orbit step's shell
+    // parameter); a tile's last star, whose neighbour is in the next tile,
+    // gets its slope from k_slope_seams
+    double w = bound ? s_m[q] : 0.0;
+    if (slopes) {
+      w = 0.0;
+      if (bound) {
+        if (p + 1 >= R.bound_end) w = div_rn(0.0 - ph, s_x[q] - 0.0);
+        else if (e + 1 < kTile) {
+          const int q1 = pad8(e + 1);
+          w = div_rn(s_p[q1] - ph, s_x[q] - s_x[q1]);
+        }
+      }
+    }
+    if (Mout) Mout[p] = w;
+    if (node) node[p] = make_double4_32a(r[p], s_x[q], ph, w);
     if (tdf) tdf[p] = float_pairs(s_x[q], ph);
   }
+}
+
+// The slopes k_potential leaves to the seams between tiles: the last star
+// of every tile whose next star (in the next tile) is bound.
+__global__ void k_slope_seams(Seg S, const int64_t* esc, bool sub, const double* r,
+                              const double* x, const double* phi, double* M,
+                              double4_32a* node, int64_t n_tiles) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  TR R = tile_of(S, esc, t, sub);
+  const int64_t p = R.end - 1;
+  if (p < R.begin || p + 1 >= R.bound_end) return;
+  const double xj = x[p], pj = phi[p], xj1 = x[p + 1], pj1 = phi[p + 1];
+  const double w = div_rn(pj1 - pj, xj - xj1);
+  if (M) M[p] = w;
+  node[p] = make_double4_32a(r[p], xj, pj, w);
 }
 
 // ---------------------------------------------------- energy correction
@@ -710,30 +743,6 @@ __global__ void k_make_nodes(int64_t n, const double* r, const double* x, const 
   tdf[p] = float_pairs(x[p], phi[p]);
 }
 
-// Mixed mode's FP64 tables after the potential, per segment: the slope of
-// Eq. 6 in 1/r across each shell, (Phi_{k+1} - Phi_k) / (x_k - x_{k+1})
-// (Phi = 0 at 1/r = 0 beyond the last bound star), the shell parameter B
-// the FP64 orbit step takes for its roots, into M and the node records
-// {r, 1/r, Phi, slope}.  Stars beyond the bound ones get slope 0.
-__global__ void k_node_slopes(Seg S, const int64_t* esc, bool sub, int64_t n, const double* r,
-                              const double* x, const double* phi, double* M,
-                              double4_32a* node) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  const int c = seg_find(S.off, S.n_seg, p);
-  const int64_t k = p - __ldg(S.off + c);
-  const int64_t nbc = nb_eff(S.nb, esc, c, sub);
-  const double xj = x[p], pj = phi[p];
-  double sl = 0.0;
-  if (k < nbc) {
-    const bool last = k + 1 >= nbc;
-    const double xj1 = last ? 0.0 : x[p + 1], pj1 = last ? 0.0 : phi[p + 1];
-    sl = div_rn(pj1 - pj, xj - xj1);
-  }
-  M[p] = sl;
-  node[p] = make_double4_32a(r[p], xj, pj, sl);
-}
-
 __global__ void k_unpack_orbit(int64_t n, const uint64_t* keys, const Payload* pay,
                                double* r_new, double* vr_new, double* vt_new) {
   int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -760,13 +769,6 @@ void launch_recip(int64_t n, const double* r, double* x, cudaStream_t st) {
 void launch_make_t32(int64_t n, const double* x, const double* phi, float2* t32,
                      cudaStream_t st) {
   if (n > 0) k_make_t32<<<blocks_for(n, 256), 256, 0, st>>>(n, x, phi, t32);
-}
-
-void launch_node_slopes(const SegLayout& L, bool nb_sub, const double* r, const double* x,
-                        const double* phi, double* M, double4_32a* node, cudaStream_t st) {
-  if (L.n > 0)
-    k_node_slopes<<<blocks_for(L.n, 256), 256, 0, st>>>(L.dev(), L.esc_step, nb_sub, L.n, r, x,
-                                                        phi, M, node);
 }
 
 void launch_make_nodes(int64_t n, const double* r, const double* x, const double* phi,
@@ -886,14 +888,17 @@ void potential_prepare() {
 void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
                       double* tile_m, double* tile_mx, double* phi, float2* t32,
                       double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node,
-                      float4* tdf, bool sums_ready) {
+                      float4* tdf, bool sums_ready, bool slopes) {
   if (!L.n_tiles) return;
   Seg S = L.dev();
   if (!sums_ready)
     k_tile_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, L.esc_step, nb_sub, x, m, tile_m,
                                                          tile_mx);
   k_potential<<<(unsigned)L.n_tiles, kPotThreads, kPotentialSmem, st>>>(
-      S, L.esc_step, nb_sub, r, x, m, tile_m, tile_mx, phi, t32, Mout, node, tdf);
+      S, L.esc_step, nb_sub, r, x, m, tile_m, tile_mx, phi, t32, Mout, node, tdf, slopes);
+  if (slopes && node)
+    k_slope_seams<<<blocks_for(L.n_tiles, 128), 128, 0, st>>>(S, L.esc_step, nb_sub, r, x, phi,
+                                                              Mout, node, L.n_tiles);
 }
 
 void launch_correction(const SegLayout& L, const double* r, const double* x,

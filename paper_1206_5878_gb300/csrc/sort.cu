@@ -30,7 +30,14 @@ constexpr int kWarps = kThreads / 32;
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr unsigned long long kCountMask = (1ull << 62) - 1;
-constexpr int kSpinCap = 1 << 22;
+// Bounds of the device waits, in the library's device memory so that a
+// change reaches kernels already captured in a graph: polls of a look-back
+// word before a tile gives up on it (and reports a timeout), and moves of
+// the tie fix's insertion sort before it gives up on a run.
+constexpr int kSpinCapDefault = 1 << 22;
+constexpr long long kTieMoveCapDefault = 1ll << 22;
+__device__ int g_spin_cap = kSpinCapDefault;
+__device__ long long g_tie_move_cap = kTieMoveCapDefault;
 constexpr int kMaxPasses = 8;
 static_assert(kThreads == kBins, "one thread per digit");
 
@@ -186,22 +193,33 @@ __global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : 3))
     dg[i] = valid ? (int)((k[i] >> shift) & 0xFF) : kBins;
   }
 
-  // warp-level multisplit ranks (stable: slot order, then lane order)
+  // warp-level multisplit ranks (stable: slot order, then lane order).
+  // The leader of each group of equal digits adds the group's size to the
+  // warp's counter with a shared-memory atomic; the counts before (the
+  // atomics' results) are read only after a group of slots has been
+  // issued, so the round trips overlap.  A __syncwarp between slots orders
+  // the updates of one counter by different leaders in slot order.
   uint32_t rank[IPT];
   const unsigned lt_mask = lanemask_lt();
+  constexpr int kGrp = IPT < 4 ? IPT : 4;
 #pragma unroll
-  for (int i = 0; i < IPT; ++i) {
-    const unsigned peers = kRank == kRankMatch ? __match_any_sync(0xffffffffu, dg[i])
-                                               : peers_ballot(dg[i]);
-    int leader = __ffs(peers) - 1;
-    uint32_t old = 0;
-    if (lane == leader && dg[i] < kBins) {
-      old = S.whist[warp][dg[i]];
-      S.whist[warp][dg[i]] = old + __popc(peers);
+  for (int i0 = 0; i0 < IPT; i0 += kGrp) {
+    unsigned pe[kGrp];
+    uint32_t old[kGrp];
+#pragma unroll
+    for (int j = 0; j < kGrp; ++j) {
+      const int i = i0 + j;
+      pe[j] = kRank == kRankMatch ? __match_any_sync(0xffffffffu, dg[i]) : peers_ballot(dg[i]);
+      old[j] = 0;
+      if (lane == __ffs(pe[j]) - 1 && dg[i] < kBins)
+        old[j] = atomicAdd(&S.whist[warp][dg[i]], (uint32_t)__popc(pe[j]));
+      __syncwarp();
     }
-    old = __shfl_sync(0xffffffffu, old, leader);
-    rank[i] = old + __popc(peers & lt_mask);
-    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < kGrp; ++j) {
+      const uint32_t o = __shfl_sync(0xffffffffu, old[j], __ffs(pe[j]) - 1);
+      rank[i0 + j] = o + __popc(pe[j] & lt_mask);
+    }
   }
   __syncthreads();
 
@@ -224,11 +242,12 @@ __global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : 3))
     atomicExch(my, kFlagAgg | (unsigned long long)cnt);
     int64_t j = t - 1;
     const int64_t first = t - R.lt;
+    const int spin_cap = g_spin_cap;
     int spins = 0;
     while (j >= first) {
       unsigned long long w = ld_volatile(desc + ((size_t)q * n_tiles + j) * kBins + d);
       if ((w & ~kCountMask) == 0) {
-        if (++spins > kSpinCap) {
+        if (++spins > spin_cap) {
           set_err(err, kErrTimeout);
           --j;
           spins = 0;
@@ -281,7 +300,6 @@ __global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : 3))
 // Runs of keys equal in their bits above `shift` are put in (key, id) order
 // (insertion sort by one thread per run; a run that is already ordered
 // costs one pass): finite radii in (r, id) order, escapers in id order.
-constexpr long long kTieMoveCap = 1ll << 22;
 
 __global__ void k_tiefix(const int64_t* off, int n_seg, int64_t n, uint64_t* keys,
                          uint32_t* vals, const uint32_t* ids_by_val, int id_stride, int shift,
@@ -301,6 +319,7 @@ __global__ void k_tiefix(const int64_t* off, int n_seg, int64_t n, uint64_t* key
       return;
     }
   // insertion sort of the run by (key, id)
+  const long long move_cap = g_tie_move_cap;
   long long moves = 0;
   bool equal = false;
   for (int64_t i = p + 1; i < e; ++i) {
@@ -315,7 +334,7 @@ __global__ void k_tiefix(const int64_t* off, int n_seg, int64_t n, uint64_t* key
       keys[j + 1] = kj;
       vals[j + 1] = vals[j];
       --j;
-      if (++moves > kTieMoveCap) {
+      if (++moves > move_cap) {
         set_err(err, kErrTies);
         keys[j + 1] = kv;
         vals[j + 1] = v;
@@ -363,6 +382,14 @@ void launch_pass(const SegLayout& L, SortWork& W, bool id, const uint64_t* kin,
 }  // namespace
 
 // ------------------------------------------------------------------ host
+cudaError_t set_wait_limits(int spin_polls, long long tie_moves) {
+  const int sp = spin_polls > 0 ? spin_polls : kSpinCapDefault;
+  const long long tm = tie_moves > 0 ? tie_moves : kTieMoveCapDefault;
+  cudaError_t e = cudaMemcpyToSymbol(g_spin_cap, &sp, sizeof(sp));
+  if (!e) e = cudaMemcpyToSymbol(g_tie_move_cap, &tm, sizeof(tm));
+  return e;
+}
+
 void sort_prepare() {
   set_pass_smem<true, 8, kRankMatch>();
   set_pass_smem<false, 8, kRankMatch>();
