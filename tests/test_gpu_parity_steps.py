@@ -176,3 +176,23 @@ def test_ensemble_mixed_each_cluster_matches_its_oracle(g_stage, orc, ragged):
                 if ident in expect[i]:
                     assert rr == expect[i][ident], (step, i, ident)
     assert moved > 0.9 * 2 * sum(SIZES[3:5] + SIZES[6:])
+
+
+def test_many_escapers_take_the_radix_sort(g_stage, orc):
+    """A step with more escapers in one cluster than the shell sort lists
+    (4096) is sorted by the radix passes instead: the same state as the
+    oracle's, new radii bit for bit, escapers in id order at the end."""
+    g = g_stage
+    n = 30_000
+    d = ic.plummer(n, seed=9)
+    fast = np.random.default_rng(9).choice(n, 5000, replace=False)
+    d["vr"][fast] *= 10.0
+    d["vt"][fast] *= 10.0
+    c = g.Cluster({k: d[k] for k in ("r", "vr", "vt", "m", "id")}, [9], precision=0)
+    for step in range(2):
+        st = c.get_state()
+        o = _oracle_from(orc, st, 9, st["step"], c.escaped()[0])
+        c.step(1)
+        o.step(1)
+        _fp64_step_matches(c, o)
+    assert c.stats()[0]["escaped"] > 4096

@@ -1,8 +1,8 @@
 """The sort's bounded device waits run out, on purpose, without faulting or
-hanging anything: with a look-back limit of one poll a timestep's sort gives
-up on earlier tiles, reports CMC_ETIMEOUT and poisons its context (later
-calls return CMC_EPOISONED), while another context on the device is
-unaffected; with a tie-fix limit of a few moves the stage sort of a run of
+hanging anything: with a look-back limit of one poll, a timestep whose many
+escapers hand its sort to the radix passes gives up on earlier tiles,
+reports CMC_ETIMEOUT and poisons its context (later calls return
+CMC_EPOISONED), while another context on the device is unaffected; with a tie-fix limit of a few moves the stage sort of a run of
 equal radii falls back to sorting by id, then by radius, and still returns
 the (r, id) order.  Every wait bound is host-set (cmc_set_wait_limits) and
 restored to its default afterwards."""
@@ -27,9 +27,22 @@ def _cluster(g, n, seed):
     return g.Cluster({k: d[k] for k in ("r", "vr", "vt", "m", "id")}, [seed], autotune=0)
 
 
+def _unbound(n, seed, n_fast):
+    """A Plummer sample with n_fast stars sent out at ten times their
+    speed (E > 0: they escape in the first step)."""
+    d = ic.plummer(n, seed=seed)
+    fast = np.random.default_rng(seed).choice(n, n_fast, replace=False)
+    d["vr"][fast] *= 10.0
+    d["vt"][fast] *= 10.0
+    return d
+
+
 def test_lookback_limit_times_out_and_poisons(g):
+    """More escapers in one step than the shell sort lists hand the step to
+    the radix sort, whose look-back then runs out."""
     other = _cluster(g, 50_000, 2)  # built before the limit: unaffected later
-    c = _cluster(g, 2_000_000, 1)  # 489 sort tiles
+    d = _unbound(2_000_000, 1, 6000)  # 489 sort tiles, > 4096 escapers
+    c = g.Cluster({k: d[k] for k in ("r", "vr", "vt", "m", "id")}, [1], autotune=0)
     try:
         g.set_wait_limits(lookback_polls=1)
         with pytest.raises(g.CMCError) as ei:
