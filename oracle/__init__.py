@@ -100,6 +100,14 @@ def _declare(lib):
         "or_core_rho": (None, [_i64, _p, _p, _p]),
         "or_step": (_d, [_i64, _p, _p, _p, _p, _p, _p, _p, _u64, _u32, _i32, _d, _d,
                          _i32, _i32, _i32, _p, _p]),
+        "or_step_col": (_d, [_i64, _p, _p, _p, _p, _p, _p, _p, _p, _u64, _u32, _i32, _d, _d,
+                             _i32, _i32, _i32, _p, _p, _p]),
+        "or_encounter_radii": (ctypes.c_int, [_d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
+                                              _u64, _u32, _u32, _p]),
+        "or_relax_col": (_i64, [_i64, _p, _p, _p, _p, _p, _p, _i32, _d, _d, _u64, _u32, _p, _p,
+                                _p]),
+        "or_tcoll": (_d, [_i64, _p, _p, _p, _p, _p]),
+        "or_cbrt": (_d, [_d]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -195,6 +203,40 @@ def relax(vr, vt, m, ids, nbin, dt: float, lnL: float, seed: int, step: int,
     fails = _L().or_relax(vr.shape[0], _ptr(vr), _ptr(vt), _ptr(m), _ptr(ids), _ptr(nbin),
                           bin_size, dt, lnL, seed, step)
     return vr, vt, fails
+
+
+def encounter_radii(m1, m2, vr1, vt1, vr2, vt2, R1, R2, n, dt, lnL, seed, ident, step):
+    """The encounter with stellar radii (sticky spheres): 20 doubles, status
+    out[15] = 2 for a merger, out[16] the collision probability, out[17]
+    the dissipated energy."""
+    out = np.zeros(20)
+    _L().or_encounter_radii(m1, m2, vr1, vt1, vr2, vt2, R1, R2, n, dt, lnL, seed, ident, step,
+                            _ptr(out))
+    return out
+
+
+def relax_radii(vr, vt, m, R, ids, nbin, dt: float, lnL: float, seed: int, step: int, r,
+                phi, bin_size: int = BIN_SIZE):
+    """Relaxation with sticky-sphere mergers (r, phi: the sorted radii and
+    their potential); returns (vr, vt, m, R, mergers, their change of
+    K + W)."""
+    vr, vt, m, R = (_f64(a).copy() for a in (vr, vt, m, R))
+    r, phi = _f64(r), _f64(phi)
+    col = np.zeros(2)
+    _L().or_relax_col(vr.shape[0], _ptr(vr), _ptr(vt), _ptr(m), _ptr(R), _ptr(_u32a(ids)),
+                      _ptr(_f64(nbin)), bin_size, dt, lnL, seed, step, _ptr(col), _ptr(r),
+                      _ptr(phi))
+    return vr, vt, m, R, int(col[0]), col[1]
+
+
+def tcoll(r, vr, vt, m, R) -> float:
+    """Eq. 8's collision timestep over the innermost 300 bound stars."""
+    r, vr, vt, m, R = (_f64(a) for a in (r, vr, vt, m, R))
+    return _L().or_tcoll(r.shape[0], _ptr(r), _ptr(vr), _ptr(vt), _ptr(m), _ptr(R))
+
+
+def cbrt(v: float) -> float:
+    return _L().or_cbrt(float(v))
 
 
 def encounter(m1, m2, vr1, vt1, vr2, vt2, n, dt, lnL, seed, ident, step):
@@ -385,7 +427,7 @@ class Cluster:
     def __init__(self, r, vr, vt, m, ids, seed: int, *, theta_max: float = THETA_MAX,
                  gamma: float = GAMMA, bin_size: int = BIN_SIZE, max_trials: int = 1000,
                  energy_correction: bool = True, pot_mode: str = "recursion",
-                 rng: str = "philox"):
+                 rng: str = "philox", radii=None):
         r, vr, vt, m = _f64(r), _f64(vr), _f64(vt), _f64(m)
         ids = _u32a(ids)
         n = r.shape[0]
@@ -395,6 +437,10 @@ class Cluster:
         self.vt = vt[perm].copy()
         self.m = m[perm].copy()
         self.id = ids[perm].copy()
+        # stellar radii (sticky-sphere collisions and the Eq. 8 timestep)
+        self.R = None if radii is None else _f64(radii)[perm].copy()
+        # mergers so far and the energy they dissipated
+        self.collisions = np.zeros(2)
         self.n = n
         self.nb = int(np.count_nonzero(np.isfinite(self.r)))
         self.seed = int(seed)
@@ -426,11 +472,20 @@ class Cluster:
             if self.taus is not None:
                 _L().or_taus_bind(_ptr(self.taus))
             try:
-                dt = _L().or_step(self.n, _ptr(nb), _ptr(self.r), _ptr(self.vr),
-                                  _ptr(self.vt), _ptr(self.m), _ptr(self.id), _ptr(self.phi),
-                                  self.seed, self.step_no, self.bin_size, self.pref, self.lnL,
-                                  self.max_trials, self.ecorr, self.pot_mode, _ptr(stats),
-                                  _ptr(self.escaped))
+                if self.R is None:
+                    dt = _L().or_step(self.n, _ptr(nb), _ptr(self.r), _ptr(self.vr),
+                                      _ptr(self.vt), _ptr(self.m), _ptr(self.id),
+                                      _ptr(self.phi), self.seed, self.step_no, self.bin_size,
+                                      self.pref, self.lnL, self.max_trials, self.ecorr,
+                                      self.pot_mode, _ptr(stats), _ptr(self.escaped))
+                else:
+                    dt = _L().or_step_col(self.n, _ptr(nb), _ptr(self.r), _ptr(self.vr),
+                                          _ptr(self.vt), _ptr(self.m), _ptr(self.R),
+                                          _ptr(self.id), _ptr(self.phi), self.seed,
+                                          self.step_no, self.bin_size, self.pref, self.lnL,
+                                          self.max_trials, self.ecorr, self.pot_mode,
+                                          _ptr(stats), _ptr(self.escaped),
+                                          _ptr(self.collisions))
             finally:
                 _L().or_taus_bind(None)
             self.nb = int(nb[0])

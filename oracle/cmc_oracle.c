@@ -49,6 +49,7 @@
 #define OR_TAG_PHI 1u  /* relaxation: azimuth of the deflection about w        */
 #define OR_TAG_REJ 2u  /* orbit: rejection trials (X, X')                      */
 #define OR_TAG_SGN 3u  /* orbit: sign of the new radial velocity               */
+#define OR_TAG_COL 4u  /* relaxation pair: the sticky-sphere collision draw    */
 
 void or_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
 {
@@ -494,16 +495,50 @@ double or_timestep(int64_t nb, const double *r, const double *vr, const double *
  *   12 sin^2(beta/2), 13 cos(beta), 14 |w|, 15 status
  * status: 0 deflected, 1 skipped (no density, no mass or w = 0).
  * Returns the number of failed angle draws (normally 0). */
+/* Sticky spheres (section 2.1 step 3(iii): two bodies merge when their
+ * radii touch).  Reading: with stellar radii R1, R2 the pair's
+ * representative encounter is a collision with probability
+ *   P = n sigma |w| dt,  sigma = pi (R1 + R2)^2 (1 + 2 G (m1 + m2) / ((R1 + R2) |w|^2))
+ * (the geometric cross section with gravitational focusing, the pair's bin
+ * density n, its 3-D relative speed |w|), decided by one uniform draw of
+ * the pair (tag 4) taken after the azimuth psi; the merged star keeps the
+ * pair's momentum (3-D centre-of-mass velocity) and total mass, and the
+ * relative kinetic energy (m1 m2 / (m1 + m2)) |w|^2 / 2 is dissipated.
+ * out[] (20 doubles): as or_encounter, with status 2 for a merger (6-8 the
+ * merged star's velocity), 16 P, 17 the dissipated energy. */
+static int or_encounter_col(double m1, double m2, double vr1, double vt1, double vr2,
+                            double vt2, double R1, double R2, double n, double dt, double lnL,
+                            uint64_t seed, uint32_t id, uint32_t step, double *out);
+
 int or_encounter(double m1, double m2, double vr1, double vt1, double vr2, double vt2,
                  double n, double dt, double lnL, uint64_t seed, uint32_t id,
                  uint32_t step, double *out)
+{
+    double o[20];
+    int i, fails = or_encounter_col(m1, m2, vr1, vt1, vr2, vt2, 0.0, 0.0, n, dt, lnL, seed, id,
+                                    step, o);
+    for (i = 0; i < 16; ++i) out[i] = o[i];
+    return fails;
+}
+
+/* Test hook: the encounter with stellar radii (out: 20 doubles). */
+int or_encounter_radii(double m1, double m2, double vr1, double vt1, double vr2, double vt2,
+                       double R1, double R2, double n, double dt, double lnL, uint64_t seed,
+                       uint32_t id, uint32_t step, double *out)
+{
+    return or_encounter_col(m1, m2, vr1, vt1, vr2, vt2, R1, R2, n, dt, lnL, seed, id, step, out);
+}
+
+static int or_encounter_col(double m1, double m2, double vr1, double vt1, double vr2,
+                            double vt2, double R1, double R2, double n, double dt, double lnL,
+                            uint64_t seed, uint32_t id, uint32_t step, double *out)
 {
     double msum, cpsi = 1.0, spsi = 0.0, cphi, sphi;
     double v1x, v1y, v1z, v2x, v2y, v2z, wx, wy, wz, w2, w;
     double num, s2, sb, cosb, sinb, wp2, e1y, e1z;
     double ux, uy, uz, a1, wpx, wpy, wpz, dwx, dwy, dwz, f1, f2;
     int fails = 0, i;
-    for (i = 0; i < 16; ++i) out[i] = 0.0;
+    for (i = 0; i < 20; ++i) out[i] = 0.0;
     out[15] = 1.0;
     msum = m1 + m2;
     /* no density, no mass, or no positive Coulomb logarithm (ln(gamma N) <= 0
@@ -523,6 +558,26 @@ int or_encounter(double m1, double m2, double vr1, double vt1, double vr2, doubl
     w2 = (wx * wx + wy * wy) + wz * wz;
     if (!(w2 > 0.0)) return fails;
     w = sqrt(w2);
+    if (R1 + R2 > 0.0) {
+        double Rs = R1 + R2, focus, sig, Pc, X;
+        uint32_t cw[4];
+        focus = 1.0 + (2.0 * msum) / (Rs * w2);
+        sig = (OR_PI * (Rs * Rs)) * focus;
+        Pc = ((sig * n) * w) * dt;
+        or_draw(seed, id, step, OR_TAG_COL, 0u, cw);
+        X = or_u01(cw[0], cw[1]);
+        out[16] = Pc;
+        if (X < Pc) {
+            out[6] = (m1 * v1x + m2 * v2x) / msum;
+            out[7] = (m1 * v1y + m2 * v2y) / msum;
+            out[8] = (m1 * v1z + m2 * v2z) / msum;
+            out[9] = 0.0; out[10] = 0.0; out[11] = 0.0;
+            out[14] = w;
+            out[15] = 2.0;
+            out[17] = (0.5 * ((m1 * m2) / msum)) * w2;
+            return fails;
+        }
+    }
     num = (2.0 * OR_PI) * msum;
     num = num * msum;
     num = num * n;
@@ -566,24 +621,107 @@ int or_encounter(double m1, double m2, double vr1, double vt1, double vr2, doubl
     return fails;
 }
 
+/* Cube root by Newton's method, y <- y - (y^3 - v) / (3 y^2), eight steps
+ * from 2^floor(e/3) (e the binary exponent of v), every operation one IEEE
+ * rounding in this order (so that the GPU, taking the same steps, gets the
+ * same bits); within a few units in the last place of the cube root for
+ * normal v > 0, and 0 for v <= 0. */
+double or_cbrt(double v)
+{
+    uint64_t b;
+    int e, k, i;
+    double y;
+    if (!(v > 0.0)) return 0.0;
+    memcpy(&b, &v, sizeof b);
+    e = (int)((b >> 52) & 0x7FF) - 1023;
+    k = e >= 0 ? e / 3 : -((-e + 2) / 3);  /* floor(e / 3) */
+    b = (uint64_t)(k + 1023) << 52;
+    memcpy(&y, &b, sizeof y);
+    for (i = 0; i < 8; ++i) y = y - (y * y * y - v) / (3.0 * (y * y));
+    return y;
+}
+
 /* All pairs (2j, 2j+1) of the nb bound stars; the density of a pair is that
  * of its bin.  New v_r is the radial (x) component, new v_t the length of
- * the transverse (y, z) part. */
-int64_t or_relax(int64_t nb, double *vr, double *vt, const double *m, const uint32_t *id,
-                 const double *nbin, int32_t bs, double dt, double lnL,
-                 uint64_t seed, uint32_t step)
+ * the transverse (y, z) part.  With stellar radii R (may be NULL) a pair may
+ * merge instead (sticky spheres): the first star takes the total mass, the
+ * pair's momentum and the radius cbrt(R1^3 + R2^3) (volume kept), the second
+ * gets mass 0 and radius -1 (it leaves in the orbit step); col[0] counts
+ * the mergers, col[1] adds what they change of K + W: the relative kinetic
+ * energy dissipated, -(m_a m_b / (m_a + m_b)) |w|^2 / 2, plus the change of
+ * the shell-model W = -sum_{i<j} m_i m_j / max(r_i, r_j) when b's mass joins
+ * a (a, b adjacent, r_a <= r_b): m_b (Phi_a - Phi_b) + m_a m_b / r_a (the
+ * pair's own term leaves W, the stars inside r_a now bind b's mass at r_a);
+ * r and phi (the current potential) may be NULL when col is. */
+int64_t or_relax_col(int64_t nb, double *vr, double *vt, double *m, double *R,
+                     const uint32_t *id, const double *nbin, int32_t bs, double dt, double lnL,
+                     uint64_t seed, uint32_t step, double *col, const double *r,
+                     const double *phi)
 {
     int64_t j, npairs = nb / 2, fails = 0;
     for (j = 0; j < npairs; ++j) {
         int64_t a = 2 * j, b = a + 1;
-        double o[16];
-        fails += or_encounter(m[a], m[b], vr[a], vt[a], vr[b], vt[b], nbin[a / bs], dt,
-                              lnL, seed, id[a], step, o);
+        double o[20];
+        fails += or_encounter_col(m[a], m[b], vr[a], vt[a], vr[b], vt[b], R ? R[a] : 0.0,
+                                  R ? R[b] : 0.0, nbin[a / bs], dt, lnL, seed, id[a], step, o);
+        if (o[15] == 2.0) {
+            double R1 = R[a], R2 = R[b];
+            if (col) {
+                double dW = m[b] * (phi[a] - phi[b]) + (m[a] * m[b]) / r[a];
+                col[0] += 1.0;
+                col[1] += dW - o[17];
+            }
+            vr[a] = o[6];
+            vt[a] = sqrt(o[7] * o[7] + o[8] * o[8]);
+            m[a] = m[a] + m[b];
+            R[a] = or_cbrt(R1 * R1 * R1 + R2 * R2 * R2);
+            m[b] = 0.0;
+            R[b] = -1.0;
+            continue;
+        }
         if (o[15] != 0.0) continue;
         vr[a] = o[6]; vt[a] = sqrt(o[7] * o[7] + o[8] * o[8]);
         vr[b] = o[9]; vt[b] = sqrt(o[10] * o[10] + o[11] * o[11]);
     }
     return fails;
+}
+
+int64_t or_relax(int64_t nb, double *vr, double *vt, const double *m, const uint32_t *id,
+                 const double *nbin, int32_t bs, double dt, double lnL,
+                 uint64_t seed, uint32_t step)
+{
+    return or_relax_col(nb, vr, vt, (double *)m, NULL, id, nbin, bs, dt, lnL, seed, step, NULL,
+                        NULL, NULL);
+}
+
+/* The collision timestep (section 2.1 step 2, Eq. 8) over the innermost
+ * P = min(300, nb) bound stars (the paper averages it over the central 300):
+ *   1 / T_coll = 16 sqrt(pi) n_s <R^2> sigma (1 + G <M R> / (2 sigma^2 <R^2>))
+ * with n_s = 3 (P - 1) / (4 pi (r_{P-1}^3 - r_0^3)) (the bins' estimator),
+ * sigma^2 = <v_r^2 + v_t^2> / 3 the one-dimensional velocity dispersion, and
+ * the means over the P stars in order.  +inf without radii (<R^2> = 0). */
+double or_tcoll(int64_t nb, const double *r, const double *vr, const double *vt,
+                const double *m, const double *R)
+{
+    int64_t P = nb < 300 ? nb : 300, k;
+    double vol, ns, sv = 0.0, sr = 0.0, smr = 0.0, sig2, R2, MR, sig, inv;
+    if (P < 2 || !R) return INFINITY;
+    vol = r[P - 1] * r[P - 1] * r[P - 1] - r[0] * r[0] * r[0];
+    if (!(vol > 0.0)) return INFINITY;
+    ns = (3.0 * (double)(P - 1)) / ((4.0 * OR_PI) * vol);
+    for (k = 0; k < P; ++k) {
+        sv = sv + (vr[k] * vr[k] + vt[k] * vt[k]);
+        sr = sr + R[k] * R[k];
+        smr = smr + m[k] * R[k];
+    }
+    sig2 = (sv / (double)P) / 3.0;
+    R2 = sr / (double)P;
+    MR = smr / (double)P;
+    if (!(R2 > 0.0) || !(sig2 > 0.0)) return INFINITY;
+    sig = sqrt(sig2);
+    inv = (((16.0 * sqrt(OR_PI)) * ns) * R2) * sig;
+    inv = inv * (1.0 + MR / ((2.0 * sig2) * R2));
+    return 1.0 / inv;
 }
 
 /* Test hook for the angle draw. */
@@ -952,10 +1090,29 @@ void or_core_rho(int64_t nb, const double *r, const double *m, double *rho)
 /* e_k = Phi_k + m_k / r_k + (v_r^2 + v_t^2) / 2 the star's energy in the   */
 /* field of the others (Phi_k includes the star's own mass), in star order. */
 /* ------------------------------------------------------------------------ */
+double or_step_col(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt, double *m,
+                   double *R, uint32_t *id, double *phi, uint64_t seed, uint32_t step,
+                   int32_t bs, double pref, double lnL, int32_t max_trials, int32_t ecorr,
+                   int32_t pot_mode, int64_t *stats, double *esc_io, double *col);
+
 double or_step(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt, double *m,
                uint32_t *id, double *phi, uint64_t seed, uint32_t step, int32_t bs,
                double pref, double lnL, int32_t max_trials, int32_t ecorr,
                int32_t pot_mode, int64_t *stats, double *esc_io)
+{
+    return or_step_col(n, nb_io, r, vr, vt, m, NULL, id, phi, seed, step, bs, pref, lnL,
+                       max_trials, ecorr, pot_mode, stats, esc_io, NULL);
+}
+
+/* The timestep with stellar radii R (may be NULL: or_step): the collision
+ * timestep of Eq. 8 joins the minimum, relaxation pairs may merge (sticky
+ * spheres), and a star merged away (radius -1, mass 0) leaves in the orbit
+ * step (r = +inf, no energy carried off: it has no mass); R is permuted with
+ * the stars; col[0] += mergers, col[1] += their change of K + W. */
+double or_step_col(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt, double *m,
+                   double *R, uint32_t *id, double *phi, uint64_t seed, uint32_t step,
+                   int32_t bs, double pref, double lnL, int32_t max_trials, int32_t ecorr,
+                   int32_t pot_mode, int64_t *stats, double *esc_io, double *col)
 {
     int64_t nb = *nb_io, k;
     int64_t nbins = (nb + bs - 1) / bs;
@@ -970,14 +1127,23 @@ double or_step(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt, dou
     memset(stats, 0, 7 * sizeof(int64_t));
 
     dt = or_timestep(nb, r, vr, vt, m, bs, pref, lnL, nbin);
-    stats[6] += or_relax(nb, vr, vt, m, id, nbin, bs, dt, lnL, seed, step);
+    if (R) {
+        double tc = or_tcoll(nb, r, vr, vt, m, R);
+        if (tc < dt) dt = tc;
+    }
+    stats[6] += or_relax_col(nb, vr, vt, m, R, id, nbin, bs, dt, lnL, seed, step, col, r, phi);
 
     for (k = 0; k < n; ++k) { rn[k] = r[k]; ro[k] = r[k]; cc[k] = 0.0; }
     for (k = 0; k < nb; ++k) {
         double out[8];
         int64_t viol = 0;
-        int rc = or_orbit_star(k, nb, r, phi, vr[k], vt[k], id[k], seed, step,
-                               max_trials, out, &viol);
+        int rc;
+        if (R && R[k] < 0.0) {  /* merged into its partner in this step */
+            rn[k] = INFINITY;
+            continue;
+        }
+        rc = or_orbit_star(k, nb, r, phi, vr[k], vt[k], id[k], seed, step,
+                           max_trials, out, &viol);
         stats[3] += (int64_t)out[7];
         stats[4] += viol;
         if (rc == 1) {
@@ -1007,6 +1173,7 @@ double or_step(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt, dou
     OR_PERMUTE(vr);
     OR_PERMUTE(vt);
     OR_PERMUTE(m);
+    if (R) OR_PERMUTE(R);
     OR_PERMUTE(ro);
     OR_PERMUTE(cc);
     for (k = 0; k < n; ++k) tmp[k] = rn[perm[k]];
