@@ -78,7 +78,15 @@ enum {
                                    cluster (section 2.1 step 6's correction):
                                    the sum of m_k |T'_k| over clamped stars, as
                                    an integer in units of 2^-62 */
-    CMC_NSTATS = 10
+    CMC_STAT_COLLISIONS = 10,   /* sticky-sphere mergers (cfg.collisions); the
+                                   merged-away partners left the cluster but
+                                   are not counted as escapers */
+    CMC_STAT_COLLISION_ENERGY = 11, /* what the mergers changed of K + W (the
+                                   relative kinetic energy dissipated and the
+                                   shell-model W of the moved mass), as a signed
+                                   integer in units of 2^-62: K + W + E_esc
+                                   minus this is what the method conserves */
+    CMC_NSTATS = 12
 };
 
 typedef struct {
@@ -112,6 +120,10 @@ typedef struct {
     int32_t relax_variant;      /* relaxation kernel variant (listed at
                                    cmc_get_tuning): -1 = the autotuner's choice
                                    (0 without autotune), or 0..2 (default -1) */
+    int32_t collisions;         /* 1: stars carry radii (cmc_set_radii): the
+                                   collision timestep of Eq. 8 joins Eq. 7's, and
+                                   relaxation pairs may merge as sticky spheres
+                                   (section 2.1 step 3(iii)); default 0 */
 } cmc_config;
 
 /* Fill cfg with the defaults shown above. */
@@ -305,6 +317,22 @@ cmc_status cmc_orbit(int64_t n, const double *r, const double *phi, const double
 cmc_status cmc_energy_correction(int64_t n, const double *r, const double *phi, double *vr,
                                  double *vt, const double *r_old, const double *c,
                                  void *stream);
+
+/* Stellar radii (configuration collisions = 1; in Henon length units) of
+ * the stars in the order cmc_get_state returns them: R (n, host or device
+ * per ptr_kind) in, finite and >= 0; 0 means no radius.  With radii the
+ * collision timestep of Eq. 8 (section 2.1 step 2), over the innermost 300
+ * bound stars, joins the minimum with Eq. 7's, and a relaxation pair
+ * (section 2.1 step 3(iii)) merges with probability
+ * n pi (R1 + R2)^2 (1 + 2 G (m1 + m2) / ((R1 + R2) |w|^2)) |w| dt (the bin
+ * density n, the pair's 3-D relative speed |w|; one draw per pair): the
+ * first star keeps the pair's mass and momentum and takes the radius
+ * (R1^3 + R2^3)^(1/3), the second leaves the cluster (radius -1 afterwards).
+ * Radii travel with the stars through every sort; cmc_set_state sets them
+ * to 0.  CMC_EINVAL without collisions or for bad radii. */
+cmc_status cmc_set_radii(cmc_ctx *ctx, const double *R, int32_t ptr_kind);
+/* The stellar radii in state order (n doubles out, host or device). */
+cmc_status cmc_get_radii(cmc_ctx *ctx, double *R, int32_t ptr_kind);
 
 /* Limits of the sort's bounded device waits on the current device, for all
  * contexts and stage calls there (read by the kernels at launch, so graphs

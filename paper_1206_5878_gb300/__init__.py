@@ -173,6 +173,16 @@ class Cluster:
         out["step"] = int(step[0])
         return out
 
+    def set_radii(self, R):
+        """Stellar radii of the stars in get_state order (collisions=1)."""
+        R = np.ascontiguousarray(R, dtype=np.float64)
+        check(self.lib.cmc_set_radii(self.ctx, R.ctypes.data, 0), self.ctx)
+
+    def radii(self) -> np.ndarray:
+        out = np.empty(self.n)
+        check(self.lib.cmc_get_radii(self.ctx, out.ctypes.data, 0), self.ctx)
+        return out
+
     def set_state(self, state, step: int):
         kind = 0 if isinstance(state["r"], np.ndarray) else 1
         arrs = [self._prep(state[k], k, kind) for k in ("r", "vr", "vt", "m", "id")]

@@ -23,7 +23,8 @@ CMC_OK, CMC_EINVAL, CMC_ENOMEM, CMC_ECUDA, CMC_ENOCONV, CMC_ETIMEOUT, CMC_EPOISO
 STATUS_NAMES = {0: "CMC_OK", 1: "CMC_EINVAL", 2: "CMC_ENOMEM", 3: "CMC_ECUDA",
                 4: "CMC_ENOCONV", 5: "CMC_ETIMEOUT", 6: "CMC_EPOISONED"}
 STAT_NAMES = ("escaped", "degenerate", "cap_hits", "trials", "violations", "clamps",
-              "angle_fails", "ties", "fp64_trials", "clamp_energy")
+              "angle_fails", "ties", "fp64_trials", "clamp_energy", "collisions",
+              "collision_energy")
 CMC_NSTATS = len(STAT_NAMES)
 STAGE_NAMES = ("timestep", "relax", "turning", "orbit", "sort", "gather", "potential",
                "correction", "end")
@@ -33,7 +34,7 @@ class cmc_config(ctypes.Structure):
     _fields_ = [("precision", _i32), ("bin_size", _i32), ("theta_max", _d), ("gamma", _d),
                 ("max_trials", _i32), ("energy_correction", _i32), ("orbit_block", _i32),
                 ("autotune", _i32), ("orbit_variant", _i32), ("rng", _i32),
-                ("relax_variant", _i32)]
+                ("relax_variant", _i32), ("collisions", _i32)]
 
 
 # exported symbol -> (restype, argtypes); the list is the ABI of include/cmc.h
@@ -71,6 +72,8 @@ SIGNATURES = {
     "cmc_potential_static": (_i32, [_i64, _p, _p, _p, _p, _p]),
     "cmc_check_arith": (_i32, [_i32, _u64, _u64, _p]),
     "cmc_set_wait_limits": (_i32, [_i32, _i64]),
+    "cmc_set_radii": (_i32, [_p, _p, _i32]),
+    "cmc_get_radii": (_i32, [_p, _p, _i32]),
 }
 
 _lib = None

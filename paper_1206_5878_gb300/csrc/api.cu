@@ -43,6 +43,8 @@ struct cmc_ctx {
   int kernels_per_step = 0;
   int orbit_variant = 0;  // mixed-mode orbit kernel variant (see kOrbitVariants)
   int relax_variant = 0;  // relaxation kernel variant (see kRelaxVariants)
+  // stellar radii (cfg.collisions): the state's, and their copy through the sort
+  double *R = nullptr, *Rp = nullptr;
 };
 
 namespace {
@@ -188,8 +190,10 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   };
   mark(0);
   launch_bins(L, c->r, c->vr, c->vt, c->m, c->nbin, c->pref, st);
+  launch_tcoll(L, c->r, c->vr, c->vt, c->m, c->R, st);
   mark(1);
-  launch_relax(L, c->vr, c->vt, c->m, c->id, c->nbin, c->step, st, c->relax_variant);
+  launch_relax(L, c->vr, c->vt, c->m, c->id, c->nbin, c->step, st, c->relax_variant, c->R, c->r,
+               c->phi);
   mark(2);
   // turning points into r_old, c (free until the gather), then sampling
   if (mixed)
@@ -199,7 +203,7 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
                c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
-               c->bk.args(), c->r_old, c->cc, c->vals, c->pcount, st, false);
+               c->bk.args(), c->r_old, c->cc, c->vals, c->pcount, st, false, c->R, c->Rp);
   mark(4);
   // radix passes over bits 24-63 of the radius keys; runs equal in those
   // bits (radii within 2^-28 of each other, escapers whose ids differ in
@@ -211,7 +215,7 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
                 24);
   mark(5);
   launch_gather(L, sk, sv, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old, c->cc, st,
-                c->tile_a, c->tile_b);
+                c->tile_a, c->tile_b, c->Rp, c->R);
   mark(6);
   // mixed mode's tables carry the shell slopes of the FP64 orbit step (not
   // the scan's enclosed masses): its turning points and points are then
@@ -242,7 +246,7 @@ int count_step_kernels(const cmc_ctx* c) {
   // the tile sums, potential, [turning points, FP32 sampler, FP64
   // continuation, slopes at the tile seams, 2 bucket-index + 2 grid
   // kernels], [correction], step end
-  return 3 + 2 + 5 + 1 + 1 + 1 + (c->cfg.precision == 1 ? 8 : 0) +
+  return 3 + (c->R ? 1 : 0) + 2 + 5 + 1 + 1 + 1 + (c->cfg.precision == 1 ? 8 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 
@@ -255,6 +259,8 @@ void free_ctx(cmc_ctx* c) {
                    &c->tile_a, &c->tile_b, &c->tile_c, &c->Mbuf, &c->out3, &c->fr, &c->lag};
   for (double** p : ds) dfree(*p, st);
   dfree(c->id, st);
+  dfree(c->R, st);
+  dfree(c->Rp, st);
   dfree(c->t32, st);
   dfree(c->keys, st);
   dfree(c->vals, st);
@@ -540,6 +546,7 @@ void cmc_config_default(cmc_config* cfg) {
   cfg->orbit_variant = -1;
   cfg->rng = 0;
   cfg->relax_variant = -1;
+  cfg->collisions = 0;
 }
 
 cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
@@ -558,7 +565,7 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
       !(cfg.gamma > 0.0) || cfg.orbit_block < 0 || cfg.orbit_block > 256 ||
       (cfg.orbit_block % 32) || cfg.orbit_variant < -1 || cfg.orbit_variant >= kOrbitVariants ||
       (cfg.rng != 0 && cfg.rng != 1) || cfg.relax_variant < -1 ||
-      cfg.relax_variant >= kRelaxVariants)
+      cfg.relax_variant >= kRelaxVariants || (cfg.collisions != 0 && cfg.collisions != 1))
     return fail(nullptr, CMC_EINVAL, "cmc_init: bad configuration");
   std::vector<int64_t> sizes(n_per_cluster, n_per_cluster + n_clusters);
   std::vector<uint64_t> sd(seeds, seeds + n_clusters);
@@ -607,6 +614,11 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   CMC_ALLOC(c->err, 1);
   CMC_ALLOC(c->step, 1);
   CMC_ALLOC(c->pcount, 1);
+  if (cfg.collisions) {
+    CMC_ALLOC(c->R, n);
+    CMC_ALLOC(c->Rp, n);
+    if (!e) e = cudaMemsetAsync(c->R, 0, sizeof(double) * n, st);
+  }
 #undef CMC_ALLOC
   if (!e) e = alloc_sort(c->W, L, 8, st);
   if (!e && cfg.precision == 1) e = alloc_buckets(c->bk, L, st);
@@ -807,6 +819,8 @@ cmc_status cmc_set_state(cmc_ctx* c, const double* r, const double* vr, const do
     return fail(c, CMC_EINVAL, "cmc_set_state: bad arguments");
   DeviceGuard g(c->device);
   c->poisoned = false;
+  // a new state drops the stellar radii (they belong to the old order)
+  if (c->R) cudaMemsetAsync(c->R, 0, sizeof(double) * (size_t)c->L.n, c->stream);
   return load_state(c, r, vr, vt, m, id, ptr_kind, true, step);
 }
 
@@ -867,6 +881,40 @@ cmc_status cmc_set_escaped(cmc_ctx* c, const double* in) {
 }
 
 int32_t cmc_kernels_per_step(const cmc_ctx* c) { return c ? c->kernels_per_step : 0; }
+
+cmc_status cmc_set_radii(cmc_ctx* c, const double* R, int32_t ptr_kind) {
+  if (!c || !R || (ptr_kind != 0 && ptr_kind != 1))
+    return fail(c, CMC_EINVAL, "cmc_set_radii: bad arguments");
+  if (c->poisoned) return fail(c, CMC_EPOISONED, "cmc_set_radii: context poisoned");
+  if (!c->R) return fail(c, CMC_EINVAL, "cmc_set_radii: the context has no collisions");
+  if (ptr_kind == 0)
+    for (int64_t i = 0; i < c->L.n; ++i)
+      if (!(R[i] >= 0.0) || !(R[i] < INFINITY))
+        return fail(c, CMC_EINVAL, "cmc_set_radii: radii must be finite and >= 0");
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaMemcpyAsync(c->R, R, sizeof(double) * (size_t)c->L.n,
+                                  ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (e) return cuda_fail(c, e, "cmc_set_radii");
+  return CMC_OK;
+}
+
+cmc_status cmc_get_radii(cmc_ctx* c, double* R, int32_t ptr_kind) {
+  if (!c || !R || (ptr_kind != 0 && ptr_kind != 1))
+    return fail(c, CMC_EINVAL, "cmc_get_radii: bad arguments");
+  if (c->poisoned) return fail(c, CMC_EPOISONED, "cmc_get_radii: context poisoned");
+  if (!c->R) return fail(c, CMC_EINVAL, "cmc_get_radii: the context has no collisions");
+  DeviceGuard g(c->device);
+  cudaStream_t st = c->stream;
+  cudaError_t e = cudaMemcpyAsync(R, c->R, sizeof(double) * (size_t)c->L.n,
+                                  ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (e) return cuda_fail(c, e, "cmc_get_radii");
+  return CMC_OK;
+}
 
 cmc_status cmc_get_tuning(const cmc_ctx* c, int32_t* out) {
   if (!c || !out) return CMC_EINVAL;
@@ -1030,7 +1078,7 @@ cmc_status cmc_relax(int64_t n, double* vr, double* vt, const double* m, const u
   if (!e) e = cudaMemcpyAsync(S.L.dt_bits, &dt, sizeof(double), cudaMemcpyHostToDevice, st);
   if (!e) e = cudaMemcpyAsync(dstep, &step, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
   if (!e) {
-    launch_relax(S.L, vr, vt, m, id, nbin, dstep, st);
+    launch_relax(S.L, vr, vt, const_cast<double*>(m), id, nbin, dstep, st);
     e = cudaGetLastError();
   }
   if (!e) e = cudaStreamSynchronize(st);  // dt and step live on this stack

@@ -24,6 +24,7 @@ constexpr uint32_t kTagPsi = 0;      // relaxation: azimuth of star 2's v_t
 constexpr uint32_t kTagPhi = 1;      // relaxation: azimuth of the deflection
 constexpr uint32_t kTagRej = 2;      // orbit: rejection trials
 constexpr uint32_t kTagSgn = 3;      // orbit: sign of the new v_r
+constexpr uint32_t kTagCol = 4;      // relaxation pair: sticky-sphere collision draw
 
 // escaped stars sort after every finite radius, by id: key 0x7FF0...0 | id
 // << 20, above every finite radius (the timestep's sort orders by the top
@@ -42,8 +43,12 @@ enum : uint32_t {
 // per-segment statistics (64-bit counters)
 enum : int {
   kStEscaped = 0, kStDegenerate, kStCapHits, kStTrials, kStViolations,
-  kStClamps, kStAngleFails, kStTies, kStFp64Trials, kStClampEnergy, kStCount
+  kStClamps, kStAngleFails, kStTies, kStFp64Trials, kStClampEnergy, kStCollisions,
+  kStCollisionEnergy, kStCount
 };
+// (slot 15: the collision count at the last step end, to tell this step's
+// merged-away stars from its escapers)
+constexpr int kStCollisionsSeen = 15;
 constexpr int kStStride = 16;        // counters reserved per segment
 
 // ------------------------------------------------------- segment layout
@@ -548,6 +553,20 @@ __device__ __forceinline__ double phi_in_shell(const Table64& t, int64_t i, doub
 
 __device__ __forceinline__ double phi_of_r(const Table64& t, double q) {
   return phi_in_shell(t, shell_of(t, q), q);
+}
+
+// Cube root by Newton's method, y <- y - (y^3 - v) / (3 y^2), eight steps
+// from 2^floor(e/3) (e the binary exponent of v): the merged radius of two
+// sticky spheres; the same operations in the same order as the FP64
+// statement of the method, so the same bits; 0 for v <= 0.
+__device__ __forceinline__ double cbrt_newton(double v) {
+  if (!(v > 0.0)) return 0.0;
+  const int e = (int)((ubits(v) >> 52) & 0x7FFu) - 1023;
+  const int k = e >= 0 ? e / 3 : -((-e + 2) / 3);  // floor(e / 3)
+  double y = __longlong_as_double((long long)((unsigned long long)(k + 1023) << 52));
+#pragma unroll 1
+  for (int i = 0; i < 8; ++i) y = y - (y * y * y - v) / (3.0 * (y * y));
+  return y;
 }
 
 // ----------------------------------------------------- small utilities

@@ -131,7 +131,8 @@ void launch_rekey_radius(const SegLayout& L, const uint32_t* perm, const double*
 void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* vals,
                    const Payload* pay, double* r, double* x, double* vr, double* vt,
                    double* m, uint32_t* id, double* r_old, double* c, cudaStream_t st,
-                   double* tile_m = nullptr, double* tile_mx = nullptr);
+                   double* tile_m = nullptr, double* tile_mx = nullptr,
+                   const double* Rp = nullptr, double* Rout = nullptr);
 
 // potential: per-tile sums then the tile-local scans (Eqs. 1-5 in scan
 // form).  nb_sub: subtract esc_step from nb (after the orbit step).
@@ -156,9 +157,14 @@ void launch_correction(const SegLayout& L, const double* r, const double* x,
 void launch_bins(const SegLayout& L, const double* r, const double* vr, const double* vt,
                  const double* m, double* nbin, double pref, cudaStream_t st);
 
-void launch_relax(const SegLayout& L, double* vr, double* vt, const double* m,
-                  const uint32_t* id, const double* nbin, const uint32_t* step,
-                  cudaStream_t st, int variant = 0);
+// relaxation of the neighbour pairs; with stellar radii R (may be null)
+// pairs may merge (sticky spheres; r and phi: the current table)
+void launch_relax(const SegLayout& L, double* vr, double* vt, double* m, const uint32_t* id,
+                  const double* nbin, const uint32_t* step, cudaStream_t st, int variant = 0,
+                  double* R = nullptr, const double* r = nullptr, const double* phi = nullptr);
+// Eq. 8's collision timestep into the segments' timesteps (R: stellar radii)
+void launch_tcoll(const SegLayout& L, const double* r, const double* vr, const double* vt,
+                  const double* m, const double* R, cudaStream_t st);
 
 struct OrbitStageOut {   // optional per-star outputs of the orbit stage
   double* phi_new = nullptr;
@@ -235,7 +241,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
                   uint32_t* plist, uint32_t* pcount, cudaStream_t st,
-                  bool with_turning = true);
+                  bool with_turning = true, const double* Rv = nullptr, double* Rp = nullptr);
 // the turning-point kernel alone (mixed mode; launch_orbit(..., false)
 // then runs the sampling kernel only)
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,

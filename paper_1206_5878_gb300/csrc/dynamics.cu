@@ -87,10 +87,26 @@ __global__ void __launch_bounds__(256) k_bins(Seg S, int bs, double pref, const 
 // pair's random draws come from its first star (counters keyed by its id,
 // or its stream, kept after the draws).  kMinB: resident 128-thread blocks
 // to fit per SM (caps the registers; 1 = no cap), a launch shape only.
+//
+// With stellar radii (col.R) the pair may merge instead (sticky spheres,
+// section 2.1 step 3(iii)): with probability n pi (R1 + R2)^2 (1 + 2 G
+// (m1 + m2) / ((R1 + R2) |w|^2)) |w| dt, decided by one draw of the pair
+// after the azimuth psi, star a takes the total mass, the pair's 3-D
+// momentum and the radius (R1^3 + R2^3)^(1/3); star b gets mass 0 and
+// radius -1 (it leaves in the orbit step).  The merger's change of K + W,
+// -(m1 m2 / (m1 + m2)) |w|^2 / 2 + m_b (Phi_a - Phi_b) + m_a m_b / r_a,
+// is counted (fixed point, 2^-62).
+struct Collide {
+  double* R = nullptr;        // stellar radii (null: no collisions)
+  const double* r = nullptr;  // the current radii and potential
+  const double* phi = nullptr;
+};
+
 template <bool kTaus, int kMinB>
 __global__ void __launch_bounds__(128, kMinB) k_relax(Seg S, int bs, double* vr, double* vt,
-                                               const double* m, const uint32_t* id,
-                                               const double* nbin, const uint32_t* step_p) {
+                                               double* m, const uint32_t* id,
+                                               const double* nbin, const uint32_t* step_p,
+                                               Collide col) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= S.pair_off[S.n_seg]) return;
   const int c = seg_find(S.pair_off, S.n_seg, p);
@@ -120,6 +136,35 @@ __global__ void __launch_bounds__(128, kMinB) k_relax(Seg S, int bs, double* vr,
     return;
   }
   const double w = sqrt_rn(w2);
+  if (col.R) {
+    const double R1 = col.R[a], R2 = col.R[b];
+    if (R1 + R2 > 0.0) {
+      const double Rs = R1 + R2;
+      const double focus = 1.0 + div_rn(2.0 * msum, Rs * w2);
+      const double sig = (kPi * (Rs * Rs)) * focus;
+      const double Pc = ((sig * n) * w) * dt;
+      const U4 cw = g.block(kTagCol, 0u);
+      if (u01(cw.x, cw.y) < Pc) {
+        const double vcx = div_rn(m1 * v1x + m2 * v2x, msum);
+        const double vcy = div_rn(m1 * v1y + m2 * v2y, msum);
+        const double vcz = div_rn(m1 * v1z + m2 * v2z, msum);
+        const double dW = m2 * (col.phi[a] - col.phi[b]) + div_rn(m1 * m2, col.r[a]);
+        const double dK = (0.5 * div_rn(m1 * m2, msum)) * w2;
+        draws_keep(S, c, g);
+        vr[a] = vcx;
+        vt[a] = sqrt_rn(vcy * vcy + vcz * vcz);
+        m[a] = m1 + m2;
+        col.R[a] = cbrt_newton(R1 * R1 * R1 + R2 * R2 * R2);
+        m[b] = 0.0;
+        col.R[b] = -1.0;
+        stat_add(S.stats, c, kStCollisions, 1ull);
+        const long long e = __double2ll_rn((dW - dK) * 4611686018427387904.0);  // 2^62
+        stat_add(S.stats, c, kStCollisionEnergy, (unsigned long long)e);
+        if (fails) stat_add(S.stats, c, kStAngleFails, (unsigned long long)fails);
+        return;
+      }
+    }
+  }
   // sin^2(beta/2) = min(1, 2 pi G^2 (m1+m2)^2 n lnL dt / |w|^3)
   double num = (2.0 * kPi) * msum;
   num = num * msum;
@@ -192,6 +237,42 @@ __global__ void k_taus_init(int64_t slots, int n_seg, const int64_t* base, const
   table[e] = make_uint4(v[0], v[1], v[2], v[3]);
 }
 
+// Eq. 8's collision timestep over the innermost P = min(300, nb) bound stars
+// of each segment (one warp per segment, one lane summing in star order, as
+// the FP64 statement of the method does), into the segment's timestep (the
+// minimum with Eq. 7's):
+//   1 / T_coll = 16 sqrt(pi) n_s <R^2> sigma (1 + G <M R> / (2 sigma^2 <R^2>)),
+// n_s = 3 (P - 1) / (4 pi (r_{P-1}^3 - r_0^3)), sigma^2 = <v_r^2 + v_t^2> / 3.
+__global__ void k_tcoll(Seg S, const double* r, const double* vr, const double* vt,
+                        const double* m, const double* R) {
+  const int c = blockIdx.x;
+  if (threadIdx.x != 0 || c >= S.n_seg) return;
+  const int64_t nb = S.nb[c], sb = S.off[c];
+  const int64_t P = nb < 300 ? nb : 300;
+  if (P < 2) return;
+  const double* rr = r + sb;
+  const double vol = rr[P - 1] * rr[P - 1] * rr[P - 1] - rr[0] * rr[0] * rr[0];
+  if (!(vol > 0.0)) return;
+  const double ns = (3.0 * (double)(P - 1)) / ((4.0 * kPi) * vol);
+  double sv = 0.0, sr = 0.0, smr = 0.0;
+  for (int64_t k = 0; k < P; ++k) {
+    const int64_t p = sb + k;
+    sv = sv + (vr[p] * vr[p] + vt[p] * vt[p]);
+    sr = sr + R[p] * R[p];
+    smr = smr + m[p] * R[p];
+  }
+  const double sig2 = (sv / (double)P) / 3.0;
+  const double R2 = sr / (double)P;
+  const double MR = smr / (double)P;
+  if (!(R2 > 0.0) || !(sig2 > 0.0)) return;
+  const double sig = sqrt(sig2);
+  double inv = (((16.0 * sqrt(kPi)) * ns) * R2) * sig;
+  inv = inv * (1.0 + MR / ((2.0 * sig2) * R2));
+  const double T = 1.0 / inv;
+  if (T < __longlong_as_double(0x7FF0000000000000ll))
+    atomicMin((unsigned long long*)(S.dt_bits + c), (unsigned long long)__double_as_longlong(T));
+}
+
 }  // namespace
 
 void launch_taus_init(int64_t slots, int n_seg, const int64_t* base, const uint4* words,
@@ -199,6 +280,12 @@ void launch_taus_init(int64_t slots, int n_seg, const int64_t* base, const uint4
   if (slots > 0)
     k_taus_init<<<(unsigned)((slots + 255) / 256), 256, 0, st>>>(slots, n_seg, base, words, P,
                                                                  table);
+}
+
+void launch_tcoll(const SegLayout& L, const double* r, const double* vr, const double* vt,
+                  const double* m, const double* R, cudaStream_t st) {
+  if (!L.n || !R) return;
+  k_tcoll<<<(unsigned)L.n_seg, 32, 0, st>>>(L.dev(), r, vr, vt, m, R);
 }
 
 void launch_bins(const SegLayout& L, const double* r, const double* vr, const double* vt,
@@ -209,25 +296,31 @@ void launch_bins(const SegLayout& L, const double* r, const double* vr, const do
 }
 
 template <int kMinB>
-static void relax_shape(const SegLayout& L, double* vr, double* vt, const double* m,
+static void relax_shape(const SegLayout& L, double* vr, double* vt, double* m,
                         const uint32_t* id, const double* nbin, const uint32_t* step,
-                        cudaStream_t st) {
+                        const Collide& col, cudaStream_t st) {
   const unsigned grid = (unsigned)((L.n_pairs + 127) / 128);
   if (L.taus)
-    k_relax<true, kMinB><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin, step);
+    k_relax<true, kMinB><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin, step,
+                                               col);
   else
     k_relax<false, kMinB><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin,
-                                                step);
+                                                step, col);
 }
 
-void launch_relax(const SegLayout& L, double* vr, double* vt, const double* m,
-                  const uint32_t* id, const double* nbin, const uint32_t* step,
-                  cudaStream_t st, int variant) {
+void launch_relax(const SegLayout& L, double* vr, double* vt, double* m, const uint32_t* id,
+                  const double* nbin, const uint32_t* step, cudaStream_t st, int variant,
+                  double* R, const double* r, const double* phi) {
   if (!L.n_pairs) return;
+  Collide col;
+  col.R = R;
+  col.r = r;
+  col.phi = phi;
   // variants: registers capped for 1 (no cap), 6 or 8 resident blocks per SM
-  if (variant == 1) relax_shape<6>(L, vr, vt, m, id, nbin, step, st);
-  else if (variant == 2) relax_shape<8>(L, vr, vt, m, id, nbin, step, st);
-  else relax_shape<1>(L, vr, vt, m, id, nbin, step, st);
+  if (variant == 1) relax_shape<6>(L, vr, vt, m, id, nbin, step, col, st);
+  else if (variant == 2) relax_shape<8>(L, vr, vt, m, id, nbin, step, col, st);
+  else relax_shape<1>(L, vr, vt, m, id, nbin, step, col, st);
 }
+
 
 }  // namespace cmc

@@ -985,7 +985,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
                                                uint64_t* keys, Payload* pay, int64_t* esc,
                                                OrbitStageOut dbg, BucketArgs BA,
                                                const double* tp_min, const double* tp_max,
-                                               int64_t n) {
+                                               int64_t n, const double* Rv, double* Rp) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int c = seg_find(S.off, S.n_seg, p);
@@ -1001,11 +1001,24 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
   unsigned long long viol = 0;
   bool escaped = false;
 
+  if (Rp) Rp[p] = Rv[p];  // the stellar radius goes with the star
   if (k >= nbc) {
     // escaped in an earlier step: stays at the end, ordered by id
     keys[p] = radius_key(rk, idk);
     pay[p] = P;
     if (dbg.code) dbg.code[p] = 1;
+    return;
+  }
+  if (Rv && lt0(Rv[p])) {
+    // merged into its partner in this step (sticky spheres): it leaves
+    // with no mass, draws nothing, and carries off no energy
+    keys[p] = radius_key(__longlong_as_double(0x7FF0000000000000ll), idk);
+    pay[p] = P;
+    if (dbg.code) dbg.code[p] = 1;
+    const unsigned full = __activemask();
+    const unsigned peers = __match_any_sync(full, c);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1)
+      atomicAdd((unsigned long long*)(esc + c), (unsigned long long)__popc(peers));
     return;
   }
   const Table64 T{r + sb, x + sb, phi + sb, nbc};
@@ -1444,7 +1457,8 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   const uint32_t* step,
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
-                  uint32_t* plist, uint32_t* pcount, cudaStream_t st, bool with_turning) {
+                  uint32_t* plist, uint32_t* pcount, cudaStream_t st, bool with_turning,
+                  const double* Rv, double* Rp) {
   if (!L.n) return;
   OrbitStageOut d;
   if (dbg) d = *dbg;
@@ -1458,7 +1472,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
 #define CMC_ORBIT(P, B, T)                                                                  \
   k_orbit<P, B, T><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, Menc, vr, vt, \
                                            m, id, step, keys, pay, L.esc_step, d, ba, tp_min, \
-                                           tp_max, L.n)
+                                           tp_max, L.n, Rv, Rp)
 #define CMC_MIXED(B, T)                                                                     \
   do {                                                                                      \
     if (with_turning) CMC_TURN(B);                                                          \

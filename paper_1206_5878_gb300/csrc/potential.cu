@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_sums(
     Seg S, const int64_t* esc, int64_t n, const uint64_t* __restrict__ keys,
     const uint32_t* __restrict__ vals, const Payload* __restrict__ pay, double* r, double* x,
     double* vr, double* vt, double* m, uint32_t* id, double* r_old, double* c, double* tile_m,
-    double* tile_mx) {
+    double* tile_mx, const double* Rp, double* Rout) {
   __shared__ double s[kThreads];
   TR R = tile_of(S, esc, blockIdx.x, true);
   double am = 0.0, ax = 0.0;
@@ -155,6 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_sums(
     r[p] = rr; x[p] = xx; vr[p] = P.vr; vt[p] = P.vt; m[p] = P.m; id[p] = P.id;
     r_old[p] = P.r_old;
     c[p] = P.c;
+    if (Rout) Rout[p] = Rp[v];
     if (p < R.bound_end) {
       am = am + P.m;
       ax = ax + P.m * xx;
@@ -706,7 +707,12 @@ __global__ void __launch_bounds__(256) k_step_end(Seg S, int64_t* esc, uint64_t*
     }
     dt_last[c] = S.dt_bits[c];
     S.nb[c] = nb_new;
-    S.stats[(size_t)c * kStStride + kStEscaped] += (unsigned long long)ne;
+    // the stars merged away in this step (sticky spheres) left with the
+    // escapers; they are counted as collisions, not as escapes
+    unsigned long long* st = S.stats + (size_t)c * kStStride;
+    const unsigned long long merged = st[kStCollisions] - st[kStCollisionsSeen];
+    st[kStCollisionsSeen] = st[kStCollisions];
+    st[kStEscaped] += (unsigned long long)ne - merged;
     esc[c] = 0;
     S.dt_bits[c] = 0x7FF0000000000000ull;
     if (c == 0) *step += 1u;
@@ -867,12 +873,12 @@ void launch_rekey_radius(const SegLayout& L, const uint32_t* perm, const double*
 void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* vals,
                    const Payload* pay, double* r, double* x, double* vr, double* vt,
                    double* m, uint32_t* id, double* r_old, double* c, cudaStream_t st,
-                   double* tile_m, double* tile_mx) {
+                   double* tile_m, double* tile_mx, const double* Rp, double* Rout) {
   if (!L.n) return;
   if (tile_m && tile_mx && r_old && c && L.n_tiles)
     k_gather_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(L.dev(), L.esc_step, L.n, keys, vals,
                                                             pay, r, x, vr, vt, m, id, r_old, c,
-                                                            tile_m, tile_mx);
+                                                            tile_m, tile_mx, Rp, Rout);
   else
     k_gather<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, keys, vals, pay, r, x, vr, vt, m, id,
                                                   r_old, c);
