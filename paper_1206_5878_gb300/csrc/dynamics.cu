@@ -102,7 +102,7 @@ struct Collide {
   const double* phi = nullptr;
 };
 
-template <bool kTaus, int kMinB>
+template <bool kTaus, int kMinB, bool kCol>
 __global__ void __launch_bounds__(128, kMinB) k_relax(Seg S, int bs, double* vr, double* vt,
                                                double* m, const uint32_t* id,
                                                const double* nbin, const uint32_t* step_p,
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(128, kMinB) k_relax(Seg S, int bs, double* vr,
     return;
   }
   const double w = sqrt_rn(w2);
-  if (col.R) {
+  if (kCol) {
     const double R1 = col.R[a], R2 = col.R[b];
     if (R1 + R2 > 0.0) {
       const double Rs = R1 + R2;
@@ -300,12 +300,20 @@ static void relax_shape(const SegLayout& L, double* vr, double* vt, double* m,
                         const uint32_t* id, const double* nbin, const uint32_t* step,
                         const Collide& col, cudaStream_t st) {
   const unsigned grid = (unsigned)((L.n_pairs + 127) / 128);
-  if (L.taus)
-    k_relax<true, kMinB><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin, step,
-                                               col);
+  // (the collision code only in the kernels that need it: it costs
+  // registers)
+  if (L.taus && col.R)
+    k_relax<true, kMinB, true><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin,
+                                                     step, col);
+  else if (L.taus)
+    k_relax<true, kMinB, false><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin,
+                                                      step, col);
+  else if (col.R)
+    k_relax<false, kMinB, true><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin,
+                                                      step, col);
   else
-    k_relax<false, kMinB><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id, nbin,
-                                                step, col);
+    k_relax<false, kMinB, false><<<grid, 128, 0, st>>>(L.dev(), L.bin_size, vr, vt, m, id,
+                                                       nbin, step, col);
 }
 
 void launch_relax(const SegLayout& L, double* vr, double* vt, double* m, const uint32_t* id,
