@@ -521,12 +521,20 @@ def run_cmc(args, rank, world, local_rank):
     achieved = nflops / (dom_ms / 1e3) / 1e9
     tun = c.tuning()
     traffic_ps = profiled_traffic_per_star(kname, args.precision)
+    alg_bytes = STAGE_BYTES[dom] * n
     roof = {"kernel": kname, "stage": dom, "bound": "alu", "achieved": achieved,
             "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s", "frac": achieved / FP64_PEAK_GFLOPS,
             "peak_source": "derived (FP64): 152 SMs x 2 FMA lanes/clock x 2 flop x 2.07 GHz",
             "algorithmic_flops_per_launch": nflops,
             "traffic": None if traffic_ps is None else traffic_ps * n,
             "launch_ms": dom_ms,
+            # the same kernel against HBM: its compulsory bytes, and the
+            # DRAM bytes ncu measured (when the profile is current)
+            "algorithmic_bytes_per_launch": alg_bytes,
+            "hbm_frac_algorithmic": alg_bytes / (dom_ms / 1e3) / 1e9 / hbm,
+            "hbm_frac_dram": None if traffic_ps is None
+            else traffic_ps * n / (dom_ms / 1e3) / 1e9 / hbm,
+            "hbm_peak_gbs": hbm, "hbm_peak_source": peak_kind,
             "note": "FP64 operations of the kernel's formulas (+, -, x, /, sqrt once each); "
                     "compiled without FMA contraction for bit-exact parity, so half the FMA "
                     "peak is the issue ceiling, and / and sqrt take several FP64 issues each"}

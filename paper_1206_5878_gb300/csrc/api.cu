@@ -244,9 +244,9 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
 int count_step_kernels(const cmc_ctx* c) {
   // bins, relax, orbit, upsweep, hist scan, 5 passes, tie fix, gather with
   // the tile sums, potential, [turning points, FP32 sampler, FP64
-  // continuation, slopes at the tile seams, 2 bucket-index + 2 grid
+  // continuation, slopes at the tile seams, 2 bucket-index + 3 grid
   // kernels], [correction], step end
-  return 3 + (c->R ? 1 : 0) + 2 + 5 + 1 + 1 + 1 + (c->cfg.precision == 1 ? 8 : 0) +
+  return 3 + (c->R ? 1 : 0) + 2 + 5 + 1 + 1 + 1 + (c->cfg.precision == 1 ? 9 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 

@@ -452,6 +452,14 @@ __device__ __forceinline__ void draws_keep(const Seg& S, int c, const Draws<kTau
   if (kTaus) S.taus[__ldg(S.taus_base + c) + d.id] = d.z;
 }
 
+// Non-inlined copies of div_rn and sqrt_rn for kernels with many call
+// sites: each inlined copy is ~150 instructions, and a kernel holding a
+// dozen of them no longer fits the instruction cache (ncu: instruction
+// fetch the relaxation kernel's largest stall); one shared body costs a
+// call per use instead (measured: relaxation 1.46 -> 1.06 ms at N = 1e7).
+static __device__ __noinline__ double div_rn_nl(double a, double b) { return div_rn(a, b); }
+static __device__ __noinline__ double sqrt_rn_nl(double x) { return sqrt_rn(x); }
+
 // uniform planar direction (cos a, sin a) by rejection of a point in the
 // unit disk; the doubled angle gives cos = (u^2 - v^2)/q, sin = 2uv/q.
 //
@@ -460,9 +468,10 @@ __device__ __forceinline__ void draws_keep(const Seg& S, int c, const Draws<kTau
 // below 2), so outside a band of 2^54 around 2^104 the exact integer test
 // U^2 + V^2 <= 2^104 (128-bit) gives the same answer; inside the band the
 // FP64 expression decides.  The loop is integer work only; the FP64
-// arithmetic of the accepted draw runs once, after it.
+// arithmetic of the accepted draw runs once, after it.  Not inlined: one
+// copy serves both of the relaxation's angles (code size, as for div_rn_nl).
 template <bool kTaus>
-__device__ __forceinline__ bool disk_angle(Draws<kTaus>& g, uint32_t tag, double& c, double& s) {
+__device__ __noinline__ bool disk_angle(Draws<kTaus>& g, uint32_t tag, double& c, double& s) {
   int64_t Ua = 0, Va = 0;
   bool ok = false;
   for (uint32_t t = 0; t < 64u; ++t) {
@@ -496,8 +505,8 @@ __device__ __forceinline__ bool disk_angle(Draws<kTaus>& g, uint32_t tag, double
   }
   const double u = sym_double(Ua), v = sym_double(Va);
   const double uu = u * u, vv = v * v, q = uu + vv;
-  c = div_rn(uu - vv, q);
-  s = div_rn(scale_up<1>(u) * v, q);
+  c = div_rn_nl(uu - vv, q);
+  s = div_rn_nl(scale_up<1>(u) * v, q);
   return true;
 }
 

@@ -201,6 +201,7 @@ struct BucketWork {
   uint32_t* base = nullptr;
   int4* prm = nullptr;
   float* gphi = nullptr;
+  int* gshell = nullptr;  // shell of every grid key (scratch of the grid build)
   int64_t* goff = nullptr;
   int4* gprm = nullptr;
   float4* gaux = nullptr;

@@ -135,24 +135,24 @@ __global__ void __launch_bounds__(128, kMinB) k_relax(Seg S, int bs, double* vr,
     if (fails) stat_add(S.stats, c, kStAngleFails, (unsigned long long)fails);
     return;
   }
-  const double w = sqrt_rn(w2);
+  const double w = sqrt_rn_nl(w2);
   if (kCol) {
     const double R1 = col.R[a], R2 = col.R[b];
     if (R1 + R2 > 0.0) {
       const double Rs = R1 + R2;
-      const double focus = 1.0 + div_rn(2.0 * msum, Rs * w2);
+      const double focus = 1.0 + div_rn_nl(2.0 * msum, Rs * w2);
       const double sig = (kPi * (Rs * Rs)) * focus;
       const double Pc = ((sig * n) * w) * dt;
       const U4 cw = g.block(kTagCol, 0u);
       if (u01(cw.x, cw.y) < Pc) {
-        const double vcx = div_rn(m1 * v1x + m2 * v2x, msum);
-        const double vcy = div_rn(m1 * v1y + m2 * v2y, msum);
-        const double vcz = div_rn(m1 * v1z + m2 * v2z, msum);
-        const double dW = m2 * (col.phi[a] - col.phi[b]) + div_rn(m1 * m2, col.r[a]);
-        const double dK = (0.5 * div_rn(m1 * m2, msum)) * w2;
+        const double vcx = div_rn_nl(m1 * v1x + m2 * v2x, msum);
+        const double vcy = div_rn_nl(m1 * v1y + m2 * v2y, msum);
+        const double vcz = div_rn_nl(m1 * v1z + m2 * v2z, msum);
+        const double dW = m2 * (col.phi[a] - col.phi[b]) + div_rn_nl(m1 * m2, col.r[a]);
+        const double dK = (0.5 * div_rn_nl(m1 * m2, msum)) * w2;
         draws_keep(S, c, g);
         vr[a] = vcx;
-        vt[a] = sqrt_rn(vcy * vcy + vcz * vcz);
+        vt[a] = sqrt_rn_nl(vcy * vcy + vcz * vcz);
         m[a] = m1 + m2;
         col.R[a] = cbrt_newton(R1 * R1 * R1 + R2 * R2 * R2);
         m[b] = 0.0;
@@ -171,11 +171,11 @@ __global__ void __launch_bounds__(128, kMinB) k_relax(Seg S, int bs, double* vr,
   num = num * n;
   num = num * lnL;
   num = num * dt;
-  double s2 = div_rn(num, w2 * w);
+  double s2 = div_rn_nl(num, w2 * w);
   if (!le1(s2)) s2 = 1.0;
   // cos(beta) = 1 - 2 sin^2(beta/2), sin(beta) = 2 sin(beta/2) cos(beta/2)
   const double cosb = 1.0 - scale_up<1>(s2);
-  const double sinb = scale_up<1>(sqrt_rn(s2)) * sqrt_rn(1.0 - s2);
+  const double sinb = scale_up<1>(sqrt_rn_nl(s2)) * sqrt_rn_nl(1.0 - s2);
   if (!disk_angle(g, kTagPhi, cphi, sphi)) ++fails;
   draws_keep(S, c, g);
   // e1 = (w x xhat)/|w x xhat| = (0, wz, -wy)/|.| (yhat for radial w);
@@ -183,9 +183,9 @@ __global__ void __launch_bounds__(128, kMinB) k_relax(Seg S, int bs, double* vr,
   const double wp2 = wy * wy + wz * wz;
   double e1y, e1z;
   if (pos_num(wp2)) {
-    const double wp = sqrt_rn(wp2);
-    e1y = div_rn(wz, wp);
-    e1z = div_rn(-wy, wp);
+    const double wp = sqrt_rn_nl(wp2);
+    e1y = div_rn_nl(wz, wp);
+    e1z = div_rn_nl(-wy, wp);
   } else {
     e1y = 1.0;
     e1z = 0.0;
@@ -203,13 +203,13 @@ __global__ void __launch_bounds__(128, kMinB) k_relax(Seg S, int bs, double* vr,
   // balance the FP64 pipe's load against the integer pipes' (measured: all
   // of the kernel's products there made it a third slower, none of them 2%
   // slower)
-  const double f1 = div_rn(m2, msum), f2 = div_rn(m1, msum);
+  const double f1 = div_rn_nl(m2, msum), f2 = div_rn_nl(m1, msum);
   const double p1x = v1x + mul_rn(f1, dwx), p1y = v1y + mul_rn(f1, dwy), p1z = v1z + mul_rn(f1, dwz);
   const double p2x = v2x - mul_rn(f2, dwx), p2y = v2y - mul_rn(f2, dwy), p2z = v2z - mul_rn(f2, dwz);
   vr[a] = p1x;
-  vt[a] = sqrt_rn(p1y * p1y + p1z * p1z);
+  vt[a] = sqrt_rn_nl(p1y * p1y + p1z * p1z);
   vr[b] = p2x;
-  vt[b] = sqrt_rn(p2y * p2y + p2z * p2z);
+  vt[b] = sqrt_rn_nl(p2y * p2y + p2z * p2z);
   if (fails) stat_add(S.stats, c, kStAngleFails, (unsigned long long)fails);
 }
 

@@ -1269,49 +1269,79 @@ __global__ void k_grid_params(Seg S, const int64_t* esc, bool sub, const double*
   gaux[c] = make_float4((float)phi[sb], (float)Menc[sb + nb - 1], __uint_as_float(key0), 0.f);
 }
 
-// Phi at every grid key from the FP64 table: shell = the last star with
-// 1/r_i >= 1/r (bisection), Phi = Phi_i + M_i (1/r_i - 1/r) (Eq. 6 with
-// the enclosed-mass slope), rounded to float
-__global__ void k_grid_build(Seg S, const int64_t* esc, bool sub, const double* x,
-                             const double* phi, const double* Menc, BucketArgs B, float* gphi,
-                             float4* gaux, int64_t total) {
+// The shell of every grid key, largest i with 1/r_i >= key (-1 when none),
+// written by the stars: star k owns the keys in (1/r_{k+1}, 1/r_k], i.e. the
+// cells from gmax(k + 1) + 1 to gmax(k), gmax(k) = the last cell whose key
+// is <= 1/r_k.  A key (a positive float) is <= 1/r_k exactly when its bits
+// are <= those of 1/r_k rounded down to a float, so gmax is integer
+// arithmetic on those bits.  The outermost star also owns the cells below
+// it, the innermost one the cells above it (shell -1).  Every cell is
+// written once; the work is one pass over the stars and the cells.
+__device__ __forceinline__ int64_t grid_last_cell(double xk, int4 pr) {
+  const uint32_t kb = __float_as_uint(__double2float_rd(xk));
+  if (kb < (uint32_t)pr.x) return -1;
+  const int64_t g = (int64_t)((kb - (uint32_t)pr.x) >> pr.y);
+  return g < pr.z - 1 ? g : (int64_t)pr.z - 1;
+}
+
+__global__ void k_grid_shells(Seg S, const int64_t* esc, bool sub, const double* x,
+                              BucketArgs B, int* gshell, int64_t n) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int c = seg_find(S.off, S.n_seg, p);
+  int64_t nb = S.nb[c];
+  if (sub) nb -= esc[c];
+  const int64_t sb = S.off[c], k = p - sb;
+  if (k >= nb) return;
+  const int4 pr = B.gprm[c];
+  if (pr.z <= 0) return;
+  int* sh = gshell + B.goff[c];
+  const int64_t hi = grid_last_cell(__ldg(x + p), pr);
+  const int64_t lo = k + 1 < nb ? grid_last_cell(__ldg(x + p + 1), pr) + 1 : 0;
+  for (int64_t g = lo; g <= hi; ++g) sh[g] = (int)k;
+  if (k == 0)
+    for (int64_t g = hi + 1; g < pr.z; ++g) sh[g] = -1;
+}
+
+// Phi at every grid key from the FP64 table: Phi = Phi_i + M_i (1/r_i - 1/r)
+// in the key's shell i (Eq. 6 with the enclosed-mass slope), Phi_0 inside
+// the first star, rounded to float
+__global__ void k_grid_build(Seg S, const int64_t* esc, bool sub, const double* x,
+                             const double* phi, const double* Menc, BucketArgs B,
+                             const int* gshell, float* gphi, float4* gaux, int64_t total) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned am = __ballot_sync(0xFFFFFFFFu, p < total);
   if (p >= total) return;
   const int c = seg_find(B.goff, S.n_seg, p);
   const int4 pr = B.gprm[c];
   const int g = (int)(p - B.goff[c]);
-  if (g >= pr.z) return;
-  int64_t nb = S.nb[c];
-  if (sub) nb -= esc[c];
-  const int64_t sb = S.off[c];
-  const double xg = (double)__uint_as_float((uint32_t)pr.x + ((uint32_t)g << pr.y));
-  const double xn = (double)__uint_as_float((uint32_t)pr.x + ((uint32_t)(g + 1) << pr.y));
-  int64_t lo = -1, hi = nb, lo2 = -1, hi2 = nb;
-  while (hi - lo > 1 || hi2 - lo2 > 1) {
-    if (hi - lo > 1) {
-      const int64_t mid = lo + ((hi - lo) >> 1);
-      if (__ldg(x + sb + mid) >= xg) lo = mid; else hi = mid;
-    }
-    if (hi2 - lo2 > 1) {
-      const int64_t mid = lo2 + ((hi2 - lo2) >> 1);
-      if (__ldg(x + sb + mid) >= xn) lo2 = mid; else hi2 = mid;
+  float rel = 0.0f;
+  if (g < pr.z) {
+    const int64_t sb = S.off[c];
+    const double xg = (double)__uint_as_float((uint32_t)pr.x + ((uint32_t)g << pr.y));
+    const double xn = (double)__uint_as_float((uint32_t)pr.x + ((uint32_t)(g + 1) << pr.y));
+    const int64_t lo = gshell[p];
+    const double ph = lo < 0 ? __ldg(phi + sb)
+                             : __ldg(phi + sb + lo) + __ldg(Menc + sb + lo) * (__ldg(x + sb + lo) - xg);
+    gphi[p] = (float)ph;
+    // Phi is convex in 1/r (its slope -M(1/r) rises with 1/r), so inside the
+    // cell [xg, xn] it lies below the chord by at most (xn - xg) dM / 4, dM
+    // the mass of the stars in the cell; relative to |Phi(xg)|, the smallest
+    // |Phi| of the cell, the largest over the segment's cells bounds the
+    // grid's interpolation error (gaux.w; floats >= 0 order as their bits)
+    if (g + 1 < pr.z && ph < 0.0) {
+      const int64_t lo2 = gshell[p + 1];
+      const double Ma = lo < 0 ? 0.0 : __ldg(Menc + sb + lo);
+      const double Mb = lo2 < 0 ? 0.0 : __ldg(Menc + sb + lo2);
+      const double dM = Ma - Mb;
+      rel = (float)(((xn - xg) * (dM > 0.0 ? dM : 0.0) * 0.25) / -ph);
     }
   }
-  const double ph = lo < 0 ? __ldg(phi + sb)
-                           : __ldg(phi + sb + lo) + __ldg(Menc + sb + lo) * (__ldg(x + sb + lo) - xg);
-  gphi[p] = (float)ph;
-  // Phi is convex in 1/r (its slope -M(1/r) rises with 1/r), so inside the
-  // cell [xg, xn] it lies below the chord by at most (xn - xg) dM / 4, dM
-  // the mass of the stars in the cell; relative to |Phi(xg)|, the smallest
-  // |Phi| of the cell, the largest over the segment's cells bounds the
-  // grid's interpolation error (gaux.w; floats >= 0 order as their bits)
-  if (g + 1 < pr.z && ph < 0.0) {
-    const double Ma = lo < 0 ? 0.0 : __ldg(Menc + sb + lo);
-    const double Mb = lo2 < 0 ? 0.0 : __ldg(Menc + sb + lo2);
-    const double dM = Ma - Mb;
-    const float rel = (float)(((xn - xg) * (dM > 0.0 ? dM : 0.0) * 0.25) / -ph);
-    atomicMax(reinterpret_cast<unsigned int*>(&gaux[c].w), __float_as_uint(rel));
-  }
+  // one atomic per segment present in the warp
+  const unsigned grp = __match_any_sync(am, c);
+  const unsigned mx = __reduce_max_sync(grp, __float_as_uint(rel));
+  if ((threadIdx.x & 31) == (unsigned)(__ffs(grp) - 1) && mx)
+    atomicMax(reinterpret_cast<unsigned int*>(&gaux[c].w), mx);
 }
 
 // per segment: the indexed node range lo..hi, base = bits(x_lo), the
@@ -1392,6 +1422,7 @@ cudaError_t alloc_buckets(BucketWork& B, const SegLayout& L, cudaStream_t st) {
   if ((e = cudaMallocAsync((void**)&B.base, sizeof(uint32_t) * L.n_seg, st))) return e;
   if ((e = cudaMallocAsync((void**)&B.prm, sizeof(int4) * L.n_seg, st))) return e;
   if ((e = cudaMallocAsync((void**)&B.gphi, sizeof(float) * B.gcells, st))) return e;
+  if ((e = cudaMallocAsync((void**)&B.gshell, sizeof(int) * B.gcells, st))) return e;
   if ((e = cudaMallocAsync((void**)&B.goff, sizeof(int64_t) * (L.n_seg + 1), st))) return e;
   if ((e = cudaMallocAsync((void**)&B.gprm, sizeof(int4) * L.n_seg, st))) return e;
   if ((e = cudaMallocAsync((void**)&B.gaux, sizeof(float4) * L.n_seg, st))) return e;
@@ -1407,7 +1438,8 @@ cudaError_t alloc_buckets(BucketWork& B, const SegLayout& L, cudaStream_t st) {
 }
 
 void free_buckets(BucketWork& B, cudaStream_t st) {
-  void* ps[] = {B.start, B.off, B.base, B.prm, B.gphi, B.goff, B.gprm, B.gaux, B.node, B.tdf};
+  void* ps[] = {B.start, B.off, B.base, B.prm, B.gphi, B.gshell, B.goff, B.gprm, B.gaux, B.node,
+                B.tdf};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, st);
   B = BucketWork();
@@ -1418,8 +1450,10 @@ void launch_grid(const SegLayout& L, const double* x, const double* phi, const d
   if (!L.n || !B.gcells) return;
   k_grid_params<<<(unsigned)((L.n_seg + 127) / 128), 128, 0, st>>>(
       L.dev(), L.esc_step, nb_sub, x, phi, Menc, B.goff, B.gprm, B.gaux);
+  k_grid_shells<<<(unsigned)((L.n + 255) / 256), 256, 0, st>>>(L.dev(), L.esc_step, nb_sub, x,
+                                                              B.args(), B.gshell, L.n);
   k_grid_build<<<(unsigned)((B.gcells + 255) / 256), 256, 0, st>>>(
-      L.dev(), L.esc_step, nb_sub, x, phi, Menc, B.args(), B.gphi, B.gaux, B.gcells);
+      L.dev(), L.esc_step, nb_sub, x, phi, Menc, B.args(), B.gshell, B.gphi, B.gaux, B.gcells);
 }
 
 void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWork& B,
