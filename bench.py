@@ -302,6 +302,9 @@ def cpu_baseline(n: int, seed: int, n_orbit: int = 50_000):
 
 
 # ------------------------------------------------------------------ suite
+# cmc_config.precision of the bench's names
+PRECISIONS = {"fp64": 0, "mixed": 1, "fp64-bisection": 2}
+
 SUITE = [
     # name, N, masses, precisions, steps (the measured-workload list)
     ("plummer_1e4_fp64", 10_000, "equal", ("fp64",), 10),
@@ -342,7 +345,7 @@ def run_suite(args):
             cpu = cpu_baseline_full(n, masses) if n <= 100_000 else \
                 cpu_baseline(n, 1, n_orbit=20_000)["value"]
         for prec in precs:
-            c = g.Cluster(dev, seeds, sizes=sizes, precision=1 if prec == "mixed" else 0)
+            c = g.Cluster(dev, seeds, sizes=sizes, precision=PRECISIONS[prec])
             E0 = c.total_energy()
             c.step(2)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -483,7 +486,7 @@ def run_cmc(args, rank, world, local_rank):
     ranks = Ranks(rank, world, "cuda")
     seed = replica_seed(args.seed, rank)
     n = args.n
-    prec = 1 if args.precision == "mixed" else 0
+    prec = PRECISIONS[args.precision]
     log("rank %d: building Plummer N=%d seed=%d" % (rank, n, seed))
     d = ic.plummer(n, seed=seed)
     dev = {k: torch.from_numpy(d[k].view(np.int32) if k == "id" else d[k]).cuda()
@@ -544,7 +547,7 @@ def run_cmc(args, rank, world, local_rank):
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64+f32" if prec else "f64", "data": "synthetic",
+           "dtype": "f64+f32" if prec == 1 else "f64", "data": "synthetic",
            "config": {"workload": "Plummer N=%d equal-mass, %s orbits" % (n, args.precision)
                       + ("" if args.rng == "philox" else ", Tausworthe streams"),
                       "rng": args.rng,
@@ -567,8 +570,21 @@ def run_cmc(args, rank, world, local_rank):
         barrier()
         ms64 = max_over_ranks(e0.elapsed_time(e1))
         out["fp64"] = {"value": n * k64 * world / (ms64 / 1e3), "unit": UNIT,
-                       "ms_per_step": ms64 / k64, "steps": k64}
+                       "ms_per_step": ms64 / k64, "steps": k64,
+                       "path": "FP32 screening with error bounds, every decision FP64's"}
         c64.close()
+        # the same FP64 results by bisection on the FP64 table (one step)
+        cb = g.Cluster(dev, [seed], precision=2)
+        cb.step(1)
+        barrier()
+        e0.record(stream)
+        cb.step(1)
+        e1.record(stream)
+        barrier()
+        msb = max_over_ranks(e0.elapsed_time(e1))
+        out["fp64_bisection"] = {"value": n * world / (msb / 1e3), "unit": UNIT,
+                                 "ms_per_step": msb, "steps": 1}
+        cb.close()
 
     if args.e2e:
         # the public API with host buffers: per step, the state goes in from
@@ -612,7 +628,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cmc", choices=["cmc", "reference"])
     ap.add_argument("--n", type=int, default=10_000_000)
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--precision", default="mixed", choices=sorted(PRECISIONS))
     ap.add_argument("--rng", default="philox", choices=["philox", "taus113"],
                     help="draws: counter-based Philox (default) or the paper's combined "
                          "Tausworthe streams")

@@ -90,9 +90,16 @@ enum {
 };
 
 typedef struct {
-    int32_t precision;          /* 0: FP64 throughout; 1: mixed (orbit search,
-                                   bound and accept tests in FP32, turning
-                                   points and accepted orbit in FP64) */
+    int32_t precision;          /* 0: FP64: every result the FP64 method's
+                                   (searches, bounds and accept tests
+                                   screened in FP32 with error bounds, each
+                                   decision they cannot certify taken in
+                                   FP64); 1: mixed (as 0, but the envelope F
+                                   from FP32 samples: an equally valid
+                                   bound, a different accept sequence);
+                                   2: FP64 by bisection on the FP64 table
+                                   (Appendix A's kernels; the same results
+                                   as 0, slower) */
     int32_t bin_size;           /* stars per timestep bin, even, >= 2 (20) */
     double theta_max;           /* maximum deflection angle of Eq. 7 (pi/2) */
     double gamma;               /* Coulomb logarithm ln(gamma N) (0.1, Eq. 20) */
@@ -103,7 +110,7 @@ typedef struct {
                                    orbit block size when orbit_block is 0) on
                                    the real state and keep the fastest; results
                                    do not depend on the choice (default 1) */
-    int32_t orbit_variant;      /* mixed-mode orbit kernel variant (listed at
+    int32_t orbit_variant;      /* FP32 sampler kernel variant, precision 0 and 1 (listed at
                                    cmc_get_tuning): -1 = the autotuner's choice
                                    (0 without autotune), or 0..6 (default -1) */
     int32_t rng;                /* 0: counter-based Philox4x32-10 draws keyed by
@@ -304,7 +311,7 @@ cmc_status cmc_relax(int64_t n, double *vr, double *vt, const double *m, const u
  * per star r_new, vr_new, vt_new, phi_new (= Phi_old(r_new)), rmin, rmax,
  * F and code (0 moved, 1 escaped, 2 degenerate, 3 trial cap); escaped
  * stars get r_new = +inf.  Any output except r_new may be NULL.
- * precision: 0 FP64, 1 mixed. */
+ * precision: 0 FP64, 1 mixed, 2 FP64 by bisection (as cmc_config). */
 cmc_status cmc_orbit(int64_t n, const double *r, const double *phi, const double *vr,
                      const double *vt, const uint32_t *id, uint64_t seed, uint32_t step,
                      int32_t max_trials, int32_t precision, double *r_new, double *vr_new,

@@ -19,7 +19,7 @@ struct cmc_ctx {
   int device = 0;
   SegLayout L;
   SortWork W;
-  BucketWork bk;  // radius-bucket index of the float table (mixed mode)
+  BucketWork bk;  // radius-bucket index, grid and node records (precision 0 and 1)
   double pref = 0.0;
   // state (sorted SoA)
   double *r = nullptr, *x = nullptr, *vr = nullptr, *vt = nullptr, *m = nullptr,
@@ -35,13 +35,14 @@ struct cmc_ctx {
          *out3 = nullptr, *fr = nullptr, *lag = nullptr;
   uint32_t* err = nullptr;
   uint32_t* step = nullptr;
-  uint32_t* pcount = nullptr;  // pending stars of the mixed-mode orbit step
+  uint32_t* pcount = nullptr;  // pending stars of the sampled orbit step
+  double* Fx = nullptr;        // FP64 mode's envelope F of every star (precision 0)
   int64_t steps_taken = 0;
   cudaGraphExec_t exec = nullptr;
   bool poisoned = false;
   std::string last_error;
   int kernels_per_step = 0;
-  int orbit_variant = 0;  // mixed-mode orbit kernel variant (see kOrbitVariants)
+  int orbit_variant = 0;  // sampler kernel variant (see kOrbitVariants)
   int relax_variant = 0;  // relaxation kernel variant (see kRelaxVariants)
   // stellar radii (cfg.collisions): the state's, and their copy through the sort
   double *R = nullptr, *Rp = nullptr;
@@ -170,11 +171,13 @@ void order_state(cmc_ctx* c, cudaStream_t st) {
   }
   launch_nb_from_keys(L, c->keys, st);
   cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
-  const bool mixed = c->cfg.precision == 1;
+  // the float tables, node records and indexes of the sampled orbit step
+  // (precision 0 and 1)
+  const bool tab = c->cfg.precision != 2;
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32,
-                   mixed ? c->Mbuf : nullptr, false, st, mixed ? c->bk.node : nullptr,
-                   mixed ? c->bk.tdf : nullptr, false, true);
-  if (mixed) {
+                   tab ? c->Mbuf : nullptr, false, st, tab ? c->bk.node : nullptr,
+                   tab ? c->bk.tdf : nullptr, false, true);
+  if (tab) {
     launch_buckets(L, c->t32, false, c->bk, st);
     launch_grid(L, c->x, c->phi, c->Mbuf, false, c->bk, st);
   }
@@ -184,7 +187,7 @@ void order_state(cmc_ctx* c, cudaStream_t st) {
 // event is recorded before the first stage and after every stage.
 void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   const SegLayout& L = c->L;
-  const bool mixed = c->cfg.precision == 1;
+  const bool mixed = c->cfg.precision == 1, tab = c->cfg.precision != 2;
   auto mark = [&](int i) {
     if (ev) cudaEventRecord(ev[i], st);
   };
@@ -196,14 +199,15 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
                c->phi);
   mark(2);
   // turning points into r_old, c (free until the gather), then sampling
-  if (mixed)
+  if (tab)
     launch_turning(L, c->r, c->x, c->phi, c->Mbuf, c->vr, c->vt, c->bk.args(), c->r_old,
                    c->cc, c->cfg.orbit_block, st);
   mark(3);
   launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
-               mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
+               tab ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
                c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
-               c->bk.args(), c->r_old, c->cc, c->vals, c->pcount, st, false, c->R, c->Rp);
+               c->bk.args(), c->r_old, c->cc, c->vals, c->pcount, st, false, c->R, c->Rp,
+               c->Fx);
   mark(4);
   // radix passes over bits 24-63 of the radius keys; runs equal in those
   // bits (radii within 2^-28 of each other, escapers whose ids differ in
@@ -217,13 +221,13 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   launch_gather(L, sk, sv, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old, c->cc, st,
                 c->tile_a, c->tile_b, c->Rp, c->R);
   mark(6);
-  // mixed mode's tables carry the shell slopes of the FP64 orbit step (not
-  // the scan's enclosed masses): its turning points and points are then
-  // FP64 mode's
+  // the tables carry the shell slopes of the FP64 orbit step (not the
+  // scan's enclosed masses): the sampled step's turning points and points
+  // are then FP64 mode's
   launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
-                   mixed ? c->t32 : nullptr, mixed ? c->Mbuf : nullptr, true, st,
-                   mixed ? c->bk.node : nullptr, mixed ? c->bk.tdf : nullptr, true, true);
-  if (mixed) {
+                   tab ? c->t32 : nullptr, tab ? c->Mbuf : nullptr, true, st,
+                   tab ? c->bk.node : nullptr, tab ? c->bk.tdf : nullptr, true, true);
+  if (tab) {
     launch_buckets(L, c->t32, true, c->bk, st);
     launch_grid(L, c->x, c->phi, c->Mbuf, true, c->bk, st);
   }
@@ -243,10 +247,11 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
 
 int count_step_kernels(const cmc_ctx* c) {
   // bins, relax, orbit, upsweep, hist scan, 5 passes, tie fix, gather with
-  // the tile sums, potential, [turning points, FP32 sampler, FP64
-  // continuation, slopes at the tile seams, 2 bucket-index + 3 grid
-  // kernels], [correction], step end
-  return 3 + (c->R ? 1 : 0) + 2 + 5 + 1 + 1 + 1 + (c->cfg.precision == 1 ? 9 : 0) +
+  // the tile sums, potential, [precision 0 and 1: turning points, FP32
+  // sampler, FP64 continuation, slopes at the tile seams, 2 bucket-index + 3
+  // grid kernels; precision 0: the envelope], [correction], step end
+  const int p = c->cfg.precision;
+  return 3 + (c->R ? 1 : 0) + 2 + 5 + 1 + 1 + 1 + (p == 1 ? 9 : p == 0 ? 10 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 
@@ -268,6 +273,7 @@ void free_ctx(cmc_ctx* c) {
   dfree(c->err, st);
   dfree(c->step, st);
   dfree(c->pcount, st);
+  dfree(c->Fx, st);
   free_sort(c->W, st);
   free_buckets(c->bk, st);
   dfree(c->L.taus, st);
@@ -431,7 +437,7 @@ cmc_status init_streams(cmc_ctx* c, const uint64_t* seeds) {
 cmc_status autotune(cmc_ctx* c) {
   const SegLayout& L = c->L;
   cudaStream_t st = c->stream;
-  const bool mixed = c->cfg.precision == 1;
+  const bool tab = c->cfg.precision != 2;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -445,9 +451,9 @@ cmc_status autotune(cmc_ctx* c) {
   }
   auto run_orbit = [&](int blk, int var) {
     launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
-                 mixed ? c->Mbuf : nullptr, c->vr, c->vt, c->m,
+                 tab ? c->Mbuf : nullptr, c->vr, c->vt, c->m,
                  c->id, c->step, c->keys, c->pay, nullptr, blk, var, c->bk.args(), c->r_old,
-                 c->cc, c->vals, c->pcount, st);
+                 c->cc, c->vals, c->pcount, st, true, nullptr, nullptr, c->Fx);
   };
   auto time_it = [&](auto&& fn) {
     float best = 3.4e38f;
@@ -462,14 +468,14 @@ cmc_status autotune(cmc_ctx* c) {
     }
     return best;
   };
-  // orbit block size and (mixed mode) kernel variant
-  const int n_var = mixed ? kOrbitVariants : 1;
+  // orbit block size and (sampled step) kernel variant
+  const int n_var = tab ? kOrbitVariants : 1;
   int blk_best = c->cfg.orbit_block ? c->cfg.orbit_block : 64, var_best = c->orbit_variant;
   float tb = 3.4e38f;
   for (int var = 0; var < n_var; ++var)
     for (int blk : {64, 128, 256}) {
       if (c->cfg.orbit_block && blk != c->cfg.orbit_block) continue;
-      if (mixed && c->cfg.orbit_variant >= 0 && var != c->cfg.orbit_variant) continue;
+      if (tab && c->cfg.orbit_variant >= 0 && var != c->cfg.orbit_variant) continue;
       const float ms = time_it([&] { run_orbit(blk, var); });
       if (ms < tb) { tb = ms; blk_best = blk; var_best = var; }
     }
@@ -560,7 +566,7 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   cmc_config cfg;
   if (cfg_in) cfg = *cfg_in;
   else cmc_config_default(&cfg);
-  if ((cfg.precision != 0 && cfg.precision != 1) || cfg.bin_size < 2 || (cfg.bin_size & 1) ||
+  if (cfg.precision < 0 || cfg.precision > 2 || cfg.bin_size < 2 || (cfg.bin_size & 1) ||
       cfg.max_trials < 1 || cfg.max_trials > (1 << 24) || !(cfg.theta_max > 0.0) ||
       !(cfg.gamma > 0.0) || cfg.orbit_block < 0 || cfg.orbit_block > 256 ||
       (cfg.orbit_block % 32) || cfg.orbit_variant < -1 || cfg.orbit_variant >= kOrbitVariants ||
@@ -599,7 +605,8 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   CMC_ALLOC(c->m, n);
   CMC_ALLOC(c->phi, n);
   CMC_ALLOC(c->id, n);
-  if (cfg.precision == 1) CMC_ALLOC(c->t32, n);
+  if (cfg.precision != 2) CMC_ALLOC(c->t32, n);
+  if (cfg.precision == 0) CMC_ALLOC(c->Fx, n);
   CMC_ALLOC(c->keys, n);
   CMC_ALLOC(c->vals, n);
   CMC_ALLOC(c->pay, n);
@@ -621,7 +628,7 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   }
 #undef CMC_ALLOC
   if (!e) e = alloc_sort(c->W, L, 8, st);
-  if (!e && cfg.precision == 1) e = alloc_buckets(c->bk, L, st);
+  if (!e && cfg.precision != 2) e = alloc_buckets(c->bk, L, st);
   if (e) { cmc_status s = cuda_fail(nullptr, e, "cmc_init: allocation"); free_ctx(c); return s; }
   sort_prepare();
   potential_prepare();
@@ -1091,7 +1098,7 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
                      int32_t max_trials, int32_t precision, double* r_new, double* vr_new,
                      double* vt_new, double* phi_new, double* rmin, double* rmax, double* F,
                      int32_t* code, void* stream) {
-  if (n < 0 || max_trials < 1 || (precision != 0 && precision != 1) ||
+  if (n < 0 || max_trials < 1 || precision < 0 || precision > 2 ||
       (n > 0 && (!r || !phi || !vr || !vt || !id || !r_new)))
     return fail(nullptr, CMC_EINVAL, "cmc_orbit: bad arguments");
   if (n == 0) return CMC_OK;
@@ -1116,7 +1123,8 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
     launch_make_t32(n, x, phi, t32, st);
     BucketWork bk;
     double* sl = nullptr;  // shell slopes (enclosed masses) from the potential
-    if (precision == 1) {
+    const bool tab = precision != 2;
+    if (tab) {
       e = alloc_buckets(bk, S.L, st);
       if (!e) e = dalloc(sl, n, st);
       if (!e) {
@@ -1128,16 +1136,19 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
     }
     OrbitStageOut d;
     d.phi_new = phi_new; d.rmin = rmin; d.rmax = rmax; d.F = F; d.code = code;
-    double *tmin = nullptr, *tmax = nullptr;
+    double *tmin = nullptr, *tmax = nullptr, *Fx = nullptr;
     uint32_t *plist = nullptr, *pcnt = nullptr;
-    if (!e && precision == 1) e = dalloc(tmin, n, st);
-    if (!e && precision == 1) e = dalloc(tmax, n, st);
-    if (!e && precision == 1) e = dalloc(plist, n, st);
-    if (!e && precision == 1) e = dalloc(pcnt, 1, st);
+    if (!e && tab) e = dalloc(tmin, n, st);
+    if (!e && tab) e = dalloc(tmax, n, st);
+    if (!e && tab) e = dalloc(plist, n, st);
+    if (!e && tab) e = dalloc(pcnt, 1, st);
+    if (!e && precision == 0) e = dalloc(Fx, n, st);
     if (!e)
       launch_orbit(S.L, precision, max_trials, r, x, phi, sl, vr, vt, mm, id, dstep, keys,
-                   pay, &d, 0, 0, bk.args(), tmin, tmax, plist, pcnt, st);
+                   pay, &d, 0, 0, bk.args(), tmin, tmax, plist, pcnt, st, true, nullptr,
+                   nullptr, Fx);
     free_buckets(bk, st);
+    dfree(Fx, st);
     dfree(sl, st);
     dfree(tmin, st);
     dfree(tmax, st);

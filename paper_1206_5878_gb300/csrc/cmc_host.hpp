@@ -227,12 +227,14 @@ void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWo
 void launch_grid(const SegLayout& L, const double* x, const double* phi, const double* Menc,
                  bool nb_sub, BucketWork& B, cudaStream_t st);
 
-// Menc (mixed mode): enclosed mass M_k of every node, the slope of Phi in
-// 1/r across shell k.  launch_orbit in mixed mode runs four kernels
-// (turning points, FP32 sampler, FP64 continuation of the pending stars,
-// finishing) and needs two scratch arrays of n doubles (tp_min, tp_max:
-// the turning points), a list of n uint32 (the pending stars) and one
-// uint32 counter.
+// Menc (precision 0 and 1): the slope of Phi in 1/r across shell k.
+// precision 1 (mixed): launch_orbit runs four kernels (turning points,
+// FP32 sampler, FP64 continuation of the pending stars, finishing) and
+// needs two scratch arrays of n doubles (tp_min, tp_max: the turning
+// points), a list of n uint32 (the pending stars) and one uint32 counter.
+// precision 0 (FP64): the same kernels with FP64 mode's envelope (one more
+// kernel, into Fx: n doubles) and FP64 mode's points, every decision the
+// FP64 one.  precision 2 (FP64 by bisection): one kernel on the FP64 table.
 void launch_slopes(int64_t n, const double* x, const double* phi, double* Menc,
                    cudaStream_t st);
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
@@ -242,7 +244,8 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
                   uint32_t* plist, uint32_t* pcount, cudaStream_t st,
-                  bool with_turning = true, const double* Rv = nullptr, double* Rp = nullptr);
+                  bool with_turning = true, const double* Rv = nullptr, double* Rp = nullptr,
+                  double* Fx = nullptr);
 // the turning-point kernel alone (mixed mode; launch_orbit(..., false)
 // then runs the sampling kernel only)
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,

@@ -404,6 +404,38 @@ __device__ __forceinline__ void point64(const double4_32a* __restrict__ nd, int6
 }
 
 
+// FP64 mode: the orbit point r(s) in FP64 from an FP32 shell guess sh
+// (moved to the exact shell), Phi by Eq. 6's division form (the FP64
+// statement of the method, as phi_in_shell), L = J / r and Q
+__device__ __forceinline__ void point64_div(const double4_32a* __restrict__ nd, int64_t nb,
+                                            const Star& st, double c0, double c1, double sv,
+                                            int sh, double& rs, double& ph, double& Q) {
+  rs = c0 + c1 * (sv * (3.0 - sv * sv));
+  double4_32a a;
+  const int64_t i = fix_shell_nodes(nd, nb, sh, rs, a);
+  if (i < 0) {
+    ph = a.z;  // node 0's Phi: the central constant
+  } else {
+    const double xq = div_rn(1.0, rs);
+    double xj1 = 0.0, pj1 = 0.0;
+    if (i + 1 < nb) {
+      const double4_32a b = nd[i + 1];
+      xj1 = b.y;
+      pj1 = b.z;
+    }
+    const double den = a.y - xj1;
+    ph = !(den > 0.0) ? a.z : a.z + div_rn(a.y - xq, den) * (pj1 - a.z);
+  }
+  const double L = div_rn(st.J, rs);
+  Q = scale_up<1>(st.E - ph) - L * L;
+}
+
+// g(s) of FP64 mode at the point of point64_div
+__device__ __forceinline__ double g_of_point(double c1, double sv, double Q) {
+  if (!(Q > 0.0)) return 0.0;
+  return div_rn((3.0 * c1) * (1.0 - sv * sv), sqrt_rn(Q));
+}
+
 // (2k + 1) 2^-24 from the top 23 bits of a word: exact in float, in (0, 1)
 __device__ __forceinline__ float u01f(uint32_t hi) {
   // 1 + k 2^-23 assembled from its bits, minus 1 (exact), plus 2^-24
@@ -767,6 +799,10 @@ __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
 //   g:     1.5 * (1/2) dQ / Q + 6|c1| 2^-23 / (dr/ds) + 16u
 // Close to a turning point Q is within a few dQ of zero and the trial is
 // left undecided; elsewhere the FP32 answer is the FP64 one.
+// kExact (FP64 mode): F is the float of the FP64 envelope, and a trial
+// whose g might lie on either side of F is left undecided too, so that the
+// count of g > F (violations) is the FP64 one.
+template <bool kExact>
 __device__ __forceinline__ int accept32(const Grid& G, float E, float J, float c0, float c1,
                                         float F, float sv, float xp,
                                         unsigned long long& viol) {
@@ -785,6 +821,11 @@ __device__ __forceinline__ int accept32(const Grid& G, float E, float J, float c
   if (!(Q > 4.0f * qerr)) return -1;
   const float g = drds / sqrtf(Q);
   const float eg = (0.75f * qerr) / Q + (6.0f * ac1 * 0x1p-23f) / drds + 0x1p-20f;
+  if (kExact) {
+    const bool above = g * (1.0f - eg) > F * (1.0f + 0x1p-22f);
+    const bool below = g * (1.0f + eg) < F * (1.0f - 0x1p-22f);
+    if (!above && !below) return -1;
+  }
   const float a = F * xp, da = F * 0x1p-22f;
   if (a + da < g * (1.0f - eg)) {
     if (g > F) ++viol;
@@ -795,6 +836,107 @@ __device__ __forceinline__ int accept32(const Grid& G, float E, float J, float c
     return 0;
   }
   return -1;
+}
+
+// g(s) in FP32 at an envelope sample with the error bound of accept32
+// (the sample's float s is within 2^-25 of the FP64 one): 1 with g and its
+// relative bound eg, 0 when Q < 0 for certain (g = 0), -1 when FP32 cannot
+// tell.
+__device__ __forceinline__ int g32_bounded(const Grid& G, float E, float J, float c0, float c1,
+                                           float sv, float& g, float& eg) {
+  const float ss = sv * sv;
+  const float rs = c0 + c1 * (sv * (3.0f - ss));
+  const float drds = (3.0f * c1) * (1.0f - ss);
+  const float xq = 1.0f / rs;
+  const float ph = grid_phi(G, xq);
+  const float L = J * xq, L2 = L * L;
+  const float Q = 2.0f * (E - ph) - L2;
+  const float ac1 = fabsf(c1), aph = fabsf(ph);
+  const float dr = 3.0f * ac1 * ((1.0f - ss) + 0x1p-21f) * 0x1p-23f +
+                   0x1p-21f * (fabsf(c0) + 2.0f * ac1);
+  const float qerr = 0x1p-20f * (fabsf(E) + aph + L2) + (2.0f * G.err + 0x1p-22f) * aph +
+                     3.0f * (G.mb * xq + L2) * (dr * xq);
+  if (Q < -4.0f * qerr) return 0;
+  if (!(Q > 4.0f * qerr) || !(drds > 0.0f)) return -1;
+  g = drds / sqrtf(Q);
+  eg = (0.75f * qerr) / Q + (6.0f * ac1 * 0x1p-23f) / drds + 0x1p-20f;
+  return 1;
+}
+
+// the envelope samples s_j as floats (within 2^-25 of the FP64 ones)
+#define CMC_SJF(j) ((float)CMC_SJ(j))
+__constant__ float c_s32[21] = {CMC_SJ21(CMC_SJF)};
+
+// FP64 mode's envelope F = 1.2 max_j g(s_j) over the 21 samples, the FP64
+// value (Eq. 6's division form, as the FP64 statement of the method), for
+// about one FP64 evaluation per star: every g(s_j) is first bounded in FP32
+// (g32_bounded); only the samples whose upper bound reaches the largest
+// lower bound, and those FP32 cannot bound, can hold the maximum, and only
+// they are evaluated in FP64 (shell from the bucket index, made exact on
+// the node records).  F = 0 for stars without an orbit to sample (r_max <=
+// r_min: every g is 0 or negative there).
+__global__ void __launch_bounds__(128) k_envelope64(Seg S, const double* r, const double* phi,
+                                                    const double* vr, const double* vt,
+                                                    BucketArgs BA, const double* tp_min,
+                                                    const double* tp_max, double* Fx,
+                                                    int64_t n) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const int c = seg_find(S.off, S.n_seg, p);
+  const int64_t sb = S.off[c], nbc = S.nb[c], k = p - sb;
+  double F = 0.0;
+  const double vrk = vr[p], vtk = vt[p];
+  Star s;
+  s.k = k;
+  s.E = __ldg(phi + p) + scale_down<1>(vrk * vrk + vtk * vtk);
+  s.J = r[p] * vtk;
+  const double rmin = k < nbc ? __ldg(tp_min + p) : 0.0, rmax = k < nbc ? __ldg(tp_max + p) : 0.0;
+  if (k < nbc && lt0(s.E) && gt_pos(rmax, rmin)) {
+    const double c0 = scale_down<1>(rmax + rmin);
+    const double c1 = scale_down<2>(rmax - rmin);
+    const float c0f = f32_rn(c0), c1f = f32_rn(c1), E32 = f32_rn(s.E), J32 = f32_rn(s.J);
+    const Grid GD = grid_of(BA, c);
+    float hi[21];
+    unsigned pos = 0u, cand = 0u;
+    float lo_max = 0.0f;
+#pragma unroll
+    for (int j = 0; j < 21; ++j) {
+      float g = 0.0f, eg = 0.0f;
+      const int st = g32_bounded(GD, E32, J32, c0f, c1f, c_s32[j], g, eg);
+      hi[j] = 0.0f;
+      if (st > 0) {
+        const float lo = g * (1.0f - eg);
+        hi[j] = g * (1.0f + eg);
+        lo_max = lo > lo_max ? lo : lo_max;
+        pos |= 1u << j;
+      } else if (st < 0) {
+        cand |= 1u << j;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 21; ++j)
+      if (((pos >> j) & 1u) && hi[j] >= lo_max) cand |= 1u << j;
+    Buckets BK;
+    const int4 pr = BA.prm[c];
+    BK.start = BA.start + BA.off[c];
+    BK.base = BA.base[c];
+    BK.shift = pr.x;
+    BK.nbk = pr.y;
+    BK.lo = pr.z;
+    BK.hi = pr.w;
+    double gmax = 0.0;
+    while (cand) {
+      const int j = __ffs(cand) - 1;
+      cand &= cand - 1u;
+      double rs, ph, Q;
+      point64_div(BA.node + sb, nbc, s, c0, c1, c_s64[j],
+                  shell32_of(BA.node + sb, (int)nbc, BK, c0f, c1f, c_s32[j]), rs, ph, Q);
+      const double g = g_of_point(c1, c_s64[j], Q);
+      if (g > gmax) gmax = g;
+    }
+    F = 1.2 * gmax;
+  }
+  Fx[p] = F;
 }
 
 // Result of the FP32 sampler in a star's key slot: bits 0-29 the trial
@@ -811,14 +953,17 @@ enum : uint32_t { kSmpAccepted = 0, kSmpPending = 1, kSmpDegenerate = 2, kSmpCap
 // samples is as valid an envelope as the FP64 one (it differs from it by up
 // to ~1e-4 at the outer samples, so the two modes draw different, equally
 // exact, accept sequences).
-template <int kMinB, bool kTaus>
+// kExact (FP64 mode): F is FP64 mode's envelope from k_envelope64 (Fx),
+// and a trial is decided here only where the FP64 decision and violation
+// count are certain.
+template <int kMinB, bool kTaus, bool kExact>
 __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, const double* r,
                                                   const double* phi, const double* vr,
                                                   const double* vt, const uint32_t* id,
                                                   const uint32_t* step_p, BucketArgs BA,
                                                   const double* tp_min, const double* tp_max,
                                                   uint64_t* keys, uint32_t* plist,
-                                                  uint32_t* pcount, int64_t n) {
+                                                  uint32_t* pcount, int64_t n, const double* Fx) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long viol = 0;
   bool pend = false;
@@ -835,22 +980,31 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
       const double c1 = scale_down<2>(rmax - rmin);
       const float c0f = f32_rn(c0), c1f = f32_rn(c1), E32 = f32_rn(E), J32 = f32_rn(J);
       const Grid GD = grid_of(BA, c);
-      float gmax = 0.0f;
+      float F32;
+      bool degenerate;
+      if (kExact) {
+        const double F64 = __ldg(Fx + p);
+        F32 = f32_rn(F64);
+        degenerate = !gt_pos(rmax, rmin) || !(F64 > 0.0);
+      } else {
+        float gmax = 0.0f;
 #pragma unroll 3
-      for (int j = 0; j < 21; ++j) {
-        const float g = g32_grid(GD, E32, J32, c0f, c1f, c_sa32[j], c_sb32[j]);
-        gmax = g > gmax ? g : gmax;
+        for (int j = 0; j < 21; ++j) {
+          const float g = g32_grid(GD, E32, J32, c0f, c1f, c_sa32[j], c_sb32[j]);
+          gmax = g > gmax ? g : gmax;
+        }
+        F32 = 1.2f * gmax;
+        degenerate = !gt_pos(rmax, rmin) || !(F32 > 0.0f);
       }
-      const float F32 = 1.2f * gmax;
       uint32_t st = kSmpCap;
       int t = 0;
-      if (!gt_pos(rmax, rmin) || !(F32 > 0.0f)) {
+      if (degenerate) {
         st = kSmpDegenerate;
       } else {
         Draws<kTaus> g = draws_of<kTaus>(S, c, id[p], *step_p);
         for (; t < max_trials; ++t) {
           const U4 w = g.block(kTagRej, (uint32_t)t);
-          const int d = accept32(GD, E32, J32, c0f, c1f, F32, 2.0f * u01f(w.y) - 1.0f,
+          const int d = accept32<kExact>(GD, E32, J32, c0f, c1f, F32, 2.0f * u01f(w.y) - 1.0f,
                                  u01f(w.w), viol);
           if (d == 0) continue;
           st = d > 0 ? kSmpAccepted : kSmpPending;
@@ -885,7 +1039,8 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
 // kSmpAccepted and the accepted trial, or kSmpCap.  Most threads find no
 // pending star and leave at once.
 // one pending star (p = n: an idle lane); counts go to the statistics
-template <bool kTaus>
+// kExact (FP64 mode): F from Fx, the points and g as FP64 mode's
+template <bool kTaus, bool kExact>
 __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double* r,
                                              const double* x, const double* phi,
                                              const double* Menc,
@@ -893,7 +1048,7 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
                                              const uint32_t* id, const uint32_t* step_p,
                                              BucketArgs BA, const double* tp_min,
                                              const double* tp_max, uint64_t* keys, int64_t p,
-                                             int64_t n) {
+                                             int64_t n, const double* Fx) {
   unsigned long long viol = 0;
   unsigned int n64 = 0;
   int c = -1;
@@ -920,7 +1075,7 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
         const double c0 = scale_down<1>(rmax + rmin);
         const double c1 = scale_down<2>(rmax - rmin);
         const float c0f = f32_rn(c0), c1f = f32_rn(c1);
-        const double F = (double)__uint_as_float((uint32_t)(res >> 32));
+        const double F = kExact ? __ldg(Fx + p) : (double)__uint_as_float((uint32_t)(res >> 32));
         uint32_t st = kSmpCap;
         int t = (int)(res & 0x3FFFFFFFull);
         // stream mode: the blocks of trials 0 .. t-1 were the FP32 sampler's
@@ -929,11 +1084,18 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
         for (; t < max_trials; ++t) {
           const U4 w = g.block(kTagRej, (uint32_t)t);
           const double sv = sym_double(sym_int(w.x, w.y));
-          double rs, xs, ph, L, Q;
-          point64(BA.node + sb, nbc, s, c0, c1, sv,
-                  shell32_of(BA.node + sb, (int)nbc, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs,
-                  xs, ph, L, Q);
-          const double g64v = pos_num(Q) ? div_rn((3.0 * c1) * (1.0 - sv * sv), sqrt_rn(Q)) : 0.0;
+          const int guess =
+              shell32_of(BA.node + sb, (int)nbc, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f);
+          double g64v;
+          if (kExact) {
+            double rs, ph, Q;
+            point64_div(BA.node + sb, nbc, s, c0, c1, sv, guess, rs, ph, Q);
+            g64v = g_of_point(c1, sv, Q);
+          } else {
+            double rs, xs, ph, L, Q;
+            point64(BA.node + sb, nbc, s, c0, c1, sv, guess, rs, xs, ph, L, Q);
+            g64v = pos_num(Q) ? div_rn((3.0 * c1) * (1.0 - sv * sv), sqrt_rn(Q)) : 0.0;
+          }
           ++n64;
           if (g64v > F) ++viol;
           if (F * u01(w.z, w.w) < g64v) { st = kSmpAccepted; break; }
@@ -954,7 +1116,7 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
   }
 }
 
-template <bool kTaus>
+template <bool kTaus, bool kExact>
 __global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const double* r,
                                                    const double* x, const double* phi,
                                                    const double* Menc,
@@ -963,19 +1125,24 @@ __global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const 
                                                    BucketArgs BA, const double* tp_min,
                                                    const double* tp_max, uint64_t* keys,
                                                    const uint32_t* plist,
-                                                   const uint32_t* pcount, int64_t n) {
+                                                   const uint32_t* pcount, int64_t n,
+                                                   const double* Fx) {
   const uint32_t np = *pcount;
   for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < np; i0 += gridDim.x * blockDim.x) {
-    pending_star<kTaus>(S, max_trials, r, x, phi, Menc, vr, vt, id, step_p, BA, tp_min,
-                        tp_max, keys, i0 + threadIdx.x < np ? (int64_t)plist[i0 + threadIdx.x] : n,
-                        n);
+    pending_star<kTaus, kExact>(S, max_trials, r, x, phi, Menc, vr, vt, id, step_p, BA, tp_min,
+                                tp_max, keys,
+                                i0 + threadIdx.x < np ? (int64_t)plist[i0 + threadIdx.x] : n, n,
+                                Fx);
   }
 }
 
-// kPrec: 0 FP64, 1 mixed (turning points from k_turning_mixed in tp_min,
-// tp_max, FP32 sampler result from k_sample32 / k_pending64 in the key
-// slot).  kMinB: resident 256-thread blocks to fit (caps registers; 1 = no
-// cap).
+// kPrec: 0 FP64 by bisection (Appendix A's kernels: brackets, envelope and
+// trials all on the FP64 table), 1 mixed (turning points from
+// k_turning_mixed in tp_min, tp_max, FP32 sampler result from k_sample32 /
+// k_pending64 in the key slot), 2 FP64 through the mixed kernels (their
+// FP64 turning points, FP64 mode's envelope from k_envelope64 in Fx, the
+// accepted point as FP64 mode computes it).  kMinB: resident 256-thread
+// blocks to fit (caps registers; 1 = no cap).
 template <int kPrec, int kMinB, bool kTaus>
 __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, const double* r,
                                                const double* x, const double* phi,
@@ -985,7 +1152,8 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
                                                uint64_t* keys, Payload* pay, int64_t* esc,
                                                OrbitStageOut dbg, BucketArgs BA,
                                                const double* tp_min, const double* tp_max,
-                                               int64_t n, const double* Rv, double* Rp) {
+                                               int64_t n, const double* Rv, double* Rp,
+                                               const double* Fx) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int c = seg_find(S.off, S.n_seg, p);
@@ -1038,7 +1206,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
   } else {
     int64_t jmax, jmin;
     Buckets BK;
-    if (kPrec == 1) {
+    if (kPrec >= 1) {
       const int4 pr = BA.prm[c];
       BK.start = BA.start + BA.off[c];
       BK.base = BA.base[c];
@@ -1111,7 +1279,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
       const uint64_t res = keys[p];
       const uint32_t st = (uint32_t)(res >> 30) & 3u;
       int t = (int)(res & 0x3FFFFFFFull);
-      F = (double)__uint_as_float((uint32_t)(res >> 32));
+      F = kPrec == 2 ? __ldg(Fx + p) : (double)__uint_as_float((uint32_t)(res >> 32));
       if (st == kSmpDegenerate) {
         code = 2;
       } else if (st == kSmpCap) {
@@ -1137,17 +1305,22 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
           g.skip((uint32_t)t);  // stream mode: the rejected trials' blocks
           const U4 w = g.block(kTagRej, (uint32_t)t);
           const double sv = sym_double(sym_int(w.x, w.y));
-          double rs, xs, ph, L, Q;
-          point64(BA.node + sb, nbc, s, c0, c1, sv,
-                  shell32_of(BA.node + sb, nb32, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f), rs, xs, ph,
-                  L, Q);
+          const int guess = shell32_of(BA.node + sb, nb32, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f);
+          double rs, ph, Q, vtn;
+          if (kPrec == 2) {
+            point64_div(BA.node + sb, nbc, s, c0, c1, sv, guess, rs, ph, Q);
+            vtn = div_rn(s.J, rs);
+          } else {
+            double xs;
+            point64(BA.node + sb, nbc, s, c0, c1, sv, guess, rs, xs, ph, vtn, Q);
+          }
           if (!pos_num(Q)) Q = 0.0;
           const double sq = sqrt_rn(Q);
           U4 sg = g.block(kTagSgn, 0u);
           draws_keep(S, c, g);
           r_new = rs;
           P.vr = (sg.x & 1u) ? -sq : sq;
-          P.vt = L;
+          P.vt = vtn;
           P.c = __ldg(T.phi + k) - ph;
           ph_new = ph;
         }
@@ -1492,7 +1665,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
                   uint32_t* plist, uint32_t* pcount, cudaStream_t st, bool with_turning,
-                  const double* Rv, double* Rp) {
+                  const double* Rv, double* Rp, double* Fx) {
   if (!L.n) return;
   OrbitStageOut d;
   if (dbg) d = *dbg;
@@ -1500,37 +1673,55 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
   const unsigned grid = (unsigned)((L.n + block - 1) / block);
   // the pending list is short: a grid of a few blocks per SM walks it
   const unsigned pgrid = (unsigned)((L.n + 127) / 128 < 1216 ? (L.n + 127) / 128 : 1216);
+  // precision 0: FP64 through the mixed kernels (kPrec 2); 1 mixed; 2 FP64
+  // by bisection (kPrec 0)
+  const bool exact = precision == 0;
 #define CMC_TURN(B)                                                                          \
   k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, Menc, vr, vt, ba,      \
                                              tp_min, tp_max, L.n)
 #define CMC_ORBIT(P, B, T)                                                                  \
   k_orbit<P, B, T><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, Menc, vr, vt, \
                                            m, id, step, keys, pay, L.esc_step, d, ba, tp_min, \
-                                           tp_max, L.n, Rv, Rp)
-#define CMC_MIXED(B, T)                                                                     \
+                                           tp_max, L.n, Rv, Rp, Fx)
+#define CMC_SAMPLED(B, T, X)                                                                \
   do {                                                                                      \
     if (with_turning) CMC_TURN(B);                                                          \
+    if (X)                                                                                  \
+      k_envelope64<<<(unsigned)((L.n + 127) / 128), 128, 0, st>>>(L.dev(), r, phi, vr, vt, \
+                                                                 ba, tp_min, tp_max, Fx, L.n); \
     cudaMemsetAsync(pcount, 0, sizeof(uint32_t), st);                                      \
-    k_sample32<B, T><<<grid, block, 0, st>>>(L.dev(), max_trials, r, phi, vr, vt, id, step, \
-                                             ba, tp_min, tp_max, keys, plist, pcount, L.n); \
-    k_pending64<T><<<pgrid, 128, 0, st>>>(L.dev(), max_trials, r, x, phi, Menc, vr, vt, \
-                                          id, step, ba, tp_min, tp_max, keys, plist, pcount, \
-                                          L.n);                                             \
-    CMC_ORBIT(1, 5, T);                                                                     \
+    k_sample32<B, T, X><<<grid, block, 0, st>>>(L.dev(), max_trials, r, phi, vr, vt, id, step, \
+                                                ba, tp_min, tp_max, keys, plist, pcount, L.n, \
+                                                Fx);                                        \
+    k_pending64<T, X><<<pgrid, 128, 0, st>>>(L.dev(), max_trials, r, x, phi, Menc, vr, vt, \
+                                             id, step, ba, tp_min, tp_max, keys, plist, pcount, \
+                                             L.n, Fx);                                      \
+    CMC_ORBIT(X ? 2 : 1, 5, T);                                                             \
   } while (0)
-  if (L.taus) {
+#define CMC_VARIANTS(X)                                                                     \
+  do {                                                                                      \
+    if (variant == 1) CMC_SAMPLED(2, false, X);                                             \
+    else if (variant == 2) CMC_SAMPLED(3, false, X);                                        \
+    else if (variant == 3) CMC_SAMPLED(4, false, X);                                        \
+    else if (variant == 4) CMC_SAMPLED(5, false, X);                                        \
+    else if (variant == 5) CMC_SAMPLED(6, false, X);                                        \
+    else if (variant == 6) CMC_SAMPLED(8, false, X);                                        \
+    else CMC_SAMPLED(1, false, X);                                                          \
+  } while (0)
+  if (precision == 2) {
+    if (L.taus) CMC_ORBIT(0, 1, true);
+    else CMC_ORBIT(0, 1, false);
+  } else if (L.taus) {
     // stream mode: one launch shape of the sampler
-    if (precision == 0) CMC_ORBIT(0, 1, true);
-    else CMC_MIXED(5, true);
-  } else if (precision == 0) CMC_ORBIT(0, 1, false);
-  else if (variant == 1) CMC_MIXED(2, false);
-  else if (variant == 2) CMC_MIXED(3, false);
-  else if (variant == 3) CMC_MIXED(4, false);
-  else if (variant == 4) CMC_MIXED(5, false);
-  else if (variant == 5) CMC_MIXED(6, false);
-  else if (variant == 6) CMC_MIXED(8, false);
-  else CMC_MIXED(1, false);
-#undef CMC_MIXED
+    if (exact) CMC_SAMPLED(5, true, true);
+    else CMC_SAMPLED(5, true, false);
+  } else if (exact) {
+    CMC_VARIANTS(true);
+  } else {
+    CMC_VARIANTS(false);
+  }
+#undef CMC_VARIANTS
+#undef CMC_SAMPLED
 #undef CMC_TURN
 #undef CMC_ORBIT
 }

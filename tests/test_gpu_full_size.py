@@ -54,7 +54,7 @@ def test_timestep_and_relaxation_full_size(g_stage, orc, big):
     np.testing.assert_array_equal(host(vt), vto)
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_orbit_sampled_full_size(g_stage, orc, big, precision):
     g = g_stage
     _, _, st = big
@@ -68,7 +68,7 @@ def test_orbit_sampled_full_size(g_stage, orc, big, precision):
         o = orc.orbit_star(int(k), st["r"], st["phi"], st["vr"][k], st["vt"][k],
                            int(st["id"][k]), 1, 0)
         assert got["code"][k] == o["code"]
-        if precision == 0:
+        if precision != 1:
             for key in ("r_new", "vr", "vt", "phi_new", "rmin", "rmax", "F"):
                 assert got[key][k] == o[key], (k, key)
         else:
@@ -87,11 +87,13 @@ def test_orbit_sampled_full_size(g_stage, orc, big, precision):
 
 
 def test_mixed_turning_points_equal_fp64_on_every_star(g_stage, big):
-    """Mixed mode's r_min and r_max (float-pair bracket walks, certified or
-    walked again in FP64) equal FP64 mode's (FP64 bisection) bit for bit on
-    all 10^7 stars, at the start and after three mixed steps; about 250 stars
-    a step take the walks' fallback (an FP32 bisection), so that path is
-    covered too."""
+    """The sampled step's r_min and r_max (float-pair bracket walks,
+    certified or walked again in FP64) equal the FP64 bisection's bit for
+    bit on all 10^7 stars, at the start and after three mixed steps; about
+    250 stars a step take the walks' fallback (an FP32 bisection), so that
+    path is covered too.  And the two FP64 paths (precision 0: FP32
+    screening with FP64 decisions; 2: bisection on the FP64 table) give the
+    same new orbit, envelope and code on every star."""
     g = g_stage
     d, _, st0 = big
     c = g.Cluster({k: d[k] for k in ("r", "vr", "vt", "m", "id")}, [1], precision=1,
@@ -103,10 +105,17 @@ def test_mixed_turning_points_equal_fp64_on_every_star(g_stage, big):
         c.close()
     for st, nb in states:
         cut = {k: st[k][:nb] for k in ("r", "phi", "vr", "vt", "id")}
-        o = [g.stage_orbit(dev(cut["r"]), dev(cut["phi"]), dev(cut["vr"]), dev(cut["vt"]),
-                           dev(cut["id"]), 1, 5, precision=p) for p in (0, 1)]
+        o = {p: {k: host(v) for k, v in
+                 g.stage_orbit(dev(cut["r"]), dev(cut["phi"]), dev(cut["vr"]), dev(cut["vt"]),
+                               dev(cut["id"]), 1, 5, precision=p).items()}
+             for p in (2, 1, 0)}
         for key in ("rmin", "rmax"):
-            a, b = host(o[0][key]), host(o[1][key])
+            a, b = o[2][key], o[1][key]
+            bad = np.nonzero(a.view(np.int64) != b.view(np.int64))[0]
+            assert bad.size == 0, (key, bad[:5], a[bad[:5]], b[bad[:5]])
+        np.testing.assert_array_equal(o[0]["code"], o[2]["code"])
+        for key in ("rmin", "rmax", "F", "r_new", "vr", "vt", "phi_new"):
+            a, b = o[0][key], o[2][key]
             bad = np.nonzero(a.view(np.int64) != b.view(np.int64))[0]
             assert bad.size == 0, (key, bad[:5], a[bad[:5]], b[bad[:5]])
 

@@ -105,19 +105,25 @@ def _orbit_inputs(n, seed, masses="equal"):
     return s
 
 
+# precision 0: FP64 through the certified FP32 screening (float-pair
+# brackets, FP32 envelope bounds and accept tests, FP64 where undecided);
+# precision 2: FP64 bisection on the FP64 table.  Both are the oracle's
+# FP64 method, bit for bit.
+@pytest.mark.parametrize("precision", [0, 2])
 @pytest.mark.parametrize("n", [1, 2, 3, 21, 4097, 30_001])
 @pytest.mark.parametrize("masses", ["equal", "salpeter"])
-def test_orbit_fp64_bit_exact(g, orc, n, masses):
+def test_orbit_fp64_bit_exact(g, orc, n, masses, precision):
     s = _orbit_inputs(n, seed=n + 1, masses=masses)
     out = g.stage_orbit(dev(s["r"]), dev(s["phi"]), dev(s["vr"]), dev(s["vt"]), dev(s["id"]),
-                        1234, 3, precision=0)
+                        1234, 3, precision=precision)
     ref = orc.orbit_all(s["r"], s["phi"], s["vr"], s["vt"], s["id"], 1234, 3)
     np.testing.assert_array_equal(host(out["code"]), ref["code"])
     for k in ("r_new", "vr", "vt", "phi_new", "rmin", "rmax", "F"):
         np.testing.assert_array_equal(host(out[k]), ref[k], err_msg=k)
 
 
-def test_orbit_special_stars_bit_exact(g, orc):
+@pytest.mark.parametrize("precision", [0, 2])
+def test_orbit_special_stars_bit_exact(g, orc, precision):
     """Escapers (E >= 0), radial orbits (J = 0), a trial cap of 1."""
     s = _orbit_inputs(5000, seed=3)
     vr, vt = s["vr"].copy(), s["vt"].copy()
@@ -127,7 +133,7 @@ def test_orbit_special_stars_bit_exact(g, orc):
     vt[1::7] = 0.0
     for trials in (1, 1000):
         out = g.stage_orbit(dev(s["r"]), dev(s["phi"]), dev(vr), dev(vt), dev(s["id"]), 5, 0,
-                            max_trials=trials, precision=0)
+                            max_trials=trials, precision=precision)
         ref = orc.orbit_all(s["r"], s["phi"], vr, vt, s["id"], 5, 0, max_trials=trials)
         np.testing.assert_array_equal(host(out["code"]), ref["code"])
         for k in ("r_new", "vr", "vt", "phi_new", "rmin", "rmax", "F"):

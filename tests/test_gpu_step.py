@@ -188,12 +188,12 @@ def test_resume_is_bit_identical(g):
     np.testing.assert_array_equal(a.escaped(), c.escaped())
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_launch_shape_does_not_change_bits(g, precision):
     d = ic.plummer(20_000, seed=4)
     outs = []
     shapes = [(32, 0, 0), (128, 0, 1), (256, 0, 2)]
-    if precision == 1:
+    if precision != 2:
         shapes += [(64, v, v % 3) for v in range(1, 7)]
     for blk, var, rv in shapes:
         c = _cluster(g, d, 4, orbit_block=blk, precision=precision, orbit_variant=var,
@@ -207,7 +207,7 @@ def test_launch_shape_does_not_change_bits(g, precision):
         assert st == outs[0][1]
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_autotuned_shapes_do_not_change_bits(g, precision):
     d = ic.plummer(30_001, seed=6, masses="salpeter")
     a = _cluster(g, d, 6, autotune=0, precision=precision)
@@ -330,3 +330,26 @@ def test_set_state_in_order_and_shuffled(g):
     with pytest.raises(g.CMCError) as ei:
         b.set_state(dup, 0)
     assert ei.value.status == 1  # CMC_EINVAL
+
+
+@pytest.mark.parametrize("n,masses,rng", [(30_011, "equal", "philox"),
+                                          (50_000, "salpeter", "philox"),
+                                          (20_000, "equal", "taus113")])
+def test_fp64_paths_agree_over_steps(g, n, masses, rng):
+    """FP64 mode through the certified FP32 screening (precision 0) and by
+    bisection on the FP64 table (precision 2) are the same method: over
+    five timesteps the states, the statistics and the escapers' budget are
+    identical bit for bit."""
+    d = ic.plummer(n, seed=12, masses=masses)
+    a = _cluster(g, d, 12, precision=0, rng=1 if rng == "taus113" else 0)
+    b = _cluster(g, d, 12, precision=2, rng=1 if rng == "taus113" else 0)
+    a.step(5)
+    b.step(5)
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("r", "vr", "vt", "m", "id", "phi"):
+        np.testing.assert_array_equal(sa[k], sb[k], err_msg=k)
+    sta, stb = a.stats()[0], b.stats()[0]
+    for k in sta:
+        if k != "fp64_trials":  # the screened path's own count
+            assert sta[k] == stb[k], k
+    np.testing.assert_array_equal(a.escaped(), b.escaped())
