@@ -86,7 +86,10 @@ enum {
                                    shell-model W of the moved mass), as a signed
                                    integer in units of 2^-62: K + W + E_esc
                                    minus this is what the method conserves */
-    CMC_NSTATS = 12
+    CMC_STAT_ENVELOPE_FP64 = 12,    /* FP64 mode (precision 0): envelope samples
+                                   evaluated in FP64 because their FP32 bounds
+                                   could not rule them out of the maximum */
+    CMC_NSTATS = 13
 };
 
 typedef struct {
@@ -131,6 +134,10 @@ typedef struct {
                                    collision timestep of Eq. 8 joins Eq. 7's, and
                                    relaxation pairs may merge as sticky spheres
                                    (section 2.1 step 3(iii)); default 0 */
+    int32_t diag_ring;          /* records per cluster of the per-step
+                                   diagnostics ring (cmc_get_diagnostics), 0 =
+                                   off (default); on, every step also computes
+                                   K and W (four more kernels per step) */
 } cmc_config;
 
 /* Fill cfg with the defaults shown above. */
@@ -225,6 +232,32 @@ cmc_status cmc_get_stats(cmc_ctx *ctx, int64_t *out);
  * n_clusters x 2, finite) restores them when a run is resumed. */
 cmc_status cmc_get_escaped(cmc_ctx *ctx, double *out);
 cmc_status cmc_set_escaped(cmc_ctx *ctx, const double *in);
+
+/* Per-step diagnostics ring (cmc_config.diag_ring = capacity R > 0): at the
+ * end of every step each cluster appends one record of CMC_DIAG_FIELDS
+ * doubles, written on the device inside the step (no host round trip):
+ * the step count after the step, its timestep, N_bound, K and W of the
+ * bound stars (as cmc_energy), K + W + E_esc, M_esc, E_esc, the cumulative
+ * rejection trials and the context's device error bits.  out (host,
+ * n_clusters x R x CMC_DIAG_FIELDS, may be NULL) receives the last
+ * min(R, steps) records of each cluster, oldest first, and *n_records
+ * their count.  CMC_EINVAL when the ring is off. */
+enum {
+    CMC_DIAG_STEP = 0, CMC_DIAG_DT = 1, CMC_DIAG_NBOUND = 2, CMC_DIAG_K = 3, CMC_DIAG_W = 4,
+    CMC_DIAG_ETOTAL = 5, CMC_DIAG_MESC = 6, CMC_DIAG_EESC = 7, CMC_DIAG_TRIALS = 8,
+    CMC_DIAG_ERR = 9, CMC_DIAG_FIELDS = 10
+};
+cmc_status cmc_get_diagnostics(cmc_ctx *ctx, double *out, int32_t *n_records);
+
+/* Debug builds (libcmc_debug.so, compiled with -DCMC_DEBUG): every table
+ * probe and scatter index that a wrong bracket, bucket or segment offset
+ * could send out of range is checked on the device; a failed check skips
+ * the access and records its site.  cmc_debug_check writes to *site (host)
+ * the first failed site since the last call (translation unit x 100000 +
+ * source line; 0: none) and clears the records; in a release build it
+ * always writes 0.  cmc_is_debug_build returns 1 in a debug build. */
+cmc_status cmc_debug_check(uint32_t *site);
+int32_t cmc_is_debug_build(void);
 
 /* Stages of one timestep, as timed by cmc_step_profiled. */
 enum {

@@ -60,10 +60,10 @@ class Cluster:
     sizes: stars per cluster (default: one cluster); seeds: one per cluster.
     """
 
-    def __init__(self, state, seeds, sizes=None, stream=None, **cfg):
+    def __init__(self, state, seeds, sizes=None, stream=None, debug=False, **cfg):
         """cfg: cmc_config fields by name; rng may also be given as
         "philox" (0) or "taus113" (1)."""
-        self.lib = load()
+        self.lib = load(debug)  # debug: the build with device-side index checks
         if isinstance(cfg.get("rng"), str):
             cfg["rng"] = {"philox": 0, "taus113": 1}[cfg["rng"]]
         r = state["r"]
@@ -85,7 +85,7 @@ class Cluster:
         st = self.lib.cmc_init(ctypes.byref(ctx), ctypes.byref(self.cfg), self.n_clusters,
                                self._sizes.ctypes.data, self._seeds.ctypes.data,
                                *[_ptr(a) for a in arrs], kind, self.stream)
-        check(st, None)
+        check(st, None, self.lib)
         self.ctx = ctx
 
     @staticmethod
@@ -118,43 +118,43 @@ class Cluster:
 
     # -- API ---------------------------------------------------------------
     def step(self, n_steps: int = 1):
-        check(self.lib.cmc_step(self.ctx, int(n_steps)), self.ctx)
+        check(self.lib.cmc_step(self.ctx, int(n_steps)), self.ctx, self.lib)
         return self
 
     def step_profiled(self, n_steps: int = 1) -> dict:
         """Like step(); returns the summed device milliseconds per stage."""
         ms = np.zeros(len(_native.STAGE_NAMES))
-        check(self.lib.cmc_step_profiled(self.ctx, int(n_steps), ms.ctypes.data), self.ctx)
+        check(self.lib.cmc_step_profiled(self.ctx, int(n_steps), ms.ctypes.data), self.ctx, self.lib)
         return dict(zip(_native.STAGE_NAMES, (float(v) for v in ms)))
 
     def energy(self) -> np.ndarray:
         out = np.zeros((self.n_clusters, 3))
-        check(self.lib.cmc_energy(self.ctx, out.ctypes.data), self.ctx)
+        check(self.lib.cmc_energy(self.ctx, out.ctypes.data), self.ctx, self.lib)
         return out
 
     def lagrange_radii(self, fracs) -> np.ndarray:
         fr = np.ascontiguousarray(fracs, dtype=np.float64)
         out = np.zeros((self.n_clusters, fr.shape[0]))
         check(self.lib.cmc_lagrange_radii(self.ctx, fr.ctypes.data, fr.shape[0],
-                                          out.ctypes.data), self.ctx)
+                                          out.ctypes.data), self.ctx, self.lib)
         return out
 
     def rng_state(self) -> np.ndarray:
         """The Tausworthe stream states (4 words per slot), rng = taus113 only."""
         nw = np.zeros(1, dtype=np.int64)
-        check(self.lib.cmc_get_rng_state(self.ctx, None, nw.ctypes.data), self.ctx)
+        check(self.lib.cmc_get_rng_state(self.ctx, None, nw.ctypes.data), self.ctx, self.lib)
         out = np.zeros(int(nw[0]), dtype=np.uint32)
-        check(self.lib.cmc_get_rng_state(self.ctx, out.ctypes.data, nw.ctypes.data), self.ctx)
+        check(self.lib.cmc_get_rng_state(self.ctx, out.ctypes.data, nw.ctypes.data), self.ctx, self.lib)
         return out
 
     def set_rng_state(self, words):
         words = np.ascontiguousarray(words, dtype=np.uint32)
-        check(self.lib.cmc_set_rng_state(self.ctx, words.ctypes.data, words.shape[0]), self.ctx)
+        check(self.lib.cmc_set_rng_state(self.ctx, words.ctypes.data, words.shape[0]), self.ctx, self.lib)
 
     def core(self) -> np.ndarray:
         """Per cluster {rho_c, r_c, number of estimates} (Eq. 19)."""
         out = np.zeros((self.n_clusters, 3))
-        check(self.lib.cmc_core(self.ctx, out.ctypes.data), self.ctx)
+        check(self.lib.cmc_core(self.ctx, out.ctypes.data), self.ctx, self.lib)
         return out
 
     def get_state(self, out=None):
@@ -169,51 +169,62 @@ class Cluster:
         check(self.lib.cmc_get_state(self.ctx, _ptr(out.get("r")), _ptr(out.get("vr")),
                                      _ptr(out.get("vt")), _ptr(out.get("m")),
                                      _ptr(out.get("id")), _ptr(out.get("phi")),
-                                     step.ctypes.data, kind), self.ctx)
+                                     step.ctypes.data, kind), self.ctx, self.lib)
         out["step"] = int(step[0])
         return out
 
     def set_radii(self, R):
         """Stellar radii of the stars in get_state order (collisions=1)."""
         R = np.ascontiguousarray(R, dtype=np.float64)
-        check(self.lib.cmc_set_radii(self.ctx, R.ctypes.data, 0), self.ctx)
+        check(self.lib.cmc_set_radii(self.ctx, R.ctypes.data, 0), self.ctx, self.lib)
 
     def radii(self) -> np.ndarray:
         out = np.empty(self.n)
-        check(self.lib.cmc_get_radii(self.ctx, out.ctypes.data, 0), self.ctx)
+        check(self.lib.cmc_get_radii(self.ctx, out.ctypes.data, 0), self.ctx, self.lib)
         return out
 
     def set_state(self, state, step: int):
         kind = 0 if isinstance(state["r"], np.ndarray) else 1
         arrs = [self._prep(state[k], k, kind) for k in ("r", "vr", "vt", "m", "id")]
         check(self.lib.cmc_set_state(self.ctx, *[_ptr(a) for a in arrs], int(step), kind),
-              self.ctx)
+              self.ctx, self.lib)
 
     def nbound(self) -> np.ndarray:
         out = np.zeros(self.n_clusters, dtype=np.int64)
-        check(self.lib.cmc_get_nbound(self.ctx, out.ctypes.data), self.ctx)
+        check(self.lib.cmc_get_nbound(self.ctx, out.ctypes.data), self.ctx, self.lib)
         return out
 
     def dt(self) -> np.ndarray:
         out = np.zeros(self.n_clusters)
-        check(self.lib.cmc_get_dt(self.ctx, out.ctypes.data), self.ctx)
+        check(self.lib.cmc_get_dt(self.ctx, out.ctypes.data), self.ctx, self.lib)
         return out
 
     def stats(self) -> list:
         out = np.zeros((self.n_clusters, _native.CMC_NSTATS), dtype=np.int64)
-        check(self.lib.cmc_get_stats(self.ctx, out.ctypes.data), self.ctx)
+        check(self.lib.cmc_get_stats(self.ctx, out.ctypes.data), self.ctx, self.lib)
         return [dict(zip(STAT_NAMES, (int(v) for v in row))) for row in out]
 
     def escaped(self) -> np.ndarray:
         """(n_clusters, 2): mass and energy carried off by escapers; the
         conserved total is energy()[:, 2] + escaped()[:, 1]."""
         out = np.zeros((self.n_clusters, 2))
-        check(self.lib.cmc_get_escaped(self.ctx, out.ctypes.data), self.ctx)
+        check(self.lib.cmc_get_escaped(self.ctx, out.ctypes.data), self.ctx, self.lib)
         return out
+
+    def diagnostics(self) -> np.ndarray:
+        """(n_clusters, records, len(DIAG_FIELDS)): the per-step diagnostics
+        ring (config diag_ring > 0), oldest record first."""
+        nrec = ctypes.c_int32(0)
+        check(self.lib.cmc_get_diagnostics(self.ctx, None, ctypes.byref(nrec)), self.ctx, self.lib)
+        cap = self.cfg.diag_ring
+        out = np.zeros((self.n_clusters, cap, len(_native.DIAG_FIELDS)))
+        check(self.lib.cmc_get_diagnostics(self.ctx, out.ctypes.data, ctypes.byref(nrec)),
+              self.ctx, self.lib)
+        return out[:, : nrec.value]
 
     def set_escaped(self, budget):
         b = np.ascontiguousarray(budget, dtype=np.float64).reshape(self.n_clusters, 2)
-        check(self.lib.cmc_set_escaped(self.ctx, b.ctypes.data), self.ctx)
+        check(self.lib.cmc_set_escaped(self.ctx, b.ctypes.data), self.ctx, self.lib)
 
     def total_energy(self) -> np.ndarray:
         """K + W of the bound stars plus the energy the escapers took."""
@@ -227,14 +238,14 @@ class Cluster:
         multisplit (match or ballot), the mixed-mode orbit variant and the
         relaxation variant."""
         out = np.zeros(5, dtype=np.int32)
-        check(self.lib.cmc_get_tuning(self.ctx, out.ctypes.data), self.ctx)
+        check(self.lib.cmc_get_tuning(self.ctx, out.ctypes.data), self.ctx, self.lib)
         return {"orbit_block": int(out[0]), "sort_keys_per_thread": int(out[1]),
                 "sort_multisplit": "ballot" if out[2] else "match",
                 "orbit_variant": int(out[3]), "relax_variant": int(out[4])}
 
     def set_stream(self, stream):
         self.stream = _stream_ptr(stream)
-        check(self.lib.cmc_set_stream(self.ctx, self.stream), self.ctx)
+        check(self.lib.cmc_set_stream(self.ctx, self.stream), self.ctx, self.lib)
 
 
 # --------------------------------------------------------------- stages

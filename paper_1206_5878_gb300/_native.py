@@ -24,8 +24,10 @@ STATUS_NAMES = {0: "CMC_OK", 1: "CMC_EINVAL", 2: "CMC_ENOMEM", 3: "CMC_ECUDA",
                 4: "CMC_ENOCONV", 5: "CMC_ETIMEOUT", 6: "CMC_EPOISONED"}
 STAT_NAMES = ("escaped", "degenerate", "cap_hits", "trials", "violations", "clamps",
               "angle_fails", "ties", "fp64_trials", "clamp_energy", "collisions",
-              "collision_energy")
+              "collision_energy", "envelope_fp64")
 CMC_NSTATS = len(STAT_NAMES)
+DIAG_FIELDS = ("step", "dt", "nbound", "K", "W", "E_total", "M_esc", "E_esc", "trials",
+               "err")
 STAGE_NAMES = ("timestep", "relax", "turning", "orbit", "sort", "gather", "potential",
                "correction", "end")
 
@@ -34,7 +36,7 @@ class cmc_config(ctypes.Structure):
     _fields_ = [("precision", _i32), ("bin_size", _i32), ("theta_max", _d), ("gamma", _d),
                 ("max_trials", _i32), ("energy_correction", _i32), ("orbit_block", _i32),
                 ("autotune", _i32), ("orbit_variant", _i32), ("rng", _i32),
-                ("relax_variant", _i32), ("collisions", _i32)]
+                ("relax_variant", _i32), ("collisions", _i32), ("diag_ring", _i32)]
 
 
 # exported symbol -> (restype, argtypes); the list is the ABI of include/cmc.h
@@ -55,6 +57,9 @@ SIGNATURES = {
     "cmc_get_dt": (_i32, [_p, _p]),
     "cmc_get_stats": (_i32, [_p, _p]),
     "cmc_get_escaped": (_i32, [_p, _p]),
+    "cmc_get_diagnostics": (_i32, [_p, _p, _p]),
+    "cmc_debug_check": (_i32, [_p]),
+    "cmc_is_debug_build": (_i32, []),
     "cmc_set_escaped": (_i32, [_p, _p]),
     "cmc_kernels_per_step": (_i32, [_p]),
     "cmc_get_tuning": (_i32, [_p, _p]),
@@ -76,28 +81,30 @@ SIGNATURES = {
     "cmc_get_radii": (_i32, [_p, _p, _i32]),
 }
 
-_lib = None
+_libs = {}
 
 
-def lib_path() -> str:
-    return _build.LIB
+def lib_path(debug: bool = False) -> str:
+    return _build.LIB_DEBUG if debug else _build.LIB
 
 
-def load():
-    """Load libcmc.so (raises RuntimeError when it has not been built)."""
-    global _lib
-    if _lib is not None:
-        return _lib
-    if not os.path.exists(_build.LIB):
+def load(debug: bool = False):
+    """Load libcmc.so, or with debug=True libcmc_debug.so (the build with
+    device-side index checks); raises RuntimeError when it has not been
+    built."""
+    if debug in _libs:
+        return _libs[debug]
+    path = lib_path(debug)
+    if not os.path.exists(path):
         raise RuntimeError(
-            "libcmc.so is not built; run paper_1206_5878_gb300._build.build() "
-            "(needs nvcc) before using the CUDA path")
-    lib = ctypes.CDLL(_build.LIB)
+            "%s is not built; run paper_1206_5878_gb300._build.build(debug=%s) "
+            "(needs nvcc) before using the CUDA path" % (os.path.basename(path), debug))
+    lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
-    _lib = lib
+    _libs[debug] = lib
     return lib
 
 
@@ -107,7 +114,7 @@ class CMCError(RuntimeError):
         self.status = status
 
 
-def check(status: int, ctx=None):
+def check(status: int, ctx=None, lib=None):
     if status != CMC_OK:
-        msg = load().cmc_last_error(ctx)
+        msg = (lib or load()).cmc_last_error(ctx)
         raise CMCError(status, msg.decode() if msg else "")

@@ -7,6 +7,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cmc_host.hpp"
 #include "../../include/cmc.h"
 
@@ -37,6 +39,7 @@ struct cmc_ctx {
   uint32_t* step = nullptr;
   uint32_t* pcount = nullptr;  // pending stars of the sampled orbit step
   double* Fx = nullptr;        // FP64 mode's envelope F of every star (precision 0)
+  double* ring = nullptr;      // per-step diagnostics (cfg.diag_ring records per cluster)
   int64_t steps_taken = 0;
   cudaGraphExec_t exec = nullptr;
   bool poisoned = false;
@@ -183,13 +186,22 @@ void order_state(cmc_ctx* c, cudaStream_t st) {
   }
 }
 
+// stage names (cmc_step_profiled, NVTX ranges)
+const char* const kStageName[CMC_NSTAGES] = {"timestep", "relax",     "turning",
+                                             "orbit",    "sort",      "gather",
+                                             "potential", "correction", "end"};
+
 // The kernels of one timestep, in the order of section 3.3.  With ev, an
-// event is recorded before the first stage and after every stage.
+// event is recorded before the first stage and after every stage, and
+// every stage is an NVTX range (for timeline tools).
 void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   const SegLayout& L = c->L;
   const bool mixed = c->cfg.precision == 1, tab = c->cfg.precision != 2;
   auto mark = [&](int i) {
-    if (ev) cudaEventRecord(ev[i], st);
+    if (!ev) return;
+    cudaEventRecord(ev[i], st);
+    if (i > 0) nvtxRangePop();
+    if (i < CMC_NSTAGES) nvtxRangePushA(kStageName[i]);
   };
   mark(0);
   launch_bins(L, c->r, c->vr, c->vt, c->m, c->nbin, c->pref, st);
@@ -242,6 +254,12 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   }
   mark(8);
   launch_step_end(L, c->step, c->r_old, c->cc, c->m, st);
+  if (c->ring) {
+    // K and W of the new state (r_old is free scratch now), then the record
+    launch_energy(L, c->r, c->vr, c->vt, c->m, c->tile_a, c->tile_b, c->tile_c, c->r_old,
+                  c->out3, st);
+    launch_diag_ring(L, c->out3, c->step, c->err, c->ring, c->cfg.diag_ring, st);
+  }
   mark(9);
 }
 
@@ -251,7 +269,8 @@ int count_step_kernels(const cmc_ctx* c) {
   // sampler, FP64 continuation, slopes at the tile seams, 2 bucket-index + 3
   // grid kernels; precision 0: the envelope], [correction], step end
   const int p = c->cfg.precision;
-  return 3 + (c->R ? 1 : 0) + 2 + 5 + 1 + 1 + 1 + (p == 1 ? 9 : p == 0 ? 10 : 0) +
+  return 3 + (c->R ? 1 : 0) + (c->ring ? 4 : 0) + 2 + 5 + 1 + 1 + 1 +
+         (p == 1 ? 9 : p == 0 ? 10 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 
@@ -274,6 +293,7 @@ void free_ctx(cmc_ctx* c) {
   dfree(c->step, st);
   dfree(c->pcount, st);
   dfree(c->Fx, st);
+  dfree(c->ring, st);
   free_sort(c->W, st);
   free_buckets(c->bk, st);
   dfree(c->L.taus, st);
@@ -536,6 +556,10 @@ cmc_status autotune(cmc_ctx* c) {
 
 }  // namespace
 
+namespace cmc {
+CMC_DEBUG_SITE_ACCESSOR
+}  // namespace cmc
+
 extern "C" {
 
 void cmc_config_default(cmc_config* cfg) {
@@ -553,6 +577,7 @@ void cmc_config_default(cmc_config* cfg) {
   cfg->rng = 0;
   cfg->relax_variant = -1;
   cfg->collisions = 0;
+  cfg->diag_ring = 0;
 }
 
 cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
@@ -571,7 +596,8 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
       !(cfg.gamma > 0.0) || cfg.orbit_block < 0 || cfg.orbit_block > 256 ||
       (cfg.orbit_block % 32) || cfg.orbit_variant < -1 || cfg.orbit_variant >= kOrbitVariants ||
       (cfg.rng != 0 && cfg.rng != 1) || cfg.relax_variant < -1 ||
-      cfg.relax_variant >= kRelaxVariants || (cfg.collisions != 0 && cfg.collisions != 1))
+      cfg.relax_variant >= kRelaxVariants || (cfg.collisions != 0 && cfg.collisions != 1) ||
+      cfg.diag_ring < 0 || cfg.diag_ring > (1 << 20))
     return fail(nullptr, CMC_EINVAL, "cmc_init: bad configuration");
   std::vector<int64_t> sizes(n_per_cluster, n_per_cluster + n_clusters);
   std::vector<uint64_t> sd(seeds, seeds + n_clusters);
@@ -607,6 +633,11 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   CMC_ALLOC(c->id, n);
   if (cfg.precision != 2) CMC_ALLOC(c->t32, n);
   if (cfg.precision == 0) CMC_ALLOC(c->Fx, n);
+  if (cfg.diag_ring > 0) {
+    CMC_ALLOC(c->ring, (size_t)n_clusters * cfg.diag_ring * kDiagFields);
+    if (!e) e = cudaMemsetAsync(c->ring, 0, sizeof(double) * (size_t)n_clusters *
+                                                cfg.diag_ring * kDiagFields, st);
+  }
   CMC_ALLOC(c->keys, n);
   CMC_ALLOC(c->vals, n);
   CMC_ALLOC(c->pay, n);
@@ -679,12 +710,15 @@ cmc_status cmc_step(cmc_ctx* c, int32_t n_steps) {
     cudaGraphDestroy(graph);
     if (e) { c->exec = nullptr; return cuda_fail(c, e, "cmc_step: instantiate"); }
   }
+  nvtxRangePushA("cmc_step");
   for (int32_t i = 0; i < n_steps; ++i) {
     e = cudaGraphLaunch(c->exec, c->stream);
-    if (e) return cuda_fail(c, e, "cmc_step: launch");
+    if (e) { nvtxRangePop(); return cuda_fail(c, e, "cmc_step: launch"); }
   }
   c->steps_taken += n_steps;
-  return check_err_flags(c);
+  const cmc_status s = check_err_flags(c);
+  nvtxRangePop();
+  return s;
 }
 
 cmc_status cmc_step_profiled(cmc_ctx* c, int32_t n_steps, double* stage_ms) {
@@ -873,6 +907,56 @@ cmc_status cmc_get_escaped(cmc_ctx* c, double* out) {
   if (!e) e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_fail(c, e, "cmc_get_escaped");
   return CMC_OK;
+}
+
+cmc_status cmc_get_diagnostics(cmc_ctx* c, double* out, int32_t* n_records) {
+  if (!c || !n_records) return fail(c, CMC_EINVAL, "cmc_get_diagnostics: bad arguments");
+  if (!c->ring) return fail(c, CMC_EINVAL, "cmc_get_diagnostics: the ring is off (diag_ring 0)");
+  const int cap = c->cfg.diag_ring;
+  const int64_t steps = c->steps_taken;
+  const int nrec = steps < cap ? (int)steps : cap;
+  *n_records = nrec;
+  if (!out || nrec == 0) return CMC_OK;
+  DeviceGuard g(c->device);
+  const size_t nseg = (size_t)c->L.n_seg;
+  std::vector<double> h(nseg * cap * kDiagFields);
+  cudaError_t e = cudaMemcpyAsync(h.data(), c->ring, sizeof(double) * h.size(),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, "cmc_get_diagnostics");
+  // the step counter of the newest record: slot (step - 1) mod cap
+  const double* first = h.data();
+  uint32_t newest = 0;
+  for (int j = 0; j < cap; ++j) {
+    const uint32_t s = (uint32_t)first[(size_t)j * kDiagFields];
+    if (s > newest) newest = s;
+  }
+  for (size_t cl = 0; cl < nseg; ++cl)
+    for (int i = 0; i < nrec; ++i) {
+      const uint32_t stp = newest - (uint32_t)(nrec - 1 - i);
+      const size_t slot = (stp - 1u) % (uint32_t)cap;
+      std::memcpy(out + (cl * cap + i) * kDiagFields, h.data() + (cl * cap + slot) * kDiagFields,
+                  sizeof(double) * kDiagFields);
+    }
+  return CMC_OK;
+}
+
+cmc_status cmc_debug_check(uint32_t* site) {
+  if (!site) return fail(nullptr, CMC_EINVAL, "cmc_debug_check: bad arguments");
+  const uint32_t v[5] = {cmc::debug_site_tu1(), cmc::debug_site_tu2(), cmc::debug_site_tu3(),
+                         cmc::debug_site_tu4(), cmc::debug_site_tu5()};
+  *site = 0u;
+  for (uint32_t x : v)
+    if (x && !*site) *site = x;
+  return CMC_OK;
+}
+
+int32_t cmc_is_debug_build(void) {
+#ifdef CMC_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
 }
 
 cmc_status cmc_set_escaped(cmc_ctx* c, const double* in) {

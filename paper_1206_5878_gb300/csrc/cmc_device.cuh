@@ -32,6 +32,29 @@ constexpr uint32_t kTagCol = 4;      // relaxation pair: sticky-sphere collision
 // their low 4 bits -- in (key, id) order, which for these keys is id order)
 constexpr uint64_t kEscKeyBase = 0x7FF0000000000000ull;
 
+// Debug builds (-DCMC_DEBUG, libcmc_debug.so): index checks at the table
+// probes and scatters that a wrong bracket, bucket or segment offset would
+// send out of range.  A failed check records the first failing site of its
+// translation unit (CMC_TU x 100000 + source line) in that unit's
+// g_debug_site, and the access is skipped; release builds compile the
+// checks to nothing.
+#ifndef CMC_TU
+#define CMC_TU 0
+#endif
+#ifdef CMC_DEBUG
+static __device__ unsigned int g_debug_site = 0u;
+__device__ __forceinline__ bool debug_in(unsigned long long i, unsigned long long n,
+                                         unsigned site) {
+  if (i < n) return true;
+  atomicCAS(&g_debug_site, 0u, site);
+  return false;
+}
+#define CMC_IN(i, n) \
+  ::cmc::debug_in((unsigned long long)(i), (unsigned long long)(n), CMC_TU * 100000u + __LINE__)
+#else
+#define CMC_IN(i, n) true
+#endif
+
 // error bits (fatal: they poison the context)
 enum : uint32_t {
   kErrTimeout = 1u << 0,   // a bounded device wait gave up
@@ -44,12 +67,13 @@ enum : uint32_t {
 enum : int {
   kStEscaped = 0, kStDegenerate, kStCapHits, kStTrials, kStViolations,
   kStClamps, kStAngleFails, kStTies, kStFp64Trials, kStClampEnergy, kStCollisions,
-  kStCollisionEnergy, kStCount
+  kStCollisionEnergy, kStEnvelope64, kStCount
 };
 // (slot 15: the collision count at the last step end, to tell this step's
 // merged-away stars from its escapers)
 constexpr int kStCollisionsSeen = 15;
 constexpr int kStStride = 16;        // counters reserved per segment
+constexpr int kDiagFields = 10;      // doubles per diagnostics record
 
 // ------------------------------------------------------- segment layout
 // Clusters of an ensemble are stored back to back.  Segment c owns global

@@ -237,6 +237,9 @@ void launch_grid(const SegLayout& L, const double* x, const double* phi, const d
 // FP64 one.  precision 2 (FP64 by bisection): one kernel on the FP64 table.
 void launch_slopes(int64_t n, const double* x, const double* phi, double* Menc,
                    cudaStream_t st);
+// one diagnostics record per segment (after the step end; K, W in out3)
+void launch_diag_ring(const SegLayout& L, const double* out3, const uint32_t* step,
+                      const uint32_t* err, double* ring, int cap, cudaStream_t st);
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
                   const double* x, const double* phi, const double* Menc,
                   const double* vr,
@@ -314,5 +317,27 @@ void launch_taus_init(int64_t slots, int n_seg, const int64_t* base, const uint4
                       const uint32_t* P, uint4* table, cudaStream_t st);
 void launch_check_ids(const SegLayout& L, const uint64_t* sorted_ids, uint32_t* err,
                       cudaStream_t st);
+
+// The first failed index check of each translation unit of a debug build
+// since the last call (0: none), cleared; 0 in a release build.
+uint32_t debug_site_tu1();
+uint32_t debug_site_tu2();
+uint32_t debug_site_tu3();
+uint32_t debug_site_tu4();
+uint32_t debug_site_tu5();
+#define CMC_CAT2(a, b) a##b
+#define CMC_CAT(a, b) CMC_CAT2(a, b)
+#ifdef CMC_DEBUG
+#define CMC_DEBUG_SITE_ACCESSOR                                              \
+  uint32_t CMC_CAT(debug_site_tu, CMC_TU)() {                                \
+    unsigned int v = 0u, z = 0u;                                             \
+    cudaMemcpyFromSymbol(&v, g_debug_site, sizeof(v));                       \
+    cudaMemcpyToSymbol(g_debug_site, &z, sizeof(z));                         \
+    return v;                                                                \
+  }
+#else
+#define CMC_DEBUG_SITE_ACCESSOR \
+  uint32_t CMC_CAT(debug_site_tu, CMC_TU)() { return 0u; }
+#endif
 
 }  // namespace cmc

@@ -114,6 +114,7 @@ __global__ void __launch_bounds__(128, kMinB) k_relax(Seg S, int bs, double* vr,
   const int64_t la = 2 * j;
   if (la + 1 >= S.nb[c]) return;
   const int64_t a = S.off[c] + la, b = a + 1;
+  if (!CMC_IN(S.bin_off[c] + la / bs, S.bin_off[c + 1])) return;
   const double n = nbin[S.bin_off[c] + la / bs];
   const double m1 = m[a], m2 = m[b];
   const double msum = m1 + m2;
@@ -330,5 +331,7 @@ void launch_relax(const SegLayout& L, double* vr, double* vt, double* m, const u
   else relax_shape<1>(L, vr, vt, m, id, nbin, step, col, st);
 }
 
+
+CMC_DEBUG_SITE_ACCESSOR
 
 }  // namespace cmc

@@ -132,6 +132,7 @@ __device__ __forceinline__ int64_t fix_shell_nodes(const double4_32a* __restrict
   if (i < -1) i = -1;
   if (i >= nb) i = nb - 1;
   const long long qb = dbits(q);
+  if (!CMC_IN(i < 0 ? 0 : i, nb)) i = -1;
   a = nd[i < 0 ? 0 : i];
   double4_32a b = i + 1 < nb ? nd[i + 1] : a;
   for (int w = 0; w < 64; ++w) {
@@ -275,6 +276,7 @@ __device__ __forceinline__ void shells32_bk(const Tab& tab, int nb, const Bucket
     if (d < 0) { lo[q] = -1; hi[q] = B.lo; continue; }           // inner tail
     const long long b = d >> B.shift;
     if (b >= B.nbk) { lo[q] = B.hi; hi[q] = nb; continue; }      // outer tail
+    if (!CMC_IN(b + 1, B.nbk + 1)) { lo[q] = -1; hi[q] = nb; continue; }
     const int s0 = __ldg(B.start + b), s1 = __ldg(B.start + b + 1);
     lo[q] = s0 - 1;
     hi[q] = s1;
@@ -297,7 +299,7 @@ __device__ __forceinline__ void shells32_bk(const Tab& tab, int nb, const Bucket
         mj = mj < lo[q] + 1 ? lo[q] + 1 : mj;
         mj = mj > hi[q] - 1 ? hi[q] - 1 : mj;
         m[q][j] = mj;
-        v[q][j] = c > 0 ? tab.load(mj) : typename Tab::V(0);
+        v[q][j] = c > 0 && CMC_IN(mj, nb) ? tab.load(mj) : typename Tab::V(0);
       }
     }
 #pragma unroll
@@ -351,6 +353,7 @@ __device__ __forceinline__ float grid_phi(const Grid& G, float xq) {
   if (key < G.key0) return __ldg(G.phi) + G.mb * (G.x0 - xq);     // beyond the last
   const uint32_t d = key - G.key0;
   const int g = (int)(d >> G.sh);
+  if (!CMC_IN(g + 1, G.cells)) return G.phi0;
   // f = (d mod 2^sh) 2^-sh, exact: 1 + f assembled from its bits, minus 1
   const float f =
       __uint_as_float(0x3F800000u | ((d & ((1u << G.sh) - 1u)) << (23 - G.sh))) - 1.0f;
@@ -406,7 +409,9 @@ __device__ __forceinline__ void point64(const double4_32a* __restrict__ nd, int6
 
 // FP64 mode: the orbit point r(s) in FP64 from an FP32 shell guess sh
 // (moved to the exact shell), Phi by Eq. 6's division form (the FP64
-// statement of the method, as phi_in_shell), L = J / r and Q
+// statement of the method, as phi_in_shell), L = J / r and Q.  Its
+// quotients go through the shared bodies (div_rn_nl): measured faster in
+// the long kernels that use it.
 __device__ __forceinline__ void point64_div(const double4_32a* __restrict__ nd, int64_t nb,
                                             const Star& st, double c0, double c1, double sv,
                                             int sh, double& rs, double& ph, double& Q) {
@@ -416,7 +421,7 @@ __device__ __forceinline__ void point64_div(const double4_32a* __restrict__ nd, 
   if (i < 0) {
     ph = a.z;  // node 0's Phi: the central constant
   } else {
-    const double xq = div_rn(1.0, rs);
+    const double xq = div_rn_nl(1.0, rs);
     double xj1 = 0.0, pj1 = 0.0;
     if (i + 1 < nb) {
       const double4_32a b = nd[i + 1];
@@ -424,16 +429,16 @@ __device__ __forceinline__ void point64_div(const double4_32a* __restrict__ nd, 
       pj1 = b.z;
     }
     const double den = a.y - xj1;
-    ph = !(den > 0.0) ? a.z : a.z + div_rn(a.y - xq, den) * (pj1 - a.z);
+    ph = !(den > 0.0) ? a.z : a.z + div_rn_nl(a.y - xq, den) * (pj1 - a.z);
   }
-  const double L = div_rn(st.J, rs);
+  const double L = div_rn_nl(st.J, rs);
   Q = scale_up<1>(st.E - ph) - L * L;
 }
 
 // g(s) of FP64 mode at the point of point64_div
 __device__ __forceinline__ double g_of_point(double c1, double sv, double Q) {
   if (!(Q > 0.0)) return 0.0;
-  return div_rn((3.0 * c1) * (1.0 - sv * sv), sqrt_rn(Q));
+  return div_rn_nl((3.0 * c1) * (1.0 - sv * sv), sqrt_rn_nl(Q));
 }
 
 // (2k + 1) 2^-24 from the top 23 bits of a word: exact in float, in (0, 1)
@@ -868,75 +873,139 @@ __device__ __forceinline__ int g32_bounded(const Grid& G, float E, float J, floa
 __constant__ float c_s32[21] = {CMC_SJ21(CMC_SJF)};
 
 // FP64 mode's envelope F = 1.2 max_j g(s_j) over the 21 samples, the FP64
-// value (Eq. 6's division form, as the FP64 statement of the method), for
-// about one FP64 evaluation per star: every g(s_j) is first bounded in FP32
-// (g32_bounded); only the samples whose upper bound reaches the largest
-// lower bound, and those FP32 cannot bound, can hold the maximum, and only
-// they are evaluated in FP64 (shell from the bucket index, made exact on
-// the node records).  F = 0 for stars without an orbit to sample (r_max <=
-// r_min: every g is 0 or negative there).
-__global__ void __launch_bounds__(128) k_envelope64(Seg S, const double* r, const double* phi,
-                                                    const double* vr, const double* vt,
-                                                    BucketArgs BA, const double* tp_min,
-                                                    const double* tp_max, double* Fx,
-                                                    int64_t n) {
-  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
-  const int c = seg_find(S.off, S.n_seg, p);
-  const int64_t sb = S.off[c], nbc = S.nb[c], k = p - sb;
-  double F = 0.0;
-  const double vrk = vr[p], vtk = vt[p];
+// value (Eq. 6's division form, as the FP64 statement of the method):
+// every g(s_j) is first bounded in FP32 (g32_bounded); only the samples
+// whose upper bound reaches the largest lower bound, and those FP32 cannot
+// bound, can hold the maximum, and only they are evaluated in FP64.  Nearly
+// circular orbits have a flat g and FP32 bounds too loose to rank their
+// samples, so the candidates per star range from 1 to 21: each warp pools
+// its lanes' (star, sample) candidates and evaluates them 32 at a time
+// (shell from the bucket index made exact on the node records), the
+// maximum per star kept in shared memory as bits (g >= 0 orders as its
+// bits).  F = 0 for stars without an orbit to sample (r_max <= r_min: every
+// g is 0 or negative there).
+constexpr int kEnvThreads = 128;
+
+// FP64 g at sample j of a star (the noinline quotients keep this copy small)
+__device__ __noinline__ double g64_sample(const double4_32a* __restrict__ nd, int64_t nb,
+                                          const Buckets& BK, double E, double J, double c0,
+                                          double c1, int j) {
   Star s;
-  s.k = k;
-  s.E = __ldg(phi + p) + scale_down<1>(vrk * vrk + vtk * vtk);
-  s.J = r[p] * vtk;
-  const double rmin = k < nbc ? __ldg(tp_min + p) : 0.0, rmax = k < nbc ? __ldg(tp_max + p) : 0.0;
-  if (k < nbc && lt0(s.E) && gt_pos(rmax, rmin)) {
-    const double c0 = scale_down<1>(rmax + rmin);
-    const double c1 = scale_down<2>(rmax - rmin);
-    const float c0f = f32_rn(c0), c1f = f32_rn(c1), E32 = f32_rn(s.E), J32 = f32_rn(s.J);
-    const Grid GD = grid_of(BA, c);
-    float hi[21];
-    unsigned pos = 0u, cand = 0u;
-    float lo_max = 0.0f;
-#pragma unroll
-    for (int j = 0; j < 21; ++j) {
-      float g = 0.0f, eg = 0.0f;
-      const int st = g32_bounded(GD, E32, J32, c0f, c1f, c_s32[j], g, eg);
-      hi[j] = 0.0f;
-      if (st > 0) {
-        const float lo = g * (1.0f - eg);
-        hi[j] = g * (1.0f + eg);
-        lo_max = lo > lo_max ? lo : lo_max;
-        pos |= 1u << j;
-      } else if (st < 0) {
-        cand |= 1u << j;
+  s.k = 0;
+  s.E = E;
+  s.J = J;
+  const float c0f = f32_rn(c0), c1f = f32_rn(c1);
+  double rs, ph, Q;
+  point64_div(nd, nb, s, c0, c1, c_s64[j], shell32_of(nd, (int)nb, BK, c0f, c1f, c_s32[j]), rs,
+              ph, Q);
+  return g_of_point(c1, c_s64[j], Q);
+}
+
+__global__ void __launch_bounds__(kEnvThreads) k_envelope64(Seg S, const double* r,
+                                                            const double* phi, const double* vr,
+                                                            const double* vt, BucketArgs BA,
+                                                            const double* tp_min,
+                                                            const double* tp_max, double* Fx,
+                                                            int64_t n) {
+  __shared__ unsigned long long s_gmax[kEnvThreads];
+  __shared__ float s_hi[21][kEnvThreads];  // upper bounds of the samples
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int wbase = threadIdx.x & ~31;
+  s_gmax[threadIdx.x] = 0ull;
+  int c = -1;
+  double E = 0.0, J = 0.0, c0 = 0.0, c1 = 0.0;
+  unsigned cand = 0u;
+  if (p < n) {
+    c = seg_find(S.off, S.n_seg, p);
+    const int64_t nbc = S.nb[c], k = p - S.off[c];
+    const double vrk = vr[p], vtk = vt[p];
+    E = __ldg(phi + p) + scale_down<1>(vrk * vrk + vtk * vtk);
+    J = r[p] * vtk;
+    const double rmin = k < nbc ? __ldg(tp_min + p) : 0.0;
+    const double rmax = k < nbc ? __ldg(tp_max + p) : 0.0;
+    if (k < nbc && lt0(E) && gt_pos(rmax, rmin)) {
+      c0 = scale_down<1>(rmax + rmin);
+      c1 = scale_down<2>(rmax - rmin);
+      const float c0f = f32_rn(c0), c1f = f32_rn(c1), E32 = f32_rn(E), J32 = f32_rn(J);
+      const Grid GD = grid_of(BA, c);
+      unsigned pos = 0u;
+      float lo_max = 0.0f;
+      // one copy of the sample code (not unrolled: code size), the upper
+      // bounds kept in shared memory
+#pragma unroll 1
+      for (int jj = 0; jj < 21; ++jj) {
+        float g = 0.0f, eg = 0.0f;
+        const int st = g32_bounded(GD, E32, J32, c0f, c1f, c_s32[jj], g, eg);
+        float h = 0.0f;
+        if (st > 0) {
+          const float lo = g * (1.0f - eg);
+          h = g * (1.0f + eg);
+          lo_max = lo > lo_max ? lo : lo_max;
+          pos |= 1u << jj;
+        } else if (st < 0) {
+          cand |= 1u << jj;
+        }
+        s_hi[jj][threadIdx.x] = h;
       }
+#pragma unroll 1
+      for (int jj = 0; jj < 21; ++jj)
+        if (((pos >> jj) & 1u) && s_hi[jj][threadIdx.x] >= lo_max) cand |= 1u << jj;
     }
-#pragma unroll
-    for (int j = 0; j < 21; ++j)
-      if (((pos >> j) & 1u) && hi[j] >= lo_max) cand |= 1u << j;
-    Buckets BK;
-    const int4 pr = BA.prm[c];
-    BK.start = BA.start + BA.off[c];
-    BK.base = BA.base[c];
-    BK.shift = pr.x;
-    BK.nbk = pr.y;
-    BK.lo = pr.z;
-    BK.hi = pr.w;
-    double gmax = 0.0;
-    while (cand) {
-      const int j = __ffs(cand) - 1;
-      cand &= cand - 1u;
-      double rs, ph, Q;
-      point64_div(BA.node + sb, nbc, s, c0, c1, c_s64[j],
-                  shell32_of(BA.node + sb, (int)nbc, BK, c0f, c1f, c_s32[j]), rs, ph, Q);
-      const double g = g_of_point(c1, c_s64[j], Q);
-      if (g > gmax) gmax = g;
-    }
-    F = 1.2 * gmax;
   }
-  Fx[p] = F;
+  __syncwarp();
+  // the warp's candidates, numbered lane by lane
+  const unsigned cnt = (unsigned)__popc(cand);
+  unsigned incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+    if (lane >= o) incl += v;
+  }
+  const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+  for (unsigned t0 = 0; t0 < total; t0 += 32) {
+    const unsigned t = t0 + (unsigned)lane;
+    // owner: the first lane whose inclusive count exceeds t
+    int own = 0;
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const unsigned v = __shfl_sync(0xFFFFFFFFu, incl, own + step - 1);
+      if (v <= t) own += step;
+    }
+    const unsigned o_incl = __shfl_sync(0xFFFFFFFFu, incl, own);
+    const unsigned o_cnt = __shfl_sync(0xFFFFFFFFu, cnt, own);
+    const unsigned o_cand = __shfl_sync(0xFFFFFFFFu, cand, own);
+    const int o_c = __shfl_sync(0xFFFFFFFFu, c, own);
+    const double o_E = __shfl_sync(0xFFFFFFFFu, E, own);
+    const double o_J = __shfl_sync(0xFFFFFFFFu, J, own);
+    const double o_c0 = __shfl_sync(0xFFFFFFFFu, c0, own);
+    const double o_c1 = __shfl_sync(0xFFFFFFFFu, c1, own);
+    if (t < total) {
+      const int rank = (int)(t - (o_incl - o_cnt));  // which of the owner's candidates
+      const int jj = (int)__fns(o_cand, 0u, rank + 1);
+      const int64_t sb = S.off[o_c], nbc = S.nb[o_c];
+      Buckets BK;
+      const int4 pr = BA.prm[o_c];
+      BK.start = BA.start + BA.off[o_c];
+      BK.base = BA.base[o_c];
+      BK.shift = pr.x;
+      BK.nbk = pr.y;
+      BK.lo = pr.z;
+      BK.hi = pr.w;
+      const double g = g64_sample(BA.node + sb, nbc, BK, o_E, o_J, o_c0, o_c1, jj);
+      if (g > 0.0)
+        atomicMax(&s_gmax[wbase + own], (unsigned long long)__double_as_longlong(g));
+    }
+  }
+  __syncwarp();
+  if (p < n) Fx[p] = 1.2 * __longlong_as_double((long long)s_gmax[threadIdx.x]);
+  // FP64 evaluations: one atomic per segment present in the warp
+  const unsigned am = __ballot_sync(0xFFFFFFFFu, p < n);
+  if (p < n) {
+    const unsigned peers = __match_any_sync(am, c);
+    const unsigned tot = __reduce_add_sync(peers, cnt);
+    if (lane == __ffs(peers) - 1) stat_add(S.stats, c, kStEnvelope64, tot);
+  }
 }
 
 // Result of the FP32 sampler in a star's key slot: bits 0-29 the trial
@@ -1309,7 +1378,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
           double rs, ph, Q, vtn;
           if (kPrec == 2) {
             point64_div(BA.node + sb, nbc, s, c0, c1, sv, guess, rs, ph, Q);
-            vtn = div_rn(s.J, rs);
+            vtn = div_rn_nl(s.J, rs);
           } else {
             double xs;
             point64(BA.node + sb, nbc, s, c0, c1, sv, guess, rs, xs, ph, vtn, Q);
@@ -1471,7 +1540,8 @@ __global__ void k_grid_shells(Seg S, const int64_t* esc, bool sub, const double*
   int* sh = gshell + B.goff[c];
   const int64_t hi = grid_last_cell(__ldg(x + p), pr);
   const int64_t lo = k + 1 < nb ? grid_last_cell(__ldg(x + p + 1), pr) + 1 : 0;
-  for (int64_t g = lo; g <= hi; ++g) sh[g] = (int)k;
+  for (int64_t g = lo; g <= hi; ++g)
+    if (CMC_IN(g, pr.z)) sh[g] = (int)k;
   if (k == 0)
     for (int64_t g = hi + 1; g < pr.z; ++g) sh[g] = -1;
 }
@@ -1558,7 +1628,8 @@ __global__ void k_bucket_build(Seg S, const int64_t* esc, bool sub, const float2
   const long long bk = (long long)((base - __float_as_uint(t32[p].x)) >> sh);
   const long long bp =
       k == pr.z ? -1ll : (long long)((base - __float_as_uint(t32[p - 1].x)) >> sh);
-  for (long long b = bp + 1; b <= bk && b < nbk; ++b) st[b] = (int)k;
+  for (long long b = bp + 1; b <= bk && b < nbk; ++b)
+    if (CMC_IN(b, B.off[c + 1] - B.off[c])) st[b] = (int)k;
   if (k == pr.w)
     for (long long b = bk + 1; b <= nbk; ++b) st[b] = (int)nb;
 }
@@ -1725,5 +1796,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
 #undef CMC_TURN
 #undef CMC_ORBIT
 }
+
+CMC_DEBUG_SITE_ACCESSOR
 
 }  // namespace cmc

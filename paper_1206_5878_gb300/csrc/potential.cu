@@ -719,6 +719,28 @@ __global__ void __launch_bounds__(256) k_step_end(Seg S, int64_t* esc, uint64_t*
   }
 }
 
+// one record of the diagnostics ring per segment, after the step end (the
+// step counter already advanced): slot (step - 1) mod cap
+__global__ void k_diag_ring(Seg S, const double* out3, const uint64_t* dt_last,
+                            const double* esc_me, const uint32_t* step, const uint32_t* err,
+                            double* ring, int cap) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= S.n_seg) return;
+  const uint32_t stp = *step;
+  double* rec = ring + ((size_t)c * cap + (stp - 1u) % (uint32_t)cap) * kDiagFields;
+  const double K = out3[3 * c], W = out3[3 * c + 1];
+  rec[0] = (double)stp;
+  rec[1] = __longlong_as_double((long long)dt_last[c]);
+  rec[2] = (double)S.nb[c];
+  rec[3] = K;
+  rec[4] = W;
+  rec[5] = (K + W) + esc_me[2 * c + 1];
+  rec[6] = esc_me[2 * c];
+  rec[7] = esc_me[2 * c + 1];
+  rec[8] = (double)S.stats[(size_t)c * kStStride + kStTrials];
+  rec[9] = (double)*err;
+}
+
 __global__ void k_nb_from_keys(Seg S, const uint64_t* keys) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= S.n_seg) return;
@@ -929,6 +951,13 @@ void launch_energy(const SegLayout& L, const double* r, const double* vr, const 
   k_energy_final<<<(unsigned)L.n_seg, kThreads, 0, st>>>(S, tile_k, tile_w, out3);
 }
 
+void launch_diag_ring(const SegLayout& L, const double* out3, const uint32_t* step,
+                      const uint32_t* err, double* ring, int cap, cudaStream_t st) {
+  if (!L.n_seg || cap <= 0) return;
+  k_diag_ring<<<(unsigned)((L.n_seg + 127) / 128), 128, 0, st>>>(L.dev(), out3, L.dt_last,
+                                                                L.esc_me, step, err, ring, cap);
+}
+
 void launch_core(const SegLayout& L, const double* r, const double* m, double* tiles4,
                  double* out3, cudaStream_t st) {
   if (!L.n_tiles) return;
@@ -975,5 +1004,7 @@ void launch_step_end(const SegLayout& L, uint32_t* step, const double* r_old, co
   k_step_end<<<L.n_seg, 256, 0, st>>>(L.dev(), L.esc_step, L.dt_last, step, r_old, c, m,
                                       L.esc_me);
 }
+
+CMC_DEBUG_SITE_ACCESSOR
 
 }  // namespace cmc

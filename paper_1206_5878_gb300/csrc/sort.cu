@@ -511,4 +511,6 @@ void launch_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out,
   k_philox<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, ctr, seed, out);
 }
 
+CMC_DEBUG_SITE_ACCESSOR
+
 }  // namespace cmc

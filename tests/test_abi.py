@@ -62,3 +62,15 @@ def test_init_rejects_bad_arguments_without_a_gpu(libpath):
                       None)
     assert st == _native.CMC_EINVAL and not ctx.value
     assert b"bad arguments" in lib.cmc_last_error(None)
+
+
+def test_release_build_has_no_debug_checks(libpath):
+    """The release library reports no failed device index checks (its
+    checks are compiled out); the debug build is a separate library."""
+    from paper_1206_5878_gb300 import _build, _native
+    lib = _native.load()
+    assert lib.cmc_is_debug_build() == 0
+    site = ctypes.c_uint32(7)
+    assert lib.cmc_debug_check(ctypes.byref(site)) == 0 and site.value == 0
+    assert lib.cmc_debug_check(None) == _native.CMC_EINVAL
+    assert _build.LIB_DEBUG != _build.LIB
