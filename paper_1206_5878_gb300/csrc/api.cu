@@ -18,6 +18,8 @@ struct cmc_ctx {
   cmc_config cfg{};
   cudaStream_t stream = nullptr;      // caller's stream (may be the default)
   cudaStream_t cap = nullptr;         // private stream used to capture the graph
+                                      // (and as a second stream by load_state)
+  cudaEvent_t ev_rim = nullptr, ev_aux = nullptr;  // load_state's ordering
   int device = 0;
   SegLayout L;
   SortWork W;
@@ -148,30 +150,29 @@ bool staged_in_order(cmc_ctx* c, std::vector<unsigned long long>& bitoff, cudaSt
 // already in order (a state read back and set again) keep their places: the
 // order was checked, the ids are checked with a bitmap, and both sorts and
 // the gather are skipped.
-void order_state(cmc_ctx* c, cudaStream_t st) {
+// Stars already in (r, id) order: the ids checked with a bitmap, the keys
+// and 1/r written in place (r and id only: no sort, no gather).  False when
+// the bitmap's scratch could not be had.
+bool order_in_place(cmc_ctx* c, const std::vector<unsigned long long>& bitoff,
+                    cudaStream_t st) {
   const SegLayout& L = c->L;
-  std::vector<unsigned long long> bitoff;
   unsigned long long* dbo = nullptr;
-  if (L.n > 0 && staged_in_order(c, bitoff, st) && !dalloc(dbo, bitoff.size(), st)) {
-    cudaMemcpyAsync(dbo, bitoff.data(), sizeof(unsigned long long) * bitoff.size(),
-                    cudaMemcpyHostToDevice, st);
-    // the bitmap lives in the key scratch (64 bits per star)
-    cudaMemsetAsync(c->keys, 0, sizeof(uint64_t) * (size_t)L.n, st);
-    launch_ids_bitmap(L, c->id, dbo, reinterpret_cast<unsigned long long*>(c->keys), c->err, st);
-    launch_make_keys(L, c->r, c->vr, c->vt, c->m, c->id, c->keys, nullptr, st);
-    launch_recip(L.n, c->r, c->x, st);
-    cudaStreamSynchronize(st);  // bitoff lives on this stack frame
-    dfree(dbo, st);
-  } else {
-    launch_id_keys(L, c->id, c->keys, st);
-    sort_segments(L, c->W, c->keys, c->vals, 0, 4, true, c->err, st);
-    launch_check_ids(L, c->keys, c->err, st);
-    launch_rekey_radius(L, c->vals, c->r, c->id, c->keys, st);
-    sort_segments(L, c->W, c->keys, c->vals, 0, 8, false, c->err, st);
-    launch_make_keys(L, c->r, c->vr, c->vt, c->m, c->id, c->W.keys_alt, c->pay, st);
-    launch_gather(L, c->keys, c->vals, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, nullptr,
-                  nullptr, st);
-  }
+  if (dalloc(dbo, bitoff.size(), st)) return false;
+  cudaMemcpyAsync(dbo, bitoff.data(), sizeof(unsigned long long) * bitoff.size(),
+                  cudaMemcpyHostToDevice, st);
+  // the bitmap lives in the key scratch (64 bits per star)
+  cudaMemsetAsync(c->keys, 0, sizeof(uint64_t) * (size_t)L.n, st);
+  launch_ids_bitmap(L, c->id, dbo, reinterpret_cast<unsigned long long*>(c->keys), c->err, st);
+  launch_make_keys(L, c->r, nullptr, nullptr, nullptr, c->id, c->keys, nullptr, st);
+  launch_recip(L.n, c->r, c->x, st);
+  cudaStreamSynchronize(st);  // bitoff lives on the caller's stack frame
+  dfree(dbo, st);
+  return true;
+}
+
+// N_bound from the keys, then the potential and the orbit step's tables
+void finish_order(cmc_ctx* c, cudaStream_t st) {
+  const SegLayout& L = c->L;
   launch_nb_from_keys(L, c->keys, st);
   cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
   // the float tables, node records and indexes of the sampled orbit step
@@ -184,6 +185,22 @@ void order_state(cmc_ctx* c, cudaStream_t st) {
     launch_buckets(L, c->t32, false, c->bk, st);
     launch_grid(L, c->x, c->phi, c->Mbuf, false, c->bk, st);
   }
+}
+
+void order_state(cmc_ctx* c, cudaStream_t st) {
+  const SegLayout& L = c->L;
+  std::vector<unsigned long long> bitoff;
+  if (!(L.n > 0 && staged_in_order(c, bitoff, st) && order_in_place(c, bitoff, st))) {
+    launch_id_keys(L, c->id, c->keys, st);
+    sort_segments(L, c->W, c->keys, c->vals, 0, 4, true, c->err, st);
+    launch_check_ids(L, c->keys, c->err, st);
+    launch_rekey_radius(L, c->vals, c->r, c->id, c->keys, st);
+    sort_segments(L, c->W, c->keys, c->vals, 0, 8, false, c->err, st);
+    launch_make_keys(L, c->r, c->vr, c->vt, c->m, c->id, c->W.keys_alt, c->pay, st);
+    launch_gather(L, c->keys, c->vals, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, nullptr,
+                  nullptr, st);
+  }
+  finish_order(c, st);
 }
 
 // stage names (cmc_step_profiled, NVTX ranges)
@@ -301,42 +318,55 @@ void free_ctx(cmc_ctx* c) {
   free_layout(c->L, st);
   cudaStreamSynchronize(st);
   if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->ev_rim) cudaEventDestroy(c->ev_rim);
+  if (c->ev_aux) cudaEventDestroy(c->ev_aux);
   delete c;
 }
 
-cmc_status copy_in(cmc_ctx* c, const double* r, const double* vr, const double* vt,
-                   const double* m, const uint32_t* id, int32_t ptr_kind) {
-  const size_t n = (size_t)c->L.n;
-  cudaMemcpyKind k = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
-  cudaStream_t st = c->stream;
-  cudaError_t e = cudaSuccess;
-  if (!e) e = cudaMemcpyAsync(c->r, r, n * sizeof(double), k, st);
-  if (!e) e = cudaMemcpyAsync(c->vr, vr, n * sizeof(double), k, st);
-  if (!e) e = cudaMemcpyAsync(c->vt, vt, n * sizeof(double), k, st);
-  if (!e) e = cudaMemcpyAsync(c->m, m, n * sizeof(double), k, st);
-  if (!e) e = cudaMemcpyAsync(c->id, id, n * sizeof(uint32_t), k, st);
-  if (e) return cuda_fail(c, e, "copy in");
-  return CMC_OK;
-}
-
+// A state set from outside.  r, id and m are copied first: the order check,
+// N_bound, the potential and its tables need only them, so on the second
+// stream they run while v_r and v_t are still arriving (from host memory
+// the copies are the longer part).  A state in (r, id) order keeps its
+// places; validation (every array) follows once all have landed.  A state
+// out of order is validated first (the sort needs finite keys), then
+// sorted.
 cmc_status load_state(cmc_ctx* c, const double* r, const double* vr, const double* vt,
                       const double* m, const uint32_t* id, int32_t ptr_kind, bool allow_inf,
                       int64_t step) {
-  cmc_status s = copy_in(c, r, vr, vt, m, id, ptr_kind);
-  if (s != CMC_OK) return s;
-  cudaStream_t st = c->stream;
+  const SegLayout& L = c->L;
+  const size_t n = (size_t)L.n;
+  const cudaMemcpyKind k = ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  cudaStream_t st = c->stream, aux = c->cap;
   cudaMemsetAsync(c->err, 0, sizeof(uint32_t), st);
   uint32_t st32 = (uint32_t)step;
-  cudaMemcpyAsync(c->step, &st32, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
-  launch_validate(c->L, c->r, c->vr, c->vt, c->m, allow_inf, c->err, st);
-  // a state that fails validation is not ordered (the sort needs finite keys)
-  s = check_err_flags(c);
-  if (s != CMC_OK) return s;
-  order_state(c, st);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaMemcpyAsync(c->step, &st32, sizeof(uint32_t), cudaMemcpyHostToDevice, st);
+  if (!e) e = cudaMemcpyAsync(c->r, r, n * sizeof(double), k, st);
+  if (!e) e = cudaMemcpyAsync(c->id, id, n * sizeof(uint32_t), k, st);
+  if (!e) e = cudaMemcpyAsync(c->m, m, n * sizeof(double), k, st);
+  if (!e) e = cudaEventRecord(c->ev_rim, st);
+  if (!e) e = cudaMemcpyAsync(c->vr, vr, n * sizeof(double), k, st);
+  if (!e) e = cudaMemcpyAsync(c->vt, vt, n * sizeof(double), k, st);
+  if (!e) e = cudaStreamWaitEvent(aux, c->ev_rim, 0);
+  if (e) return cuda_fail(c, e, "copy in");
+  std::vector<unsigned long long> bitoff;
+  bool placed = false;
+  if (L.n > 0 && staged_in_order(c, bitoff, aux) && order_in_place(c, bitoff, aux)) {
+    finish_order(c, aux);
+    placed = true;
+  }
+  e = cudaEventRecord(c->ev_aux, aux);
+  if (!e) e = cudaStreamWaitEvent(st, c->ev_aux, 0);
   if (e) return cuda_fail(c, e, "ordering the state");
-  s = check_err_flags(c);
+  launch_validate(c->L, c->r, c->vr, c->vt, c->m, allow_inf, c->err, st);
+  cmc_status s = check_err_flags(c);
   if (s != CMC_OK) return s;
+  if (!placed) {
+    order_state(c, st);
+    e = cudaGetLastError();
+    if (e) return cuda_fail(c, e, "ordering the state");
+    s = check_err_flags(c);
+    if (s != CMC_OK) return s;
+  }
   c->steps_taken = step;
   return CMC_OK;
 }
@@ -617,6 +647,8 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   c->pref = t_rel_prefactor(cfg.theta_max);
   cudaGetDevice(&c->device);
   cudaError_t e = cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking);
+  if (!e) e = cudaEventCreateWithFlags(&c->ev_rim, cudaEventDisableTiming);
+  if (!e) e = cudaEventCreateWithFlags(&c->ev_aux, cudaEventDisableTiming);
   if (e) { cmc_status s = cuda_fail(nullptr, e, "cmc_init"); free_ctx(c); return s; }
   cudaStream_t st = c->stream;
   e = alloc_layout(c->L, sizes, sd, lnL, cfg.bin_size, st);
