@@ -30,7 +30,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "star-updates/s per timestep at N=1e7 (1 GB300) + HBM roofline %, mixed vs FP64"
 UNIT = "star-updates/s"
-PROFILE = os.path.join(ROOT, "profiles", "step_kernels_N1e7_mixed.md")
+# the step profiles (ncu launch lists at N = 1e7) the roofline's traffic comes from
+PROFILES = [os.path.join(ROOT, "profiles", "step_kernels_N1e7_%s.md" % p)
+            for p in ("mixed", "fp64")]
 
 
 def log(*a):
@@ -118,18 +120,19 @@ def kernel_source_hash() -> str:
 def profiled_traffic_per_star(kernel: str, precision: str):
     """DRAM bytes per star of one kernel launch from the committed ncu
     summary, or None when a kernel source changed since it was taken."""
-    if not os.path.exists(PROFILE):
-        return None
-    src, val = None, None
-    with open(PROFILE) as f:
-        for line in f:
-            if line.startswith("source_hash:"):
-                src = line.split(":", 1)[1].strip()
-            if line.startswith("dram_bytes_per_star_%s_%s:" % (kernel, precision)):
-                val = float(line.split(":", 1)[1])
-    if src != kernel_source_hash():
-        return None
-    return val
+    for path in PROFILES:
+        if not os.path.exists(path):
+            continue
+        src, val = None, None
+        with open(path) as f:
+            for line in f:
+                if line.startswith("source_hash:"):
+                    src = line.split(":", 1)[1].strip()
+                if line.startswith("dram_bytes_per_star_%s_%s:" % (kernel, precision)):
+                    val = float(line.split(":", 1)[1])
+        if val is not None:
+            return val if src == kernel_source_hash() else None
+    return None
 
 
 # Compulsory HBM bytes per star of each stage's kernels (table probes and
