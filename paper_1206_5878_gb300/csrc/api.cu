@@ -177,14 +177,12 @@ void finish_order(cmc_ctx* c, cudaStream_t st) {
   cudaMemsetAsync(L.esc_step, 0, sizeof(int64_t) * L.n_seg, st);
   // the float tables, node records and indexes of the sampled orbit step
   // (precision 0 and 1)
-  const bool tab = c->cfg.precision != 2;
-  launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32,
-                   tab ? c->Mbuf : nullptr, false, st, tab ? c->bk.node : nullptr,
-                   tab ? c->bk.tdf : nullptr, false, true);
-  if (tab) {
-    launch_buckets(L, c->t32, false, c->bk, st);
-    launch_grid(L, c->x, c->phi, c->Mbuf, false, c->bk, st);
-  }
+  if (c->cfg.precision != 2)
+    launch_potential_tables(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32, c->Mbuf,
+                            false, false, c->bk, st);
+  else
+    launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, nullptr, nullptr, false,
+                     st);
 }
 
 void order_state(cmc_ctx* c, cudaStream_t st) {
@@ -253,13 +251,12 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   // the tables carry the shell slopes of the FP64 orbit step (not the
   // scan's enclosed masses): the sampled step's turning points and points
   // are then FP64 mode's
-  launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi,
-                   tab ? c->t32 : nullptr, tab ? c->Mbuf : nullptr, true, st,
-                   tab ? c->bk.node : nullptr, tab ? c->bk.tdf : nullptr, true, true);
-  if (tab) {
-    launch_buckets(L, c->t32, true, c->bk, st);
-    launch_grid(L, c->x, c->phi, c->Mbuf, true, c->bk, st);
-  }
+  if (tab)
+    launch_potential_tables(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, c->t32, c->Mbuf,
+                            true, true, c->bk, st);
+  else
+    launch_potential(L, c->r, c->x, c->m, c->tile_a, c->tile_b, c->phi, nullptr, nullptr, true,
+                     st, nullptr, nullptr, true);
   mark(7);
   if (c->cfg.energy_correction) {
     if (mixed)
@@ -281,13 +278,13 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
 }
 
 int count_step_kernels(const cmc_ctx* c) {
-  // bins, relax, orbit, upsweep, hist scan, 5 passes, tie fix, gather with
+  // bins, relax, orbit, upsweep (with the histograms' scans), 5 passes, tie fix, gather with
   // the tile sums, potential, [precision 0 and 1: turning points, FP32
-  // sampler, FP64 continuation, slopes at the tile seams, 2 bucket-index + 3
-  // grid kernels; precision 0: the envelope], [correction], step end
+  // sampler, FP64 continuation, the tables' parameters, the grid's values
+  // with the seams' slopes; precision 0: the envelope], [correction], step end
   const int p = c->cfg.precision;
-  return 3 + (c->R ? 1 : 0) + (c->ring ? 4 : 0) + 2 + 5 + 1 + 1 + 1 +
-         (p == 1 ? 9 : p == 0 ? 10 : 0) +
+  return 3 + (c->R ? 1 : 0) + (c->ring ? 4 : 0) + 1 + 5 + 1 + 1 + 1 +
+         (p == 1 ? 5 : p == 0 ? 6 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 

@@ -621,4 +621,49 @@ __device__ __forceinline__ void clamp_energy_add(unsigned long long* st, int seg
   if (e > 0.0) stat_add(st, seg, kStClampEnergy, __double2ull_rn(e));
 }
 
+// ------------------------------------------- the orbit step's index tables
+// Both are written star by star, in one pass over the sorted stars (by the
+// potential kernel, or by stand-alone kernels for a given potential).
+// Bucket index of a segment (prm: shift, bucket count, first and last
+// indexed node; base: float key bits of 1/r at the first indexed node):
+// star k writes start[b] = k for the buckets from its predecessor's bucket
+// (exclusive) to its own; the last indexed star closes the table with nb.
+// key_k, key_km1: float bits of 1/r of stars k and k - 1.
+__device__ __forceinline__ void bucket_starts_of(int64_t k, int64_t nb, int4 prm, uint32_t base,
+                                                 uint32_t key_k, uint32_t key_km1, int* st,
+                                                 int64_t cap) {
+  if (k < prm.z || k > prm.w) return;
+  const int sh = prm.x, nbk = prm.y;
+  const long long bk = (long long)((base - key_k) >> sh);
+  const long long bp = k == prm.z ? -1ll : (long long)((base - key_km1) >> sh);
+  for (long long b = bp + 1; b <= bk && b < nbk; ++b)
+    if (CMC_IN(b, cap)) st[b] = (int)k;
+  if (k == prm.w)
+    for (long long b = bk + 1; b <= nbk; ++b) st[b] = (int)nb;
+}
+
+// The potential grid's key shells (pr: key0, sh, cells): star k owns the
+// keys in (1/r_{k+1}, 1/r_k], i.e. the cells from gmax(k + 1) + 1 to
+// gmax(k), gmax(k) = the last cell whose key is <= 1/r_k.  A key (a
+// positive float) is <= 1/r_k exactly when its bits are <= those of 1/r_k
+// rounded down to a float.  The outermost star also owns the cells below
+// it, the innermost one the cells above it (shell -1).
+__device__ __forceinline__ int64_t grid_last_cell(double xk, int4 pr) {
+  const uint32_t kb = __float_as_uint(__double2float_rd(xk));
+  if (kb < (uint32_t)pr.x) return -1;
+  const int64_t g = (int64_t)((kb - (uint32_t)pr.x) >> pr.y);
+  return g < pr.z - 1 ? g : (int64_t)pr.z - 1;
+}
+
+__device__ __forceinline__ void grid_shells_of(int64_t k, int64_t nb, double xk, double xk1,
+                                               int4 pr, int* sh) {
+  if (pr.z <= 0) return;
+  const int64_t hi = grid_last_cell(xk, pr);
+  const int64_t lo = k + 1 < nb ? grid_last_cell(xk1, pr) + 1 : 0;
+  for (int64_t g = lo; g <= hi; ++g)
+    if (CMC_IN(g, pr.z)) sh[g] = (int)k;
+  if (k == 0)
+    for (int64_t g = hi + 1; g < pr.z; ++g) sh[g] = -1;
+}
+
 }  // namespace cmc

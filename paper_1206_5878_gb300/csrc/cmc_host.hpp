@@ -59,6 +59,7 @@ struct SortWork {
   unsigned long long* desc = nullptr;   // [passes][n_tiles][256] look-back words
   uint32_t* hist = nullptr;             // [n_seg][passes][256]
   uint32_t* tickets = nullptr;          // [passes]
+  uint32_t* done = nullptr;             // [n_seg] upsweep blocks finished
   size_t zero_bytes = 0;                // desc + hist + tickets, zeroed per sort
   void* zero_base = nullptr;
   int max_passes = 0;
@@ -141,10 +142,23 @@ void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* val
 // kernels that read a few nodes at random).  slopes: Mout and the records
 // carry the slope of Eq. 6 across each shell instead of M_k (the shell
 // parameter the FP64 orbit step takes).
+// The orbit step's index tables as the potential kernel writes them beside
+// Phi: the bucket starts and the grid's key shells (their per-segment
+// parameters computed before it, from 1/r).
+struct TableOut {
+  int* start = nullptr;
+  const int64_t* boff = nullptr;
+  const uint32_t* base = nullptr;
+  const int4* prm = nullptr;
+  int* gshell = nullptr;
+  const int64_t* goff = nullptr;
+  const int4* gprm = nullptr;
+};
 void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
                       double* tile_m, double* tile_mx, double* phi, float2* t32,
                       double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node = nullptr,
-                      float4* tdf = nullptr, bool sums_ready = false, bool slopes = false);
+                      float4* tdf = nullptr, bool sums_ready = false, bool slopes = false,
+                      const TableOut* tables = nullptr);
 // node records (and float-pair table) from the arrays (stage calls)
 void launch_make_nodes(int64_t n, const double* r, const double* x, const double* phi,
                        const double* M, double4_32a* node, float4* tdf, cudaStream_t st);
@@ -226,6 +240,15 @@ void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWo
 // build the potential grid from the FP64 table (x, Phi, enclosed masses)
 void launch_grid(const SegLayout& L, const double* x, const double* phi, const double* Menc,
                  bool nb_sub, BucketWork& B, cudaStream_t st);
+// The potential with the orbit step's tables in three kernels: the
+// segments' bucket and grid parameters (from 1/r), the potential writing Phi,
+// the slopes, node records, float tables, bucket starts and grid key shells,
+// then the grid's values with the slopes at the tile seams.  The same tables
+// as launch_potential + launch_buckets + launch_grid (slopes mode).
+void launch_potential_tables(const SegLayout& L, const double* r, const double* x,
+                             const double* m, double* tile_m, double* tile_mx, double* phi,
+                             float2* t32, double* Menc, bool nb_sub, bool sums_ready,
+                             BucketWork& B, cudaStream_t st);
 
 // Menc (precision 0 and 1): the slope of Phi in 1/r across shell k.
 // precision 1 (mixed): launch_orbit runs four kernels (turning points,

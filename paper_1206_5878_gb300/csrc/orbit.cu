@@ -1512,20 +1512,7 @@ __global__ void k_grid_params(Seg S, const int64_t* esc, bool sub, const double*
 }
 
 // The shell of every grid key, largest i with 1/r_i >= key (-1 when none),
-// written by the stars: star k owns the keys in (1/r_{k+1}, 1/r_k], i.e. the
-// cells from gmax(k + 1) + 1 to gmax(k), gmax(k) = the last cell whose key
-// is <= 1/r_k.  A key (a positive float) is <= 1/r_k exactly when its bits
-// are <= those of 1/r_k rounded down to a float, so gmax is integer
-// arithmetic on those bits.  The outermost star also owns the cells below
-// it, the innermost one the cells above it (shell -1).  Every cell is
-// written once; the work is one pass over the stars and the cells.
-__device__ __forceinline__ int64_t grid_last_cell(double xk, int4 pr) {
-  const uint32_t kb = __float_as_uint(__double2float_rd(xk));
-  if (kb < (uint32_t)pr.x) return -1;
-  const int64_t g = (int64_t)((kb - (uint32_t)pr.x) >> pr.y);
-  return g < pr.z - 1 ? g : (int64_t)pr.z - 1;
-}
-
+// written by the stars (grid_shells_of) in one pass over stars and cells.
 __global__ void k_grid_shells(Seg S, const int64_t* esc, bool sub, const double* x,
                               BucketArgs B, int* gshell, int64_t n) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1535,37 +1522,60 @@ __global__ void k_grid_shells(Seg S, const int64_t* esc, bool sub, const double*
   if (sub) nb -= esc[c];
   const int64_t sb = S.off[c], k = p - sb;
   if (k >= nb) return;
-  const int4 pr = B.gprm[c];
-  if (pr.z <= 0) return;
-  int* sh = gshell + B.goff[c];
-  const int64_t hi = grid_last_cell(__ldg(x + p), pr);
-  const int64_t lo = k + 1 < nb ? grid_last_cell(__ldg(x + p + 1), pr) + 1 : 0;
-  for (int64_t g = lo; g <= hi; ++g)
-    if (CMC_IN(g, pr.z)) sh[g] = (int)k;
-  if (k == 0)
-    for (int64_t g = hi + 1; g < pr.z; ++g) sh[g] = -1;
+  grid_shells_of(k, nb, __ldg(x + p), k + 1 < nb ? __ldg(x + p + 1) : 0.0, B.gprm[c],
+                 gshell + B.goff[c]);
 }
 
 // Phi at every grid key from the FP64 table: Phi = Phi_i + M_i (1/r_i - 1/r)
 // in the key's shell i (Eq. 6 with the enclosed-mass slope), Phi_0 inside
 // the first star, rounded to float
+// fused (launch_potential_tables): the slopes at the tile seams, which the
+// potential kernel leaves, are computed here by n_tiles more threads (and
+// locally where a cell needs one), and each segment's cell 0 fills Phi_0 and
+// the bound mass into gaux
 __global__ void k_grid_build(Seg S, const int64_t* esc, bool sub, const double* x,
-                             const double* phi, const double* Menc, BucketArgs B,
-                             const int* gshell, float* gphi, float4* gaux, int64_t total) {
+                             const double* phi, double* Menc, BucketArgs B,
+                             const int* gshell, float* gphi, float4* gaux, int64_t total,
+                             bool fused, const double* r, double4_32a* node, int64_t n_tiles) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned am = __ballot_sync(0xFFFFFFFFu, p < total);
-  if (p >= total) return;
+  if (p >= total) {
+    const int64_t t = p - total;
+    if (!fused || t >= n_tiles) return;
+    const int cs = seg_find(S.tile_off, S.n_seg, t);
+    const int64_t sbs = S.off[cs], nbs = S.nb[cs] - (sub ? esc[cs] : 0);
+    const int64_t k = (t - S.tile_off[cs]) * kTile + kTile - 1;  // the tile's last star
+    if (k + 1 >= nbs) return;
+    const int64_t q = sbs + k;
+    const double xj = x[q], pj = phi[q];
+    const double w = div_rn(phi[q + 1] - pj, xj - x[q + 1]);
+    Menc[q] = w;
+    node[q] = make_double4_32a(r[q], xj, pj, w);
+    return;
+  }
   const int c = seg_find(B.goff, S.n_seg, p);
   const int4 pr = B.gprm[c];
   const int g = (int)(p - B.goff[c]);
+  const int64_t sb = S.off[c];
+  const int64_t nb = S.nb[c] - (sub ? esc[c] : 0);
+  // shell i's slope (a seam's computed as the seam threads do)
+  auto slope = [&](int64_t i) {
+    if (fused && i % kTile == kTile - 1 && i + 1 < nb)
+      return div_rn(__ldg(phi + sb + i + 1) - __ldg(phi + sb + i),
+                    __ldg(x + sb + i) - __ldg(x + sb + i + 1));
+    return __ldg(Menc + sb + i);
+  };
   float rel = 0.0f;
   if (g < pr.z) {
-    const int64_t sb = S.off[c];
+    if (fused && g == 0) {
+      gaux[c].x = (float)__ldg(phi + sb);
+      gaux[c].y = (float)__ldg(Menc + sb + nb - 1);
+    }
     const double xg = (double)__uint_as_float((uint32_t)pr.x + ((uint32_t)g << pr.y));
     const double xn = (double)__uint_as_float((uint32_t)pr.x + ((uint32_t)(g + 1) << pr.y));
     const int64_t lo = gshell[p];
     const double ph = lo < 0 ? __ldg(phi + sb)
-                             : __ldg(phi + sb + lo) + __ldg(Menc + sb + lo) * (__ldg(x + sb + lo) - xg);
+                             : __ldg(phi + sb + lo) + slope(lo) * (__ldg(x + sb + lo) - xg);
     gphi[p] = (float)ph;
     // Phi is convex in 1/r (its slope -M(1/r) rises with 1/r), so inside the
     // cell [xg, xn] it lies below the chord by at most (xn - xg) dM / 4, dM
@@ -1574,8 +1584,8 @@ __global__ void k_grid_build(Seg S, const int64_t* esc, bool sub, const double* 
     // grid's interpolation error (gaux.w; floats >= 0 order as their bits)
     if (g + 1 < pr.z && ph < 0.0) {
       const int64_t lo2 = gshell[p + 1];
-      const double Ma = lo < 0 ? 0.0 : __ldg(Menc + sb + lo);
-      const double Mb = lo2 < 0 ? 0.0 : __ldg(Menc + sb + lo2);
+      const double Ma = lo < 0 ? 0.0 : slope(lo);
+      const double Mb = lo2 < 0 ? 0.0 : slope(lo2);
       const double dM = Ma - Mb;
       rel = (float)(((xn - xg) * (dM > 0.0 ? dM : 0.0) * 0.25) / -ph);
     }
@@ -1585,6 +1595,49 @@ __global__ void k_grid_build(Seg S, const int64_t* esc, bool sub, const double* 
   const unsigned mx = __reduce_max_sync(grp, __float_as_uint(rel));
   if ((threadIdx.x & 31) == (unsigned)(__ffs(grp) - 1) && mx)
     atomicMax(reinterpret_cast<unsigned int*>(&gaux[c].w), mx);
+}
+
+// Both tables' per-segment parameters from 1/r alone (before the potential
+// kernel writes the tables): as k_bucket_params (its float keys are the
+// floats nearest 1/r, as t32 holds them) and k_grid_params, with Phi_0 and
+// the bound mass left to k_grid_build (fused)
+__global__ void k_table_params(Seg S, const int64_t* esc, bool sub, const double* x,
+                               const int64_t* boff, uint32_t* base, int4* prm,
+                               const int64_t* goff, int4* gprm, float4* gaux) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= S.n_seg) return;
+  int64_t nb = S.nb[c];
+  if (sub) nb -= esc[c];
+  if (nb <= 0) {
+    base[c] = 0;
+    prm[c] = make_int4(0, 0, 0, -1);
+    gprm[c] = make_int4(0, 0, 0, 0);
+    gaux[c] = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const int64_t sb = S.off[c];
+  // buckets
+  const int tail = nb >= 4096 ? (int)(nb >> 10) : 0;
+  const int lo = tail, hi = (int)nb - 1 - tail;
+  const uint32_t b0 = __float_as_uint(f32_rn(x[sb + lo]));
+  const uint32_t b1 = __float_as_uint(f32_rn(x[sb + hi]));
+  const uint32_t span = b0 >= b1 ? b0 - b1 : 0u;
+  const int64_t bcap = boff[c + 1] - boff[c] - 1;
+  int bs = 0;
+  while ((int64_t)(span >> bs) + 1 > bcap) ++bs;
+  base[c] = b0;
+  prm[c] = make_int4(bs, (int)((span >> bs) + 1), lo, hi);
+  // grid
+  const uint32_t klo = __float_as_uint((float)x[sb + nb - 1]);
+  const uint32_t khi = __float_as_uint((float)x[sb]);
+  const int64_t gcap = goff[c + 1] - goff[c];
+  int gp = 10;
+  while (gp > 0 && (int64_t)((khi >> (23 - gp)) - (klo >> (23 - gp))) + 2 > gcap) --gp;
+  const int sh = 23 - gp;
+  const uint32_t key0 = (klo >> sh) << sh;
+  const int cells = (int)((khi - key0) >> sh) + 2;
+  gprm[c] = make_int4((int)key0, sh, cells, (int)khi);
+  gaux[c] = make_float4(0.f, 0.f, __uint_as_float(key0), 0.f);
 }
 
 // per segment: the indexed node range lo..hi, base = bits(x_lo), the
@@ -1620,18 +1673,11 @@ __global__ void k_bucket_build(Seg S, const int64_t* esc, bool sub, const float2
   int64_t nb = S.nb[c];
   if (sub) nb -= esc[c];
   const int4 pr = B.prm[c];
-  const int64_t sb = S.off[c], k = p - sb;
+  const int64_t k = p - S.off[c];
   if (k < pr.z || k > pr.w) return;
-  const uint32_t base = B.base[c];
-  const int sh = pr.x, nbk = pr.y;
-  int* st = start + B.off[c];
-  const long long bk = (long long)((base - __float_as_uint(t32[p].x)) >> sh);
-  const long long bp =
-      k == pr.z ? -1ll : (long long)((base - __float_as_uint(t32[p - 1].x)) >> sh);
-  for (long long b = bp + 1; b <= bk && b < nbk; ++b)
-    if (CMC_IN(b, B.off[c + 1] - B.off[c])) st[b] = (int)k;
-  if (k == pr.w)
-    for (long long b = bk + 1; b <= nbk; ++b) st[b] = (int)nb;
+  bucket_starts_of(k, nb, pr, B.base[c], __float_as_uint(t32[p].x),
+                   k == pr.z ? 0u : __float_as_uint(t32[p - 1].x), start + B.off[c],
+                   B.off[c + 1] - B.off[c]);
 }
 
 // slope of Phi in 1/r across each shell of one table, for callers that
@@ -1697,7 +1743,31 @@ void launch_grid(const SegLayout& L, const double* x, const double* phi, const d
   k_grid_shells<<<(unsigned)((L.n + 255) / 256), 256, 0, st>>>(L.dev(), L.esc_step, nb_sub, x,
                                                               B.args(), B.gshell, L.n);
   k_grid_build<<<(unsigned)((B.gcells + 255) / 256), 256, 0, st>>>(
-      L.dev(), L.esc_step, nb_sub, x, phi, Menc, B.args(), B.gshell, B.gphi, B.gaux, B.gcells);
+      L.dev(), L.esc_step, nb_sub, x, phi, const_cast<double*>(Menc), B.args(), B.gshell,
+      B.gphi, B.gaux, B.gcells, false, nullptr, nullptr, 0);
+}
+
+void launch_potential_tables(const SegLayout& L, const double* r, const double* x,
+                             const double* m, double* tile_m, double* tile_mx, double* phi,
+                             float2* t32, double* Menc, bool nb_sub, bool sums_ready,
+                             BucketWork& B, cudaStream_t st) {
+  if (!L.n) return;
+  k_table_params<<<(unsigned)((L.n_seg + 127) / 128), 128, 0, st>>>(
+      L.dev(), L.esc_step, nb_sub, x, B.off, B.base, B.prm, B.goff, B.gprm, B.gaux);
+  TableOut T;
+  T.start = B.start;
+  T.boff = B.off;
+  T.base = B.base;
+  T.prm = B.prm;
+  T.gshell = B.gshell;
+  T.goff = B.goff;
+  T.gprm = B.gprm;
+  launch_potential(L, r, x, m, tile_m, tile_mx, phi, t32, Menc, nb_sub, st, B.node, B.tdf,
+                   sums_ready, true, &T);
+  const int64_t threads = B.gcells + L.n_tiles;
+  k_grid_build<<<(unsigned)((threads + 255) / 256), 256, 0, st>>>(
+      L.dev(), L.esc_step, nb_sub, x, phi, Menc, B.args(), B.gshell, B.gphi, B.gaux, B.gcells,
+      true, r, B.node, L.n_tiles);
 }
 
 void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWork& B,

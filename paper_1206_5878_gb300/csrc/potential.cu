@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(Seg S, const int64_t*
                                                            const double* tile_mx, double* phi,
                                                            float2* t32, double* Mout,
                                                            double4_32a* node, float4* tdf,
-                                                           bool slopes) {
+                                                           bool slopes, TableOut T) {
   extern __shared__ double smem[];
   double* s_m = smem;               // m, then M_k
   double* s_x = smem + kPad8N;      // x
@@ -416,6 +416,22 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(Seg S, const int64_t*
     if (Mout) Mout[p] = w;
     if (node) node[p] = make_double4_32a(r[p], s_x[q], ph, w);
     if (tdf) tdf[p] = float_pairs(s_x[q], ph);
+    if (T.start && bound) {
+      // the orbit step's index tables, star by star: bucket starts (from the
+      // float keys of 1/r of this star and its predecessor, as t32 holds
+      // them) and the grid cells between 1/r of this star and the next
+      const int c = R.seg;
+      const int64_t k = p - R.seg_begin, nb = R.bound_end - R.seg_begin;
+      const int4 pr = T.prm[c];
+      if (k >= pr.z && k <= pr.w) {
+        const double xm1 = e > 0 ? s_x[pad8(e - 1)] : (k > 0 ? __ldg(x + p - 1) : 0.0);
+        bucket_starts_of(k, nb, pr, T.base[c], __float_as_uint(f32_pair(s_x[q]).hi),
+                         k > pr.z ? __float_as_uint(f32_pair(xm1).hi) : 0u,
+                         T.start + T.boff[c], T.boff[c + 1] - T.boff[c]);
+      }
+      const double xk1 = k + 1 < nb ? (e + 1 < kTile ? s_x[pad8(e + 1)] : __ldg(x + p + 1)) : 0.0;
+      grid_shells_of(k, nb, s_x[q], xk1, T.gprm[c], T.gshell + T.goff[c]);
+    }
   }
 }
 
@@ -916,15 +932,17 @@ void potential_prepare() {
 void launch_potential(const SegLayout& L, const double* r, const double* x, const double* m,
                       double* tile_m, double* tile_mx, double* phi, float2* t32,
                       double* Mout, bool nb_sub, cudaStream_t st, double4_32a* node,
-                      float4* tdf, bool sums_ready, bool slopes) {
+                      float4* tdf, bool sums_ready, bool slopes, const TableOut* tables) {
   if (!L.n_tiles) return;
   Seg S = L.dev();
   if (!sums_ready)
     k_tile_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(S, L.esc_step, nb_sub, x, m, tile_m,
                                                          tile_mx);
   k_potential<<<(unsigned)L.n_tiles, kPotThreads, kPotentialSmem, st>>>(
-      S, L.esc_step, nb_sub, r, x, m, tile_m, tile_mx, phi, t32, Mout, node, tdf, slopes);
-  if (slopes && node)
+      S, L.esc_step, nb_sub, r, x, m, tile_m, tile_mx, phi, t32, Mout, node, tdf, slopes,
+      tables ? *tables : TableOut());
+  // with the tables, the seams' slopes come with the grid's values
+  if (slopes && node && !tables)
     k_slope_seams<<<blocks_for(L.n_tiles, 128), 128, 0, st>>>(S, L.esc_step, nb_sub, r, x, phi,
                                                               Mout, node, L.n_tiles);
 }

@@ -98,11 +98,14 @@ __device__ __forceinline__ uint32_t block_excl_scan_u32(uint32_t v, uint32_t* s_
 // Per-segment histogram of every pass digit over tiles of kTile keys.  Each
 // warp counts into its own shared-memory histogram (collisions only among
 // its 32 lanes); the warps' histograms are summed before one global atomic
-// per bin.
+// per bin.  The last block of a segment to finish (a counter per segment,
+// no waiting) turns that segment's histograms into exclusive scans.
 __global__ void __launch_bounds__(kThreads) k_upsweep(const int64_t* off, const int64_t* tile_off,
                                                       int n_seg, const uint64_t* keys,
                                                       int first_pass, int passes,
-                                                      uint32_t* hist) {
+                                                      uint32_t* hist, uint32_t* done) {
+  __shared__ uint32_t s_warp[kWarps];
+  __shared__ bool s_last;
   extern __shared__ uint32_t h[];  // [kWarps][passes][kBins]
   const int warp = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kWarps * passes * kBins; i += kThreads) h[i] = 0;
@@ -120,15 +123,22 @@ __global__ void __launch_bounds__(kThreads) k_upsweep(const int64_t* off, const 
     for (int w = 0; w < kWarps; ++w) s += h[(size_t)w * passes * kBins + i];
     if (s) atomicAdd(&hist[((size_t)R.seg * passes) * kBins + i], s);
   }
-}
-
-// exclusive scan of each (segment, pass) histogram in place
-__global__ void __launch_bounds__(kThreads) k_hist_scan(uint32_t* hist) {
-  __shared__ uint32_t s_warp[kWarps];
-  uint32_t* h = hist + (size_t)blockIdx.x * kBins;
-  uint32_t v = h[threadIdx.x];
-  uint32_t e = block_excl_scan_u32(v, s_warp);
-  h[threadIdx.x] = e;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this block's counts before its arrival
+    const uint32_t tiles = (uint32_t)(tile_off[R.seg + 1] - tile_off[R.seg]);
+    s_last = atomicAdd(&done[R.seg], 1u) == tiles - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();  // every block's counts, read past L1
+  for (int q = 0; q < passes; ++q) {
+    uint32_t* hq = hist + ((size_t)R.seg * passes + q) * kBins;
+    const uint32_t v = __ldcg(hq + threadIdx.x);
+    const uint32_t e = block_excl_scan_u32(v, s_warp);
+    hq[threadIdx.x] = e;
+    __syncthreads();  // s_warp is read by the scan's last step
+  }
 }
 
 template <int IPT>
@@ -439,11 +449,13 @@ cudaError_t alloc_sort(SortWork& W, const SegLayout& L, int max_passes, cudaStre
   size_t desc_b = sizeof(unsigned long long) * (size_t)max_passes * max_tiles * kBins;
   size_t hist_b = sizeof(uint32_t) * (size_t)L.n_seg * max_passes * kBins;
   size_t tick_b = sizeof(uint32_t) * 16;
-  W.zero_bytes = desc_b + hist_b + tick_b;
+  size_t done_b = sizeof(uint32_t) * (size_t)L.n_seg;
+  W.zero_bytes = desc_b + hist_b + tick_b + done_b;
   if ((e = cudaMallocAsync(&W.zero_base, W.zero_bytes, st))) return e;
   W.desc = (unsigned long long*)W.zero_base;
   W.hist = (uint32_t*)((char*)W.zero_base + desc_b);
   W.tickets = (uint32_t*)((char*)W.zero_base + desc_b + hist_b);
+  W.done = (uint32_t*)((char*)W.zero_base + desc_b + hist_b + tick_b);
   return sort_set_shape(L, W, 16, 0, st);
 }
 
@@ -463,8 +475,7 @@ cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint3
   if (passes <= 0 || passes > W.max_passes || L.n_tiles == 0) return cudaSuccess;
   cudaMemsetAsync(W.zero_base, 0, W.zero_bytes, st);
   k_upsweep<<<(unsigned)L.n_tiles, kThreads, sizeof(uint32_t) * kWarps * passes * kBins, st>>>(
-      L.off, L.tile_off, L.n_seg, keys, first_pass, passes, W.hist);
-  k_hist_scan<<<(unsigned)(L.n_seg * passes), kThreads, 0, st>>>(W.hist);
+      L.off, L.tile_off, L.n_seg, keys, first_pass, passes, W.hist, W.done);
   uint64_t* kin = keys;
   uint32_t* vin = vals;
   uint64_t* kout = W.keys_alt;
