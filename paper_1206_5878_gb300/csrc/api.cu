@@ -259,9 +259,11 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
                      st, nullptr, nullptr, true);
   mark(7);
   if (c->cfg.energy_correction) {
-    if (mixed)
+    // with the tables (precision 0 and 1) the shell of r_old comes from the
+    // bucket index; FP64 mode evaluates Phi in Eq. 6's division form
+    if (tab)
       launch_correction_mixed(L, c->r, c->x, c->phi, c->Mbuf, c->bk.args(), c->vr, c->vt,
-                              c->r_old, c->cc, c->m, st);
+                              c->r_old, c->cc, c->m, st, !mixed);
     else
       launch_correction(L, c->r, c->x, c->phi, c->vr, c->vt, c->r_old, c->cc, true, c->err, st,
                         c->m);

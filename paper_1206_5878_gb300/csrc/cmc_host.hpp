@@ -292,7 +292,8 @@ constexpr int kRelaxVariants = 3;  // relaxation kernel register caps (launch_re
 void launch_correction_mixed(const SegLayout& L, const double* r, const double* x,
                              const double* phi, const double* Menc,
                              const BucketArgs& ba, double* vr, double* vt, const double* r_old,
-                             const double* c, const double* m, cudaStream_t st);
+                             const double* c, const double* m, cudaStream_t st,
+                             bool div_form = false);
 
 void launch_step_end(const SegLayout& L, uint32_t* step, const double* r_old, const double* c,
                      const double* m, cudaStream_t st);

@@ -69,9 +69,11 @@ __device__ __forceinline__ double shell_root64(const Table64& T, const Star& s, 
 // Phi = Phi_j + M_j (x_j - x) needs no division (mixed mode).  The cores
 // take the node values, so that values loaded ahead and the table give
 // the same arithmetic.  The clamps are the FP64 comparisons restated on
-// the bit patterns (radii are positive).  They keep the FP64 square root and
-// division: in the register-capped turning-point kernel the integer-pipe
-// forms cost more in spills than they save (measured 0.05 ms at N = 10^7).
+// the bit patterns (radii are positive).  Their quotients go to the integer
+// pipes through the shared body and their square roots stay on the FP64
+// pipe: that balance measured fastest in this FP64-bound kernel (turning
+// points 1.39 -> 1.36 ms at N = 10^7; both on the integer pipes, inlined or
+// shared, 0.04-0.05 ms slower).
 __device__ __forceinline__ double rmax_core(const Star& s, double rj, double xj, double pj,
                                             double Mj, bool has_next, double rj1) {
   const double B = Mj;
@@ -81,7 +83,7 @@ __device__ __forceinline__ double rmax_core(const Star& s, double rj, double xj,
   if (!pos_num(D)) D = 0.0;
   const double sD = sqrt(D);
   // 2 (A - E) = -(2 (E - A)) exactly
-  double root = (B + sD) / -scale_up<1>(em);
+  double root = div_rn_nl(B + sD, -scale_up<1>(em));
   if (!ge_pos(root, rj)) root = rj;
   if (has_next && ubits(root) > ubits(rj1)) root = rj1;
   return root;
@@ -106,7 +108,7 @@ __device__ __forceinline__ double rmin_core(const Star& s, bool central, double 
     if (!pos_num(D)) D = 0.0;
     num = s.J * s.J;
   }
-  double root = num / (B + sqrt(D));
+  double root = div_rn_nl(num, B + sqrt(D));
   if (central) {
     // root >= 0 (-0 included, NaN not), then root <= r_0
     const unsigned long long u = ubits(root);
@@ -414,7 +416,8 @@ __device__ __forceinline__ void point64(const double4_32a* __restrict__ nd, int6
 // the long kernels that use it.
 __device__ __forceinline__ void point64_div(const double4_32a* __restrict__ nd, int64_t nb,
                                             const Star& st, double c0, double c1, double sv,
-                                            int sh, double& rs, double& ph, double& Q) {
+                                            int sh, double& rs, double& ph, double& Q,
+                                            double& L) {
   rs = c0 + c1 * (sv * (3.0 - sv * sv));
   double4_32a a;
   const int64_t i = fix_shell_nodes(nd, nb, sh, rs, a);
@@ -431,7 +434,7 @@ __device__ __forceinline__ void point64_div(const double4_32a* __restrict__ nd, 
     const double den = a.y - xj1;
     ph = !(den > 0.0) ? a.z : a.z + div_rn_nl(a.y - xq, den) * (pj1 - a.z);
   }
-  const double L = div_rn_nl(st.J, rs);
+  L = div_rn_nl(st.J, rs);
   Q = scale_up<1>(st.E - ph) - L * L;
 }
 
@@ -846,25 +849,34 @@ __device__ __forceinline__ int accept32(const Grid& G, float E, float J, float c
 // g(s) in FP32 at an envelope sample with the error bound of accept32
 // (the sample's float s is within 2^-25 of the FP64 one): 1 with g and its
 // relative bound eg, 0 when Q < 0 for certain (g = 0), -1 when FP32 cannot
-// tell.
+// tell.  The reciprocal and the inverse square root are the one-instruction
+// approximations (relative errors below 2^-22): the reciprocal's error is an
+// error in r (added to dr, as r's own), the inverse square root's goes into
+// eg (2^-21), and eg itself, computed with them, is taken 2^-16 larger.
 __device__ __forceinline__ int g32_bounded(const Grid& G, float E, float J, float c0, float c1,
                                            float sv, float& g, float& eg) {
   const float ss = sv * sv;
   const float rs = c0 + c1 * (sv * (3.0f - ss));
   const float drds = (3.0f * c1) * (1.0f - ss);
-  const float xq = 1.0f / rs;
+  float xq;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xq) : "f"(rs));
   const float ph = grid_phi(G, xq);
   const float L = J * xq, L2 = L * L;
   const float Q = 2.0f * (E - ph) - L2;
   const float ac1 = fabsf(c1), aph = fabsf(ph);
   const float dr = 3.0f * ac1 * ((1.0f - ss) + 0x1p-21f) * 0x1p-23f +
-                   0x1p-21f * (fabsf(c0) + 2.0f * ac1);
+                   0x1p-21f * (fabsf(c0) + 2.0f * ac1) + 0x1p-22f * fabsf(rs);
   const float qerr = 0x1p-20f * (fabsf(E) + aph + L2) + (2.0f * G.err + 0x1p-22f) * aph +
                      3.0f * (G.mb * xq + L2) * (dr * xq);
   if (Q < -4.0f * qerr) return 0;
-  if (!(Q > 4.0f * qerr) || !(drds > 0.0f)) return -1;
-  g = drds / sqrtf(Q);
-  eg = (0.75f * qerr) / Q + (6.0f * ac1 * 0x1p-23f) / drds + 0x1p-20f;
+  if (!(Q > 4.0f * qerr) || !(drds > 0x1p-100f)) return -1;
+  float rq, rd;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rq) : "f"(Q));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd) : "f"(drds));
+  g = drds * rq;
+  eg = ((0.75f * qerr) * (rq * rq) + (6.0f * ac1 * 0x1p-23f) * rd + 0x1p-20f + 0x1p-21f) *
+       (1.0f + 0x1p-16f);
+  if (!(eg < 0.25f)) return -1;
   return 1;
 }
 
@@ -895,9 +907,9 @@ __device__ __noinline__ double g64_sample(const double4_32a* __restrict__ nd, in
   s.E = E;
   s.J = J;
   const float c0f = f32_rn(c0), c1f = f32_rn(c1);
-  double rs, ph, Q;
+  double rs, ph, Q, L;
   point64_div(nd, nb, s, c0, c1, c_s64[j], shell32_of(nd, (int)nb, BK, c0f, c1f, c_s32[j]), rs,
-              ph, Q);
+              ph, Q, L);
   return g_of_point(c1, c_s64[j], Q);
 }
 
@@ -1157,8 +1169,8 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
               shell32_of(BA.node + sb, (int)nbc, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f);
           double g64v;
           if (kExact) {
-            double rs, ph, Q;
-            point64_div(BA.node + sb, nbc, s, c0, c1, sv, guess, rs, ph, Q);
+            double rs, ph, Q, L;
+            point64_div(BA.node + sb, nbc, s, c0, c1, sv, guess, rs, ph, Q, L);
             g64v = g_of_point(c1, sv, Q);
           } else {
             double rs, xs, ph, L, Q;
@@ -1377,8 +1389,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
           const int guess = shell32_of(BA.node + sb, nb32, BK, c0f, c1f, 2.0f * u01f(w.y) - 1.0f);
           double rs, ph, Q, vtn;
           if (kPrec == 2) {
-            point64_div(BA.node + sb, nbc, s, c0, c1, sv, guess, rs, ph, Q);
-            vtn = div_rn_nl(s.J, rs);
+            point64_div(BA.node + sb, nbc, s, c0, c1, sv, guess, rs, ph, Q, vtn);  // v_t = J / r
           } else {
             double xs;
             point64(BA.node + sb, nbc, s, c0, c1, sv, guess, rs, xs, ph, vtn, Q);
@@ -1430,6 +1441,10 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
 // enclosed mass of that shell (Eq. 6 without its division), then
 // T' = T + 1/2 [(Phi_new(r_old) - Phi_new,k) - c] clamped at 0 and both
 // velocity components scaled by sqrt(T'/T), as in the FP64 kernel.
+// kDiv (FP64 mode): Phi_new(r_old) by Eq. 6's division form and the FP64
+// kernel's comparisons, as the FP64 statement computes them, the shell found
+// the same way (the shell of a radius is unique).
+template <bool kDiv>
 __global__ void __launch_bounds__(128, 12) k_correction_mixed(Seg S, const int64_t* esc,
                                                           const double* r, const double* x,
                                                           const double* phi,
@@ -1458,18 +1473,32 @@ __global__ void __launch_bounds__(128, 12) k_correction_mixed(Seg S, const int64
   shells32_bk<1>(NodeKeys{BA.node + sb}, (int)nbc, BK, xq, sh);
   double4_32a nd;
   const int64_t i = fix_shell_nodes(BA.node + sb, nbc, sh[0], ro, nd);
-  const double pn = i < 0 ? nd.z : nd.z + nd.w * (nd.y - xo);
+  double pn;
+  if (!kDiv) {
+    pn = i < 0 ? nd.z : nd.z + nd.w * (nd.y - xo);
+  } else if (i < 0) {
+    pn = nd.z;
+  } else {
+    double xj1 = 0.0, pj1 = 0.0;
+    if (i + 1 < nbc) {
+      const double4_32a nx = BA.node[sb + i + 1];
+      xj1 = nx.y;
+      pj1 = nx.z;
+    }
+    const double den = nd.y - xj1;
+    pn = !(den > 0.0) ? nd.z : nd.z + div_rn(nd.y - xo, den) * (pj1 - nd.z);
+  }
   const double a = vr[p], b = vt[p];
   const double Tk = scale_down<1>(a * a + b * b);
   const double dnew = pn - phi[p];
   double Tp = Tk + scale_down<1>(dnew - cc[p]);
   bool clamp = false;
-  if (lt0(Tp)) {
+  if (kDiv ? Tp < 0.0 : lt0(Tp)) {
     clamp_energy_add(S.stats, c, m[p], Tp);
     Tp = 0.0;
     clamp = true;
   }
-  if (pos_num(Tk)) {
+  if (kDiv ? Tk > 0.0 : pos_num(Tk)) {
     const double f = sqrt_rn(div_rn(Tp, Tk));
     vr[p] = a * f;
     vt[p] = b * f;
@@ -1782,10 +1811,15 @@ void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWo
 void launch_correction_mixed(const SegLayout& L, const double* r, const double* x,
                              const double* phi, const double* Menc,
                              const BucketArgs& ba, double* vr, double* vt, const double* r_old,
-                             const double* c, const double* m, cudaStream_t st) {
+                             const double* c, const double* m, cudaStream_t st,
+                             bool div_form) {
   if (!L.n) return;
-  k_correction_mixed<<<(unsigned)((L.n + 127) / 128), 128, 0, st>>>(
-      L.dev(), L.esc_step, r, x, phi, Menc, ba, vr, vt, r_old, c, m, L.n);
+  if (div_form)
+    k_correction_mixed<true><<<(unsigned)((L.n + 127) / 128), 128, 0, st>>>(
+        L.dev(), L.esc_step, r, x, phi, Menc, ba, vr, vt, r_old, c, m, L.n);
+  else
+    k_correction_mixed<false><<<(unsigned)((L.n + 127) / 128), 128, 0, st>>>(
+        L.dev(), L.esc_step, r, x, phi, Menc, ba, vr, vt, r_old, c, m, L.n);
 }
 
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,
