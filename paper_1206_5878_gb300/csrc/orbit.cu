@@ -801,10 +801,12 @@ __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
 // X' (53 bits); the float values use 23 bits of each, so |s32 - s| and
 // |X'32 - X'| are at most 2^-23 and 2^-24.  Bounds (u = 2^-24):
 //   r(s):  |r32 - r| <= 3|c1| (1 - s^2 + 2^-21) 2^-23 + 8u (|c0| + 2|c1|)
+//          + 2^-22 |r|                         1/r by the approximate reciprocal
 //   Q:     16u (|E| + |Phi| + L^2)             float operations and inputs
 //          + (2 err_grid + 4u) |Phi|           grid interpolation and values
 //          + 1.5 * 2 (M x + L^2) |dr| / r      Q's slope in r, M <= M_bound
 //   g:     1.5 * (1/2) dQ / Q + 6|c1| 2^-23 / (dr/ds) + 16u
+//          + 2^-21                             the approximate 1/sqrt(Q)
 // Close to a turning point Q is within a few dQ of zero and the trial is
 // left undecided; elsewhere the FP32 answer is the FP64 one.
 // kExact (FP64 mode): F is the float of the FP64 envelope, and a trial
@@ -817,18 +819,28 @@ __device__ __forceinline__ int accept32(const Grid& G, float E, float J, float c
   const float ss = sv * sv;
   const float rs = c0 + c1 * (sv * (3.0f - ss));
   const float drds = (3.0f * c1) * (1.0f - ss);
-  const float xq = 1.0f / rs;
+  // the one-instruction reciprocal and inverse square root (relative
+  // errors below 2^-22): the reciprocal's error counts as an error in r (in
+  // dr), the inverse square root's in eg (2^-21), and eg, computed with them,
+  // is taken 2^-16 larger
+  float xq;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(xq) : "f"(rs));
   const float ph = grid_phi(G, xq);
   const float L = J * xq, L2 = L * L;
   const float Q = 2.0f * (E - ph) - L2;
   const float ac1 = fabsf(c1), aph = fabsf(ph);
   const float dr = 3.0f * ac1 * ((1.0f - ss) + 0x1p-21f) * 0x1p-23f +
-                   0x1p-21f * (fabsf(c0) + 2.0f * ac1);
+                   0x1p-21f * (fabsf(c0) + 2.0f * ac1) + 0x1p-22f * fabsf(rs);
   const float qerr = 0x1p-20f * (fabsf(E) + aph + L2) + (2.0f * G.err + 0x1p-22f) * aph +
                      3.0f * (G.mb * xq + L2) * (dr * xq);
-  if (!(Q > 4.0f * qerr)) return -1;
-  const float g = drds / sqrtf(Q);
-  const float eg = (0.75f * qerr) / Q + (6.0f * ac1 * 0x1p-23f) / drds + 0x1p-20f;
+  if (!(Q > 4.0f * qerr) || !(drds > 0x1p-100f)) return -1;
+  float rq, rd;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(rq) : "f"(Q));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rd) : "f"(drds));
+  const float g = drds * rq;
+  const float eg = ((0.75f * qerr) * (rq * rq) + (6.0f * ac1 * 0x1p-23f) * rd + 0x1p-20f +
+                    0x1p-21f) * (1.0f + 0x1p-16f);
+  if (!(eg < 0.25f)) return -1;
   if (kExact) {
     const bool above = g * (1.0f - eg) > F * (1.0f + 0x1p-22f);
     const bool below = g * (1.0f + eg) < F * (1.0f - 0x1p-22f);
