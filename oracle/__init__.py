@@ -101,7 +101,9 @@ def _declare(lib):
         "or_step": (_d, [_i64, _p, _p, _p, _p, _p, _p, _p, _u64, _u32, _i32, _d, _d,
                          _i32, _i32, _i32, _p, _p]),
         "or_step_col": (_d, [_i64, _p, _p, _p, _p, _p, _p, _p, _p, _u64, _u32, _i32, _d, _d,
-                             _i32, _i32, _i32, _p, _p, _p]),
+                             _i32, _i32, _i32, _p, _p, _p, _p, _d, _d, _d]),
+        "or_tbinary": (_d, [_i64, _p, _p, _p, _p, _p, _d, _d, _p]),
+        "or_tse": (_d, [_d, _d, _d]),
         "or_encounter_radii": (ctypes.c_int, [_d, _d, _d, _d, _d, _d, _d, _d, _d, _d, _d,
                                               _u64, _u32, _u32, _p]),
         "or_relax_col": (_i64, [_i64, _p, _p, _p, _p, _p, _p, _i32, _d, _d, _u64, _u32, _p, _p,
@@ -233,6 +235,21 @@ def tcoll(r, vr, vt, m, R) -> float:
     """Eq. 8's collision timestep over the innermost 300 bound stars."""
     r, vr, vt, m, R = (_f64(a) for a in (r, vr, vt, m, R))
     return _L().or_tcoll(r.shape[0], _ptr(r), _ptr(vr), _ptr(vt), _ptr(m), _ptr(R))
+
+
+def tbinary(r, vr, vt, m, A, x_bb: float = 1.0, x_bs: float = 1.0):
+    """Eqs. 9 and 10's binary-binary and binary-single timesteps over the
+    innermost 300 bound stars (binaries: A > 0); returns (T_bb, T_bs)."""
+    r, vr, vt, m, A = (_f64(a) for a in (r, vr, vt, m, A))
+    tbs = np.zeros(1)
+    tbb = _L().or_tbinary(r.shape[0], _ptr(r), _ptr(vr), _ptr(vt), _ptr(m), _ptr(A),
+                          float(x_bb), float(x_bs), _ptr(tbs))
+    return tbb, float(tbs[0])
+
+
+def tse(M: float, T_prev: float, dm_se: float) -> float:
+    """Eq. 11's stellar-evolution timestep."""
+    return _L().or_tse(float(M), float(T_prev), float(dm_se))
 
 
 def cbrt(v: float) -> float:
@@ -427,7 +444,8 @@ class Cluster:
     def __init__(self, r, vr, vt, m, ids, seed: int, *, theta_max: float = THETA_MAX,
                  gamma: float = GAMMA, bin_size: int = BIN_SIZE, max_trials: int = 1000,
                  energy_correction: bool = True, pot_mode: str = "recursion",
-                 rng: str = "philox", radii=None):
+                 rng: str = "philox", radii=None, semi_major=None, x_bb: float = 1.0,
+                 x_bs: float = 1.0):
         r, vr, vt, m = _f64(r), _f64(vr), _f64(vt), _f64(m)
         ids = _u32a(ids)
         n = r.shape[0]
@@ -439,6 +457,11 @@ class Cluster:
         self.id = ids[perm].copy()
         # stellar radii (sticky-sphere collisions and the Eq. 8 timestep)
         self.R = None if radii is None else _f64(radii)[perm].copy()
+        # binaries' semi-major axes (0: a single star) and Eqs. 9-10's X
+        self.A = None if semi_major is None else _f64(semi_major)[perm].copy()
+        self.x_bb, self.x_bs = float(x_bb), float(x_bs)
+        # an outside bound on the next timesteps (e.g. Eq. 11's), 0: none
+        self.dt_cap = 0.0
         # mergers so far and the energy they dissipated
         self.collisions = np.zeros(2)
         self.n = n
@@ -472,20 +495,22 @@ class Cluster:
             if self.taus is not None:
                 _L().or_taus_bind(_ptr(self.taus))
             try:
-                if self.R is None:
+                if self.R is None and self.A is None and not self.dt_cap > 0.0:
                     dt = _L().or_step(self.n, _ptr(nb), _ptr(self.r), _ptr(self.vr),
                                       _ptr(self.vt), _ptr(self.m), _ptr(self.id),
                                       _ptr(self.phi), self.seed, self.step_no, self.bin_size,
                                       self.pref, self.lnL, self.max_trials, self.ecorr,
                                       self.pot_mode, _ptr(stats), _ptr(self.escaped))
                 else:
+                    opt = lambda a: None if a is None else _ptr(a)
                     dt = _L().or_step_col(self.n, _ptr(nb), _ptr(self.r), _ptr(self.vr),
-                                          _ptr(self.vt), _ptr(self.m), _ptr(self.R),
+                                          _ptr(self.vt), _ptr(self.m), opt(self.R),
                                           _ptr(self.id), _ptr(self.phi), self.seed,
                                           self.step_no, self.bin_size, self.pref, self.lnL,
                                           self.max_trials, self.ecorr, self.pot_mode,
                                           _ptr(stats), _ptr(self.escaped),
-                                          _ptr(self.collisions))
+                                          _ptr(self.collisions), opt(self.A), self.x_bb,
+                                          self.x_bs, float(self.dt_cap))
             finally:
                 _L().or_taus_bind(None)
             self.nb = int(nb[0])

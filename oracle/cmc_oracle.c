@@ -724,6 +724,68 @@ double or_tcoll(int64_t nb, const double *r, const double *vr, const double *vt,
     return 1.0 / inv;
 }
 
+/* The binary timesteps (section 2.1 step 2, Eqs. 9 and 10) over the
+ * innermost P = min(300, nb) bound stars, a star being a binary when its
+ * semi-major axis A[k] > 0 (its mass m[k] the binary's total):
+ *   1 / T_bb = 16 sqrt(pi) n_b X_bb^2 <a^2> sigma
+ *              (1 + G <M a> / (2 sigma^2 X_bb <a^2>))
+ *   1 / T_bs = 4 sqrt(pi) n_s X_bs^2 <a^2> sigma
+ *              (1 + G <M> <a> / (sigma^2 X_bs <a^2>))
+ * Readings: n_b and n_s are the central density of Eq. 8's estimator,
+ * n = 3 (P - 1) / (4 pi (r_{P-1}^3 - r_0^3)), times the binaries' and the
+ * single stars' shares of the P stars; <a^2>, <M a>, <a> are means over
+ * the binaries among them, <M> the mean mass of all P, sigma as in Eq. 8.
+ * +inf where there is no binary (or, for T_bs, no single star).  Returns
+ * T_bb; *tbs = T_bs. */
+double or_tbinary(int64_t nb, const double *r, const double *vr, const double *vt,
+                  const double *m, const double *A, double x_bb, double x_bs, double *tbs)
+{
+    int64_t P = nb < 300 ? nb : 300, k, nbin = 0;
+    double vol, n, sv = 0.0, sm = 0.0, sa = 0.0, sa2 = 0.0, sma = 0.0;
+    double sig2, sig, a2, ma, am, mm, nbd, nsd, inv;
+    *tbs = INFINITY;
+    if (P < 2 || !A) return INFINITY;
+    vol = r[P - 1] * r[P - 1] * r[P - 1] - r[0] * r[0] * r[0];
+    if (!(vol > 0.0)) return INFINITY;
+    n = (3.0 * (double)(P - 1)) / ((4.0 * OR_PI) * vol);
+    for (k = 0; k < P; ++k) {
+        sv = sv + (vr[k] * vr[k] + vt[k] * vt[k]);
+        sm = sm + m[k];
+        if (A[k] > 0.0) {
+            nbin += 1;
+            sa = sa + A[k];
+            sa2 = sa2 + A[k] * A[k];
+            sma = sma + m[k] * A[k];
+        }
+    }
+    sig2 = (sv / (double)P) / 3.0;
+    if (nbin == 0 || !(sig2 > 0.0)) return INFINITY;
+    sig = sqrt(sig2);
+    a2 = sa2 / (double)nbin;
+    ma = sma / (double)nbin;
+    am = sa / (double)nbin;
+    mm = sm / (double)P;
+    nbd = n * ((double)nbin / (double)P);
+    nsd = n * ((double)(P - nbin) / (double)P);
+    if (nbin < P) {
+        inv = (((4.0 * sqrt(OR_PI)) * nsd) * ((x_bs * x_bs) * a2)) * sig;
+        inv = inv * (1.0 + (mm * am) / ((sig2 * x_bs) * a2));
+        *tbs = 1.0 / inv;
+    }
+    inv = (((16.0 * sqrt(OR_PI)) * nbd) * ((x_bb * x_bb) * a2)) * sig;
+    inv = inv * (1.0 + ma / (((2.0 * sig2) * x_bb) * a2));
+    return 1.0 / inv;
+}
+
+/* The stellar-evolution timestep (Eq. 11): T_se = 0.001 M T_prev / dm_se,
+ * the step in which stellar evolution, losing dm_se in the previous step of
+ * length T_prev, takes 0.1% of the cluster's mass M; +inf without loss. */
+double or_tse(double M, double T_prev, double dm_se)
+{
+    if (!(dm_se > 0.0)) return INFINITY;
+    return ((0.001 * M) * T_prev) / dm_se;
+}
+
 /* Test hook for the angle draw. */
 int or_disk_angle_pub(uint64_t seed, uint32_t id, uint32_t step, uint32_t tag, double *cs)
 {
@@ -1093,7 +1155,8 @@ void or_core_rho(int64_t nb, const double *r, const double *m, double *rho)
 double or_step_col(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt, double *m,
                    double *R, uint32_t *id, double *phi, uint64_t seed, uint32_t step,
                    int32_t bs, double pref, double lnL, int32_t max_trials, int32_t ecorr,
-                   int32_t pot_mode, int64_t *stats, double *esc_io, double *col);
+                   int32_t pot_mode, int64_t *stats, double *esc_io, double *col,
+                   double *A, double x_bb, double x_bs, double dt_cap);
 
 double or_step(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt, double *m,
                uint32_t *id, double *phi, uint64_t seed, uint32_t step, int32_t bs,
@@ -1101,18 +1164,22 @@ double or_step(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt, dou
                int32_t pot_mode, int64_t *stats, double *esc_io)
 {
     return or_step_col(n, nb_io, r, vr, vt, m, NULL, id, phi, seed, step, bs, pref, lnL,
-                       max_trials, ecorr, pot_mode, stats, esc_io, NULL);
+                       max_trials, ecorr, pot_mode, stats, esc_io, NULL, NULL, 1.0, 1.0, 0.0);
 }
 
 /* The timestep with stellar radii R (may be NULL: or_step): the collision
  * timestep of Eq. 8 joins the minimum, relaxation pairs may merge (sticky
  * spheres), and a star merged away (radius -1, mass 0) leaves in the orbit
  * step (r = +inf, no energy carried off: it has no mass); R is permuted with
- * the stars; col[0] += mergers, col[1] += their change of K + W. */
+ * the stars; col[0] += mergers, col[1] += their change of K + W.  With the
+ * binaries' semi-major axes A (may be NULL; permuted with the stars), T_bb
+ * and T_bs of Eqs. 9 and 10 join the minimum; a positive finite dt_cap (an
+ * outside bound such as Eq. 11's stellar-evolution step) joins it too. */
 double or_step_col(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt, double *m,
                    double *R, uint32_t *id, double *phi, uint64_t seed, uint32_t step,
                    int32_t bs, double pref, double lnL, int32_t max_trials, int32_t ecorr,
-                   int32_t pot_mode, int64_t *stats, double *esc_io, double *col)
+                   int32_t pot_mode, int64_t *stats, double *esc_io, double *col,
+                   double *A, double x_bb, double x_bs, double dt_cap)
 {
     int64_t nb = *nb_io, k;
     int64_t nbins = (nb + bs - 1) / bs;
@@ -1131,6 +1198,12 @@ double or_step_col(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt,
         double tc = or_tcoll(nb, r, vr, vt, m, R);
         if (tc < dt) dt = tc;
     }
+    if (A) {
+        double tbs, tbb = or_tbinary(nb, r, vr, vt, m, A, x_bb, x_bs, &tbs);
+        if (tbb < dt) dt = tbb;
+        if (tbs < dt) dt = tbs;
+    }
+    if (dt_cap > 0.0 && dt_cap < dt) dt = dt_cap;
     stats[6] += or_relax_col(nb, vr, vt, m, R, id, nbin, bs, dt, lnL, seed, step, col, r, phi);
 
     for (k = 0; k < n; ++k) { rn[k] = r[k]; ro[k] = r[k]; cc[k] = 0.0; }
@@ -1174,6 +1247,7 @@ double or_step_col(int64_t n, int64_t *nb_io, double *r, double *vr, double *vt,
     OR_PERMUTE(vt);
     OR_PERMUTE(m);
     if (R) OR_PERMUTE(R);
+    if (A) OR_PERMUTE(A);
     OR_PERMUTE(ro);
     OR_PERMUTE(cc);
     for (k = 0; k < n; ++k) tmp[k] = rn[perm[k]];
