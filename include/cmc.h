@@ -138,6 +138,13 @@ typedef struct {
                                    diagnostics ring (cmc_get_diagnostics), 0 =
                                    off (default); on, every step also computes
                                    K and W (four more kernels per step) */
+    int32_t binaries;           /* 1: stars carry semi-major axes
+                                   (cmc_set_binaries; 0 for a single star, a
+                                   binary's mass its total): the binary-binary
+                                   and binary-single timesteps of Eqs. 9 and 10
+                                   join Eq. 7's; default 0 */
+    double x_bb;                /* strong-interaction parameter X_bb of Eq. 9 (1) */
+    double x_bs;                /* strong-interaction parameter X_bs of Eq. 10 (1) */
 } cmc_config;
 
 /* Fill cfg with the defaults shown above. */
@@ -373,6 +380,43 @@ cmc_status cmc_energy_correction(int64_t n, const double *r, const double *phi, 
 cmc_status cmc_set_radii(cmc_ctx *ctx, const double *R, int32_t ptr_kind);
 /* The stellar radii in state order (n doubles out, host or device). */
 cmc_status cmc_get_radii(cmc_ctx *ctx, double *R, int32_t ptr_kind);
+
+/* Semi-major axes of binaries (configuration binaries = 1; Henon length
+ * units) of the stars in the order cmc_get_state returns them: a (n, host
+ * or device per ptr_kind) in, finite and >= 0; 0 marks a single star, and a
+ * binary's entry of m is the pair's total mass.  With them the binary
+ * timesteps of section 2.1 step 2 join the minimum with Eq. 7's, over the
+ * innermost P = min(300, N_bound) stars of each cluster (Eqs. 9 and 10):
+ *   1/T_bb = 16 sqrt(pi) n_b X_bb^2 <a^2> sigma
+ *            (1 + G <M a> / (2 sigma^2 X_bb <a^2>)),
+ *   1/T_bs = 4 sqrt(pi) n_s X_bs^2 <a^2> sigma
+ *            (1 + G <M> <a> / (sigma^2 X_bs <a^2>)),
+ * with n = 3 (P - 1) / (4 pi (r_{P-1}^3 - r_0^3)), n_b and n_s that density
+ * times the binaries' and the single stars' shares of the P stars, <a^2>,
+ * <M a>, <a> means over the binaries among them, <M> the mean mass of all
+ * P, sigma^2 = <v_r^2 + v_t^2> / 3 over all P.  No binary: no T_bb or T_bs;
+ * no single star: no T_bs.  The axes travel with the stars through every
+ * sort (the interactions that would change them are outside this
+ * library); cmc_set_state sets them to 0.  CMC_EINVAL without binaries or
+ * for bad values (checked for host input). */
+cmc_status cmc_set_binaries(cmc_ctx *ctx, const double *a, int32_t ptr_kind);
+/* The semi-major axes in state order (n doubles out, host or device). */
+cmc_status cmc_get_binaries(cmc_ctx *ctx, double *a, int32_t ptr_kind);
+
+/* An outside bound on the next steps of each cluster (host, n_clusters
+ * doubles, each finite and >= 0; 0 = none, the initial value): every later
+ * step of cluster c takes min(its timestep, cap[c]).  It carries the
+ * timesteps that other processes put on the step (section 2.1 step 2: Eq.
+ * 11's stellar-evolution step, say, from cmc_tse).  Stays until set again.
+ * CMC_EINVAL for bad values. */
+cmc_status cmc_set_dt_cap(cmc_ctx *ctx, const double *cap);
+
+/* The stellar-evolution timestep of Eq. 11: the step in which stellar
+ * evolution, having taken dm_se of mass in the previous step of length
+ * T_prev, takes 0.1% of the cluster mass M:
+ * T_se = ((0.001 M) T_prev) / dm_se, in that order of operations;
+ * +inf when dm_se <= 0 (no loss).  Host arithmetic only. */
+double cmc_tse(double M, double T_prev, double dm_se);
 
 /* Limits of the sort's bounded device waits on the current device, for all
  * contexts and stage calls there (read by the kernels at launch, so graphs

@@ -17,7 +17,7 @@ from ._native import CMCError, STAT_NAMES, cmc_config, check, load
 
 __all__ = ["Cluster", "CMCError", "config", "load", "STAT_NAMES", "stage_philox",
            "stage_sort_radius", "stage_potential", "stage_timestep", "stage_relax",
-           "stage_orbit", "stage_energy_correction"]
+           "stage_orbit", "stage_energy_correction", "tse"]
 
 
 def config(**kw) -> cmc_config:
@@ -183,6 +183,25 @@ class Cluster:
         check(self.lib.cmc_get_radii(self.ctx, out.ctypes.data, 0), self.ctx, self.lib)
         return out
 
+    def set_binaries(self, a):
+        """Semi-major axes of the stars in get_state order (binaries=1; 0 for
+        a single star): the binary timesteps of Eqs. 9 and 10 then bound
+        the step."""
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        check(self.lib.cmc_set_binaries(self.ctx, a.ctypes.data, 0), self.ctx, self.lib)
+
+    def binaries(self) -> np.ndarray:
+        out = np.empty(self.n)
+        check(self.lib.cmc_get_binaries(self.ctx, out.ctypes.data, 0), self.ctx, self.lib)
+        return out
+
+    def set_dt_cap(self, cap):
+        """An outside bound on each cluster's next timesteps (0 = none):
+        Eq. 11's stellar-evolution step (tse), say."""
+        cap = np.ascontiguousarray(np.broadcast_to(np.asarray(cap, dtype=np.float64),
+                                                   (self.n_clusters,)))
+        check(self.lib.cmc_set_dt_cap(self.ctx, cap.ctypes.data), self.ctx, self.lib)
+
     def set_state(self, state, step: int):
         kind = 0 if isinstance(state["r"], np.ndarray) else 1
         arrs = [self._prep(state[k], k, kind) for k in ("r", "vr", "vt", "m", "id")]
@@ -323,6 +342,11 @@ def stage_energy_correction(r, phi, vr, vt, r_old, c, stream=None):
     check(load().cmc_energy_correction(r.shape[0], _t(r), _t(phi), _t(vr), _t(vt), _t(r_old),
                                        _t(c), _stream_ptr(stream)))
     return vr, vt
+
+
+def tse(M: float, T_prev: float, dm_se: float) -> float:
+    """The stellar-evolution timestep of Eq. 11 (+inf without mass loss)."""
+    return float(load().cmc_tse(float(M), float(T_prev), float(dm_se)))
 
 
 def set_wait_limits(lookback_polls: int = 0, tie_moves: int = 0):

@@ -36,7 +36,8 @@ class cmc_config(ctypes.Structure):
     _fields_ = [("precision", _i32), ("bin_size", _i32), ("theta_max", _d), ("gamma", _d),
                 ("max_trials", _i32), ("energy_correction", _i32), ("orbit_block", _i32),
                 ("autotune", _i32), ("orbit_variant", _i32), ("rng", _i32),
-                ("relax_variant", _i32), ("collisions", _i32), ("diag_ring", _i32)]
+                ("relax_variant", _i32), ("collisions", _i32), ("diag_ring", _i32),
+                ("binaries", _i32), ("x_bb", _d), ("x_bs", _d)]
 
 
 # exported symbol -> (restype, argtypes); the list is the ABI of include/cmc.h
@@ -79,6 +80,10 @@ SIGNATURES = {
     "cmc_set_wait_limits": (_i32, [_i32, _i64]),
     "cmc_set_radii": (_i32, [_p, _p, _i32]),
     "cmc_get_radii": (_i32, [_p, _p, _i32]),
+    "cmc_set_binaries": (_i32, [_p, _p, _i32]),
+    "cmc_get_binaries": (_i32, [_p, _p, _i32]),
+    "cmc_set_dt_cap": (_i32, [_p, _p]),
+    "cmc_tse": (_d, [_d, _d, _d]),
 }
 
 _libs = {}

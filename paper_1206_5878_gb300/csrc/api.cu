@@ -51,6 +51,8 @@ struct cmc_ctx {
   int relax_variant = 0;  // relaxation kernel variant (see kRelaxVariants)
   // stellar radii (cfg.collisions): the state's, and their copy through the sort
   double *R = nullptr, *Rp = nullptr;
+  // semi-major axes (cfg.binaries; 0 for single stars), likewise
+  double *A = nullptr, *Ap = nullptr;
 };
 
 namespace {
@@ -220,7 +222,7 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   };
   mark(0);
   launch_bins(L, c->r, c->vr, c->vt, c->m, c->nbin, c->pref, st);
-  launch_tcoll(L, c->r, c->vr, c->vt, c->m, c->R, st);
+  launch_tcentral(L, c->r, c->vr, c->vt, c->m, c->R, c->A, c->cfg.x_bb, c->cfg.x_bs, st);
   mark(1);
   launch_relax(L, c->vr, c->vt, c->m, c->id, c->nbin, c->step, st, c->relax_variant, c->R, c->r,
                c->phi);
@@ -234,7 +236,7 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
                tab ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
                c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
                c->bk.args(), c->r_old, c->cc, c->vals, c->pcount, st, false, c->R, c->Rp,
-               c->Fx);
+               c->Fx, c->A, c->Ap);
   mark(4);
   // radix passes over bits 24-63 of the radius keys; runs equal in those
   // bits (radii within 2^-28 of each other, escapers whose ids differ in
@@ -246,7 +248,7 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
                 24);
   mark(5);
   launch_gather(L, sk, sv, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old, c->cc, st,
-                c->tile_a, c->tile_b, c->Rp, c->R);
+                c->tile_a, c->tile_b, c->Rp, c->R, c->Ap, c->A);
   mark(6);
   // the tables carry the shell slopes of the FP64 orbit step (not the
   // scan's enclosed masses): the sampled step's turning points and points
@@ -285,7 +287,7 @@ int count_step_kernels(const cmc_ctx* c) {
   // sampler, FP64 continuation, the tables' parameters, the grid's values
   // with the seams' slopes; precision 0: the envelope], [correction], step end
   const int p = c->cfg.precision;
-  return 3 + (c->R ? 1 : 0) + (c->ring ? 4 : 0) + 1 + 5 + 1 + 1 + 1 +
+  return 3 + ((c->R || c->A) ? 1 : 0) + (c->ring ? 4 : 0) + 1 + 5 + 1 + 1 + 1 +
          (p == 1 ? 5 : p == 0 ? 6 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
@@ -301,6 +303,8 @@ void free_ctx(cmc_ctx* c) {
   dfree(c->id, st);
   dfree(c->R, st);
   dfree(c->Rp, st);
+  dfree(c->A, st);
+  dfree(c->Ap, st);
   dfree(c->t32, st);
   dfree(c->keys, st);
   dfree(c->vals, st);
@@ -583,6 +587,45 @@ cmc_status autotune(cmc_ctx* c) {
   return check_err_flags(c);
 }
 
+// A per-star attribute of the sorted state (stellar radii, semi-major
+// axes): set from, or read to, caller memory (ptr_kind 0 host, 1 device);
+// host values must be finite and >= 0.
+cmc_status attr_set(cmc_ctx* c, double* dst, const double* src, int32_t ptr_kind,
+                    const char* call, const char* option) {
+  const std::string who(call);
+  if (!c || !src || (ptr_kind != 0 && ptr_kind != 1))
+    return fail(c, CMC_EINVAL, who + ": bad arguments");
+  if (c->poisoned) return fail(c, CMC_EPOISONED, who + ": context poisoned");
+  if (!dst) return fail(c, CMC_EINVAL, who + ": the context has no " + option);
+  if (ptr_kind == 0)
+    for (int64_t i = 0; i < c->L.n; ++i)
+      if (!(src[i] >= 0.0) || !(src[i] < INFINITY))
+        return fail(c, CMC_EINVAL, who + ": values must be finite and >= 0");
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)c->L.n,
+                                  ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, call);
+  return CMC_OK;
+}
+
+cmc_status attr_get(cmc_ctx* c, const double* src, double* dst, int32_t ptr_kind,
+                    const char* call, const char* option) {
+  const std::string who(call);
+  if (!c || !dst || (ptr_kind != 0 && ptr_kind != 1))
+    return fail(c, CMC_EINVAL, who + ": bad arguments");
+  if (c->poisoned) return fail(c, CMC_EPOISONED, who + ": context poisoned");
+  if (!src) return fail(c, CMC_EINVAL, who + ": the context has no " + option);
+  DeviceGuard g(c->device);
+  cudaError_t e = cudaMemcpyAsync(dst, src, sizeof(double) * (size_t)c->L.n,
+                                  ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                                  c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_fail(c, e, call);
+  return CMC_OK;
+}
+
 }  // namespace
 
 namespace cmc {
@@ -607,6 +650,9 @@ void cmc_config_default(cmc_config* cfg) {
   cfg->relax_variant = -1;
   cfg->collisions = 0;
   cfg->diag_ring = 0;
+  cfg->binaries = 0;
+  cfg->x_bb = 1.0;
+  cfg->x_bs = 1.0;
 }
 
 cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
@@ -626,7 +672,9 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
       (cfg.orbit_block % 32) || cfg.orbit_variant < -1 || cfg.orbit_variant >= kOrbitVariants ||
       (cfg.rng != 0 && cfg.rng != 1) || cfg.relax_variant < -1 ||
       cfg.relax_variant >= kRelaxVariants || (cfg.collisions != 0 && cfg.collisions != 1) ||
-      cfg.diag_ring < 0 || cfg.diag_ring > (1 << 20))
+      cfg.diag_ring < 0 || cfg.diag_ring > (1 << 20) ||
+      (cfg.binaries != 0 && cfg.binaries != 1) || !(cfg.x_bb > 0.0) || !(cfg.x_bb < INFINITY) ||
+      !(cfg.x_bs > 0.0) || !(cfg.x_bs < INFINITY))
     return fail(nullptr, CMC_EINVAL, "cmc_init: bad configuration");
   std::vector<int64_t> sizes(n_per_cluster, n_per_cluster + n_clusters);
   std::vector<uint64_t> sd(seeds, seeds + n_clusters);
@@ -687,6 +735,11 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
     CMC_ALLOC(c->R, n);
     CMC_ALLOC(c->Rp, n);
     if (!e) e = cudaMemsetAsync(c->R, 0, sizeof(double) * n, st);
+  }
+  if (cfg.binaries) {
+    CMC_ALLOC(c->A, n);
+    CMC_ALLOC(c->Ap, n);
+    if (!e) e = cudaMemsetAsync(c->A, 0, sizeof(double) * n, st);
   }
 #undef CMC_ALLOC
   if (!e) e = alloc_sort(c->W, L, 8, st);
@@ -891,8 +944,10 @@ cmc_status cmc_set_state(cmc_ctx* c, const double* r, const double* vr, const do
     return fail(c, CMC_EINVAL, "cmc_set_state: bad arguments");
   DeviceGuard g(c->device);
   c->poisoned = false;
-  // a new state drops the stellar radii (they belong to the old order)
+  // a new state drops the stellar radii and semi-major axes (they belong
+  // to the old order)
   if (c->R) cudaMemsetAsync(c->R, 0, sizeof(double) * (size_t)c->L.n, c->stream);
+  if (c->A) cudaMemsetAsync(c->A, 0, sizeof(double) * (size_t)c->L.n, c->stream);
   return load_state(c, r, vr, vt, m, id, ptr_kind, true, step);
 }
 
@@ -1005,37 +1060,38 @@ cmc_status cmc_set_escaped(cmc_ctx* c, const double* in) {
 int32_t cmc_kernels_per_step(const cmc_ctx* c) { return c ? c->kernels_per_step : 0; }
 
 cmc_status cmc_set_radii(cmc_ctx* c, const double* R, int32_t ptr_kind) {
-  if (!c || !R || (ptr_kind != 0 && ptr_kind != 1))
-    return fail(c, CMC_EINVAL, "cmc_set_radii: bad arguments");
-  if (c->poisoned) return fail(c, CMC_EPOISONED, "cmc_set_radii: context poisoned");
-  if (!c->R) return fail(c, CMC_EINVAL, "cmc_set_radii: the context has no collisions");
-  if (ptr_kind == 0)
-    for (int64_t i = 0; i < c->L.n; ++i)
-      if (!(R[i] >= 0.0) || !(R[i] < INFINITY))
-        return fail(c, CMC_EINVAL, "cmc_set_radii: radii must be finite and >= 0");
-  DeviceGuard g(c->device);
-  cudaStream_t st = c->stream;
-  cudaError_t e = cudaMemcpyAsync(c->R, R, sizeof(double) * (size_t)c->L.n,
-                                  ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                                  st);
-  if (!e) e = cudaStreamSynchronize(st);
-  if (e) return cuda_fail(c, e, "cmc_set_radii");
-  return CMC_OK;
+  return attr_set(c, c ? c->R : nullptr, R, ptr_kind, "cmc_set_radii", "collisions");
 }
 
 cmc_status cmc_get_radii(cmc_ctx* c, double* R, int32_t ptr_kind) {
-  if (!c || !R || (ptr_kind != 0 && ptr_kind != 1))
-    return fail(c, CMC_EINVAL, "cmc_get_radii: bad arguments");
-  if (c->poisoned) return fail(c, CMC_EPOISONED, "cmc_get_radii: context poisoned");
-  if (!c->R) return fail(c, CMC_EINVAL, "cmc_get_radii: the context has no collisions");
+  return attr_get(c, c ? c->R : nullptr, R, ptr_kind, "cmc_get_radii", "collisions");
+}
+
+cmc_status cmc_set_binaries(cmc_ctx* c, const double* a, int32_t ptr_kind) {
+  return attr_set(c, c ? c->A : nullptr, a, ptr_kind, "cmc_set_binaries", "binaries");
+}
+
+cmc_status cmc_get_binaries(cmc_ctx* c, double* a, int32_t ptr_kind) {
+  return attr_get(c, c ? c->A : nullptr, a, ptr_kind, "cmc_get_binaries", "binaries");
+}
+
+cmc_status cmc_set_dt_cap(cmc_ctx* c, const double* cap) {
+  if (!c || !cap) return fail(c, CMC_EINVAL, "cmc_set_dt_cap: bad arguments");
+  if (c->poisoned) return fail(c, CMC_EPOISONED, "cmc_set_dt_cap: context poisoned");
+  for (int s = 0; s < c->L.n_seg; ++s)
+    if (!(cap[s] >= 0.0) || !(cap[s] < INFINITY))
+      return fail(c, CMC_EINVAL, "cmc_set_dt_cap: bounds must be finite and >= 0");
   DeviceGuard g(c->device);
-  cudaStream_t st = c->stream;
-  cudaError_t e = cudaMemcpyAsync(R, c->R, sizeof(double) * (size_t)c->L.n,
-                                  ptr_kind ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                                  st);
-  if (!e) e = cudaStreamSynchronize(st);
-  if (e) return cuda_fail(c, e, "cmc_get_radii");
+  cudaError_t e = cudaMemcpyAsync(c->L.dt_cap, cap, sizeof(double) * c->L.n_seg,
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);  // cap lives in the caller's memory
+  if (e) return cuda_fail(c, e, "cmc_set_dt_cap");
   return CMC_OK;
+}
+
+double cmc_tse(double M, double T_prev, double dm_se) {
+  if (!(dm_se > 0.0)) return INFINITY;
+  return ((0.001 * M) * T_prev) / dm_se;
 }
 
 cmc_status cmc_get_tuning(const cmc_ctx* c, int32_t* out) {

@@ -87,6 +87,7 @@ struct Seg {
   const double* lnL;       // ln(gamma N_c), per segment
   int64_t* nb;             // bound stars per segment (device, changes)
   uint64_t* dt_bits;       // timestep per segment as double bits
+  const double* dt_cap;    // per segment: an outside bound on the timestep (0: none)
   unsigned long long* stats;  // kStStride counters per segment
   uint4* taus;             // combined-Tausworthe streams, one per id slot (or null)
   const int64_t* taus_base;  // per segment: first stream slot (slot = base + id)

@@ -36,6 +36,7 @@ struct SegLayout {
   int64_t* esc_step = nullptr;      // stars escaped during the current step
   uint64_t* dt_bits = nullptr;
   uint64_t* dt_last = nullptr;      // timestep of the last completed step
+  double* dt_cap = nullptr;         // outside bounds on the timestep (cmc_set_dt_cap; 0: none)
   unsigned long long* stats = nullptr;
   double* esc_me = nullptr;         // [n_seg][2]: mass, energy carried off by escapers
   uint4* taus = nullptr;            // combined-Tausworthe streams (stream mode only)
@@ -45,7 +46,8 @@ struct SegLayout {
   Seg dev() const {
     Seg s;
     s.off = off; s.tile_off = tile_off; s.pair_off = pair_off; s.bin_off = bin_off;
-    s.seed = seed; s.lnL = lnL; s.nb = nb; s.dt_bits = dt_bits; s.stats = stats;
+    s.seed = seed; s.lnL = lnL; s.nb = nb; s.dt_bits = dt_bits; s.dt_cap = dt_cap;
+    s.stats = stats;
     s.taus = taus; s.taus_base = taus_base;
     s.n_seg = n_seg;
     return s;
@@ -133,7 +135,8 @@ void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* val
                    const Payload* pay, double* r, double* x, double* vr, double* vt,
                    double* m, uint32_t* id, double* r_old, double* c, cudaStream_t st,
                    double* tile_m = nullptr, double* tile_mx = nullptr,
-                   const double* Rp = nullptr, double* Rout = nullptr);
+                   const double* Rp = nullptr, double* Rout = nullptr,
+                   const double* Ap = nullptr, double* Aout = nullptr);
 
 // potential: per-tile sums then the tile-local scans (Eqs. 1-5 in scan
 // form).  nb_sub: subtract esc_step from nb (after the orbit step).
@@ -176,9 +179,12 @@ void launch_bins(const SegLayout& L, const double* r, const double* vr, const do
 void launch_relax(const SegLayout& L, double* vr, double* vt, double* m, const uint32_t* id,
                   const double* nbin, const uint32_t* step, cudaStream_t st, int variant = 0,
                   double* R = nullptr, const double* r = nullptr, const double* phi = nullptr);
-// Eq. 8's collision timestep into the segments' timesteps (R: stellar radii)
-void launch_tcoll(const SegLayout& L, const double* r, const double* vr, const double* vt,
-                  const double* m, const double* R, cudaStream_t st);
+// The timesteps over the innermost 300 bound stars into the segments'
+// timesteps: Eq. 8's collision step (R: stellar radii, may be null) and
+// Eqs. 9-10's binary steps (A: semi-major axes, may be null)
+void launch_tcentral(const SegLayout& L, const double* r, const double* vr, const double* vt,
+                     const double* m, const double* R, const double* A, double x_bb,
+                     double x_bs, cudaStream_t st);
 
 struct OrbitStageOut {   // optional per-star outputs of the orbit stage
   double* phi_new = nullptr;
@@ -271,7 +277,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
                   uint32_t* plist, uint32_t* pcount, cudaStream_t st,
                   bool with_turning = true, const double* Rv = nullptr, double* Rp = nullptr,
-                  double* Fx = nullptr);
+                  double* Fx = nullptr, const double* Av = nullptr, double* Ap = nullptr);
 // the turning-point kernel alone (mixed mode; launch_orbit(..., false)
 // then runs the sampling kernel only)
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,

@@ -64,6 +64,15 @@ __global__ void __launch_bounds__(256) k_bins(Seg S, int bs, double pref, const 
       }
     }
     nbin[b] = n;
+    // an outside bound on the segment's timestep (Eq. 11's stellar-evolution
+    // step, say), with its first bin
+    if (lb == 0 && S.dt_cap) {
+      const double cap = S.dt_cap[c];
+      if (cap > 0.0 && cap < __longlong_as_double(0x7FF0000000000000ll)) {
+        const unsigned long long cb = (unsigned long long)__double_as_longlong(cap);
+        tb = cb < tb ? cb : tb;
+      }
+    }
   }
   // positive doubles order like their bit patterns: min over the block for
   // the block's first segment, direct atomics for any other segment
@@ -238,14 +247,21 @@ __global__ void k_taus_init(int64_t slots, int n_seg, const int64_t* base, const
   table[e] = make_uint4(v[0], v[1], v[2], v[3]);
 }
 
-// Eq. 8's collision timestep over the innermost P = min(300, nb) bound stars
-// of each segment (one warp per segment, one lane summing in star order, as
-// the FP64 statement of the method does), into the segment's timestep (the
-// minimum with Eq. 7's):
+// The timesteps over the innermost P = min(300, nb) bound stars of each
+// segment (one thread per segment summing in star order, as the FP64
+// statement of the method does), into the segment's timestep (the minimum
+// with Eq. 7's).  With stellar radii R, Eq. 8's collision timestep
 //   1 / T_coll = 16 sqrt(pi) n_s <R^2> sigma (1 + G <M R> / (2 sigma^2 <R^2>)),
 // n_s = 3 (P - 1) / (4 pi (r_{P-1}^3 - r_0^3)), sigma^2 = <v_r^2 + v_t^2> / 3.
-__global__ void k_tcoll(Seg S, const double* r, const double* vr, const double* vt,
-                        const double* m, const double* R) {
+// With binaries (semi-major axes A > 0, the star's mass the binary's),
+// Eqs. 9 and 10:
+//   1 / T_bb = 16 sqrt(pi) n_b X_bb^2 <a^2> sigma (1 + G <M a> / (2 sigma^2 X_bb <a^2>))
+//   1 / T_bs = 4 sqrt(pi) n_s X_bs^2 <a^2> sigma (1 + G <M> <a> / (sigma^2 X_bs <a^2>))
+// with n_b, n_s the central density times the binaries' and singles' shares
+// of the P stars, <a^2>, <M a>, <a> over the binaries, <M> over all P.
+__global__ void k_tcentral(Seg S, const double* r, const double* vr, const double* vt,
+                           const double* m, const double* R, const double* A, double x_bb,
+                           double x_bs) {
   const int c = blockIdx.x;
   if (threadIdx.x != 0 || c >= S.n_seg) return;
   const int64_t nb = S.nb[c], sb = S.off[c];
@@ -255,23 +271,62 @@ __global__ void k_tcoll(Seg S, const double* r, const double* vr, const double* 
   const double vol = rr[P - 1] * rr[P - 1] * rr[P - 1] - rr[0] * rr[0] * rr[0];
   if (!(vol > 0.0)) return;
   const double ns = (3.0 * (double)(P - 1)) / ((4.0 * kPi) * vol);
-  double sv = 0.0, sr = 0.0, smr = 0.0;
-  for (int64_t k = 0; k < P; ++k) {
-    const int64_t p = sb + k;
-    sv = sv + (vr[p] * vr[p] + vt[p] * vt[p]);
-    sr = sr + R[p] * R[p];
-    smr = smr + m[p] * R[p];
+  const double inf = __longlong_as_double(0x7FF0000000000000ll);
+  double Tmin = inf;
+  if (R) {
+    double sv = 0.0, sr = 0.0, smr = 0.0;
+    for (int64_t k = 0; k < P; ++k) {
+      const int64_t p = sb + k;
+      sv = sv + (vr[p] * vr[p] + vt[p] * vt[p]);
+      sr = sr + R[p] * R[p];
+      smr = smr + m[p] * R[p];
+    }
+    const double sig2 = (sv / (double)P) / 3.0;
+    const double R2 = sr / (double)P;
+    const double MR = smr / (double)P;
+    if (R2 > 0.0 && sig2 > 0.0) {
+      const double sig = sqrt(sig2);
+      double inv = (((16.0 * sqrt(kPi)) * ns) * R2) * sig;
+      inv = inv * (1.0 + MR / ((2.0 * sig2) * R2));
+      const double T = 1.0 / inv;
+      if (T < Tmin) Tmin = T;
+    }
   }
-  const double sig2 = (sv / (double)P) / 3.0;
-  const double R2 = sr / (double)P;
-  const double MR = smr / (double)P;
-  if (!(R2 > 0.0) || !(sig2 > 0.0)) return;
-  const double sig = sqrt(sig2);
-  double inv = (((16.0 * sqrt(kPi)) * ns) * R2) * sig;
-  inv = inv * (1.0 + MR / ((2.0 * sig2) * R2));
-  const double T = 1.0 / inv;
-  if (T < __longlong_as_double(0x7FF0000000000000ll))
-    atomicMin((unsigned long long*)(S.dt_bits + c), (unsigned long long)__double_as_longlong(T));
+  if (A) {
+    int64_t nbin = 0;
+    double sv = 0.0, sm = 0.0, sa = 0.0, sa2 = 0.0, sma = 0.0;
+    for (int64_t k = 0; k < P; ++k) {
+      const int64_t p = sb + k;
+      sv = sv + (vr[p] * vr[p] + vt[p] * vt[p]);
+      sm = sm + m[p];
+      if (A[p] > 0.0) {
+        nbin += 1;
+        sa = sa + A[p];
+        sa2 = sa2 + A[p] * A[p];
+        sma = sma + m[p] * A[p];
+      }
+    }
+    const double sig2 = (sv / (double)P) / 3.0;
+    if (nbin > 0 && sig2 > 0.0) {
+      const double sig = sqrt(sig2);
+      const double a2 = sa2 / (double)nbin, ma = sma / (double)nbin, am = sa / (double)nbin;
+      const double mm = sm / (double)P;
+      const double nbd = ns * ((double)nbin / (double)P);
+      const double nsd = ns * ((double)(P - nbin) / (double)P);
+      if (nbin < P) {
+        double inv = (((4.0 * sqrt(kPi)) * nsd) * ((x_bs * x_bs) * a2)) * sig;
+        inv = inv * (1.0 + (mm * am) / ((sig2 * x_bs) * a2));
+        const double T = 1.0 / inv;
+        if (T < Tmin) Tmin = T;
+      }
+      double inv = (((16.0 * sqrt(kPi)) * nbd) * ((x_bb * x_bb) * a2)) * sig;
+      inv = inv * (1.0 + ma / (((2.0 * sig2) * x_bb) * a2));
+      const double T = 1.0 / inv;
+      if (T < Tmin) Tmin = T;
+    }
+  }
+  if (Tmin < inf)
+    atomicMin((unsigned long long*)(S.dt_bits + c), (unsigned long long)__double_as_longlong(Tmin));
 }
 
 }  // namespace
@@ -283,10 +338,11 @@ void launch_taus_init(int64_t slots, int n_seg, const int64_t* base, const uint4
                                                                  table);
 }
 
-void launch_tcoll(const SegLayout& L, const double* r, const double* vr, const double* vt,
-                  const double* m, const double* R, cudaStream_t st) {
-  if (!L.n || !R) return;
-  k_tcoll<<<(unsigned)L.n_seg, 32, 0, st>>>(L.dev(), r, vr, vt, m, R);
+void launch_tcentral(const SegLayout& L, const double* r, const double* vr, const double* vt,
+                     const double* m, const double* R, const double* A, double x_bb,
+                     double x_bs, cudaStream_t st) {
+  if (!L.n || (!R && !A)) return;
+  k_tcentral<<<(unsigned)L.n_seg, 32, 0, st>>>(L.dev(), r, vr, vt, m, R, A, x_bb, x_bs);
 }
 
 void launch_bins(const SegLayout& L, const double* r, const double* vr, const double* vt,

@@ -1246,7 +1246,8 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
                                                OrbitStageOut dbg, BucketArgs BA,
                                                const double* tp_min, const double* tp_max,
                                                int64_t n, const double* Rv, double* Rp,
-                                               const double* Fx) {
+                                               const double* Fx, const double* Av,
+                                               double* Ap) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int c = seg_find(S.off, S.n_seg, p);
@@ -1263,6 +1264,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
   bool escaped = false;
 
   if (Rp) Rp[p] = Rv[p];  // the stellar radius goes with the star
+  if (Ap) Ap[p] = Av[p];  // and the binary's semi-major axis
   if (k >= nbc) {
     // escaped in an earlier step: stays at the end, ordered by id
     keys[p] = radius_key(rk, idk);
@@ -1852,7 +1854,8 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
                   uint32_t* plist, uint32_t* pcount, cudaStream_t st, bool with_turning,
-                  const double* Rv, double* Rp, double* Fx) {
+                  const double* Rv, double* Rp, double* Fx, const double* Av,
+                  double* Ap) {
   if (!L.n) return;
   OrbitStageOut d;
   if (dbg) d = *dbg;
@@ -1869,7 +1872,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
 #define CMC_ORBIT(P, B, T)                                                                  \
   k_orbit<P, B, T><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, Menc, vr, vt, \
                                            m, id, step, keys, pay, L.esc_step, d, ba, tp_min, \
-                                           tp_max, L.n, Rv, Rp, Fx)
+                                           tp_max, L.n, Rv, Rp, Fx, Av, Ap)
 #define CMC_SAMPLED(B, T, X)                                                                \
   do {                                                                                      \
     if (with_turning) CMC_TURN(B);                                                          \

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_sums(
     Seg S, const int64_t* esc, int64_t n, const uint64_t* __restrict__ keys,
     const uint32_t* __restrict__ vals, const Payload* __restrict__ pay, double* r, double* x,
     double* vr, double* vt, double* m, uint32_t* id, double* r_old, double* c, double* tile_m,
-    double* tile_mx, const double* Rp, double* Rout) {
+    double* tile_mx, const double* Rp, double* Rout, const double* Ap, double* Aout) {
   __shared__ double s[kThreads];
   TR R = tile_of(S, esc, blockIdx.x, true);
   double am = 0.0, ax = 0.0;
@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_gather_sums(
     r_old[p] = P.r_old;
     c[p] = P.c;
     if (Rout) Rout[p] = Rp[v];
+    if (Aout) Aout[p] = Ap[v];
     if (p < R.bound_end) {
       am = am + P.m;
       ax = ax + P.m * xx;
@@ -866,6 +867,7 @@ cudaError_t alloc_layout(SegLayout& L, const std::vector<int64_t>& sizes,
   CMC_A(L.dt_last, sizeof(uint64_t) * L.n_seg);
   CMC_A(L.stats, sizeof(unsigned long long) * kStStride * L.n_seg);
   CMC_A(L.esc_me, sizeof(double) * 2 * L.n_seg);
+  CMC_A(L.dt_cap, sizeof(double) * L.n_seg);
 #undef CMC_A
   cudaMemcpyAsync(L.off, L.h_off.data(), s1, cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(L.tile_off, L.h_tile_off.data(), s1, cudaMemcpyHostToDevice, st);
@@ -881,13 +883,14 @@ cudaError_t alloc_layout(SegLayout& L, const std::vector<int64_t>& sizes,
   cudaMemcpyAsync(L.dt_last, inf.data(), sizeof(uint64_t) * L.n_seg, cudaMemcpyHostToDevice, st);
   cudaMemsetAsync(L.stats, 0, sizeof(unsigned long long) * kStStride * L.n_seg, st);
   cudaMemsetAsync(L.esc_me, 0, sizeof(double) * 2 * L.n_seg, st);
+  cudaMemsetAsync(L.dt_cap, 0, sizeof(double) * L.n_seg, st);
   // the host vectors above must outlive the copies
   return cudaStreamSynchronize(st);
 }
 
 void free_layout(SegLayout& L, cudaStream_t st) {
   void* ps[] = {L.off, L.tile_off, L.pair_off, L.bin_off, L.seed, L.lnL,
-                L.nb, L.esc_step, L.dt_bits, L.dt_last, L.stats, L.esc_me};
+                L.nb, L.esc_step, L.dt_bits, L.dt_last, L.stats, L.esc_me, L.dt_cap};
   for (void* p : ps)
     if (p) cudaFreeAsync(p, st);
   L = SegLayout();
@@ -911,12 +914,14 @@ void launch_rekey_radius(const SegLayout& L, const uint32_t* perm, const double*
 void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* vals,
                    const Payload* pay, double* r, double* x, double* vr, double* vt,
                    double* m, uint32_t* id, double* r_old, double* c, cudaStream_t st,
-                   double* tile_m, double* tile_mx, const double* Rp, double* Rout) {
+                   double* tile_m, double* tile_mx, const double* Rp, double* Rout,
+                   const double* Ap, double* Aout) {
   if (!L.n) return;
   if (tile_m && tile_mx && r_old && c && L.n_tiles)
     k_gather_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(L.dev(), L.esc_step, L.n, keys, vals,
                                                             pay, r, x, vr, vt, m, id, r_old, c,
-                                                            tile_m, tile_mx, Rp, Rout);
+                                                            tile_m, tile_mx, Rp, Rout, Ap,
+                                                            Aout);
   else
     k_gather<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, keys, vals, pay, r, x, vr, vt, m, id,
                                                   r_old, c);

@@ -1,5 +1,5 @@
 """The C-ABI library builds for sm_103a, loads, and exports every function
-that include/cmc.h declares (no GPU needed: nothing is computed)."""
+that include/cmc.h declares (no GPU needed: no device work)."""
 import ctypes
 import os
 import re
@@ -74,3 +74,18 @@ def test_release_build_has_no_debug_checks(libpath):
     assert lib.cmc_debug_check(ctypes.byref(site)) == 0 and site.value == 0
     assert lib.cmc_debug_check(None) == _native.CMC_EINVAL
     assert _build.LIB_DEBUG != _build.LIB
+
+
+def test_stellar_evolution_timestep_is_the_oracles(libpath):
+    """cmc_tse is host arithmetic: Eq. 11 as the oracle writes it, to the
+    bit, +inf without mass loss."""
+    import math
+
+    import oracle
+    lib = ctypes.CDLL(libpath)
+    lib.cmc_tse.restype = ctypes.c_double
+    lib.cmc_tse.argtypes = [ctypes.c_double] * 3
+    for M, T, dm in ((0.83, 0.02, 3e-5), (1.0, 17.3, 0.25), (5e4, 1e-3, 7.0)):
+        assert lib.cmc_tse(M, T, dm) == oracle.tse(M, T, dm)
+    assert lib.cmc_tse(1.0, 1.0, 0.0) == math.inf
+    assert lib.cmc_tse(1.0, 1.0, -1.0) == math.inf
