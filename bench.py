@@ -135,6 +135,23 @@ def profiled_traffic_per_star(kernel: str, precision: str):
     return None
 
 
+def profiled_fp64_pipe(kernel: str):
+    """The FP64 pipe's active fraction in one kernel from the committed ncu
+    counter summary (N = 4e6, mixed), or None when a kernel source changed
+    since it was taken."""
+    path = os.path.join(ROOT, "profiles", "kernels_counters_N4e6_mixed.md")
+    if not os.path.exists(path):
+        return None
+    src, val = None, None
+    with open(path) as f:
+        for line in f:
+            if line.startswith("source_hash:"):
+                src = line.split(":", 1)[1].strip()
+            if line.startswith("fp64_pipe_pct_%s:" % kernel):
+                val = float(line.split(":", 1)[1]) / 100.0
+    return val if val is not None and src == kernel_source_hash() else None
+
+
 # Compulsory HBM bytes per star of each stage's kernels (table probes and
 # scratch between the kernels of one stage not counted), and the kernel
 # that carries the stage (mixed mode).
@@ -541,6 +558,8 @@ def run_cmc(args, rank, world, local_rank):
             "hbm_frac_dram": None if traffic_ps is None
             else traffic_ps * n / (dom_ms / 1e3) / 1e9 / hbm,
             "hbm_peak_gbs": hbm, "hbm_peak_source": peak_kind,
+            # what bounds it: the FP64 pipe's active fraction (ncu, N = 4e6)
+            "fp64_pipe_active_ncu": profiled_fp64_pipe(kname),
             "note": "FP64 operations of the kernel's formulas (+, -, x, /, sqrt once each); "
                     "compiled without FMA contraction for bit-exact parity, so half the FMA "
                     "peak is the issue ceiling, and / and sqrt take several FP64 issues each"}
