@@ -40,7 +40,7 @@ struct cmc_ctx {
   uint32_t* err = nullptr;
   uint32_t* step = nullptr;
   uint32_t* pcount = nullptr;  // pending stars of the sampled orbit step
-  double* Fx = nullptr;        // FP64 mode's envelope F of every star (precision 0)
+  EnvWork env;                 // FP64 mode's envelope (precision 0)
   double* ring = nullptr;      // per-step diagnostics (cfg.diag_ring records per cluster)
   int64_t steps_taken = 0;
   cudaGraphExec_t exec = nullptr;
@@ -236,7 +236,7 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
                tab ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
                c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
                c->bk.args(), c->r_old, c->cc, c->vals, c->pcount, st, false, c->R, c->Rp,
-               c->Fx, c->A, c->Ap);
+               c->cfg.precision == 0 ? &c->env : nullptr, c->A, c->Ap);
   mark(4);
   // radix passes over bits 24-63 of the radius keys; runs equal in those
   // bits (radii within 2^-28 of each other, escapers whose ids differ in
@@ -285,10 +285,11 @@ int count_step_kernels(const cmc_ctx* c) {
   // bins, relax, orbit, upsweep (with the histograms' scans), 5 passes, tie fix, gather with
   // the tile sums, potential, [precision 0 and 1: turning points, FP32
   // sampler, FP64 continuation, the tables' parameters, the grid's values
-  // with the seams' slopes; precision 0: the envelope], [correction], step end
+  // with the seams' slopes; precision 0: the envelope's screen and
+  // evaluation], [correction], step end
   const int p = c->cfg.precision;
   return 3 + ((c->R || c->A) ? 1 : 0) + (c->ring ? 4 : 0) + 1 + 5 + 1 + 1 + 1 +
-         (p == 1 ? 5 : p == 0 ? 6 : 0) +
+         (p == 1 ? 5 : p == 0 ? 7 : 0) +
          (c->cfg.energy_correction ? 1 : 0) + 1;
 }
 
@@ -312,7 +313,7 @@ void free_ctx(cmc_ctx* c) {
   dfree(c->err, st);
   dfree(c->step, st);
   dfree(c->pcount, st);
-  dfree(c->Fx, st);
+  free_env(c->env, st);
   dfree(c->ring, st);
   free_sort(c->W, st);
   free_buckets(c->bk, st);
@@ -506,7 +507,8 @@ cmc_status autotune(cmc_ctx* c) {
     launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                  tab ? c->Mbuf : nullptr, c->vr, c->vt, c->m,
                  c->id, c->step, c->keys, c->pay, nullptr, blk, var, c->bk.args(), c->r_old,
-                 c->cc, c->vals, c->pcount, st, true, nullptr, nullptr, c->Fx);
+                 c->cc, c->vals, c->pcount, st, true, nullptr, nullptr,
+                 c->cfg.precision == 0 ? &c->env : nullptr);
   };
   auto time_it = [&](auto&& fn) {
     float best = 3.4e38f;
@@ -711,7 +713,7 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   CMC_ALLOC(c->phi, n);
   CMC_ALLOC(c->id, n);
   if (cfg.precision != 2) CMC_ALLOC(c->t32, n);
-  if (cfg.precision == 0) CMC_ALLOC(c->Fx, n);
+  if (!e && cfg.precision == 0) e = alloc_env(c->env, (int64_t)n, st);
   if (cfg.diag_ring > 0) {
     CMC_ALLOC(c->ring, (size_t)n_clusters * cfg.diag_ring * kDiagFields);
     if (!e) e = cudaMemsetAsync(c->ring, 0, sizeof(double) * (size_t)n_clusters *
@@ -1307,19 +1309,20 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
     }
     OrbitStageOut d;
     d.phi_new = phi_new; d.rmin = rmin; d.rmax = rmax; d.F = F; d.code = code;
-    double *tmin = nullptr, *tmax = nullptr, *Fx = nullptr;
+    double *tmin = nullptr, *tmax = nullptr;
+    EnvWork env;
     uint32_t *plist = nullptr, *pcnt = nullptr;
     if (!e && tab) e = dalloc(tmin, n, st);
     if (!e && tab) e = dalloc(tmax, n, st);
     if (!e && tab) e = dalloc(plist, n, st);
     if (!e && tab) e = dalloc(pcnt, 1, st);
-    if (!e && precision == 0) e = dalloc(Fx, n, st);
+    if (!e && precision == 0) e = alloc_env(env, n, st);
     if (!e)
       launch_orbit(S.L, precision, max_trials, r, x, phi, sl, vr, vt, mm, id, dstep, keys,
                    pay, &d, 0, 0, bk.args(), tmin, tmax, plist, pcnt, st, true, nullptr,
-                   nullptr, Fx);
+                   nullptr, precision == 0 ? &env : nullptr);
     free_buckets(bk, st);
-    dfree(Fx, st);
+    free_env(env, st);
     dfree(sl, st);
     dfree(tmin, st);
     dfree(tmax, st);

@@ -261,14 +261,29 @@ void launch_potential_tables(const SegLayout& L, const double* r, const double* 
 // FP32 sampler, FP64 continuation of the pending stars, finishing) and
 // needs two scratch arrays of n doubles (tp_min, tp_max: the turning
 // points), a list of n uint32 (the pending stars) and one uint32 counter.
-// precision 0 (FP64): the same kernels with FP64 mode's envelope (one more
-// kernel, into Fx: n doubles) and FP64 mode's points, every decision the
-// FP64 one.  precision 2 (FP64 by bisection): one kernel on the FP64 table.
+// precision 0 (FP64): the same kernels with FP64 mode's envelope (two more
+// kernels, into an EnvWork) and FP64 mode's points, every decision the FP64
+// one.  precision 2 (FP64 by bisection): one kernel on the FP64 table.
 void launch_slopes(int64_t n, const double* x, const double* phi, double* Menc,
                    cudaStream_t st);
 // one diagnostics record per segment (after the step end; K, W in out3)
 void launch_diag_ring(const SegLayout& L, const double* out3, const uint32_t* step,
                       const uint32_t* err, double* ring, int cap, cudaStream_t st);
+// FP64 mode's envelope F = 1.2 max_j g(s_j): gmax (n doubles) the maximum
+// per star; the (star, sample) pairs that FP32 bounds cannot rule out, each
+// evaluated in FP64 by one thread (list: cap entries p << 5 | j); the stars
+// whose pairs found the list full (spill: n entries p << 21 | sample mask);
+// cnt[0] pairs, cnt[1] spilled stars
+struct EnvWork {
+  double* gmax = nullptr;
+  uint64_t* list = nullptr;
+  uint64_t* spill = nullptr;
+  unsigned long long* cnt = nullptr;
+  int64_t cap = 0;
+};
+cudaError_t alloc_env(EnvWork& W, int64_t n, cudaStream_t st);
+void free_env(EnvWork& W, cudaStream_t st);
+
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
                   const double* x, const double* phi, const double* Menc,
                   const double* vr,
@@ -277,7 +292,8 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
                   uint32_t* plist, uint32_t* pcount, cudaStream_t st,
                   bool with_turning = true, const double* Rv = nullptr, double* Rp = nullptr,
-                  double* Fx = nullptr, const double* Av = nullptr, double* Ap = nullptr);
+                  const EnvWork* env = nullptr, const double* Av = nullptr,
+                  double* Ap = nullptr);
 // the turning-point kernel alone (mixed mode; launch_orbit(..., false)
 // then runs the sampling kernel only)
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,

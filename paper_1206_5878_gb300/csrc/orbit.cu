@@ -902,13 +902,16 @@ __constant__ float c_s32[21] = {CMC_SJ21(CMC_SJF)};
 // whose upper bound reaches the largest lower bound, and those FP32 cannot
 // bound, can hold the maximum, and only they are evaluated in FP64.  Nearly
 // circular orbits have a flat g and FP32 bounds too loose to rank their
-// samples, so the candidates per star range from 1 to 21: each warp pools
-// its lanes' (star, sample) candidates and evaluates them 32 at a time
-// (shell from the bucket index made exact on the node records), the
-// maximum per star kept in shared memory as bits (g >= 0 orders as its
-// bits).  F = 0 for stars without an orbit to sample (r_max <= r_min: every
-// g is 0 or negative there).
+// samples, so the candidates per star range from 1 to 21 (about 1.1 on
+// average).  Two kernels: k_env_screen bounds the samples and lists the
+// candidate (star, sample) pairs; k_env_eval evaluates them one pair per
+// thread (whole warps busy, where one warp pooling its own stars' pairs
+// left most lanes idle in its last round), the maximum per star kept in
+// gmax as bits (g >= 0 orders as its bits).  gmax = 0 for stars without an
+// orbit to sample (r_max <= r_min: every g is 0 or negative there); the
+// readers take F = 1.2 gmax.
 constexpr int kEnvThreads = 128;
+constexpr uint64_t kEnvNone = ~0ull;  // a list slot left empty
 
 // FP64 g at sample j of a star (the noinline quotients keep this copy small)
 __device__ __noinline__ double g64_sample(const double4_32a* __restrict__ nd, int64_t nb,
@@ -925,32 +928,51 @@ __device__ __noinline__ double g64_sample(const double4_32a* __restrict__ nd, in
   return g_of_point(c1, c_s64[j], Q);
 }
 
-__global__ void __launch_bounds__(kEnvThreads) k_envelope64(Seg S, const double* r,
+__device__ __forceinline__ Buckets buckets_of(const BucketArgs& BA, int c) {
+  Buckets BK;
+  const int4 pr = BA.prm[c];
+  BK.start = BA.start + BA.off[c];
+  BK.base = BA.base[c];
+  BK.shift = pr.x;
+  BK.nbk = pr.y;
+  BK.lo = pr.z;
+  BK.hi = pr.w;
+  return BK;
+}
+
+// E, J and the orbit's c0 = (r_max + r_min) / 2, c1 = (r_max - r_min) / 4
+// of star p (segment c); false where there is no orbit to sample
+__device__ __forceinline__ bool env_star(const Seg& S, const double* r, const double* phi,
+                                         const double* vr, const double* vt,
+                                         const double* tp_min, const double* tp_max, int64_t p,
+                                         int& c, double& E, double& J, double& c0, double& c1) {
+  c = seg_find(S.off, S.n_seg, p);
+  const int64_t nbc = S.nb[c], k = p - S.off[c];
+  const double vrk = vr[p], vtk = vt[p];
+  E = __ldg(phi + p) + scale_down<1>(vrk * vrk + vtk * vtk);
+  J = r[p] * vtk;
+  const double rmin = k < nbc ? __ldg(tp_min + p) : 0.0;
+  const double rmax = k < nbc ? __ldg(tp_max + p) : 0.0;
+  if (!(k < nbc && lt0(E) && gt_pos(rmax, rmin))) return false;
+  c0 = scale_down<1>(rmax + rmin);
+  c1 = scale_down<2>(rmax - rmin);
+  return true;
+}
+
+__global__ void __launch_bounds__(kEnvThreads) k_env_screen(Seg S, const double* r,
                                                             const double* phi, const double* vr,
                                                             const double* vt, BucketArgs BA,
                                                             const double* tp_min,
-                                                            const double* tp_max, double* Fx,
+                                                            const double* tp_max, EnvWork W,
                                                             int64_t n) {
-  __shared__ unsigned long long s_gmax[kEnvThreads];
   __shared__ float s_hi[21][kEnvThreads];  // upper bounds of the samples
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const int wbase = threadIdx.x & ~31;
-  s_gmax[threadIdx.x] = 0ull;
   int c = -1;
-  double E = 0.0, J = 0.0, c0 = 0.0, c1 = 0.0;
   unsigned cand = 0u;
   if (p < n) {
-    c = seg_find(S.off, S.n_seg, p);
-    const int64_t nbc = S.nb[c], k = p - S.off[c];
-    const double vrk = vr[p], vtk = vt[p];
-    E = __ldg(phi + p) + scale_down<1>(vrk * vrk + vtk * vtk);
-    J = r[p] * vtk;
-    const double rmin = k < nbc ? __ldg(tp_min + p) : 0.0;
-    const double rmax = k < nbc ? __ldg(tp_max + p) : 0.0;
-    if (k < nbc && lt0(E) && gt_pos(rmax, rmin)) {
-      c0 = scale_down<1>(rmax + rmin);
-      c1 = scale_down<2>(rmax - rmin);
+    double E, J, c0, c1;
+    if (env_star(S, r, phi, vr, vt, tp_min, tp_max, p, c, E, J, c0, c1)) {
       const float c0f = f32_rn(c0), c1f = f32_rn(c1), E32 = f32_rn(E), J32 = f32_rn(J);
       const Grid GD = grid_of(BA, c);
       unsigned pos = 0u;
@@ -976,9 +998,9 @@ __global__ void __launch_bounds__(kEnvThreads) k_envelope64(Seg S, const double*
       for (int jj = 0; jj < 21; ++jj)
         if (((pos >> jj) & 1u) && s_hi[jj][threadIdx.x] >= lo_max) cand |= 1u << jj;
     }
+    W.gmax[p] = 0.0;
   }
-  __syncwarp();
-  // the warp's candidates, numbered lane by lane
+  // the warp's pairs go to the list in lane order, with one atomic
   const unsigned cnt = (unsigned)__popc(cand);
   unsigned incl = cnt;
 #pragma unroll
@@ -987,48 +1009,100 @@ __global__ void __launch_bounds__(kEnvThreads) k_envelope64(Seg S, const double*
     if (lane >= o) incl += v;
   }
   const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
-  for (unsigned t0 = 0; t0 < total; t0 += 32) {
-    const unsigned t = t0 + (unsigned)lane;
-    // owner: the first lane whose inclusive count exceeds t
-    int own = 0;
-#pragma unroll
-    for (int step = 16; step > 0; step >>= 1) {
-      const unsigned v = __shfl_sync(0xFFFFFFFFu, incl, own + step - 1);
-      if (v <= t) own += step;
-    }
-    const unsigned o_incl = __shfl_sync(0xFFFFFFFFu, incl, own);
-    const unsigned o_cnt = __shfl_sync(0xFFFFFFFFu, cnt, own);
-    const unsigned o_cand = __shfl_sync(0xFFFFFFFFu, cand, own);
-    const int o_c = __shfl_sync(0xFFFFFFFFu, c, own);
-    const double o_E = __shfl_sync(0xFFFFFFFFu, E, own);
-    const double o_J = __shfl_sync(0xFFFFFFFFu, J, own);
-    const double o_c0 = __shfl_sync(0xFFFFFFFFu, c0, own);
-    const double o_c1 = __shfl_sync(0xFFFFFFFFu, c1, own);
-    if (t < total) {
-      const int rank = (int)(t - (o_incl - o_cnt));  // which of the owner's candidates
-      const int jj = (int)__fns(o_cand, 0u, rank + 1);
-      const int64_t sb = S.off[o_c], nbc = S.nb[o_c];
-      Buckets BK;
-      const int4 pr = BA.prm[o_c];
-      BK.start = BA.start + BA.off[o_c];
-      BK.base = BA.base[o_c];
-      BK.shift = pr.x;
-      BK.nbk = pr.y;
-      BK.lo = pr.z;
-      BK.hi = pr.w;
-      const double g = g64_sample(BA.node + sb, nbc, BK, o_E, o_J, o_c0, o_c1, jj);
-      if (g > 0.0)
-        atomicMax(&s_gmax[wbase + own], (unsigned long long)__double_as_longlong(g));
+  if (total) {
+    unsigned long long base = 0ull;
+    if (lane == 0) base = atomicAdd(W.cnt, (unsigned long long)total);
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    const unsigned long long cap = (unsigned long long)W.cap;
+    if (base + total <= cap) {
+      unsigned long long at = base + (incl - cnt);
+      for (unsigned m = cand; m; m &= m - 1u)
+        W.list[at++] = ((uint64_t)p << 5) | (uint64_t)(__ffs(m) - 1);
+    } else {
+      // the list is full: its slots reserved here stay empty, and the
+      // stars go to the spill list (one entry per star, never full)
+      for (unsigned long long e = base + lane; e < base + total && e < cap; e += 32)
+        W.list[e] = kEnvNone;
+      if (cnt) {
+        const unsigned long long at = atomicAdd(W.cnt + 1, 1ull);
+        W.spill[at] = ((uint64_t)p << 21) | (uint64_t)cand;
+      }
     }
   }
-  __syncwarp();
-  if (p < n) Fx[p] = 1.2 * __longlong_as_double((long long)s_gmax[threadIdx.x]);
   // FP64 evaluations: one atomic per segment present in the warp
   const unsigned am = __ballot_sync(0xFFFFFFFFu, p < n);
   if (p < n) {
     const unsigned peers = __match_any_sync(am, c);
     const unsigned tot = __reduce_add_sync(peers, cnt);
     if (lane == __ffs(peers) - 1) stat_add(S.stats, c, kStEnvelope64, tot);
+  }
+}
+
+// FP64 g of one listed pair into its star's maximum
+__device__ __forceinline__ void env_pair(const Seg& S, const double* r, const double* phi,
+                                         const double* vr, const double* vt,
+                                         const BucketArgs& BA, const double* tp_min,
+                                         const double* tp_max, double* gmax, int64_t p, int jj) {
+  int c;
+  double E, J, c0, c1;
+  if (!env_star(S, r, phi, vr, vt, tp_min, tp_max, p, c, E, J, c0, c1)) return;
+  const int64_t sb = S.off[c];
+  const Buckets BK = buckets_of(BA, c);
+  const double g = g64_sample(BA.node + sb, S.nb[c], BK, E, J, c0, c1, jj);
+  if (g > 0.0) atomicMax((unsigned long long*)(gmax + p), (unsigned long long)__double_as_longlong(g));
+}
+
+__global__ void __launch_bounds__(kEnvThreads) k_env_eval(Seg S, const double* r,
+                                                          const double* phi, const double* vr,
+                                                          const double* vt, BucketArgs BA,
+                                                          const double* tp_min,
+                                                          const double* tp_max, EnvWork W) {
+  const unsigned long long cap = (unsigned long long)W.cap;
+  const unsigned long long np = W.cnt[0] < cap ? W.cnt[0] : cap;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long e = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; e < np;
+       e += stride) {
+    const uint64_t w = W.list[e];
+    if (w == kEnvNone) continue;
+    env_pair(S, r, phi, vr, vt, BA, tp_min, tp_max, W.gmax, (int64_t)(w >> 5), (int)(w & 31u));
+  }
+  // spilled stars: 32 at a time per warp, each warp pooling their pairs
+  const unsigned long long ns = W.cnt[1];
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warps = stride / 32;
+  for (unsigned long long w0 = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) / 32 * 32;
+       w0 < ns; w0 += warps * 32) {
+    const unsigned long long i = w0 + lane;
+    const uint64_t w = i < ns ? W.spill[i] : 0ull;
+    const unsigned cand = (unsigned)(w & 0x1FFFFFu);
+    const int64_t ps = (int64_t)(w >> 21);
+    const unsigned cnt = (unsigned)__popc(cand);
+    unsigned incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    const unsigned total = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    for (unsigned t0 = 0; t0 < total; t0 += 32) {
+      const unsigned t = t0 + (unsigned)lane;
+      // owner: the first lane whose inclusive count exceeds t
+      int own = 0;
+#pragma unroll
+      for (int step = 16; step > 0; step >>= 1) {
+        const unsigned v = __shfl_sync(0xFFFFFFFFu, incl, own + step - 1);
+        if (v <= t) own += step;
+      }
+      const unsigned o_incl = __shfl_sync(0xFFFFFFFFu, incl, own);
+      const unsigned o_cnt = __shfl_sync(0xFFFFFFFFu, cnt, own);
+      const unsigned o_cand = __shfl_sync(0xFFFFFFFFu, cand, own);
+      const long long o_p = __shfl_sync(0xFFFFFFFFu, (long long)ps, own);
+      if (t < total) {
+        const int rank = (int)(t - (o_incl - o_cnt));  // which of the owner's pairs
+        env_pair(S, r, phi, vr, vt, BA, tp_min, tp_max, W.gmax, (int64_t)o_p,
+                 (int)__fns(o_cand, 0u, rank + 1));
+      }
+    }
   }
 }
 
@@ -1046,7 +1120,7 @@ enum : uint32_t { kSmpAccepted = 0, kSmpPending = 1, kSmpDegenerate = 2, kSmpCap
 // samples is as valid an envelope as the FP64 one (it differs from it by up
 // to ~1e-4 at the outer samples, so the two modes draw different, equally
 // exact, accept sequences).
-// kExact (FP64 mode): F is FP64 mode's envelope from k_envelope64 (Fx),
+// kExact (FP64 mode): F is FP64 mode's envelope, 1.2 Fx (Fx from k_env_eval),
 // and a trial is decided here only where the FP64 decision and violation
 // count are certain.
 template <int kMinB, bool kTaus, bool kExact>
@@ -1076,7 +1150,7 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
       float F32;
       bool degenerate;
       if (kExact) {
-        const double F64 = __ldg(Fx + p);
+        const double F64 = 1.2 * __ldg(Fx + p);
         F32 = f32_rn(F64);
         degenerate = !gt_pos(rmax, rmin) || !(F64 > 0.0);
       } else {
@@ -1132,7 +1206,7 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
 // kSmpAccepted and the accepted trial, or kSmpCap.  Most threads find no
 // pending star and leave at once.
 // one pending star (p = n: an idle lane); counts go to the statistics
-// kExact (FP64 mode): F from Fx, the points and g as FP64 mode's
+// kExact (FP64 mode): F = 1.2 Fx, the points and g as FP64 mode's
 template <bool kTaus, bool kExact>
 __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double* r,
                                              const double* x, const double* phi,
@@ -1168,7 +1242,8 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
         const double c0 = scale_down<1>(rmax + rmin);
         const double c1 = scale_down<2>(rmax - rmin);
         const float c0f = f32_rn(c0), c1f = f32_rn(c1);
-        const double F = kExact ? __ldg(Fx + p) : (double)__uint_as_float((uint32_t)(res >> 32));
+        const double F =
+            kExact ? 1.2 * __ldg(Fx + p) : (double)__uint_as_float((uint32_t)(res >> 32));
         uint32_t st = kSmpCap;
         int t = (int)(res & 0x3FFFFFFFull);
         // stream mode: the blocks of trials 0 .. t-1 were the FP32 sampler's
@@ -1233,7 +1308,7 @@ __global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const 
 // trials all on the FP64 table), 1 mixed (turning points from
 // k_turning_mixed in tp_min, tp_max, FP32 sampler result from k_sample32 /
 // k_pending64 in the key slot), 2 FP64 through the mixed kernels (their
-// FP64 turning points, FP64 mode's envelope from k_envelope64 in Fx, the
+// FP64 turning points, FP64 mode's envelope 1.2 Fx (Fx from k_env_eval), the
 // accepted point as FP64 mode computes it).  kMinB: resident 256-thread
 // blocks to fit (caps registers; 1 = no cap).
 template <int kPrec, int kMinB, bool kTaus>
@@ -1374,7 +1449,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
       const uint64_t res = keys[p];
       const uint32_t st = (uint32_t)(res >> 30) & 3u;
       int t = (int)(res & 0x3FFFFFFFull);
-      F = kPrec == 2 ? __ldg(Fx + p) : (double)__uint_as_float((uint32_t)(res >> 32));
+      F = kPrec == 2 ? 1.2 * __ldg(Fx + p) : (double)__uint_as_float((uint32_t)(res >> 32));
       if (st == kSmpDegenerate) {
         code = 2;
       } else if (st == kSmpCap) {
@@ -1822,6 +1897,23 @@ void launch_buckets(const SegLayout& L, const float2* t32, bool nb_sub, BucketWo
                                                                t32, B.args(), B.start, L.n);
 }
 
+cudaError_t alloc_env(EnvWork& W, int64_t n, cudaStream_t st) {
+  const int64_t m = n > 0 ? n : 1;
+  W.cap = 2 * m + 1024;  // the pairs: 1.1 per star measured on Plummer models
+  cudaError_t e = cudaMallocAsync((void**)&W.gmax, sizeof(double) * m, st);
+  if (!e) e = cudaMallocAsync((void**)&W.list, sizeof(uint64_t) * W.cap, st);
+  if (!e) e = cudaMallocAsync((void**)&W.spill, sizeof(uint64_t) * m, st);
+  if (!e) e = cudaMallocAsync((void**)&W.cnt, 2 * sizeof(unsigned long long), st);
+  return e;
+}
+
+void free_env(EnvWork& W, cudaStream_t st) {
+  void* ps[] = {W.gmax, W.list, W.spill, W.cnt};
+  for (void* q : ps)
+    if (q) cudaFreeAsync(q, st);
+  W = EnvWork();
+}
+
 void launch_correction_mixed(const SegLayout& L, const double* r, const double* x,
                              const double* phi, const double* Menc,
                              const BucketArgs& ba, double* vr, double* vt, const double* r_old,
@@ -1854,10 +1946,16 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   uint64_t* keys, Payload* pay, const OrbitStageOut* dbg, int block,
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
                   uint32_t* plist, uint32_t* pcount, cudaStream_t st, bool with_turning,
-                  const double* Rv, double* Rp, double* Fx, const double* Av,
+                  const double* Rv, double* Rp, const EnvWork* env, const double* Av,
                   double* Ap) {
   if (!L.n) return;
   OrbitStageOut d;
+  EnvWork W;
+  if (env) W = *env;
+  double* Fx = W.gmax;
+  // the envelope's pairs, about 1.1 per star: one thread each (a grid for
+  // 1.25 per star, striding over any more)
+  const unsigned egrid = (unsigned)((L.n + L.n / 4 + kEnvThreads - 1) / kEnvThreads);
   if (dbg) d = *dbg;
   if (block <= 0) block = 64;
   const unsigned grid = (unsigned)((L.n + block - 1) / block);
@@ -1876,9 +1974,12 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
 #define CMC_SAMPLED(B, T, X)                                                                \
   do {                                                                                      \
     if (with_turning) CMC_TURN(B);                                                          \
-    if (X)                                                                                  \
-      k_envelope64<<<(unsigned)((L.n + 127) / 128), 128, 0, st>>>(L.dev(), r, phi, vr, vt, \
-                                                                 ba, tp_min, tp_max, Fx, L.n); \
+    if (X) {                                                                                \
+      cudaMemsetAsync(W.cnt, 0, 2 * sizeof(unsigned long long), st);                        \
+      k_env_screen<<<(unsigned)((L.n + kEnvThreads - 1) / kEnvThreads), kEnvThreads, 0, st>>>( \
+          L.dev(), r, phi, vr, vt, ba, tp_min, tp_max, W, L.n);                              \
+      k_env_eval<<<egrid, kEnvThreads, 0, st>>>(L.dev(), r, phi, vr, vt, ba, tp_min, tp_max, W); \
+    }                                                                                       \
     cudaMemsetAsync(pcount, 0, sizeof(uint32_t), st);                                      \
     k_sample32<B, T, X><<<grid, block, 0, st>>>(L.dev(), max_trials, r, phi, vr, vt, id, step, \
                                                 ba, tp_min, tp_max, keys, plist, pcount, L.n, \
