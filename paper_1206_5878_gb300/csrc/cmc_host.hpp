@@ -270,12 +270,14 @@ void launch_slopes(int64_t n, const double* x, const double* phi, double* Menc,
 void launch_diag_ring(const SegLayout& L, const double* out3, const uint32_t* step,
                       const uint32_t* err, double* ring, int cap, cudaStream_t st);
 // FP64 mode's envelope F = 1.2 max_j g(s_j): gmax (n doubles) the maximum
-// per star; the (star, sample) pairs that FP32 bounds cannot rule out, each
+// per star; star (n records) the values its evaluations share; the (star,
+// sample) pairs that FP32 bounds cannot rule out, each
 // evaluated in FP64 by one thread (list: cap entries p << 5 | j); the stars
 // whose pairs found the list full (spill: n entries p << 21 | sample mask);
 // cnt[0] pairs, cnt[1] spilled stars
 struct EnvWork {
   double* gmax = nullptr;
+  double4_32a* star = nullptr;  // E, J, c0, c1 of each star with pairs
   uint64_t* list = nullptr;
   uint64_t* spill = nullptr;
   unsigned long long* cnt = nullptr;

@@ -414,11 +414,13 @@ __device__ __forceinline__ void point64(const double4_32a* __restrict__ nd, int6
 // statement of the method, as phi_in_shell), L = J / r and Q.  Its
 // quotients go through the shared bodies (div_rn_nl): measured faster in
 // the long kernels that use it.
-__device__ __forceinline__ void point64_div(const double4_32a* __restrict__ nd, int64_t nb,
-                                            const Star& st, double c0, double c1, double sv,
-                                            int sh, double& rs, double& ph, double& Q,
-                                            double& L) {
-  rs = c0 + c1 * (sv * (3.0 - sv * sv));
+// sa = s (3 - s^2), the factor of c1 in r(s) (a table entry at the
+// envelope's samples)
+__device__ __forceinline__ void point64_div_sa(const double4_32a* __restrict__ nd, int64_t nb,
+                                               const Star& st, double c0, double c1, double sa,
+                                               int sh, double& rs, double& ph, double& Q,
+                                               double& L) {
+  rs = c0 + c1 * sa;
   double4_32a a;
   const int64_t i = fix_shell_nodes(nd, nb, sh, rs, a);
   if (i < 0) {
@@ -438,10 +440,21 @@ __device__ __forceinline__ void point64_div(const double4_32a* __restrict__ nd, 
   Q = scale_up<1>(st.E - ph) - L * L;
 }
 
-// g(s) of FP64 mode at the point of point64_div
-__device__ __forceinline__ double g_of_point(double c1, double sv, double Q) {
+__device__ __forceinline__ void point64_div(const double4_32a* __restrict__ nd, int64_t nb,
+                                            const Star& st, double c0, double c1, double sv,
+                                            int sh, double& rs, double& ph, double& Q,
+                                            double& L) {
+  point64_div_sa(nd, nb, st, c0, c1, sv * (3.0 - sv * sv), sh, rs, ph, Q, L);
+}
+
+// g(s) of FP64 mode at the point of point64_div, sb = 1 - s^2
+__device__ __forceinline__ double g_of_point_sb(double c1, double sb, double Q) {
   if (!(Q > 0.0)) return 0.0;
-  return div_rn_nl((3.0 * c1) * (1.0 - sv * sv), sqrt_rn_nl(Q));
+  return div_rn_nl((3.0 * c1) * sb, sqrt_rn_nl(Q));
+}
+
+__device__ __forceinline__ double g_of_point(double c1, double sv, double Q) {
+  return g_of_point_sb(c1, 1.0 - sv * sv, Q);
 }
 
 // (2k + 1) 2^-24 from the top 23 bits of a word: exact in float, in (0, 1)
@@ -913,6 +926,18 @@ __constant__ float c_s32[21] = {CMC_SJ21(CMC_SJF)};
 constexpr int kEnvThreads = 128;
 constexpr uint64_t kEnvNone = ~0ull;  // a list slot left empty
 
+// s_j (3 - s_j^2) and 1 - s_j^2 at the 21 samples, computed once on the
+// device with the operations of point64_div and g_of_point (k_env_tables)
+__device__ double g_env_sa[21], g_env_sb[21];
+
+__global__ void k_env_tables() {
+  const int j = threadIdx.x;
+  if (j >= 21) return;
+  const double sv = c_s64[j];
+  g_env_sa[j] = sv * (3.0 - sv * sv);
+  g_env_sb[j] = 1.0 - sv * sv;
+}
+
 // FP64 g at sample j of a star (the noinline quotients keep this copy small)
 __device__ __noinline__ double g64_sample(const double4_32a* __restrict__ nd, int64_t nb,
                                           const Buckets& BK, double E, double J, double c0,
@@ -923,9 +948,9 @@ __device__ __noinline__ double g64_sample(const double4_32a* __restrict__ nd, in
   s.J = J;
   const float c0f = f32_rn(c0), c1f = f32_rn(c1);
   double rs, ph, Q, L;
-  point64_div(nd, nb, s, c0, c1, c_s64[j], shell32_of(nd, (int)nb, BK, c0f, c1f, c_s32[j]), rs,
-              ph, Q, L);
-  return g_of_point(c1, c_s64[j], Q);
+  point64_div_sa(nd, nb, s, c0, c1, g_env_sa[j],
+                 shell32_of(nd, (int)nb, BK, c0f, c1f, c_s32[j]), rs, ph, Q, L);
+  return g_of_point_sb(c1, g_env_sb[j], Q);
 }
 
 __device__ __forceinline__ Buckets buckets_of(const BucketArgs& BA, int c) {
@@ -973,6 +998,8 @@ __global__ void __launch_bounds__(kEnvThreads) k_env_screen(Seg S, const double*
   if (p < n) {
     double E, J, c0, c1;
     if (env_star(S, r, phi, vr, vt, tp_min, tp_max, p, c, E, J, c0, c1)) {
+      // the star's values for the evaluation of its pairs
+      W.star[p] = make_double4_32a(E, J, c0, c1);
       const float c0f = f32_rn(c0), c1f = f32_rn(c1), E32 = f32_rn(E), J32 = f32_rn(J);
       const Grid GD = grid_of(BA, c);
       unsigned pos = 0u;
@@ -1038,25 +1065,20 @@ __global__ void __launch_bounds__(kEnvThreads) k_env_screen(Seg S, const double*
   }
 }
 
-// FP64 g of one listed pair into its star's maximum
-__device__ __forceinline__ void env_pair(const Seg& S, const double* r, const double* phi,
-                                         const double* vr, const double* vt,
-                                         const BucketArgs& BA, const double* tp_min,
-                                         const double* tp_max, double* gmax, int64_t p, int jj) {
-  int c;
-  double E, J, c0, c1;
-  if (!env_star(S, r, phi, vr, vt, tp_min, tp_max, p, c, E, J, c0, c1)) return;
+// FP64 g of one listed pair into its star's maximum (E, J, c0, c1 from the
+// screening kernel's record of the star)
+__device__ __forceinline__ void env_pair(const Seg& S, const BucketArgs& BA, const EnvWork& W,
+                                         int64_t p, int jj) {
+  const int c = seg_find(S.off, S.n_seg, p);
+  const double4_32a v = W.star[p];
   const int64_t sb = S.off[c];
   const Buckets BK = buckets_of(BA, c);
-  const double g = g64_sample(BA.node + sb, S.nb[c], BK, E, J, c0, c1, jj);
+  double* gmax = W.gmax;
+  const double g = g64_sample(BA.node + sb, S.nb[c], BK, v.x, v.y, v.z, v.w, jj);
   if (g > 0.0) atomicMax((unsigned long long*)(gmax + p), (unsigned long long)__double_as_longlong(g));
 }
 
-__global__ void __launch_bounds__(kEnvThreads) k_env_eval(Seg S, const double* r,
-                                                          const double* phi, const double* vr,
-                                                          const double* vt, BucketArgs BA,
-                                                          const double* tp_min,
-                                                          const double* tp_max, EnvWork W) {
+__global__ void __launch_bounds__(kEnvThreads) k_env_eval(Seg S, BucketArgs BA, EnvWork W) {
   const unsigned long long cap = (unsigned long long)W.cap;
   const unsigned long long np = W.cnt[0] < cap ? W.cnt[0] : cap;
   const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
@@ -1064,7 +1086,7 @@ __global__ void __launch_bounds__(kEnvThreads) k_env_eval(Seg S, const double* r
        e += stride) {
     const uint64_t w = W.list[e];
     if (w == kEnvNone) continue;
-    env_pair(S, r, phi, vr, vt, BA, tp_min, tp_max, W.gmax, (int64_t)(w >> 5), (int)(w & 31u));
+    env_pair(S, BA, W, (int64_t)(w >> 5), (int)(w & 31u));
   }
   // spilled stars: 32 at a time per warp, each warp pooling their pairs
   const unsigned long long ns = W.cnt[1];
@@ -1099,8 +1121,7 @@ __global__ void __launch_bounds__(kEnvThreads) k_env_eval(Seg S, const double* r
       const long long o_p = __shfl_sync(0xFFFFFFFFu, (long long)ps, own);
       if (t < total) {
         const int rank = (int)(t - (o_incl - o_cnt));  // which of the owner's pairs
-        env_pair(S, r, phi, vr, vt, BA, tp_min, tp_max, W.gmax, (int64_t)o_p,
-                 (int)__fns(o_cand, 0u, rank + 1));
+        env_pair(S, BA, W, (int64_t)o_p, (int)__fns(o_cand, 0u, rank + 1));
       }
     }
   }
@@ -1901,14 +1922,19 @@ cudaError_t alloc_env(EnvWork& W, int64_t n, cudaStream_t st) {
   const int64_t m = n > 0 ? n : 1;
   W.cap = 2 * m + 1024;  // the pairs: 1.1 per star measured on Plummer models
   cudaError_t e = cudaMallocAsync((void**)&W.gmax, sizeof(double) * m, st);
+  if (!e) e = cudaMallocAsync((void**)&W.star, sizeof(double4_32a) * m, st);
   if (!e) e = cudaMallocAsync((void**)&W.list, sizeof(uint64_t) * W.cap, st);
   if (!e) e = cudaMallocAsync((void**)&W.spill, sizeof(uint64_t) * m, st);
   if (!e) e = cudaMallocAsync((void**)&W.cnt, 2 * sizeof(unsigned long long), st);
+  if (!e) {
+    k_env_tables<<<1, 32, 0, st>>>();
+    e = cudaGetLastError();
+  }
   return e;
 }
 
 void free_env(EnvWork& W, cudaStream_t st) {
-  void* ps[] = {W.gmax, W.list, W.spill, W.cnt};
+  void* ps[] = {W.gmax, W.star, W.list, W.spill, W.cnt};
   for (void* q : ps)
     if (q) cudaFreeAsync(q, st);
   W = EnvWork();
@@ -1978,7 +2004,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
       cudaMemsetAsync(W.cnt, 0, 2 * sizeof(unsigned long long), st);                        \
       k_env_screen<<<(unsigned)((L.n + kEnvThreads - 1) / kEnvThreads), kEnvThreads, 0, st>>>( \
           L.dev(), r, phi, vr, vt, ba, tp_min, tp_max, W, L.n);                              \
-      k_env_eval<<<egrid, kEnvThreads, 0, st>>>(L.dev(), r, phi, vr, vt, ba, tp_min, tp_max, W); \
+      k_env_eval<<<egrid, kEnvThreads, 0, st>>>(L.dev(), ba, W);                             \
     }                                                                                       \
     cudaMemsetAsync(pcount, 0, sizeof(uint32_t), st);                                      \
     k_sample32<B, T, X><<<grid, block, 0, st>>>(L.dev(), max_trials, r, phi, vr, vt, id, step, \
