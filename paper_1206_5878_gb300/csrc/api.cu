@@ -41,6 +41,7 @@ struct cmc_ctx {
   uint32_t* step = nullptr;
   uint32_t* pcount = nullptr;  // pending stars of the sampled orbit step
   EnvWork env;                 // FP64 mode's envelope (precision 0)
+  double4_32a* orb = nullptr;  // E, J, c0, c1 of every star's orbit (precision 0 and 1)
   double* ring = nullptr;      // per-step diagnostics (cfg.diag_ring records per cluster)
   int64_t steps_taken = 0;
   cudaGraphExec_t exec = nullptr;
@@ -227,16 +228,16 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   launch_relax(L, c->vr, c->vt, c->m, c->id, c->nbin, c->step, st, c->relax_variant, c->R, c->r,
                c->phi);
   mark(2);
-  // turning points into r_old, c (free until the gather), then sampling
+  // the turning points (as the orbit records), then sampling
   if (tab)
-    launch_turning(L, c->r, c->x, c->phi, c->Mbuf, c->vr, c->vt, c->bk.args(), c->r_old,
-                   c->cc, c->cfg.orbit_block, st);
+    launch_turning(L, c->r, c->x, c->phi, c->Mbuf, c->vr, c->vt, c->bk.args(), nullptr,
+                   nullptr, c->orb, c->cfg.orbit_block, st);
   mark(3);
   launch_orbit(L, c->cfg.precision, c->cfg.max_trials, c->r, c->x, c->phi,
                tab ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
                c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
                c->bk.args(), c->r_old, c->cc, c->vals, c->pcount, st, false, c->R, c->Rp,
-               c->cfg.precision == 0 ? &c->env : nullptr, c->A, c->Ap);
+               c->cfg.precision == 0 ? &c->env : nullptr, c->A, c->Ap, c->orb);
   mark(4);
   // radix passes over bits 24-63 of the radius keys; runs equal in those
   // bits (radii within 2^-28 of each other, escapers whose ids differ in
@@ -314,6 +315,7 @@ void free_ctx(cmc_ctx* c) {
   dfree(c->step, st);
   dfree(c->pcount, st);
   free_env(c->env, st);
+  dfree(c->orb, st);
   dfree(c->ring, st);
   free_sort(c->W, st);
   free_buckets(c->bk, st);
@@ -508,7 +510,7 @@ cmc_status autotune(cmc_ctx* c) {
                  tab ? c->Mbuf : nullptr, c->vr, c->vt, c->m,
                  c->id, c->step, c->keys, c->pay, nullptr, blk, var, c->bk.args(), c->r_old,
                  c->cc, c->vals, c->pcount, st, true, nullptr, nullptr,
-                 c->cfg.precision == 0 ? &c->env : nullptr);
+                 c->cfg.precision == 0 ? &c->env : nullptr, nullptr, nullptr, c->orb);
   };
   auto time_it = [&](auto&& fn) {
     float best = 3.4e38f;
@@ -714,6 +716,7 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
   CMC_ALLOC(c->id, n);
   if (cfg.precision != 2) CMC_ALLOC(c->t32, n);
   if (!e && cfg.precision == 0) e = alloc_env(c->env, (int64_t)n, st);
+  if (cfg.precision != 2) CMC_ALLOC(c->orb, n);
   if (cfg.diag_ring > 0) {
     CMC_ALLOC(c->ring, (size_t)n_clusters * cfg.diag_ring * kDiagFields);
     if (!e) e = cudaMemsetAsync(c->ring, 0, sizeof(double) * (size_t)n_clusters *
@@ -1310,22 +1313,25 @@ cmc_status cmc_orbit(int64_t n, const double* r, const double* phi, const double
     OrbitStageOut d;
     d.phi_new = phi_new; d.rmin = rmin; d.rmax = rmax; d.F = F; d.code = code;
     double *tmin = nullptr, *tmax = nullptr;
+    double4_32a* orb = nullptr;
     EnvWork env;
     uint32_t *plist = nullptr, *pcnt = nullptr;
     if (!e && tab) e = dalloc(tmin, n, st);
     if (!e && tab) e = dalloc(tmax, n, st);
+    if (!e && tab) e = dalloc(orb, n, st);
     if (!e && tab) e = dalloc(plist, n, st);
     if (!e && tab) e = dalloc(pcnt, 1, st);
     if (!e && precision == 0) e = alloc_env(env, n, st);
     if (!e)
       launch_orbit(S.L, precision, max_trials, r, x, phi, sl, vr, vt, mm, id, dstep, keys,
                    pay, &d, 0, 0, bk.args(), tmin, tmax, plist, pcnt, st, true, nullptr,
-                   nullptr, precision == 0 ? &env : nullptr);
+                   nullptr, precision == 0 ? &env : nullptr, nullptr, nullptr, orb);
     free_buckets(bk, st);
     free_env(env, st);
     dfree(sl, st);
     dfree(tmin, st);
     dfree(tmax, st);
+    dfree(orb, st);
     dfree(plist, st);
     dfree(pcnt, st);
     launch_unpack_orbit(n, keys, pay, r_new, vr_new, vt_new, st);

@@ -259,8 +259,11 @@ void launch_potential_tables(const SegLayout& L, const double* r, const double* 
 // Menc (precision 0 and 1): the slope of Phi in 1/r across shell k.
 // precision 1 (mixed): launch_orbit runs four kernels (turning points,
 // FP32 sampler, FP64 continuation of the pending stars, finishing) and
-// needs two scratch arrays of n doubles (tp_min, tp_max: the turning
-// points), a list of n uint32 (the pending stars) and one uint32 counter.
+// needs n records orb (E, J, c0 = (r_max + r_min) / 2, c1 = (r_max -
+// r_min) / 4, from the turning-point kernel, for the sampling kernels), a
+// list of n uint32 (the pending stars) and one uint32 counter; tp_min,
+// tp_max (n doubles each: the turning points) only with the stage outputs
+// of dbg (rmin, rmax).
 // precision 0 (FP64): the same kernels with FP64 mode's envelope (two more
 // kernels, into an EnvWork) and FP64 mode's points, every decision the FP64
 // one.  precision 2 (FP64 by bisection): one kernel on the FP64 table.
@@ -295,13 +298,13 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   uint32_t* plist, uint32_t* pcount, cudaStream_t st,
                   bool with_turning = true, const double* Rv = nullptr, double* Rp = nullptr,
                   const EnvWork* env = nullptr, const double* Av = nullptr,
-                  double* Ap = nullptr);
+                  double* Ap = nullptr, double4_32a* orb = nullptr);
 // the turning-point kernel alone (mixed mode; launch_orbit(..., false)
 // then runs the sampling kernel only)
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,
                     const double* Menc, const double* vr, const double* vt,
-                    const BucketArgs& ba, double* tp_min, double* tp_max, int block,
-                    cudaStream_t st);
+                    const BucketArgs& ba, double* tp_min, double* tp_max, double4_32a* orb,
+                    int block, cudaStream_t st);
 // mixed-mode orbit variants: register caps for 1 (none), 2, 3, 4, 5, 6 and
 // 8 resident 256-thread blocks per SM (128, 80, 64, 48, 40 and 32
 // registers; the kernel is latency-bound, and occupancy buys more than the

@@ -776,7 +776,7 @@ template <int kMinB>
 __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
     Seg S, const double* r, const double* x, const double* phi,
     const double* Menc, const double* vr, const double* vt, BucketArgs BA, double* tp_min,
-    double* tp_max, int64_t n) {
+    double* tp_max, double4_32a* orb, int64_t n) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int c = seg_find(S.off, S.n_seg, p);
@@ -793,7 +793,10 @@ __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
   // E < 0 on the bit pattern (negative, nonzero, not NaN); otherwise an
   // escaper, which the sampling kernel handles
   const unsigned long long eb = ubits(s.E);
-  if (!(eb > 0x8000000000000000ull && eb <= 0xFFF0000000000000ull)) return;
+  if (!(eb > 0x8000000000000000ull && eb <= 0xFFF0000000000000ull)) {
+    orb[p] = make_double4_32a(s.E, s.J, 0.0, 0.0);
+    return;
+  }
   double rmin, rmax;
   Buckets BK;
   const int4 pr = BA.prm[c];
@@ -804,8 +807,14 @@ __global__ void __launch_bounds__(256, kMinB) k_turning_mixed(
   BK.lo = pr.z;
   BK.hi = pr.w;
   turning_mixed(T, BA.tdf + sb, BA.node + sb, grid_of(BA, c), BK, s, rmin, rmax);
-  tp_min[p] = rmin;
-  tp_max[p] = rmax;
+  if (tp_min) {
+    tp_min[p] = rmin;
+    tp_max[p] = rmax;
+  }
+  // the orbit's record for the sampling kernels: E, J, c0 = (r_max + r_min)
+  // / 2 and c1 = (r_max - r_min) / 4 (c1 > 0 exactly when r_max > r_min:
+  // radii are far from the underflow range)
+  orb[p] = make_double4_32a(s.E, s.J, scale_down<1>(rmax + rmin), scale_down<2>(rmax - rmin));
 }
 
 // One trial's accept test in FP32 with a bound on its error: +1 accepted,
@@ -966,29 +975,23 @@ __device__ __forceinline__ Buckets buckets_of(const BucketArgs& BA, int c) {
 }
 
 // E, J and the orbit's c0 = (r_max + r_min) / 2, c1 = (r_max - r_min) / 4
-// of star p (segment c); false where there is no orbit to sample
-__device__ __forceinline__ bool env_star(const Seg& S, const double* r, const double* phi,
-                                         const double* vr, const double* vt,
-                                         const double* tp_min, const double* tp_max, int64_t p,
+// of star p (segment c) from the turning-point kernel's record; false where
+// there is no orbit to sample
+__device__ __forceinline__ bool env_star(const Seg& S, const double4_32a* orb, int64_t p,
                                          int& c, double& E, double& J, double& c0, double& c1) {
   c = seg_find(S.off, S.n_seg, p);
   const int64_t nbc = S.nb[c], k = p - S.off[c];
-  const double vrk = vr[p], vtk = vt[p];
-  E = __ldg(phi + p) + scale_down<1>(vrk * vrk + vtk * vtk);
-  J = r[p] * vtk;
-  const double rmin = k < nbc ? __ldg(tp_min + p) : 0.0;
-  const double rmax = k < nbc ? __ldg(tp_max + p) : 0.0;
-  if (!(k < nbc && lt0(E) && gt_pos(rmax, rmin))) return false;
-  c0 = scale_down<1>(rmax + rmin);
-  c1 = scale_down<2>(rmax - rmin);
-  return true;
+  if (!(k < nbc)) return false;
+  const double4_32a o = orb[p];
+  E = o.x;
+  J = o.y;
+  c0 = o.z;
+  c1 = o.w;
+  return lt0(E) && gt_pos(c1, 0.0);
 }
 
-__global__ void __launch_bounds__(kEnvThreads) k_env_screen(Seg S, const double* r,
-                                                            const double* phi, const double* vr,
-                                                            const double* vt, BucketArgs BA,
-                                                            const double* tp_min,
-                                                            const double* tp_max, EnvWork W,
+__global__ void __launch_bounds__(kEnvThreads) k_env_screen(Seg S, BucketArgs BA,
+                                                            const double4_32a* orb, EnvWork W,
                                                             int64_t n) {
   __shared__ float s_hi[21][kEnvThreads];  // upper bounds of the samples
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -997,7 +1000,7 @@ __global__ void __launch_bounds__(kEnvThreads) k_env_screen(Seg S, const double*
   unsigned cand = 0u;
   if (p < n) {
     double E, J, c0, c1;
-    if (env_star(S, r, phi, vr, vt, tp_min, tp_max, p, c, E, J, c0, c1)) {
+    if (env_star(S, orb, p, c, E, J, c0, c1)) {
       // the star's values for the evaluation of its pairs
       W.star[p] = make_double4_32a(E, J, c0, c1);
       const float c0f = f32_rn(c0), c1f = f32_rn(c1), E32 = f32_rn(E), J32 = f32_rn(J);
@@ -1145,11 +1148,10 @@ enum : uint32_t { kSmpAccepted = 0, kSmpPending = 1, kSmpDegenerate = 2, kSmpCap
 // and a trial is decided here only where the FP64 decision and violation
 // count are certain.
 template <int kMinB, bool kTaus, bool kExact>
-__global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, const double* r,
-                                                  const double* phi, const double* vr,
-                                                  const double* vt, const uint32_t* id,
+__global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials,
+                                                  const uint32_t* id,
                                                   const uint32_t* step_p, BucketArgs BA,
-                                                  const double* tp_min, const double* tp_max,
+                                                  const double4_32a* orb,
                                                   uint64_t* keys, uint32_t* plist,
                                                   uint32_t* pcount, int64_t n, const double* Fx) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1159,13 +1161,11 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
   if (p < n) {
     c = seg_find(S.off, S.n_seg, p);
     const int64_t k = p - S.off[c];
-    const double vrk = vr[p], vtk = vt[p];
-    const double E = __ldg(phi + p) + scale_down<1>(vrk * vrk + vtk * vtk);
+    // E, J, c0, c1 from the turning-point kernel
+    const double4_32a o = k < S.nb[c] ? orb[p] : make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    const double E = o.x;
     if (k < S.nb[c] && lt0(E)) {
-      const double J = r[p] * vtk;
-      const double rmin = __ldg(tp_min + p), rmax = __ldg(tp_max + p);
-      const double c0 = scale_down<1>(rmax + rmin);
-      const double c1 = scale_down<2>(rmax - rmin);
+      const double J = o.y, c0 = o.z, c1 = o.w;
       const float c0f = f32_rn(c0), c1f = f32_rn(c1), E32 = f32_rn(E), J32 = f32_rn(J);
       const Grid GD = grid_of(BA, c);
       float F32;
@@ -1173,7 +1173,7 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
       if (kExact) {
         const double F64 = 1.2 * __ldg(Fx + p);
         F32 = f32_rn(F64);
-        degenerate = !gt_pos(rmax, rmin) || !(F64 > 0.0);
+        degenerate = !gt_pos(c1, 0.0) || !(F64 > 0.0);
       } else {
         float gmax = 0.0f;
 #pragma unroll 3
@@ -1182,7 +1182,7 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
           gmax = g > gmax ? g : gmax;
         }
         F32 = 1.2f * gmax;
-        degenerate = !gt_pos(rmax, rmin) || !(F32 > 0.0f);
+        degenerate = !gt_pos(c1, 0.0) || !(F32 > 0.0f);
       }
       uint32_t st = kSmpCap;
       int t = 0;
@@ -1229,13 +1229,9 @@ __global__ void __launch_bounds__(256, kMinB) k_sample32(Seg S, int max_trials, 
 // one pending star (p = n: an idle lane); counts go to the statistics
 // kExact (FP64 mode): F = 1.2 Fx, the points and g as FP64 mode's
 template <bool kTaus, bool kExact>
-__device__ __forceinline__ void pending_star(Seg S, int max_trials, const double* r,
-                                             const double* x, const double* phi,
-                                             const double* Menc,
-                                             const double* vr, const double* vt,
-                                             const uint32_t* id, const uint32_t* step_p,
-                                             BucketArgs BA, const double* tp_min,
-                                             const double* tp_max, uint64_t* keys, int64_t p,
+__device__ __forceinline__ void pending_star(Seg S, int max_trials, const uint32_t* id,
+                                             const uint32_t* step_p, BucketArgs BA,
+                                             const double4_32a* orb, uint64_t* keys, int64_t p,
                                              int64_t n, const double* Fx) {
   unsigned long long viol = 0;
   unsigned int n64 = 0;
@@ -1245,11 +1241,11 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
     const int64_t sb = S.off[c], nbc = S.nb[c], k = p - sb;
     if (k < nbc) {
       const uint64_t res = keys[p];
-      const double vrk = vr[p], vtk = vt[p];
+      const double4_32a o = orb[p];  // E, J, c0, c1 from the turning-point kernel
       Star s;
       s.k = k;
-      s.E = __ldg(phi + p) + scale_down<1>(vrk * vrk + vtk * vtk);
-      s.J = r[p] * vtk;
+      s.E = o.x;
+      s.J = o.y;
       if (lt0(s.E) && ((uint32_t)(res >> 30) & 3u) == kSmpPending) {
         Buckets BK;
         const int4 pr = BA.prm[c];
@@ -1259,9 +1255,7 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
         BK.nbk = pr.y;
         BK.lo = pr.z;
         BK.hi = pr.w;
-        const double rmin = __ldg(tp_min + p), rmax = __ldg(tp_max + p);
-        const double c0 = scale_down<1>(rmax + rmin);
-        const double c1 = scale_down<2>(rmax - rmin);
+        const double c0 = o.z, c1 = o.w;
         const float c0f = f32_rn(c0), c1f = f32_rn(c1);
         const double F =
             kExact ? 1.2 * __ldg(Fx + p) : (double)__uint_as_float((uint32_t)(res >> 32));
@@ -1306,20 +1300,15 @@ __device__ __forceinline__ void pending_star(Seg S, int max_trials, const double
 }
 
 template <bool kTaus, bool kExact>
-__global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const double* r,
-                                                   const double* x, const double* phi,
-                                                   const double* Menc,
-                                                   const double* vr, const double* vt,
-                                                   const uint32_t* id, const uint32_t* step_p,
-                                                   BucketArgs BA, const double* tp_min,
-                                                   const double* tp_max, uint64_t* keys,
+__global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const uint32_t* id,
+                                                   const uint32_t* step_p, BucketArgs BA,
+                                                   const double4_32a* orb, uint64_t* keys,
                                                    const uint32_t* plist,
                                                    const uint32_t* pcount, int64_t n,
                                                    const double* Fx) {
   const uint32_t np = *pcount;
   for (uint32_t i0 = blockIdx.x * blockDim.x; i0 < np; i0 += gridDim.x * blockDim.x) {
-    pending_star<kTaus, kExact>(S, max_trials, r, x, phi, Menc, vr, vt, id, step_p, BA, tp_min,
-                                tp_max, keys,
+    pending_star<kTaus, kExact>(S, max_trials, id, step_p, BA, orb, keys,
                                 i0 + threadIdx.x < np ? (int64_t)plist[i0 + threadIdx.x] : n, n,
                                 Fx);
   }
@@ -1341,6 +1330,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
                                                uint64_t* keys, Payload* pay, int64_t* esc,
                                                OrbitStageOut dbg, BucketArgs BA,
                                                const double* tp_min, const double* tp_max,
+                                               const double4_32a* orb,
                                                int64_t n, const double* Rv, double* Rp,
                                                const double* Fx, const double* Av,
                                                double* Ap) {
@@ -1383,8 +1373,18 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
   const Table64 T{r + sb, x + sb, phi + sb, nbc};
   Star s;
   s.k = k;
-  s.E = __ldg(T.phi + k) + scale_down<1>(vrk * vrk + vtk * vtk);
-  s.J = rk * vtk;
+  double c0o = 0.0, c1o = 0.0;
+  if (kPrec >= 1) {
+    // E, J, c0, c1 from the turning-point kernel
+    const double4_32a o = orb[p];
+    s.E = o.x;
+    s.J = o.y;
+    c0o = o.z;
+    c1o = o.w;
+  } else {
+    s.E = __ldg(T.phi + k) + scale_down<1>(vrk * vrk + vtk * vtk);
+    s.J = rk * vtk;
+  }
   Draws<kTaus> g = draws_of<kTaus>(S, c, idk, *step_p);
   double ph_new = __ldg(T.phi + k);
 
@@ -1409,8 +1409,8 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
     if (kPrec == 0) {
       jmax = bisect_rmax64(T, s);
       jmin = bisect_rmin64(T, s);
-    } else {
-      // turning points from k_turning_mixed
+    } else if (dbg.rmin) {
+      // turning points from k_turning_mixed (for the stage outputs)
       rmin = __ldg(tp_min + p);
       rmax = __ldg(tp_max + p);
     }
@@ -1418,8 +1418,8 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
       rmax = shell_root64(T, s, jmax, true);
       rmin = jmin < 0 ? central_root64(T, s) : shell_root64(T, s, jmin, false);
     }
-    const double c0 = scale_down<1>(rmax + rmin);
-    const double c1 = scale_down<2>(rmax - rmin);
+    const double c0 = kPrec == 0 ? scale_down<1>(rmax + rmin) : c0o;
+    const double c1 = kPrec == 0 ? scale_down<2>(rmax - rmin) : c1o;
     if (kPrec == 0) {
       double gmax = 0.0;
       for (int j = 0; j <= 20; ++j) {
@@ -1956,13 +1956,13 @@ void launch_correction_mixed(const SegLayout& L, const double* r, const double* 
 
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,
                     const double* Menc, const double* vr, const double* vt,
-                    const BucketArgs& ba, double* tp_min, double* tp_max, int block,
-                    cudaStream_t st) {
+                    const BucketArgs& ba, double* tp_min, double* tp_max, double4_32a* orb,
+                    int block, cudaStream_t st) {
   if (!L.n) return;
   if (block <= 0) block = 64;
   const unsigned grid = (unsigned)((L.n + block - 1) / block);
   k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, Menc, vr, vt, ba, tp_min,
-                                             tp_max, L.n);
+                                             tp_max, orb, L.n);
 }
 
 void launch_orbit(const SegLayout& L, int precision, int max_trials, const double* r,
@@ -1973,7 +1973,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
                   uint32_t* plist, uint32_t* pcount, cudaStream_t st, bool with_turning,
                   const double* Rv, double* Rp, const EnvWork* env, const double* Av,
-                  double* Ap) {
+                  double* Ap, double4_32a* orb) {
   if (!L.n) return;
   OrbitStageOut d;
   EnvWork W;
@@ -1992,27 +1992,25 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
   const bool exact = precision == 0;
 #define CMC_TURN(B)                                                                          \
   k_turning_mixed<5><<<grid, block, 0, st>>>(L.dev(), r, x, phi, Menc, vr, vt, ba,      \
-                                             tp_min, tp_max, L.n)
+                                             tp_min, tp_max, orb, L.n)
 #define CMC_ORBIT(P, B, T)                                                                  \
   k_orbit<P, B, T><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, Menc, vr, vt, \
                                            m, id, step, keys, pay, L.esc_step, d, ba, tp_min, \
-                                           tp_max, L.n, Rv, Rp, Fx, Av, Ap)
+                                           tp_max, orb, L.n, Rv, Rp, Fx, Av, Ap)
 #define CMC_SAMPLED(B, T, X)                                                                \
   do {                                                                                      \
     if (with_turning) CMC_TURN(B);                                                          \
     if (X) {                                                                                \
       cudaMemsetAsync(W.cnt, 0, 2 * sizeof(unsigned long long), st);                        \
       k_env_screen<<<(unsigned)((L.n + kEnvThreads - 1) / kEnvThreads), kEnvThreads, 0, st>>>( \
-          L.dev(), r, phi, vr, vt, ba, tp_min, tp_max, W, L.n);                              \
+          L.dev(), ba, orb, W, L.n);                                                         \
       k_env_eval<<<egrid, kEnvThreads, 0, st>>>(L.dev(), ba, W);                             \
     }                                                                                       \
     cudaMemsetAsync(pcount, 0, sizeof(uint32_t), st);                                      \
-    k_sample32<B, T, X><<<grid, block, 0, st>>>(L.dev(), max_trials, r, phi, vr, vt, id, step, \
-                                                ba, tp_min, tp_max, keys, plist, pcount, L.n, \
-                                                Fx);                                        \
-    k_pending64<T, X><<<pgrid, 128, 0, st>>>(L.dev(), max_trials, r, x, phi, Menc, vr, vt, \
-                                             id, step, ba, tp_min, tp_max, keys, plist, pcount, \
-                                             L.n, Fx);                                      \
+    k_sample32<B, T, X><<<grid, block, 0, st>>>(L.dev(), max_trials, id, step, ba, orb, keys, \
+                                                plist, pcount, L.n, Fx);                    \
+    k_pending64<T, X><<<pgrid, 128, 0, st>>>(L.dev(), max_trials, id, step, ba, orb, keys,  \
+                                             plist, pcount, L.n, Fx);                       \
     CMC_ORBIT(X ? 2 : 1, 5, T);                                                             \
   } while (0)
 #define CMC_VARIANTS(X)                                                                     \
