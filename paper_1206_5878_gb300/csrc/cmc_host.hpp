@@ -62,7 +62,8 @@ struct SortWork {
   uint32_t* hist = nullptr;             // [n_seg][passes][256]
   uint32_t* tickets = nullptr;          // [passes]
   uint32_t* done = nullptr;             // [n_seg] upsweep blocks finished
-  size_t zero_bytes = 0;                // desc + hist + tickets, zeroed per sort
+  size_t zero_bytes = 0;                // hist + tickets + done, then desc
+  size_t zero_head = 0;                 // bytes before desc (zeroed with it per sort)
   void* zero_base = nullptr;
   int max_passes = 0;
   // shape of the digit passes: keys per thread (8 or 16) and multisplit

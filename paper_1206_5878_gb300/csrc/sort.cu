@@ -450,12 +450,16 @@ cudaError_t alloc_sort(SortWork& W, const SegLayout& L, int max_passes, cudaStre
   size_t hist_b = sizeof(uint32_t) * (size_t)L.n_seg * max_passes * kBins;
   size_t tick_b = sizeof(uint32_t) * 16;
   size_t done_b = sizeof(uint32_t) * (size_t)L.n_seg;
-  W.zero_bytes = desc_b + hist_b + tick_b + done_b;
+  // histograms, tickets and done counters first, then the look-back words:
+  // a sort zeroes the counters and the words of its own passes and tiles
+  const size_t head_b = (hist_b + tick_b + done_b + 255) / 256 * 256;
+  W.zero_bytes = head_b + desc_b;
+  W.zero_head = head_b;
   if ((e = cudaMallocAsync(&W.zero_base, W.zero_bytes, st))) return e;
-  W.desc = (unsigned long long*)W.zero_base;
-  W.hist = (uint32_t*)((char*)W.zero_base + desc_b);
-  W.tickets = (uint32_t*)((char*)W.zero_base + desc_b + hist_b);
-  W.done = (uint32_t*)((char*)W.zero_base + desc_b + hist_b + tick_b);
+  W.hist = (uint32_t*)W.zero_base;
+  W.tickets = (uint32_t*)((char*)W.zero_base + hist_b);
+  W.done = (uint32_t*)((char*)W.zero_base + hist_b + tick_b);
+  W.desc = (unsigned long long*)((char*)W.zero_base + head_b);
   return sort_set_shape(L, W, 16, 0, st);
 }
 
@@ -473,7 +477,10 @@ cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint3
   if (keys_res) *keys_res = keys;
   if (vals_res) *vals_res = vals;
   if (passes <= 0 || passes > W.max_passes || L.n_tiles == 0) return cudaSuccess;
-  cudaMemsetAsync(W.zero_base, 0, W.zero_bytes, st);
+  cudaMemsetAsync(W.zero_base, 0,
+                  W.zero_head + sizeof(unsigned long long) * (size_t)passes *
+                                    (size_t)W.n_stiles * kBins,
+                  st);
   k_upsweep<<<(unsigned)L.n_tiles, kThreads, sizeof(uint32_t) * kWarps * passes * kBins, st>>>(
       L.off, L.tile_off, L.n_seg, keys, first_pass, passes, W.hist, W.done);
   uint64_t* kin = keys;
