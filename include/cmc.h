@@ -145,6 +145,12 @@ typedef struct {
                                    join Eq. 7's; default 0 */
     double x_bb;                /* strong-interaction parameter X_bb of Eq. 9 (1) */
     double x_bs;                /* strong-interaction parameter X_bs of Eq. 10 (1) */
+    int32_t sort_packed;        /* 1: when every cluster has at most 2^24 stars, the
+                                   timestep's sort moves 8-byte keys that carry
+                                   each star's index in their low 24 bits (bits
+                                   the radix passes leave to the tie fix) instead
+                                   of keys and 4-byte values (default 1); 0: keys
+                                   and values.  Results do not depend on it. */
 } cmc_config;
 
 /* Fill cfg with the defaults shown above. */

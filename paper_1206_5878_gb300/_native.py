@@ -37,7 +37,7 @@ class cmc_config(ctypes.Structure):
                 ("max_trials", _i32), ("energy_correction", _i32), ("orbit_block", _i32),
                 ("autotune", _i32), ("orbit_variant", _i32), ("rng", _i32),
                 ("relax_variant", _i32), ("collisions", _i32), ("diag_ring", _i32),
-                ("binaries", _i32), ("x_bb", _d), ("x_bs", _d)]
+                ("binaries", _i32), ("x_bb", _d), ("x_bs", _d), ("sort_packed", _i32)]
 
 
 # exported symbol -> (restype, argtypes); the list is the ABI of include/cmc.h

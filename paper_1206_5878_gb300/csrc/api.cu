@@ -42,6 +42,7 @@ struct cmc_ctx {
   uint32_t* pcount = nullptr;  // pending stars of the sampled orbit step
   EnvWork env;                 // FP64 mode's envelope (precision 0)
   double4_32a* orb = nullptr;  // E, J, c0, c1 of every star's orbit (precision 0 and 1)
+  bool packed = false;         // the timestep sorts packed keys (cfg.sort_packed, clusters < 2^24)
   double* ring = nullptr;      // per-step diagnostics (cfg.diag_ring records per cluster)
   int64_t steps_taken = 0;
   cudaGraphExec_t exec = nullptr;
@@ -237,19 +238,22 @@ void record_step(cmc_ctx* c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
                tab ? c->Mbuf : nullptr, c->vr, c->vt, c->m, c->id,
                c->step, c->keys, c->pay, nullptr, c->cfg.orbit_block, c->orbit_variant,
                c->bk.args(), c->r_old, c->cc, c->vals, c->pcount, st, false, c->R, c->Rp,
-               c->cfg.precision == 0 ? &c->env : nullptr, c->A, c->Ap, c->orb);
+               c->cfg.precision == 0 ? &c->env : nullptr, c->A, c->Ap, c->orb, c->packed);
   mark(4);
   // radix passes over bits 24-63 of the radius keys; runs equal in those
   // bits (radii within 2^-28 of each other, escapers whose ids differ in
   // their low 4 bits) are put in (key, id) order after
   uint64_t* sk = nullptr;
   uint32_t* sv = nullptr;
-  sort_segments(L, c->W, c->keys, c->vals, 3, 5, true, c->err, st, &sk, &sv);
-  launch_tiefix(L, sk, sv, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)), c->err, st,
-                24);
+  sort_segments(L, c->W, c->keys, c->vals, 3, 5, true, c->err, st, &sk, &sv, c->packed);
+  if (c->packed)
+    launch_tiefix_packed(L, sk, c->pay, c->err, st);
+  else
+    launch_tiefix(L, sk, sv, &c->pay[0].id, (int)(sizeof(Payload) / sizeof(uint32_t)), c->err,
+                  st, 24);
   mark(5);
   launch_gather(L, sk, sv, c->pay, c->r, c->x, c->vr, c->vt, c->m, c->id, c->r_old, c->cc, st,
-                c->tile_a, c->tile_b, c->Rp, c->R, c->Ap, c->A);
+                c->tile_a, c->tile_b, c->Rp, c->R, c->Ap, c->A, c->packed);
   mark(6);
   // the tables carry the shell slopes of the FP64 orbit step (not the
   // scan's enclosed masses): the sampled step's turning points and points
@@ -571,7 +575,8 @@ cmc_status autotune(cmc_ctx* c) {
       if (sort_set_shape(L, c->W, ipt, rank, st)) continue;
       const float ms = time_it([&] {
         cudaMemcpyAsync(c->keys, saved, sizeof(uint64_t) * L.n, cudaMemcpyDeviceToDevice, st);
-        sort_segments(L, c->W, c->keys, c->vals, 3, 5, true, c->err, st);
+        sort_segments(L, c->W, c->keys, c->vals, 3, 5, true, c->err, st, nullptr, nullptr,
+                      c->packed);
       });
       if (ms < tbest) { tbest = ms; best_ipt = ipt; best_rank = rank; }
     }
@@ -657,6 +662,7 @@ void cmc_config_default(cmc_config* cfg) {
   cfg->binaries = 0;
   cfg->x_bb = 1.0;
   cfg->x_bs = 1.0;
+  cfg->sort_packed = 1;
 }
 
 cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
@@ -678,7 +684,8 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
       cfg.relax_variant >= kRelaxVariants || (cfg.collisions != 0 && cfg.collisions != 1) ||
       cfg.diag_ring < 0 || cfg.diag_ring > (1 << 20) ||
       (cfg.binaries != 0 && cfg.binaries != 1) || !(cfg.x_bb > 0.0) || !(cfg.x_bb < INFINITY) ||
-      !(cfg.x_bs > 0.0) || !(cfg.x_bs < INFINITY))
+      !(cfg.x_bs > 0.0) || !(cfg.x_bs < INFINITY) ||
+      (cfg.sort_packed != 0 && cfg.sort_packed != 1))
     return fail(nullptr, CMC_EINVAL, "cmc_init: bad configuration");
   std::vector<int64_t> sizes(n_per_cluster, n_per_cluster + n_clusters);
   std::vector<uint64_t> sd(seeds, seeds + n_clusters);
@@ -694,6 +701,9 @@ cmc_status cmc_init(cmc_ctx** out, const cmc_config* cfg_in, int32_t n_clusters,
 
   cmc_ctx* c = new cmc_ctx();
   c->cfg = cfg;
+  c->packed = cfg.sort_packed != 0;
+  for (int k = 0; k < n_clusters; ++k)
+    if (sizes[k] > kPackMax) c->packed = false;
   c->stream = (cudaStream_t)stream;
   c->pref = t_rel_prefactor(cfg.theta_max);
   cudaGetDevice(&c->device);

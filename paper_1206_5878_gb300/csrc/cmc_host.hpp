@@ -96,7 +96,7 @@ void free_sort(SortWork& W, cudaStream_t st);
 cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint32_t* vals,
                           int first_pass, int passes, bool vals_identity, uint32_t* err,
                           cudaStream_t st, uint64_t** keys_res = nullptr,
-                          uint32_t** vals_res = nullptr);
+                          uint32_t** vals_res = nullptr, bool packed = false);
 
 // Order every run of finite keys equal in their bits from `shift` up by
 // (key, id of the element: ids_by_val[vals[p] * id_stride]), so that after
@@ -114,8 +114,18 @@ void launch_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out,
 // its energy in the field of the others, Phi_k + m_k / r_k + v^2 / 2.
 struct Payload {
   double vr, vt, m, r_old, c;
-  uint32_t id, pad;
+  uint32_t id, pad;  // pad: with packed keys, the key's own low 24 bits
 };
+
+// Packed sort keys (every segment below 2^24 stars): a key's low 24 bits,
+// which the timestep's radix passes do not sort, hold the star's index in
+// its segment (the key's own low bits go to the payload), so that the
+// passes move 8-byte keys and no values.
+constexpr uint64_t kPackMask = 0xFFFFFFull;
+constexpr int64_t kPackMax = (int64_t)1 << 24;
+// the tie fix of packed keys (runs equal in bits 24-63 into (key, id) order)
+void launch_tiefix_packed(const SegLayout& L, uint64_t* keys, const Payload* pay,
+                          uint32_t* err, cudaStream_t st);
 
 // keys of the current state (radius_key of r, id) and the payload (if pay)
 void launch_make_keys(const SegLayout& L, const double* r, const double* vr,
@@ -137,7 +147,8 @@ void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* val
                    double* m, uint32_t* id, double* r_old, double* c, cudaStream_t st,
                    double* tile_m = nullptr, double* tile_mx = nullptr,
                    const double* Rp = nullptr, double* Rout = nullptr,
-                   const double* Ap = nullptr, double* Aout = nullptr);
+                   const double* Ap = nullptr, double* Aout = nullptr,
+                   bool packed = false);
 
 // potential: per-tile sums then the tile-local scans (Eqs. 1-5 in scan
 // form).  nb_sub: subtract esc_step from nb (after the orbit step).
@@ -299,7 +310,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   uint32_t* plist, uint32_t* pcount, cudaStream_t st,
                   bool with_turning = true, const double* Rv = nullptr, double* Rp = nullptr,
                   const EnvWork* env = nullptr, const double* Av = nullptr,
-                  double* Ap = nullptr, double4_32a* orb = nullptr);
+                  double* Ap = nullptr, double4_32a* orb = nullptr, bool packed = false);
 // the turning-point kernel alone (mixed mode; launch_orbit(..., false)
 // then runs the sampling kernel only)
 void launch_turning(const SegLayout& L, const double* r, const double* x, const double* phi,

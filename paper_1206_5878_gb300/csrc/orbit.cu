@@ -1314,6 +1314,18 @@ __global__ void __launch_bounds__(128) k_pending64(Seg S, int max_trials, const 
   }
 }
 
+// the star's sort key and payload record; packed: the key's low 24 bits go
+// to the record and the star's index in the segment takes their place
+__device__ __forceinline__ void put_key(uint64_t* keys, Payload* pay, Payload& P, int64_t p,
+                                        int64_t sb, uint64_t key, bool packed) {
+  if (packed) {
+    P.pad = (uint32_t)(key & kPackMask);
+    key = (key & ~kPackMask) | (uint64_t)(p - sb);
+  }
+  keys[p] = key;
+  pay[p] = P;
+}
+
 // kPrec: 0 FP64 by bisection (Appendix A's kernels: brackets, envelope and
 // trials all on the FP64 table), 1 mixed (turning points from
 // k_turning_mixed in tp_min, tp_max, FP32 sampler result from k_sample32 /
@@ -1333,7 +1345,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
                                                const double4_32a* orb,
                                                int64_t n, const double* Rv, double* Rp,
                                                const double* Fx, const double* Av,
-                                               double* Ap) {
+                                               double* Ap, bool packed) {
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   const int c = seg_find(S.off, S.n_seg, p);
@@ -1353,16 +1365,15 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
   if (Ap) Ap[p] = Av[p];  // and the binary's semi-major axis
   if (k >= nbc) {
     // escaped in an earlier step: stays at the end, ordered by id
-    keys[p] = radius_key(rk, idk);
-    pay[p] = P;
+    put_key(keys, pay, P, p, sb, radius_key(rk, idk), packed);
     if (dbg.code) dbg.code[p] = 1;
     return;
   }
   if (Rv && lt0(Rv[p])) {
     // merged into its partner in this step (sticky spheres): it leaves
     // with no mass, draws nothing, and carries off no energy
-    keys[p] = radius_key(__longlong_as_double(0x7FF0000000000000ll), idk);
-    pay[p] = P;
+    put_key(keys, pay, P, p, sb, radius_key(__longlong_as_double(0x7FF0000000000000ll), idk),
+            packed);
     if (dbg.code) dbg.code[p] = 1;
     const unsigned full = __activemask();
     const unsigned peers = __match_any_sync(full, c);
@@ -1517,8 +1528,7 @@ __global__ void __launch_bounds__(256, kMinB) k_orbit(Seg S, int max_trials, con
       }
     }
   }
-  keys[p] = radius_key(r_new, idk);
-  pay[p] = P;
+  put_key(keys, pay, P, p, sb, radius_key(r_new, idk), packed);
 
   // statistics: one atomic per counter per segment present in the warp
   const unsigned full = __activemask();
@@ -1973,7 +1983,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
                   int variant, const BucketArgs& ba, double* tp_min, double* tp_max,
                   uint32_t* plist, uint32_t* pcount, cudaStream_t st, bool with_turning,
                   const double* Rv, double* Rp, const EnvWork* env, const double* Av,
-                  double* Ap, double4_32a* orb) {
+                  double* Ap, double4_32a* orb, bool packed) {
   if (!L.n) return;
   OrbitStageOut d;
   EnvWork W;
@@ -1996,7 +2006,7 @@ void launch_orbit(const SegLayout& L, int precision, int max_trials, const doubl
 #define CMC_ORBIT(P, B, T)                                                                  \
   k_orbit<P, B, T><<<grid, block, 0, st>>>(L.dev(), max_trials, r, x, phi, Menc, vr, vt, \
                                            m, id, step, keys, pay, L.esc_step, d, ba, tp_min, \
-                                           tp_max, orb, L.n, Rv, Rp, Fx, Av, Ap)
+                                           tp_max, orb, L.n, Rv, Rp, Fx, Av, Ap, packed)
 #define CMC_SAMPLED(B, T, X)                                                                \
   do {                                                                                      \
     if (with_turning) CMC_TURN(B);                                                          \

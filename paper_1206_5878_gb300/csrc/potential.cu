@@ -137,7 +137,8 @@ __global__ void __launch_bounds__(kThreads) k_gather_sums(
     Seg S, const int64_t* esc, int64_t n, const uint64_t* __restrict__ keys,
     const uint32_t* __restrict__ vals, const Payload* __restrict__ pay, double* r, double* x,
     double* vr, double* vt, double* m, uint32_t* id, double* r_old, double* c, double* tile_m,
-    double* tile_mx, const double* Rp, double* Rout, const double* Ap, double* Aout) {
+    double* tile_mx, const double* Rp, double* Rout, const double* Ap, double* Aout,
+    bool packed) {
   __shared__ double s[kThreads];
   TR R = tile_of(S, esc, blockIdx.x, true);
   double am = 0.0, ax = 0.0;
@@ -145,10 +146,12 @@ __global__ void __launch_bounds__(kThreads) k_gather_sums(
   for (int i = 0; i < kPer; ++i) {
     const int64_t p = R.begin + (int64_t)i * kThreads + threadIdx.x;
     if (p >= R.end) continue;
-    const uint64_t k = keys[p];
-    const uint32_t v = vals[p];
-    if ((int64_t)v >= n) continue;  // only after a reported sort failure
+    uint64_t k = keys[p];
+    // packed keys: the star's index in the segment in the low 24 bits
+    const int64_t v = packed ? R.seg_begin + (int64_t)(k & kPackMask) : (int64_t)vals[p];
+    if (v >= n) continue;  // only after a reported sort failure
     const Payload P = pay[v];
+    if (packed) k = (k & ~kPackMask) | (uint64_t)P.pad;
     double rr, xx;
     if (key_is_escaper(k)) { rr = __longlong_as_double(0x7FF0000000000000ll); xx = 0.0; }
     else { rr = __longlong_as_double((long long)k); xx = div_rn(1.0, rr); }
@@ -915,13 +918,13 @@ void launch_gather(const SegLayout& L, const uint64_t* keys, const uint32_t* val
                    const Payload* pay, double* r, double* x, double* vr, double* vt,
                    double* m, uint32_t* id, double* r_old, double* c, cudaStream_t st,
                    double* tile_m, double* tile_mx, const double* Rp, double* Rout,
-                   const double* Ap, double* Aout) {
+                   const double* Ap, double* Aout, bool packed) {
   if (!L.n) return;
   if (tile_m && tile_mx && r_old && c && L.n_tiles)
     k_gather_sums<<<(unsigned)L.n_tiles, kThreads, 0, st>>>(L.dev(), L.esc_step, L.n, keys, vals,
                                                             pay, r, x, vr, vt, m, id, r_old, c,
                                                             tile_m, tile_mx, Rp, Rout, Ap,
-                                                            Aout);
+                                                            Aout, packed);
   else
     k_gather<<<blocks_for(L.n, 256), 256, 0, st>>>(L.n, keys, vals, pay, r, x, vr, vt, m, id,
                                                   r_old, c);

@@ -141,10 +141,12 @@ __global__ void __launch_bounds__(kThreads) k_upsweep(const int64_t* off, const 
   }
 }
 
-template <int IPT>
+// kPacked: keys only (each key carries its star's index in its unsorted low
+// bits), no values
+template <int IPT, bool kPacked>
 struct PassSmem {
   uint64_t key[kThreads * IPT];
-  uint32_t val[kThreads * IPT];
+  uint32_t val[kPacked ? 1 : kThreads * IPT];
   uint32_t whist[kWarps][kBins];
   int64_t gbase[kBins];
   uint32_t dstart[kBins];
@@ -169,8 +171,8 @@ constexpr int kRankMatch = 0;   // __match_any_sync
 constexpr int kRankBallot = 1;  // nine __ballot_sync
 
 // ------------------------------------------------------------- onesweep
-template <bool kValIdentity, int IPT, int kRank>
-__global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : 3))
+template <bool kValIdentity, int IPT, int kRank, bool kPacked>
+__global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : (kPacked ? 4 : 3)))
     k_pass(const int64_t* off, const int64_t* tile_off, int n_seg, int64_t n_tiles,
            const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
            uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int pass, int q,
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : 3))
            uint32_t* err) {
   constexpr int kTileKeys = kThreads * IPT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  PassSmem<IPT>& S = *reinterpret_cast<PassSmem<IPT>*>(smem_raw);
+  PassSmem<IPT, kPacked>& S = *reinterpret_cast<PassSmem<IPT, kPacked>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int shift = 8 * pass;
 
@@ -199,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : 3))
     int64_t p = R.begin + e;
     bool valid = e < n_items;
     k[i] = valid ? keys_in[p] : 0ull;
-    v[i] = valid ? (kValIdentity ? (uint32_t)p : vals_in[p]) : 0u;
+    v[i] = (valid && !kPacked) ? (kValIdentity ? (uint32_t)p : vals_in[p]) : 0u;
     dg[i] = valid ? (int)((k[i] >> shift) & 0xFF) : kBins;
   }
 
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : 3))
     if (dg[i] < kBins) {
       uint32_t lp = S.dstart[dg[i]] + S.whist[warp][dg[i]] + rank[i];
       S.key[lp] = k[i];
-      S.val[lp] = v[i];
+      if (!kPacked) S.val[lp] = v[i];
     }
   }
   __syncthreads();
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : 3))
       continue;
     }
     keys_out[dest] = kk;
-    vals_out[dest] = S.val[lp];
+    if (!kPacked) vals_out[dest] = S.val[lp];
   }
 }
 
@@ -357,6 +359,56 @@ __global__ void k_tiefix(const int64_t* off, int n_seg, int64_t n, uint64_t* key
   if (equal && stats) atomicAdd(stats + (size_t)c * kStStride + kStTies, 1ull);
 }
 
+// The same for packed keys: the low 24 bits of a sorted word hold its star's
+// index in the segment, the key's own low 24 bits and the id are in the
+// star's payload record (lo24 in pad); runs equal in bits 24-63 are put in
+// (key, id) order by moving the words.
+__global__ void k_tiefix_packed(const int64_t* off, int n_seg, int64_t n, uint64_t* keys,
+                                const Payload* pay, uint32_t* err,
+                                unsigned long long* stats) {
+  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  int c = seg_find(off, n_seg, p);
+  int64_t sb = __ldg(off + c), se = __ldg(off + c + 1);
+  const uint64_t hp = keys[p] >> 24;
+  if (p + 1 >= se || (keys[p + 1] >> 24) != hp) return;
+  if (p > sb && (keys[p - 1] >> 24) == hp) return;  // not the start of the run
+  int64_t e = p + 2;
+  while (e < se && (keys[e] >> 24) == hp) ++e;
+  for (int64_t i = p; i < e; ++i)
+    if ((int64_t)(keys[i] & 0xFFFFFFull) >= se - sb) {
+      set_err(err, kErrTimeout);
+      return;
+    }
+  const Payload* P = pay + sb;
+  auto full = [&](uint64_t w) { return (w & ~0xFFFFFFull) | (uint64_t)P[w & 0xFFFFFFull].pad; };
+  auto idof = [&](uint64_t w) { return P[w & 0xFFFFFFull].id; };
+  const long long move_cap = g_tie_move_cap;
+  long long moves = 0;
+  bool equal = false;
+  for (int64_t i = p + 1; i < e; ++i) {
+    const uint64_t wv = keys[i];
+    const uint64_t kv = full(wv);
+    const uint32_t idv = idof(wv);
+    int64_t j = i - 1;
+    while (j >= p) {
+      const uint64_t wj = keys[j];
+      const uint64_t kj = full(wj);
+      if (kj == kv) equal = true;
+      if (!(kj > kv || (kj == kv && idof(wj) > idv))) break;
+      keys[j + 1] = wj;
+      --j;
+      if (++moves > move_cap) {
+        set_err(err, kErrTies);
+        keys[j + 1] = wv;
+        return;
+      }
+    }
+    keys[j + 1] = wv;
+  }
+  if (equal && stats) atomicAdd(stats + (size_t)c * kStStride + kStTies, 1ull);
+}
+
 __global__ void k_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -365,25 +417,32 @@ __global__ void k_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t
   reinterpret_cast<uint4*>(out)[i] = make_uint4(w.x, w.y, w.z, w.w);
 }
 
-template <bool kId, int IPT, int kRank>
+template <bool kId, int IPT, int kRank, bool kPacked>
 void set_pass_smem() {
-  cudaFuncSetAttribute(k_pass<kId, IPT, kRank>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)sizeof(PassSmem<IPT>));
+  cudaFuncSetAttribute(k_pass<kId, IPT, kRank, kPacked>,
+                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sizeof(PassSmem<IPT, kPacked>));
 }
 
 template <int IPT, int kRank>
 void launch_pass(const SegLayout& L, SortWork& W, bool id, const uint64_t* kin,
                  const uint32_t* vin, uint64_t* kout, uint32_t* vout, int pass, int q,
-                 int passes, uint32_t* err, cudaStream_t st) {
+                 int passes, uint32_t* err, cudaStream_t st, bool packed) {
   const unsigned grid = (unsigned)W.n_stiles;
-  const size_t sm = sizeof(PassSmem<IPT>);
+  if (packed) {
+    k_pass<false, IPT, kRank, true><<<grid, kThreads, sizeof(PassSmem<IPT, true>), st>>>(
+        L.off, W.stile_off, L.n_seg, W.n_stiles, kin, nullptr, kout, nullptr, pass, q, passes,
+        W.hist, W.desc, W.tickets, err);
+    return;
+  }
+  const size_t sm = sizeof(PassSmem<IPT, false>);
   if (id)
-    k_pass<true, IPT, kRank><<<grid, kThreads, sm, st>>>(L.off, W.stile_off, L.n_seg,
+    k_pass<true, IPT, kRank, false><<<grid, kThreads, sm, st>>>(L.off, W.stile_off, L.n_seg,
                                                          W.n_stiles, kin, vin, kout, vout, pass,
                                                          q, passes, W.hist, W.desc, W.tickets,
                                                          err);
   else
-    k_pass<false, IPT, kRank><<<grid, kThreads, sm, st>>>(L.off, W.stile_off, L.n_seg,
+    k_pass<false, IPT, kRank, false><<<grid, kThreads, sm, st>>>(L.off, W.stile_off, L.n_seg,
                                                           W.n_stiles, kin, vin, kout, vout,
                                                           pass, q, passes, W.hist, W.desc,
                                                           W.tickets, err);
@@ -401,14 +460,18 @@ cudaError_t set_wait_limits(int spin_polls, long long tie_moves) {
 }
 
 void sort_prepare() {
-  set_pass_smem<true, 8, kRankMatch>();
-  set_pass_smem<false, 8, kRankMatch>();
-  set_pass_smem<true, 8, kRankBallot>();
-  set_pass_smem<false, 8, kRankBallot>();
-  set_pass_smem<true, 16, kRankMatch>();
-  set_pass_smem<false, 16, kRankMatch>();
-  set_pass_smem<true, 16, kRankBallot>();
-  set_pass_smem<false, 16, kRankBallot>();
+  set_pass_smem<true, 8, kRankMatch, false>();
+  set_pass_smem<false, 8, kRankMatch, false>();
+  set_pass_smem<true, 8, kRankBallot, false>();
+  set_pass_smem<false, 8, kRankBallot, false>();
+  set_pass_smem<true, 16, kRankMatch, false>();
+  set_pass_smem<false, 16, kRankMatch, false>();
+  set_pass_smem<true, 16, kRankBallot, false>();
+  set_pass_smem<false, 16, kRankBallot, false>();
+  set_pass_smem<false, 8, kRankMatch, true>();
+  set_pass_smem<false, 8, kRankBallot, true>();
+  set_pass_smem<false, 16, kRankMatch, true>();
+  set_pass_smem<false, 16, kRankBallot, true>();
   cudaFuncSetAttribute(k_upsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(sizeof(uint32_t) * kWarps * kMaxPasses * kBins));
 }
@@ -473,7 +536,8 @@ void free_sort(SortWork& W, cudaStream_t st) {
 
 cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint32_t* vals,
                           int first_pass, int passes, bool vals_identity, uint32_t* err,
-                          cudaStream_t st, uint64_t** keys_res, uint32_t** vals_res) {
+                          cudaStream_t st, uint64_t** keys_res, uint32_t** vals_res,
+                          bool packed) {
   if (keys_res) *keys_res = keys;
   if (vals_res) *vals_res = vals;
   if (passes <= 0 || passes > W.max_passes || L.n_tiles == 0) return cudaSuccess;
@@ -491,13 +555,17 @@ cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint3
     const bool id = q == 0 && vals_identity;
     const int pass = first_pass + q;
     if (W.ipt == 8 && W.rank == kRankMatch)
-      launch_pass<8, kRankMatch>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st);
+      launch_pass<8, kRankMatch>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st,
+                                 packed);
     else if (W.ipt == 8)
-      launch_pass<8, kRankBallot>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st);
+      launch_pass<8, kRankBallot>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st,
+                                  packed);
     else if (W.rank == kRankMatch)
-      launch_pass<16, kRankMatch>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st);
+      launch_pass<16, kRankMatch>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st,
+                                  packed);
     else
-      launch_pass<16, kRankBallot>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st);
+      launch_pass<16, kRankBallot>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st,
+                                   packed);
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
@@ -509,7 +577,9 @@ cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint3
       *vals_res = vin;
     } else {
       cudaMemcpyAsync(keys, kin, sizeof(uint64_t) * (size_t)L.n, cudaMemcpyDeviceToDevice, st);
-      cudaMemcpyAsync(vals, vin, sizeof(uint32_t) * (size_t)L.n, cudaMemcpyDeviceToDevice, st);
+      if (!packed)
+        cudaMemcpyAsync(vals, vin, sizeof(uint32_t) * (size_t)L.n, cudaMemcpyDeviceToDevice,
+                        st);
     }
   }
   return cudaGetLastError();
@@ -521,6 +591,13 @@ void launch_tiefix(const SegLayout& L, uint64_t* keys, uint32_t* vals,
   if (L.n == 0) return;
   k_tiefix<<<(unsigned)((L.n + 255) / 256), 256, 0, st>>>(
       L.off, L.n_seg, L.n, keys, vals, ids_by_val, id_stride, shift, err, L.stats);
+}
+
+void launch_tiefix_packed(const SegLayout& L, uint64_t* keys, const Payload* pay,
+                          uint32_t* err, cudaStream_t st) {
+  if (L.n == 0) return;
+  k_tiefix_packed<<<(unsigned)((L.n + 255) / 256), 256, 0, st>>>(L.off, L.n_seg, L.n, keys, pay,
+                                                                 err, L.stats);
 }
 
 void launch_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out,

@@ -353,3 +353,30 @@ def test_fp64_paths_agree_over_steps(g, n, masses, rng):
         if k not in ("fp64_trials", "envelope_fp64"):  # the screened path's own counts
             assert sta[k] == stb[k], k
     np.testing.assert_array_equal(a.escaped(), b.escaped())
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_packed_sort_keys_change_nothing(g_stage, precision):
+    """The timestep's sort on packed keys (each key's low 24 bits, which the
+    radix passes leave to the tie fix, carrying the star's index) against
+    the keys-and-values sort: the same states, bit for bit, after several
+    steps of one cluster and of a ragged ensemble (escapers included)."""
+    g = g_stage
+    sizes = [1, 3, 20, 4097, 9000, 2, 12_289]
+    seeds = [500 + i for i in range(len(sizes))]
+    parts = [ic.plummer(n, s) for n, s in zip(sizes, seeds)]
+    ens = {k: np.concatenate([p[k] for p in parts]) for k in ("r", "vr", "vt", "m", "id")}
+    d = ic.plummer(50_000, seed=6)
+    one = {k: d[k] for k in ("r", "vr", "vt", "m", "id")}
+    for state, sd, sz in ((one, [6], None), (ens, seeds, sizes)):
+        a = g.Cluster(state, sd, sizes=sz, precision=precision, sort_packed=1)
+        b = g.Cluster(state, sd, sizes=sz, precision=precision, sort_packed=0)
+        a.step(6)
+        b.step(6)
+        sa, sb = a.get_state(), b.get_state()
+        for k in ("r", "vr", "vt", "m", "id", "phi"):
+            np.testing.assert_array_equal(sa[k], sb[k], err_msg=k)
+        np.testing.assert_array_equal(a.nbound(), b.nbound())
+        assert a.stats() == b.stats()
+        a.close()
+        b.close()
