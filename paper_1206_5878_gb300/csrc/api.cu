@@ -570,8 +570,10 @@ cmc_status autotune(cmc_ctx* c) {
   cudaMemcpyAsync(saved, c->keys, sizeof(uint64_t) * L.n, cudaMemcpyDeviceToDevice, st);
   int best_ipt = 16, best_rank = 0;
   float tbest = 3.4e38f;
-  for (int ipt : {8, 16})
+  for (int ipt : {8, 16, 24, 32})
     for (int rank : {0, 1}) {
+      // 24 and 32 keys per thread: packed keys only
+      if (ipt > 16 && !c->packed) continue;
       if (sort_set_shape(L, c->W, ipt, rank, st)) continue;
       const float ms = time_it([&] {
         cudaMemcpyAsync(c->keys, saved, sizeof(uint64_t) * L.n, cudaMemcpyDeviceToDevice, st);

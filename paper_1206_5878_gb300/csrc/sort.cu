@@ -172,7 +172,7 @@ constexpr int kRankBallot = 1;  // nine __ballot_sync
 
 // ------------------------------------------------------------- onesweep
 template <bool kValIdentity, int IPT, int kRank, bool kPacked>
-__global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : (kPacked ? 4 : 3)))
+__global__ void __launch_bounds__(kThreads, (IPT <= 8 ? 6 : IPT <= 16 ? (kPacked ? 4 : 3) : 2))
     k_pass(const int64_t* off, const int64_t* tile_off, int n_seg, int64_t n_tiles,
            const uint64_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
            uint64_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int pass, int q,
@@ -448,6 +448,22 @@ void launch_pass(const SegLayout& L, SortWork& W, bool id, const uint64_t* kin,
                                                           W.tickets, err);
 }
 
+// the larger tiles (24 or 32 keys per thread) of packed keys
+template <int IPT>
+void launch_packed_pass(const SegLayout& L, SortWork& W, const uint64_t* kin, uint64_t* kout,
+                        int pass, int q, int passes, uint32_t* err, cudaStream_t st) {
+  const unsigned grid = (unsigned)W.n_stiles;
+  const size_t sm = sizeof(PassSmem<IPT, true>);
+  if (W.rank == kRankMatch)
+    k_pass<false, IPT, kRankMatch, true><<<grid, kThreads, sm, st>>>(
+        L.off, W.stile_off, L.n_seg, W.n_stiles, kin, nullptr, kout, nullptr, pass, q, passes,
+        W.hist, W.desc, W.tickets, err);
+  else
+    k_pass<false, IPT, kRankBallot, true><<<grid, kThreads, sm, st>>>(
+        L.off, W.stile_off, L.n_seg, W.n_stiles, kin, nullptr, kout, nullptr, pass, q, passes,
+        W.hist, W.desc, W.tickets, err);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host
@@ -472,6 +488,10 @@ void sort_prepare() {
   set_pass_smem<false, 8, kRankBallot, true>();
   set_pass_smem<false, 16, kRankMatch, true>();
   set_pass_smem<false, 16, kRankBallot, true>();
+  set_pass_smem<false, 24, kRankMatch, true>();
+  set_pass_smem<false, 24, kRankBallot, true>();
+  set_pass_smem<false, 32, kRankMatch, true>();
+  set_pass_smem<false, 32, kRankBallot, true>();
   cudaFuncSetAttribute(k_upsweep, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)(sizeof(uint32_t) * kWarps * kMaxPasses * kBins));
 }
@@ -487,7 +507,8 @@ static std::vector<int64_t> sort_tile_offsets(const SegLayout& L, int tile) {
 
 cudaError_t sort_set_shape(const SegLayout& L, SortWork& W, int ipt, int rank,
                            cudaStream_t st) {
-  if ((ipt != 8 && ipt != 16) || (rank != 0 && rank != 1)) return cudaErrorInvalidValue;
+  if ((ipt != 8 && ipt != 16 && ipt != 24 && ipt != 32) || (rank != 0 && rank != 1))
+    return cudaErrorInvalidValue;
   std::vector<int64_t> o = sort_tile_offsets(L, kThreads * ipt);
   cudaError_t e = cudaMemcpyAsync(W.stile_off, o.data(), sizeof(int64_t) * o.size(),
                                   cudaMemcpyHostToDevice, st);
@@ -541,6 +562,17 @@ cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint3
   if (keys_res) *keys_res = keys;
   if (vals_res) *vals_res = vals;
   if (passes <= 0 || passes > W.max_passes || L.n_tiles == 0) return cudaSuccess;
+  // tiles of 24 or 32 keys per thread exist for packed keys only: a sort of
+  // keys and values (a new state's ordering, outside any graph capture)
+  // takes tiles of 16 and then restores the shape
+  if (!packed && W.ipt > 16) {
+    const int ipt = W.ipt, rank = W.rank;
+    cudaError_t e = sort_set_shape(L, W, 16, rank, st);
+    if (!e) e = sort_segments(L, W, keys, vals, first_pass, passes, vals_identity, err, st,
+                              keys_res, vals_res, false);
+    const cudaError_t e2 = sort_set_shape(L, W, ipt, rank, st);
+    return e ? e : e2;
+  }
   cudaMemsetAsync(W.zero_base, 0,
                   W.zero_head + sizeof(unsigned long long) * (size_t)passes *
                                     (size_t)W.n_stiles * kBins,
@@ -554,7 +586,11 @@ cudaError_t sort_segments(const SegLayout& L, SortWork& W, uint64_t* keys, uint3
   for (int q = 0; q < passes; ++q) {
     const bool id = q == 0 && vals_identity;
     const int pass = first_pass + q;
-    if (W.ipt == 8 && W.rank == kRankMatch)
+    if (packed && W.ipt == 24)
+      launch_packed_pass<24>(L, W, kin, kout, pass, q, passes, err, st);
+    else if (packed && W.ipt == 32)
+      launch_packed_pass<32>(L, W, kin, kout, pass, q, passes, err, st);
+    else if (W.ipt == 8 && W.rank == kRankMatch)
       launch_pass<8, kRankMatch>(L, W, id, kin, vin, kout, vout, pass, q, passes, err, st,
                                  packed);
     else if (W.ipt == 8)
