@@ -283,42 +283,103 @@ __device__ __forceinline__ double block_sum_pot(double v, double* w17) {
   return r;
 }
 
-// exclusive forward scan of vm and backward scan of vs over kPotThreads
-// threads, in a fixed order: inclusive scans inside each warp by shuffles,
+// Fixed point for the sums inside a tile: v >= 0 as round(v 2^S) in 64
+// bits, S = 49 - (the largest unbiased exponent among the tile's values),
+// so that a sum of 4096 values stays below 2^62; the largest values keep
+// 50 significant bits, the sums are then exact (and independent of their
+// order), and only the conversion back rounds.  Integer instructions only:
+// the FP64 pipe is left to the products.
+__device__ __forceinline__ int exp_of(double v) {  // biased exponent (0 for zero)
+  return (int)((ubits(v) >> 52) & 0x7FFull);
+}
+
+__device__ __forceinline__ long long fix_of(double v, int S) {
+  const unsigned long long u = ubits(v);
+  const int e = (int)((u >> 52) & 0x7FFull);
+  if (e == 0) return 0;  // zero (and subnormals, far below any sum here)
+  const unsigned long long mant = (u & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = e - 1075 + S;  // v = mant 2^(e - 1075); sh <= -3 for the largest
+  if (sh >= 0) return (long long)(mant << sh);
+  if (sh < -60) return 0;
+  const int d = -sh;
+  // round to nearest, ties to even
+  const unsigned long long q = mant >> d, rem = mant & ((1ull << d) - 1ull),
+                           half = 1ull << (d - 1);
+  return (long long)(q + ((rem > half || (rem == half && (q & 1ull))) ? 1ull : 0ull));
+}
+
+// V 2^-S (V >= 0) as the nearest double, ties to even
+__device__ __forceinline__ double dbl_of_fix(long long V, int S) {
+  if (V <= 0) return 0.0;
+  const unsigned long long a = (unsigned long long)V;
+  int top = 63 - __clzll((long long)a);
+  unsigned long long m;
+  if (top <= 52) {
+    m = a << (52 - top);
+  } else {
+    const int d = top - 52;
+    m = a >> d;
+    const unsigned long long rem = a & ((1ull << d) - 1ull), half = 1ull << (d - 1);
+    if (rem > half || (rem == half && (m & 1ull))) ++m;
+    if (m >> 53) {
+      m >>= 1;
+      ++top;
+    }
+  }
+  return __longlong_as_double(
+      (long long)(((unsigned long long)(top - S + 1023) << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// the largest of one int per thread over kPotThreads threads
+__device__ __forceinline__ int block_max_pot(int v, int* w17) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = (int)__reduce_max_sync(0xFFFFFFFFu, (unsigned)v);
+  if (lane == 0) w17[w] = v;
+  __syncthreads();
+  int r = 0;
+#pragma unroll
+  for (int i = 0; i < kPotWarps; ++i) r = w17[i] > r ? w17[i] : r;
+  __syncthreads();
+  return r;
+}
+
+// exclusive forward scan of vm and backward scan of vs (64-bit integers)
+// over kPotThreads threads: inclusive scans inside each warp by shuffles,
 // the 16 warp totals scanned by one warp, then (totals of the warps before
 // or after) + (lanes before or after in the warp)
-__device__ __forceinline__ void block_scans_pot(double vm, double vs, double* wm, double* ws,
-                                                double& pre_m, double& suf_s) {
+__device__ __forceinline__ void block_scans_fix(long long vm, long long vs, long long* wm,
+                                                long long* ws, long long& pre_m,
+                                                long long& suf_s) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  double a = vm, b = vs;
+  long long a = vm, b = vs;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const double ua = __shfl_up_sync(0xFFFFFFFFu, a, o);
-    const double db = __shfl_down_sync(0xFFFFFFFFu, b, o);
+    const long long ua = __shfl_up_sync(0xFFFFFFFFu, a, o);
+    const long long db = __shfl_down_sync(0xFFFFFFFFu, b, o);
     if (lane >= o) a = ua + a;
     if (lane + o < 32) b = b + db;
   }
-  const double ea = __shfl_up_sync(0xFFFFFFFFu, a, 1);    // lanes before
-  const double eb = __shfl_down_sync(0xFFFFFFFFu, b, 1);  // lanes after
+  const long long ea = __shfl_up_sync(0xFFFFFFFFu, a, 1);
+  const long long eb = __shfl_down_sync(0xFFFFFFFFu, b, 1);
   if (lane == 31) wm[w] = a;
   if (lane == 0) ws[w] = b;
   __syncthreads();
   if (w == 0) {
-    double ta = lane < kPotWarps ? wm[lane] : 0.0;
-    double tb = lane < kPotWarps ? ws[lane] : 0.0;
+    long long ta = lane < kPotWarps ? wm[lane] : 0ll;
+    long long tb = lane < kPotWarps ? ws[lane] : 0ll;
 #pragma unroll
     for (int o = 1; o < kPotWarps; o <<= 1) {
-      const double ua = __shfl_up_sync(0xFFFFFFFFu, ta, o);
-      const double db = __shfl_down_sync(0xFFFFFFFFu, tb, o);
+      const long long ua = __shfl_up_sync(0xFFFFFFFFu, ta, o);
+      const long long db = __shfl_down_sync(0xFFFFFFFFu, tb, o);
       if (lane >= o) ta = ua + ta;
       if (lane + o < kPotWarps) tb = tb + db;
     }
-    const double xa = __shfl_up_sync(0xFFFFFFFFu, ta, 1);
-    const double xb = __shfl_down_sync(0xFFFFFFFFu, tb, 1);
+    const long long xa = __shfl_up_sync(0xFFFFFFFFu, ta, 1);
+    const long long xb = __shfl_down_sync(0xFFFFFFFFu, tb, 1);
     __syncwarp();
     if (lane < kPotWarps) {
-      wm[lane] = lane > 0 ? xa : 0.0;
-      ws[lane] = lane + 1 < kPotWarps ? xb : 0.0;
+      wm[lane] = lane > 0 ? xa : 0ll;
+      ws[lane] = lane + 1 < kPotWarps ? xb : 0ll;
     }
   }
   __syncthreads();
@@ -345,6 +406,8 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(Seg S, const int64_t*
   double* s_x = smem + kPad8N;      // x
   double* s_p = smem + 2 * kPad8N;  // Phi
   __shared__ double wm[kPotWarps + 1], ws[kPotWarps];
+  __shared__ long long wq[kPotWarps], wr[kPotWarps];
+  __shared__ int we[kPotWarps];
   TR R = tile_of(S, esc, blockIdx.x, sub);
   const int64_t t0 = blockIdx.x - R.lt;
   const int t = threadIdx.x;
@@ -366,27 +429,41 @@ __global__ void __launch_bounds__(kPotThreads) k_potential(Seg S, const int64_t*
   }
   __syncthreads();
   const int e0 = t * kPotPer;
-  // exclusive suffix of m x along the thread's run, and its total
-  double suf[kPotPer];
-  double ax = 0.0;
-#pragma unroll
-  for (int i = kPotPer - 1; i >= 0; --i) {
-    suf[i] = ax;
-    ax = ax + s_m[pad8(e0 + i)] * s_x[pad8(e0 + i)];
-  }
-  double am = 0.0;
-#pragma unroll
-  for (int i = 0; i < kPotPer; ++i) am = am + s_m[pad8(e0 + i)];
-  double pre_m, suf_s;
-  block_scans_pot(am, ax, wm, ws, pre_m, suf_s);
-  const double bm = Mbefore + pre_m, bs = Safter + suf_s;
-  double run = 0.0;
+  // the tile's sums of m and m x in fixed point (exact inside the tile):
+  // the scales from the largest exponents, then the thread's run of 8
+  double mx[kPotPer];
+  int em = 0, ex = 0;
 #pragma unroll
   for (int i = 0; i < kPotPer; ++i) {
     const int q = pad8(e0 + i);
-    run = run + s_m[q];
-    const double Mk = bm + run;
-    const double ph = -(Mk * s_x[q] + (bs + suf[i]));
+    mx[i] = s_m[q] * s_x[q];
+    const int a = exp_of(s_m[q]), b = exp_of(mx[i]);
+    em = a > em ? a : em;
+    ex = b > ex ? b : ex;
+  }
+  const int Sm = 49 - (block_max_pot(em, we) - 1023);
+  const int Sx = 49 - (block_max_pot(ex, we) - 1023);
+  // exclusive suffix of m x along the thread's run, and its total
+  long long suf[kPotPer];
+  long long ax = 0;
+#pragma unroll
+  for (int i = kPotPer - 1; i >= 0; --i) {
+    suf[i] = ax;
+    ax = ax + fix_of(mx[i], Sx);
+  }
+  long long am = 0;
+#pragma unroll
+  for (int i = 0; i < kPotPer; ++i) am = am + fix_of(s_m[pad8(e0 + i)], Sm);
+  long long pre_m, suf_s;
+  block_scans_fix(am, ax, wq, wr, pre_m, suf_s);
+  long long run = pre_m;
+#pragma unroll
+  for (int i = 0; i < kPotPer; ++i) {
+    const int q = pad8(e0 + i);
+    run = run + fix_of(s_m[q], Sm);
+    const double Mk = Mbefore + dbl_of_fix(run, Sm);
+    const double Sk = Safter + dbl_of_fix(suf_s + suf[i], Sx);
+    const double ph = -(Mk * s_x[q] + Sk);
     s_m[q] = Mk;
     s_p[q] = ph;
   }
