@@ -92,102 +92,6 @@ __global__ void __launch_bounds__(256) k_bins(Seg S, int bs, double pref, const 
   }
 }
 
-// The same bins with one thread per pair: a block of 256 threads takes
-// 256 / (bs/2) consecutive bins; each thread computes its pair's terms
-// sqrt(v_a^2 + v_b^2) and (m_a + m_b)^2 (coalesced loads, the square roots
-// side by side), and the bin's first thread adds them in pair order, as
-// the one-thread-per-bin kernel does, so the sums are the same bits.
-__global__ void __launch_bounds__(256) k_bins_pairs(Seg S, int bs, double pref,
-                                                    const double* r, const double* vr,
-                                                    const double* vt, const double* m,
-                                                    double* nbin, int bpb) {
-  __shared__ double s_sv[256], s_sm[256];
-  __shared__ unsigned long long s_min[8];
-  __shared__ int s_seg0;
-  const int hp = bs / 2;
-  const int lbin = threadIdx.x / hp, j = threadIdx.x - lbin * hp;
-  const int64_t b0 = (int64_t)blockIdx.x * bpb;
-  const int64_t b = b0 + lbin;
-  const int64_t nbins = S.bin_off[S.n_seg];
-  if (threadIdx.x == 0) s_seg0 = seg_find(S.bin_off, S.n_seg, b0);
-  const bool live = lbin < bpb && b < nbins;
-  int c = 0;
-  int64_t sb = 0, first = 0, P = 0;
-  double tv = 0.0, tm = 0.0;
-  if (live) {
-    c = seg_find(S.bin_off, S.n_seg, b);
-    const int64_t lb = b - S.bin_off[c];
-    const int64_t nbc = S.nb[c];
-    sb = S.off[c];
-    first = lb * bs;
-    if (first < nbc) {
-      P = nbc - first < bs ? nbc - first : bs;
-      if (j < P / 2) {
-        const int64_t a = sb + first + 2 * j;
-        const double va2 = vr[a] * vr[a] + vt[a] * vt[a];
-        const double vb2 = vr[a + 1] * vr[a + 1] + vt[a + 1] * vt[a + 1];
-        const double ms = m[a] + m[a + 1];
-        tv = sqrt_rn(va2 + vb2);
-        tm = ms * ms;
-      }
-    }
-  }
-  s_sv[threadIdx.x] = tv;
-  s_sm[threadIdx.x] = tm;
-  __syncthreads();
-  unsigned long long tb = 0x7FF0000000000000ull;  // +inf
-  if (live && j == 0) {
-    double n = 0.0;
-    if (P >= 2) {
-      const int64_t g = sb + first;
-      double rf = r[g], rl = r[g + P - 1];
-      double vol = rl * rl * rl - rf * rf * rf;
-      if (vol > 0.0) {
-        n = div_rn(3.0 * (double)(P - 1), (4.0 * kPi) * vol);
-        const int q = (int)(P / 2);
-        double sv = 0.0, sm = 0.0;
-        for (int k = 0; k < q; ++k) {
-          sv = sv + s_sv[threadIdx.x + k];
-          sm = sm + s_sm[threadIdx.x + k];
-        }
-        double v = div_rn(sv, (double)q);
-        double msq = div_rn(sm, (double)q);
-        double num = pref * (v * v * v);
-        double den = (S.lnL[c] * n) * msq;
-        if (den > 0.0) {
-          double T = div_rn(num, den);
-          if (T < __longlong_as_double(0x7FF0000000000000ll))
-            tb = (unsigned long long)__double_as_longlong(T);
-        }
-      }
-    }
-    nbin[b] = n;
-    if (b == S.bin_off[c] && S.dt_cap) {
-      const double cap = S.dt_cap[c];
-      if (cap > 0.0 && cap < __longlong_as_double(0x7FF0000000000000ll)) {
-        const unsigned long long cb = (unsigned long long)__double_as_longlong(cap);
-        tb = cb < tb ? cb : tb;
-      }
-    }
-  }
-  // min over the block for the block's first segment, direct atomics for
-  // any other segment
-  unsigned long long mine = (c == s_seg0) ? tb : 0x7FF0000000000000ull;
-  if (c != s_seg0 && tb != 0x7FF0000000000000ull)
-    atomicMin((unsigned long long*)(S.dt_bits + c), tb);
-  for (int o = 16; o > 0; o >>= 1) {
-    unsigned long long y = __shfl_down_sync(0xffffffffu, mine, o);
-    mine = y < mine ? y : mine;
-  }
-  if ((threadIdx.x & 31) == 0) s_min[threadIdx.x >> 5] = mine;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned long long v = s_min[0];
-    for (int w = 1; w < 8; ++w) v = s_min[w] < v ? s_min[w] : v;
-    if (v != 0x7FF0000000000000ull) atomicMin((unsigned long long*)(S.dt_bits + s_seg0), v);
-  }
-}
-
 // One thread per pair slot: stars a = 2j and b = 2j + 1 of a segment.  The
 // pair's random draws come from its first star (counters keyed by its id,
 // or its stream, kept after the draws).  kMinB: resident 128-thread blocks
@@ -444,14 +348,6 @@ void launch_tcentral(const SegLayout& L, const double* r, const double* vr, cons
 void launch_bins(const SegLayout& L, const double* r, const double* vr, const double* vt,
                  const double* m, double* nbin, double pref, cudaStream_t st) {
   if (!L.n_bins) return;
-  const int hp = L.bin_size / 2;
-  if (hp >= 1 && hp <= 256) {
-    // one thread per pair, 256 / (bs/2) bins per block
-    const int bpb = 256 / hp;
-    k_bins_pairs<<<(unsigned)((L.n_bins + bpb - 1) / bpb), 256, 0, st>>>(
-        L.dev(), L.bin_size, pref, r, vr, vt, m, nbin, bpb);
-    return;
-  }
   k_bins<<<(unsigned)((L.n_bins + 255) / 256), 256, 0, st>>>(L.dev(), L.bin_size, pref, r, vr,
                                                              vt, m, nbin);
 }
