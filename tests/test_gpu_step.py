@@ -216,7 +216,8 @@ def test_autotuned_shapes_do_not_change_bits(g, precision):
     assert ta == {"orbit_block": 64, "sort_keys_per_thread": 16, "sort_multisplit": "match",
                   "orbit_variant": 0, "relax_variant": 0}
     assert tb["relax_variant"] in (0, 1, 2)
-    assert tb["orbit_block"] in (64, 128, 256) and tb["sort_keys_per_thread"] in (8, 16)
+    assert tb["orbit_block"] in (64, 128, 256)
+    assert tb["sort_keys_per_thread"] in (8, 16, 24, 32)  # 24 and 32: packed keys only
     assert b.stats()[0]["trials"] == 0  # the tuner's dry run left no trace
     a.step(3)
     b.step(3)
@@ -380,3 +381,24 @@ def test_packed_sort_keys_change_nothing(g_stage, precision):
         assert a.stats() == b.stats()
         a.close()
         b.close()
+
+
+def test_unsorted_state_after_the_tuned_sort_shape(g):
+    """A new state in no particular order is ordered by the keys-and-values
+    sort, which takes tiles of 16 keys per thread whatever shape the tuner
+    chose for the timestep's packed keys (24 or 32 at large N), and puts the
+    tuned shape back: the same sorted state, bit for bit, and steps go on."""
+    d = ic.plummer(2_000_000, seed=12)
+    c = _cluster(g, d, 12)
+    tuned = c.tuning()
+    c.step(1)
+    st = c.get_state()
+    perm = np.random.default_rng(1).permutation(len(st["r"]))
+    c.set_state({k: np.ascontiguousarray(st[k][perm]) for k in ("r", "vr", "vt", "m", "id")},
+                st["step"])
+    again = c.get_state()
+    for k in ("r", "vr", "vt", "m", "id", "phi"):
+        np.testing.assert_array_equal(again[k], st[k], err_msg=k)
+    assert c.tuning() == tuned
+    c.step(2)
+    assert np.all(np.isfinite(c.get_state()["r"][: int(c.nbound()[0])]))
