@@ -363,11 +363,9 @@ __global__ void k_tiefix(const int64_t* off, int n_seg, int64_t n, uint64_t* key
 // index in the segment, the key's own low 24 bits and the id are in the
 // star's payload record (lo24 in pad); runs equal in bits 24-63 are put in
 // (key, id) order by moving the words.
-__global__ void k_tiefix_packed(const int64_t* off, int n_seg, int64_t n, uint64_t* keys,
-                                const Payload* pay, uint32_t* err,
-                                unsigned long long* stats) {
-  int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= n) return;
+__device__ __forceinline__ void tiefix_packed_at(const int64_t* off, int n_seg, int64_t p,
+                                                 uint64_t* keys, const Payload* pay,
+                                                 uint32_t* err, unsigned long long* stats) {
   int c = seg_find(off, n_seg, p);
   int64_t sb = __ldg(off + c), se = __ldg(off + c + 1);
   const uint64_t hp = keys[p] >> 24;
@@ -407,6 +405,38 @@ __global__ void k_tiefix_packed(const int64_t* off, int n_seg, int64_t n, uint64
     keys[j + 1] = wv;
   }
   if (equal && stats) atomicAdd(stats + (size_t)c * kStStride + kStTies, 1ull);
+}
+
+// four positions per thread: the keys read once (two 16-byte loads), a run
+// start looked for only where two neighbours agree in bits 24-63 (a few per
+// cent of them)
+__global__ void k_tiefix_packed(const int64_t* off, int n_seg, int64_t n, uint64_t* keys,
+                                const Payload* pay, uint32_t* err,
+                                unsigned long long* stats) {
+  const int64_t p0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 4;
+  if (p0 >= n) return;
+  uint64_t k[6];  // keys[p0 - 1 .. p0 + 4]
+  if (p0 + 4 <= n) {
+    const uint4 a = reinterpret_cast<const uint4*>(keys + p0)[0];
+    const uint4 b = reinterpret_cast<const uint4*>(keys + p0)[1];
+    k[1] = ((uint64_t)a.y << 32) | a.x;
+    k[2] = ((uint64_t)a.w << 32) | a.z;
+    k[3] = ((uint64_t)b.y << 32) | b.x;
+    k[4] = ((uint64_t)b.w << 32) | b.z;
+  } else {
+    for (int i = 0; i < 4; ++i) k[1 + i] = p0 + i < n ? keys[p0 + i] : 0ull;
+  }
+  k[0] = p0 > 0 ? keys[p0 - 1] : 0ull;
+  k[5] = p0 + 4 < n ? keys[p0 + 4] : 0ull;
+  bool any = false;
+  for (int i = 0; i < 4; ++i)
+    any |= p0 + i + 1 < n && (k[1 + i] >> 24) == (k[2 + i] >> 24);
+  if (!any) return;
+  // the full test (segment bounds, run start) where a run may begin; the
+  // keys are re-read there, after any earlier run in this thread moved them
+  for (int i = 0; i < 4 && p0 + i < n; ++i)
+    if (p0 + i + 1 < n && (k[1 + i] >> 24) == (k[2 + i] >> 24))
+      tiefix_packed_at(off, n_seg, p0 + i, keys, pay, err, stats);
 }
 
 __global__ void k_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out) {
@@ -632,8 +662,9 @@ void launch_tiefix(const SegLayout& L, uint64_t* keys, uint32_t* vals,
 void launch_tiefix_packed(const SegLayout& L, uint64_t* keys, const Payload* pay,
                           uint32_t* err, cudaStream_t st) {
   if (L.n == 0) return;
-  k_tiefix_packed<<<(unsigned)((L.n + 255) / 256), 256, 0, st>>>(L.off, L.n_seg, L.n, keys, pay,
-                                                                 err, L.stats);
+  const int64_t nt = (L.n + 3) / 4;
+  k_tiefix_packed<<<(unsigned)((nt + 255) / 256), 256, 0, st>>>(L.off, L.n_seg, L.n, keys, pay,
+                                                               err, L.stats);
 }
 
 void launch_philox(int64_t n, const uint32_t* ctr, uint64_t seed, uint32_t* out,
